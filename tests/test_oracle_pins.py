@@ -1,0 +1,403 @@
+"""Pins of the float64 oracle against facts that do not come from the oracle itself:
+closed forms, brute force, library routines (numpy eigh / svd), finite
+differences and the paper's theorems.  CPU only."""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rng(seed):
+    return np.random.default_rng(seed)
+
+
+def _simplex(rng, k):
+    w = rng.random(k) + 0.1
+    return w / w.sum()
+
+
+# --------------------------------------------------------------------------- cost
+
+def test_cost_matches_entrywise_loop():
+    rng = _rng(0)
+    X = rng.standard_normal((5, 3)).astype(np.float32)
+    Y = rng.standard_normal((7, 3)).astype(np.float32)
+    C = O.sq_euclidean_cost(X, Y)
+    for i in range(5):
+        for j in range(7):
+            ref = sum((float(X[i, k]) - float(Y[j, k])) ** 2 for k in range(3))
+            assert C[i, j] == pytest.approx(ref, rel=1e-14, abs=1e-15)
+    Cn = O.sq_euclidean_cost(X, Y, normalize=True)
+    assert Cn.max() == pytest.approx(1.0, rel=1e-15)
+    assert np.allclose(Cn * C.max(), C, rtol=1e-14)
+    t = np.array([0.5, -2.0, 3.0], dtype=np.float32)
+    assert np.allclose(O.sq_euclidean_cost(X.astype(np.float64) + t, Y.astype(np.float64) + t), C,
+                       rtol=1e-12, atol=1e-12)
+    e = O.cost_entries(X, Y, [1, 4], [6, 0])
+    assert e[0] == pytest.approx(C[1, 6], rel=1e-14) and e[1] == pytest.approx(C[4, 0], rel=1e-14)
+
+
+# ------------------------------------------------------------------ c-transforms
+
+def test_c_transform_direct_summation():
+    """Eq. (foc_g)/(foc_f) written out with math.exp/math.log at a safe scale."""
+    rng = _rng(1)
+    n, m, eps = 5, 7, 0.7
+    C = rng.random((n, m))
+    a, b = _simplex(rng, n), _simplex(rng, m)
+    f, g = rng.standard_normal(n), rng.standard_normal(m)
+    gt = O.c_transform_f(f, C, a, eps)
+    ft = O.c_transform_g(g, C, b, eps)
+    for j in range(m):
+        s = sum(a[i] * math.exp((f[i] - C[i, j]) / eps) for i in range(n))
+        assert gt[j] == pytest.approx(-eps * math.log(s), rel=1e-13, abs=1e-14)
+    for i in range(n):
+        s = sum(b[j] * math.exp((g[j] - C[i, j]) / eps) for j in range(m))
+        assert ft[i] == pytest.approx(-eps * math.log(s), rel=1e-13, abs=1e-14)
+
+
+def test_c_transform_separable_cost_closed_form():
+    """C_ij = u_i + v_j, f = u + c  =>  f^{C,eps} = v - c exactly and pi = a b^T."""
+    rng = _rng(2)
+    n, m = 9, 13
+    u, v = rng.random(n), rng.random(m)
+    C = u[:, None] + v[None, :]
+    a, b = _simplex(rng, n), _simplex(rng, m)
+    for eps in (1e-3, 1e-1, 10.0):
+        c = 0.37
+        g = O.c_transform_f(u + c, C, a, eps)
+        assert np.allclose(g, v - c, rtol=0, atol=1e-12)
+        res = O.sinkhorn(C, a, b, eps, tol=1e-12, max_iter=5)
+        assert res.iters == 1
+        P = O.plan(res.f, res.g, C, a, b, eps)
+        assert np.allclose(P, a[:, None] * b[None, :], rtol=1e-10, atol=0)
+
+
+def test_single_column_closed_form():
+    """m = 1: f_i = C_i1 - g, pi_i1 = a_i after one iteration."""
+    rng = _rng(3)
+    n = 11
+    C = rng.random((n, 1))
+    a, b = _simplex(rng, n), np.ones(1)
+    res = O.sinkhorn(C, a, b, 1e-2, tol=1e-13, max_iter=3)
+    assert res.iters == 1
+    assert np.allclose(res.f + res.g[0], C[:, 0], atol=1e-13)
+    P = O.plan(res.f, res.g, C, a, b, 1e-2)
+    assert np.allclose(P[:, 0], a, rtol=1e-12)
+
+
+def test_large_eps_limit_is_product_coupling():
+    """eps -> infinity: the optimal coupling tends to a b^T (error O(1/eps))."""
+    rng = _rng(4)
+    n, m = 17, 23
+    C = rng.random((n, m))
+    a, b = _simplex(rng, n), _simplex(rng, m)
+    res = O.sinkhorn(C, a, b, 1e6, tol=1e-14, max_iter=50)
+    P = O.plan(res.f, res.g, C, a, b, 1e6)
+    ab = a[:, None] * b[None, :]
+    assert np.abs(P / ab - 1).max() < 5e-6
+
+
+def test_permutation_equivariance():
+    rng = _rng(5)
+    n, m, eps = 8, 6, 0.05
+    C = rng.random((n, m))
+    a, b = _simplex(rng, n), _simplex(rng, m)
+    f = rng.standard_normal(n) * 0.1
+    p, q = rng.permutation(n), rng.permutation(m)
+    g1 = O.c_transform_f(f, C, a, eps)
+    g2 = O.c_transform_f(f[p], C[p][:, q], a[p], eps)
+    assert np.allclose(g2, g1[q], rtol=1e-13, atol=1e-15)
+
+
+# --------------------------------------------------------------------- 2x2 case
+
+def test_two_by_two_closed_form_and_sk_rate():
+    """a = b = (1/2, 1/2): pi = [[p, 1/2-p], [1/2-p, p]] with
+    p / (1/2 - p) = exp(-(C11 + C22 - C12 - C21) / (2 eps)); rho_1 = |1 - 4p| is the
+    second singular value of R (Hermitization, proof of Thm 3.1) and Lemma 3.2
+    gives the SK contraction factor rho_1^2."""
+    C = np.array([[0.1, 0.7], [0.5, 0.2]])
+    a = b = np.array([0.5, 0.5])
+    eps = 0.3
+    t = math.exp(-(C[0, 0] + C[1, 1] - C[0, 1] - C[1, 0]) / (2 * eps))
+    p = t / (2 * (1 + t))
+    res = O.sinkhorn(C, a, b, eps, tol=1e-15, max_iter=1000)
+    P = O.plan(res.f, res.g, C, a, b, eps)
+    assert np.allclose(P, [[p, 0.5 - p], [0.5 - p, p]], atol=1e-14)
+    rho1 = abs(1 - 4 * p)
+    _, rho2 = O.spectral_modes_dense(res.f, res.g, C, a, b, eps, 1)
+    assert rho2[0] == pytest.approx(rho1 ** 2, rel=1e-10)
+    # contraction factor of the SK map on f (modulo constants)
+    f = np.array([0.4, -0.3])
+    errs = []
+    for _ in range(12):
+        g = O.c_transform_f(f, C, a, eps)
+        f = O.c_transform_g(g, C, b, eps)
+        errs.append(abs((f[0] - f[1]) - (res.f[0] - res.f[1])))
+    ratios = [errs[k + 1] / errs[k] for k in range(len(errs) - 1) if errs[k + 1] > 1e-12]
+    assert ratios[-1] == pytest.approx(rho1 ** 2, rel=1e-3)
+
+
+# --------------------------------------------------------------- eps -> 0 limit
+
+def test_bruteforce_ot_small_eps():
+    """n = m = 6 uniform: W0 (permutation enumeration) <= <pi_eps, C> and
+    W0 <= W_eps <= W0 + eps log n; pi_eps -> the optimal permutation / n."""
+    rng = _rng(7)
+    n = 6
+    X, Y = rng.random((n, 2)), rng.random((n, 2))
+    C = O.sq_euclidean_cost(X, Y)
+    a = b = np.full(n, 1.0 / n)
+    w0, perm = O.bruteforce_ot(C)
+    # independent check of the enumeration itself
+    assert w0 == pytest.approx(min(sum(C[i, s[i]] for i in range(n)) / n
+                                   for s in itertools.permutations(range(n))), rel=1e-15)
+    Pperm = np.zeros((n, n))
+    Pperm[np.arange(n), perm] = 1.0 / n
+    prev = None
+    # SK-NR with the full a-complement basis (a Newton method) reaches tight
+    # marginals at small eps where plain Sinkhorn stalls.
+    B = np.eye(n)[:, 1:] - np.ones((n, 1)) * a[1:][None, :]
+    for eps in (1e-1, 3e-2, 1e-2, 3e-3, 1e-3):
+        res = O.sknr(C, a, b, eps, B, tol=1e-10, max_iter=2000, record=True)
+        assert res.err_history[-1] < 1e-9
+        P = O.plan(res.f, res.g, C, a, b, eps)
+        w_eps = O.primal_value(P, C, a, b, eps)
+        assert w0 <= (P * C).sum() + 1e-9
+        assert w0 - 1e-9 <= w_eps <= w0 + eps * math.log(n) + 1e-9
+        dist = np.abs(P - Pperm).sum()
+        if prev is not None:
+            assert dist <= prev + 1e-12
+        prev = dist
+    assert prev < 1e-6
+
+
+# ------------------------------------------------------------ derivatives / FD
+
+def test_semidual_gradient_and_hessian_finite_differences():
+    rng = _rng(8)
+    n, m, eps = 7, 9, 0.2
+    C = rng.random((n, m))
+    a, b = _simplex(rng, n), _simplex(rng, m)
+    f = rng.standard_normal(n) * 0.1
+    gr = O.grad_semi(f, C, a, b, eps)
+    H = O.hess_semi(f, C, a, b, eps)
+    h = 1e-5
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = h
+        fd = (O.q_semi(f + e, C, a, b, eps) - O.q_semi(f - e, C, a, b, eps)) / (2 * h)
+        assert gr[i] == pytest.approx(fd, abs=1e-8)
+        fdg = (O.grad_semi(f + e, C, a, b, eps) - O.grad_semi(f - e, C, a, b, eps)) / (2 * h)
+        assert np.allclose(H[:, i], fdg, atol=1e-6)
+    assert np.allclose(H @ np.ones(n), 0, atol=1e-12)
+    assert abs(gr.sum()) < 1e-13
+    assert np.allclose(H, H.T, atol=1e-13)
+    assert np.linalg.eigvalsh(H).max() < 1e-12
+
+
+def test_dual_gradient_finite_differences():
+    """Eq. (dQ): the directional derivative of Q_eps, against finite differences."""
+    rng = _rng(9)
+    n, m, eps = 5, 6, 0.3
+    C = rng.random((n, m))
+    a, b = _simplex(rng, n), _simplex(rng, m)
+    f, g = rng.standard_normal(n) * 0.1, rng.standard_normal(m) * 0.1
+    f1, g1 = rng.standard_normal(n), rng.standard_normal(m)
+    P = O.plan(f, g, C, a, b, eps)
+    dq = f1 @ a + g1 @ b - (P * (f1[:, None] + g1[None, :])).sum()
+    h = 1e-6
+    fd = (O.q_dual(f + h * f1, g + h * g1, C, a, b, eps)
+          - O.q_dual(f - h * f1, g - h * g1, C, a, b, eps)) / (2 * h)
+    assert dq == pytest.approx(fd, abs=1e-8)
+    Hd = O.hess_dual(f, g, C, a, b, eps)
+    x = np.concatenate([f1, g1])
+    d2 = -(1 / eps) * (P * (f1[:, None] + g1[None, :]) ** 2).sum()
+    assert x @ Hd @ x == pytest.approx(d2, rel=1e-12)
+
+
+# ---------------------------------------------------------- spectral structure
+
+def _solved(n=30, m=40, eps=0.03, seed=10):
+    rng = _rng(seed)
+    X, Y = rng.random((n, 2)), rng.random((m, 2))
+    C = O.sq_euclidean_cost(X, Y, normalize=True)
+    a, b = _simplex(rng, n), _simplex(rng, m)
+    res = O.sinkhorn(C, a, b, eps, tol=1e-14, max_iter=200000)
+    assert res.converged
+    return C, a, b, eps, res.f, res.g
+
+
+def test_structure_theorem_invariants():
+    """Thm 3.1: spectrum of K in [-1, 1], symmetric, rho_0 = 1 with eigenvector
+    1 (+) 1; eigenvalues = +- singular values of R (numpy svd); the dual Hessian
+    in L2 coordinates is -(1/eps)(Id + K)."""
+    C, a, b, eps, f, g = _solved()
+    n, m = C.shape
+    K = O.operator_K(f, g, C, a, b, eps)
+    one = np.ones(n + m)
+    assert np.allclose(K @ one, one, atol=1e-11)
+    lam = np.sort(np.linalg.eigvals(K).real)
+    assert lam.max() == pytest.approx(1.0, abs=1e-10)
+    assert lam.min() >= -1 - 1e-10
+    k = min(n, m)
+    assert np.allclose(lam[:k], -lam[::-1][:k], atol=1e-9)
+    s = np.linalg.svd(O.R_matrix(f, g, C, a, b, eps), compute_uv=False)
+    assert np.allclose(lam[::-1][:k], s, atol=1e-9)
+    D = np.sqrt(np.concatenate([a, b]))
+    Hl2 = O.hess_dual(f, g, C, a, b, eps) / D[:, None] / D[None, :]
+    Ksym = np.zeros((n + m, n + m))
+    R = O.R_matrix(f, g, C, a, b, eps)
+    Ksym[:n, n:] = R
+    Ksym[n:, :n] = R.T
+    assert np.allclose(Hl2, -(1 / eps) * (np.eye(n + m) + Ksym), atol=1e-7)
+
+
+def test_semidual_hessian_identity():
+    """App. A.4 (Eq. semidual_Hessian): at the optimum the semi-dual Hessian is
+    -(1/eps)(Id - Op(pi) o Op(pi)^T) in L2(a)."""
+    C, a, b, eps, f, g = _solved()
+    H = O.hess_semi(f, C, a, b, eps)
+    M = O.semidual_operator_M(f, g, C, a, b, eps)
+    assert np.allclose(H, -(1 / eps) * (np.diag(a) - a[:, None] * M), atol=1e-8)
+    # Op(pi) and Op(pi)^T against the dense operator
+    rng = _rng(11)
+    g1, f1 = rng.standard_normal(C.shape[1]), rng.standard_normal(C.shape[0])
+    Kd = O.operator_K(f, g, C, a, b, eps)
+    n = C.shape[0]
+    out = Kd @ np.concatenate([f1, g1])
+    assert np.allclose(out[:n], O.op_pi(g1, f, g, C, a, b, eps))
+    assert np.allclose(out[n:], O.op_pi_T(f1, f, g, C, a, b, eps))
+
+
+def test_subspace_iteration_matches_eigh():
+    C, a, b, eps, f, g = _solved(n=60, m=70, eps=0.05, seed=12)
+    ell = 5
+    Vd, rd = O.spectral_modes_dense(f, g, C, a, b, eps, ell)
+    Vs, rs, it, res = O.spectral_modes_subspace(f, g, C, a, b, eps, ell, oversample=8,
+                                                tol=1e-10, max_iter=2000)
+    assert res <= 1e-10
+    assert np.allclose(rs, rd, atol=1e-9)
+    # a-orthonormal, orthogonal to constants, same subspace
+    G = Vs.T @ (a[:, None] * Vs)
+    assert np.allclose(G, np.eye(ell), atol=1e-10)
+    assert np.abs(a @ Vs).max() < 1e-10
+    Pd = Vd @ Vd.T @ np.diag(a)
+    assert np.allclose(Pd @ Vs, Vs, atol=1e-6)
+    assert 0 < rd[-1] <= rd[0] < 1
+
+
+def test_splitmix64_reference_outputs():
+    with open(os.path.join(GOLDEN, "splitmix64_seed0.txt")) as fh:
+        vals = [int(line, 16) for line in fh.read().splitlines()
+                if line.strip() and not line.startswith("#")]
+    gamma = 0x9E3779B97F4A7C15
+    for k, v in enumerate(vals):
+        assert O.eot_oracle._splitmix64(((k + 1) * gamma) & ((1 << 64) - 1)) == v
+    u = O.splitmix64_uniform(0, 3)
+    assert np.allclose(u, [2 * (v >> 11) / 2.0 ** 53 - 1 for v in vals], rtol=0, atol=0)
+
+
+# -------------------------------------------------------- rates (Lemma 3.2, Thm 4.2)
+
+def test_sk_and_sknr_rates():
+    """Lemma 3.2: SK contracts f - f* by rho_1^2.  Thm 4.2: SK-NR(l) with the
+    exact modes V_l(eps) contracts by rho_{l+1}^2."""
+    C, a, b, eps, fs, gs = _solved(n=40, m=50, eps=0.02, seed=3)
+    V, rho2 = O.spectral_modes_dense(fs, gs, C, a, b, eps, 6)
+
+    def err(f):
+        d = f - fs
+        d = d - d @ a
+        return math.sqrt(a @ d ** 2)
+
+    f = np.zeros(C.shape[0])
+    errs = []
+    for _ in range(60):
+        g = O.c_transform_f(f, C, a, eps)
+        f = O.c_transform_g(g, C, b, eps)
+        errs.append(err(f))
+    assert errs[-1] / errs[-2] == pytest.approx(rho2[0], rel=2e-3)
+    for ell in (1, 2):
+        f = np.zeros(C.shape[0])
+        errs = []
+        for _ in range(30):
+            f = O.sknr(C, a, b, eps, V[:, :ell], tol=0, max_iter=1, f0=f).f
+            errs.append(err(f))
+            if errs[-1] < 1e-10:
+                break
+        assert errs[-1] / errs[-2] == pytest.approx(rho2[ell], rel=1e-2)
+
+
+def test_sknr_full_basis_is_newton_and_monotone():
+    """SK-NR(n-1) with V spanning the a-complement of the constants reaches the
+    same optimum as a dense direct Newton solve and as tight Sinkhorn; the
+    semi-dual value never decreases along the iterates (Thm 4.2, step 1)."""
+    rng = _rng(13)
+    n, m, eps = 6, 8, 0.05
+    C = O.sq_euclidean_cost(rng.random((n, 2)), rng.random((m, 2)), normalize=True)
+    a, b = _simplex(rng, n), _simplex(rng, m)
+    sk = O.sinkhorn(C, a, b, eps, tol=1e-14, max_iter=100000)
+    fN = O.dense_newton(C, a, b, eps, f0=O.sinkhorn(C, a, b, eps, tol=1e-2).f)
+    B = np.eye(n)[:, 1:] - np.ones((n, 1)) * a[1:][None, :]
+    f_start = O.sinkhorn(C, a, b, eps, tol=1e-2).f
+    res = O.sknr(C, a, b, eps, B, tol=1e-13, max_iter=50, f0=f_start, record=True)
+    # inside the basin the full-space Newton step converges quadratically
+    assert res.converged and res.iters <= 8
+    e = res.err_history
+    assert e[-2] < 1e-6 and e[-1] < 1e-13
+    for fx in (fN, res.f):
+        d = fx - sk.f
+        assert np.abs(d - d @ a).max() < 1e-9
+    q = res.qsemi_history
+    assert all(q[k + 1] >= q[k] - 1e-15 for k in range(len(q) - 1))
+    sk2 = O.sinkhorn(C, a, b, eps, tol=1e-12, max_iter=20, record=True)
+    qs = []
+    f = np.zeros(n)
+    for _ in range(20):
+        f = O.c_transform_g(O.c_transform_f(f, C, a, eps), C, b, eps)
+        qs.append(O.q_semi(f, C, a, b, eps))
+    assert all(qs[k + 1] >= qs[k] - 1e-15 for k in range(len(qs) - 1))
+    assert len(sk2.err_history) >= 1
+
+
+def test_gap_vanishes_and_gauge():
+    C, a, b, eps, f, g = _solved(n=25, m=35, eps=0.05, seed=14)
+    ev = O.evaluate(f, g, C, a, b, eps)
+    assert ev["l1"] < 1e-12 and abs(ev["gap"]) < 1e-12
+    assert ev["q_dual"] == pytest.approx(ev["q_semi"], abs=1e-12)
+    P = O.plan(f, g, C, a, b, eps)
+    assert O.primal_value(P, C, a, b, eps) == pytest.approx(ev["q_dual"], abs=1e-12)
+    fn, gn = O.gauge_normalize(f + 3.0, g - 3.0, a, b)
+    assert fn @ a == pytest.approx(gn @ b, abs=1e-13)
+    assert np.allclose(O.plan(fn, gn, C, a, b, eps), P, rtol=1e-10)
+
+
+def test_eps_schedule():
+    lv = O.eps_schedule(1e-1, 1e-3, 0.5)
+    assert len(lv) == 8 and lv[0] == 1e-1 and lv[-1] == 1e-3
+    assert lv[-2] == pytest.approx(1.5625e-3)
+    assert O.eps_schedule(1e-3, 1e-3, 0.5) == [1e-3]
+
+
+def test_continuation_sknr_beats_sk_iterations():
+    """Sec. 5 (qualitative): on a clustered cloud the spectral warm start needs
+    far fewer iterations than Sinkhorn at the final eps, same optimum."""
+    p = W.gaussian_mixture(160, 160, seed=1)
+    C = O.sq_euclidean_cost(p.X, p.Y, normalize=True)
+    sk, hs = O.continuation(C, p.a, p.b, 2e-3, tol=1e-8, eps_start=1e-1, ell=0,
+                            return_levels=True)
+    nr, hn = O.continuation(C, p.a, p.b, 2e-3, tol=1e-8, eps_start=1e-1, ell=20,
+                            return_levels=True)
+    assert hn[-1]["iters"] * 4 < hs[-1]["iters"]
+    f1, g1 = O.gauge_normalize(sk.f, sk.g, p.a, p.b)
+    f2, g2 = O.gauge_normalize(nr.f, nr.g, p.a, p.b)
+    assert np.abs(f1 - f2).max() < 1e-5 * 2e-3 * 1e3
