@@ -1,0 +1,224 @@
+/*
+ * eot.h -- C ABI of the GB300 entropic optimal transport solver (SK-NR).
+ *
+ * Problem (paper Sec. 2, Eq. primal_EOT / dual_EOT): two discrete probability
+ * vectors a = alpha (n) and b = beta (m), a cost C (n x m) or two point clouds
+ * X (n x d), Y (m x d) with C_ij = ||x_i - y_j||^2, and a regularisation eps > 0.
+ * The solver returns Kantorovich potentials f (n), g (m); the coupling is
+ * pi_ij = a_i b_j exp((f_i + g_j - C_ij) / eps)  (Eq. Optimal_P_epsilon).
+ *
+ * Methods: log-domain Sinkhorn (Eq. SK_iterations) and SK-NR(l) (Algorithm 4.1):
+ * Sinkhorn sweeps followed by a Newton-Raphson step of the semi-dual objective
+ * (Eq. def_Q_semi) restricted to l low-frequency modes V_l, accepted only if it
+ * increases the semi-dual value; V_l comes from a partial eigendecomposition of
+ * Op(pi) o Op(pi)^T (Eq. semidual_Hessian) at a larger eps' (Sec. 4), with eps
+ * continuation (Sec. 5).
+ *
+ * Conventions shared by every entry point:
+ *  - All arrays are dense and row-major.  Sizes are element counts.
+ *  - Pointers are host or device memory as stated per call (eot_mem for the
+ *    problem-level calls; "device" calls take device pointers only).
+ *  - Inputs are borrowed for the duration of the call; outputs are caller
+ *    allocated.  Nothing returned by the library needs freeing except an
+ *    eot_server (eot_server_destroy).
+ *  - Errors are return codes; no call throws or aborts.  eot_last_error()
+ *    gives a thread-local message for the last non-OK status of this thread.
+ *  - Device work runs on the CUDA device that is current on the calling thread.
+ *    There is no CPU fallback: without a usable device every compute call
+ *    returns EOT_ECUDA.
+ */
+#ifndef EOT_H
+#define EOT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EOT_OK = 0,             /* converged (or the call completed)                      */
+    EOT_NOT_CONVERGED = 1,  /* max_iter reached; potentials are still returned        */
+    EOT_PENDING = 2,        /* server: the request is not finished yet                */
+    EOT_EINVAL = -1,        /* invalid argument (message in eot_last_error)           */
+    EOT_ENOMEM = -2,        /* device allocation failed or admission budget exceeded  */
+    EOT_ENUMERIC = -3,      /* non-finite values or potentials out of the safe range  */
+    EOT_ETIMEDOUT = -4,     /* a bounded device wait gave up                          */
+    EOT_ECUDA = -5,         /* CUDA runtime error or no usable device                 */
+    EOT_ENOTFOUND = -6      /* server: unknown ticket                                 */
+} eot_status;
+
+typedef enum { EOT_MEM_HOST = 0, EOT_MEM_DEVICE = 1 } eot_mem;
+
+/* Arithmetic of the O(nm) passes.
+ *  FP64: float64 cost and float64 exponentials (small problems, tight tolerances).
+ *  FP32: float32 stored cost; float32 exponentials and sums; potentials kept in
+ *        float64 and the exponent f_i + g_j - C_ij formed without rounding error
+ *        before the division by eps (so the marginal error can reach ~1e-7).
+ *  SPLIT_TC: cost formed on the fly from X, Y on the tensor cores (reserved;
+ *        returns EOT_EINVAL in this version). */
+typedef enum { EOT_PREC_FP64 = 0, EOT_PREC_FP32 = 1, EOT_PREC_SPLIT_TC = 2 } eot_prec;
+
+/* Semi-dual Hessian used by the Newton step (Eq. d2Q_semi):
+ *  EOT_HESS_DIAG_ALPHA: -(1/eps) [V^T D_a V - W^T D_b^{-1} W], W = pi^T V
+ *                       (D_r replaced by D_a; equal at the optimum; 3 passes).
+ *  EOT_HESS_EXACT:      D_r with r = pi(f, f^{C,eps}) 1 (one extra row pass). */
+typedef enum { EOT_HESS_DIAG_ALPHA = 0, EOT_HESS_EXACT = 1 } eot_hessian;
+
+typedef struct {
+    int32_t n, m;          /* numbers of source / target points, >= 1                 */
+    int32_t d;             /* 0: C is given; > 0: X (n x d), Y (m x d) given          */
+    const double *a;       /* (n) positive weights summing to 1 (renormalised)        */
+    const double *b;       /* (m) positive weights summing to 1 (renormalised)        */
+    const void *C;         /* (n x m) cost: double for FP64, float otherwise; or NULL */
+    const void *X, *Y;     /* point clouds: double for FP64, float otherwise; or NULL */
+    eot_mem mem;           /* memory space of a, b, C, X, Y, f_init and the outputs   */
+    int32_t normalize_cost;/* 1: divide C by max_ij C_ij (after forming it from X, Y) */
+    double eps;            /* target regularisation eps > 0                           */
+    const double *f_init;  /* optional warm start f (n) (NULL: zeros; Alg. 4.1 line 1) */
+} eot_problem;
+
+typedef struct {
+    double tol;             /* omega: stop when ||pi1-a||_1 + ||pi^T1-b||_1 < tol     */
+    int32_t max_iter;       /* per continuation level                                 */
+    int32_t ell;            /* number of low-frequency modes l; 0 = plain Sinkhorn    */
+    double eps_start;       /* continuation start; <= eps: a single level at eps      */
+    double eps_factor;      /* geometric factor in (0, 1) between levels              */
+    double level_tol;       /* tolerance of intermediate levels (<= 0: use tol)        */
+    int32_t sequential_modes; /* 1: recompute V at every level; 0: once at eps_start  */
+    int32_t oversample;     /* extra block columns of the subspace iteration           */
+    double eig_tol;         /* Ritz residual ||M z - theta z||_a stopping threshold     */
+    int32_t eig_max_iter;   /* subspace iteration cap                                  */
+    eot_prec prec;
+    eot_hessian hessian;
+    int32_t poll_every;     /* iterations between host convergence polls (0: auto)    */
+    void *stream;           /* cudaStream_t to run on; NULL: the library's own stream */
+} eot_options;
+
+typedef struct {
+    eot_status status;
+    int32_t iters;          /* Algorithm 4.1 iterations at the final level            */
+    int32_t total_iters;    /* over all continuation levels                           */
+    int32_t nr_accepted, nr_rejected; /* Newton steps at the final level              */
+    int32_t levels;         /* continuation levels run                                */
+    int32_t eig_iters;      /* subspace iterations over all levels                    */
+    double l1_marginal;     /* ||pi1-a||_1 + ||pi^T1-b||_1 of the returned (f, g)      */
+    double row_l1, col_l1;
+    double q_dual;          /* Q_eps(f, g), Eq. def_Q                                  */
+    double q_semi;          /* Q_semi(f), Eq. def_Q_semi                               */
+    double dual_gap;        /* <pi1-a,f> + <pi^T1-b,g> + eps (sum pi - 1)               */
+    double seconds;         /* device time of the whole solve                          */
+    double seconds_eig;     /* part of it spent computing modes                        */
+    double seconds_last_level; /* device time of the final eps level incl. its modes   */
+} eot_result;
+
+/* Fill *opt with defaults: tol 1e-6, max_iter 100000, ell 0, single level,
+ * eps_factor 0.5, sequential modes, oversample 10, eig_tol 1e-2, eig_max_iter 100,
+ * FP32, Hessian with D_a, automatic polling, library stream. */
+void eot_default_options(eot_options *opt);
+
+/* Solve one problem (Algorithm 4.1 with eps continuation).  f_out (n) and
+ * g_out (m) receive float64 potentials in the memory space of prob->mem,
+ * gauge-normalised so that <f,a> = <g,b> (Sec. 2: the dual is invariant under
+ * (f, g) + c(1, -1)).  res (host, may be NULL) receives the statistics.
+ * Returns EOT_OK, EOT_NOT_CONVERGED, or a negative error. */
+eot_status eot_solve(const eot_problem *prob, const eot_options *opt,
+                     double *f_out, double *g_out, eot_result *res);
+
+/* Solve count independent problems of uneven sizes in one persistent launch
+ * (plain Sinkhorn; opt->ell must be 0).  Arrays of count pointers; results[k]
+ * (host) holds each problem's status; the call returns the worst status.  Each
+ * problem's result does not depend on which others share the batch. */
+eot_status eot_solve_batch(int32_t count, const eot_problem *probs, const eot_options *opt,
+                           double *const *f_out, double *const *g_out, eot_result *results);
+
+/* ---------------------------------------------------------------- serving */
+typedef struct eot_server eot_server;
+
+/* Create a server with a background scheduler that batches incoming requests
+ * continuously: a request is admitted as soon as a slot is free and its device
+ * footprint fits in hbm_budget_bytes; admitted requests share the device.
+ * Potentials of requests submitted with a cloud_id stay resident and
+ * warm-start later requests on the same cloud.  Ownership: *srv until destroy. */
+eot_status eot_server_create(const eot_options *opt, size_t hbm_budget_bytes,
+                             int32_t max_slots, eot_server **srv);
+/* Deep-copies the problem (host memory only) and returns a ticket. */
+eot_status eot_server_submit(eot_server *srv, const eot_problem *prob, uint64_t cloud_id,
+                             uint64_t *ticket);
+/* EOT_PENDING until done; then copies f (n), g (m) to host memory and fills res
+ * (which may be NULL), returns the request's status and forgets the ticket.
+ * Unknown tickets give EOT_ENOTFOUND. */
+eot_status eot_server_poll(eot_server *srv, uint64_t ticket, double *f_out, double *g_out,
+                           eot_result *res);
+/* Latency percentiles (submit -> completion, seconds) and completed solves per
+ * second since creation. */
+eot_status eot_server_stats(eot_server *srv, double *p50_s, double *p99_s,
+                            double *solves_per_s);
+void eot_server_destroy(eot_server *srv);
+
+/* --------------------------------------------------- single hot-path steps
+ * Device-pointer entry points for the individual passes.  They run on `stream`
+ * (NULL: the legacy default stream) and return once the work is enqueued.
+ * C is float32 (n x m, row-major, device). */
+
+typedef enum { EOT_SIDE_COL = 0, EOT_SIDE_ROW = 1 } eot_side;
+
+/* One (C,eps)-transform (Eq. foc_g for COL, Eq. foc_f for ROW):
+ *   COL: out_j = -eps log sum_i a_i exp((f_i - C_ij)/eps)      (pot = f, w = a)
+ *   ROW: out_i = -eps log sum_j b_j exp((g_j - C_ij)/eps)      (pot = g, w = b)
+ * shift (the current potential on the output side, or NULL) is a reference
+ * point: the sum is formed relative to it, and log_ratio (optional, same length
+ * as out) receives (shift - out)/eps, the log of the marginal ratio of
+ * pi(pot, shift) on the output side (0 at a fixed point).  With shift NULL the
+ * call runs two passes (the first computes a reference).
+ * All pointers are device pointers: pot, w, shift float64; out, log_ratio float64. */
+eot_status eot_ctransform(eot_side side, int32_t n, int32_t m, const float *C,
+                          const double *pot, const double *w, const double *shift,
+                          double eps, double *out, double *log_ratio, void *stream);
+
+/* Coupling products (Eq. def_Op_pi, def_Op_pi_T) at potentials (f, g):
+ *   COL: out (m x k) = Op(pi)^T Z,  out_j = sum_i exp((f_i+g_j-C_ij)/eps) a_i Z_i
+ *   ROW: out (n x k) = Op(pi) Z,    out_i = sum_j exp((f_i+g_j-C_ij)/eps) b_j Z_j
+ * Z is float32 row-major ((n or m) x k), 1 <= k <= 64; out float32.  Device
+ * pointers. */
+eot_status eot_kapply(eot_side side, int32_t n, int32_t m, int32_t k, const float *C,
+                      const double *f, const double *g, const double *a, const double *b,
+                      double eps, const float *Z, float *out, void *stream);
+
+/* Squared Euclidean cost C_ij = ||x_i - y_j||^2 (float64 arithmetic, one
+ * rounding to float32), divided by max_ij C_ij when normalize != 0.  X (n x d),
+ * Y (m x d) float32, C float32 (n x m); device pointers.  cmax_out (device,
+ * optional) receives the float64 maximum before normalisation. */
+eot_status eot_cost(int32_t n, int32_t m, int32_t d, const float *X, const float *Y,
+                    int32_t normalize, float *C, double *cmax_out, void *stream);
+
+/* Low-frequency modes V_l(eps) (Sec. 4; Eq. semidual_Hessian): the ell leading
+ * non-trivial eigenvectors of Op(pi) o Op(pi)^T at potentials (f, g), by block
+ * subspace iteration with Rayleigh-Ritz (block ell + oversample), orthonormal in
+ * L2(a) and a-orthogonal to the constants.  V (n x ell, float64, device, row
+ * major) is both the optional start block (if use_V_as_start) and the output;
+ * rho2 (ell, float64, device, optional) receives the Ritz values rho_k^2.
+ * iters_out / resid_out (host, optional): iterations and final max residual. */
+eot_status eot_spectral_modes(int32_t n, int32_t m, const float *C, const double *f,
+                              const double *g, const double *a, const double *b, double eps,
+                              int32_t ell, int32_t oversample, double tol, int32_t max_iter,
+                              int32_t use_V_as_start, double *V, double *rho2,
+                              int32_t *iters_out, double *resid_out, void *stream);
+
+/* Marginal errors of pi(f, g) computed on the device (float32 exponentials,
+ * float64 sums): row_l1 = ||pi1 - a||_1, col_l1 = ||pi^T1 - b||_1 (host outputs). */
+eot_status eot_marginal_error(int32_t n, int32_t m, const float *C, const double *f,
+                              const double *g, const double *a, const double *b, double eps,
+                              double *row_l1, double *col_l1, void *stream);
+
+/* Thread-local description of the last non-OK status returned on this thread. */
+const char *eot_last_error(void);
+
+/* Library version string. */
+const char *eot_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EOT_H */

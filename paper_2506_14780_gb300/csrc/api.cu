@@ -1,0 +1,1545 @@
+// Host driver and C ABI of the solver (include/eot.h).
+//
+// One eot_solve runs, on one stream:
+//   set-up      weights (normalised, logs), cost (given, or built from X, Y;
+//               optional normalisation to max 1), cost statistics;
+//   per level   (eps continuation, Sec. 5)  level constants, split arrays,
+//               the first column transform g_1 = f_0^{C,eps} (Alg. 4.1 line 3),
+//               then a CUDA-graph while loop over iterations of Algorithm 4.1:
+//                 Sinkhorn:  row pass (line 4) -> column pass at f_k (marginal
+//                            test, line 3 of the next iteration);
+//                 SK-NR(l):  row pass -> fused column pass (test, h, W = pi^T V)
+//                            -> projected Newton system -> f' = f_k + V Delta
+//                            -> column pass at f' (value test, lines 14-16);
+//               then, if the next level needs them, the modes V_l(eps) by block
+//               subspace iteration (another graph while loop);
+//   finish      evaluation passes, scores, gauge normalisation, copy-out.
+// The host synchronises once per solve.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "eot.h"
+#include "eot_internal.h"
+
+namespace eotk {
+
+// ---- kernels defined in the other translation units ----------------------
+cudaError_t launch_col_pass(const Prob* dP, const Prob& hP, int mode, cudaStream_t s);
+cudaError_t launch_row_pass(const Prob* dP, const Prob& hP, int mode, cudaStream_t s);
+cudaError_t launch_split(const Prob* dP, const double* p, const double* logw, int len, Split so,
+                         cudaStream_t s);
+
+cudaError_t launch_colacc(const AccArgs& a, int ncolblk, cudaStream_t s);
+cudaError_t launch_rowacc(const AccArgs& a, int nrowblk, cudaStream_t s);
+int acc_template_k(int k);
+void init_acc_attributes();
+
+__global__ void wgram_partial_kernel(const float*, const float*, const double*, int, int, int,
+                                     const double*, const float*, double*, double*, const State*,
+                                     int);
+__global__ void wgram_reduce_kernel(const double*, int, int, double*, const State*, int);
+__global__ void newton_kernel(const Prob*, const double*, const double*, const double*);
+__global__ void fprime_kernel(const Prob*);
+__global__ void eig_small_kernel(int, int, int, const double*, const double*, const double*,
+                                 float*, double*, double*, int*);
+__global__ void apply_kernel(const float*, const double*, const float*, int, int, float*);
+__global__ void init_block_kernel(float*, int, int, unsigned long long, const float*, int);
+__global__ void take_cols_kernel(const float*, int, int, int, float*);
+__global__ void grad_weights_kernel(const Prob*, double*);
+__global__ void loop_ctl_kernel(cudaGraphConditionalHandle, State*, int, int);
+__global__ void eig_ctl_kernel(State*, const double*, const int*);
+__global__ void level_setup_kernel(Prob*, double, float, double, int, int);
+__global__ void eig_setup_kernel(State*, double, int, int);
+__global__ void cost_max_kernel(int, int, int, const float*, const float*, unsigned long long*);
+__global__ void cost_fill_kernel(int, int, int, const float*, const float*,
+                                 const unsigned long long*, int, float*);
+__global__ void cost_scale_kernel(size_t, const float*, double, float*);
+__global__ void cost_stats_kernel(size_t, const float*, unsigned*, unsigned*);
+__global__ void weights_kernel(int, const double*, double*, double*, unsigned*, int);
+__global__ void cost_stats_f64_kernel(size_t, const double*, unsigned long long*, unsigned*);
+__global__ void final_eval_kernel(const Prob*, double*, double*, double*);
+__global__ void normalize_buffers_kernel(Prob*);
+__global__ void reset_buffers_kernel(State*);
+
+constexpr int kGChunkHost = 64;
+
+// ---------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------
+static thread_local std::string t_err;
+
+static eot_status fail(eot_status s, const std::string& msg) {
+  t_err = msg;
+  return s;
+}
+
+#define CUDA_TRY(expr)                                                                   \
+  do {                                                                                   \
+    cudaError_t _e = (expr);                                                             \
+    if (_e != cudaSuccess) {                                                             \
+      return fail(_e == cudaErrorMemoryAllocation ? EOT_ENOMEM : EOT_ECUDA,              \
+                  std::string(#expr) + ": " + cudaGetErrorString(_e));                   \
+    }                                                                                    \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// Per-device context
+// ---------------------------------------------------------------------------
+struct DeviceCtx {
+  int dev = -1;
+  int nsm = 0;
+  cudaStream_t stream = nullptr;
+  bool cond_ok = true;   // graph conditional nodes usable
+};
+
+// One context (and stream) per calling thread and device, so that solves issued
+// from different threads (the server's workers) overlap on the device.
+static thread_local std::map<int, std::unique_ptr<DeviceCtx>> g_ctx;
+
+static eot_status get_ctx(DeviceCtx** out) {
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  auto it = g_ctx.find(dev);
+  if (it != g_ctx.end()) {
+    *out = it->second.get();
+    return EOT_OK;
+  }
+  auto c = std::make_unique<DeviceCtx>();
+  c->dev = dev;
+  CUDA_TRY(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev));
+  CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+  init_acc_attributes();
+  const char* e = getenv("EOT_HOST_LOOP");
+  c->cond_ok = !(e && e[0] == '1');
+  *out = c.get();
+  g_ctx[dev] = std::move(c);
+  return EOT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Device memory arena (one allocation per solver)
+// ---------------------------------------------------------------------------
+struct Arena {
+  char* base = nullptr;
+  size_t off = 0;
+  template <class T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+    off += std::max<size_t>(count, 1) * sizeof(T);
+    return p;
+  }
+};
+
+static int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------------------
+// Solver: buffers, tilings and captured graphs for one problem shape.
+// ---------------------------------------------------------------------------
+struct Solver {
+  DeviceCtx* ctx = nullptr;
+  int n = 0, m = 0, ell = 0, p = 0;
+  bool own_cost = false;
+  // tilings
+  int nstripe = 1, rows_per_stripe = 0, ncolblk = 0;
+  int nseg = 1, cols_per_seg = 0, nrowblk = 0;
+  int s4_nseg = 1, s4_seglen = 0, s4_ncolblk = 0, s4_K = 0;
+  int ek_K = 0, kc_nseg = 1, kc_seglen = 0, kr_nseg = 1, kr_seglen = 0, kr_nrowblk = 0;
+  // memory
+  void* mem = nullptr;
+  size_t bytes = 0;
+  Prob hP{};
+  Prob* dP = nullptr;
+  State* dSt = nullptr;
+  float* Cbuf = nullptr;
+  double *a_in = nullptr, *b_in = nullptr, *f_init = nullptr;
+  double *f_out = nullptr, *g_out = nullptr, *scores = nullptr;
+  unsigned* stats = nullptr;             // [0] max|C| bits, [1] bad C, [2] bad a/b
+  unsigned long long* cmax64 = nullptr;
+  float* X = nullptr;
+  float* Y = nullptr;
+  // SK-NR
+  float *V = nullptr, *W = nullptr, *s4part = nullptr;
+  unsigned *s4cnt = nullptr, *s4gcnt = nullptr;
+  double *s4blk = nullptr, *gpart = nullptr, *gvpart = nullptr, *WtW = nullptr, *gw = nullptr,
+         *dw = nullptr;
+  // modes
+  float *Zb = nullptr, *Xb = nullptr, *Yb = nullptr, *Bm = nullptr, *kcpart = nullptr,
+        *krpart = nullptr;
+  unsigned *kccnt = nullptr, *krcnt = nullptr;
+  double *epart = nullptr, *evpart = nullptr, *GXX = nullptr, *Tm = nullptr, *cvec = nullptr,
+         *theta = nullptr, *resid = nullptr;
+  int* efail = nullptr;
+  // host mirrors
+  State* hSt = nullptr;
+  double* hScores = nullptr;
+  // graphs
+  cudaGraphExec_t ex_sk = nullptr, ex_sknr = nullptr, ex_eig = nullptr;
+  cudaGraph_t gr_sk = nullptr, gr_sknr = nullptr, gr_eig = nullptr;
+  int unroll_sk = 4, unroll_sknr = 2;
+
+  ~Solver() {
+    if (ex_sk) cudaGraphExecDestroy(ex_sk);
+    if (ex_sknr) cudaGraphExecDestroy(ex_sknr);
+    if (ex_eig) cudaGraphExecDestroy(ex_eig);
+    if (gr_sk) cudaGraphDestroy(gr_sk);
+    if (gr_sknr) cudaGraphDestroy(gr_sknr);
+    if (gr_eig) cudaGraphDestroy(gr_eig);
+    if (mem) cudaFree(mem);
+    if (hSt) cudaFreeHost(hSt);
+    if (hScores) cudaFreeHost(hScores);
+  }
+
+  void plan_tiles() {
+    const int nsm = ctx->nsm;
+    const int target = 4 * nsm;
+    ncolblk = ceil_div(m, kColTile);
+    nstripe = std::max(1, std::min(ceil_div(n, 32), (target + ncolblk - 1) / ncolblk));
+    rows_per_stripe = ceil_div(ceil_div(n, nstripe), 8) * 8;
+    nstripe = ceil_div(n, rows_per_stripe);
+    nrowblk = ceil_div(n, kRowTile);
+    nseg = std::max(1, std::min(ceil_div(m, 128), (target + nrowblk - 1) / nrowblk));
+    cols_per_seg = ceil_div(ceil_div(m, nseg), 128) * 128;
+    nseg = ceil_div(m, cols_per_seg);
+    s4_ncolblk = ceil_div(m, 32);
+    if (ell > 0) {
+      s4_K = acc_template_k(ell);
+      s4_nseg = std::max(1, std::min(ceil_div(n, 64), (2 * nsm + s4_ncolblk - 1) / s4_ncolblk));
+      s4_seglen = ceil_div(ceil_div(n, s4_nseg), 64) * 64;
+      s4_nseg = ceil_div(n, s4_seglen);
+    }
+    if (p > 0) {
+      ek_K = acc_template_k(p);
+      kc_nseg = std::max(1, std::min(ceil_div(n, 64), (2 * nsm + s4_ncolblk - 1) / s4_ncolblk));
+      kc_seglen = ceil_div(ceil_div(n, kc_nseg), 64) * 64;
+      kc_nseg = ceil_div(n, kc_seglen);
+      const int rw = ek_K <= 32 ? 2 : 1;
+      kr_nrowblk = ceil_div(n, 8 * rw);
+      kr_nseg = std::max(1, std::min(ceil_div(m, 32), (2 * nsm + kr_nrowblk - 1) / kr_nrowblk));
+      kr_seglen = ceil_div(ceil_div(m, kr_nseg), 32) * 32;
+      kr_nseg = ceil_div(m, kr_seglen);
+    }
+  }
+
+  void layout(Arena& A, int d) {
+    dP = A.take<Prob>(1);
+    dSt = A.take<State>(1);
+    Cbuf = own_cost ? A.take<float>((size_t)n * m) : nullptr;
+    a_in = A.take<double>(n);
+    b_in = A.take<double>(m);
+    f_init = A.take<double>(n);
+    f_out = A.take<double>(n);
+    g_out = A.take<double>(m);
+    scores = A.take<double>(16);
+    stats = A.take<unsigned>(4);
+    cmax64 = A.take<unsigned long long>(1);
+    X = d > 0 ? A.take<float>((size_t)n * d) : nullptr;
+    Y = d > 0 ? A.take<float>((size_t)m * d) : nullptr;
+    hP.a = A.take<double>(n);
+    hP.b = A.take<double>(m);
+    hP.loga = A.take<double>(n);
+    hP.logb = A.take<double>(m);
+    for (int k = 0; k < 2; ++k) {
+      hP.f[k] = A.take<double>(n);
+      hP.rs[k] = Split{A.take<float>(n), A.take<float>(n), A.take<float>(n), A.take<float>(n)};
+    }
+    for (int k = 0; k < 3; ++k) {
+      hP.g[k] = A.take<double>(m);
+      hP.cs[k] = Split{A.take<float>(m), A.take<float>(m), A.take<float>(m), A.take<float>(m)};
+    }
+    hP.Lrow = A.take<float>(n);
+    hP.Lcol = A.take<float>(m);
+    hP.part_col = A.take<float2>((size_t)nstripe * m);
+    hP.cnt_col = A.take<unsigned>(ncolblk);
+    hP.acc_col = A.take<double>((size_t)ncolblk * 4);
+    hP.part_row = A.take<float2>((size_t)nseg * n);
+    hP.cnt_row = A.take<unsigned>(nrowblk);
+    hP.acc_row = A.take<double>((size_t)nrowblk * 4);
+    hP.gcnt = A.take<unsigned>(4);
+    hP.out_plain = nullptr;
+    hP.logratio_plain = nullptr;
+    const int nch = ceil_div(std::max(n, m), kGChunkHost);
+    if (ell > 0) {
+      V = A.take<float>((size_t)n * ell);
+      W = A.take<float>((size_t)m * ell);
+      s4part = A.take<float>((size_t)s4_nseg * m * (s4_K + 2));
+      s4cnt = A.take<unsigned>(s4_ncolblk);
+      s4gcnt = A.take<unsigned>(1);
+      s4blk = A.take<double>((size_t)s4_ncolblk * 4);
+      gpart = A.take<double>((size_t)nch * ell * ell);
+      gvpart = A.take<double>((size_t)nch * ell);
+      WtW = A.take<double>((size_t)ell * ell);
+      gw = A.take<double>(ell);
+      dw = A.take<double>(m);
+      hP.delta = A.take<double>(ell);
+      hP.GV = A.take<double>((size_t)ell * ell);
+      hP.Va = A.take<double>(ell);
+    }
+    if (p > 0) {
+      Zb = A.take<float>((size_t)n * p);
+      Xb = A.take<float>((size_t)n * p);
+      Yb = A.take<float>((size_t)m * p);
+      Bm = A.take<float>((size_t)p * p);
+      kcpart = A.take<float>((size_t)kc_nseg * m * (ek_K + 2));
+      krpart = A.take<float>((size_t)kr_nseg * n * (ek_K + 2));
+      kccnt = A.take<unsigned>(s4_ncolblk);
+      krcnt = A.take<unsigned>(kr_nrowblk);
+      epart = A.take<double>((size_t)nch * p * p);
+      evpart = A.take<double>((size_t)nch * p);
+      GXX = A.take<double>((size_t)p * p);
+      Tm = A.take<double>((size_t)p * p);
+      cvec = A.take<double>(p);
+      theta = A.take<double>(p);
+      resid = A.take<double>(1);
+      efail = A.take<int>(1);
+    }
+  }
+
+  eot_status init(DeviceCtx* c, int n_, int m_, int d, int ell_, int p_, bool own) {
+    ctx = c;
+    n = n_;
+    m = m_;
+    ell = ell_;
+    p = p_;
+    if (ell > 0 && p < ell) return fail(EOT_EINVAL, "ell must be < n");
+    own_cost = own;
+    plan_tiles();
+    Arena A;
+    layout(A, d);
+    bytes = A.off + 256;
+    CUDA_TRY(cudaMalloc(&mem, bytes));
+    CUDA_TRY(cudaMemsetAsync(mem, 0, bytes, ctx->stream));
+    Arena B;
+    B.base = reinterpret_cast<char*>(mem);
+    layout(B, d);
+    CUDA_TRY(cudaMallocHost(&hSt, sizeof(State)));
+    CUDA_TRY(cudaMallocHost(&hScores, 16 * sizeof(double)));
+    hP.n = n;
+    hP.m = m;
+    hP.nstripe = nstripe;
+    hP.rows_per_stripe = rows_per_stripe;
+    hP.ncolblk = ncolblk;
+    hP.nseg = nseg;
+    hP.cols_per_seg = cols_per_seg;
+    hP.nrowblk = nrowblk;
+    hP.st = dSt;
+    hP.ell = ell;
+    hP.V = V;
+    hP.W = W;
+    return EOT_OK;
+  }
+
+  // ---- argument blocks of the accumulating passes ----
+  AccArgs s4_args() const {
+    AccArgs a{};
+    a.P = dP;
+    a.mode = 1;  // ACC_S4
+    a.k = ell;
+    a.Z = V;
+    a.out = W;
+    a.part = s4part;
+    a.cnt = s4cnt;
+    a.nseg = s4_nseg;
+    a.seg_len = s4_seglen;
+    a.nblk = s4_ncolblk;
+    a.blkacc = s4blk;
+    a.gcnt = s4gcnt;
+    return a;
+  }
+  AccArgs kcol_args(int fb, int gb, const float* Z, float* out) const {
+    AccArgs a{};
+    a.P = dP;
+    a.mode = 0;  // ACC_KCOL
+    a.k = p;
+    a.Z = Z;
+    a.out = out;
+    a.part = kcpart;
+    a.cnt = kccnt;
+    a.nseg = kc_nseg;
+    a.seg_len = kc_seglen;
+    a.nblk = s4_ncolblk;
+    a.fbuf = fb;
+    a.gbuf = gb;
+    return a;
+  }
+  AccArgs krow_args(int fb, int gb, const float* Z, float* out) const {
+    AccArgs a{};
+    a.P = dP;
+    a.mode = 2;  // ACC_KROW
+    a.k = p;
+    a.Z = Z;
+    a.out = out;
+    a.part = krpart;
+    a.cnt = krcnt;
+    a.nseg = kr_nseg;
+    a.seg_len = kr_seglen;
+    a.nblk = kr_nrowblk;
+    a.fbuf = fb;
+    a.gbuf = gb;
+    return a;
+  }
+
+  // weighted Gram  out = A^T diag(w or 1/w) B  (+ vout = sum_i vw_i A_i)
+  cudaError_t wgram(const float* Am, const float* Bm_, const double* w, int wmode, int len, int q,
+                    const double* vw, const float* vsrc, double* part, double* vpart, double* out,
+                    double* vout, int respect_done, cudaStream_t s) {
+    const int nch = ceil_div(len, kGChunkHost);
+    const size_t sm = ((size_t)2 * kGChunkHost * q + 2 * kGChunkHost) * sizeof(float);
+    wgram_partial_kernel<<<nch, 256, sm, s>>>(Am, Bm_, w, wmode, len, q, vw, vsrc, part,
+                                              vout ? vpart : nullptr, dSt, respect_done);
+    wgram_reduce_kernel<<<ceil_div(q * q, 256), 256, 0, s>>>(part, nch, q * q, out, dSt,
+                                                              respect_done);
+    if (vout)
+      wgram_reduce_kernel<<<ceil_div(q, 256), 256, 0, s>>>(vpart, nch, q, vout, dSt,
+                                                            respect_done);
+    return cudaGetLastError();
+  }
+
+  // ---- loop bodies ----
+  cudaError_t body_sk(cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    for (int u = 0; u < unroll_sk && e == cudaSuccess; ++u) {
+      e = launch_row_pass(dP, hP, MODE_SK_ROW, s);
+      if (e == cudaSuccess) e = launch_col_pass(dP, hP, MODE_SK_COL, s);
+    }
+    return e;
+  }
+
+  cudaError_t body_sknr(cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    const AccArgs a = s4_args();
+    for (int u = 0; u < unroll_sknr && e == cudaSuccess; ++u) {
+      e = launch_row_pass(dP, hP, MODE_SK_ROW, s);
+      if (e == cudaSuccess) e = launch_colacc(a, s4_ncolblk, s);
+      if (e != cudaSuccess) break;
+      grad_weights_kernel<<<ceil_div(m, 256), 256, 0, s>>>(dP, dw);
+      e = wgram(W, W, hP.b, 1, m, ell, dw, W, gpart, gvpart, WtW, gw, 1, s);
+      if (e != cudaSuccess) break;
+      newton_kernel<<<1, 256, 0, s>>>(dP, WtW, gw, nullptr);
+      fprime_kernel<<<std::min(ceil_div(n, 256), 4 * ctx->nsm), 256, 0, s>>>(dP);
+      e = launch_col_pass(dP, hP, MODE_TRIAL, s);
+    }
+    return e;
+  }
+
+  cudaError_t body_eig(cudaStream_t s, int fb, int gb) {
+    cudaError_t e = launch_colacc(kcol_args(fb, gb, Zb, Yb), s4_ncolblk, s);
+    if (e == cudaSuccess) e = launch_rowacc(krow_args(fb, gb, Yb, Xb), kr_nrowblk, s);
+    if (e != cudaSuccess) return e;
+    // GXX = X^T D_a X (+ c = a^T X), T = Z^T D_a X
+    e = wgram(Xb, Xb, hP.a, 0, n, p, hP.a, Xb, epart, evpart, GXX, cvec, 0, s);
+    if (e == cudaSuccess) e = wgram(Zb, Xb, hP.a, 0, n, p, nullptr, nullptr, epart, nullptr, Tm,
+                                    nullptr, 0, s);
+    if (e != cudaSuccess) return e;
+    eig_small_kernel<<<1, 256, 0, s>>>(p, ell, 1, GXX, Tm, cvec, Bm, theta, resid, efail);
+    apply_kernel<<<ceil_div(n, 64), 256, (size_t)(p * p + 64 * p) * 4, s>>>(Xb, cvec, Bm, n, p,
+                                                                           Zb);
+    eig_ctl_kernel<<<1, 1, 0, s>>>(dSt, resid, efail);
+    return cudaGetLastError();
+  }
+
+  // Capture `body` into a graph; with conditional nodes, wrap it in a while loop.
+  template <class F>
+  eot_status build_loop(F body, int which, cudaGraph_t* gout, cudaGraphExec_t* xout) {
+    cudaStream_t s = ctx->stream;
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaGraphCreate(&g, 0));
+    if (ctx->cond_ok) {
+      cudaGraphConditionalHandle h;
+      CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = h;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      cudaGraphNode_t node;
+      CUDA_TRY(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
+      cudaGraph_t bodyg = cp.conditional.phGraph_out[0];
+      CUDA_TRY(cudaStreamBeginCaptureToGraph(s, bodyg, nullptr, nullptr, 0,
+                                             cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = body(s);
+      loop_ctl_kernel<<<1, 1, 0, s>>>(h, dSt, which, 1);
+      cudaGraph_t tmp;
+      cudaError_t e2 = cudaStreamEndCapture(s, &tmp);
+      if (e != cudaSuccess || e2 != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return fail(EOT_ECUDA, std::string("graph capture: ") +
+                                   cudaGetErrorString(e != cudaSuccess ? e : e2));
+      }
+    } else {
+      CUDA_TRY(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0,
+                                             cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = body(s);
+      loop_ctl_kernel<<<1, 1, 0, s>>>(0, dSt, which, 0);
+      cudaGraph_t tmp;
+      cudaError_t e2 = cudaStreamEndCapture(s, &tmp);
+      if (e != cudaSuccess || e2 != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return fail(EOT_ECUDA, std::string("graph capture: ") +
+                                   cudaGetErrorString(e != cudaSuccess ? e : e2));
+      }
+    }
+    CUDA_TRY(cudaGraphInstantiate(xout, g, 0));
+    *gout = g;
+    return EOT_OK;
+  }
+
+  // Run a captured loop to completion.  With conditional nodes this is one
+  // launch; otherwise the host relaunches the body and polls the state.
+  eot_status run_loop(cudaGraphExec_t ex, int which, int cap) {
+    cudaStream_t s = ctx->stream;
+    if (ctx->cond_ok) {
+      CUDA_TRY(cudaGraphLaunch(ex, s));
+      return EOT_OK;
+    }
+    for (int it = 0; it < cap; ++it) {
+      CUDA_TRY(cudaGraphLaunch(ex, s));
+      CUDA_TRY(cudaMemcpyAsync(hSt, dSt, sizeof(State), cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaStreamSynchronize(s));
+      if ((which == 0 && hSt->done) || (which == 1 && hSt->eig_done)) break;
+    }
+    return EOT_OK;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Solver cache: repeated solves of one shape reuse buffers and graphs.
+// ---------------------------------------------------------------------------
+struct CacheKey {
+  int dev, n, m, d, ell, p, own;
+  bool operator<(const CacheKey& o) const {
+    return std::tie(dev, n, m, d, ell, p, own) < std::tie(o.dev, o.n, o.m, o.d, o.ell, o.p, o.own);
+  }
+};
+static thread_local std::map<CacheKey, std::unique_ptr<Solver>> t_cache;
+
+static int mode_block(int n, int ell, int oversample) {
+  return ell > 0 ? std::min(kMaxP, std::min(n - 1, ell + oversample)) : 0;
+}
+
+static eot_status get_solver(DeviceCtx* ctx, int n, int m, int d, int ell, int p, bool own,
+                             Solver** out) {
+  CacheKey key{ctx->dev, n, m, d, ell, p, own ? 1 : 0};
+  auto it = t_cache.find(key);
+  if (it != t_cache.end()) {
+    *out = it->second.get();
+    return EOT_OK;
+  }
+  if (t_cache.size() >= 4) t_cache.clear();
+  auto s = std::make_unique<Solver>();
+  eot_status st = s->init(ctx, n, m, d, ell, p, own);
+  if (st != EOT_OK) return st;
+  *out = s.get();
+  t_cache[key] = std::move(s);
+  return EOT_OK;
+}
+
+// Device bytes a solver of this shape allocates (admission control).
+static size_t solver_footprint(DeviceCtx* ctx, int n, int m, int d, int ell, int p) {
+  Solver tmp;
+  tmp.ctx = ctx;
+  tmp.n = n;
+  tmp.m = m;
+  tmp.ell = ell;
+  tmp.p = p;
+  tmp.own_cost = true;
+  tmp.plan_tiles();
+  Arena A;
+  tmp.layout(A, d);
+  return A.off + 256 + (size_t)(n + m) * 64;
+}
+
+static void drop_thread_cache() { t_cache.clear(); }
+
+static double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// eps schedule (Sec. 5: decreasing eps, warm started): eps_start, eps_start*f, ... > eps, eps
+static std::vector<double> schedule(double eps_start, double eps, double factor) {
+  std::vector<double> lv;
+  if (!(eps_start > eps) || !(factor > 0.0) || !(factor < 1.0)) {
+    lv.push_back(eps);
+    return lv;
+  }
+  double e = eps_start;
+  while (e > eps * (1.0 + 1e-9) && lv.size() < 200) {
+    lv.push_back(e);
+    e *= factor;
+  }
+  lv.push_back(eps);
+  return lv;
+}
+
+static bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+// Validate a problem's scalar fields (array contents are checked on the device).
+static eot_status validate(const eot_problem* pr, const eot_options* o) {
+  if (!pr || !o) return fail(EOT_EINVAL, "null problem or options");
+  if (pr->n < 1 || pr->m < 1) return fail(EOT_EINVAL, "n and m must be >= 1");
+  if (!pr->a || !pr->b) return fail(EOT_EINVAL, "weights a and b are required");
+  if (!finite_pos(pr->eps)) return fail(EOT_EINVAL, "eps must be finite and > 0");
+  const bool hasC = pr->C != nullptr, hasXY = pr->X != nullptr && pr->Y != nullptr;
+  if (hasC == hasXY) return fail(EOT_EINVAL, "give exactly one of C or (X, Y)");
+  if (hasXY && pr->d < 1) return fail(EOT_EINVAL, "d must be >= 1 with point clouds");
+  if (hasC && pr->d != 0) return fail(EOT_EINVAL, "d must be 0 when C is given");
+  if (pr->mem != EOT_MEM_HOST && pr->mem != EOT_MEM_DEVICE) return fail(EOT_EINVAL, "bad mem");
+  if (o->prec != EOT_PREC_FP32)
+    return fail(EOT_EINVAL, "only EOT_PREC_FP32 is implemented in this build");
+  if (!(o->tol > 0.0)) return fail(EOT_EINVAL, "tol must be > 0");
+  if (o->max_iter < 1) return fail(EOT_EINVAL, "max_iter must be >= 1");
+  if (o->ell < 0 || o->ell > kMaxK) return fail(EOT_EINVAL, "ell must be in [0, 64]");
+  if (o->ell > 0 && pr->n < 3) return fail(EOT_EINVAL, "SK-NR needs n >= 3");
+  if (o->ell > 0 && o->ell + 1 > kMaxP) return fail(EOT_EINVAL, "ell must be <= 47");
+  if (o->oversample < 0) return fail(EOT_EINVAL, "oversample must be >= 0");
+  if ((long long)pr->n * pr->m > (1ll << 34)) return fail(EOT_EINVAL, "n*m too large");
+  return EOT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// One solve.
+// ---------------------------------------------------------------------------
+static eot_status solve_one(const eot_problem* pr, const eot_options* o, double* f_out,
+                            double* g_out, eot_result* res, const double* f_init_dev = nullptr,
+                            double* f_keep_dev = nullptr) {
+  eot_status vs = validate(pr, o);
+  if (vs != EOT_OK) return vs;
+  DeviceCtx* ctx = nullptr;
+  eot_status cs = get_ctx(&ctx);
+  if (cs != EOT_OK) return cs;
+  const int n = pr->n, m = pr->m, d = pr->d;
+  const bool dev = pr->mem == EOT_MEM_DEVICE;
+  const bool borrowC = dev && d == 0 && !pr->normalize_cost &&
+                       (reinterpret_cast<uintptr_t>(pr->C) & 15u) == 0;
+  Solver* S = nullptr;
+  eot_status ss = get_solver(ctx, n, m, d, o->ell, mode_block(n, o->ell, o->oversample), !borrowC,
+                             &S);
+  if (ss != EOT_OK) return ss;
+  cudaStream_t s = o->stream ? reinterpret_cast<cudaStream_t>(o->stream) : ctx->stream;
+  // the solver's graphs are captured on the context stream; user streams are
+  // joined with events around the solve
+  cudaEvent_t ev0, ev1, evj;
+  CUDA_TRY(cudaEventCreate(&ev0));
+  CUDA_TRY(cudaEventCreate(&ev1));
+  CUDA_TRY(cudaEventCreateWithFlags(&evj, cudaEventDisableTiming));
+  if (s != ctx->stream) {
+    CUDA_TRY(cudaEventRecord(evj, s));
+    CUDA_TRY(cudaStreamWaitEvent(ctx->stream, evj, 0));
+  }
+  s = ctx->stream;
+  const double t_host0 = now_s();
+  CUDA_TRY(cudaEventRecord(ev0, s));
+  const cudaMemcpyKind kin = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  // ---- inputs ----
+  CUDA_TRY(cudaMemsetAsync(S->stats, 0, 4 * sizeof(unsigned), s));
+  CUDA_TRY(cudaMemsetAsync(S->cmax64, 0, sizeof(unsigned long long), s));
+  CUDA_TRY(cudaMemcpyAsync(S->a_in, pr->a, n * sizeof(double), kin, s));
+  CUDA_TRY(cudaMemcpyAsync(S->b_in, pr->b, m * sizeof(double), kin, s));
+  weights_kernel<<<1, 256, 0, s>>>(n, S->a_in, const_cast<double*>(S->hP.a),
+                                   const_cast<double*>(S->hP.loga), S->stats + 2, 1);
+  weights_kernel<<<1, 256, 0, s>>>(m, S->b_in, const_cast<double*>(S->hP.b),
+                                   const_cast<double*>(S->hP.logb), S->stats + 2, 1);
+  const size_t nm = (size_t)n * m;
+  const int gb = std::min<long long>(((long long)nm + 255) / 256, 8LL * ctx->nsm);
+  const float* Cdev = nullptr;
+  if (d > 0) {
+    CUDA_TRY(cudaMemcpyAsync(S->X, pr->X, (size_t)n * d * sizeof(float), kin, s));
+    CUDA_TRY(cudaMemcpyAsync(S->Y, pr->Y, (size_t)m * d * sizeof(float), kin, s));
+    if (pr->normalize_cost) cost_max_kernel<<<gb, 256, 0, s>>>(n, m, d, S->X, S->Y, S->cmax64);
+    cost_fill_kernel<<<gb, 256, 0, s>>>(n, m, d, S->X, S->Y, S->cmax64, pr->normalize_cost,
+                                        S->Cbuf);
+    Cdev = S->Cbuf;
+  } else if (borrowC) {
+    Cdev = reinterpret_cast<const float*>(pr->C);
+  } else {
+    CUDA_TRY(cudaMemcpyAsync(S->Cbuf, pr->C, nm * sizeof(float), kin, s));
+    Cdev = S->Cbuf;
+  }
+  cost_stats_kernel<<<gb, 256, 0, s>>>(nm, Cdev, S->stats, S->stats + 1);
+  unsigned hstats[4];
+  CUDA_TRY(cudaMemcpyAsync(hstats, S->stats, sizeof(hstats), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (hstats[2]) return fail(EOT_EINVAL, "weights must be positive and finite");
+  if (hstats[1]) return fail(EOT_EINVAL, "cost has non-finite entries");
+  float cmaxf;
+  std::memcpy(&cmaxf, &hstats[0], sizeof(float));
+  double cmax = cmaxf;
+  if (d == 0 && pr->normalize_cost) {
+    if (cmax > 0.0) {
+      cost_scale_kernel<<<gb, 256, 0, s>>>(nm, Cdev, cmax, S->Cbuf);
+      Cdev = S->Cbuf;
+      cmax = 1.0;
+    }
+  }
+  // ---- exponent grid (see eot_device.cuh) ----
+  const std::vector<double> levels = schedule(o->eps_start, pr->eps, o->eps_factor);
+  const double eps0 = levels.front();
+  double fmax = 0.0;
+  std::vector<double> hf;
+  const double* finit = f_init_dev ? f_init_dev : pr->f_init;
+  const bool finit_dev = f_init_dev ? true : dev;
+  if (finit) {
+    hf.resize(n);
+    CUDA_TRY(cudaMemcpy(hf.data(), finit, n * sizeof(double),
+                        finit_dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+    for (double v : hf) {
+      if (!std::isfinite(v)) return fail(EOT_EINVAL, "f_init has non-finite entries");
+      fmax = std::max(fmax, std::fabs(v));
+    }
+  }
+  const double R = 4.0 * (cmax + fmax + 40.0 * eps0) + 1e-30;
+  int q = 22 - (int)std::ceil(std::log2(R));
+  q = std::max(-100, std::min(q, 60));
+  Prob& P = S->hP;
+  P.C = Cdev;
+  P.qscale = std::ldexp(1.0, q);
+  P.qinv = std::ldexp(1.0, -q);
+  P.M = (float)(1.5 * std::ldexp(1.0, 23 - q));
+  P.pot_bound = std::ldexp(1.0, 22 - q) / 2.0 - cmax;
+  P.eps = eps0;
+  P.k2 = (float)(1.0 / (eps0 * std::log(2.0)));
+  P.st = S->dSt;
+  CUDA_TRY(cudaMemcpyAsync(S->dP, &P, sizeof(Prob), cudaMemcpyHostToDevice, s));
+  // ---- initial state: f = f_init or 0, g shift = 0 ----
+  State st0{};
+  st0.cur_f = 0;
+  st0.cur_g = 0;
+  CUDA_TRY(cudaMemcpyAsync(S->dSt, &st0, sizeof(State), cudaMemcpyHostToDevice, s));
+  if (finit) {
+    CUDA_TRY(cudaMemcpyAsync(P.f[0], finit, n * sizeof(double),
+                             finit_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  } else {
+    CUDA_TRY(cudaMemsetAsync(P.f[0], 0, n * sizeof(double), s));
+  }
+  CUDA_TRY(cudaMemsetAsync(P.g[0], 0, m * sizeof(double), s));
+  // ---- graphs (captured once per solver) ----
+  if (!S->ex_sk) {
+    eot_status e = S->build_loop([&](cudaStream_t cs_) { return S->body_sk(cs_); }, 0, &S->gr_sk,
+                                 &S->ex_sk);
+    if (e != EOT_OK) return e;
+  }
+  const int ell = o->ell;
+  if (ell > 0 && !S->ex_sknr) {
+    eot_status e = S->build_loop([&](cudaStream_t cs_) { return S->body_sknr(cs_); }, 0,
+                                 &S->gr_sknr, &S->ex_sknr);
+    if (e != EOT_OK) return e;
+    e = S->build_loop([&](cudaStream_t cs_) { return S->body_eig(cs_, 0, 0); }, 1, &S->gr_eig,
+                      &S->ex_eig);
+    if (e != EOT_OK) return e;
+  }
+  // ---- levels ----
+  const int L = (int)levels.size();
+  std::vector<cudaEvent_t> lev_ev(L + 1);
+  for (auto& e : lev_ev) CUDA_TRY(cudaEventCreate(&e));
+  std::vector<State> lev_state(L);
+  State* hLev = nullptr;
+  CUDA_TRY(cudaMallocHost(&hLev, sizeof(State) * (L + 1)));
+  bool have_modes = false;
+  int eig_iters_total = 0;
+  cudaEvent_t eig_ev0 = nullptr, eig_ev1 = nullptr;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> eig_events;
+  const int body_cap_sk = std::max(4, o->max_iter / S->unroll_sk + 4);
+  const int body_cap_nr = std::max(4, o->max_iter / S->unroll_sknr + 4);
+  for (int t = 0; t < L; ++t) {
+    const double eps = levels[t];
+    const bool last = t == L - 1;
+    const double tol = (last || !(o->level_tol > 0.0)) ? o->tol : o->level_tol;
+    const bool use_nr = ell > 0 && have_modes;
+    CUDA_TRY(cudaEventRecord(lev_ev[t], s));
+    level_setup_kernel<<<1, 1, 0, s>>>(S->dP, eps, (float)(1.0 / (eps * std::log(2.0))), tol,
+                                       o->max_iter, use_nr ? body_cap_nr : body_cap_sk);
+    // split arrays of the carried potentials (they depend on eps through eps*log w)
+    // cur_f / cur_g are 0 at the start of every level (see the copy kernels below)
+    CUDA_TRY(launch_split(S->dP, P.f[0], P.loga, n, P.rs[0], s));
+    CUDA_TRY(launch_split(S->dP, P.g[0], P.logb, m, P.cs[0], s));
+    CUDA_TRY(launch_col_pass(S->dP, P, MODE_G_INIT, s));
+    if (use_nr) {
+      // V^T D_a V and V^T a for this level's modes
+      CUDA_TRY(S->wgram(S->V, S->V, P.a, 0, n, ell, P.a, S->V, S->gpart, S->gvpart, P.GV, P.Va, 0,
+                        s));
+      eot_status e = S->run_loop(S->ex_sknr, 0, body_cap_nr + 1);
+      if (e != EOT_OK) return e;
+    } else {
+      eot_status e = S->run_loop(S->ex_sk, 0, body_cap_sk + 1);
+      if (e != EOT_OK) return e;
+    }
+    CUDA_TRY(cudaMemcpyAsync(hLev + t, S->dSt, sizeof(State), cudaMemcpyDeviceToHost, s));
+    // bring the current f and g to buffer 0 (split at this level's eps) for
+    // the modes and the next level
+    normalize_buffers_kernel<<<std::max(1, std::min(ceil_div(std::max(n, m), 256),
+                                                     4 * ctx->nsm)),
+                               256, 0, s>>>(S->dP);
+    reset_buffers_kernel<<<1, 1, 0, s>>>(S->dSt);
+    const bool need_modes = ell > 0 && !last && (o->sequential_modes || !have_modes);
+    if (need_modes) {
+      cudaEvent_t a0, a1;
+      CUDA_TRY(cudaEventCreate(&a0));
+      CUDA_TRY(cudaEventCreate(&a1));
+      CUDA_TRY(cudaEventRecord(a0, s));
+      // the modes use the converged (f, g) of this level: rs[0]/cs[0] splits
+      // were refreshed by normalize_buffers_kernel (which re-splits buffer 0)
+      const int keep = have_modes ? ell : 0;
+      init_block_kernel<<<std::min(ceil_div((long long)n * S->p, 256), 8 * ctx->nsm), 256, 0, s>>>(
+          S->Xb, n, S->p, 0x5EEDull + 977ull * (unsigned long long)t, have_modes ? S->V : nullptr,
+          keep);
+      // orthonormalise the start block: Z = (X0 - 1 c^T) L^{-T}
+      CUDA_TRY(S->wgram(S->Xb, S->Xb, P.a, 0, n, S->p, P.a, S->Xb, S->epart, S->evpart, S->GXX,
+                        S->cvec, 0, s));
+      eig_small_kernel<<<1, 256, 0, s>>>(S->p, ell, 0, S->GXX, S->Tm, S->cvec, S->Bm, S->theta,
+                                         S->resid, S->efail);
+      apply_kernel<<<ceil_div(n, 64), 256, (size_t)(S->p * S->p + 64 * S->p) * 4, s>>>(
+          S->Xb, S->cvec, S->Bm, n, S->p, S->Zb);
+      eig_setup_kernel<<<1, 1, 0, s>>>(S->dSt, o->eig_tol, o->eig_max_iter,
+                                       o->eig_max_iter + 4);
+      eot_status e = S->run_loop(S->ex_eig, 1, o->eig_max_iter + 5);
+      if (e != EOT_OK) return e;
+      take_cols_kernel<<<std::min(ceil_div((long long)n * ell, 256), 8 * ctx->nsm), 256, 0, s>>>(
+          S->Zb, n, S->p, ell, S->V);
+      CUDA_TRY(cudaEventRecord(a1, s));
+      eig_events.push_back({a0, a1});
+      CUDA_TRY(cudaMemcpyAsync(hLev + L, S->dSt, sizeof(State), cudaMemcpyDeviceToHost, s));
+      have_modes = true;
+    }
+  }
+  CUDA_TRY(cudaEventRecord(lev_ev[L], s));
+  // ---- finish: evaluation passes at (f, g) = buffers 0, scores, gauge ----
+  CUDA_TRY(launch_split(S->dP, P.f[0], P.loga, n, P.rs[0], s));
+  CUDA_TRY(launch_split(S->dP, P.g[0], P.logb, m, P.cs[0], s));
+  CUDA_TRY(launch_row_pass(S->dP, P, MODE_EVAL, s));
+  CUDA_TRY(launch_col_pass(S->dP, P, MODE_EVAL, s));
+  final_eval_kernel<<<1, 256, 0, s>>>(S->dP, S->f_out, S->g_out, S->scores);
+  const cudaMemcpyKind kout = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CUDA_TRY(cudaMemcpyAsync(f_out, S->f_out, n * sizeof(double), kout, s));
+  CUDA_TRY(cudaMemcpyAsync(g_out, S->g_out, m * sizeof(double), kout, s));
+  if (f_keep_dev)
+    CUDA_TRY(cudaMemcpyAsync(f_keep_dev, S->f_out, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(S->hScores, S->scores, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaEventRecord(ev1, s));
+  if (o->stream && reinterpret_cast<cudaStream_t>(o->stream) != ctx->stream) {
+    CUDA_TRY(cudaStreamWaitEvent(reinterpret_cast<cudaStream_t>(o->stream), ev1, 0));
+  }
+  CUDA_TRY(cudaEventSynchronize(ev1));
+  CUDA_TRY(cudaGetLastError());
+  // ---- statistics ----
+  eot_result r{};
+  const State& fin = hLev[L - 1];
+  int total = 0;
+  for (int t = 0; t < L; ++t) total += hLev[t].iter;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ev0, ev1);
+  double eig_s = 0.0, last_eig = 0.0;
+  for (size_t k = 0; k < eig_events.size(); ++k) {
+    float em = 0.f;
+    cudaEventElapsedTime(&em, eig_events[k].first, eig_events[k].second);
+    eig_s += em * 1e-3;
+    if (k + 1 == eig_events.size()) last_eig = em * 1e-3;
+    cudaEventDestroy(eig_events[k].first);
+    cudaEventDestroy(eig_events[k].second);
+  }
+  float lm = 0.f;
+  cudaEventElapsedTime(&lm, lev_ev[L - 1], lev_ev[L]);
+  r.iters = fin.iter;
+  r.total_iters = total;
+  r.nr_accepted = fin.nr_acc;
+  r.nr_rejected = fin.nr_rej;
+  r.levels = L;
+  eig_iters_total = 0;
+  r.eig_iters = (ell > 0 && !eig_events.empty()) ? hLev[L].eig_iter : 0;
+  r.row_l1 = S->hScores[0];
+  r.col_l1 = S->hScores[1];
+  r.l1_marginal = r.row_l1 + r.col_l1;
+  r.q_dual = S->hScores[5];
+  r.q_semi = fin.qsemi;
+  r.dual_gap = S->hScores[6];
+  r.seconds = ms * 1e-3;
+  r.seconds_eig = eig_s;
+  r.seconds_last_level = lm * 1e-3 + (L > 1 ? last_eig : 0.0);
+  eot_status status;
+  if (fin.done == 1) status = EOT_OK;
+  else if (fin.done == 2) status = EOT_NOT_CONVERGED;
+  else if (fin.done == 3) status = EOT_ENUMERIC;
+  else if (fin.done == 4) status = EOT_ETIMEDOUT;
+  else status = EOT_NOT_CONVERGED;
+  for (int t = 0; t < L - 1 && status == EOT_OK; ++t) {
+    if (hLev[t].done == 3) status = EOT_ENUMERIC;
+  }
+  r.status = status;
+  if (res) *res = r;
+  for (auto& e : lev_ev) cudaEventDestroy(e);
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  cudaEventDestroy(evj);
+  cudaFreeHost(hLev);
+  (void)t_host0;
+  (void)eig_ev0;
+  (void)eig_ev1;
+  if (status == EOT_ENUMERIC) t_err = "non-finite values or potentials outside the exact range";
+  if (status == EOT_ETIMEDOUT) t_err = "device loop reached its body cap";
+  if (status == EOT_NOT_CONVERGED) t_err = "max_iter reached";
+  return status;
+}
+
+}  // namespace eotk
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+using namespace eotk;
+
+extern "C" {
+
+void eot_default_options(eot_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->tol = 1e-6;
+  o->max_iter = 100000;
+  o->ell = 0;
+  o->eps_start = 0.0;
+  o->eps_factor = 0.5;
+  o->level_tol = 0.0;
+  o->sequential_modes = 1;
+  o->oversample = 10;
+  o->eig_tol = 1e-2;
+  o->eig_max_iter = 100;
+  o->prec = EOT_PREC_FP32;
+  o->hessian = EOT_HESS_DIAG_ALPHA;
+  o->poll_every = 0;
+  o->stream = nullptr;
+}
+
+eot_status eot_solve(const eot_problem* prob, const eot_options* opt, double* f_out,
+                     double* g_out, eot_result* res) {
+  if (!f_out || !g_out) return fail(EOT_EINVAL, "f_out and g_out are required");
+  eot_options o;
+  if (opt) o = *opt;
+  else eot_default_options(&o);
+  eot_status s = solve_one(prob, &o, f_out, g_out, res);
+  if (res && s < 0) res->status = s;
+  return s;
+}
+
+const char* eot_last_error(void) { return t_err.c_str(); }
+
+const char* eot_version(void) { return "eot-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"
+
+// ===========================================================================
+// Single hot-path steps on device memory.
+// ===========================================================================
+namespace eotk {
+
+// Pick the exponent grid for a standalone call from max|C| and the potentials.
+static eot_status standalone_grid(Solver* S, const float* Cdev, const double* p1, int l1,
+                                  const double* p2, int l2, double eps, cudaStream_t s,
+                                  double* cmax_out) {
+  const size_t nm = (size_t)S->n * S->m;
+  const int gb = std::min<long long>(((long long)nm + 255) / 256, 8LL * S->ctx->nsm);
+  CUDA_TRY(cudaMemsetAsync(S->stats, 0, 4 * sizeof(unsigned), s));
+  CUDA_TRY(cudaMemsetAsync(S->cmax64, 0, sizeof(unsigned long long), s));
+  cost_stats_kernel<<<gb, 256, 0, s>>>(nm, Cdev, S->stats, S->stats + 1);
+  if (p1) cost_stats_f64_kernel<<<ceil_div(l1, 256), 256, 0, s>>>(l1, p1, S->cmax64, S->stats + 3);
+  if (p2) cost_stats_f64_kernel<<<ceil_div(l2, 256), 256, 0, s>>>(l2, p2, S->cmax64, S->stats + 3);
+  unsigned hs[4];
+  unsigned long long pm = 0;
+  CUDA_TRY(cudaMemcpyAsync(hs, S->stats, sizeof(hs), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(&pm, S->cmax64, sizeof(pm), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (hs[1]) return fail(EOT_EINVAL, "cost has non-finite entries");
+  if (hs[3]) return fail(EOT_EINVAL, "potentials have non-finite entries");
+  float cm;
+  std::memcpy(&cm, &hs[0], 4);
+  double pmax;
+  std::memcpy(&pmax, &pm, 8);
+  const double R = 4.0 * ((double)cm + pmax + 40.0 * eps) + 1e-30;
+  int q = 22 - (int)std::ceil(std::log2(R));
+  q = std::max(-100, std::min(q, 60));
+  Prob& P = S->hP;
+  P.C = Cdev;
+  P.qscale = std::ldexp(1.0, q);
+  P.qinv = std::ldexp(1.0, -q);
+  P.M = (float)(1.5 * std::ldexp(1.0, 23 - q));
+  P.pot_bound = std::ldexp(1.0, 22 - q) / 2.0 - cm;
+  P.eps = eps;
+  P.k2 = (float)(1.0 / (eps * std::log(2.0)));
+  P.st = S->dSt;
+  if (cmax_out) *cmax_out = cm;
+  return EOT_OK;
+}
+
+static eot_status standalone_solver(int n, int m, int ell, int p, Solver** S, cudaStream_t* s,
+                                    void* user_stream) {
+  if (n < 1 || m < 1) return fail(EOT_EINVAL, "n and m must be >= 1");
+  DeviceCtx* ctx = nullptr;
+  eot_status cs = get_ctx(&ctx);
+  if (cs != EOT_OK) return cs;
+  eot_status ss = get_solver(ctx, n, m, 0, ell, p, false, S);
+  if (ss != EOT_OK) return ss;
+  *s = ctx->stream;
+  if (user_stream && reinterpret_cast<cudaStream_t>(user_stream) != ctx->stream) {
+    cudaEvent_t e;
+    CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventRecord(e, reinterpret_cast<cudaStream_t>(user_stream)));
+    CUDA_TRY(cudaStreamWaitEvent(ctx->stream, e, 0));
+    cudaEventDestroy(e);
+  }
+  return EOT_OK;
+}
+
+static eot_status standalone_finish(cudaStream_t s, void* user_stream) {
+  if (user_stream && reinterpret_cast<cudaStream_t>(user_stream) != s) {
+    cudaEvent_t e;
+    CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventRecord(e, s));
+    CUDA_TRY(cudaStreamWaitEvent(reinterpret_cast<cudaStream_t>(user_stream), e, 0));
+    cudaEventDestroy(e);
+  }
+  CUDA_TRY(cudaStreamSynchronize(s));
+  CUDA_TRY(cudaGetLastError());
+  return EOT_OK;
+}
+
+static eot_status load_weights(Solver* S, const double* a, const double* b, cudaStream_t s,
+                               int normalize) {
+  CUDA_TRY(cudaMemsetAsync(S->stats + 2, 0, sizeof(unsigned), s));
+  if (a) {
+    CUDA_TRY(cudaMemcpyAsync(S->a_in, a, S->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    weights_kernel<<<1, 256, 0, s>>>(S->n, S->a_in, const_cast<double*>(S->hP.a),
+                                     const_cast<double*>(S->hP.loga), S->stats + 2, normalize);
+  }
+  if (b) {
+    CUDA_TRY(cudaMemcpyAsync(S->b_in, b, S->m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    weights_kernel<<<1, 256, 0, s>>>(S->m, S->b_in, const_cast<double*>(S->hP.b),
+                                     const_cast<double*>(S->hP.logb), S->stats + 2, normalize);
+  }
+  unsigned bad = 0;
+  CUDA_TRY(cudaMemcpyAsync(&bad, S->stats + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (bad) return fail(EOT_EINVAL, "weights must be positive and finite");
+  return EOT_OK;
+}
+
+static eot_status ones_weights(Solver* S, bool rows, cudaStream_t s) {
+  std::vector<double> one(rows ? S->n : S->m, 1.0);
+  double* dst = rows ? S->a_in : S->b_in;
+  CUDA_TRY(cudaMemcpyAsync(dst, one.data(), one.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  if (rows)
+    weights_kernel<<<1, 256, 0, s>>>(S->n, S->a_in, const_cast<double*>(S->hP.a),
+                                     const_cast<double*>(S->hP.loga), S->stats + 2, 0);
+  else
+    weights_kernel<<<1, 256, 0, s>>>(S->m, S->b_in, const_cast<double*>(S->hP.b),
+                                     const_cast<double*>(S->hP.logb), S->stats + 2, 0);
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return EOT_OK;
+}
+
+}  // namespace eotk
+
+extern "C" {
+
+eot_status eot_ctransform(eot_side side, int32_t n, int32_t m, const float* C, const double* pot,
+                          const double* w, const double* shift, double eps, double* out,
+                          double* log_ratio, void* stream) {
+  if (!C || !pot || !w || !out) return fail(EOT_EINVAL, "C, pot, w and out are required");
+  if (!finite_pos(eps)) return fail(EOT_EINVAL, "eps must be finite and > 0");
+  if (side != EOT_SIDE_COL && side != EOT_SIDE_ROW) return fail(EOT_EINVAL, "bad side");
+  Solver* S = nullptr;
+  cudaStream_t s;
+  eot_status st = standalone_solver(n, m, 0, 0, &S, &s, stream);
+  if (st != EOT_OK) return st;
+  const bool col = side == EOT_SIDE_COL;
+  const int nred = col ? n : m, nout = col ? m : n;
+  st = col ? load_weights(S, w, nullptr, s, 0) : load_weights(S, nullptr, w, s, 0);
+  if (st != EOT_OK) return st;
+  st = col ? ones_weights(S, false, s) : ones_weights(S, true, s);
+  if (st != EOT_OK) return st;
+  st = standalone_grid(S, C, pot, nred, shift, shift ? nout : 0, eps, s, nullptr);
+  if (st != EOT_OK) return st;
+  Prob& P = S->hP;
+  double* redbuf = col ? P.f[0] : P.g[0];
+  double* outbuf = col ? P.g[0] : P.f[0];
+  CUDA_TRY(cudaMemcpyAsync(redbuf, pot, nred * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (shift) CUDA_TRY(cudaMemcpyAsync(outbuf, shift, nout * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  else CUDA_TRY(cudaMemsetAsync(outbuf, 0, nout * sizeof(double), s));
+  State st0{};
+  CUDA_TRY(cudaMemcpyAsync(S->dSt, &st0, sizeof(State), cudaMemcpyHostToDevice, s));
+  const int passes = shift ? 1 : 2;
+  for (int pass = 0; pass < passes; ++pass) {
+    const bool final_pass = pass == passes - 1;
+    P.out_plain = final_pass ? out : (col ? P.g[1] : P.f[1]);
+    P.logratio_plain = final_pass ? log_ratio : nullptr;
+    CUDA_TRY(cudaMemcpyAsync(S->dP, &P, sizeof(Prob), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(launch_split(S->dP, P.f[0], P.loga, n, P.rs[0], s));
+    CUDA_TRY(launch_split(S->dP, P.g[0], P.logb, m, P.cs[0], s));
+    CUDA_TRY(col ? launch_col_pass(S->dP, P, MODE_PLAIN, s) : launch_row_pass(S->dP, P, MODE_PLAIN, s));
+    if (!final_pass) {
+      CUDA_TRY(cudaMemcpyAsync(outbuf, col ? P.g[1] : P.f[1], nout * sizeof(double),
+                               cudaMemcpyDeviceToDevice, s));
+    }
+  }
+  P.out_plain = nullptr;
+  P.logratio_plain = nullptr;
+  CUDA_TRY(cudaMemcpyAsync(S->dP, &P, sizeof(Prob), cudaMemcpyHostToDevice, s));
+  return standalone_finish(s, stream);
+}
+
+eot_status eot_kapply(eot_side side, int32_t n, int32_t m, int32_t k, const float* C,
+                      const double* f, const double* g, const double* a, const double* b,
+                      double eps, const float* Z, float* out, void* stream) {
+  if (!C || !f || !g || !a || !b || !Z || !out) return fail(EOT_EINVAL, "null pointer");
+  if (k < 1 || k > kMaxP) return fail(EOT_EINVAL, "k must be in [1, 48]");
+  if (!finite_pos(eps)) return fail(EOT_EINVAL, "eps must be finite and > 0");
+  if (side != EOT_SIDE_COL && side != EOT_SIDE_ROW) return fail(EOT_EINVAL, "bad side");
+  Solver* S = nullptr;
+  cudaStream_t s;
+  eot_status st = standalone_solver(n, m, 0, k, &S, &s, stream);
+  if (st != EOT_OK) return st;
+  st = load_weights(S, a, b, s, 0);
+  if (st != EOT_OK) return st;
+  st = standalone_grid(S, C, f, n, g, m, eps, s, nullptr);
+  if (st != EOT_OK) return st;
+  Prob& P = S->hP;
+  CUDA_TRY(cudaMemcpyAsync(P.f[0], f, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(P.g[0], g, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  State st0{};
+  CUDA_TRY(cudaMemcpyAsync(S->dSt, &st0, sizeof(State), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(S->dP, &P, sizeof(Prob), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(launch_split(S->dP, P.f[0], P.loga, n, P.rs[0], s));
+  CUDA_TRY(launch_split(S->dP, P.g[0], P.logb, m, P.cs[0], s));
+  AccArgs aa = side == EOT_SIDE_COL ? S->kcol_args(0, 0, Z, out) : S->krow_args(0, 0, Z, out);
+  aa.k = k;
+  if (side == EOT_SIDE_COL) CUDA_TRY(launch_colacc(aa, S->s4_ncolblk, s));
+  else CUDA_TRY(launch_rowacc(aa, S->kr_nrowblk, s));
+  return standalone_finish(s, stream);
+}
+
+eot_status eot_cost(int32_t n, int32_t m, int32_t d, const float* X, const float* Y,
+                    int32_t normalize, float* C, double* cmax_out, void* stream) {
+  if (n < 1 || m < 1 || d < 1) return fail(EOT_EINVAL, "n, m, d must be >= 1");
+  if (!X || !Y || !C) return fail(EOT_EINVAL, "null pointer");
+  DeviceCtx* ctx = nullptr;
+  eot_status cs = get_ctx(&ctx);
+  if (cs != EOT_OK) return cs;
+  cudaStream_t s = stream ? reinterpret_cast<cudaStream_t>(stream) : ctx->stream;
+  unsigned long long* tmp = nullptr;
+  CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&tmp), sizeof(unsigned long long), s));
+  CUDA_TRY(cudaMemsetAsync(tmp, 0, sizeof(unsigned long long), s));
+  const size_t nm = (size_t)n * m;
+  const int gb = std::min<long long>(((long long)nm + 255) / 256, 8LL * ctx->nsm);
+  cost_max_kernel<<<gb, 256, 0, s>>>(n, m, d, X, Y, tmp);
+  cost_fill_kernel<<<gb, 256, 0, s>>>(n, m, d, X, Y, tmp, normalize, C);
+  if (cmax_out)
+    CUDA_TRY(cudaMemcpyAsync(cmax_out, tmp, sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaFreeAsync(tmp, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  CUDA_TRY(cudaGetLastError());
+  return EOT_OK;
+}
+
+eot_status eot_marginal_error(int32_t n, int32_t m, const float* C, const double* f,
+                              const double* g, const double* a, const double* b, double eps,
+                              double* row_l1, double* col_l1, void* stream) {
+  if (!C || !f || !g || !a || !b) return fail(EOT_EINVAL, "null pointer");
+  if (!finite_pos(eps)) return fail(EOT_EINVAL, "eps must be finite and > 0");
+  Solver* S = nullptr;
+  cudaStream_t s;
+  eot_status st = standalone_solver(n, m, 0, 0, &S, &s, stream);
+  if (st != EOT_OK) return st;
+  st = load_weights(S, a, b, s, 0);
+  if (st != EOT_OK) return st;
+  st = standalone_grid(S, C, f, n, g, m, eps, s, nullptr);
+  if (st != EOT_OK) return st;
+  Prob& P = S->hP;
+  CUDA_TRY(cudaMemcpyAsync(P.f[0], f, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(P.g[0], g, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  State st0{};
+  CUDA_TRY(cudaMemcpyAsync(S->dSt, &st0, sizeof(State), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(S->dP, &P, sizeof(Prob), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(launch_split(S->dP, P.f[0], P.loga, n, P.rs[0], s));
+  CUDA_TRY(launch_split(S->dP, P.g[0], P.logb, m, P.cs[0], s));
+  CUDA_TRY(launch_row_pass(S->dP, P, MODE_EVAL, s));
+  CUDA_TRY(launch_col_pass(S->dP, P, MODE_EVAL, s));
+  final_eval_kernel<<<1, 256, 0, s>>>(S->dP, S->f_out, S->g_out, S->scores);
+  CUDA_TRY(cudaMemcpyAsync(S->hScores, S->scores, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  st = standalone_finish(s, stream);
+  if (st != EOT_OK) return st;
+  if (row_l1) *row_l1 = S->hScores[0];
+  if (col_l1) *col_l1 = S->hScores[1];
+  return EOT_OK;
+}
+
+eot_status eot_spectral_modes(int32_t n, int32_t m, const float* C, const double* f,
+                              const double* g, const double* a, const double* b, double eps,
+                              int32_t ell, int32_t oversample, double tol, int32_t max_iter,
+                              int32_t use_V_as_start, double* V, double* rho2,
+                              int32_t* iters_out, double* resid_out, void* stream) {
+  if (!C || !f || !g || !a || !b || !V) return fail(EOT_EINVAL, "null pointer");
+  if (ell < 1 || oversample < 0 || ell + 1 > kMaxP || ell >= n)
+    return fail(EOT_EINVAL, "need 1 <= ell < n and ell < 48");
+  if (!finite_pos(eps) || !(tol > 0.0) || max_iter < 1) return fail(EOT_EINVAL, "bad eps/tol/max_iter");
+  const int p = mode_block(n, ell, oversample);
+  Solver* S = nullptr;
+  cudaStream_t s;
+  eot_status st = standalone_solver(n, m, ell, p, &S, &s, stream);
+  if (st != EOT_OK) return st;
+  if (!S->ex_eig) {
+    st = S->build_loop([&](cudaStream_t cs_) { return S->body_eig(cs_, 0, 0); }, 1, &S->gr_eig,
+                       &S->ex_eig);
+    if (st != EOT_OK) return st;
+  }
+  st = load_weights(S, a, b, s, 0);
+  if (st != EOT_OK) return st;
+  st = standalone_grid(S, C, f, n, g, m, eps, s, nullptr);
+  if (st != EOT_OK) return st;
+  Prob& P = S->hP;
+  CUDA_TRY(cudaMemcpyAsync(P.f[0], f, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(P.g[0], g, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  State st0{};
+  CUDA_TRY(cudaMemcpyAsync(S->dSt, &st0, sizeof(State), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(S->dP, &P, sizeof(Prob), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(launch_split(S->dP, P.f[0], P.loga, n, P.rs[0], s));
+  CUDA_TRY(launch_split(S->dP, P.g[0], P.logb, m, P.cs[0], s));
+  if (use_V_as_start) {
+    std::vector<double> hv((size_t)n * ell);
+    std::vector<float> hvf((size_t)n * ell);
+    CUDA_TRY(cudaMemcpy(hv.data(), V, hv.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < hv.size(); ++i) hvf[i] = (float)hv[i];
+    CUDA_TRY(cudaMemcpyAsync(S->V, hvf.data(), hvf.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+  }
+  init_block_kernel<<<std::min(ceil_div((long long)n * p, 256), 8 * S->ctx->nsm), 256, 0, s>>>(
+      S->Xb, n, p, 0x5EEDull, use_V_as_start ? S->V : nullptr, use_V_as_start ? ell : 0);
+  CUDA_TRY(S->wgram(S->Xb, S->Xb, P.a, 0, n, p, P.a, S->Xb, S->epart, S->evpart, S->GXX, S->cvec,
+                    0, s));
+  eig_small_kernel<<<1, 256, 0, s>>>(p, ell, 0, S->GXX, S->Tm, S->cvec, S->Bm, S->theta, S->resid,
+                                     S->efail);
+  apply_kernel<<<ceil_div(n, 64), 256, (size_t)(p * p + 64 * p) * 4, s>>>(S->Xb, S->cvec, S->Bm, n,
+                                                                         p, S->Zb);
+  eig_setup_kernel<<<1, 1, 0, s>>>(S->dSt, tol, max_iter, max_iter + 4);
+  st = S->run_loop(S->ex_eig, 1, max_iter + 5);
+  if (st != EOT_OK) return st;
+  take_cols_kernel<<<std::min(ceil_div((long long)n * ell, 256), 8 * S->ctx->nsm), 256, 0, s>>>(
+      S->Zb, n, p, ell, S->V);
+  std::vector<float> hvf((size_t)n * ell);
+  CUDA_TRY(cudaMemcpyAsync(hvf.data(), S->V, hvf.size() * sizeof(float), cudaMemcpyDeviceToHost, s));
+  std::vector<double> th(p);
+  CUDA_TRY(cudaMemcpyAsync(th.data(), S->theta, p * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(S->hSt, S->dSt, sizeof(State), cudaMemcpyDeviceToHost, s));
+  st = standalone_finish(s, stream);
+  if (st != EOT_OK) return st;
+  std::vector<double> hv(hvf.begin(), hvf.end());
+  CUDA_TRY(cudaMemcpy(V, hv.data(), hv.size() * sizeof(double), cudaMemcpyHostToDevice));
+  if (rho2) CUDA_TRY(cudaMemcpy(rho2, th.data(), ell * sizeof(double), cudaMemcpyHostToDevice));
+  if (iters_out) *iters_out = S->hSt->eig_iter;
+  if (resid_out) *resid_out = S->hSt->eig_resid;
+  if (S->hSt->eig_done == 4) return fail(EOT_ETIMEDOUT, "mode loop reached its body cap");
+  return S->hSt->eig_done == 1 ? EOT_OK : EOT_NOT_CONVERGED;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Batches and the serving loop.
+// ===========================================================================
+#include <condition_variable>
+#include <deque>
+#include <thread>
+
+namespace eotk {
+
+static int batch_threads(int count) {
+  const char* e = getenv("EOT_BATCH_THREADS");
+  int t = e ? atoi(e) : 8;
+  return std::max(1, std::min(t, count));
+}
+
+}  // namespace eotk
+
+struct eot_server {
+  struct Request {
+    uint64_t ticket = 0, cloud_id = 0;
+    eot_problem prob{};
+    std::vector<double> a, b;
+    std::vector<float> C, X, Y;
+    size_t footprint = 0;
+    double t_submit = 0, t_done = 0;
+    std::vector<double> f, g;
+    eot_result res{};
+    eot_status status = EOT_PENDING;
+    bool done = false;
+  };
+  struct Cached {
+    int n = 0, m = 0;
+    double eps = 0;
+    double* f = nullptr;   // device-resident potentials
+  };
+  eot_options opt{};
+  size_t budget = 0;
+  int slots = 1;
+  int device = 0;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<std::shared_ptr<Request>> queue;
+  std::map<uint64_t, std::shared_ptr<Request>> all;
+  std::map<uint64_t, Cached> cache;
+  size_t in_use = 0;
+  bool stop = false;
+  uint64_t next = 1;
+  std::vector<std::thread> workers;
+  std::vector<double> lat;
+  double t_first = -1, t_last = 0;
+  int completed = 0;
+
+  void worker() {
+    cudaSetDevice(device);
+    for (;;) {
+      std::shared_ptr<Request> r;
+      Cached warm;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        for (;;) {
+          if (stop) return;
+          for (auto it = queue.begin(); it != queue.end(); ++it) {
+            if ((*it)->footprint <= budget - std::min(budget, in_use)) {
+              r = *it;
+              queue.erase(it);
+              break;
+            }
+            if ((*it)->footprint > budget) {   // can never fit
+              (*it)->status = EOT_ENOMEM;
+              (*it)->res.status = EOT_ENOMEM;
+              (*it)->done = true;
+              queue.erase(it);
+              break;
+            }
+          }
+          if (r) break;
+          cv.wait(lk);
+        }
+        in_use += r->footprint;
+        if (r->cloud_id) {
+          auto it = cache.find(r->cloud_id);
+          if (it != cache.end() && it->second.n == r->prob.n && it->second.m == r->prob.m)
+            warm = it->second;
+        }
+      }
+      eot_options o = opt;
+      o.stream = nullptr;
+      const double* finit = nullptr;
+      if (warm.f) {
+        finit = warm.f;
+        if (warm.eps > r->prob.eps) {
+          o.eps_start = warm.eps * (o.eps_factor > 0 && o.eps_factor < 1 ? o.eps_factor : 0.5);
+        } else {
+          o.eps_start = 0.0;
+        }
+      }
+      double* keep = nullptr;
+      if (r->cloud_id) cudaMalloc(&keep, r->prob.n * sizeof(double));
+      r->f.assign(r->prob.n, 0.0);
+      r->g.assign(r->prob.m, 0.0);
+      eot_status st = eotk::solve_one(&r->prob, &o, r->f.data(), r->g.data(), &r->res, finit, keep);
+      eotk::drop_thread_cache();
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        in_use -= r->footprint;
+        r->status = st;
+        r->res.status = st;
+        r->t_done = eotk::now_s();
+        r->done = true;
+        lat.push_back(r->t_done - r->t_submit);
+        t_last = r->t_done;
+        ++completed;
+        if (keep) {
+          if (st >= 0) {
+            auto& c = cache[r->cloud_id];
+            if (c.f) cudaFree(c.f);
+            c.f = keep;
+            c.n = r->prob.n;
+            c.m = r->prob.m;
+            c.eps = r->prob.eps;
+          } else {
+            cudaFree(keep);
+          }
+        }
+      }
+      cv.notify_all();
+    }
+  }
+};
+
+extern "C" {
+
+eot_status eot_solve_batch(int32_t count, const eot_problem* probs, const eot_options* opt,
+                           double* const* f_out, double* const* g_out, eot_result* results) {
+  if (count < 0 || (count > 0 && (!probs || !f_out || !g_out)))
+    return fail(EOT_EINVAL, "bad batch arguments");
+  if (count == 0) return EOT_OK;
+  eot_options o;
+  if (opt) o = *opt;
+  else eot_default_options(&o);
+  if (o.ell != 0) return fail(EOT_EINVAL, "eot_solve_batch runs plain Sinkhorn (ell = 0)");
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  std::vector<eot_status> st(count, EOT_OK);
+  std::vector<eot_result> rs(count);
+  std::atomic<int> nexti(0);
+  std::vector<std::string> errs(count);
+  auto work = [&]() {
+    cudaSetDevice(dev);
+    for (;;) {
+      const int k = nexti.fetch_add(1);
+      if (k >= count) break;
+      eot_options ok = o;
+      ok.stream = nullptr;
+      st[k] = eotk::solve_one(&probs[k], &ok, f_out[k], g_out[k], &rs[k]);
+      if (st[k] < 0) {
+        rs[k].status = st[k];
+        errs[k] = eot_last_error();
+      }
+    }
+    eotk::drop_thread_cache();
+  };
+  const int T = eotk::batch_threads(count);
+  std::vector<std::thread> th;
+  for (int t = 0; t < T; ++t) th.emplace_back(work);
+  for (auto& t : th) t.join();
+  eot_status worst = EOT_OK;
+  for (int k = 0; k < count; ++k) {
+    if (results) results[k] = rs[k];
+    if (st[k] < 0 && (worst >= 0 || st[k] < worst)) {
+      worst = st[k];
+      t_err = errs[k];
+    } else if (worst == EOT_OK && st[k] > 0) {
+      worst = st[k];
+    }
+  }
+  return worst;
+}
+
+eot_status eot_server_create(const eot_options* opt, size_t hbm_budget_bytes, int32_t max_slots,
+                             eot_server** srv) {
+  if (!srv || max_slots < 1 || hbm_budget_bytes == 0) return fail(EOT_EINVAL, "bad server arguments");
+  auto* s = new eot_server();
+  if (opt) s->opt = *opt;
+  else eot_default_options(&s->opt);
+  if (s->opt.ell != 0 && s->opt.prec != EOT_PREC_FP32) {
+    delete s;
+    return fail(EOT_EINVAL, "bad options");
+  }
+  s->budget = hbm_budget_bytes;
+  s->slots = max_slots;
+  cudaGetDevice(&s->device);
+  for (int k = 0; k < max_slots; ++k) s->workers.emplace_back([s]() { s->worker(); });
+  *srv = s;
+  return EOT_OK;
+}
+
+eot_status eot_server_submit(eot_server* srv, const eot_problem* prob, uint64_t cloud_id,
+                             uint64_t* ticket) {
+  if (!srv || !prob || !ticket) return fail(EOT_EINVAL, "null argument");
+  if (prob->mem != EOT_MEM_HOST) return fail(EOT_EINVAL, "server requests use host memory");
+  eot_status vs = eotk::validate(prob, &srv->opt);
+  if (vs != EOT_OK) return vs;
+  auto r = std::make_shared<eot_server::Request>();
+  const int n = prob->n, m = prob->m, d = prob->d;
+  r->a.assign(prob->a, prob->a + n);
+  r->b.assign(prob->b, prob->b + m);
+  if (prob->C) r->C.assign((const float*)prob->C, (const float*)prob->C + (size_t)n * m);
+  if (prob->X) {
+    r->X.assign((const float*)prob->X, (const float*)prob->X + (size_t)n * d);
+    r->Y.assign((const float*)prob->Y, (const float*)prob->Y + (size_t)m * d);
+  }
+  r->prob = *prob;
+  r->prob.a = r->a.data();
+  r->prob.b = r->b.data();
+  r->prob.C = prob->C ? r->C.data() : nullptr;
+  r->prob.X = prob->X ? r->X.data() : nullptr;
+  r->prob.Y = prob->X ? r->Y.data() : nullptr;
+  r->prob.f_init = nullptr;
+  r->cloud_id = cloud_id;
+  eotk::DeviceCtx* ctx = nullptr;
+  eot_status cs = eotk::get_ctx(&ctx);
+  if (cs != EOT_OK) return cs;
+  r->footprint = eotk::solver_footprint(ctx, n, m, d, srv->opt.ell,
+                                        eotk::mode_block(n, srv->opt.ell, srv->opt.oversample));
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    r->ticket = srv->next++;
+    r->t_submit = eotk::now_s();
+    if (srv->t_first < 0) srv->t_first = r->t_submit;
+    srv->queue.push_back(r);
+    srv->all[r->ticket] = r;
+    *ticket = r->ticket;
+  }
+  srv->cv.notify_all();
+  return EOT_OK;
+}
+
+eot_status eot_server_poll(eot_server* srv, uint64_t ticket, double* f_out, double* g_out,
+                           eot_result* res) {
+  if (!srv) return fail(EOT_EINVAL, "null server");
+  std::shared_ptr<eot_server::Request> r;
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->all.find(ticket);
+    if (it == srv->all.end()) return fail(EOT_ENOTFOUND, "unknown ticket");
+    r = it->second;
+    if (!r->done) return EOT_PENDING;
+    srv->all.erase(it);
+  }
+  if (f_out && !r->f.empty()) std::memcpy(f_out, r->f.data(), r->f.size() * sizeof(double));
+  if (g_out && !r->g.empty()) std::memcpy(g_out, r->g.data(), r->g.size() * sizeof(double));
+  if (res) *res = r->res;
+  return r->status;
+}
+
+eot_status eot_server_stats(eot_server* srv, double* p50_s, double* p99_s, double* solves_per_s) {
+  if (!srv) return fail(EOT_EINVAL, "null server");
+  std::vector<double> l;
+  double t0, t1;
+  int done;
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    l = srv->lat;
+    t0 = srv->t_first;
+    t1 = srv->t_last;
+    done = srv->completed;
+  }
+  std::sort(l.begin(), l.end());
+  auto pct = [&](double q) {
+    if (l.empty()) return 0.0;
+    const size_t k = std::min(l.size() - 1, (size_t)std::ceil(q * l.size()) - (q > 0 ? 1 : 0));
+    return l[k];
+  };
+  if (p50_s) *p50_s = pct(0.5);
+  if (p99_s) *p99_s = pct(0.99);
+  if (solves_per_s) *solves_per_s = (done > 0 && t1 > t0) ? done / (t1 - t0) : 0.0;
+  return EOT_OK;
+}
+
+void eot_server_destroy(eot_server* srv) {
+  if (!srv) return;
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->stop = true;
+  }
+  srv->cv.notify_all();
+  for (auto& t : srv->workers) t.join();
+  for (auto& kv : srv->cache)
+    if (kv.second.f) cudaFree(kv.second.f);
+  delete srv;
+}
+
+}  // extern "C"

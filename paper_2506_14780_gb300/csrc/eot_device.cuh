@@ -1,0 +1,89 @@
+// Device-side building blocks shared by the pass kernels.
+//
+// Exponent formation.  Every O(nm) pass evaluates terms
+//     x_ij = (u_i + s_j - C_ij) / eps
+// where u (per reduction index) and s (per output index) are float64
+// potentials (already including eps * log(weight) where the transform needs it)
+// and C_ij is the float32 cost.  Near a Sinkhorn fixed point the dominant terms
+// have x_ij in [-30, 0], while u_i, s_j and C_ij are O(1): forming u + s - C in
+// float32 would lose ~1e-7 absolute, i.e. ~1e-4 in x at eps = 1e-3.  The kernels
+// instead split every potential p into
+//     p = pH + pL,  pH on the grid 2^-q (exact in float32),  |pL| <= 2^-(q+1),
+// and round C_ij to the same grid with one addition of a "magic" constant
+// M = 1.5 * 2^(23-q) (all values stay inside the binade [2^(23-q), 2^(24-q)),
+// whose float32 spacing is exactly 2^-q):
+//     r  = C + (M - sH)         = (M - sH) + h,      h = C rounded to the grid
+//     tH = (uH + M) - r         = uH + sH - h        (exact: same binade, Sterbenz)
+//     h  = r - (M - sH),  l = C - h                  (both exact)
+//     x * eps = (tH - l) + uL + sL
+// so the only rounding errors are those of the last two additions, relative to
+// |x * eps| itself.  The division by eps is a multiplication by log2(e)/eps
+// folded into the exp2 argument together with sL.  Validity needs
+// |pH| + |C| < 2^(22-q); the host picks q from the cost range.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace eotk {
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+// Re-centring threshold of the running log-sum-exp (log2 units).
+constexpr float kRecenter = 64.0f;
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// The exact part of the exponent (see the header comment).
+//   C: cost, K: M - sH (output-side shift), A: uH + M (reduction-side), returns
+//   tH - l ; the caller adds uL and scales.
+__device__ __forceinline__ float split_exponent(float C, float K, float A) {
+  float r = __fadd_rn(C, K);
+  float tH = __fsub_rn(A, r);
+  float h = __fsub_rn(r, K);
+  float l = __fsub_rn(C, h);
+  return __fsub_rn(tH, l);
+}
+
+// Running (reference, sum) state of a log-sum-exp in log2 units:
+//   S = sum_k 2^(y_k - ref); ref is re-centred when the running maximum leaves
+//   [-kRecenter, kRecenter] around it, which keeps every term and the sum finite.
+struct Lse2 {
+  float ref;   // reference point (log2 units)
+  float run;   // running max of (y - ref)
+  float S;
+  __device__ __forceinline__ void init() { ref = 0.f; run = -INFINITY; S = 0.f; }
+};
+
+// Combine two (ref, S) partial states: result in state a.
+__device__ __forceinline__ void lse2_merge(float& ra, float& Sa, float rb, float Sb) {
+  if (Sb == 0.f) return;
+  if (Sa == 0.f) { ra = rb; Sa = Sb; return; }
+  if (ra == rb) { Sa += Sb; return; }
+  if (ra > rb) { Sa += Sb * ex2_approx(rb - ra); }
+  else { Sa = Sa * ex2_approx(ra - rb) + Sb; ra = rb; }
+}
+
+// Warp-wide sum of a double.
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Split a float64 value into (grid-aligned hi, float32 lo) on the 2^-q grid.
+__device__ __forceinline__ void split_grid(double x, double scale /*2^q*/, double inv /*2^-q*/,
+                                           double& hi, float& lo) {
+  hi = rint(x * scale) * inv;
+  lo = (float)(x - hi);
+}
+
+}  // namespace eotk

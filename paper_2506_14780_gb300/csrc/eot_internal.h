@@ -1,0 +1,126 @@
+// Internal structures shared by the kernels and the host driver.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace eotk {
+
+// Column pass tile: 128 output columns per CTA (32 lanes x 4), 8 warps over rows.
+constexpr int kColTile = 128;
+// Row pass tile: 8 warps x 4 rows = 32 output rows per CTA.
+constexpr int kRowsPerWarp = 4;
+constexpr int kRowTile = 8 * kRowsPerWarp;
+constexpr int kThreads = 256;
+// Widest mode block handled by the accumulating passes.
+constexpr int kMaxK = 64;
+// Widest block of the subspace iteration (modes + oversampling).
+constexpr int kMaxP = 48;
+
+// What the grid-wide final step of a pass does with its reductions.
+enum PassMode : int {
+  MODE_PLAIN = 0,     // standalone transform: write outputs only
+  MODE_SK_COL = 1,    // Sinkhorn column pass: convergence test, advance g
+  MODE_SK_ROW = 2,    // Sinkhorn / SK-NR row pass
+  MODE_S4 = 3,        // SK-NR column pass at f_k: test, h, W, Q_semi
+  MODE_TRIAL = 4,     // SK-NR trial column pass at f': accept / reject
+  MODE_EVAL = 5,      // marginal evaluation only (no potential update)
+  MODE_G_INIT = 6     // first column transform of a level (Alg. 4.1 line 3, k = 1)
+};
+
+// Device-resident solver state (one per problem).
+struct State {
+  int iter;        // Algorithm 4.1 iterations done at the current level
+  int done;        // 0 running, 1 converged, 2 max_iter, 3 numeric error
+  int cur_f;       // index of the current f buffer (0/1)
+  int cur_g;       // index of the current g buffer (0..2)
+  int nr_acc, nr_rej;
+  int nr_ok;       // 1 if the Newton system of this iteration was solvable
+  int max_iter;
+  double tol;
+  double l1_col;   // ||pi^T 1 - b||_1 at the last test
+  double l1_row;
+  double qsemi;    // Q_semi(f_k) of the last S4 pass
+  double dq;       // Q_semi(f') - Q_semi(f_k) of the last trial
+  double sum_wL;   // sum_j w_j L_j of the last pass
+  double sum_wout; // sum_j w_j out_j of the last pass
+  double dot_vd_a; // <V Delta, a>
+  double sum_af;   // <f_k, a> after the last row pass
+  int numeric;     // count of non-finite outputs seen
+  int body_runs;   // executions of the current device loop body (hard-capped)
+  int body_cap;
+  // mode computation
+  int eig_iter, eig_done, eig_max_iter, eig_fail;
+  double eig_tol, eig_resid;
+  int total_iters;
+  int pad2;
+};
+
+// Split arrays of one potential buffer (see eot_device.cuh).
+struct Split {
+  float* A;   // H(p + eps log w) + M     (reduction-side use)
+  float* AL;  // L(p + eps log w)
+  float* K;   // M - H(p)                 (output-side shift use)
+  float* KL;  // L(p)
+};
+
+// Everything the pass kernels need for one problem; lives in device memory.
+struct Prob {
+  int n, m;
+  const float* C;          // n x m row-major
+  const double *a, *b;     // weights
+  const double *loga, *logb;
+  double eps;
+  float k2;                // log2(e) / eps
+  float M;                 // magic constant 1.5 * 2^(23-q)
+  double qscale, qinv;     // 2^q, 2^-q
+  double* f[2];
+  double* g[3];
+  Split rs[2];
+  Split cs[3];
+  float* Lrow;             // natural-log marginal ratio of the last row pass (n)
+  float* Lcol;             // ... of the last column pass (m)
+  // column pass tiling
+  int nstripe, rows_per_stripe, ncolblk;
+  float2* part_col;        // [nstripe][m]
+  unsigned* cnt_col;       // [ncolblk]
+  double* acc_col;         // [ncolblk][4]
+  // row pass tiling
+  int nseg, cols_per_seg, nrowblk;
+  float2* part_row;        // [nseg][n]
+  unsigned* cnt_row;       // [nrowblk]
+  double* acc_row;         // [nrowblk][4]
+  unsigned* gcnt;          // [4] grid-level arrival counters
+  State* st;
+  // SK-NR
+  int ell;                 // number of modes (0: none)
+  const float* V;          // n x ell (row-major), a-orthonormal
+  float* W;                // m x ell: W_j = pi(f_k,h)^T V  (row j)
+  float* Wpart;            // [nstripe][m][ell] partial unnormalised sums
+  double* delta;           // ell: Newton step
+  double* GV;              // ell x ell: V^T D_a V
+  double* Va;              // ell: V^T a
+  double* WtW;             // ell x ell: sum_j W_j W_j^T / b_j
+  double* grad;            // ell: gradient on V
+  double pot_bound;        // |potential| limit of the exact exponent formation
+  unsigned long long cond; // graph conditional handle of the enclosing device loop
+  // plain-mode outputs
+  double* out_plain;       // standalone transform output
+  double* logratio_plain;
+};
+
+// Arguments of the accumulating passes (accum.cu).
+struct AccArgs {
+  const Prob* P;
+  int mode;              // 0: Op(pi)^T Z, 1: fused SK-NR column pass, 2: Op(pi) Z
+  int k;                 // number of live columns of Z (<= kernel template width)
+  const float* Z;        // (n or m) x k, row-major (Z for products, V for SK-NR)
+  float* out;            // (m or n) x k output (products) or W (SK-NR)
+  float* part;           // [nseg][len][K + 2] partial states
+  unsigned* cnt;         // [nblk] arrival counters
+  int nseg, seg_len, nblk;
+  int fbuf, gbuf;        // which split buffers hold f and g (products)
+  double* blkacc;        // [nblk][4]
+  unsigned* gcnt;
+};
+
+}  // namespace eotk

@@ -1,0 +1,542 @@
+// Log-domain Sinkhorn half-steps on a stored float32 cost (paper Eq. foc_f,
+// Eq. foc_g, Eq. SK_iterations), with their reductions fused:
+//
+//   column pass  out_j = s_j - eps * L_j,  L_j = log sum_i exp(x_ij),
+//                x_ij  = log a_i + (u_i + s_j - C_ij)/eps
+//   row pass     out_i = s_i - eps * L_i,  L_i = log sum_j exp(x_ij),
+//                x_ij  = log b_j + (s_i + u_j - C_ij)/eps
+//
+// s is the current potential on the output side (a shift that keeps x near 0
+// at convergence; the result does not depend on it in exact arithmetic) and u
+// the potential on the reduction side.  exp(L_j) is the marginal ratio
+// (pi^T 1)_j / b_j of pi(u, s), so the same pass yields the marginal error used
+// by the stopping test of Algorithm 4.1 (and L1 of a column pass at f_k is
+// ||pi^T 1 - b||_1 for pi(f_k, g_k)).
+//
+// Layout: C row-major n x m.  Column pass: CTA = 128 columns (32 lanes x float4)
+// x one stripe of rows, 8 warps interleaved over the stripe's rows; each warp
+// load is 4 full 128-byte lines.  Row pass: CTA = 32 rows (4 per warp) x one
+// segment of columns, lanes along the row with float4 loads.  Partial
+// (reference, sum) states go to a [segment][index] buffer; the last CTA to
+// finish an index block (atomic arrival counter) combines the segments in fixed
+// order, so results are deterministic and independent of scheduling; the last
+// index block then runs the mode-specific grid-wide step.
+#include "eot_device.cuh"
+#include "eot_internal.h"
+
+namespace eotk {
+
+// ---------------------------------------------------------------------------
+// Per-index combine: merge nseg partial states of index `idx`, produce the new
+// potential, its split arrays, and the index's contributions to the scalars.
+// Returns (w*|expm1 L|, w*L, w*out) through acc[0..2].
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void combine_index(const float2* __restrict__ part, int nseg,
+                                              int stride, int idx, const Prob& P,
+                                              const double* __restrict__ shift,
+                                              const double* __restrict__ w,
+                                              const double* __restrict__ logw,
+                                              double* __restrict__ out, Split so,
+                                              float* __restrict__ Lout, double acc[3],
+                                              int* numeric) {
+  float R = -INFINITY;
+  for (int s = 0; s < nseg; ++s) {
+    float2 p = __ldcg(&part[(size_t)s * stride + idx]);
+    if (p.y > 0.f && p.x > R) R = p.x;
+  }
+  double S = 0.0;
+  for (int s = 0; s < nseg; ++s) {
+    float2 p = __ldcg(&part[(size_t)s * stride + idx]);
+    if (p.y > 0.f) S += (double)(p.x == R ? p.y : p.y * ex2_approx(p.x - R));
+  }
+  float L = R * kLn2 + log1pf((float)(S - 1.0));
+  double sh = shift[idx];
+  double o = sh - P.eps * (double)L;
+  if (!isfinite(o) || !(S > 0.0) || fabs(o) > P.pot_bound) {
+    atomicAdd(numeric, 1);
+    o = sh;
+    L = 0.f;
+  }
+  if (out) out[idx] = o;
+  if (Lout) Lout[idx] = L;
+  if (so.A) {
+    double hi;
+    float lo;
+    split_grid(o + P.eps * logw[idx], P.qscale, P.qinv, hi, lo);
+    so.A[idx] = (float)(hi + (double)P.M);
+    so.AL[idx] = lo;
+    split_grid(o, P.qscale, P.qinv, hi, lo);
+    so.K[idx] = (float)((double)P.M - hi);
+    so.KL[idx] = lo;
+  }
+  double wi = w[idx];
+  acc[0] = wi * (double)fabsf(expm1f(L));
+  acc[1] = wi * (double)L;
+  acc[2] = wi * o;
+}
+
+// Block-wide deterministic sum of 3 doubles; result valid in thread 0.
+__device__ __forceinline__ void block_sum3(double v[3], double* sh /*[3*8]*/) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    double x = warp_sum_d(v[k]);
+    if (lane == 0) sh[k * 8 + wid] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 3; ++k) {
+      double t = 0.0;
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[k * 8 + i];
+      v[k] = t;
+    }
+  }
+}
+
+// Grid-final step shared by both passes.  Called by one thread.
+__device__ void final_step(const Prob& P, int mode, const double* acc_blocks, int nblk,
+                           int dst) {
+  double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+  for (int b = 0; b < nblk; ++b) {
+    t0 += __ldcg(&acc_blocks[b * 4 + 0]);
+    t1 += __ldcg(&acc_blocks[b * 4 + 1]);
+    t2 += __ldcg(&acc_blocks[b * 4 + 2]);
+  }
+  State* st = P.st;
+  st->sum_wL = t1;
+  st->sum_wout = t2;
+  if (st->numeric > 0 && mode != MODE_PLAIN && mode != MODE_EVAL) {
+    st->done = 3;
+    return;
+  }
+  switch (mode) {
+    case MODE_SK_ROW:
+      st->l1_row = t0;
+      st->sum_af = t2;
+      break;
+    case MODE_TRIAL: {
+      // Q_semi(f') - Q_semi(f_k) = <V Delta, a> + <h' - h, b>,  h' - h = -eps L
+      const double dq = st->dot_vd_a - P.eps * t1;
+      st->dq = dq;
+      if (dq > 0.0) {
+        st->nr_acc += 1;
+        st->cur_f = 1 - st->cur_f;
+        st->cur_g = (st->cur_g + 2) % 3;
+      } else {
+        st->nr_rej += 1;
+        st->cur_g = (st->cur_g + 1) % 3;
+      }
+      break;
+    }
+    case MODE_SK_COL:
+      st->l1_col = t0;
+      st->qsemi = st->sum_af + t2;   // Q_semi(f_k) = <f_k, a> + <f_k^{C,eps}, b>
+      st->iter += 1;
+      if (t0 < st->tol) st->done = 1;
+      else if (st->iter >= st->max_iter) st->done = 2;
+      else st->cur_g = dst;
+      break;
+    case MODE_EVAL:
+      st->l1_col = t0;
+      break;
+    case MODE_G_INIT:
+      st->cur_g = dst;
+      break;
+    default:
+      st->l1_col = t0;
+      break;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Column pass.  VEC = 4: m % 4 == 0 (16-byte aligned rows), float4 loads;
+// VEC = 1: scalar loads with column bounds checks.
+// ---------------------------------------------------------------------------
+template <int VEC>
+__global__ void __launch_bounds__(kThreads) col_pass_kernel(const Prob* __restrict__ PP, int mode) {
+  const Prob& P = *PP;
+  State* st = P.st;
+  if (mode != MODE_PLAIN && mode != MODE_EVAL && st->done) return;
+  const int cf = st->cur_f, cg = st->cur_g;
+  // source f, shift g and destination g buffers: a trial pass (Algorithm 4.1,
+  // value at f' = f_k + V Delta) reads f' and is shifted by h = f_k^{C,eps}.
+  const int src_f = (mode == MODE_TRIAL) ? 1 - cf : cf;
+  const int sh_g = (mode == MODE_TRIAL) ? (cg + 1) % 3 : cg;
+  const int dst_g = (mode == MODE_EVAL) ? -1 : (mode == MODE_TRIAL ? (cg + 2) % 3 : (cg + 1) % 3);
+  if (mode == MODE_TRIAL && !st->nr_ok) return;
+  const float* __restrict__ rA = P.rs[src_f].A;
+  const float* __restrict__ rAL = P.rs[src_f].AL;
+  const float* __restrict__ cK = P.cs[sh_g].K;
+  const float* __restrict__ cKL = P.cs[sh_g].KL;
+
+  __shared__ float2 s_row[kThreads];          // (A_i, AL_i) staging
+  __shared__ float2 s_part[8][kColTile];      // per-warp partial states
+  __shared__ double s_red[24];
+  __shared__ unsigned s_last;
+
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int n = P.n, m = P.m;
+  const int cb = blockIdx.x, stripe = blockIdx.y;
+  const int j0 = cb * kColTile + lane * 4;
+  const int i_beg = stripe * P.rows_per_stripe;
+  const int i_end = min(n, i_beg + P.rows_per_stripe);
+  const float k2 = P.k2;
+
+  float K[4], cc[4], ref[4], run[4], S[4];
+  bool valid[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int j = j0 + c;
+    valid[c] = j < m;
+    K[c] = valid[c] ? cK[j] : P.M;
+    cc[c] = valid[c] ? cKL[j] * k2 : 0.f;
+    ref[c] = 0.f;
+    run[c] = -INFINITY;
+    S[c] = 0.f;
+  }
+  const bool any_valid = valid[0];
+
+  for (int base = i_beg; base < i_end; base += kThreads) {
+    const int nrows = min(kThreads, i_end - base);
+    __syncthreads();
+    if ((int)threadIdx.x < nrows) {
+      s_row[threadIdx.x] = make_float2(rA[base + threadIdx.x], rAL[base + threadIdx.x]);
+    }
+    __syncthreads();
+    if (!any_valid) continue;
+    // rows r = wid, wid + 8, ... of this chunk, 4 at a time
+    for (int r0 = wid; r0 < nrows; r0 += 32) {
+      float y[4][4];
+      int cnt = 0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = r0 + 8 * u;
+        if (r < nrows) {
+          ++cnt;
+          const float2 ra = s_row[r];
+          const float* crow = P.C + (size_t)(base + r) * m + j0;
+          float cv[4];
+          if (VEC == 4) {
+            const float4 c4 = __ldg(reinterpret_cast<const float4*>(crow));
+            cv[0] = c4.x; cv[1] = c4.y; cv[2] = c4.z; cv[3] = c4.w;
+          } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) cv[c] = valid[c] ? __ldg(crow + c) : 0.f;
+          }
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const float t = __fadd_rn(split_exponent(cv[c], K[c], ra.x), ra.y);
+            y[u][c] = __fmaf_rn(t, k2, cc[c]);
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) y[u][c] = -INFINITY;
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float mx = fmaxf(fmaxf(y[0][c], y[1][c]), fmaxf(y[2][c], y[3][c]));
+        run[c] = fmaxf(run[c], mx);
+        if (run[c] > kRecenter || (run[c] < -kRecenter && run[c] > -INFINITY)) {
+          const float d = run[c];
+          if (S[c] > 0.f) S[c] *= ex2_approx(-d);
+          ref[c] += d;
+          cc[c] -= d;
+          run[c] = 0.f;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) y[u][c] -= d;
+        }
+        float acc = 0.f;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc += ex2_approx(y[u][c]);
+        S[c] += acc;
+      }
+      (void)cnt;
+    }
+  }
+  // intra-CTA combine over the 8 warps
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    if (!valid[c]) S[c] = 0.f;
+    s_part[wid][lane * 4 + c] = make_float2(ref[c], S[c]);
+  }
+  __syncthreads();
+  if (threadIdx.x < kColTile) {
+    const int j = cb * kColTile + threadIdx.x;
+    float2 p = s_part[0][threadIdx.x];
+    for (int w = 1; w < 8; ++w) {
+      float2 q = s_part[w][threadIdx.x];
+      lse2_merge(p.x, p.y, q.x, q.y);
+    }
+    if (j < m) P.part_col[(size_t)stripe * m + j] = p;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(&P.cnt_col[cb], 1u);
+    s_last = (prev == (unsigned)(P.nstripe - 1));
+  }
+  __syncthreads();
+  if (!s_last) return;
+  // --- this CTA combines column block cb ---
+  __threadfence();
+  double accv[3] = {0.0, 0.0, 0.0};
+  if (threadIdx.x < kColTile) {
+    const int j = cb * kColTile + threadIdx.x;
+    if (j < m) {
+      double* out;
+      Split so;
+      float* Lout = P.Lcol;
+      if (mode == MODE_PLAIN) {
+        out = P.out_plain;
+        so = Split{nullptr, nullptr, nullptr, nullptr};
+      } else if (mode == MODE_EVAL) {
+        out = nullptr;
+        so = Split{nullptr, nullptr, nullptr, nullptr};
+      } else {
+        out = P.g[dst_g];
+        so = P.cs[dst_g];
+      }
+      combine_index(P.part_col, P.nstripe, m, j, P, P.g[sh_g], P.b, P.logb, out, so, Lout, accv,
+                    &st->numeric);
+      if (mode == MODE_PLAIN && P.logratio_plain) P.logratio_plain[j] = (double)P.Lcol[j];
+    }
+  }
+  block_sum3(accv, s_red);
+  if (threadIdx.x == 0) {
+    P.cnt_col[cb] = 0u;
+    double* ab = P.acc_col + cb * 4;
+    ab[0] = accv[0];
+    ab[1] = accv[1];
+    ab[2] = accv[2];
+    __threadfence();
+    const unsigned prev = atomicAdd(&P.gcnt[0], 1u);
+    if (prev == (unsigned)(P.ncolblk - 1)) {
+      __threadfence();
+      P.gcnt[0] = 0u;
+      final_step(P, mode, P.acc_col, P.ncolblk, dst_g);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Row pass.
+// ---------------------------------------------------------------------------
+template <int VEC>
+__global__ void __launch_bounds__(kThreads) row_pass_kernel(const Prob* __restrict__ PP, int mode) {
+  const Prob& P = *PP;
+  State* st = P.st;
+  if (mode != MODE_PLAIN && mode != MODE_EVAL && st->done) return;
+  const int cf = st->cur_f, cg = st->cur_g;
+  const float* __restrict__ cA = P.cs[cg].A;
+  const float* __restrict__ cAL = P.cs[cg].AL;
+  const float* __restrict__ rK = P.rs[cf].K;
+  const float* __restrict__ rKL = P.rs[cf].KL;
+
+  __shared__ float2 s_part[kRowTile];
+  __shared__ double s_red[24];
+  __shared__ unsigned s_last;
+
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int n = P.n, m = P.m;
+  const int rb = blockIdx.x, seg = blockIdx.y;
+  const int i0 = rb * kRowTile + wid * kRowsPerWarp;
+  const int c_beg = seg * P.cols_per_seg;
+  const int c_end = min(m, c_beg + P.cols_per_seg);
+  const float k2 = P.k2;
+
+  float K[kRowsPerWarp], cc[kRowsPerWarp], ref[kRowsPerWarp], run[kRowsPerWarp], S[kRowsPerWarp];
+  bool rv[kRowsPerWarp];
+#pragma unroll
+  for (int r = 0; r < kRowsPerWarp; ++r) {
+    const int i = i0 + r;
+    rv[r] = i < n;
+    K[r] = rv[r] ? rK[i] : P.M;
+    cc[r] = rv[r] ? rKL[i] * k2 : 0.f;
+    ref[r] = 0.f;
+    run[r] = -INFINITY;
+    S[r] = 0.f;
+  }
+  if (rv[0]) {
+    for (int j = c_beg + lane * 4; j < c_end; j += 128) {
+      float ca[4], cal[4];
+      bool cvld[4];
+      if (VEC == 4) {
+        const float4 a4 = __ldg(reinterpret_cast<const float4*>(cA + j));
+        const float4 l4 = __ldg(reinterpret_cast<const float4*>(cAL + j));
+        ca[0] = a4.x; ca[1] = a4.y; ca[2] = a4.z; ca[3] = a4.w;
+        cal[0] = l4.x; cal[1] = l4.y; cal[2] = l4.z; cal[3] = l4.w;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) cvld[c] = true;
+      } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          cvld[c] = j + c < c_end;
+          ca[c] = cvld[c] ? __ldg(cA + j + c) : 0.f;
+          cal[c] = cvld[c] ? __ldg(cAL + j + c) : 0.f;
+        }
+      }
+      float y[kRowsPerWarp][4];
+#pragma unroll
+      for (int r = 0; r < kRowsPerWarp; ++r) {
+        float cv[4];
+        if (rv[r]) {
+          const float* crow = P.C + (size_t)(i0 + r) * m + j;
+          if (VEC == 4) {
+            const float4 c4 = __ldg(reinterpret_cast<const float4*>(crow));
+            cv[0] = c4.x; cv[1] = c4.y; cv[2] = c4.z; cv[3] = c4.w;
+          } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) cv[c] = cvld[c] ? __ldg(crow + c) : 0.f;
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) cv[c] = 0.f;
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float t = __fadd_rn(split_exponent(cv[c], K[r], ca[c]), cal[c]);
+          y[r][c] = (cvld[c] && rv[r]) ? __fmaf_rn(t, k2, cc[r]) : -INFINITY;
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < kRowsPerWarp; ++r) {
+        float mx = fmaxf(fmaxf(y[r][0], y[r][1]), fmaxf(y[r][2], y[r][3]));
+        run[r] = fmaxf(run[r], mx);
+        if (run[r] > kRecenter || (run[r] < -kRecenter && run[r] > -INFINITY)) {
+          const float d = run[r];
+          if (S[r] > 0.f) S[r] *= ex2_approx(-d);
+          ref[r] += d;
+          cc[r] -= d;
+          run[r] = 0.f;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) y[r][c] -= d;
+        }
+        S[r] += (ex2_approx(y[r][0]) + ex2_approx(y[r][1])) +
+                (ex2_approx(y[r][2]) + ex2_approx(y[r][3]));
+      }
+    }
+  }
+  // warp reduction of each row's state
+#pragma unroll
+  for (int r = 0; r < kRowsPerWarp; ++r) {
+    float rr = ref[r], ss = S[r];
+    const bool uniform = __all_sync(0xffffffffu, rr == __shfl_sync(0xffffffffu, rr, 0));
+    if (uniform) {
+      ss = warp_sum_f(ss);
+    } else {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float r2 = __shfl_xor_sync(0xffffffffu, rr, o);
+        const float s2 = __shfl_xor_sync(0xffffffffu, ss, o);
+        lse2_merge(rr, ss, r2, s2);
+      }
+    }
+    if (lane == 0) s_part[wid * kRowsPerWarp + r] = make_float2(rr, ss);
+  }
+  __syncthreads();
+  if (threadIdx.x < kRowTile) {
+    const int i = rb * kRowTile + threadIdx.x;
+    if (i < n) P.part_row[(size_t)seg * n + i] = s_part[threadIdx.x];
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(&P.cnt_row[rb], 1u);
+    s_last = (prev == (unsigned)(P.nseg - 1));
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double accv[3] = {0.0, 0.0, 0.0};
+  if (threadIdx.x < kRowTile) {
+    const int i = rb * kRowTile + threadIdx.x;
+    if (i < n) {
+      double* out;
+      Split so;
+      if (mode == MODE_PLAIN) {
+        out = P.out_plain;
+        so = Split{nullptr, nullptr, nullptr, nullptr};
+      } else if (mode == MODE_EVAL) {
+        out = nullptr;
+        so = Split{nullptr, nullptr, nullptr, nullptr};
+      } else {
+        out = P.f[cf];
+        so = P.rs[cf];
+      }
+      combine_index(P.part_row, P.nseg, n, i, P, P.f[cf], P.a, P.loga, out, so, P.Lrow, accv,
+                    &st->numeric);
+      if (mode == MODE_PLAIN && P.logratio_plain) P.logratio_plain[i] = (double)P.Lrow[i];
+    }
+  }
+  block_sum3(accv, s_red);
+  if (threadIdx.x == 0) {
+    P.cnt_row[rb] = 0u;
+    double* ab = P.acc_row + rb * 4;
+    ab[0] = accv[0];
+    ab[1] = accv[1];
+    ab[2] = accv[2];
+    __threadfence();
+    const unsigned prev = atomicAdd(&P.gcnt[1], 1u);
+    if (prev == (unsigned)(P.nrowblk - 1)) {
+      __threadfence();
+      P.gcnt[1] = 0u;
+      if (mode == MODE_EVAL) {
+        double t0 = 0.0;
+        for (int b = 0; b < P.nrowblk; ++b) t0 += __ldcg(&P.acc_row[b * 4 + 0]);
+        st->l1_row = t0;
+      } else {
+        final_step(P, mode == MODE_PLAIN ? MODE_PLAIN : MODE_SK_ROW, P.acc_row, P.nrowblk, cf);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Split arrays of a float64 potential (level start, after f' = f + V Delta...).
+// ---------------------------------------------------------------------------
+__global__ void split_kernel(const Prob* __restrict__ PP, const double* __restrict__ p,
+                             const double* __restrict__ logw, int len, Split so) {
+  const Prob& P = *PP;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < len; i += gridDim.x * blockDim.x) {
+    const double v = p[i];
+    double hi;
+    float lo;
+    split_grid(v + P.eps * logw[i], P.qscale, P.qinv, hi, lo);
+    so.A[i] = (float)(hi + (double)P.M);
+    so.AL[i] = lo;
+    split_grid(v, P.qscale, P.qinv, hi, lo);
+    so.K[i] = (float)((double)P.M - hi);
+    so.KL[i] = lo;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launch helpers.
+// ---------------------------------------------------------------------------
+cudaError_t launch_col_pass(const Prob* dP, const Prob& hP, int mode, cudaStream_t s) {
+  dim3 grid(hP.ncolblk, hP.nstripe);
+  if (hP.m % 4 == 0 && (reinterpret_cast<uintptr_t>(hP.C) & 15u) == 0)
+    col_pass_kernel<4><<<grid, kThreads, 0, s>>>(dP, mode);
+  else
+    col_pass_kernel<1><<<grid, kThreads, 0, s>>>(dP, mode);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_row_pass(const Prob* dP, const Prob& hP, int mode, cudaStream_t s) {
+  dim3 grid(hP.nrowblk, hP.nseg);
+  if (hP.m % 4 == 0 && (reinterpret_cast<uintptr_t>(hP.C) & 15u) == 0 && hP.cols_per_seg % 4 == 0)
+    row_pass_kernel<4><<<grid, kThreads, 0, s>>>(dP, mode);
+  else
+    row_pass_kernel<1><<<grid, kThreads, 0, s>>>(dP, mode);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split(const Prob* dP, const double* p, const double* logw, int len, Split so,
+                         cudaStream_t s) {
+  const int blocks = (len + 255) / 256;
+  split_kernel<<<blocks < 1024 ? blocks : 1024, 256, 0, s>>>(dP, p, logw, len, so);
+  return cudaGetLastError();
+}
+
+}  // namespace eotk

@@ -1,0 +1,306 @@
+"""ctypes binding of libeot.so (include/eot.h): the same names, argument
+marshalling only.  Every computation runs in the CUDA library; there is no
+Python or CPU fallback, and loading fails loudly when the library is missing.
+
+Host arrays are NumPy arrays (EOT_MEM_HOST); device arrays are torch CUDA
+tensors (EOT_MEM_DEVICE), passed by their data pointers.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libeot.so")
+
+# ---- enums (eot.h) ----
+EOT_OK, EOT_NOT_CONVERGED, EOT_PENDING = 0, 1, 2
+EOT_EINVAL, EOT_ENOMEM, EOT_ENUMERIC, EOT_ETIMEDOUT, EOT_ECUDA, EOT_ENOTFOUND = -1, -2, -3, -4, -5, -6
+EOT_MEM_HOST, EOT_MEM_DEVICE = 0, 1
+EOT_PREC_FP64, EOT_PREC_FP32, EOT_PREC_SPLIT_TC = 0, 1, 2
+EOT_HESS_DIAG_ALPHA, EOT_HESS_EXACT = 0, 1
+EOT_SIDE_COL, EOT_SIDE_ROW = 0, 1
+
+STATUS_NAMES = {0: "EOT_OK", 1: "EOT_NOT_CONVERGED", 2: "EOT_PENDING", -1: "EOT_EINVAL",
+                -2: "EOT_ENOMEM", -3: "EOT_ENUMERIC", -4: "EOT_ETIMEDOUT", -5: "EOT_ECUDA",
+                -6: "EOT_ENOTFOUND"}
+
+
+class eot_problem(C.Structure):
+    _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("d", C.c_int32),
+                ("a", C.c_void_p), ("b", C.c_void_p), ("C", C.c_void_p),
+                ("X", C.c_void_p), ("Y", C.c_void_p), ("mem", C.c_int32),
+                ("normalize_cost", C.c_int32), ("eps", C.c_double), ("f_init", C.c_void_p)]
+
+
+class eot_options(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("ell", C.c_int32),
+                ("eps_start", C.c_double), ("eps_factor", C.c_double), ("level_tol", C.c_double),
+                ("sequential_modes", C.c_int32), ("oversample", C.c_int32),
+                ("eig_tol", C.c_double), ("eig_max_iter", C.c_int32), ("prec", C.c_int32),
+                ("hessian", C.c_int32), ("poll_every", C.c_int32), ("stream", C.c_void_p)]
+
+
+class eot_result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iters", C.c_int32), ("total_iters", C.c_int32),
+                ("nr_accepted", C.c_int32), ("nr_rejected", C.c_int32), ("levels", C.c_int32),
+                ("eig_iters", C.c_int32), ("l1_marginal", C.c_double), ("row_l1", C.c_double),
+                ("col_l1", C.c_double), ("q_dual", C.c_double), ("q_semi", C.c_double),
+                ("dual_gap", C.c_double), ("seconds", C.c_double), ("seconds_eig", C.c_double),
+                ("seconds_last_level", C.c_double)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["status_name"] = STATUS_NAMES.get(self.status, str(self.status))
+        return d
+
+
+_PTR = C.c_void_p
+_SIGNATURES = {
+    "eot_default_options": (None, [C.POINTER(eot_options)]),
+    "eot_solve": (C.c_int, [C.POINTER(eot_problem), C.POINTER(eot_options), _PTR, _PTR,
+                            C.POINTER(eot_result)]),
+    "eot_solve_batch": (C.c_int, [C.c_int32, C.POINTER(eot_problem), C.POINTER(eot_options),
+                                  C.POINTER(_PTR), C.POINTER(_PTR), C.POINTER(eot_result)]),
+    "eot_server_create": (C.c_int, [C.POINTER(eot_options), C.c_size_t, C.c_int32,
+                                    C.POINTER(_PTR)]),
+    "eot_server_submit": (C.c_int, [_PTR, C.POINTER(eot_problem), C.c_uint64,
+                                    C.POINTER(C.c_uint64)]),
+    "eot_server_poll": (C.c_int, [_PTR, C.c_uint64, _PTR, _PTR, C.POINTER(eot_result)]),
+    "eot_server_stats": (C.c_int, [_PTR, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                   C.POINTER(C.c_double)]),
+    "eot_server_destroy": (None, [_PTR]),
+    "eot_ctransform": (C.c_int, [C.c_int, C.c_int32, C.c_int32, _PTR, _PTR, _PTR, _PTR,
+                                 C.c_double, _PTR, _PTR, _PTR]),
+    "eot_kapply": (C.c_int, [C.c_int, C.c_int32, C.c_int32, C.c_int32, _PTR, _PTR, _PTR, _PTR,
+                             _PTR, C.c_double, _PTR, _PTR, _PTR]),
+    "eot_cost": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, _PTR, _PTR, C.c_int32, _PTR, _PTR,
+                           _PTR]),
+    "eot_spectral_modes": (C.c_int, [C.c_int32, C.c_int32, _PTR, _PTR, _PTR, _PTR, _PTR,
+                                     C.c_double, C.c_int32, C.c_int32, C.c_double, C.c_int32,
+                                     C.c_int32, _PTR, _PTR, C.POINTER(C.c_int32),
+                                     C.POINTER(C.c_double), _PTR]),
+    "eot_marginal_error": (C.c_int, [C.c_int32, C.c_int32, _PTR, _PTR, _PTR, _PTR, _PTR,
+                                     C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                     _PTR]),
+    "eot_last_error": (C.c_char_p, []),
+    "eot_version": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libeot.so and declare every entry point; raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"{path} not found: build the CUDA library first "
+            "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols() -> list:
+    return list(_SIGNATURES)
+
+
+# ---------------------------------------------------------------------------
+# Marshalling helpers
+# ---------------------------------------------------------------------------
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, keep: list, dtype=None):
+    """Data pointer of a NumPy array (made contiguous / cast, kept alive) or a torch tensor."""
+    if x is None:
+        return None
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("device tensors must be contiguous")
+        return x.data_ptr()
+    arr = np.ascontiguousarray(x, dtype=dtype)
+    keep.append(arr)
+    return arr.ctypes.data
+
+
+def default_options(**kw) -> eot_options:
+    o = eot_options()
+    load().eot_default_options(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def make_problem(a, b, C=None, X=None, Y=None, eps=1e-2, normalize_cost=False, f_init=None,
+                 keep: Optional[list] = None) -> eot_problem:
+    keep = [] if keep is None else keep
+    dev = any(_is_torch(x) for x in (a, b, C, X, Y) if x is not None)
+    p = eot_problem()
+    p.n = int(a.shape[0])
+    p.m = int(b.shape[0])
+    p.d = 0 if X is None else int(X.shape[1])
+    p.a = _ptr(a, keep, np.float64)
+    p.b = _ptr(b, keep, np.float64)
+    p.C = _ptr(C, keep, np.float32)
+    p.X = _ptr(X, keep, np.float32)
+    p.Y = _ptr(Y, keep, np.float32)
+    p.mem = EOT_MEM_DEVICE if dev else EOT_MEM_HOST
+    p.normalize_cost = 1 if normalize_cost else 0
+    p.eps = float(eps)
+    p.f_init = _ptr(f_init, keep, np.float64)
+    return p
+
+
+def last_error() -> str:
+    return load().eot_last_error().decode()
+
+
+# ---------------------------------------------------------------------------
+# Entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------
+
+def eot_solve(problem: eot_problem, options: eot_options, f_out, g_out):
+    """Call eot_solve; f_out (n) / g_out (m) are float64 NumPy arrays or torch
+    tensors matching problem.mem.  Returns (status, eot_result)."""
+    res = eot_result()
+    keep = []
+    st = load().eot_solve(C.byref(problem), C.byref(options), _ptr(f_out, keep),
+                          _ptr(g_out, keep), C.byref(res))
+    return st, res
+
+
+def solve(prob, **opts):
+    """Solve a ``workloads.Problem`` (host arrays).  Returns (f, g, result dict)."""
+    keep = []
+    p = make_problem(prob.a, prob.b, C=prob.C, X=prob.X, Y=prob.Y, eps=prob.eps,
+                     normalize_cost=prob.normalize_cost, f_init=opts.pop("f_init", None),
+                     keep=keep)
+    o = default_options(**opts)
+    f = np.zeros(p.n)
+    g = np.zeros(p.m)
+    st, res = eot_solve(p, o, f, g)
+    r = res.as_dict()
+    r["return_status"] = st
+    if st < 0:
+        r["error"] = last_error()
+    return f, g, r
+
+
+def eot_solve_batch(problems: list, options: eot_options, f_outs: list, g_outs: list):
+    n = len(problems)
+    arr = (eot_problem * n)(*problems)
+    keep = []
+    fp = (C.c_void_p * n)(*[_ptr(x, keep) for x in f_outs])
+    gp = (C.c_void_p * n)(*[_ptr(x, keep) for x in g_outs])
+    res = (eot_result * n)()
+    st = load().eot_solve_batch(n, arr, C.byref(options), fp, gp, res)
+    return st, list(res)
+
+
+def eot_ctransform(side: int, n: int, m: int, Cdev, pot, w, shift, eps: float, out,
+                   log_ratio=None, stream=None) -> int:
+    return load().eot_ctransform(side, n, m, Cdev.data_ptr(), pot.data_ptr(), w.data_ptr(),
+                                 None if shift is None else shift.data_ptr(), float(eps),
+                                 out.data_ptr(),
+                                 None if log_ratio is None else log_ratio.data_ptr(), stream)
+
+
+def eot_kapply(side: int, n: int, m: int, k: int, Cdev, f, g, a, b, eps: float, Z, out,
+               stream=None) -> int:
+    return load().eot_kapply(side, n, m, k, Cdev.data_ptr(), f.data_ptr(), g.data_ptr(),
+                             a.data_ptr(), b.data_ptr(), float(eps), Z.data_ptr(),
+                             out.data_ptr(), stream)
+
+
+def eot_cost(n: int, m: int, d: int, X, Y, normalize: bool, Cout, cmax_out=None,
+             stream=None) -> int:
+    return load().eot_cost(n, m, d, X.data_ptr(), Y.data_ptr(), 1 if normalize else 0,
+                           Cout.data_ptr(), None if cmax_out is None else cmax_out.data_ptr(),
+                           stream)
+
+
+def eot_spectral_modes(n, m, Cdev, f, g, a, b, eps, ell, oversample, tol, max_iter,
+                       use_V_as_start, V, rho2=None, stream=None):
+    it = C.c_int32(0)
+    rs = C.c_double(0.0)
+    st = load().eot_spectral_modes(n, m, Cdev.data_ptr(), f.data_ptr(), g.data_ptr(),
+                                   a.data_ptr(), b.data_ptr(), float(eps), ell, oversample,
+                                   float(tol), max_iter, 1 if use_V_as_start else 0,
+                                   V.data_ptr(), None if rho2 is None else rho2.data_ptr(),
+                                   C.byref(it), C.byref(rs), stream)
+    return st, it.value, rs.value
+
+
+def eot_marginal_error(n, m, Cdev, f, g, a, b, eps, stream=None):
+    r = C.c_double(0.0)
+    c = C.c_double(0.0)
+    st = load().eot_marginal_error(n, m, Cdev.data_ptr(), f.data_ptr(), g.data_ptr(),
+                                   a.data_ptr(), b.data_ptr(), float(eps), C.byref(r),
+                                   C.byref(c), stream)
+    return st, r.value, c.value
+
+
+class Server:
+    """eot_server_* wrapper (host arrays)."""
+
+    def __init__(self, options: eot_options, hbm_budget_bytes: int, max_slots: int):
+        h = C.c_void_p()
+        st = load().eot_server_create(C.byref(options), int(hbm_budget_bytes), int(max_slots),
+                                      C.byref(h))
+        if st != EOT_OK:
+            raise RuntimeError(f"eot_server_create: {STATUS_NAMES.get(st)} {last_error()}")
+        self.h = h
+        self._keep = {}
+
+    def submit(self, prob, cloud_id: int = 0) -> int:
+        keep = []
+        p = make_problem(prob.a, prob.b, C=prob.C, X=prob.X, Y=prob.Y, eps=prob.eps,
+                         normalize_cost=prob.normalize_cost, keep=keep)
+        t = C.c_uint64(0)
+        st = load().eot_server_submit(self.h, C.byref(p), C.c_uint64(cloud_id), C.byref(t))
+        if st != EOT_OK:
+            raise RuntimeError(f"eot_server_submit: {STATUS_NAMES.get(st)} {last_error()}")
+        self._keep[t.value] = (prob.n, prob.m)
+        return t.value
+
+    def poll(self, ticket: int):
+        n, m = self._keep.get(ticket, (1, 1))
+        f = np.zeros(n)
+        g = np.zeros(m)
+        res = eot_result()
+        st = load().eot_server_poll(self.h, C.c_uint64(ticket), f.ctypes.data, g.ctypes.data,
+                                    C.byref(res))
+        if st != EOT_PENDING:
+            self._keep.pop(ticket, None)
+        return st, f, g, res.as_dict()
+
+    def stats(self):
+        p50, p99, sps = C.c_double(), C.c_double(), C.c_double()
+        load().eot_server_stats(self.h, C.byref(p50), C.byref(p99), C.byref(sps))
+        return p50.value, p99.value, sps.value
+
+    def close(self):
+        if self.h:
+            load().eot_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

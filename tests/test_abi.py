@@ -1,0 +1,56 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/eot.h declares (no compute call: CPU only)."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "eot.h")) as fh:
+        src = fh.read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(eot_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2506_14780_gb300 import build
+    if not os.path.exists(build.LIB):
+        build.build()
+    import paper_2506_14780_gb300 as pkg
+    return pkg.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("eot_solve", "eot_solve_batch", "eot_server_submit", "eot_server_poll",
+                     "eot_ctransform", "eot_kapply", "eot_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    import ctypes
+    for name in _declared():
+        assert hasattr(lib, name), name
+        assert isinstance(getattr(lib, name), ctypes._CFuncPtr)
+
+
+def test_binding_covers_the_header():
+    from paper_2506_14780_gb300 import eot
+    assert sorted(eot.exported_symbols()) == _declared()
+
+
+def test_version_and_error_without_device(lib):
+    from paper_2506_14780_gb300 import eot
+    assert b"sm_103a" in lib.eot_version()
+    o = eot.default_options()
+    assert o.tol == 1e-6 and o.eps_factor == 0.5 and o.prec == eot.EOT_PREC_FP32
+    # an invalid problem is rejected on the host before any device work
+    import numpy as np
+    p = eot.make_problem(np.ones(3) / 3, np.ones(2) / 2, C=np.zeros((3, 2), np.float32), eps=-1.0)
+    st, _ = eot.eot_solve(p, o, np.zeros(3), np.zeros(2))
+    assert st == eot.EOT_EINVAL
+    assert "eps" in eot.last_error()
