@@ -62,7 +62,8 @@ __global__ void __launch_bounds__(kThreads) colacc_kernel(AccArgs args) {
   const int i_end = min(n, i_beg + args.seg_len);
   const float k2 = P.k2;
   const float Kj = jv ? cK[j] : P.M;
-  float cc = jv ? cKL[j] * k2 : 0.f;
+  const float cc0 = jv ? cKL[j] * k2 : 0.f;
+  float cc = cc0;
   float ref = 0.f, run = -INFINITY, S = 0.f;
   float acc[K];
 #pragma unroll
@@ -86,15 +87,14 @@ __global__ void __launch_bounds__(kThreads) colacc_kernel(AccArgs args) {
       if (y > run) {
         run = y;
         if (run > kRecenter || (run < -kRecenter && run > -INFINITY)) {
-          const float d = run;
-          const float sc = ex2_approx(-d);
-          S *= sc;
+          const float d = rintf(run);
+          S = scale2(S, -d);
 #pragma unroll
-          for (int k = 0; k < K; ++k) acc[k] *= sc;
+          for (int k = 0; k < K; ++k) acc[k] = scale2(acc[k], -d);
           ref += d;
-          cc -= d;
-          run = 0.f;
-          y -= d;
+          cc = __fsub_rn(cc0, ref);
+          run -= d;
+          y = __fmaf_rn(t, k2, cc);
         }
       }
       const float e = ex2_approx(y);
@@ -135,8 +135,7 @@ __global__ void __launch_bounds__(kThreads) colacc_kernel(AccArgs args) {
           const float* src = sRed + (w * 32 + col) * (K + 2);
           const float rw = src[0];
           if (rw == -INFINITY) continue;
-          const float sc = (rw == R) ? 1.f : ex2_approx(rw - R);
-          v += src[e] * sc;
+          v += (rw == R) ? src[e] : scale2(src[e], rw - R);
         }
       }
       if (jj < m) args.part[((size_t)seg * m + jj) * (K + 2) + e] = v;
@@ -168,13 +167,13 @@ __global__ void __launch_bounds__(kThreads) colacc_kernel(AccArgs args) {
         const float Ss = __ldcg(src + 1);
         if (Ss > 0.f) {
           const float rs = __ldcg(src);
-          Stot += (double)(rs == R ? Ss : Ss * ex2_approx(rs - R));
+          Stot += (double)(rs == R ? Ss : scale2(Ss, rs - R));
         }
       }
       // out = scale * sum_s 2^(R_s - R) acc_s
       float scale;
       if (s4) scale = (float)(P.b[jj] / Stot);          // b_j * softmax normalisation
-      else scale = exp2f(R);                             // un-normalised K-apply
+      else scale = scale2(1.f, R);                       // un-normalised K-apply
       for (int k = sl; k < kk; k += 8) {
         float v = 0.f;
         for (int s = 0; s < args.nseg; ++s) {
@@ -182,14 +181,14 @@ __global__ void __launch_bounds__(kThreads) colacc_kernel(AccArgs args) {
           const float Ss = __ldcg(src + 1);
           if (Ss > 0.f) {
             const float rs = __ldcg(src);
-            v += __ldcg(src + 2 + k) * (rs == R ? 1.f : ex2_approx(rs - R));
+            v += (rs == R) ? __ldcg(src + 2 + k) : scale2(__ldcg(src + 2 + k), rs - R);
           }
         }
         args.out[(size_t)jj * kk + k] = v * scale;
       }
       if (s4 && sl == 0) {
         // column transform h and the marginal test, as in the Sinkhorn column pass
-        float L = R * kLn2 + log1pf((float)(Stot - 1.0));
+        float L = R * kLn2 + log_sum(Stot);
         const double sh = P.g[gb][jj];
         double o = sh - P.eps * (double)L;
         if (!isfinite(o) || !(Stot > 0.0) || fabs(o) > P.pot_bound) {
@@ -275,7 +274,7 @@ __global__ void __launch_bounds__(kThreads) rowacc_kernel(AccArgs args) {
   const int c_beg = seg * args.seg_len;
   const int c_end = min(m, c_beg + args.seg_len);
   const float k2 = P.k2;
-  float Kr[RW], cc[RW], ref[RW], run[RW], S[RW];
+  float Kr[RW], cc0[RW], cc[RW], ref[RW], run[RW], S[RW];
   bool rv[RW];
   float acc[RW][K];
 #pragma unroll
@@ -283,7 +282,8 @@ __global__ void __launch_bounds__(kThreads) rowacc_kernel(AccArgs args) {
     const int i = i0 + r;
     rv[r] = i < n;
     Kr[r] = rv[r] ? rK[i] : P.M;
-    cc[r] = rv[r] ? rKL[i] * k2 : 0.f;
+    cc0[r] = rv[r] ? rKL[i] * k2 : 0.f;
+    cc[r] = cc0[r];
     ref[r] = 0.f;
     run[r] = -INFINITY;
     S[r] = 0.f;
@@ -303,15 +303,14 @@ __global__ void __launch_bounds__(kThreads) rowacc_kernel(AccArgs args) {
         if (y > run[r]) {
           run[r] = y;
           if (run[r] > kRecenter || (run[r] < -kRecenter && run[r] > -INFINITY)) {
-            const float d = run[r];
-            const float sc = ex2_approx(-d);
-            S[r] *= sc;
+            const float d = rintf(run[r]);
+            S[r] = scale2(S[r], -d);
 #pragma unroll
-            for (int k = 0; k < K; ++k) acc[r][k] *= sc;
+            for (int k = 0; k < K; ++k) acc[r][k] = scale2(acc[r][k], -d);
             ref[r] += d;
-            cc[r] -= d;
-            run[r] = 0.f;
-            y -= d;
+            cc[r] = __fsub_rn(cc0[r], ref[r]);
+            run[r] -= d;
+            y = __fmaf_rn(t, k2, cc[r]);
           }
         }
         e[r] = ex2_approx(y);
@@ -352,11 +351,12 @@ __global__ void __launch_bounds__(kThreads) rowacc_kernel(AccArgs args) {
     float R = (S[r] > 0.f) ? ref[r] : -INFINITY;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) R = fmaxf(R, __shfl_xor_sync(0xffffffffu, R, o));
-    const float sc = (S[r] > 0.f) ? ((ref[r] == R) ? 1.f : ex2_approx(ref[r] - R)) : 0.f;
+    const bool live = S[r] > 0.f;
+    const float dr = (ref[r] == R) ? 0.f : ref[r] - R;
     my[r * (K + 2) + 0] = R;
-    my[r * (K + 2) + 1] = S[r] * sc;
+    my[r * (K + 2) + 1] = live ? scale2(S[r], dr) : 0.f;
 #pragma unroll
-    for (int k = 0; k < K; ++k) my[r * (K + 2) + 2 + k] = acc[r][k] * sc;
+    for (int k = 0; k < K; ++k) my[r * (K + 2) + 2 + k] = live ? scale2(acc[r][k], dr) : 0.f;
   }
   __syncwarp();
   // lane l sums entries l, l+32, ... over the warp's 32 lanes
@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(kThreads) rowacc_kernel(AccArgs args) {
         const float* src = args.part + ((size_t)s * n + i) * (K + 2);
         if (__ldcg(src + 1) > 0.f) R = fmaxf(R, __ldcg(src));
       }
-      const float scale = exp2f(R);
+      const float scale = scale2(1.f, R);
       for (int k = sl; k < kk; k += TPR) {
         float v = 0.f;
         for (int s = 0; s < args.nseg; ++s) {
@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(kThreads) rowacc_kernel(AccArgs args) {
           const float Ss = __ldcg(src + 1);
           if (Ss > 0.f) {
             const float rs = __ldcg(src);
-            v += __ldcg(src + 2 + k) * (rs == R ? 1.f : ex2_approx(rs - R));
+            v += (rs == R) ? __ldcg(src + 2 + k) : scale2(__ldcg(src + 2 + k), rs - R);
           }
         }
         args.out[(size_t)i * kk + k] = v * scale;

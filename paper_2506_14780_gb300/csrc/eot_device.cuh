@@ -58,13 +58,19 @@ struct Lse2 {
   __device__ __forceinline__ void init() { ref = 0.f; run = -INFINITY; S = 0.f; }
 };
 
-// Combine two (ref, S) partial states: result in state a.
+// Scale by 2^k (k an integer held in a float): exact, underflows to 0.
+__device__ __forceinline__ float scale2(float x, float k) {
+  return ldexpf(x, (int)fmaxf(fminf(k, 300.f), -300.f));
+}
+
+// Combine two (ref, S) partial states: result in state a.  References are
+// integers (log2 units), so the rescaling is an exact power of two.
 __device__ __forceinline__ void lse2_merge(float& ra, float& Sa, float rb, float Sb) {
   if (Sb == 0.f) return;
   if (Sa == 0.f) { ra = rb; Sa = Sb; return; }
   if (ra == rb) { Sa += Sb; return; }
-  if (ra > rb) { Sa += Sb * ex2_approx(rb - ra); }
-  else { Sa = Sa * ex2_approx(ra - rb) + Sb; ra = rb; }
+  if (ra > rb) { Sa += scale2(Sb, rb - ra); }
+  else { Sa = scale2(Sa, ra - rb) + Sb; ra = rb; }
 }
 
 // Warp-wide sum of a double.
@@ -77,6 +83,13 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// Natural log of a positive float64 sum S: log1p of the exact S - 1 near 1 (so
+// that a marginal ratio close to one keeps its relative precision), log of S
+// otherwise (S - 1 would lose it when S << 1).
+__device__ __forceinline__ float log_sum(double S) {
+  return (S > 0.5 && S < 2.0) ? log1pf((float)(S - 1.0)) : logf((float)S);
 }
 
 // Split a float64 value into (grid-aligned hi, float32 lo) on the 2^-q grid.

@@ -47,9 +47,9 @@ __device__ __forceinline__ void combine_index(const float2* __restrict__ part, i
   double S = 0.0;
   for (int s = 0; s < nseg; ++s) {
     float2 p = __ldcg(&part[(size_t)s * stride + idx]);
-    if (p.y > 0.f) S += (double)(p.x == R ? p.y : p.y * ex2_approx(p.x - R));
+    if (p.y > 0.f) S += (double)(p.x == R ? p.y : scale2(p.y, p.x - R));
   }
-  float L = R * kLn2 + log1pf((float)(S - 1.0));
+  float L = R * kLn2 + log_sum(S);
   double sh = shift[idx];
   double o = sh - P.eps * (double)L;
   if (!isfinite(o) || !(S > 0.0) || fabs(o) > P.pot_bound) {
@@ -182,14 +182,15 @@ __global__ void __launch_bounds__(kThreads) col_pass_kernel(const Prob* __restri
   const int i_end = min(n, i_beg + P.rows_per_stripe);
   const float k2 = P.k2;
 
-  float K[4], cc[4], ref[4], run[4], S[4];
+  float K[4], cc0[4], cc[4], ref[4], run[4], S[4];
   bool valid[4];
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     const int j = j0 + c;
     valid[c] = j < m;
     K[c] = valid[c] ? cK[j] : P.M;
-    cc[c] = valid[c] ? cKL[j] * k2 : 0.f;
+    cc0[c] = valid[c] ? cKL[j] * k2 : 0.f;
+    cc[c] = cc0[c];
     ref[c] = 0.f;
     run[c] = -INFINITY;
     S[c] = 0.f;
@@ -206,13 +207,11 @@ __global__ void __launch_bounds__(kThreads) col_pass_kernel(const Prob* __restri
     if (!any_valid) continue;
     // rows r = wid, wid + 8, ... of this chunk, 4 at a time
     for (int r0 = wid; r0 < nrows; r0 += 32) {
-      float y[4][4];
-      int cnt = 0;
+      float t[4][4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int r = r0 + 8 * u;
         if (r < nrows) {
-          ++cnt;
           const float2 ra = s_row[r];
           const float* crow = P.C + (size_t)(base + r) * m + j0;
           float cv[4];
@@ -224,34 +223,30 @@ __global__ void __launch_bounds__(kThreads) col_pass_kernel(const Prob* __restri
             for (int c = 0; c < 4; ++c) cv[c] = valid[c] ? __ldg(crow + c) : 0.f;
           }
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const float t = __fadd_rn(split_exponent(cv[c], K[c], ra.x), ra.y);
-            y[u][c] = __fmaf_rn(t, k2, cc[c]);
-          }
+          for (int c = 0; c < 4; ++c) t[u][c] = __fadd_rn(split_exponent(cv[c], K[c], ra.x), ra.y);
         } else {
 #pragma unroll
-          for (int c = 0; c < 4; ++c) y[u][c] = -INFINITY;
+          for (int c = 0; c < 4; ++c) t[u][c] = -INFINITY;
         }
       }
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        float mx = fmaxf(fmaxf(y[0][c], y[1][c]), fmaxf(y[2][c], y[3][c]));
+        float y[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) y[u] = __fmaf_rn(t[u][c], k2, cc[c]);
+        const float mx = fmaxf(fmaxf(y[0], y[1]), fmaxf(y[2], y[3]));
         run[c] = fmaxf(run[c], mx);
         if (run[c] > kRecenter || (run[c] < -kRecenter && run[c] > -INFINITY)) {
-          const float d = run[c];
-          if (S[c] > 0.f) S[c] *= ex2_approx(-d);
+          const float d = rintf(run[c]);
+          S[c] = scale2(S[c], -d);
           ref[c] += d;
-          cc[c] -= d;
-          run[c] = 0.f;
+          cc[c] = __fsub_rn(cc0[c], ref[c]);
+          run[c] -= d;
 #pragma unroll
-          for (int u = 0; u < 4; ++u) y[u][c] -= d;
+          for (int u = 0; u < 4; ++u) y[u] = __fmaf_rn(t[u][c], k2, cc[c]);
         }
-        float acc = 0.f;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) acc += ex2_approx(y[u][c]);
-        S[c] += acc;
+        S[c] += (ex2_approx(y[0]) + ex2_approx(y[1])) + (ex2_approx(y[2]) + ex2_approx(y[3]));
       }
-      (void)cnt;
     }
   }
   // intra-CTA combine over the 8 warps
@@ -345,14 +340,16 @@ __global__ void __launch_bounds__(kThreads) row_pass_kernel(const Prob* __restri
   const int c_end = min(m, c_beg + P.cols_per_seg);
   const float k2 = P.k2;
 
-  float K[kRowsPerWarp], cc[kRowsPerWarp], ref[kRowsPerWarp], run[kRowsPerWarp], S[kRowsPerWarp];
+  float K[kRowsPerWarp], cc0[kRowsPerWarp], cc[kRowsPerWarp], ref[kRowsPerWarp], run[kRowsPerWarp],
+      S[kRowsPerWarp];
   bool rv[kRowsPerWarp];
 #pragma unroll
   for (int r = 0; r < kRowsPerWarp; ++r) {
     const int i = i0 + r;
     rv[r] = i < n;
     K[r] = rv[r] ? rK[i] : P.M;
-    cc[r] = rv[r] ? rKL[i] * k2 : 0.f;
+    cc0[r] = rv[r] ? rKL[i] * k2 : 0.f;
+    cc[r] = cc0[r];
     ref[r] = 0.f;
     run[r] = -INFINITY;
     S[r] = 0.f;
@@ -376,7 +373,6 @@ __global__ void __launch_bounds__(kThreads) row_pass_kernel(const Prob* __restri
           cal[c] = cvld[c] ? __ldg(cAL + j + c) : 0.f;
         }
       }
-      float y[kRowsPerWarp][4];
 #pragma unroll
       for (int r = 0; r < kRowsPerWarp; ++r) {
         float cv[4];
@@ -393,27 +389,24 @@ __global__ void __launch_bounds__(kThreads) row_pass_kernel(const Prob* __restri
 #pragma unroll
           for (int c = 0; c < 4; ++c) cv[c] = 0.f;
         }
+        float t[4], y[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          const float t = __fadd_rn(split_exponent(cv[c], K[r], ca[c]), cal[c]);
-          y[r][c] = (cvld[c] && rv[r]) ? __fmaf_rn(t, k2, cc[r]) : -INFINITY;
+          t[c] = (cvld[c] && rv[r]) ? __fadd_rn(split_exponent(cv[c], K[r], ca[c]), cal[c]) : -INFINITY;
+          y[c] = __fmaf_rn(t[c], k2, cc[r]);
         }
-      }
-#pragma unroll
-      for (int r = 0; r < kRowsPerWarp; ++r) {
-        float mx = fmaxf(fmaxf(y[r][0], y[r][1]), fmaxf(y[r][2], y[r][3]));
+        const float mx = fmaxf(fmaxf(y[0], y[1]), fmaxf(y[2], y[3]));
         run[r] = fmaxf(run[r], mx);
         if (run[r] > kRecenter || (run[r] < -kRecenter && run[r] > -INFINITY)) {
-          const float d = run[r];
-          if (S[r] > 0.f) S[r] *= ex2_approx(-d);
+          const float d = rintf(run[r]);
+          S[r] = scale2(S[r], -d);
           ref[r] += d;
-          cc[r] -= d;
-          run[r] = 0.f;
+          cc[r] = __fsub_rn(cc0[r], ref[r]);
+          run[r] -= d;
 #pragma unroll
-          for (int c = 0; c < 4; ++c) y[r][c] -= d;
+          for (int c = 0; c < 4; ++c) y[c] = __fmaf_rn(t[c], k2, cc[r]);
         }
-        S[r] += (ex2_approx(y[r][0]) + ex2_approx(y[r][1])) +
-                (ex2_approx(y[r][2]) + ex2_approx(y[r][3]));
+        S[r] += (ex2_approx(y[0]) + ex2_approx(y[1])) + (ex2_approx(y[2]) + ex2_approx(y[3]));
       }
     }
   }

@@ -20,7 +20,8 @@ namespace eotk {
 
 constexpr int kGChunk = 64;
 
-// part[chunk][p*p] (+ vpart[chunk][p]) partial sums over rows of one chunk.
+// part[chunk][p*p] (+ vpart[chunk][p] = sum_i vw_i A_i) partial sums over the
+// rows of one chunk.
 __global__ void __launch_bounds__(256) wgram_partial_kernel(
     const float* __restrict__ A, const float* __restrict__ B, const double* __restrict__ w,
     int wmode /*0: w, 1: 1/w*/, int len, int p, const double* __restrict__ vw,
@@ -60,7 +61,7 @@ __global__ void __launch_bounds__(256) wgram_partial_kernel(
   if (vpart) {
     for (int k = threadIdx.x; k < p; k += blockDim.x) {
       float s = 0.f;
-      for (int r = 0; r < nr; ++r) s = __fmaf_rn(svw[r], (vsrc ? vsrc : sA)[r * p + k], s);
+      for (int r = 0; r < nr; ++r) s = __fmaf_rn(svw[r], sA[r * p + k], s);
       vpart[(size_t)chunk * p + k] = (double)s;
     }
   }
