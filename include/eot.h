@@ -111,6 +111,7 @@ typedef struct {
     double seconds;         /* device time of the whole solve                          */
     double seconds_eig;     /* part of it spent computing modes                        */
     double seconds_last_level; /* device time of the final eps level incl. its modes   */
+    int64_t kernel_launches; /* device kernels this solve launched (all levels)        */
 } eot_result;
 
 /* Fill *opt with defaults: tol 1e-6, max_iter 100000, ell 0, single level,

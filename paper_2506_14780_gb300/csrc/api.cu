@@ -745,7 +745,9 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   for (auto& e : lev_ev) CUDA_TRY(cudaEventCreate(&e));
   std::vector<State> lev_state(L);
   State* hLev = nullptr;
-  CUDA_TRY(cudaMallocHost(&hLev, sizeof(State) * (L + 1)));
+  CUDA_TRY(cudaMallocHost(&hLev, sizeof(State) * (2 * L + 1)));
+  std::memset(hLev, 0, sizeof(State) * (2 * L + 1));
+  std::vector<int> lev_nr(L, 0), lev_eig(L, 0);
   bool have_modes = false;
   int eig_iters_total = 0;
   cudaEvent_t eig_ev0 = nullptr, eig_ev1 = nullptr;
@@ -776,6 +778,7 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
       if (e != EOT_OK) return e;
     }
     CUDA_TRY(cudaMemcpyAsync(hLev + t, S->dSt, sizeof(State), cudaMemcpyDeviceToHost, s));
+    lev_nr[t] = use_nr ? 1 : 0;
     // bring the current f and g to buffer 0 (split at this level's eps) for
     // the modes and the next level
     normalize_buffers_kernel<<<std::max(1, std::min(ceil_div(std::max(n, m), 256),
@@ -809,7 +812,8 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
           S->Zb, n, S->p, ell, S->V);
       CUDA_TRY(cudaEventRecord(a1, s));
       eig_events.push_back({a0, a1});
-      CUDA_TRY(cudaMemcpyAsync(hLev + L, S->dSt, sizeof(State), cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaMemcpyAsync(hLev + L + t, S->dSt, sizeof(State), cudaMemcpyDeviceToHost, s));
+      lev_eig[t] = 1;
       have_modes = true;
     }
   }
@@ -856,7 +860,20 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   r.nr_rejected = fin.nr_rej;
   r.levels = L;
   eig_iters_total = 0;
-  r.eig_iters = (ell > 0 && !eig_events.empty()) ? hLev[L].eig_iter : 0;
+  r.eig_iters = 0;
+  // kernel launches (fixed per phase + loop bodies as counted on the device)
+  long long launches = 2 + 1 + (d > 0 ? (pr->normalize_cost ? 2 : 1) : (pr->normalize_cost ? 1 : 0));
+  for (int t = 0; t < L; ++t) {
+    launches += 1 + 2 + 1 + 2;   // level set-up, splits, first column pass, buffer copy
+    if (lev_nr[t]) launches += 3 + (long long)hLev[t].body_runs * (9 * S->unroll_sknr + 1);
+    else launches += (long long)hLev[t].body_runs * (2 * S->unroll_sk + 1);
+    if (lev_eig[t]) {
+      r.eig_iters += hLev[L + t].eig_iter;
+      launches += 1 + 3 + 1 + 1 + 1 + (long long)hLev[L + t].body_runs * 11 + 1;
+    }
+  }
+  launches += 5;
+  r.kernel_launches = launches;
   r.row_l1 = S->hScores[0];
   r.col_l1 = S->hScores[1];
   r.l1_marginal = r.row_l1 + r.col_l1;

@@ -50,7 +50,7 @@ class eot_result(C.Structure):
                 ("eig_iters", C.c_int32), ("l1_marginal", C.c_double), ("row_l1", C.c_double),
                 ("col_l1", C.c_double), ("q_dual", C.c_double), ("q_semi", C.c_double),
                 ("dual_gap", C.c_double), ("seconds", C.c_double), ("seconds_eig", C.c_double),
-                ("seconds_last_level", C.c_double)]
+                ("seconds_last_level", C.c_double), ("kernel_launches", C.c_int64)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
