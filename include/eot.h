@@ -213,6 +213,25 @@ eot_status eot_marginal_error(int32_t n, int32_t m, const float *C, const double
                               const double *g, const double *a, const double *b, double eps,
                               double *row_l1, double *col_l1, void *stream);
 
+/* The (C,eps)-transform of eot_ctransform (same arguments, same result) for
+ * callers that may not allocate device memory: code that runs inside a device
+ * memory pool owned by another allocator (a framework's caching allocator, an
+ * application that sized the device at start-up), where a foreign cudaMalloc
+ * can fail or break the pool's budget, and latency-critical loops, where
+ * cudaMalloc / cudaFree may synchronise the device.  The paper has no
+ * counterpart; this is a deployment variant of the same pass.
+ * It allocates nothing: its temporaries live in one static device array of
+ * 4 MiB that every GPU loading the library holds until the process exits.
+ * Limits: n, m <= 16384 (EOT_EINVAL beyond).  The first call on a device looks
+ * up the array's address, so make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents: calls that
+ * overlap on the GPU (other streams or threads without ordering) race.  Runs
+ * on `stream` (NULL: the legacy default stream) and returns after it has
+ * synchronised. */
+eot_status eot_ctransform_noalloc(eot_side side, int32_t n, int32_t m, const float *C,
+                                  const double *pot, const double *w, const double *shift,
+                                  double eps, double *out, double *log_ratio, void *stream);
+
 /* Thread-local description of the last non-OK status returned on this thread. */
 const char *eot_last_error(void);
 

@@ -85,6 +85,8 @@ static eot_status fail(eot_status s, const std::string& msg) {
   return s;
 }
 
+void set_last_error(const std::string& msg) { t_err = msg; }
+
 #define CUDA_TRY(expr)                                                                   \
   do {                                                                                   \
     cudaError_t _e = (expr);                                                             \

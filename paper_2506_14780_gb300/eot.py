@@ -75,6 +75,8 @@ _SIGNATURES = {
     "eot_server_destroy": (None, [_PTR]),
     "eot_ctransform": (C.c_int, [C.c_int, C.c_int32, C.c_int32, _PTR, _PTR, _PTR, _PTR,
                                  C.c_double, _PTR, _PTR, _PTR]),
+    "eot_ctransform_noalloc": (C.c_int, [C.c_int, C.c_int32, C.c_int32, _PTR, _PTR, _PTR, _PTR,
+                                         C.c_double, _PTR, _PTR, _PTR]),
     "eot_kapply": (C.c_int, [C.c_int, C.c_int32, C.c_int32, C.c_int32, _PTR, _PTR, _PTR, _PTR,
                              _PTR, C.c_double, _PTR, _PTR, _PTR]),
     "eot_cost": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, _PTR, _PTR, C.c_int32, _PTR, _PTR,
@@ -218,6 +220,16 @@ def eot_ctransform(side: int, n: int, m: int, Cdev, pot, w, shift, eps: float, o
                                  None if shift is None else shift.data_ptr(), float(eps),
                                  out.data_ptr(),
                                  None if log_ratio is None else log_ratio.data_ptr(), stream)
+
+
+def eot_ctransform_noalloc(side: int, n: int, m: int, Cdev, pot, w, shift, eps: float, out,
+                           log_ratio=None, stream=None) -> int:
+    return load().eot_ctransform_noalloc(side, n, m, Cdev.data_ptr(), pot.data_ptr(),
+                                         w.data_ptr(),
+                                         None if shift is None else shift.data_ptr(), float(eps),
+                                         out.data_ptr(),
+                                         None if log_ratio is None else log_ratio.data_ptr(),
+                                         stream)
 
 
 def eot_kapply(side: int, n: int, m: int, k: int, Cdev, f, g, a, b, eps: float, Z, out,
