@@ -9,23 +9,48 @@
 //    the same pass as a log-sum-exp),
 //        W_j = sum_i pi(f_k, h)_ij V_i = b_j * softmax_i(x_ij) . V,
 //    the semi-dual coupling of Eq. (dQ_semi) applied to the modes; plus the
-//    marginal test of the iteration and the new column potential h.
+//    marginal test of the iteration, the new column potential h, the gradient
+//    weights d_j = 1 - exp((g_j - h_j)/eps) and, per block of 32 columns, the
+//    partial sums of W_j W_j^T / b_j and d_j W_j (Eq. d2Q_semi, dQ_semi on V).
 //
 // Exponents are formed exactly as in the Sinkhorn passes (eot_device.cuh).
 // Column direction: one thread per column (warp = 32 consecutive columns, one
-// 128-byte line per row), 8 warps interleaved over a stripe of rows, the stripe's
-// rows of Z staged in shared memory and broadcast.  Row direction: a warp owns
-// two rows, lanes stride along the columns, Z_j read per column and shared by
-// the two rows.  Partial (reference, sum, k accumulators) per segment are
-// combined in fixed order by the last-arriving CTA of each index block.
+// 128-byte line per row), 8 warps interleaved over a segment of rows; the
+// segment is walked in chunks of 64 rows whose rows of Z are staged in shared
+// memory (double buffered) while the next chunk's cost entries and Z rows are
+// already in flight.  Row direction: a warp owns one or two rows, lanes stride
+// along the columns, chunks of 128 columns of Z are staged in shared memory
+// (double buffered, conflict-free padding) and shared by the CTA's warps.
+// Partial (reference, sum, k accumulators) per segment are merged in parallel
+// and in fixed order by the last-arriving CTA of each index block.
 #include "eot_device.cuh"
 #include "eot_internal.h"
+#include "reduce.cuh"
 
 namespace eotk {
 
 enum AccMode : int { ACC_KCOL = 0, ACC_S4 = 1, ACC_KROW = 2 };
 
+constexpr int kCH = 64;   // rows per chunk (column direction)
+constexpr int kCC = 128;  // columns per chunk (row direction)
 
+template <int K>
+struct ColAccSmem {
+  static constexpr int KS = K + 4;
+  static constexpr size_t tiles = (size_t)2 * (kCH * KS + 2 * kCH) * 4;
+  static constexpr size_t red = (size_t)8 * 32 * (K + 2) * 4;
+  static constexpr size_t extra = (size_t)32 * (K + 1) * 4 + 32 * 8 * 2;
+  static constexpr size_t bytes = (tiles > red ? tiles : red) + extra;
+};
+
+template <int K>
+struct RowAccSmem {
+  static constexpr int RW = (K <= 32) ? 2 : 1;
+  static constexpr int KS = K + 4;
+  static constexpr size_t tiles = (size_t)2 * (kCC * KS + 2 * kCC) * 4;
+  static constexpr size_t red = (size_t)8 * 32 * (RW * (K + 2) + 1) * 4;
+  static constexpr size_t bytes = tiles > red ? tiles : red;
+};
 
 // ---------------------------------------------------------------------------
 // Column direction (K-apply col, S4).
@@ -43,13 +68,17 @@ __global__ void __launch_bounds__(kThreads) colacc_kernel(AccArgs args) {
   const float* __restrict__ rAL = P.rs[fb].AL;
   const float* __restrict__ cK = P.cs[gb].K;
   const float* __restrict__ cKL = P.cs[gb].KL;
+  using SM = ColAccSmem<K>;
+  constexpr int KS = SM::KS;
+  constexpr int VPT = (kCH * K) / kThreads;   // staged Z values per thread per chunk
 
-  constexpr int CH = 64;          // rows per staged chunk
-  constexpr int KS = K + 4;       // padded smem stride
-  extern __shared__ float smem[];
-  float* sZ = smem;                       // [CH][KS]
-  float2* sRow = reinterpret_cast<float2*>(sZ + CH * KS);   // [CH]
-  float* sRed = reinterpret_cast<float*>(sRow + CH);        // [8][32][K+2]
+  extern __shared__ __align__(16) float smem[];
+  float* sZ = smem;                                     // [2][kCH][KS]
+  float2* sRow = reinterpret_cast<float2*>(smem + 2 * kCH * KS);   // [2][kCH]
+  float* sRed = smem;                                   // reused after the loop
+  float* sW = smem + (SM::tiles > SM::red ? SM::tiles : SM::red) / 4;   // [32][K+1]
+  double* sD = reinterpret_cast<double*>(sW + 32 * (K + 1));          // [32] d_j
+  double* sB = sD + 32;                                               // [32] 1/b_j
   __shared__ double s_red[24];
   __shared__ unsigned s_last;
 
@@ -60,6 +89,7 @@ __global__ void __launch_bounds__(kThreads) colacc_kernel(AccArgs args) {
   const bool jv = j < m;
   const int i_beg = seg * args.seg_len;
   const int i_end = min(n, i_beg + args.seg_len);
+  const int nchunks = (i_end - i_beg + kCH - 1) / kCH;
   const float k2 = P.k2;
   const float Kj = jv ? cK[j] : P.M;
   const float cc0 = jv ? cKL[j] * k2 : 0.f;
@@ -69,49 +99,85 @@ __global__ void __launch_bounds__(kThreads) colacc_kernel(AccArgs args) {
 #pragma unroll
   for (int k = 0; k < K; ++k) acc[k] = 0.f;
 
-  for (int base = i_beg; base < i_end; base += CH) {
-    const int nr = min(CH, i_end - base);
-    __syncthreads();
-    for (int t = threadIdx.x; t < CH * K; t += kThreads) {
-      const int r = t / K, k = t - r * K;
-      sZ[r * KS + k] = (r < nr && k < kk) ? args.Z[(size_t)(base + r) * kk + k] : 0.f;
-    }
-    if ((int)threadIdx.x < nr) sRow[threadIdx.x] = make_float2(rA[base + threadIdx.x], rAL[base + threadIdx.x]);
-    __syncthreads();
-    if (!jv) continue;
-    for (int r = wid; r < nr; r += 8) {
-      const float c = __ldg(P.C + (size_t)(base + r) * m + j);
-      const float2 ra = sRow[r];
-      const float t = __fadd_rn(split_exponent(c, Kj, ra.x), ra.y);
-      float y = __fmaf_rn(t, k2, cc);
-      if (y > run) {
-        run = y;
-        if (run > kRecenter || (run < -kRecenter && run > -INFINITY)) {
-          const float d = rintf(run);
-          S = scale2(S, -d);
+  float zn[VPT];
+  float2 rn = make_float2(0.f, 0.f);
+  float cn[8];
+  auto fetch = [&](int ch) {
+    const int base = i_beg + ch * kCH;
+    const int nr = min(kCH, i_end - base);
 #pragma unroll
-          for (int k = 0; k < K; ++k) acc[k] = scale2(acc[k], -d);
-          ref += d;
-          cc = __fsub_rn(cc0, ref);
-          run -= d;
-          y = __fmaf_rn(t, k2, cc);
+    for (int q = 0; q < VPT; ++q) {
+      const int t = threadIdx.x + q * kThreads;
+      const int r = t / K, k = t - r * K;
+      zn[q] = (r < nr && k < kk) ? __ldg(args.Z + (size_t)(base + r) * kk + k) : 0.f;
+    }
+    if ((int)threadIdx.x < nr) rn = make_float2(__ldg(rA + base + threadIdx.x), __ldg(rAL + base + threadIdx.x));
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int r = wid + 8 * u;
+      cn[u] = (jv && r < nr) ? __ldg(P.C + (size_t)(base + r) * m + j) : 0.f;
+    }
+  };
+  auto publish = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < VPT; ++q) {
+      const int t = threadIdx.x + q * kThreads;
+      const int r = t / K, k = t - r * K;
+      sZ[(buf * kCH + r) * KS + k] = zn[q];
+    }
+    if ((int)threadIdx.x < kCH) sRow[buf * kCH + threadIdx.x] = rn;
+  };
+  if (nchunks > 0) {
+    fetch(0);
+    publish(0);
+  }
+  __syncthreads();
+  for (int ch = 0; ch < nchunks; ++ch) {
+    const int buf = ch & 1;
+    const int nr = min(kCH, i_end - (i_beg + ch * kCH));
+    float cv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) cv[u] = cn[u];
+    if (ch + 1 < nchunks) fetch(ch + 1);
+    if (jv) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int r = wid + 8 * u;
+        if (r < nr) {
+          const float2 ra = sRow[buf * kCH + r];
+          const float t = __fadd_rn(split_exponent(cv[u], Kj, ra.x), ra.y);
+          float y = __fmaf_rn(t, k2, cc);
+          if (y > run) {
+            run = y;
+            if (run > kRecenter || (run < -kRecenter && run > -INFINITY)) {
+              const float d = rintf(run);
+              S = scale2(S, -d);
+#pragma unroll
+              for (int k = 0; k < K; ++k) acc[k] = scale2(acc[k], -d);
+              ref += d;
+              cc = __fsub_rn(cc0, ref);
+              run -= d;
+              y = __fmaf_rn(t, k2, cc);
+            }
+          }
+          const float e = ex2_approx(y);
+          S += e;
+          const float4* z4 = reinterpret_cast<const float4*>(sZ + (buf * kCH + r) * KS);
+#pragma unroll
+          for (int k4 = 0; k4 < K / 4; ++k4) {
+            const float4 z = z4[k4];
+            acc[4 * k4 + 0] = __fmaf_rn(e, z.x, acc[4 * k4 + 0]);
+            acc[4 * k4 + 1] = __fmaf_rn(e, z.y, acc[4 * k4 + 1]);
+            acc[4 * k4 + 2] = __fmaf_rn(e, z.z, acc[4 * k4 + 2]);
+            acc[4 * k4 + 3] = __fmaf_rn(e, z.w, acc[4 * k4 + 3]);
+          }
         }
       }
-      const float e = ex2_approx(y);
-      S += e;
-      const float4* z4 = reinterpret_cast<const float4*>(sZ + r * KS);
-#pragma unroll
-      for (int k4 = 0; k4 < K / 4; ++k4) {
-        const float4 z = z4[k4];
-        acc[4 * k4 + 0] = __fmaf_rn(e, z.x, acc[4 * k4 + 0]);
-        acc[4 * k4 + 1] = __fmaf_rn(e, z.y, acc[4 * k4 + 1]);
-        acc[4 * k4 + 2] = __fmaf_rn(e, z.z, acc[4 * k4 + 2]);
-        acc[4 * k4 + 3] = __fmaf_rn(e, z.w, acc[4 * k4 + 3]);
-      }
     }
+    if (ch + 1 < nchunks) publish(buf ^ 1);
+    __syncthreads();
   }
   // intra-CTA combine over the 8 warps: rescale to the CTA maximum reference
-  __syncthreads();
   {
     float* my = sRed + (wid * 32 + lane) * (K + 2);
     my[0] = (S > 0.f) ? ref : -INFINITY;
@@ -120,7 +186,6 @@ __global__ void __launch_bounds__(kThreads) colacc_kernel(AccArgs args) {
     for (int k = 0; k < K; ++k) my[2 + k] = acc[k];
   }
   __syncthreads();
-  // thread t: column t & 31, slice (t >> 5) of the K+2 entries
   {
     const int col = threadIdx.x & 31, sl = threadIdx.x >> 5;
     float R = -INFINITY;
@@ -157,34 +222,29 @@ __global__ void __launch_bounds__(kThreads) colacc_kernel(AccArgs args) {
     const int jj = cb * 32 + col;
     if (jj < m) {
       float R = -INFINITY;
-      for (int s = 0; s < args.nseg; ++s) {
-        const float* src = args.part + ((size_t)s * m + jj) * (K + 2);
-        if (__ldcg(src + 1) > 0.f) R = fmaxf(R, __ldcg(src));
-      }
       double Stot = 0.0;
-      for (int s = 0; s < args.nseg; ++s) {
-        const float* src = args.part + ((size_t)s * m + jj) * (K + 2);
-        const float Ss = __ldcg(src + 1);
-        if (Ss > 0.f) {
-          const float rs = __ldcg(src);
-          Stot += (double)(rs == R ? Ss : scale2(Ss, rs - R));
-        }
-      }
-      // out = scale * sum_s 2^(R_s - R) acc_s
+      merge_segments_k(args.part, args.nseg, m, K + 2, jj, R, Stot);
       float scale;
       if (s4) scale = (float)(P.b[jj] / Stot);          // b_j * softmax normalisation
-      else scale = scale2(1.f, R);                       // un-normalised K-apply
+      else scale = scale2(1.f, R);                       // un-normalised product
       for (int k = sl; k < kk; k += 8) {
         float v = 0.f;
-        for (int s = 0; s < args.nseg; ++s) {
-          const float* src = args.part + ((size_t)s * m + jj) * (K + 2);
-          const float Ss = __ldcg(src + 1);
-          if (Ss > 0.f) {
-            const float rs = __ldcg(src);
-            v += (rs == R) ? __ldcg(src + 2 + k) : scale2(__ldcg(src + 2 + k), rs - R);
+        for (int s0 = 0; s0 < args.nseg; s0 += 4) {
+          float pr[4], pv[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int s = s0 + q;
+            const float* src = args.part + ((size_t)s * m + jj) * (K + 2);
+            pr[q] = s < args.nseg ? __ldcg(src) : -INFINITY;
+            pv[q] = s < args.nseg ? __ldcg(src + 2 + k) : 0.f;
           }
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (pr[q] > -INFINITY) v += (pr[q] == R) ? pv[q] : scale2(pv[q], pr[q] - R);
         }
-        args.out[(size_t)jj * kk + k] = v * scale;
+        const float wv = v * scale;
+        args.out[(size_t)jj * kk + k] = wv;
+        if (s4) sW[col * (K + 1) + k] = wv;
       }
       if (s4 && sl == 0) {
         // column transform h and the marginal test, as in the Sinkhorn column pass
@@ -207,9 +267,19 @@ __global__ void __launch_bounds__(kThreads) colacc_kernel(AccArgs args) {
         P.cs[dst_g].K[jj] = (float)((double)P.M - hi);
         P.cs[dst_g].KL[jj] = lo;
         const double wj = P.b[jj];
+        const double dj = -(double)expm1f(L);     // 1 - exp((g_j - h_j)/eps)
+        args.dw[jj] = dj;
+        sD[col] = dj;
+        sB[col] = 1.0 / wj;
         accv[0] = wj * (double)fabsf(expm1f(L));
         accv[1] = wj * (double)L;
         accv[2] = wj * o;
+      }
+    } else if (s4) {
+      for (int k = sl; k < kk; k += 8) sW[col * (K + 1) + k] = 0.f;
+      if (sl == 0) {
+        sD[col] = 0.0;
+        sB[col] = 0.0;
       }
     }
   }
@@ -217,7 +287,24 @@ __global__ void __launch_bounds__(kThreads) colacc_kernel(AccArgs args) {
     if (threadIdx.x == 0) args.cnt[cb] = 0u;
     return;
   }
-  // block sums (only warp 0 holds values) and the grid-final step
+  __syncthreads();
+  // block partials of W^T D_b^{-1} W (kk x kk) and of sum_j d_j W_j (kk)
+  {
+    double* dst = args.wtw_part + (size_t)cb * (kk * kk + kk);
+    for (int e = threadIdx.x; e < kk * kk + kk; e += kThreads) {
+      double s = 0.0;
+      if (e < kk * kk) {
+        const int r = e / kk, c = e - r * kk;
+        for (int q = 0; q < 32; ++q)
+          s += (double)(sW[q * (K + 1) + r] * sW[q * (K + 1) + c]) * sB[q];
+      } else {
+        const int r = e - kk * kk;
+        for (int q = 0; q < 32; ++q) s += sD[q] * (double)sW[q * (K + 1) + r];
+      }
+      dst[e] = s;
+    }
+  }
+  // block sums and the grid-final step
   {
     double v0 = warp_sum_d(accv[0]), v1 = warp_sum_d(accv[1]), v2 = warp_sum_d(accv[2]);
     if (threadIdx.x == 0) {
@@ -228,31 +315,64 @@ __global__ void __launch_bounds__(kThreads) colacc_kernel(AccArgs args) {
       ab[2] = v2;
       __threadfence();
       const unsigned prev = atomicAdd(args.gcnt, 1u);
-      if (prev == (unsigned)(args.nblk - 1)) {
-        __threadfence();
-        *args.gcnt = 0u;
-        double t0 = 0.0, t1 = 0.0, t2 = 0.0;
-        for (int b2 = 0; b2 < args.nblk; ++b2) {
-          t0 += __ldcg(&args.blkacc[b2 * 4 + 0]);
-          t1 += __ldcg(&args.blkacc[b2 * 4 + 1]);
-          t2 += __ldcg(&args.blkacc[b2 * 4 + 2]);
-        }
-        st->l1_col = t0;
-        st->sum_wL = t1;
-        st->qsemi = st->sum_af + t2;   // Q_semi(f_k) = <f_k, a> + <h, b>
-        st->iter += 1;
-        st->nr_ok = 0;
-        if (st->numeric > 0) st->done = 3;
-        else if (t0 < st->tol) st->done = 1;
-        else if (st->iter >= st->max_iter) st->done = 2;
-      }
+      s_last = (prev == (unsigned)(args.nblk - 1));
     }
   }
-  (void)s_red;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double tot[3];
+  grid_sum3(args.blkacc, args.nblk, tot, s_red);
+  if (threadIdx.x == 0) {
+    *args.gcnt = 0u;
+    st->l1_col = tot[0];
+    st->sum_wL = tot[1];
+    st->qsemi = st->sum_af + tot[2];   // Q_semi(f_k) = <f_k, a> + <h, b>
+    st->iter += 1;
+    st->nr_ok = 0;
+    if (st->numeric > 0) st->done = 3;
+    else if (tot[0] < st->tol) st->done = 1;
+    else if (st->iter >= st->max_iter) st->done = 2;
+  }
+}
+
+// Sum of the per-block partials of W^T D_b^{-1} W and sum_j d_j W_j: a CTA owns
+// 32 entries, its 8 warps take interleaved blocks, the warps' sums are added in
+// a fixed order.
+__global__ void __launch_bounds__(256) wtw_reduce_kernel(const AccArgs args,
+                                                         double* __restrict__ WtW,
+                                                         double* __restrict__ gw) {
+  const State* st = args.P->st;
+  if (st->done) return;
+  __shared__ double sh[8][32];
+  const int kk = args.k, cnt = kk * kk + kk;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int e = blockIdx.x * 32 + lane;
+  double s = 0.0;
+  if (e < cnt) {
+    for (int b0 = wid; b0 < args.nblk; b0 += 32) {
+      double v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int b = b0 + 8 * q;
+        v[q] = b < args.nblk ? __ldcg(&args.wtw_part[(size_t)b * cnt + e]) : 0.0;
+      }
+      s += (v[0] + v[1]) + (v[2] + v[3]);
+    }
+  }
+  sh[wid][lane] = s;
+  __syncthreads();
+  if (wid == 0 && e < cnt) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += sh[w][lane];
+    if (e < kk * kk) WtW[e] = t;
+    else gw[e - kk * kk] = t;
+  }
 }
 
 // ---------------------------------------------------------------------------
-// Row direction (K-apply row): out_i = sum_j 2^{y_ij} Z_j, two rows per warp.
+// Row direction (K-apply row): out_i = sum_j 2^{y_ij} Z_j.
 // ---------------------------------------------------------------------------
 template <int K>
 __global__ void __launch_bounds__(kThreads) rowacc_kernel(AccArgs args) {
@@ -261,9 +381,14 @@ __global__ void __launch_bounds__(kThreads) rowacc_kernel(AccArgs args) {
   const float* __restrict__ cAL = P.cs[args.gbuf].AL;
   const float* __restrict__ rK = P.rs[args.fbuf].K;
   const float* __restrict__ rKL = P.rs[args.fbuf].KL;
-  constexpr int RW = (K <= 32) ? 2 : 1;
-  extern __shared__ float smem[];
-  float* sRed = smem;   // [8 warps][32 lanes][RW*(K+2)+1]
+  using SM = RowAccSmem<K>;
+  constexpr int RW = SM::RW;
+  constexpr int KS = SM::KS;
+  constexpr int VPT = (kCC * K) / kThreads;   // staged Z values per thread per chunk
+  extern __shared__ __align__(16) float smem[];
+  float* sZ = smem;                                            // [2][kCC][KS]
+  float2* sCol = reinterpret_cast<float2*>(smem + 2 * kCC * KS);  // [2][kCC]
+  float* sRed = smem;                                          // reused after the loop
   constexpr int SR = RW * (K + 2) + 1;
   __shared__ unsigned s_last;
 
@@ -273,6 +398,7 @@ __global__ void __launch_bounds__(kThreads) rowacc_kernel(AccArgs args) {
   const int i0 = rb * (8 * RW) + wid * RW;
   const int c_beg = seg * args.seg_len;
   const int c_end = min(m, c_beg + args.seg_len);
+  const int nchunks = (c_end - c_beg + kCC - 1) / kCC;
   const float k2 = P.k2;
   float Kr[RW], cc0[RW], cc[RW], ref[RW], run[RW], S[RW];
   bool rv[RW];
@@ -290,59 +416,97 @@ __global__ void __launch_bounds__(kThreads) rowacc_kernel(AccArgs args) {
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[r][k] = 0.f;
   }
-  if (rv[0]) {
-    for (int j = c_beg + lane; j < c_end; j += 32) {
-      const float ca = __ldg(cA + j), cal = __ldg(cAL + j);
-      float e[RW];
+  float zn[VPT];
+  float2 coln = make_float2(0.f, 0.f);
+  float cn[RW][4];
+  auto fetch = [&](int ch) {
+    const int base = c_beg + ch * kCC;
+    const int nc = min(kCC, c_end - base);
 #pragma unroll
-      for (int r = 0; r < RW; ++r) {
-        if (!rv[r]) { e[r] = 0.f; continue; }
-        const float c = __ldg(P.C + (size_t)(i0 + r) * m + j);
-        const float t = __fadd_rn(split_exponent(c, Kr[r], ca), cal);
-        float y = __fmaf_rn(t, k2, cc[r]);
-        if (y > run[r]) {
-          run[r] = y;
-          if (run[r] > kRecenter || (run[r] < -kRecenter && run[r] > -INFINITY)) {
-            const float d = rintf(run[r]);
-            S[r] = scale2(S[r], -d);
+    for (int q = 0; q < VPT; ++q) {
+      const int t = threadIdx.x + q * kThreads;
+      const int c = t / K, k = t - c * K;
+      zn[q] = (c < nc && k < kk) ? __ldg(args.Z + (size_t)(base + c) * kk + k) : 0.f;
+    }
+    if ((int)threadIdx.x < nc)
+      coln = make_float2(__ldg(cA + base + threadIdx.x), __ldg(cAL + base + threadIdx.x));
 #pragma unroll
-            for (int k = 0; k < K; ++k) acc[r][k] = scale2(acc[r][k], -d);
-            ref[r] += d;
-            cc[r] = __fsub_rn(cc0[r], ref[r]);
-            run[r] -= d;
-            y = __fmaf_rn(t, k2, cc[r]);
-          }
-        }
-        e[r] = ex2_approx(y);
-        S[r] += e[r];
+    for (int r = 0; r < RW; ++r)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = lane + 32 * q;
+        cn[r][q] = (rv[r] && c < nc) ? __ldg(P.C + (size_t)(i0 + r) * m + base + c) : 0.f;
       }
-      const float* zr = args.Z + (size_t)j * kk;
-      if ((kk & 3) == 0) {
-        const float4* z4 = reinterpret_cast<const float4*>(zr);
+  };
+  auto publish = [&](int buf) {
 #pragma unroll
-        for (int k4 = 0; k4 < K / 4; ++k4) {
-          if (4 * k4 < kk) {
-            const float4 z = __ldg(z4 + k4);
+    for (int q = 0; q < VPT; ++q) {
+      const int t = threadIdx.x + q * kThreads;
+      const int c = t / K, k = t - c * K;
+      sZ[(buf * kCC + c) * KS + k] = zn[q];
+    }
+    if ((int)threadIdx.x < kCC) sCol[buf * kCC + threadIdx.x] = coln;
+  };
+  if (nchunks > 0) {
+    fetch(0);
+    publish(0);
+  }
+  __syncthreads();
+  for (int ch = 0; ch < nchunks; ++ch) {
+    const int buf = ch & 1;
+    const int nc = min(kCC, c_end - (c_beg + ch * kCC));
+    float cv[RW][4];
 #pragma unroll
-            for (int r = 0; r < RW; ++r) {
-              acc[r][4 * k4 + 0] = __fmaf_rn(e[r], z.x, acc[r][4 * k4 + 0]);
-              acc[r][4 * k4 + 1] = __fmaf_rn(e[r], z.y, acc[r][4 * k4 + 1]);
-              acc[r][4 * k4 + 2] = __fmaf_rn(e[r], z.z, acc[r][4 * k4 + 2]);
-              acc[r][4 * k4 + 3] = __fmaf_rn(e[r], z.w, acc[r][4 * k4 + 3]);
+    for (int r = 0; r < RW; ++r)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) cv[r][q] = cn[r][q];
+    if (ch + 1 < nchunks) fetch(ch + 1);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = lane + 32 * q;
+      if (c < nc) {
+        const float2 ca = sCol[buf * kCC + c];
+        float e[RW];
+#pragma unroll
+        for (int r = 0; r < RW; ++r) {
+          if (!rv[r]) {
+            e[r] = 0.f;
+            continue;
+          }
+          const float t = __fadd_rn(split_exponent(cv[r][q], Kr[r], ca.x), ca.y);
+          float y = __fmaf_rn(t, k2, cc[r]);
+          if (y > run[r]) {
+            run[r] = y;
+            if (run[r] > kRecenter || (run[r] < -kRecenter && run[r] > -INFINITY)) {
+              const float d = rintf(run[r]);
+              S[r] = scale2(S[r], -d);
+#pragma unroll
+              for (int k = 0; k < K; ++k) acc[r][k] = scale2(acc[r][k], -d);
+              ref[r] += d;
+              cc[r] = __fsub_rn(cc0[r], ref[r]);
+              run[r] -= d;
+              y = __fmaf_rn(t, k2, cc[r]);
             }
           }
+          e[r] = ex2_approx(y);
+          S[r] += e[r];
         }
-      } else {
+        const float4* z4 = reinterpret_cast<const float4*>(sZ + (buf * kCC + c) * KS);
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-          if (k < kk) {
-            const float z = __ldg(zr + k);
+        for (int k4 = 0; k4 < K / 4; ++k4) {
+          const float4 z = z4[k4];
 #pragma unroll
-            for (int r = 0; r < RW; ++r) acc[r][k] = __fmaf_rn(e[r], z, acc[r][k]);
+          for (int r = 0; r < RW; ++r) {
+            acc[r][4 * k4 + 0] = __fmaf_rn(e[r], z.x, acc[r][4 * k4 + 0]);
+            acc[r][4 * k4 + 1] = __fmaf_rn(e[r], z.y, acc[r][4 * k4 + 1]);
+            acc[r][4 * k4 + 2] = __fmaf_rn(e[r], z.z, acc[r][4 * k4 + 2]);
+            acc[r][4 * k4 + 3] = __fmaf_rn(e[r], z.w, acc[r][4 * k4 + 3]);
           }
         }
       }
     }
+    if (ch + 1 < nchunks) publish(buf ^ 1);
+    __syncthreads();
   }
   // warp reduction through shared memory: bring all lanes to the warp max ref
   float* my = sRed + (wid * 32 + lane) * SR;
@@ -359,7 +523,6 @@ __global__ void __launch_bounds__(kThreads) rowacc_kernel(AccArgs args) {
     for (int k = 0; k < K; ++k) my[r * (K + 2) + 2 + k] = live ? scale2(acc[r][k], dr) : 0.f;
   }
   __syncwarp();
-  // lane l sums entries l, l+32, ... over the warp's 32 lanes
   for (int e = lane; e < RW * (K + 2); e += 32) {
     float v;
     if ((e % (K + 2)) == 0) {
@@ -388,20 +551,23 @@ __global__ void __launch_bounds__(kThreads) rowacc_kernel(AccArgs args) {
     const int i = rb * (8 * RW) + rr;
     if (i < n) {
       float R = -INFINITY;
-      for (int s = 0; s < args.nseg; ++s) {
-        const float* src = args.part + ((size_t)s * n + i) * (K + 2);
-        if (__ldcg(src + 1) > 0.f) R = fmaxf(R, __ldcg(src));
-      }
+      double Stot = 0.0;
+      merge_segments_k(args.part, args.nseg, n, K + 2, i, R, Stot);
       const float scale = scale2(1.f, R);
       for (int k = sl; k < kk; k += TPR) {
         float v = 0.f;
-        for (int s = 0; s < args.nseg; ++s) {
-          const float* src = args.part + ((size_t)s * n + i) * (K + 2);
-          const float Ss = __ldcg(src + 1);
-          if (Ss > 0.f) {
-            const float rs = __ldcg(src);
-            v += (rs == R) ? __ldcg(src + 2 + k) : scale2(__ldcg(src + 2 + k), rs - R);
+        for (int s0 = 0; s0 < args.nseg; s0 += 4) {
+          float pr[4], pv[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int s = s0 + q;
+            const float* src = args.part + ((size_t)s * n + i) * (K + 2);
+            pr[q] = s < args.nseg ? __ldcg(src) : -INFINITY;
+            pv[q] = s < args.nseg ? __ldcg(src + 2 + k) : 0.f;
           }
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (pr[q] > -INFINITY) v += (pr[q] == R) ? pv[q] : scale2(pv[q], pr[q] - R);
         }
         args.out[(size_t)i * kk + k] = v * scale;
       }
@@ -413,28 +579,24 @@ __global__ void __launch_bounds__(kThreads) rowacc_kernel(AccArgs args) {
 // ---------------------------------------------------------------------------
 template <int K>
 static cudaError_t launch_colacc_k(const AccArgs& a, int ncolblk, cudaStream_t s) {
-  constexpr int CH = 64, KS = K + 4;
-  const size_t sm = (size_t)CH * KS * 4 + CH * 8 + (size_t)8 * 32 * (K + 2) * 4;
   dim3 grid(ncolblk, a.nseg);
-  colacc_kernel<K><<<grid, kThreads, sm, s>>>(a);
+  colacc_kernel<K><<<grid, kThreads, ColAccSmem<K>::bytes, s>>>(a);
   return cudaGetLastError();
 }
 
 template <int K>
 static cudaError_t launch_rowacc_k(const AccArgs& a, int nrowblk, cudaStream_t s) {
-  const size_t sm = (size_t)8 * 32 * ((K <= 32 ? 2 : 1) * (K + 2) + 1) * 4;
   dim3 grid(nrowblk, a.nseg);
-  rowacc_kernel<K><<<grid, kThreads, sm, s>>>(a);
+  rowacc_kernel<K><<<grid, kThreads, RowAccSmem<K>::bytes, s>>>(a);
   return cudaGetLastError();
 }
 
 template <int K>
 static void set_acc_attr() {
-  constexpr int CH = 64, KS = K + 4;
-  const size_t smc = (size_t)CH * KS * 4 + CH * 8 + (size_t)8 * 32 * (K + 2) * 4;
-  cudaFuncSetAttribute(colacc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
-  const size_t smr = (size_t)8 * 32 * ((K <= 32 ? 2 : 1) * (K + 2) + 1) * 4;
-  cudaFuncSetAttribute(rowacc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+  cudaFuncSetAttribute(colacc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)ColAccSmem<K>::bytes);
+  cudaFuncSetAttribute(rowacc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)RowAccSmem<K>::bytes);
 }
 
 // Dynamic shared-memory limits of every instantiation (once per device, before
@@ -447,6 +609,9 @@ void init_acc_attributes() {
 }
 
 int acc_template_k(int k) { return k <= 16 ? 16 : k <= 32 ? 32 : k <= 48 ? 48 : 64; }
+
+// Rows per CTA of the row-direction product for a given width.
+int rowacc_rows(int k) { return acc_template_k(k) <= 32 ? 16 : 8; }
 
 cudaError_t launch_colacc(const AccArgs& a, int ncolblk, cudaStream_t s) {
   switch (acc_template_k(a.k)) {
@@ -464,6 +629,12 @@ cudaError_t launch_rowacc(const AccArgs& a, int nrowblk, cudaStream_t s) {
     case 48: return launch_rowacc_k<48>(a, nrowblk, s);
     default: return launch_rowacc_k<64>(a, nrowblk, s);
   }
+}
+
+cudaError_t launch_wtw_reduce(const AccArgs& a, double* WtW, double* gw, cudaStream_t s) {
+  const int cnt = a.k * a.k + a.k;
+  wtw_reduce_kernel<<<(cnt + 31) / 32, 256, 0, s>>>(a, WtW, gw);
+  return cudaGetLastError();
 }
 
 }  // namespace eotk

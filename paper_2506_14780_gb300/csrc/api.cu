@@ -44,7 +44,14 @@ cudaError_t launch_split(const Prob* dP, const double* p, const double* logw, in
 cudaError_t launch_colacc(const AccArgs& a, int ncolblk, cudaStream_t s);
 cudaError_t launch_rowacc(const AccArgs& a, int nrowblk, cudaStream_t s);
 int acc_template_k(int k);
+int rowacc_rows(int k);
 void init_acc_attributes();
+cudaError_t launch_wtw_reduce(const AccArgs& a, double* WtW, double* gw, cudaStream_t s);
+cudaError_t launch_colmma(const AccArgs& a, const float* tiles, int ncolblk, cudaStream_t s);
+cudaError_t launch_build_tiles(const float* Z, int n, int kk, float* tiles, cudaStream_t s);
+int mma_record(int k);
+size_t mma_tiles_floats(int n, int k);
+void init_mma_attributes();
 
 __global__ void wgram_partial_kernel(const float*, const float*, const double*, int, int, int,
                                      const double*, const float*, double*, double*, const State*,
@@ -123,6 +130,7 @@ static eot_status get_ctx(DeviceCtx** out) {
   CUDA_TRY(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev));
   CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
   init_acc_attributes();
+  init_mma_attributes();
   const char* e = getenv("EOT_HOST_LOOP");
   c->cond_ok = !(e && e[0] == '1');
   *out = c.get();
@@ -159,6 +167,7 @@ struct Solver {
   int nseg = 1, cols_per_seg = 0, nrowblk = 0;
   int s4_nseg = 1, s4_seglen = 0, s4_ncolblk = 0, s4_K = 0;
   int ek_K = 0, kc_nseg = 1, kc_seglen = 0, kr_nseg = 1, kr_seglen = 0, kr_nrowblk = 0;
+  int mm_ncolblk = 0, mm_nseg = 1, mm_seglen = 0;   // tensor-core column products
   // memory
   void* mem = nullptr;
   size_t bytes = 0;
@@ -173,9 +182,9 @@ struct Solver {
   float* X = nullptr;
   float* Y = nullptr;
   // SK-NR
-  float *V = nullptr, *W = nullptr, *s4part = nullptr;
+  float *V = nullptr, *W = nullptr, *s4part = nullptr, *tilesV = nullptr, *tilesZ = nullptr;
   unsigned *s4cnt = nullptr, *s4gcnt = nullptr;
-  double *s4blk = nullptr, *gpart = nullptr, *gvpart = nullptr, *WtW = nullptr, *gw = nullptr,
+  double *s4blk = nullptr, *wtw_part = nullptr, *gpart = nullptr, *gvpart = nullptr, *WtW = nullptr, *gw = nullptr,
          *dw = nullptr;
   // modes
   float *Zb = nullptr, *Xb = nullptr, *Yb = nullptr, *Bm = nullptr, *kcpart = nullptr,
@@ -216,6 +225,10 @@ struct Solver {
     cols_per_seg = ceil_div(ceil_div(m, nseg), 128) * 128;
     nseg = ceil_div(m, cols_per_seg);
     s4_ncolblk = ceil_div(m, 32);
+    mm_ncolblk = ceil_div(m, 128);
+    mm_nseg = std::max(1, std::min(ceil_div(n, 32), (2 * nsm) / std::max(1, mm_ncolblk)));
+    mm_seglen = ceil_div(ceil_div(n, mm_nseg), 32) * 32;
+    mm_nseg = ceil_div(n, mm_seglen);
     if (ell > 0) {
       s4_K = acc_template_k(ell);
       s4_nseg = std::max(1, std::min(ceil_div(n, 64), (2 * nsm + s4_ncolblk - 1) / s4_ncolblk));
@@ -227,8 +240,7 @@ struct Solver {
       kc_nseg = std::max(1, std::min(ceil_div(n, 64), (2 * nsm + s4_ncolblk - 1) / s4_ncolblk));
       kc_seglen = ceil_div(ceil_div(n, kc_nseg), 64) * 64;
       kc_nseg = ceil_div(n, kc_seglen);
-      const int rw = ek_K <= 32 ? 2 : 1;
-      kr_nrowblk = ceil_div(n, 8 * rw);
+      kr_nrowblk = ceil_div(n, rowacc_rows(p));
       kr_nseg = std::max(1, std::min(ceil_div(m, 32), (2 * nsm + kr_nrowblk - 1) / kr_nrowblk));
       kr_seglen = ceil_div(ceil_div(m, kr_nseg), 32) * 32;
       kr_nseg = ceil_div(m, kr_seglen);
@@ -276,10 +288,12 @@ struct Solver {
     if (ell > 0) {
       V = A.take<float>((size_t)n * ell);
       W = A.take<float>((size_t)m * ell);
-      s4part = A.take<float>((size_t)s4_nseg * m * (s4_K + 2));
-      s4cnt = A.take<unsigned>(s4_ncolblk);
+      s4part = A.take<float>((size_t)mm_nseg * m * mma_record(ell));
+      s4cnt = A.take<unsigned>(mm_ncolblk);
       s4gcnt = A.take<unsigned>(1);
-      s4blk = A.take<double>((size_t)s4_ncolblk * 4);
+      s4blk = A.take<double>((size_t)mm_ncolblk * 4);
+      wtw_part = A.take<double>((size_t)mm_ncolblk * (ell * ell + ell));
+      tilesV = A.take<float>(mma_tiles_floats(n, ell));
       gpart = A.take<double>((size_t)nch * ell * ell);
       gvpart = A.take<double>((size_t)nch * ell);
       WtW = A.take<double>((size_t)ell * ell);
@@ -294,9 +308,10 @@ struct Solver {
       Xb = A.take<float>((size_t)n * p);
       Yb = A.take<float>((size_t)m * p);
       Bm = A.take<float>((size_t)p * p);
-      kcpart = A.take<float>((size_t)kc_nseg * m * (ek_K + 2));
+      kcpart = A.take<float>((size_t)mm_nseg * m * mma_record(p));
+      tilesZ = A.take<float>(mma_tiles_floats(n, p));
       krpart = A.take<float>((size_t)kr_nseg * n * (ek_K + 2));
-      kccnt = A.take<unsigned>(s4_ncolblk);
+      kccnt = A.take<unsigned>(mm_ncolblk);
       krcnt = A.take<unsigned>(kr_nrowblk);
       epart = A.take<double>((size_t)nch * p * p);
       evpart = A.take<double>((size_t)nch * p);
@@ -353,11 +368,13 @@ struct Solver {
     a.out = W;
     a.part = s4part;
     a.cnt = s4cnt;
-    a.nseg = s4_nseg;
-    a.seg_len = s4_seglen;
-    a.nblk = s4_ncolblk;
+    a.nseg = mm_nseg;
+    a.seg_len = mm_seglen;
+    a.nblk = mm_ncolblk;
     a.blkacc = s4blk;
     a.gcnt = s4gcnt;
+    a.dw = dw;
+    a.wtw_part = wtw_part;
     return a;
   }
   AccArgs kcol_args(int fb, int gb, const float* Z, float* out) const {
@@ -369,9 +386,9 @@ struct Solver {
     a.out = out;
     a.part = kcpart;
     a.cnt = kccnt;
-    a.nseg = kc_nseg;
-    a.seg_len = kc_seglen;
-    a.nblk = s4_ncolblk;
+    a.nseg = mm_nseg;
+    a.seg_len = mm_seglen;
+    a.nblk = mm_ncolblk;
     a.fbuf = fb;
     a.gbuf = gb;
     return a;
@@ -424,12 +441,11 @@ struct Solver {
     const AccArgs a = s4_args();
     for (int u = 0; u < unroll_sknr && e == cudaSuccess; ++u) {
       e = launch_row_pass(dP, hP, MODE_SK_ROW, s);
-      if (e == cudaSuccess) e = launch_colacc(a, s4_ncolblk, s);
+      if (e == cudaSuccess) e = launch_colmma(a, tilesV, mm_ncolblk, s);
       if (e != cudaSuccess) break;
-      grad_weights_kernel<<<ceil_div(m, 256), 256, 0, s>>>(dP, dw);
-      e = wgram(W, W, hP.b, 1, m, ell, dw, W, gpart, gvpart, WtW, gw, 1, s);
+      e = launch_wtw_reduce(a, WtW, gw, s);
       if (e != cudaSuccess) break;
-      newton_kernel<<<1, 256, 0, s>>>(dP, WtW, gw, nullptr);
+      newton_kernel<<<1, 32, 0, s>>>(dP, WtW, gw, nullptr);
       fprime_kernel<<<std::min(ceil_div(n, 256), 4 * ctx->nsm), 256, 0, s>>>(dP);
       e = launch_col_pass(dP, hP, MODE_TRIAL, s);
     }
@@ -437,7 +453,8 @@ struct Solver {
   }
 
   cudaError_t body_eig(cudaStream_t s, int fb, int gb) {
-    cudaError_t e = launch_colacc(kcol_args(fb, gb, Zb, Yb), s4_ncolblk, s);
+    cudaError_t e = launch_build_tiles(Zb, n, p, tilesZ, s);
+    if (e == cudaSuccess) e = launch_colmma(kcol_args(fb, gb, Zb, Yb), tilesZ, mm_ncolblk, s);
     if (e == cudaSuccess) e = launch_rowacc(krow_args(fb, gb, Yb, Xb), kr_nrowblk, s);
     if (e != cudaSuccess) return e;
     // GXX = X^T D_a X (+ c = a^T X), T = Z^T D_a X
@@ -773,6 +790,7 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
       // V^T D_a V and V^T a for this level's modes
       CUDA_TRY(S->wgram(S->V, S->V, P.a, 0, n, ell, P.a, S->V, S->gpart, S->gvpart, P.GV, P.Va, 0,
                         s));
+      CUDA_TRY(launch_build_tiles(S->V, n, ell, S->tilesV, s));
       eot_status e = S->run_loop(S->ex_sknr, 0, body_cap_nr + 1);
       if (e != EOT_OK) return e;
     } else {
@@ -867,11 +885,11 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   long long launches = 2 + 1 + (d > 0 ? (pr->normalize_cost ? 2 : 1) : (pr->normalize_cost ? 1 : 0));
   for (int t = 0; t < L; ++t) {
     launches += 1 + 2 + 1 + 2;   // level set-up, splits, first column pass, buffer copy
-    if (lev_nr[t]) launches += 3 + (long long)hLev[t].body_runs * (9 * S->unroll_sknr + 1);
+    if (lev_nr[t]) launches += 4 + (long long)hLev[t].body_runs * (6 * S->unroll_sknr + 1);
     else launches += (long long)hLev[t].body_runs * (2 * S->unroll_sk + 1);
     if (lev_eig[t]) {
       r.eig_iters += hLev[L + t].eig_iter;
-      launches += 1 + 3 + 1 + 1 + 1 + (long long)hLev[L + t].body_runs * 11 + 1;
+      launches += 1 + 3 + 1 + 1 + 1 + (long long)hLev[L + t].body_runs * 12 + 1;
     }
   }
   launches += 5;
@@ -1139,8 +1157,12 @@ eot_status eot_kapply(eot_side side, int32_t n, int32_t m, int32_t k, const floa
   CUDA_TRY(launch_split(S->dP, P.g[0], P.logb, m, P.cs[0], s));
   AccArgs aa = side == EOT_SIDE_COL ? S->kcol_args(0, 0, Z, out) : S->krow_args(0, 0, Z, out);
   aa.k = k;
-  if (side == EOT_SIDE_COL) CUDA_TRY(launch_colacc(aa, S->s4_ncolblk, s));
-  else CUDA_TRY(launch_rowacc(aa, S->kr_nrowblk, s));
+  if (side == EOT_SIDE_COL) {
+    CUDA_TRY(launch_build_tiles(Z, n, k, S->tilesZ, s));
+    CUDA_TRY(launch_colmma(aa, S->tilesZ, S->mm_ncolblk, s));
+  } else {
+    CUDA_TRY(launch_rowacc(aa, S->kr_nrowblk, s));
+  }
   return standalone_finish(s, stream);
 }
 

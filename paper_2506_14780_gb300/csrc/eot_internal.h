@@ -52,7 +52,7 @@ struct State {
   int eig_iter, eig_done, eig_max_iter, eig_fail;
   double eig_tol, eig_resid;
   int total_iters;
-  int pad2;
+  int nr_degenerate;   // set when the SK-NR products saw exponentials out of range
 };
 
 // Split arrays of one potential buffer (see eot_device.cuh).
@@ -121,6 +121,8 @@ struct AccArgs {
   int fbuf, gbuf;        // which split buffers hold f and g (products)
   double* blkacc;        // [nblk][4]
   unsigned* gcnt;
+  double* dw;            // (m) gradient weights d_j (SK-NR)
+  double* wtw_part;      // [nblk][k*k + k] block partials (SK-NR)
 };
 
 }  // namespace eotk

@@ -1,0 +1,468 @@
+// Column-direction coupling products on the tensor cores (tcgen05, TMEM):
+//
+//   Op(pi)^T Z:  out_j = sum_i exp((f_i + g_j - C_ij)/eps) a_i Z_i  (Eq. def_Op_pi_T)
+//   SK-NR fused column pass at f_k (Algorithm 4.1): h = f_k^{C,eps} by a
+//   log-sum-exp and W_j = sum_i pi(f_k, h)_ij V_i, plus the marginal test, the
+//   gradient weights d_j and per-block partials of W^T D_b^{-1} W, d^T W
+//   (Eq. dQ_semi, d2Q_semi restricted to V).
+//
+// The contraction E^T Z with E_ij = 2^{y_ij} is a dense m x n x k product:
+// a CTA owns 128 columns (the MMA's M) and a segment of rows, walked in chunks
+// of 32 rows (4 MMAs of K = 8).  Its 256 threads form the exponentials exactly
+// as the Sinkhorn passes do (two threads per column, 16 rows each), keep the
+// column's running log-sum-exp, and write E as the A operand: each thread its
+// own 64-byte piece of row "column j" of a K-major, 128-byte-swizzled tile.
+// Z (V for SK-NR) enters as the B operand from pre-built swizzled tiles of the
+// transposed rows.  Precision: every operand is split into TF32 hi + lo and the
+// three products hi*hi + hi*lo + lo*hi are accumulated in float32 in TMEM
+// (relative error ~1e-6, the accuracy of a float32 sum).  One thread issues the
+// MMAs; two buffers let the tensor core work on chunk c while the threads form
+// chunk c + 1; completion is tracked with tcgen05.commit on an mbarrier whose
+// waits are bounded.
+#include "eot_device.cuh"
+#include "eot_internal.h"
+#include "reduce.cuh"
+#include "tc.cuh"
+
+namespace eotk {
+
+constexpr int kMmaM = 128;      // columns per CTA
+constexpr int kMmaKC = 32;      // rows per chunk
+constexpr int kMmaWait = 1 << 22;
+
+// Swizzled tiles of Z^T: for chunk c of 32 rows, tile (c, part) holds NN rows
+// (the k index, padded with zeros) of 32 floats (the chunk's rows of Z), part 0
+// the TF32-rounded value, part 1 the TF32-rounded remainder.
+__global__ void build_tiles_kernel(const float* __restrict__ Z, int n, int kk, int NN,
+                                   float* __restrict__ tiles) {
+  const int nch = (n + kMmaKC - 1) / kMmaKC;
+  const long total = (long)nch * NN * kMmaKC;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const int k = (int)(e % kMmaKC);
+    const int r = (int)((e / kMmaKC) % NN);
+    const int c = (int)(e / ((long)kMmaKC * NN));
+    const int i = c * kMmaKC + k;
+    const float v = (i < n && r < kk) ? Z[(size_t)i * kk + r] : 0.f;
+    const float hi = to_tf32(v);
+    const float lo = to_tf32(v - hi);
+    const size_t off = sw128_off(r, k >> 2) / 4 + (k & 3);
+    tiles[((size_t)c * 2 + 0) * NN * kMmaKC + off] = hi;
+    tiles[((size_t)c * 2 + 1) * NN * kMmaKC + off] = lo;
+  }
+}
+
+template <int NN>
+struct MmaSmem {
+  static constexpr size_t a_tile = (size_t)kMmaM * 128;           // 16 KB
+  static constexpr size_t b_tile = (size_t)NN * 128;
+  static constexpr size_t a_off = 0;                              // [2 buf][hi, lo]
+  static constexpr size_t b_off = 4 * a_tile;                     // [2 buf][hi, lo]
+  static constexpr size_t row_off = b_off + 4 * b_tile;           // [2][32] float2
+  static constexpr size_t bytes = row_off + 2 * 32 * 8 + 1024;    // + alignment slack
+};
+
+template <int NN>
+__global__ void __launch_bounds__(256) colmma_kernel(AccArgs args, const float* __restrict__ tiles) {
+  const Prob& P = *args.P;
+  State* st = P.st;
+  const bool s4 = args.mode == 1;
+  if (s4 && st->done) return;
+  const int fb = s4 ? st->cur_f : args.fbuf;
+  const int gb = s4 ? st->cur_g : args.gbuf;
+  const int dst_g = (st->cur_g + 1) % 3;
+  const float* __restrict__ rA = P.rs[fb].A;
+  const float* __restrict__ rAL = P.rs[fb].AL;
+  const float* __restrict__ cK = P.cs[gb].K;
+  const float* __restrict__ cKL = P.cs[gb].KL;
+  using SM = MmaSmem<NN>;
+
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t s_mbar[2];
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_err;
+  __shared__ float s_lr[2][kMmaM];
+  __shared__ double s_ls[2][kMmaM];
+  __shared__ double s_red[24];
+  __shared__ unsigned s_last;
+  const uint32_t raw = smem_addr(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char* sbase = smem_raw + (base - raw);
+  float2* sRow = reinterpret_cast<float2*>(sbase + SM::row_off);
+
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int c = tid & (kMmaM - 1), h = tid >> 7;     // column within the tile, row half
+  const int n = P.n, m = P.m, kk = args.k;
+  const int cb = blockIdx.x, seg = blockIdx.y;
+  const int j = cb * kMmaM + c;
+  const bool jv = j < m;
+  const int i_beg = seg * args.seg_len;
+  const int i_end = min(n, i_beg + args.seg_len);
+  const int nch = (i_end - i_beg + kMmaKC - 1) / kMmaKC;
+  const int gch0 = i_beg / kMmaKC;                   // global chunk index of chunk 0
+  const float k2 = P.k2;
+  const float Kj = jv ? cK[j] : P.M;
+  const float cc0 = jv ? cKL[j] * k2 : 0.f;
+  float cc = cc0, ref = 0.f, run = -INFINITY, S = 0.f;
+  constexpr uint32_t idesc = idesc_tf32(kMmaM, NN);
+  constexpr uint32_t tcols = NN <= 32 ? 32 : (NN <= 64 ? 64 : 128);
+  constexpr int BV = (2 * NN * kMmaKC) / (4 * 256);  // float4 of B tiles per thread per chunk
+
+  if (tid == 0) {
+    mbar_init(smem_addr(&s_mbar[0]), 1);
+    mbar_init(smem_addr(&s_mbar[1]), 1);
+    mbar_init_fence();
+    s_err = 0;
+  }
+  if (wid == 0) tmem_alloc(smem_addr(&s_tmem), tcols);
+
+  // ---- prefetch registers ----
+  float cn[16];
+  float2 rn = make_float2(0.f, 0.f);
+  float4 bn[BV > 0 ? BV : 1];
+  auto fetch = [&](int ch) {
+    const int base_i = i_beg + ch * kMmaKC;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int i = base_i + h * 16 + u;
+      cn[u] = (jv && i < i_end) ? __ldg(P.C + (size_t)i * m + j) : 0.f;
+    }
+    if (tid < kMmaKC) {
+      const int i = base_i + tid;
+      rn = i < i_end ? make_float2(__ldg(rA + i), __ldg(rAL + i)) : make_float2(0.f, 0.f);
+    }
+    const float4* src = reinterpret_cast<const float4*>(tiles + (size_t)(gch0 + ch) * 2 * NN * kMmaKC);
+#pragma unroll
+    for (int q = 0; q < BV; ++q) bn[q] = __ldg(src + tid + q * 256);
+  };
+  auto publish = [&](int buf) {
+    float4* dstb = reinterpret_cast<float4*>(sbase + SM::b_off + (size_t)buf * 2 * SM::b_tile);
+#pragma unroll
+    for (int q = 0; q < BV; ++q) dstb[tid + q * 256] = bn[q];
+    if (tid < kMmaKC) sRow[buf * kMmaKC + tid] = rn;
+  };
+  if (nch > 0) {
+    fetch(0);
+    publish(0);
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  const uint32_t mbar0 = smem_addr(&s_mbar[0]), mbar1 = smem_addr(&s_mbar[1]);
+
+  int last_issued = -1;
+  for (int ch = 0; ch < nch; ++ch) {
+    const int buf = ch & 1;
+    last_issued = ch;
+    float cv[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) cv[u] = cn[u];
+    if (ch + 1 < nch) fetch(ch + 1);
+    const int base_i = i_beg + ch * kMmaKC;
+    // exponentials of this thread's 16 rows, written as A (hi and lo tiles)
+    float ew[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int r = h * 16 + u;
+      ew[u] = 0.f;
+      if (jv && base_i + r < i_end) {
+        const float2 ra = sRow[buf * kMmaKC + r];
+        const float t = __fadd_rn(split_exponent(cv[u], Kj, ra.x), ra.y);
+        float y = __fmaf_rn(t, k2, cc);
+        if (y > run) {
+          run = y;
+          if (run > kRecenter || (run < -kRecenter && run > -INFINITY)) {
+            const float d = rintf(run);
+            S = scale2(S, -d);
+            ref += d;
+            cc = __fsub_rn(cc0, ref);
+            run -= d;
+            y = __fmaf_rn(t, k2, cc);
+          }
+        }
+        const float e = ex2_approx(y);
+        S += e;
+        ew[u] = (ref == 0.f) ? e : scale2(e, ref);   // absolute scale for the product
+      }
+    }
+    {
+      unsigned char* ahi = sbase + SM::a_off + (size_t)buf * 2 * SM::a_tile;
+      unsigned char* alo = ahi + SM::a_tile;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float4 vh, vl;
+        vh.x = to_tf32(ew[4 * q + 0]); vl.x = to_tf32(ew[4 * q + 0] - vh.x);
+        vh.y = to_tf32(ew[4 * q + 1]); vl.y = to_tf32(ew[4 * q + 1] - vh.y);
+        vh.z = to_tf32(ew[4 * q + 2]); vl.z = to_tf32(ew[4 * q + 2] - vh.z);
+        vh.w = to_tf32(ew[4 * q + 3]); vl.w = to_tf32(ew[4 * q + 3] - vh.w);
+        const uint32_t off = sw128_off(c, h * 4 + q);
+        *reinterpret_cast<float4*>(ahi + off) = vh;
+        *reinterpret_cast<float4*>(alo + off) = vl;
+      }
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t ahi = base + (uint32_t)(SM::a_off + (size_t)buf * 2 * SM::a_tile);
+      const uint32_t alo = ahi + (uint32_t)SM::a_tile;
+      const uint32_t bhi = base + (uint32_t)(SM::b_off + (size_t)buf * 2 * SM::b_tile);
+      const uint32_t blo = bhi + (uint32_t)SM::b_tile;
+#pragma unroll
+      for (int s = 0; s < kMmaKC / 8; ++s) {
+        const uint32_t ko = s * 32;
+        mma_tf32(tmem, sdesc_sw128(ahi + ko), sdesc_sw128(bhi + ko), idesc, (ch > 0 || s > 0) ? 1u : 0u);
+        mma_tf32(tmem, sdesc_sw128(ahi + ko), sdesc_sw128(blo + ko), idesc, 1u);
+        mma_tf32(tmem, sdesc_sw128(alo + ko), sdesc_sw128(bhi + ko), idesc, 1u);
+      }
+      mma_commit(buf ? mbar1 : mbar0);
+    }
+    if (ch + 1 < nch) {
+      const int nb = buf ^ 1;
+      if (ch >= 1) {   // chunk ch - 1 used buffer nb: wait for its products
+        if (!mbar_wait(nb ? mbar1 : mbar0, ((ch - 1) >> 1) & 1, kMmaWait)) s_err = 1;
+      }
+      publish(nb);
+      fence_async_smem();
+      __syncthreads();
+      if (s_err) break;
+    }
+  }
+  // all products done (or, after a failed wait, given a bounded chance to
+  // finish) before the accumulator is read and TMEM is released
+  bool ok = true;
+  if (last_issued >= 0) {
+    const int l1 = last_issued;
+    ok = mbar_wait((l1 & 1) ? mbar1 : mbar0, (l1 >> 1) & 1, kMmaWait);
+    if (l1 >= 1) {
+      const int l2 = l1 - 1;
+      ok = mbar_wait((l2 & 1) ? mbar1 : mbar0, (l2 >> 1) & 1, kMmaWait) && ok;
+    }
+  }
+  if (!ok) s_err = 1;
+  tc_fence_after();
+  // LSE halves -> one state per column
+  s_lr[h][c] = (S > 0.f) ? ref : -INFINITY;
+  s_ls[h][c] = (double)S;
+  __syncthreads();
+  const bool err = s_err != 0;
+  if (tid < kMmaM) {
+    float R = -INFINITY;
+    double Sd = 0.0;
+    merge_d(R, Sd, s_lr[0][c], (float)s_ls[0][c]);
+    merge_d(R, Sd, s_lr[1][c], (float)s_ls[1][c]);
+    float* dst = args.part + ((size_t)seg * m + (jv ? j : 0)) * (NN + 4);
+    // accumulator row c lives in TMEM lane c (warp w reads lanes 32w..32w+31)
+#pragma unroll
+    for (int q = 0; q < NN / 16; ++q) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(wid * 32) << 16) + q * 16, v);
+      if (jv) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) dst[4 + q * 16 + u] = (err || nch == 0) ? 0.f : v[u];
+      }
+    }
+    if (jv) {
+      dst[0] = R;
+      dst[1] = (float)Sd;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (wid == 0) tmem_dealloc(tmem, tcols);
+  if (err && tid == 0) atomicAdd(&st->numeric, 1);
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    const unsigned prev = atomicAdd(&args.cnt[cb], 1u);
+    s_last = (prev == (unsigned)(args.nseg - 1));
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // ---- this CTA combines the segments of its 128 columns ----
+  float* sW = reinterpret_cast<float*>(sbase);          // [128][kk + 1], reuses the A tiles
+  float* sD = sW + kMmaM * (NN + 1);    // [128] d_j
+  float* sB = sD + kMmaM;               // [128] 1 / b_j
+  double accv[3] = {0.0, 0.0, 0.0};
+  if (tid < kMmaM) {
+    float R = -INFINITY;
+    double Stot = 0.0;
+    if (jv) merge_segments_k(args.part, args.nseg, m, NN + 4, j, R, Stot);
+    double scale = 1.0;
+    if (s4 && jv) scale = P.b[j] / (Stot * ldexp(1.0, (int)R));   // b_j / sum_i 2^{y_ij}
+    float acc[NN];
+#pragma unroll
+    for (int k = 0; k < NN; ++k) acc[k] = 0.f;
+    if (jv) {
+      for (int sg = 0; sg < args.nseg; ++sg) {
+        const float4* src =
+            reinterpret_cast<const float4*>(args.part + ((size_t)sg * m + j) * (NN + 4) + 4);
+#pragma unroll
+        for (int q = 0; q < NN / 4; ++q) {
+          const float4 v = __ldcg(src + q);
+          acc[4 * q + 0] += v.x;
+          acc[4 * q + 1] += v.y;
+          acc[4 * q + 2] += v.z;
+          acc[4 * q + 3] += v.w;
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < NN; ++k) {
+      if (k < kk) {
+        const float wv = (float)(acc[k] * scale);
+        if (jv) args.out[(size_t)j * kk + k] = wv;
+        if (s4) sW[c * (NN + 1) + k] = jv ? wv : 0.f;
+      }
+    }
+    if (s4) {
+      sD[c] = 0.f;
+      sB[c] = 0.f;
+      if (jv) {
+        float L = R * kLn2 + log_sum(Stot);
+        const double sh = P.g[gb][j];
+        double o = sh - P.eps * (double)L;
+        if (!isfinite(o) || !(Stot > 0.0) || fabs(o) > P.pot_bound) {
+          atomicAdd(&st->numeric, 1);
+          o = sh;
+          L = 0.f;
+        }
+        // the products need the exponentials in range: flag a column whose
+        // largest term lies far from 1 (the Newton step is then skipped)
+        if (R > 60.f || R < -60.f) atomicOr(&st->nr_degenerate, 1);
+        P.g[dst_g][j] = o;
+        P.Lcol[j] = L;
+        double hi;
+        float lo;
+        split_grid(o + P.eps * P.logb[j], P.qscale, P.qinv, hi, lo);
+        P.cs[dst_g].A[j] = (float)(hi + (double)P.M);
+        P.cs[dst_g].AL[j] = lo;
+        split_grid(o, P.qscale, P.qinv, hi, lo);
+        P.cs[dst_g].K[j] = (float)((double)P.M - hi);
+        P.cs[dst_g].KL[j] = lo;
+        const double wj = P.b[j];
+        const double dj = -(double)expm1f(L);     // 1 - exp((g_j - h_j)/eps)
+        args.dw[j] = dj;
+        sD[c] = (float)dj;
+        sB[c] = (float)(1.0 / wj);
+        accv[0] = wj * (double)fabsf(expm1f(L));
+        accv[1] = wj * (double)L;
+        accv[2] = wj * o;
+      }
+    }
+  }
+  if (!s4) {
+    if (tid == 0) args.cnt[cb] = 0u;
+    return;
+  }
+  __syncthreads();
+  {
+    // block partials of W^T D_b^{-1} W and d^T W over the 128 columns
+    double* dstp = args.wtw_part + (size_t)cb * (kk * kk + kk);
+    // float32 sums over the 128 columns (float64 across blocks)
+    for (int e = tid; e < kk * kk + kk; e += 256) {
+      float s = 0.f;
+      if (e < kk * kk) {
+        const int r = e / kk, q2 = e - r * kk;
+        for (int q = 0; q < kMmaM; ++q)
+          s = __fmaf_rn(sW[q * (NN + 1) + r] * sB[q], sW[q * (NN + 1) + q2], s);
+      } else {
+        const int r = e - kk * kk;
+        for (int q = 0; q < kMmaM; ++q) s = __fmaf_rn(sD[q], sW[q * (NN + 1) + r], s);
+      }
+      dstp[e] = (double)s;
+    }
+  }
+  {
+    double v0 = warp_sum_d(accv[0]), v1 = warp_sum_d(accv[1]), v2 = warp_sum_d(accv[2]);
+    if (lane == 0) {
+      s_red[wid] = v0;
+      s_red[8 + wid] = v1;
+      s_red[16 + wid] = v2;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+      for (int w = 0; w < 8; ++w) {
+        t0 += s_red[w];
+        t1 += s_red[8 + w];
+        t2 += s_red[16 + w];
+      }
+      args.cnt[cb] = 0u;
+      double* ab = args.blkacc + cb * 4;
+      ab[0] = t0;
+      ab[1] = t1;
+      ab[2] = t2;
+      __threadfence();
+      const unsigned prev = atomicAdd(args.gcnt, 1u);
+      s_last = (prev == (unsigned)(args.nblk - 1));
+    }
+    __syncthreads();
+  }
+  if (!s_last) return;
+  __threadfence();
+  double tot[3];
+  grid_sum3(args.blkacc, args.nblk, tot, s_red);
+  if (tid == 0) {
+    *args.gcnt = 0u;
+    st->l1_col = tot[0];
+    st->sum_wL = tot[1];
+    st->qsemi = st->sum_af + tot[2];   // Q_semi(f_k) = <f_k, a> + <h, b>
+    st->iter += 1;
+    st->nr_ok = 0;
+    if (st->numeric > 0) st->done = 3;
+    else if (tot[0] < st->tol) st->done = 1;
+    else if (st->iter >= st->max_iter) st->done = 2;
+  }
+}
+
+// ---------------------------------------------------------------------------
+int mma_width(int k) { return k <= 16 ? 16 : k <= 32 ? 32 : k <= 48 ? 48 : 64; }
+
+int mma_record(int k) { return mma_width(k) + 4; }
+
+size_t mma_tiles_floats(int n, int k) {
+  return (size_t)((n + kMmaKC - 1) / kMmaKC) * 2 * mma_width(k) * kMmaKC;
+}
+
+template <int NN>
+static cudaError_t launch_colmma_k(const AccArgs& a, const float* tiles, int ncolblk,
+                                   cudaStream_t s) {
+  dim3 grid(ncolblk, a.nseg);
+  colmma_kernel<NN><<<grid, 256, MmaSmem<NN>::bytes, s>>>(a, tiles);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_colmma(const AccArgs& a, const float* tiles, int ncolblk, cudaStream_t s) {
+  switch (mma_width(a.k)) {
+    case 16: return launch_colmma_k<16>(a, tiles, ncolblk, s);
+    case 32: return launch_colmma_k<32>(a, tiles, ncolblk, s);
+    case 48: return launch_colmma_k<48>(a, tiles, ncolblk, s);
+    default: return launch_colmma_k<64>(a, tiles, ncolblk, s);
+  }
+}
+
+cudaError_t launch_build_tiles(const float* Z, int n, int kk, float* tiles, cudaStream_t s) {
+  const int NN = mma_width(kk);
+  const long total = (long)((n + kMmaKC - 1) / kMmaKC) * NN * kMmaKC;
+  const int blocks = (int)((total + 255) / 256);
+  build_tiles_kernel<<<blocks < 4096 ? blocks : 4096, 256, 0, s>>>(Z, n, kk, NN, tiles);
+  return cudaGetLastError();
+}
+
+void init_mma_attributes() {
+  cudaFuncSetAttribute(colmma_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)MmaSmem<16>::bytes);
+  cudaFuncSetAttribute(colmma_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)MmaSmem<32>::bytes);
+  cudaFuncSetAttribute(colmma_kernel<48>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)MmaSmem<48>::bytes);
+  cudaFuncSetAttribute(colmma_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)MmaSmem<64>::bytes);
+}
+
+}  // namespace eotk

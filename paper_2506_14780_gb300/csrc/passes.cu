@@ -14,43 +14,34 @@
 // ||pi^T 1 - b||_1 for pi(f_k, g_k)).
 //
 // Layout: C row-major n x m.  Column pass: CTA = 128 columns (32 lanes x float4)
-// x one stripe of rows, 8 warps interleaved over the stripe's rows; each warp
-// load is 4 full 128-byte lines.  Row pass: CTA = 32 rows (4 per warp) x one
-// segment of columns, lanes along the row with float4 loads.  Partial
-// (reference, sum) states go to a [segment][index] buffer; the last CTA to
-// finish an index block (atomic arrival counter) combines the segments in fixed
-// order, so results are deterministic and independent of scheduling; the last
-// index block then runs the mode-specific grid-wide step.
+// x one stripe of rows, 8 warps interleaved over the stripe's rows, every warp
+// load a 512-byte run; the next four rows of a warp are fetched into registers
+// while the current four are reduced.  Row pass: CTA = 32 rows (4 per warp) x
+// one segment of columns, lanes along the row with float4 loads, the next step
+// prefetched the same way.  Partial (reference, sum) states go to a
+// [segment][index] buffer; the last CTA to finish an index block (atomic
+// arrival counter) merges the segments in parallel and in a fixed order, so
+// results are deterministic; the last index block then runs the mode-specific
+// grid-wide step.
 #include "eot_device.cuh"
 #include "eot_internal.h"
+#include "reduce.cuh"
 
 namespace eotk {
 
 // ---------------------------------------------------------------------------
-// Per-index combine: merge nseg partial states of index `idx`, produce the new
-// potential, its split arrays, and the index's contributions to the scalars.
-// Returns (w*|expm1 L|, w*L, w*out) through acc[0..2].
+// Finish one index from its merged (R, S): new potential, split arrays, the
+// index's contributions (w |expm1 L|, w L, w out) to the scalars.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void combine_index(const float2* __restrict__ part, int nseg,
-                                              int stride, int idx, const Prob& P,
-                                              const double* __restrict__ shift,
-                                              const double* __restrict__ w,
-                                              const double* __restrict__ logw,
-                                              double* __restrict__ out, Split so,
-                                              float* __restrict__ Lout, double acc[3],
-                                              int* numeric) {
-  float R = -INFINITY;
-  for (int s = 0; s < nseg; ++s) {
-    float2 p = __ldcg(&part[(size_t)s * stride + idx]);
-    if (p.y > 0.f && p.x > R) R = p.x;
-  }
-  double S = 0.0;
-  for (int s = 0; s < nseg; ++s) {
-    float2 p = __ldcg(&part[(size_t)s * stride + idx]);
-    if (p.y > 0.f) S += (double)(p.x == R ? p.y : scale2(p.y, p.x - R));
-  }
+__device__ __forceinline__ void finish_index(float R, double S, int idx, const Prob& P,
+                                             const double* __restrict__ shift,
+                                             const double* __restrict__ w,
+                                             const double* __restrict__ logw,
+                                             double* __restrict__ out, Split so,
+                                             float* __restrict__ Lout, double acc[3],
+                                             int* numeric) {
   float L = R * kLn2 + log_sum(S);
-  double sh = shift[idx];
+  const double sh = shift[idx];
   double o = sh - P.eps * (double)L;
   if (!isfinite(o) || !(S > 0.0) || fabs(o) > P.pot_bound) {
     atomicAdd(numeric, 1);
@@ -69,7 +60,7 @@ __device__ __forceinline__ void combine_index(const float2* __restrict__ part, i
     so.K[idx] = (float)((double)P.M - hi);
     so.KL[idx] = lo;
   }
-  double wi = w[idx];
+  const double wi = w[idx];
   acc[0] = wi * (double)fabsf(expm1f(L));
   acc[1] = wi * (double)L;
   acc[2] = wi * o;
@@ -91,32 +82,26 @@ __device__ __forceinline__ void block_sum3(double v[3], double* sh /*[3*8]*/) {
       v[k] = t;
     }
   }
+  __syncthreads();
 }
 
-// Grid-final step shared by both passes.  Called by one thread.
-__device__ void final_step(const Prob& P, int mode, const double* acc_blocks, int nblk,
-                           int dst) {
-  double t0 = 0.0, t1 = 0.0, t2 = 0.0;
-  for (int b = 0; b < nblk; ++b) {
-    t0 += __ldcg(&acc_blocks[b * 4 + 0]);
-    t1 += __ldcg(&acc_blocks[b * 4 + 1]);
-    t2 += __ldcg(&acc_blocks[b * 4 + 2]);
-  }
+// Grid-final step shared by both passes.  Called by one thread with the sums.
+__device__ void final_step(const Prob& P, int mode, const double t[3], int dst) {
   State* st = P.st;
-  st->sum_wL = t1;
-  st->sum_wout = t2;
+  st->sum_wL = t[1];
+  st->sum_wout = t[2];
   if (st->numeric > 0 && mode != MODE_PLAIN && mode != MODE_EVAL) {
     st->done = 3;
     return;
   }
   switch (mode) {
     case MODE_SK_ROW:
-      st->l1_row = t0;
-      st->sum_af = t2;
+      st->l1_row = t[0];
+      st->sum_af = t[2];
       break;
     case MODE_TRIAL: {
       // Q_semi(f') - Q_semi(f_k) = <V Delta, a> + <h' - h, b>,  h' - h = -eps L
-      const double dq = st->dot_vd_a - P.eps * t1;
+      const double dq = st->dot_vd_a - P.eps * t[1];
       st->dq = dq;
       if (dq > 0.0) {
         st->nr_acc += 1;
@@ -129,21 +114,21 @@ __device__ void final_step(const Prob& P, int mode, const double* acc_blocks, in
       break;
     }
     case MODE_SK_COL:
-      st->l1_col = t0;
-      st->qsemi = st->sum_af + t2;   // Q_semi(f_k) = <f_k, a> + <f_k^{C,eps}, b>
+      st->l1_col = t[0];
+      st->qsemi = st->sum_af + t[2];   // Q_semi(f_k) = <f_k, a> + <f_k^{C,eps}, b>
       st->iter += 1;
-      if (t0 < st->tol) st->done = 1;
+      if (t[0] < st->tol) st->done = 1;
       else if (st->iter >= st->max_iter) st->done = 2;
       else st->cur_g = dst;
       break;
     case MODE_EVAL:
-      st->l1_col = t0;
+      st->l1_col = t[0];
       break;
     case MODE_G_INIT:
       st->cur_g = dst;
       break;
     default:
-      st->l1_col = t0;
+      st->l1_col = t[0];
       break;
   }
 }
@@ -169,8 +154,9 @@ __global__ void __launch_bounds__(kThreads) col_pass_kernel(const Prob* __restri
   const float* __restrict__ cK = P.cs[sh_g].K;
   const float* __restrict__ cKL = P.cs[sh_g].KL;
 
-  __shared__ float2 s_row[kThreads];          // (A_i, AL_i) staging
-  __shared__ float2 s_part[8][kColTile];      // per-warp partial states
+  __shared__ float2 s_part[8][kColTile];
+  __shared__ float s_cr[2][kColTile];
+  __shared__ double s_cs[2][kColTile];
   __shared__ double s_red[24];
   __shared__ unsigned s_last;
 
@@ -179,7 +165,7 @@ __global__ void __launch_bounds__(kThreads) col_pass_kernel(const Prob* __restri
   const int cb = blockIdx.x, stripe = blockIdx.y;
   const int j0 = cb * kColTile + lane * 4;
   const int i_beg = stripe * P.rows_per_stripe;
-  const int i_end = min(n, i_beg + P.rows_per_stripe);
+  const int nrows = min(n, i_beg + P.rows_per_stripe) - i_beg;
   const float k2 = P.k2;
 
   float K[4], cc0[4], cc[4], ref[4], run[4], S[4];
@@ -195,39 +181,47 @@ __global__ void __launch_bounds__(kThreads) col_pass_kernel(const Prob* __restri
     run[c] = -INFINITY;
     S[c] = 0.f;
   }
-  const bool any_valid = valid[0];
 
-  for (int base = i_beg; base < i_end; base += kThreads) {
-    const int nrows = min(kThreads, i_end - base);
-    __syncthreads();
-    if ((int)threadIdx.x < nrows) {
-      s_row[threadIdx.x] = make_float2(rA[base + threadIdx.x], rAL[base + threadIdx.x]);
-    }
-    __syncthreads();
-    if (!any_valid) continue;
-    // rows r = wid, wid + 8, ... of this chunk, 4 at a time
-    for (int r0 = wid; r0 < nrows; r0 += 32) {
-      float t[4][4];
+  if (valid[0]) {
+    // rows r = wid + 8 t of the stripe, four at a time, prefetched one step ahead
+    float cn[4][4], an[4], aln[4];
+    auto fetch = [&](int r0) {
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int r = r0 + 8 * u;
         if (r < nrows) {
-          const float2 ra = s_row[r];
-          const float* crow = P.C + (size_t)(base + r) * m + j0;
-          float cv[4];
+          const int i = i_beg + r;
+          const float* crow = P.C + (size_t)i * m + j0;
           if (VEC == 4) {
             const float4 c4 = __ldg(reinterpret_cast<const float4*>(crow));
-            cv[0] = c4.x; cv[1] = c4.y; cv[2] = c4.z; cv[3] = c4.w;
+            cn[u][0] = c4.x; cn[u][1] = c4.y; cn[u][2] = c4.z; cn[u][3] = c4.w;
           } else {
 #pragma unroll
-            for (int c = 0; c < 4; ++c) cv[c] = valid[c] ? __ldg(crow + c) : 0.f;
+            for (int c = 0; c < 4; ++c) cn[u][c] = valid[c] ? __ldg(crow + c) : 0.f;
           }
-#pragma unroll
-          for (int c = 0; c < 4; ++c) t[u][c] = __fadd_rn(split_exponent(cv[c], K[c], ra.x), ra.y);
-        } else {
-#pragma unroll
-          for (int c = 0; c < 4; ++c) t[u][c] = -INFINITY;
+          an[u] = __ldg(rA + i);
+          aln[u] = __ldg(rAL + i);
         }
+      }
+    };
+    fetch(wid);
+    for (int r0 = wid; r0 < nrows; r0 += 32) {
+      float cv[4][4], av[4], alv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        av[u] = an[u];
+        alv[u] = aln[u];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) cv[u][c] = cn[u][c];
+      }
+      if (r0 + 32 < nrows) fetch(r0 + 32);
+      float t[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const bool rvalid = r0 + 8 * u < nrows;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          t[u][c] = rvalid ? __fadd_rn(split_exponent(cv[u][c], K[c], av[u]), alv[u]) : -INFINITY;
       }
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
@@ -249,21 +243,20 @@ __global__ void __launch_bounds__(kThreads) col_pass_kernel(const Prob* __restri
       }
     }
   }
-  // intra-CTA combine over the 8 warps
+  // intra-CTA combine over the 8 warps (float64 sum at the largest reference)
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    if (!valid[c]) S[c] = 0.f;
-    s_part[wid][lane * 4 + c] = make_float2(ref[c], S[c]);
-  }
+  for (int c = 0; c < 4; ++c) s_part[wid][lane * 4 + c] = make_float2(ref[c], valid[c] ? S[c] : 0.f);
   __syncthreads();
   if (threadIdx.x < kColTile) {
     const int j = cb * kColTile + threadIdx.x;
-    float2 p = s_part[0][threadIdx.x];
-    for (int w = 1; w < 8; ++w) {
-      float2 q = s_part[w][threadIdx.x];
-      lse2_merge(p.x, p.y, q.x, q.y);
+    float R = -INFINITY;
+    double Sd = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      const float2 q = s_part[w][threadIdx.x];
+      merge_d(R, Sd, q.x, q.y);
     }
-    if (j < m) P.part_col[(size_t)stripe * m + j] = p;
+    if (j < m) P.part_col[(size_t)stripe * m + j] = make_float2(R, (float)Sd);
   }
   __threadfence();
   __syncthreads();
@@ -273,15 +266,28 @@ __global__ void __launch_bounds__(kThreads) col_pass_kernel(const Prob* __restri
   }
   __syncthreads();
   if (!s_last) return;
-  // --- this CTA combines column block cb ---
+  // --- this CTA combines column block cb: both halves of the CTA merge half
+  //     of the stripes each, then thread c merges the two halves ---
   __threadfence();
+  {
+    const int c = threadIdx.x & (kColTile - 1), h = threadIdx.x >> 7;
+    const int j = cb * kColTile + c;
+    float R = -INFINITY;
+    double Sd = 0.0;
+    if (j < m) merge_segments(P.part_col, P.nstripe, m, j, h, 2, R, Sd);
+    s_cr[h][c] = R;
+    s_cs[h][c] = Sd;
+  }
+  __syncthreads();
   double accv[3] = {0.0, 0.0, 0.0};
   if (threadIdx.x < kColTile) {
     const int j = cb * kColTile + threadIdx.x;
     if (j < m) {
+      float R = s_cr[0][threadIdx.x];
+      double Sd = s_cs[0][threadIdx.x];
+      merge_dd(R, Sd, s_cr[1][threadIdx.x], s_cs[1][threadIdx.x]);
       double* out;
       Split so;
-      float* Lout = P.Lcol;
       if (mode == MODE_PLAIN) {
         out = P.out_plain;
         so = Split{nullptr, nullptr, nullptr, nullptr};
@@ -292,8 +298,7 @@ __global__ void __launch_bounds__(kThreads) col_pass_kernel(const Prob* __restri
         out = P.g[dst_g];
         so = P.cs[dst_g];
       }
-      combine_index(P.part_col, P.nstripe, m, j, P, P.g[sh_g], P.b, P.logb, out, so, Lout, accv,
-                    &st->numeric);
+      finish_index(R, Sd, j, P, P.g[sh_g], P.b, P.logb, out, so, P.Lcol, accv, &st->numeric);
       if (mode == MODE_PLAIN && P.logratio_plain) P.logratio_plain[j] = (double)P.Lcol[j];
     }
   }
@@ -306,11 +311,16 @@ __global__ void __launch_bounds__(kThreads) col_pass_kernel(const Prob* __restri
     ab[2] = accv[2];
     __threadfence();
     const unsigned prev = atomicAdd(&P.gcnt[0], 1u);
-    if (prev == (unsigned)(P.ncolblk - 1)) {
-      __threadfence();
-      P.gcnt[0] = 0u;
-      final_step(P, mode, P.acc_col, P.ncolblk, dst_g);
-    }
+    s_last = (prev == (unsigned)(P.ncolblk - 1));
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double tot[3];
+  grid_sum3(P.acc_col, P.ncolblk, tot, s_red);
+  if (threadIdx.x == 0) {
+    P.gcnt[0] = 0u;
+    final_step(P, mode, tot, dst_g);
   }
 }
 
@@ -329,6 +339,8 @@ __global__ void __launch_bounds__(kThreads) row_pass_kernel(const Prob* __restri
   const float* __restrict__ rKL = P.rs[cf].KL;
 
   __shared__ float2 s_part[kRowTile];
+  __shared__ float s_cr[8][kRowTile];
+  __shared__ double s_cs[8][kRowTile];
   __shared__ double s_red[24];
   __shared__ unsigned s_last;
 
@@ -340,8 +352,8 @@ __global__ void __launch_bounds__(kThreads) row_pass_kernel(const Prob* __restri
   const int c_end = min(m, c_beg + P.cols_per_seg);
   const float k2 = P.k2;
 
-  float K[kRowsPerWarp], cc0[kRowsPerWarp], cc[kRowsPerWarp], ref[kRowsPerWarp], run[kRowsPerWarp],
-      S[kRowsPerWarp];
+  float K[kRowsPerWarp], cc0[kRowsPerWarp], cc[kRowsPerWarp], ref[kRowsPerWarp],
+      run[kRowsPerWarp], S[kRowsPerWarp];
   bool rv[kRowsPerWarp];
 #pragma unroll
   for (int r = 0; r < kRowsPerWarp; ++r) {
@@ -355,44 +367,59 @@ __global__ void __launch_bounds__(kThreads) row_pass_kernel(const Prob* __restri
     S[r] = 0.f;
   }
   if (rv[0]) {
-    for (int j = c_beg + lane * 4; j < c_end; j += 128) {
-      float ca[4], cal[4];
-      bool cvld[4];
+    float can[4], caln[4], cn[kRowsPerWarp][4];
+    auto fetch = [&](int j) {
       if (VEC == 4) {
         const float4 a4 = __ldg(reinterpret_cast<const float4*>(cA + j));
         const float4 l4 = __ldg(reinterpret_cast<const float4*>(cAL + j));
-        ca[0] = a4.x; ca[1] = a4.y; ca[2] = a4.z; ca[3] = a4.w;
-        cal[0] = l4.x; cal[1] = l4.y; cal[2] = l4.z; cal[3] = l4.w;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) cvld[c] = true;
+        can[0] = a4.x; can[1] = a4.y; can[2] = a4.z; can[3] = a4.w;
+        caln[0] = l4.x; caln[1] = l4.y; caln[2] = l4.z; caln[3] = l4.w;
       } else {
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          cvld[c] = j + c < c_end;
-          ca[c] = cvld[c] ? __ldg(cA + j + c) : 0.f;
-          cal[c] = cvld[c] ? __ldg(cAL + j + c) : 0.f;
+          const bool v = j + c < c_end;
+          can[c] = v ? __ldg(cA + j + c) : 0.f;
+          caln[c] = v ? __ldg(cAL + j + c) : 0.f;
         }
       }
 #pragma unroll
       for (int r = 0; r < kRowsPerWarp; ++r) {
-        float cv[4];
         if (rv[r]) {
           const float* crow = P.C + (size_t)(i0 + r) * m + j;
           if (VEC == 4) {
             const float4 c4 = __ldg(reinterpret_cast<const float4*>(crow));
-            cv[0] = c4.x; cv[1] = c4.y; cv[2] = c4.z; cv[3] = c4.w;
+            cn[r][0] = c4.x; cn[r][1] = c4.y; cn[r][2] = c4.z; cn[r][3] = c4.w;
           } else {
 #pragma unroll
-            for (int c = 0; c < 4; ++c) cv[c] = cvld[c] ? __ldg(crow + c) : 0.f;
+            for (int c = 0; c < 4; ++c) cn[r][c] = (j + c < c_end) ? __ldg(crow + c) : 0.f;
           }
-        } else {
-#pragma unroll
-          for (int c = 0; c < 4; ++c) cv[c] = 0.f;
         }
+      }
+    };
+    int j = c_beg + lane * 4;
+    if (j < c_end) fetch(j);
+    for (; j < c_end; j += 128) {
+      float ca[4], cal[4], cv[kRowsPerWarp][4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        ca[c] = can[c];
+        cal[c] = caln[c];
+      }
+#pragma unroll
+      for (int r = 0; r < kRowsPerWarp; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) cv[r][c] = cn[r][c];
+      if (j + 128 < c_end) fetch(j + 128);
+      bool cvld[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) cvld[c] = (VEC == 4) || (j + c < c_end);
+#pragma unroll
+      for (int r = 0; r < kRowsPerWarp; ++r) {
         float t[4], y[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          t[c] = (cvld[c] && rv[r]) ? __fadd_rn(split_exponent(cv[c], K[r], ca[c]), cal[c]) : -INFINITY;
+          t[c] = (cvld[c] && rv[r]) ? __fadd_rn(split_exponent(cv[r][c], K[r], ca[c]), cal[c])
+                                    : -INFINITY;
           y[c] = __fmaf_rn(t[c], k2, cc[r]);
         }
         const float mx = fmaxf(fmaxf(y[0], y[1]), fmaxf(y[2], y[3]));
@@ -441,10 +468,25 @@ __global__ void __launch_bounds__(kThreads) row_pass_kernel(const Prob* __restri
   __syncthreads();
   if (!s_last) return;
   __threadfence();
+  {
+    // eight groups of 32 threads merge interleaved segments of the 32 rows
+    const int rr = threadIdx.x & (kRowTile - 1), h = threadIdx.x >> 5;
+    const int i = rb * kRowTile + rr;
+    float R = -INFINITY;
+    double Sd = 0.0;
+    if (i < n) merge_segments(P.part_row, P.nseg, n, i, h, 8, R, Sd);
+    s_cr[h][rr] = R;
+    s_cs[h][rr] = Sd;
+  }
+  __syncthreads();
   double accv[3] = {0.0, 0.0, 0.0};
   if (threadIdx.x < kRowTile) {
     const int i = rb * kRowTile + threadIdx.x;
     if (i < n) {
+      float R = s_cr[0][threadIdx.x];
+      double Sd = s_cs[0][threadIdx.x];
+#pragma unroll
+      for (int h = 1; h < 8; ++h) merge_dd(R, Sd, s_cr[h][threadIdx.x], s_cs[h][threadIdx.x]);
       double* out;
       Split so;
       if (mode == MODE_PLAIN) {
@@ -457,8 +499,7 @@ __global__ void __launch_bounds__(kThreads) row_pass_kernel(const Prob* __restri
         out = P.f[cf];
         so = P.rs[cf];
       }
-      combine_index(P.part_row, P.nseg, n, i, P, P.f[cf], P.a, P.loga, out, so, P.Lrow, accv,
-                    &st->numeric);
+      finish_index(R, Sd, i, P, P.f[cf], P.a, P.loga, out, so, P.Lrow, accv, &st->numeric);
       if (mode == MODE_PLAIN && P.logratio_plain) P.logratio_plain[i] = (double)P.Lrow[i];
     }
   }
@@ -471,17 +512,17 @@ __global__ void __launch_bounds__(kThreads) row_pass_kernel(const Prob* __restri
     ab[2] = accv[2];
     __threadfence();
     const unsigned prev = atomicAdd(&P.gcnt[1], 1u);
-    if (prev == (unsigned)(P.nrowblk - 1)) {
-      __threadfence();
-      P.gcnt[1] = 0u;
-      if (mode == MODE_EVAL) {
-        double t0 = 0.0;
-        for (int b = 0; b < P.nrowblk; ++b) t0 += __ldcg(&P.acc_row[b * 4 + 0]);
-        st->l1_row = t0;
-      } else {
-        final_step(P, mode == MODE_PLAIN ? MODE_PLAIN : MODE_SK_ROW, P.acc_row, P.nrowblk, cf);
-      }
-    }
+    s_last = (prev == (unsigned)(P.nrowblk - 1));
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double tot[3];
+  grid_sum3(P.acc_row, P.nrowblk, tot, s_red);
+  if (threadIdx.x == 0) {
+    P.gcnt[1] = 0u;
+    if (mode == MODE_EVAL) st->l1_row = tot[0];
+    else final_step(P, mode == MODE_PLAIN ? MODE_PLAIN : MODE_SK_ROW, tot, cf);
   }
 }
 

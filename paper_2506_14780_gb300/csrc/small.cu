@@ -78,76 +78,78 @@ __global__ void wgram_reduce_kernel(const double* __restrict__ part, int nchunk,
 }
 
 // ---------------------------------------------------------------------------
-// Newton step on V (one CTA).  GV = V^T D_a V, WtW = sum_j W_j W_j^T / b_j,
-// gw = sum_j d_j W_j (d_j = -expm1(L_j)), Va = V^T a.
+// Newton step on V (one warp, float64).  GV = V^T D_a V (or V^T D_r V),
+// WtW = sum_j W_j W_j^T / b_j, gw = sum_j d_j W_j (d_j = -expm1(L_j)),
+// Va = V^T a.  -H_V = (GV - WtW)/eps is factorised by a right-looking Cholesky
+// with lanes over rows; Delta = (-H_V)^{-1} grad_V, grad_V = -gw.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) newton_kernel(const Prob* __restrict__ PP,
-                                                     const double* __restrict__ WtW,
-                                                     const double* __restrict__ gw,
-                                                     const double* __restrict__ Dr) {
+__global__ void __launch_bounds__(32) newton_kernel(const Prob* __restrict__ PP,
+                                                    const double* __restrict__ WtW,
+                                                    const double* __restrict__ gw,
+                                                    const double* __restrict__ Dr) {
   const Prob& P = *PP;
   State* st = P.st;
   if (st->done) return;
   const int l = P.ell;
-  __shared__ double H[kMaxK * kMaxK];
-  __shared__ double g[kMaxK];
-  __shared__ int s_fail;
+  const int lane = threadIdx.x;
+  // the matrix is assembled in float64 (the difference GV - WtW cancels), the
+  // factorisation and solves run in float32 (relative error ~1e-7 x cond)
+  __shared__ float H[kMaxK * kMaxK];
+  __shared__ float g[kMaxK];
   const double inv_eps = 1.0 / P.eps;
-  // -H_V = (1/eps) [V^T D V - W^T D_b^{-1} W]
-  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
-    const double gvd = Dr ? Dr[e] : P.GV[e];
-    H[e] = inv_eps * (gvd - WtW[e]);
-  }
-  for (int k = threadIdx.x; k < l; k += blockDim.x) g[k] = -gw[k];
-  if (threadIdx.x == 0) s_fail = 0;
-  __syncthreads();
-  // symmetrise, then right-looking Cholesky in place (lower triangle)
-  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+  for (int e = lane; e < l * l; e += 32) {
     const int r = e / l, c = e - r * l;
-    if (r > c) {
-      const double v = 0.5 * (H[e] + H[c * l + r]);
-      H[e] = v;
-      H[c * l + r] = v;
-    }
+    const double gv = Dr ? 0.5 * (Dr[r * l + c] + Dr[c * l + r]) : 0.5 * (P.GV[r * l + c] + P.GV[c * l + r]);
+    const double wt = 0.5 * (WtW[r * l + c] + WtW[c * l + r]);
+    H[e] = (float)(inv_eps * (gv - wt));
   }
-  __syncthreads();
+  for (int k = lane; k < l; k += 32) g[k] = (float)(-gw[k]);
+  __syncwarp();
+  bool fail = false;
   for (int k = 0; k < l; ++k) {
-    if (threadIdx.x == 0) {
-      const double d = H[k * l + k];
-      if (!(d > 0.0) || !isfinite(d)) s_fail = 1;
-      H[k * l + k] = (d > 0.0) ? sqrt(d) : 1.0;
+    const float d = H[k * l + k];
+    if (!(d > 0.f) || !isfinite(d)) fail = true;
+    const float dk = d > 0.f ? sqrtf(d) : 1.f;
+    __syncwarp();
+    if (lane == 0) H[k * l + k] = dk;
+    for (int r = k + 1 + lane; r < l; r += 32) H[r * l + k] /= dk;
+    __syncwarp();
+    for (int r = k + 1 + lane; r < l; r += 32) {
+      const float hrk = H[r * l + k];
+      for (int c = k + 1; c <= r; ++c) H[r * l + c] -= hrk * H[c * l + k];
     }
-    __syncthreads();
-    const double dk = H[k * l + k];
-    for (int r = k + 1 + threadIdx.x; r < l; r += blockDim.x) H[r * l + k] /= dk;
-    __syncthreads();
-    for (int e = threadIdx.x; e < (l - k - 1) * (l - k - 1); e += blockDim.x) {
-      const int r = k + 1 + e / (l - k - 1), c = k + 1 + e % (l - k - 1);
-      if (c <= r) H[r * l + c] -= H[r * l + k] * H[c * l + k];
-    }
-    __syncthreads();
+    __syncwarp();
   }
-  if (threadIdx.x == 0) {
-    // solve L y = g, L^T x = y
-    double y[kMaxK];
-    for (int r = 0; r < l; ++r) {
-      double s = g[r];
-      for (int c = 0; c < r; ++c) s -= H[r * l + c] * y[c];
-      y[r] = s / H[r * l + r];
-    }
-    for (int r = l - 1; r >= 0; --r) {
-      double s = y[r];
-      for (int c = r + 1; c < l; ++c) s -= H[c * l + r] * y[c];
-      y[r] = s / H[r * l + r];
-    }
-    double dva = 0.0;
-    bool finite = true;
-    for (int k = 0; k < l; ++k) {
-      P.delta[k] = y[k];
-      dva += y[k] * P.Va[k];
-      finite = finite && isfinite(y[k]);
-    }
-    if (s_fail || !finite) {
+  // L y = g (column oriented), then L^T x = y
+  for (int r = 0; r < l; ++r) {
+    const float yr = g[r] / H[r * l + r];
+    __syncwarp();
+    if (lane == 0) g[r] = yr;
+    for (int i = r + 1 + lane; i < l; i += 32) g[i] -= H[i * l + r] * yr;
+    __syncwarp();
+  }
+  for (int r = l - 1; r >= 0; --r) {
+    const float xr = g[r] / H[r * l + r];
+    __syncwarp();
+    if (lane == 0) g[r] = xr;
+    for (int i = lane; i < r; i += 32) g[i] -= H[r * l + i] * xr;
+    __syncwarp();
+  }
+  double dva = 0.0;
+  bool finite = true;
+  for (int k = lane; k < l; k += 32) {
+    P.delta[k] = (double)g[k];
+    dva += (double)g[k] * P.Va[k];
+    finite = finite && isfinite(g[k]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dva += __shfl_xor_sync(0xffffffffu, dva, o);
+  finite = __all_sync(0xffffffffu, finite);
+  fail = __any_sync(0xffffffffu, fail) || st->nr_degenerate != 0;
+  __syncwarp();
+  if (lane == 0) {
+    st->nr_degenerate = 0;
+    if (fail || !finite) {
       st->nr_ok = 0;
       st->nr_rej += 1;
       st->cur_g = (st->cur_g + 1) % 3;   // keep the Sinkhorn step: g_{k+1} = h
@@ -164,16 +166,19 @@ __global__ void fprime_kernel(const Prob* __restrict__ PP) {
   const State* st = P.st;
   if (st->done || !st->nr_ok) return;
   const int cf = st->cur_f, l = P.ell;
-  __shared__ double d[kMaxK];
-  for (int k = threadIdx.x; k < l; k += blockDim.x) d[k] = P.delta[k];
+  // the step V Delta is accumulated in float32 (it is a small correction; the
+  // trial pass evaluates exactly the f' stored here)
+  __shared__ float d[kMaxK];
+  for (int k = threadIdx.x; k < l; k += blockDim.x) d[k] = (float)P.delta[k];
   __syncthreads();
   const double* f = P.f[cf];
   double* fo = P.f[1 - cf];
   const Split so = P.rs[1 - cf];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
-    double v = f[i];
     const float* Vi = P.V + (size_t)i * l;
-    for (int k = 0; k < l; ++k) v += (double)Vi[k] * d[k];
+    float corr = 0.f;
+    for (int k = 0; k < l; ++k) corr = __fmaf_rn(Vi[k], d[k], corr);
+    const double v = f[i] + (double)corr;
     fo[i] = v;
     double hi;
     float lo;
@@ -187,11 +192,13 @@ __global__ void fprime_kernel(const Prob* __restrict__ PP) {
 }
 
 // ---------------------------------------------------------------------------
-// Mode computation: one CTA.
+// Mode computation: one CTA, float32 (the projected p x p problems only need
+// a good basis; the float64 Gram sums come in from wgram).
 //   inputs  GXX = X^T D_a X, T = Z^T D_a X, c = a^T X   (float64, p x p / p)
 //   mode 0 (orthonormalise only, X is the start block):  B = L^{-T},
 //           L L^T = GXX - c c^T
-//   mode 1 (Rayleigh-Ritz + power step): T = Q Theta Q^T (Jacobi, descending),
+//   mode 1 (Rayleigh-Ritz + power step): T = Q Theta Q^T (cyclic Jacobi with
+//           the circle ordering, descending Ritz values),
 //           residual_k^2 = (Q^T GXX Q)_kk - theta_k^2, then
 //           L L^T = Q^T (GXX - c c^T) Q and B = Q L^{-T}.
 //   outputs B (p x p float32), theta (p), max residual over the first l.
@@ -208,26 +215,25 @@ __global__ void __launch_bounds__(256) eig_small_kernel(int p, int l, int mode,
   __shared__ float Q[kMaxP * kMaxP];
   __shared__ float G[kMaxP * kMaxP];
   __shared__ float tmp[kMaxP * kMaxP];
-  __shared__ float rc[kMaxP], rs[kMaxP];
+  __shared__ float rc[kMaxP], rs[kMaxP], cf[kMaxP], qc[kMaxP];
   __shared__ int pairs[kMaxP];
   __shared__ float th[kMaxP];
   __shared__ int order[kMaxP];
-  __shared__ int s_fail;
-  __shared__ float s_off;
+  __shared__ float s_w[16];
+  __shared__ int s_stop, s_fail;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int pe = (p + 1) & ~1;   // padded even size for the tournament ordering
+  const int pe = (p + 1) & ~1;   // padded even size for the circle ordering
   for (int e = tid; e < pe * pe; e += nt) {
     const int r = e / pe, q = e - r * pe;
     const bool in = r < p && q < p;
-    A[e] = (mode == 1 && in) ? (float)(0.5 * (T[r * p + q] + T[q * p + r])) : (r == q && !in ? 0.f : 0.f);
+    A[e] = (mode == 1 && in) ? (float)(0.5 * (T[r * p + q] + T[q * p + r])) : 0.f;
     Q[e] = (r == q) ? 1.f : 0.f;
   }
+  for (int k = tid; k < p; k += nt) cf[k] = (float)c[k];
   if (tid == 0) s_fail = 0;
   __syncthreads();
   if (mode == 1) {
-    __shared__ float s_w[16];
-    for (int sweep = 0; sweep < 20; ++sweep) {
-      // deterministic off-diagonal / diagonal norms
+    for (int sweep = 0; sweep < 12; ++sweep) {
       float loc = 0.f, dia = 0.f;
       for (int e = tid; e < pe * pe; e += nt) {
         const int r = e / pe, q = e - r * pe;
@@ -241,14 +247,11 @@ __global__ void __launch_bounds__(256) eig_small_kernel(int p, int l, int mode,
       if (tid == 0) {
         float o = 0.f, d = 0.f;
         for (int w = 0; w < (nt >> 5); ++w) { o += s_w[w]; d += s_w[8 + w]; }
-        s_off = (o <= 1e-14f * (d + 1e-30f)) ? 1.f : 0.f;
+        s_stop = (o <= 1e-10f * (d + 1e-30f)) ? 1 : 0;
       }
       __syncthreads();
-      const bool stop = s_off != 0.f;
-      __syncthreads();
-      if (stop) break;
+      if (s_stop) break;
       for (int round = 0; round < pe - 1; ++round) {
-        // circle-method pairing: position 0 fixed, positions 1..pe-1 rotate
         if (tid < pe / 2) {
           const int pa = tid, pb = pe - 1 - tid;
           const int a = pa == 0 ? 0 : 1 + (pa - 1 + round) % (pe - 1);
@@ -268,8 +271,7 @@ __global__ void __launch_bounds__(256) eig_small_kernel(int p, int l, int mode,
           rs[tid] = sth;
         }
         __syncthreads();
-        // rows: A <- J^T A
-        for (int e = tid; e < (pe / 2) * pe; e += nt) {
+        for (int e = tid; e < (pe / 2) * pe; e += nt) {     // rows: A <- J^T A
           const int pr = e / pe, col = e - pr * pe;
           const int k = pairs[2 * pr], q = pairs[2 * pr + 1];
           const float cth = rc[pr], sth = rs[pr];
@@ -278,8 +280,7 @@ __global__ void __launch_bounds__(256) eig_small_kernel(int p, int l, int mode,
           A[q * pe + col] = sth * ak + cth * aq;
         }
         __syncthreads();
-        // columns: A <- A J, Q <- Q J
-        for (int e = tid; e < (pe / 2) * pe; e += nt) {
+        for (int e = tid; e < (pe / 2) * pe; e += nt) {     // columns: A <- A J, Q <- Q J
           const int pr = e / pe, row = e - pr * pe;
           const int k = pairs[2 * pr], q = pairs[2 * pr + 1];
           const float cth = rc[pr], sth = rs[pr];
@@ -293,7 +294,6 @@ __global__ void __launch_bounds__(256) eig_small_kernel(int p, int l, int mode,
         __syncthreads();
       }
     }
-    // sort eigenvalues descending (rank by count)
     for (int k = tid; k < p; k += nt) th[k] = A[k * pe + k];
     __syncthreads();
     for (int k = tid; k < p; k += nt) {
@@ -302,7 +302,6 @@ __global__ void __launch_bounds__(256) eig_small_kernel(int p, int l, int mode,
       order[rank] = k;
     }
     __syncthreads();
-    // tmp = Q with sorted columns
     for (int e = tid; e < p * p; e += nt) {
       const int r = e / p, q = e - r * p;
       tmp[r * p + q] = Q[r * pe + order[q]];
@@ -318,7 +317,7 @@ __global__ void __launch_bounds__(256) eig_small_kernel(int p, int l, int mode,
     }
     __syncthreads();
   }
-  // G = Q^T (GXX - c c^T) Q  (and residuals from Q^T GXX Q)
+  // G = GXX - c c^T (float), then (mode 1) G <- Q^T G Q
   for (int e = tid; e < p * p; e += nt) {
     const int r = e / p, q = e - r * p;
     G[e] = (float)(GXX[e] - c[r] * c[q]);
@@ -327,44 +326,49 @@ __global__ void __launch_bounds__(256) eig_small_kernel(int p, int l, int mode,
   if (mode == 1) {
     for (int e = tid; e < p * p; e += nt) {     // tmp = G Q
       const int r = e / p, q = e - r * p;
-      float s = 0.f;
-      for (int k = 0; k < p; ++k) s += G[r * p + k] * Q[k * p + q];
-      tmp[e] = s;
+      float acc = 0.f;
+      for (int k = 0; k < p; ++k) acc = __fmaf_rn(G[r * p + k], Q[k * p + q], acc);
+      tmp[e] = acc;
     }
     __syncthreads();
-    for (int e = tid; e < p * p; e += nt) {     // A = Q^T tmp  (reuse A, stride p)
+    for (int e = tid; e < p * p; e += nt) {     // A = Q^T tmp (stride p)
       const int r = e / p, q = e - r * p;
-      float s = 0.f;
-      for (int k = 0; k < p; ++k) s += Q[k * p + r] * tmp[k * p + q];
-      A[e] = s;
+      float acc = 0.f;
+      for (int k = 0; k < p; ++k) acc = __fmaf_rn(Q[k * p + r], tmp[k * p + q], acc);
+      A[e] = acc;
     }
+    for (int k = tid; k < p; k += nt) {         // (Q^T c)_k
+      float acc = 0.f;
+      for (int r = 0; r < p; ++r) acc = __fmaf_rn(Q[r * p + k], cf[r], acc);
+      qc[k] = acc;
+    }
+    __syncthreads();
+    // residual_k^2 = (Q^T GXX Q)_kk - theta_k^2 = G'_kk + (Q^T c)_k^2 - theta_k^2
+    float rmax = 0.f;
+    for (int k = tid; k < l && k < p; k += nt) {
+      const float t = (float)theta_out[k];
+      const float r2 = A[k * p + k] + qc[k] * qc[k] - t * t;
+      rmax = fmaxf(rmax, r2 > 0.f ? sqrtf(r2) : 0.f);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    if ((tid & 31) == 0) s_w[tid >> 5] = rmax;
     __syncthreads();
     if (tid == 0) {
-      double mx = 0.0;
-      for (int k = 0; k < l && k < p; ++k) {
-        // (Q^T GXX Q)_kk = G'_kk + (Q^T c)_k^2
-        double qc = 0.0;
-        for (int r = 0; r < p; ++r) qc += (double)Q[r * p + k] * c[r];
-        const double gkk = (double)A[k * p + k] + qc * qc;
-        const double th2 = theta_out[k] * theta_out[k];
-        const double r2 = gkk - th2;
-        mx = fmax(mx, r2 > 0.0 ? sqrt(r2) : 0.0);
-      }
-      *resid_out = mx;
+      float mx = 0.f;
+      for (int w = 0; w < (nt >> 5); ++w) mx = fmaxf(mx, s_w[w]);
+      *resid_out = (double)mx;
     }
-    __syncthreads();
     for (int e = tid; e < p * p; e += nt) G[e] = A[e];
     __syncthreads();
   }
-  // Cholesky of G (lower, in place), single thread per column step
+  // Cholesky of G (lower, in place)
   for (int k = 0; k < p; ++k) {
-    if (tid == 0) {
-      const float d = G[k * p + k];
-      if (!(d > 0.f)) s_fail = 1;
-      G[k * p + k] = d > 0.f ? sqrtf(d) : 1.f;
-    }
+    const float d = G[k * p + k];
+    const float dk = d > 0.f ? sqrtf(d) : 1.f;
+    if (tid == 0 && !(d > 0.f)) s_fail = 1;
     __syncthreads();
-    const float dk = G[k * p + k];
+    if (tid == 0) G[k * p + k] = dk;
     for (int r = k + 1 + tid; r < p; r += nt) G[r * p + k] /= dk;
     __syncthreads();
     for (int e = tid; e < (p - k - 1) * (p - k - 1); e += nt) {
@@ -373,17 +377,19 @@ __global__ void __launch_bounds__(256) eig_small_kernel(int p, int l, int mode,
     }
     __syncthreads();
   }
-  // B = Q L^{-T}:  solve B L^T = Q row by row (each thread one row)
+  // B = Q L^{-T}: row r of B solves  B_r L^T = Q_r  (thread r, in place in tmp)
+  for (int e = tid; e < p * p; e += nt) tmp[e] = Q[e];
+  __syncthreads();
   for (int r = tid; r < p; r += nt) {
-    float row[kMaxP];
-    for (int q = 0; q < p; ++q) row[q] = Q[r * p + q];
+    float* row = tmp + r * p;
     for (int q = 0; q < p; ++q) {
-      float s = row[q];
-      for (int k = 0; k < q; ++k) s -= row[k] * G[q * p + k];
-      row[q] = s / G[q * p + q];
+      float acc = row[q];
+      for (int k = 0; k < q; ++k) acc -= row[k] * G[q * p + k];
+      row[q] = acc / G[q * p + q];
     }
-    for (int q = 0; q < p; ++q) Bout[r * p + q] = row[q];
   }
+  __syncthreads();
+  for (int e = tid; e < p * p; e += nt) Bout[e] = tmp[e];
   if (tid == 0 && fail_out) *fail_out = s_fail;
 }
 
