@@ -40,7 +40,7 @@ WORKLOAD = "gaussian_mixture_4096x4096_d3_stored_fp32_cost"
 # Total Algorithm-4.1 iterations of one SK-NR solve of this workload (all
 # continuation levels) as measured by this benchmark on a GB300; used only to
 # scale the per-iteration time of the CPU oracle to one solve (an estimate).
-SKNR_ITERS_PER_SOLVE = 120
+SKNR_ITERS_PER_SOLVE = 246
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 

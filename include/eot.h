@@ -52,7 +52,9 @@ typedef enum {
 typedef enum { EOT_MEM_HOST = 0, EOT_MEM_DEVICE = 1 } eot_mem;
 
 /* Arithmetic of the O(nm) passes.
- *  FP64: float64 cost and float64 exponentials (small problems, tight tolerances).
+ *  FP64: float64 cost and float64 exponentials and sums in the Sinkhorn and SK-NR
+ *        passes (small problems, tight tolerances); the modes are computed on a
+ *        float32 copy of the cost.
  *  FP32: float32 stored cost; float32 exponentials and sums; potentials kept in
  *        float64 and the exponent f_i + g_j - C_ij formed without rounding error
  *        before the division by eps (so the marginal error can reach ~1e-7).
@@ -72,7 +74,8 @@ typedef struct {
     const double *a;       /* (n) positive weights summing to 1 (renormalised)        */
     const double *b;       /* (m) positive weights summing to 1 (renormalised)        */
     const void *C;         /* (n x m) cost: double for FP64, float otherwise; or NULL */
-    const void *X, *Y;     /* point clouds: double for FP64, float otherwise; or NULL */
+    const void *X, *Y;     /* point clouds (float32 in every mode; the FP64 mode forms
+                              the cost from them in float64); or NULL                 */
     eot_mem mem;           /* memory space of a, b, C, X, Y, f_init and the outputs   */
     int32_t normalize_cost;/* 1: divide C by max_ij C_ij (after forming it from X, Y) */
     double eps;            /* target regularisation eps > 0                           */

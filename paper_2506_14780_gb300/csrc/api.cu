@@ -40,6 +40,11 @@ cudaError_t launch_col_pass(const Prob* dP, const Prob& hP, int mode, cudaStream
 cudaError_t launch_row_pass(const Prob* dP, const Prob& hP, int mode, cudaStream_t s);
 cudaError_t launch_split(const Prob* dP, const double* p, const double* logw, int len, Split so,
                          cudaStream_t s);
+cudaError_t launch_col64(const Prob* dP, const Prob& hP, int mode, const AccArgs& a,
+                         cudaStream_t s);
+cudaError_t launch_row64(const Prob* dP, const Prob& hP, int mode, cudaStream_t s);
+cudaError_t launch_shift64(const Prob* dP, const double* p, const double* logw, int len,
+                           double* out, cudaStream_t s);
 
 cudaError_t launch_colacc(const AccArgs& a, int ncolblk, cudaStream_t s);
 cudaError_t launch_rowacc(const AccArgs& a, int nrowblk, cudaStream_t s);
@@ -78,6 +83,9 @@ __global__ void weights_kernel(int, const double*, double*, double*, unsigned*, 
 __global__ void cost_stats_f64_kernel(size_t, const double*, unsigned long long*, unsigned*);
 __global__ void final_eval_kernel(const Prob*, double*, double*, double*);
 __global__ void normalize_buffers_kernel(Prob*);
+__global__ void cost_fill64_kernel(int, int, int, const float*, const float*,
+                                   const unsigned long long*, int, double*);
+__global__ void cost64_finish_kernel(size_t, double*, const unsigned long long*, int, float*);
 __global__ void reset_buffers_kernel(State*);
 
 constexpr int kGChunkHost = 64;
@@ -162,6 +170,7 @@ struct Solver {
   DeviceCtx* ctx = nullptr;
   int n = 0, m = 0, ell = 0, p = 0;
   bool own_cost = false;
+  bool f64 = false;           // float64 passes (EOT_PREC_FP64)
   // tilings
   int nstripe = 1, rows_per_stripe = 0, ncolblk = 0;
   int nseg = 1, cols_per_seg = 0, nrowblk = 0;
@@ -279,8 +288,24 @@ struct Solver {
     hP.cnt_col = A.take<unsigned>(ncolblk);
     hP.acc_col = A.take<double>((size_t)ncolblk * 4);
     hP.part_row = A.take<float2>((size_t)nseg * n);
-    hP.cnt_row = A.take<unsigned>(nrowblk);
-    hP.acc_row = A.take<double>((size_t)nrowblk * 4);
+    const int nrb = std::max(nrowblk, ceil_div(n, 8));
+    hP.cnt_row = A.take<unsigned>(nrb);
+    hP.acc_row = A.take<double>((size_t)nrb * 4);
+    hP.ncolblk64 = ceil_div(m, 128);
+    hP.nrowblk64 = ceil_div(n, 8);
+    if (f64) {
+      hP.C64 = A.take<double>((size_t)n * m);
+      for (int k = 0; k < 2; ++k) hP.fA64[k] = A.take<double>(n);
+      for (int k = 0; k < 3; ++k) hP.gA64[k] = A.take<double>(m);
+      hP.part64_col = A.take<double2>((size_t)nstripe * m);
+      hP.part64_row = A.take<double2>((size_t)nseg * n);
+    } else {
+      hP.C64 = nullptr;
+      for (int k = 0; k < 2; ++k) hP.fA64[k] = nullptr;
+      for (int k = 0; k < 3; ++k) hP.gA64[k] = nullptr;
+      hP.part64_col = nullptr;
+      hP.part64_row = nullptr;
+    }
     hP.gcnt = A.take<unsigned>(4);
     hP.out_plain = nullptr;
     hP.logratio_plain = nullptr;
@@ -324,8 +349,9 @@ struct Solver {
     }
   }
 
-  eot_status init(DeviceCtx* c, int n_, int m_, int d, int ell_, int p_, bool own) {
+  eot_status init(DeviceCtx* c, int n_, int m_, int d, int ell_, int p_, bool own, bool f64_) {
     ctx = c;
+    f64 = f64_;
     n = n_;
     m = m_;
     ell = ell_;
@@ -427,11 +453,27 @@ struct Solver {
   }
 
   // ---- loop bodies ----
+  cudaError_t pass_col(int mode, cudaStream_t s) {
+    return f64 ? launch_col64(dP, hP, mode, s4_args(), s) : launch_col_pass(dP, hP, mode, s);
+  }
+  cudaError_t pass_row(int mode, cudaStream_t s) {
+    return f64 ? launch_row64(dP, hP, mode, s) : launch_row_pass(dP, hP, mode, s);
+  }
+  // level-start derived arrays of buffer-0 potentials (float splits; float64
+  // eps-shifted copies in FP64 mode)
+  cudaError_t prep_level(cudaStream_t s) {
+    cudaError_t e = launch_split(dP, hP.f[0], hP.loga, n, hP.rs[0], s);
+    if (e == cudaSuccess) e = launch_split(dP, hP.g[0], hP.logb, m, hP.cs[0], s);
+    if (f64 && e == cudaSuccess) e = launch_shift64(dP, hP.f[0], hP.loga, n, hP.fA64[0], s);
+    if (f64 && e == cudaSuccess) e = launch_shift64(dP, hP.g[0], hP.logb, m, hP.gA64[0], s);
+    return e;
+  }
+
   cudaError_t body_sk(cudaStream_t s) {
     cudaError_t e = cudaSuccess;
     for (int u = 0; u < unroll_sk && e == cudaSuccess; ++u) {
-      e = launch_row_pass(dP, hP, MODE_SK_ROW, s);
-      if (e == cudaSuccess) e = launch_col_pass(dP, hP, MODE_SK_COL, s);
+      e = pass_row(MODE_SK_ROW, s);
+      if (e == cudaSuccess) e = pass_col(MODE_SK_COL, s);
     }
     return e;
   }
@@ -440,14 +482,15 @@ struct Solver {
     cudaError_t e = cudaSuccess;
     const AccArgs a = s4_args();
     for (int u = 0; u < unroll_sknr && e == cudaSuccess; ++u) {
-      e = launch_row_pass(dP, hP, MODE_SK_ROW, s);
-      if (e == cudaSuccess) e = launch_colmma(a, tilesV, mm_ncolblk, s);
+      e = pass_row(MODE_SK_ROW, s);
+      if (e == cudaSuccess)
+        e = f64 ? launch_col64(dP, hP, MODE_S4, a, s) : launch_colmma(a, tilesV, mm_ncolblk, s);
       if (e != cudaSuccess) break;
       e = launch_wtw_reduce(a, WtW, gw, s);
       if (e != cudaSuccess) break;
       newton_kernel<<<1, 32, 0, s>>>(dP, WtW, gw, nullptr);
       fprime_kernel<<<std::min(ceil_div(n, 256), 4 * ctx->nsm), 256, 0, s>>>(dP);
-      e = launch_col_pass(dP, hP, MODE_TRIAL, s);
+      e = pass_col(MODE_TRIAL, s);
     }
     return e;
   }
@@ -537,9 +580,10 @@ struct Solver {
 // Solver cache: repeated solves of one shape reuse buffers and graphs.
 // ---------------------------------------------------------------------------
 struct CacheKey {
-  int dev, n, m, d, ell, p, own;
+  int dev, n, m, d, ell, p, own, f64;
   bool operator<(const CacheKey& o) const {
-    return std::tie(dev, n, m, d, ell, p, own) < std::tie(o.dev, o.n, o.m, o.d, o.ell, o.p, o.own);
+    return std::tie(dev, n, m, d, ell, p, own, f64) <
+           std::tie(o.dev, o.n, o.m, o.d, o.ell, o.p, o.own, o.f64);
   }
 };
 static thread_local std::map<CacheKey, std::unique_ptr<Solver>> t_cache;
@@ -549,8 +593,8 @@ static int mode_block(int n, int ell, int oversample) {
 }
 
 static eot_status get_solver(DeviceCtx* ctx, int n, int m, int d, int ell, int p, bool own,
-                             Solver** out) {
-  CacheKey key{ctx->dev, n, m, d, ell, p, own ? 1 : 0};
+                             Solver** out, bool f64 = false) {
+  CacheKey key{ctx->dev, n, m, d, ell, p, own ? 1 : 0, f64 ? 1 : 0};
   auto it = t_cache.find(key);
   if (it != t_cache.end()) {
     *out = it->second.get();
@@ -558,7 +602,7 @@ static eot_status get_solver(DeviceCtx* ctx, int n, int m, int d, int ell, int p
   }
   if (t_cache.size() >= 4) t_cache.clear();
   auto s = std::make_unique<Solver>();
-  eot_status st = s->init(ctx, n, m, d, ell, p, own);
+  eot_status st = s->init(ctx, n, m, d, ell, p, own, f64);
   if (st != EOT_OK) return st;
   *out = s.get();
   t_cache[key] = std::move(s);
@@ -566,9 +610,11 @@ static eot_status get_solver(DeviceCtx* ctx, int n, int m, int d, int ell, int p
 }
 
 // Device bytes a solver of this shape allocates (admission control).
-static size_t solver_footprint(DeviceCtx* ctx, int n, int m, int d, int ell, int p) {
+static size_t solver_footprint(DeviceCtx* ctx, int n, int m, int d, int ell, int p,
+                               bool f64 = false) {
   Solver tmp;
   tmp.ctx = ctx;
+  tmp.f64 = f64;
   tmp.n = n;
   tmp.m = m;
   tmp.ell = ell;
@@ -615,8 +661,8 @@ static eot_status validate(const eot_problem* pr, const eot_options* o) {
   if (hasXY && pr->d < 1) return fail(EOT_EINVAL, "d must be >= 1 with point clouds");
   if (hasC && pr->d != 0) return fail(EOT_EINVAL, "d must be 0 when C is given");
   if (pr->mem != EOT_MEM_HOST && pr->mem != EOT_MEM_DEVICE) return fail(EOT_EINVAL, "bad mem");
-  if (o->prec != EOT_PREC_FP32)
-    return fail(EOT_EINVAL, "only EOT_PREC_FP32 is implemented in this build");
+  if (o->prec != EOT_PREC_FP32 && o->prec != EOT_PREC_FP64)
+    return fail(EOT_EINVAL, "EOT_PREC_SPLIT_TC is not implemented in this build");
   if (!(o->tol > 0.0)) return fail(EOT_EINVAL, "tol must be > 0");
   if (o->max_iter < 1) return fail(EOT_EINVAL, "max_iter must be >= 1");
   if (o->ell < 0 || o->ell > kMaxK) return fail(EOT_EINVAL, "ell must be in [0, 64]");
@@ -640,11 +686,12 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   if (cs != EOT_OK) return cs;
   const int n = pr->n, m = pr->m, d = pr->d;
   const bool dev = pr->mem == EOT_MEM_DEVICE;
-  const bool borrowC = dev && d == 0 && !pr->normalize_cost &&
+  const bool f64 = o->prec == EOT_PREC_FP64;
+  const bool borrowC = !f64 && dev && d == 0 && !pr->normalize_cost &&
                        (reinterpret_cast<uintptr_t>(pr->C) & 15u) == 0;
   Solver* S = nullptr;
   eot_status ss = get_solver(ctx, n, m, d, o->ell, mode_block(n, o->ell, o->oversample), !borrowC,
-                             &S);
+                             &S, f64);
   if (ss != EOT_OK) return ss;
   cudaStream_t s = o->stream ? reinterpret_cast<cudaStream_t>(o->stream) : ctx->stream;
   // the solver's graphs are captured on the context stream; user streams are
@@ -673,12 +720,26 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   const size_t nm = (size_t)n * m;
   const int gb = std::min<long long>(((long long)nm + 255) / 256, 8LL * ctx->nsm);
   const float* Cdev = nullptr;
+  double* C64 = const_cast<double*>(S->hP.C64);
   if (d > 0) {
     CUDA_TRY(cudaMemcpyAsync(S->X, pr->X, (size_t)n * d * sizeof(float), kin, s));
     CUDA_TRY(cudaMemcpyAsync(S->Y, pr->Y, (size_t)m * d * sizeof(float), kin, s));
     if (pr->normalize_cost) cost_max_kernel<<<gb, 256, 0, s>>>(n, m, d, S->X, S->Y, S->cmax64);
-    cost_fill_kernel<<<gb, 256, 0, s>>>(n, m, d, S->X, S->Y, S->cmax64, pr->normalize_cost,
-                                        S->Cbuf);
+    if (f64) {
+      cost_fill64_kernel<<<gb, 256, 0, s>>>(n, m, d, S->X, S->Y, S->cmax64, pr->normalize_cost,
+                                            C64);
+      cost64_finish_kernel<<<gb, 256, 0, s>>>(nm, C64, S->cmax64, 0, S->Cbuf);
+    } else {
+      cost_fill_kernel<<<gb, 256, 0, s>>>(n, m, d, S->X, S->Y, S->cmax64, pr->normalize_cost,
+                                          S->Cbuf);
+    }
+    Cdev = S->Cbuf;
+  } else if (f64) {
+    // float64 cost: optional normalisation by max |C| in float64, float32 copy
+    CUDA_TRY(cudaMemcpyAsync(C64, pr->C, nm * sizeof(double), kin, s));
+    if (pr->normalize_cost)
+      cost_stats_f64_kernel<<<gb, 256, 0, s>>>(nm, C64, S->cmax64, S->stats + 3);
+    cost64_finish_kernel<<<gb, 256, 0, s>>>(nm, C64, S->cmax64, pr->normalize_cost, S->Cbuf);
     Cdev = S->Cbuf;
   } else if (borrowC) {
     Cdev = reinterpret_cast<const float*>(pr->C);
@@ -695,7 +756,7 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   float cmaxf;
   std::memcpy(&cmaxf, &hstats[0], sizeof(float));
   double cmax = cmaxf;
-  if (d == 0 && pr->normalize_cost) {
+  if (d == 0 && pr->normalize_cost && !f64) {
     if (cmax > 0.0) {
       cost_scale_kernel<<<gb, 256, 0, s>>>(nm, Cdev, cmax, S->Cbuf);
       Cdev = S->Cbuf;
@@ -769,6 +830,7 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   std::vector<int> lev_nr(L, 0), lev_eig(L, 0);
   bool have_modes = false;
   int eig_iters_total = 0;
+  int resumed_iters = 0, resumed_acc = 0, resumed_rej = 0, resumed_bodies = 0, verify_rounds = 0;
   cudaEvent_t eig_ev0 = nullptr, eig_ev1 = nullptr;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> eig_events;
   const int body_cap_sk = std::max(4, o->max_iter / S->unroll_sk + 4);
@@ -776,16 +838,23 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   for (int t = 0; t < L; ++t) {
     const double eps = levels[t];
     const bool last = t == L - 1;
-    const double tol = (last || !(o->level_tol > 0.0)) ? o->tol : o->level_tol;
+    // Final-level margins (float32 passes only): the device test and the
+    // verification below evaluate the marginal ratios with float32
+    // exponentials and sums, whose error against a float64 evaluation is a
+    // small fraction of the tolerance (about 0.2% of 1e-6 on the tested
+    // problems).  The device aims at 0.97 tol and the returned pair must
+    // verify below 0.985 tol.
+    const double tol_verify = last ? (S->f64 ? o->tol : 0.985 * o->tol) : 0.0;
+    const double tol = last ? (S->f64 ? o->tol : 0.97 * o->tol)
+                            : (o->level_tol > 0.0 ? o->level_tol : o->tol);
     const bool use_nr = ell > 0 && have_modes;
     CUDA_TRY(cudaEventRecord(lev_ev[t], s));
     level_setup_kernel<<<1, 1, 0, s>>>(S->dP, eps, (float)(1.0 / (eps * std::log(2.0))), tol,
                                        o->max_iter, use_nr ? body_cap_nr : body_cap_sk);
     // split arrays of the carried potentials (they depend on eps through eps*log w)
     // cur_f / cur_g are 0 at the start of every level (see the copy kernels below)
-    CUDA_TRY(launch_split(S->dP, P.f[0], P.loga, n, P.rs[0], s));
-    CUDA_TRY(launch_split(S->dP, P.g[0], P.logb, m, P.cs[0], s));
-    CUDA_TRY(launch_col_pass(S->dP, P, MODE_G_INIT, s));
+    CUDA_TRY(S->prep_level(s));
+    CUDA_TRY(S->pass_col(MODE_G_INIT, s));
     if (use_nr) {
       // V^T D_a V and V^T a for this level's modes
       CUDA_TRY(S->wgram(S->V, S->V, P.a, 0, n, ell, P.a, S->V, S->gpart, S->gvpart, P.GV, P.Va, 0,
@@ -796,6 +865,33 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
     } else {
       eot_status e = S->run_loop(S->ex_sk, 0, body_cap_sk + 1);
       if (e != EOT_OK) return e;
+    }
+    if (last) {
+      // The device test uses the column term of the L1 marginal error (the row
+      // term is zero in exact arithmetic after the row half-step).  Verify both
+      // terms of the returned pair with the evaluation passes and, if their sum
+      // misses the tolerance because of float32 rounding in the row term,
+      // continue the level with the column threshold lowered accordingly.
+      for (int retry = 0; retry < 3; ++retry) {
+        CUDA_TRY(S->pass_row(MODE_EVAL, s));
+        CUDA_TRY(S->pass_col(MODE_EVAL, s));
+        CUDA_TRY(cudaMemcpyAsync(S->hSt, S->dSt, sizeof(State), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        ++verify_rounds;
+        const State hs = *S->hSt;
+        if (hs.done != 1 || hs.l1_row + hs.l1_col < tol_verify) break;
+        double tdev = 0.9 * (tol_verify - hs.l1_row);
+        if (!(tdev > 0.0)) tdev = 0.1 * tol_verify;
+        resumed_iters += hs.iter;
+        resumed_bodies += hs.body_runs;
+        resumed_acc += hs.nr_acc;
+        resumed_rej += hs.nr_rej;
+        level_setup_kernel<<<1, 1, 0, s>>>(S->dP, eps, (float)(1.0 / (eps * std::log(2.0))), tdev,
+                                           o->max_iter, use_nr ? body_cap_nr : body_cap_sk);
+        eot_status e = S->run_loop(use_nr ? S->ex_sknr : S->ex_sk, 0,
+                                   (use_nr ? body_cap_nr : body_cap_sk) + 1);
+        if (e != EOT_OK) return e;
+      }
     }
     CUDA_TRY(cudaMemcpyAsync(hLev + t, S->dSt, sizeof(State), cudaMemcpyDeviceToHost, s));
     lev_nr[t] = use_nr ? 1 : 0;
@@ -839,10 +935,9 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   }
   CUDA_TRY(cudaEventRecord(lev_ev[L], s));
   // ---- finish: evaluation passes at (f, g) = buffers 0, scores, gauge ----
-  CUDA_TRY(launch_split(S->dP, P.f[0], P.loga, n, P.rs[0], s));
-  CUDA_TRY(launch_split(S->dP, P.g[0], P.logb, m, P.cs[0], s));
-  CUDA_TRY(launch_row_pass(S->dP, P, MODE_EVAL, s));
-  CUDA_TRY(launch_col_pass(S->dP, P, MODE_EVAL, s));
+  CUDA_TRY(S->prep_level(s));
+  CUDA_TRY(S->pass_row(MODE_EVAL, s));
+  CUDA_TRY(S->pass_col(MODE_EVAL, s));
   final_eval_kernel<<<1, 256, 0, s>>>(S->dP, S->f_out, S->g_out, S->scores);
   const cudaMemcpyKind kout = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   CUDA_TRY(cudaMemcpyAsync(f_out, S->f_out, n * sizeof(double), kout, s));
@@ -874,10 +969,10 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   }
   float lm = 0.f;
   cudaEventElapsedTime(&lm, lev_ev[L - 1], lev_ev[L]);
-  r.iters = fin.iter;
-  r.total_iters = total;
-  r.nr_accepted = fin.nr_acc;
-  r.nr_rejected = fin.nr_rej;
+  r.iters = fin.iter + resumed_iters;
+  r.total_iters = total + resumed_iters;
+  r.nr_accepted = fin.nr_acc + resumed_acc;
+  r.nr_rejected = fin.nr_rej + resumed_rej;
   r.levels = L;
   eig_iters_total = 0;
   r.eig_iters = 0;
@@ -892,7 +987,9 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
       launches += 1 + 3 + 1 + 1 + 1 + (long long)hLev[L + t].body_runs * 12 + 1;
     }
   }
-  launches += 5;
+  launches += 5 + 2LL * verify_rounds;
+  launches += (long long)resumed_bodies * (lev_nr[L - 1] ? 6 * S->unroll_sknr + 1 : 2 * S->unroll_sk + 1);
+  launches += (verify_rounds > 1 ? (long long)(verify_rounds - 1) : 0);   // level set-up per resume
   r.kernel_launches = launches;
   r.row_l1 = S->hScores[0];
   r.col_l1 = S->hScores[1];
@@ -1208,10 +1305,9 @@ eot_status eot_marginal_error(int32_t n, int32_t m, const float* C, const double
   State st0{};
   CUDA_TRY(cudaMemcpyAsync(S->dSt, &st0, sizeof(State), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(S->dP, &P, sizeof(Prob), cudaMemcpyHostToDevice, s));
-  CUDA_TRY(launch_split(S->dP, P.f[0], P.loga, n, P.rs[0], s));
-  CUDA_TRY(launch_split(S->dP, P.g[0], P.logb, m, P.cs[0], s));
-  CUDA_TRY(launch_row_pass(S->dP, P, MODE_EVAL, s));
-  CUDA_TRY(launch_col_pass(S->dP, P, MODE_EVAL, s));
+  CUDA_TRY(S->prep_level(s));
+  CUDA_TRY(S->pass_row(MODE_EVAL, s));
+  CUDA_TRY(S->pass_col(MODE_EVAL, s));
   final_eval_kernel<<<1, 256, 0, s>>>(S->dP, S->f_out, S->g_out, S->scores);
   CUDA_TRY(cudaMemcpyAsync(S->hScores, S->scores, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
   st = standalone_finish(s, stream);
@@ -1514,7 +1610,8 @@ eot_status eot_server_submit(eot_server* srv, const eot_problem* prob, uint64_t 
   eot_status cs = eotk::get_ctx(&ctx);
   if (cs != EOT_OK) return cs;
   r->footprint = eotk::solver_footprint(ctx, n, m, d, srv->opt.ell,
-                                        eotk::mode_block(n, srv->opt.ell, srv->opt.oversample));
+                                        eotk::mode_block(n, srv->opt.ell, srv->opt.oversample),
+                                        srv->opt.prec == EOT_PREC_FP64);
   {
     std::lock_guard<std::mutex> lk(srv->mu);
     r->ticket = srv->next++;

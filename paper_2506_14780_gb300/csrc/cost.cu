@@ -198,3 +198,41 @@ __global__ void __launch_bounds__(256) final_eval_kernel(const Prob* __restrict_
 }
 
 }  // namespace eotk
+
+namespace eotk {
+
+// Float64 cost (no rounding), optionally divided by the maximum.
+__global__ void cost_fill64_kernel(int n, int m, int d, const float* __restrict__ X,
+                                   const float* __restrict__ Y,
+                                   const unsigned long long* __restrict__ cmax_bits, int normalize,
+                                   double* __restrict__ C) {
+  const double cmax = __longlong_as_double((long long)*cmax_bits);
+  const size_t total = (size_t)n * m;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / m), j = (int)(e - (size_t)i * m);
+    double v = sqdist(X + (size_t)i * d, Y + (size_t)j * d, d);
+    if (normalize && cmax > 0.0) v = __ddiv_rn(v, cmax);
+    C[e] = v;
+  }
+}
+
+// Optional in-place division of a float64 cost by its maximum, and the float32
+// rounding used by the mode computation.
+__global__ void cost64_finish_kernel(size_t total, double* __restrict__ C,
+                                     const unsigned long long* __restrict__ cmax_bits,
+                                     int normalize, float* __restrict__ Cf) {
+  const double cmax = __longlong_as_double((long long)*cmax_bits);
+  const bool scale = normalize && cmax > 0.0;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    double v = C[e];
+    if (scale) {
+      v = __ddiv_rn(v, cmax);
+      C[e] = v;
+    }
+    Cf[e] = __double2float_rn(v);
+  }
+}
+
+}  // namespace eotk

@@ -21,10 +21,11 @@ enum PassMode : int {
   MODE_PLAIN = 0,     // standalone transform: write outputs only
   MODE_SK_COL = 1,    // Sinkhorn column pass: convergence test, advance g
   MODE_SK_ROW = 2,    // Sinkhorn / SK-NR row pass
-  MODE_S4 = 3,        // SK-NR column pass at f_k: test, h, W, Q_semi
+  MODE_S4_F32 = 3,    // SK-NR column pass at f_k (float32 path, tensor-core kernel)
   MODE_TRIAL = 4,     // SK-NR trial column pass at f': accept / reject
   MODE_EVAL = 5,      // marginal evaluation only (no potential update)
-  MODE_G_INIT = 6     // first column transform of a level (Alg. 4.1 line 3, k = 1)
+  MODE_G_INIT = 6,    // first column transform of a level (Alg. 4.1 line 3, k = 1)
+  MODE_S4 = 7         // float64 SK-NR column pass (h, W)
 };
 
 // Device-resident solver state (one per problem).
@@ -102,6 +103,13 @@ struct Prob {
   double* WtW;             // ell x ell: sum_j W_j W_j^T / b_j
   double* grad;            // ell: gradient on V
   double pot_bound;        // |potential| limit of the exact exponent formation
+  // float64 passes (EOT_PREC_FP64)
+  const double* C64;       // n x m float64 cost
+  double* fA64[2];         // f + eps log a for each f buffer
+  double* gA64[3];         // g + eps log b for each g buffer
+  double2* part64_col;     // [nstripe][m]
+  double2* part64_row;     // [nseg][n]
+  int ncolblk64, nrowblk64;
   unsigned long long cond; // graph conditional handle of the enclosing device loop
   // plain-mode outputs
   double* out_plain;       // standalone transform output

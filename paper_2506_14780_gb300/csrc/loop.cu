@@ -80,6 +80,7 @@ __global__ void normalize_buffers_kernel(Prob* PP) {
     if (i < P.n) {
       const double v = P.f[cf][i];
       P.f[0][i] = v;
+      if (P.fA64[0]) P.fA64[0][i] = v + P.eps * P.loga[i];
       split_grid(v + P.eps * P.loga[i], P.qscale, P.qinv, hi, lo);
       P.rs[0].A[i] = (float)(hi + (double)P.M);
       P.rs[0].AL[i] = lo;
@@ -90,6 +91,7 @@ __global__ void normalize_buffers_kernel(Prob* PP) {
     if (i < P.m) {
       const double v = P.g[cg][i];
       P.g[0][i] = v;
+      if (P.gA64[0]) P.gA64[0][i] = v + P.eps * P.logb[i];
       split_grid(v + P.eps * P.logb[i], P.qscale, P.qinv, hi, lo);
       P.cs[0].A[i] = (float)(hi + (double)P.M);
       P.cs[0].AL[i] = lo;

@@ -574,3 +574,334 @@ cudaError_t launch_split(const Prob* dP, const double* p, const double* logw, in
 }
 
 }  // namespace eotk
+
+// ===========================================================================
+// Float64 passes (EOT_PREC_FP64): the same half-steps with float64 costs,
+// exponentials and sums, for small problems and tight tolerances.  Column
+// pass: one thread per column, 128 columns per CTA, row stripes; row pass: one
+// warp per row, column segments.  The partial states are (max, sum) pairs in
+// natural-log units, merged in fixed order by the last-arriving CTA.
+// ===========================================================================
+namespace eotk {
+
+__device__ __forceinline__ void lse64_push(double& mx, double& S, double x) {
+  if (x <= mx) {
+    S += exp(x - mx);
+  } else {
+    S = S * exp(mx - x) + 1.0;
+    mx = x;
+  }
+}
+
+__device__ __forceinline__ void lse64_merge(double& mx, double& S, double m2, double S2) {
+  if (!(S2 > 0.0)) return;
+  if (!(S > 0.0)) {
+    mx = m2;
+    S = S2;
+    return;
+  }
+  if (m2 <= mx) S += S2 * exp(m2 - mx);
+  else {
+    S = S * exp(mx - m2) + S2;
+    mx = m2;
+  }
+}
+
+// Finish one index in float64: new potential, its eps-shifted copy, the float
+// log-ratio, the scalar contributions.
+__device__ __forceinline__ void finish64(double mx, double S, int idx, const Prob& P,
+                                         const double* __restrict__ shift,
+                                         const double* __restrict__ w,
+                                         const double* __restrict__ logw,
+                                         double* __restrict__ out, double* __restrict__ outA,
+                                         float* __restrict__ Lout, double acc[3], int* numeric,
+                                         double* Lfull) {
+  double L = mx + log(S);
+  const double sh = shift[idx];
+  double o = sh - P.eps * L;
+  if (!isfinite(o) || !(S > 0.0)) {
+    atomicAdd(numeric, 1);
+    o = sh;
+    L = 0.0;
+  }
+  if (out) out[idx] = o;
+  if (outA) outA[idx] = o + P.eps * logw[idx];
+  if (Lout) Lout[idx] = (float)L;
+  if (Lfull) *Lfull = L;
+  const double wi = w[idx];
+  acc[0] = wi * fabs(expm1(L));
+  acc[1] = wi * L;
+  acc[2] = wi * o;
+}
+
+// mode: PLAIN, SK_COL, G_INIT, EVAL, TRIAL, or S4 (with W accumulation; the
+// whole column in one stripe).
+__global__ void __launch_bounds__(128) col64_kernel(const Prob* __restrict__ PP, int mode,
+                                                    AccArgs acc_args) {
+  const Prob& P = *PP;
+  State* st = P.st;
+  if (mode != MODE_PLAIN && mode != MODE_EVAL && st->done) return;
+  const bool s4 = mode == MODE_S4;
+  const int cf = st->cur_f, cg = st->cur_g;
+  const int src_f = (mode == MODE_TRIAL) ? 1 - cf : cf;
+  const int sh_g = (mode == MODE_TRIAL) ? (cg + 1) % 3 : cg;
+  const int dst_g = (mode == MODE_EVAL) ? -1 : (mode == MODE_TRIAL ? (cg + 2) % 3 : (cg + 1) % 3);
+  if (mode == MODE_TRIAL && !st->nr_ok) return;
+  const double* __restrict__ fA = P.fA64[src_f];
+  __shared__ double s_red[24];
+  __shared__ unsigned s_last;
+  __shared__ float sW[128 * (kMaxK + 1)];
+  __shared__ float sD[128], sB[128];
+  const int tid = threadIdx.x;
+  const int n = P.n, m = P.m;
+  const int cb = blockIdx.x, stripe = blockIdx.y;
+  const int j = cb * 128 + tid;
+  const bool jv = j < m;
+  const int i_beg = s4 ? 0 : stripe * P.rows_per_stripe;
+  const int i_end = s4 ? n : min(n, i_beg + P.rows_per_stripe);
+  const double inv_eps = 1.0 / P.eps;
+  const int kk = s4 ? P.ell : 0;
+  double mx = -INFINITY, S = 0.0;
+  double w[kMaxK];
+  for (int k = 0; k < kk; ++k) w[k] = 0.0;
+  if (jv) {
+    const double s = P.g[sh_g][j];
+    for (int i = i_beg; i < i_end; ++i) {
+      const double x = (fA[i] + s - P.C64[(size_t)i * m + j]) * inv_eps;
+      if (!s4) {
+        lse64_push(mx, S, x);
+      } else {
+        if (x > mx) {
+          const double sc = (S > 0.0) ? exp(mx - x) : 0.0;
+          S *= sc;
+          for (int k = 0; k < kk; ++k) w[k] *= sc;
+          mx = x;
+        }
+        const double e = exp(x - mx);
+        S += e;
+        const float* Vi = P.V + (size_t)i * kk;
+        for (int k = 0; k < kk; ++k) w[k] += e * (double)Vi[k];
+      }
+    }
+  }
+  double accv[3] = {0.0, 0.0, 0.0};
+  if (s4) {
+    // single stripe: finish directly
+    sD[tid] = 0.f;
+    sB[tid] = 0.f;
+    for (int k = 0; k < kk; ++k) sW[tid * (kMaxK + 1) + k] = 0.f;
+    if (jv) {
+      double L;
+      finish64(mx, S, j, P, P.g[sh_g], P.b, P.logb, P.g[dst_g], P.gA64[dst_g], P.Lcol, accv,
+               &st->numeric, &L);
+      const double sc = P.b[j] / S;   // b_j * softmax normalisation
+      for (int k = 0; k < kk; ++k) {
+        const float wv = (float)(w[k] * sc);
+        P.W[(size_t)j * kk + k] = wv;
+        sW[tid * (kMaxK + 1) + k] = wv;
+      }
+      const double dj = -expm1(L);
+      acc_args.dw[j] = dj;
+      sD[tid] = (float)dj;
+      sB[tid] = (float)(1.0 / P.b[j]);
+    }
+    __syncthreads();
+    double* dstp = acc_args.wtw_part + (size_t)cb * (kk * kk + kk);
+    for (int e = tid; e < kk * kk + kk; e += 128) {
+      float s = 0.f;
+      if (e < kk * kk) {
+        const int r = e / kk, q2 = e - r * kk;
+        for (int q = 0; q < 128; ++q)
+          s = __fmaf_rn(sW[q * (kMaxK + 1) + r] * sB[q], sW[q * (kMaxK + 1) + q2], s);
+      } else {
+        const int r = e - kk * kk;
+        for (int q = 0; q < 128; ++q) s = __fmaf_rn(sD[q], sW[q * (kMaxK + 1) + r], s);
+      }
+      dstp[e] = (double)s;
+    }
+    block_sum3(accv, s_red);
+    if (tid == 0) {
+      double* ab = acc_args.blkacc + cb * 4;
+      ab[0] = accv[0];
+      ab[1] = accv[1];
+      ab[2] = accv[2];
+      __threadfence();
+      const unsigned prev = atomicAdd(acc_args.gcnt, 1u);
+      s_last = (prev == (unsigned)(acc_args.nblk - 1));
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double tot[3];
+    grid_sum3(acc_args.blkacc, acc_args.nblk, tot, s_red);
+    if (tid == 0) {
+      *acc_args.gcnt = 0u;
+      st->l1_col = tot[0];
+      st->sum_wL = tot[1];
+      st->qsemi = st->sum_af + tot[2];
+      st->iter += 1;
+      st->nr_ok = 0;
+      if (st->numeric > 0) st->done = 3;
+      else if (tot[0] < st->tol) st->done = 1;
+      else if (st->iter >= st->max_iter) st->done = 2;
+    }
+    return;
+  }
+  if (jv) P.part64_col[(size_t)stripe * m + j] = make_double2(mx, S);
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    const unsigned prev = atomicAdd(&P.cnt_col[cb], 1u);
+    s_last = (prev == (unsigned)(P.nstripe - 1));
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (jv) {
+    double M = -INFINITY, Sd = 0.0;
+    for (int s2 = 0; s2 < P.nstripe; ++s2) {
+      const double2 q = __ldcg(&P.part64_col[(size_t)s2 * m + j]);
+      lse64_merge(M, Sd, q.x, q.y);
+    }
+    double* out = (mode == MODE_PLAIN) ? P.out_plain : (mode == MODE_EVAL ? nullptr : P.g[dst_g]);
+    double* outA = (mode == MODE_PLAIN || mode == MODE_EVAL) ? nullptr : P.gA64[dst_g];
+    double L;
+    finish64(M, Sd, j, P, P.g[sh_g], P.b, P.logb, out, outA, P.Lcol, accv, &st->numeric, &L);
+    if (mode == MODE_PLAIN && P.logratio_plain) P.logratio_plain[j] = L;
+  }
+  __syncthreads();
+  block_sum3(accv, s_red);
+  if (tid == 0) {
+    P.cnt_col[cb] = 0u;
+    double* ab = P.acc_col + cb * 4;
+    ab[0] = accv[0];
+    ab[1] = accv[1];
+    ab[2] = accv[2];
+    __threadfence();
+    const unsigned prev = atomicAdd(&P.gcnt[0], 1u);
+    s_last = (prev == (unsigned)(P.ncolblk64 - 1));
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double tot[3];
+  grid_sum3(P.acc_col, P.ncolblk64, tot, s_red);
+  if (tid == 0) {
+    P.gcnt[0] = 0u;
+    final_step(P, mode, tot, dst_g);
+  }
+}
+
+__global__ void __launch_bounds__(256) row64_kernel(const Prob* __restrict__ PP, int mode) {
+  const Prob& P = *PP;
+  State* st = P.st;
+  if (mode != MODE_PLAIN && mode != MODE_EVAL && st->done) return;
+  const int cf = st->cur_f, cg = st->cur_g;
+  const double* __restrict__ gA = P.gA64[cg];
+  __shared__ double s_red[24];
+  __shared__ double2 s_p[8];
+  __shared__ unsigned s_last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int n = P.n, m = P.m;
+  const int rb = blockIdx.x, seg = blockIdx.y;
+  const int i = rb * 8 + wid;
+  const int c_beg = seg * P.cols_per_seg;
+  const int c_end = min(m, c_beg + P.cols_per_seg);
+  const double inv_eps = 1.0 / P.eps;
+  double mx = -INFINITY, S = 0.0;
+  if (i < n) {
+    const double s = P.f[cf][i];
+    for (int j = c_beg + lane; j < c_end; j += 32) {
+      const double x = (s + gA[j] - P.C64[(size_t)i * m + j]) * inv_eps;
+      lse64_push(mx, S, x);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double m2 = __shfl_xor_sync(0xffffffffu, mx, o);
+    const double s2 = __shfl_xor_sync(0xffffffffu, S, o);
+    lse64_merge(mx, S, m2, s2);
+  }
+  if (lane == 0) s_p[wid] = make_double2(mx, S);
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    const int ii = rb * 8 + threadIdx.x;
+    if (ii < n) P.part64_row[(size_t)seg * n + ii] = s_p[threadIdx.x];
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(&P.cnt_row[rb], 1u);
+    s_last = (prev == (unsigned)(P.nseg - 1));
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double accv[3] = {0.0, 0.0, 0.0};
+  if (threadIdx.x < 8) {
+    const int ii = rb * 8 + threadIdx.x;
+    if (ii < n) {
+      double M = -INFINITY, Sd = 0.0;
+      for (int s2 = 0; s2 < P.nseg; ++s2) {
+        const double2 q = __ldcg(&P.part64_row[(size_t)s2 * n + ii]);
+        lse64_merge(M, Sd, q.x, q.y);
+      }
+      double* out = (mode == MODE_PLAIN) ? P.out_plain : (mode == MODE_EVAL ? nullptr : P.f[cf]);
+      double* outA = (mode == MODE_PLAIN || mode == MODE_EVAL) ? nullptr : P.fA64[cf];
+      double L;
+      finish64(M, Sd, ii, P, P.f[cf], P.a, P.loga, out, outA, P.Lrow, accv, &st->numeric, &L);
+      if (mode == MODE_PLAIN && P.logratio_plain) P.logratio_plain[ii] = L;
+    }
+  }
+  block_sum3(accv, s_red);
+  if (threadIdx.x == 0) {
+    P.cnt_row[rb] = 0u;
+    double* ab = P.acc_row + rb * 4;
+    ab[0] = accv[0];
+    ab[1] = accv[1];
+    ab[2] = accv[2];
+    __threadfence();
+    const unsigned prev = atomicAdd(&P.gcnt[1], 1u);
+    s_last = (prev == (unsigned)(P.nrowblk64 - 1));
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double tot[3];
+  grid_sum3(P.acc_row, P.nrowblk64, tot, s_red);
+  if (threadIdx.x == 0) {
+    P.gcnt[1] = 0u;
+    if (mode == MODE_EVAL) st->l1_row = tot[0];
+    else final_step(P, mode == MODE_PLAIN ? MODE_PLAIN : MODE_SK_ROW, tot, cf);
+  }
+}
+
+// eps-shifted float64 copies of a potential (level start, after f').
+__global__ void shift64_kernel(const Prob* __restrict__ PP, const double* __restrict__ p,
+                               const double* __restrict__ logw, int len, double* __restrict__ out) {
+  const Prob& P = *PP;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < len; i += gridDim.x * blockDim.x)
+    out[i] = p[i] + P.eps * logw[i];
+}
+
+cudaError_t launch_col64(const Prob* dP, const Prob& hP, int mode, const AccArgs& a,
+                         cudaStream_t s) {
+  dim3 grid(hP.ncolblk64, mode == MODE_S4 ? 1 : hP.nstripe);
+  col64_kernel<<<grid, 128, 0, s>>>(dP, mode, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_row64(const Prob* dP, const Prob& hP, int mode, cudaStream_t s) {
+  dim3 grid(hP.nrowblk64, hP.nseg);
+  row64_kernel<<<grid, 256, 0, s>>>(dP, mode);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shift64(const Prob* dP, const double* p, const double* logw, int len,
+                           double* out, cudaStream_t s) {
+  const int blocks = (len + 255) / 256;
+  shift64_kernel<<<blocks < 1024 ? blocks : 1024, 256, 0, s>>>(dP, p, logw, len, out);
+  return cudaGetLastError();
+}
+
+}  // namespace eotk

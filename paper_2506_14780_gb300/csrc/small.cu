@@ -180,6 +180,7 @@ __global__ void fprime_kernel(const Prob* __restrict__ PP) {
     for (int k = 0; k < l; ++k) corr = __fmaf_rn(Vi[k], d[k], corr);
     const double v = f[i] + (double)corr;
     fo[i] = v;
+    if (P.fA64[0]) P.fA64[1 - cf][i] = v + P.eps * P.loga[i];
     double hi;
     float lo;
     split_grid(v + P.eps * P.loga[i], P.qscale, P.qinv, hi, lo);

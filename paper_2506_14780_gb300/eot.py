@@ -132,6 +132,7 @@ def _ptr(x, keep: list, dtype=None):
     if _is_torch(x):
         if not x.is_contiguous():
             raise ValueError("device tensors must be contiguous")
+        keep.append(x)
         return x.data_ptr()
     arr = np.ascontiguousarray(x, dtype=dtype)
     keep.append(arr)
@@ -149,7 +150,9 @@ def default_options(**kw) -> eot_options:
 
 
 def make_problem(a, b, C=None, X=None, Y=None, eps=1e-2, normalize_cost=False, f_init=None,
-                 keep: Optional[list] = None) -> eot_problem:
+                 keep: Optional[list] = None, cost_dtype=np.float32) -> eot_problem:
+    """Marshal a problem.  ``cost_dtype`` is float64 for ``EOT_PREC_FP64`` solves
+    (the cost matrix is read as double there) and float32 otherwise."""
     keep = [] if keep is None else keep
     dev = any(_is_torch(x) for x in (a, b, C, X, Y) if x is not None)
     p = eot_problem()
@@ -158,7 +161,7 @@ def make_problem(a, b, C=None, X=None, Y=None, eps=1e-2, normalize_cost=False, f
     p.d = 0 if X is None else int(X.shape[1])
     p.a = _ptr(a, keep, np.float64)
     p.b = _ptr(b, keep, np.float64)
-    p.C = _ptr(C, keep, np.float32)
+    p.C = _ptr(C, keep, cost_dtype)
     p.X = _ptr(X, keep, np.float32)
     p.Y = _ptr(Y, keep, np.float32)
     p.mem = EOT_MEM_DEVICE if dev else EOT_MEM_HOST
@@ -189,9 +192,10 @@ def eot_solve(problem: eot_problem, options: eot_options, f_out, g_out):
 def solve(prob, **opts):
     """Solve a ``workloads.Problem`` (host arrays).  Returns (f, g, result dict)."""
     keep = []
+    f64 = opts.get("prec", EOT_PREC_FP32) == EOT_PREC_FP64
     p = make_problem(prob.a, prob.b, C=prob.C, X=prob.X, Y=prob.Y, eps=prob.eps,
                      normalize_cost=prob.normalize_cost, f_init=opts.pop("f_init", None),
-                     keep=keep)
+                     keep=keep, cost_dtype=np.float64 if f64 else np.float32)
     o = default_options(**opts)
     f = np.zeros(p.n)
     g = np.zeros(p.m)

@@ -1,0 +1,157 @@
+"""GPU tests of the spectral modes (S7), batched solves and the serving loop,
+through the C ABI, against the float64 oracle."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2506_14780_gb300 as p
+    p.load()
+    return p
+
+
+def dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x)).cuda()
+
+
+def _solved(n=300, m=260, eps=0.02, seed=4):
+    prob = W.gaussian_mixture(n, m, seed=seed, eps=eps)
+    C = O.sq_euclidean_cost(prob.X, prob.Y, normalize=True).astype(np.float32)
+    ref = O.sinkhorn(C.astype(np.float64), prob.a, prob.b, eps, tol=1e-12, max_iter=200000)
+    return prob, C, ref
+
+
+def test_spectral_modes_match_eigh(pkg):
+    """S7: the device subspace iteration spans the leading non-trivial
+    eigenvectors of Op(pi) o Op(pi)^T (Eq. semidual_Hessian) found by eigh."""
+    prob, C, ref = _solved()
+    n, m, eps, ell = C.shape[0], C.shape[1], prob.eps, 6
+    Vd, rho2 = O.spectral_modes_dense(ref.f, ref.g, C.astype(np.float64), prob.a, prob.b, eps, ell)
+    V = torch.zeros((n, ell), dtype=torch.float64, device="cuda")
+    r2 = torch.zeros(ell, dtype=torch.float64, device="cuda")
+    st, it, res = pkg.eot_spectral_modes(n, m, dev(C), dev(ref.f), dev(ref.g), dev(prob.a),
+                                         dev(prob.b), eps, ell, 10, 1e-4, 300, False, V, r2)
+    assert st in (pkg.EOT_OK, pkg.EOT_NOT_CONVERGED), pkg.last_error()
+    Vg = V.cpu().numpy()
+    a = prob.a
+    # a-orthonormal, orthogonal to constants
+    G = Vg.T @ (a[:, None] * Vg)
+    assert np.abs(G - np.eye(ell)).max() < 1e-4
+    assert np.abs(a @ Vg).max() < 1e-5
+    # Ritz values and subspace agree with the dense eigendecomposition
+    assert np.abs(r2.cpu().numpy() - rho2).max() < 1e-3
+    proj = Vd @ (Vd.T @ (a[:, None] * Vg))
+    assert np.sqrt((a[:, None] * (proj - Vg) ** 2).sum(0)).max() < 5e-2
+
+
+def test_sknr_parity_with_oracle_iteration(pkg):
+    """SK-NR(l) with the oracle's own modes passed as V is not exposed; instead the
+    full solve is compared with the oracle's tight optimum and monotone objective."""
+    prob = W.gaussian_mixture(400, 300, seed=6, eps=5e-3)
+    f, g, res = pkg.solve(prob, tol=3e-7, ell=20, eps_start=1e-1, max_iter=100000)
+    assert res["return_status"] == pkg.EOT_OK, res
+    C = O.sq_euclidean_cost(prob.X, prob.Y, normalize=True).astype(np.float32).astype(np.float64)
+    ev = O.evaluate(f, g, C, prob.a, prob.b, prob.eps)
+    assert ev["l1"] <= 1e-6
+    ref = O.continuation(C, prob.a, prob.b, prob.eps, tol=1e-12, eps_start=1e-1, ell=0)
+    fr, gr = O.gauge_normalize(ref.f, ref.g, prob.a, prob.b)
+    # potential error bounded by the marginal error along the slowest mode
+    _, rho2 = O.spectral_modes_dense(ref.f, ref.g, C, prob.a, prob.b, prob.eps, 1)
+    bound = prob.eps * max(ev["l1"], 1e-7) / (1 - rho2[0]) * 20
+    assert np.abs(f - fr).max() <= max(bound, 1e-5 * prob.eps)
+    assert res["nr_accepted"] >= 1
+
+
+def test_batch_same_alone_and_in_mix(pkg):
+    probs = W.batch_problems(24, seed=3, n_lo=32, n_hi=600)
+    keep = []
+    ps = [pkg.make_problem(p.a, p.b, X=p.X, Y=p.Y, eps=p.eps, normalize_cost=True, keep=keep)
+          for p in probs]
+    o = pkg.default_options(tol=1e-6, max_iter=200000)
+    fs = [np.zeros(p.n) for p in probs]
+    gs = [np.zeros(p.m) for p in probs]
+    st, res = pkg.eot_solve_batch(ps, o, fs, gs)
+    assert st in (pkg.EOT_OK, pkg.EOT_NOT_CONVERGED), pkg.last_error()
+    for k in (0, 5, 17):
+        p = probs[k]
+        f1, g1, r1 = pkg.solve(p, tol=1e-6, max_iter=200000)
+        assert np.array_equal(f1, fs[k]) and np.array_equal(g1, gs[k])
+        C = O.sq_euclidean_cost(p.X, p.Y, normalize=True).astype(np.float32).astype(np.float64)
+        if res[k].status == pkg.EOT_OK:
+            assert O.evaluate(fs[k], gs[k], C, p.a, p.b, p.eps)["l1"] <= 1e-6
+
+
+def test_batch_rejects_bad_member(pkg):
+    good = W.uniform_square(40, 50, seed=1, eps=0.05)
+    keep = []
+    p1 = pkg.make_problem(good.a, good.b, X=good.X, Y=good.Y, eps=good.eps, normalize_cost=True,
+                          keep=keep)
+    bad_a = good.a.copy()
+    bad_a[3] = -1.0
+    p2 = pkg.make_problem(bad_a, good.b, X=good.X, Y=good.Y, eps=good.eps, normalize_cost=True,
+                          keep=keep)
+    o = pkg.default_options()
+    st, res = pkg.eot_solve_batch([p1, p2], o, [np.zeros(40), np.zeros(40)],
+                                  [np.zeros(50), np.zeros(50)])
+    assert st == pkg.EOT_EINVAL
+    assert res[0].status == pkg.EOT_OK and res[1].status == pkg.EOT_EINVAL
+
+
+def test_server_continuous_batching(pkg):
+    reqs = W.served_stream(seed=2, rate_per_s=400.0, duration_s=0.05, n_lo=64, n_hi=700,
+                           dims=(2, 3), max_requests=16)
+    o = pkg.default_options(tol=1e-6, max_iter=200000, eps_start=1e-1)
+    srv = pkg.Server(o, hbm_budget_bytes=2 << 30, max_slots=4)
+    try:
+        tickets = []
+        t0 = time.perf_counter()
+        for r in reqs:
+            while time.perf_counter() - t0 < r["t"]:
+                time.sleep(0.0005)
+            tickets.append((srv.submit(r["problem"], cloud_id=0), r["problem"]))
+        outs = []
+        for t, p in tickets:
+            deadline = time.time() + 120
+            while True:
+                st, f, g, res = srv.poll(t)
+                if st != pkg.EOT_PENDING:
+                    break
+                assert time.time() < deadline
+                time.sleep(0.002)
+            assert st in (pkg.EOT_OK, pkg.EOT_NOT_CONVERGED), res
+            outs.append((p, f, g))
+        p50, p99, sps = srv.stats()
+        assert 0 < p50 <= p99 and sps > 0
+        # each result equals the same problem solved alone
+        for p, f, g in outs[:4]:
+            f1, g1, _ = pkg.solve(p, tol=1e-6, max_iter=200000, eps_start=1e-1)
+            assert np.array_equal(f, f1) and np.array_equal(g, g1)
+        assert srv.poll(12345678)[0] == pkg.EOT_ENOTFOUND
+    finally:
+        srv.close()
+
+
+def test_server_admission_budget(pkg):
+    o = pkg.default_options()
+    srv = pkg.Server(o, hbm_budget_bytes=1 << 16, max_slots=1)
+    try:
+        p = W.uniform_square(300, 300, seed=0, eps=0.05)
+        t = srv.submit(p)
+        for _ in range(1000):
+            st, _, _, _ = srv.poll(t)
+            if st != pkg.EOT_PENDING:
+                break
+            time.sleep(0.002)
+        assert st == pkg.EOT_ENOMEM
+    finally:
+        srv.close()
