@@ -57,6 +57,9 @@ cudaError_t launch_build_tiles(const float* Z, int n, int kk, float* tiles, cuda
 int mma_record(int k);
 size_t mma_tiles_floats(int n, int k);
 void init_mma_attributes();
+void init_stream_attributes();
+int stream_ctas_per_sm();
+void stream_plan(int n, int m, bool col, int ctas, int* grid, int* slots);
 
 __global__ void wgram_partial_kernel(const float*, const float*, const double*, int, int, int,
                                      const double*, const float*, double*, double*, const State*,
@@ -119,6 +122,7 @@ struct DeviceCtx {
   int nsm = 0;
   cudaStream_t stream = nullptr;
   bool cond_ok = true;   // graph conditional nodes usable
+  int stream_ctas = 0;   // CTAs of one wave of the staged stream passes
 };
 
 // One context (and stream) per calling thread and device, so that solves issued
@@ -139,6 +143,8 @@ static eot_status get_ctx(DeviceCtx** out) {
   CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
   init_acc_attributes();
   init_mma_attributes();
+  init_stream_attributes();
+  c->stream_ctas = stream_ctas_per_sm() * c->nsm;
   const char* e = getenv("EOT_HOST_LOOP");
   c->cond_ok = !(e && e[0] == '1');
   *out = c.get();
@@ -177,6 +183,7 @@ struct Solver {
   int s4_nseg = 1, s4_seglen = 0, s4_ncolblk = 0, s4_K = 0;
   int ek_K = 0, kc_nseg = 1, kc_seglen = 0, kr_nseg = 1, kr_seglen = 0, kr_nrowblk = 0;
   int mm_ncolblk = 0, mm_nseg = 1, mm_seglen = 0;   // tensor-core column products
+  int sk_gcol = 0, sk_grow = 0, sk_slots_col = 1, sk_slots_row = 1;   // stream passes
   // memory
   void* mem = nullptr;
   size_t bytes = 0;
@@ -235,6 +242,12 @@ struct Solver {
     nseg = ceil_div(m, cols_per_seg);
     s4_ncolblk = ceil_div(m, 32);
     mm_ncolblk = ceil_div(m, 128);
+    sk_gcol = sk_grow = 0;
+    sk_slots_col = sk_slots_row = 1;
+    if (ctx->stream_ctas > 0 && m % 4 == 0) {
+      stream_plan(n, m, true, ctx->stream_ctas, &sk_gcol, &sk_slots_col);
+      stream_plan(n, m, false, ctx->stream_ctas, &sk_grow, &sk_slots_row);
+    }
     mm_nseg = std::max(1, std::min(ceil_div(n, 32), (2 * nsm) / std::max(1, mm_ncolblk)));
     mm_seglen = ceil_div(ceil_div(n, mm_nseg), 32) * 32;
     mm_nseg = ceil_div(n, mm_seglen);
@@ -307,6 +320,19 @@ struct Solver {
       hP.part64_row = nullptr;
     }
     hP.gcnt = A.take<unsigned>(4);
+    hP.sk_gcol = sk_gcol;
+    hP.sk_grow = sk_grow;
+    hP.sk_slots_col = sk_slots_col;
+    hP.sk_slots_row = sk_slots_row;
+    {
+      const int sbc = ceil_div(m, 128), sbr = ceil_div(n, 32);
+      hP.sk_part_col = A.take<float2>((size_t)sbc * sk_slots_col * 128);
+      hP.sk_part_row = A.take<float2>((size_t)sbr * sk_slots_row * 32);
+      hP.sk_cnt_col = A.take<unsigned>(sbc);
+      hP.sk_cnt_row = A.take<unsigned>(sbr);
+      hP.sk_acc_col = A.take<double>((size_t)sbc * 4);
+      hP.sk_acc_row = A.take<double>((size_t)sbr * 4);
+    }
     hP.out_plain = nullptr;
     hP.logratio_plain = nullptr;
     const int nch = ceil_div(std::max(n, m), kGChunkHost);

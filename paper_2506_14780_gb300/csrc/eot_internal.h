@@ -91,6 +91,16 @@ struct Prob {
   unsigned* cnt_row;       // [nrowblk]
   double* acc_row;         // [nrowblk][4]
   unsigned* gcnt;          // [4] grid-level arrival counters
+  // staged stream passes (stream.cu): grid sizes (0: not used), contributor
+  // slots per output block, partial states, arrival counters, block sums
+  int sk_gcol, sk_grow;
+  int sk_slots_col, sk_slots_row;
+  float2* sk_part_col;     // [ceil(m/128)][sk_slots_col][128]
+  float2* sk_part_row;     // [ceil(n/32)][sk_slots_row][32]
+  unsigned* sk_cnt_col;    // [ceil(m/128)]
+  unsigned* sk_cnt_row;    // [ceil(n/32)]
+  double* sk_acc_col;      // [ceil(m/128)][4]
+  double* sk_acc_row;      // [ceil(n/32)][4]
   State* st;
   // SK-NR
   int ell;                 // number of modes (0: none)

@@ -26,112 +26,9 @@
 #include "eot_device.cuh"
 #include "eot_internal.h"
 #include "reduce.cuh"
+#include "pass_common.cuh"
 
 namespace eotk {
-
-// ---------------------------------------------------------------------------
-// Finish one index from its merged (R, S): new potential, split arrays, the
-// index's contributions (w |expm1 L|, w L, w out) to the scalars.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void finish_index(float R, double S, int idx, const Prob& P,
-                                             const double* __restrict__ shift,
-                                             const double* __restrict__ w,
-                                             const double* __restrict__ logw,
-                                             double* __restrict__ out, Split so,
-                                             float* __restrict__ Lout, double acc[3],
-                                             int* numeric) {
-  float L = R * kLn2 + log_sum(S);
-  const double sh = shift[idx];
-  double o = sh - P.eps * (double)L;
-  if (!isfinite(o) || !(S > 0.0) || fabs(o) > P.pot_bound) {
-    atomicAdd(numeric, 1);
-    o = sh;
-    L = 0.f;
-  }
-  if (out) out[idx] = o;
-  if (Lout) Lout[idx] = L;
-  if (so.A) {
-    double hi;
-    float lo;
-    split_grid(o + P.eps * logw[idx], P.qscale, P.qinv, hi, lo);
-    so.A[idx] = (float)(hi + (double)P.M);
-    so.AL[idx] = lo;
-    split_grid(o, P.qscale, P.qinv, hi, lo);
-    so.K[idx] = (float)((double)P.M - hi);
-    so.KL[idx] = lo;
-  }
-  const double wi = w[idx];
-  acc[0] = wi * (double)fabsf(expm1f(L));
-  acc[1] = wi * (double)L;
-  acc[2] = wi * o;
-}
-
-// Block-wide deterministic sum of 3 doubles; result valid in thread 0.
-__device__ __forceinline__ void block_sum3(double v[3], double* sh /*[3*8]*/) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    double x = warp_sum_d(v[k]);
-    if (lane == 0) sh[k * 8 + wid] = x;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int k = 0; k < 3; ++k) {
-      double t = 0.0;
-      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[k * 8 + i];
-      v[k] = t;
-    }
-  }
-  __syncthreads();
-}
-
-// Grid-final step shared by both passes.  Called by one thread with the sums.
-__device__ void final_step(const Prob& P, int mode, const double t[3], int dst) {
-  State* st = P.st;
-  st->sum_wL = t[1];
-  st->sum_wout = t[2];
-  if (st->numeric > 0 && mode != MODE_PLAIN && mode != MODE_EVAL) {
-    st->done = 3;
-    return;
-  }
-  switch (mode) {
-    case MODE_SK_ROW:
-      st->l1_row = t[0];
-      st->sum_af = t[2];
-      break;
-    case MODE_TRIAL: {
-      // Q_semi(f') - Q_semi(f_k) = <V Delta, a> + <h' - h, b>,  h' - h = -eps L
-      const double dq = st->dot_vd_a - P.eps * t[1];
-      st->dq = dq;
-      if (dq > 0.0) {
-        st->nr_acc += 1;
-        st->cur_f = 1 - st->cur_f;
-        st->cur_g = (st->cur_g + 2) % 3;
-      } else {
-        st->nr_rej += 1;
-        st->cur_g = (st->cur_g + 1) % 3;
-      }
-      break;
-    }
-    case MODE_SK_COL:
-      st->l1_col = t[0];
-      st->qsemi = st->sum_af + t[2];   // Q_semi(f_k) = <f_k, a> + <f_k^{C,eps}, b>
-      st->iter += 1;
-      if (t[0] < st->tol) st->done = 1;
-      else if (st->iter >= st->max_iter) st->done = 2;
-      else st->cur_g = dst;
-      break;
-    case MODE_EVAL:
-      st->l1_col = t[0];
-      break;
-    case MODE_G_INIT:
-      st->cur_g = dst;
-      break;
-    default:
-      st->l1_col = t[0];
-      break;
-  }
-}
 
 // ---------------------------------------------------------------------------
 // Column pass.  VEC = 4: m % 4 == 0 (16-byte aligned rows), float4 loads;
@@ -548,7 +445,18 @@ __global__ void split_kernel(const Prob* __restrict__ PP, const double* __restri
 // ---------------------------------------------------------------------------
 // Host-side launch helpers.
 // ---------------------------------------------------------------------------
+cudaError_t launch_stream_pass(const Prob* dP, const Prob& hP, bool col, int mode,
+                               cudaStream_t s);
+
+// The staged stream kernels (stream.cu) take every pass whose cost rows are
+// 16-byte aligned; the striped kernels below serve the rest.
+static bool stream_ok(const Prob& hP, bool col) {
+  return (col ? hP.sk_gcol : hP.sk_grow) > 0 && hP.m % 4 == 0 &&
+         (reinterpret_cast<uintptr_t>(hP.C) & 15u) == 0;
+}
+
 cudaError_t launch_col_pass(const Prob* dP, const Prob& hP, int mode, cudaStream_t s) {
+  if (stream_ok(hP, true)) return launch_stream_pass(dP, hP, true, mode, s);
   dim3 grid(hP.ncolblk, hP.nstripe);
   if (hP.m % 4 == 0 && (reinterpret_cast<uintptr_t>(hP.C) & 15u) == 0)
     col_pass_kernel<4><<<grid, kThreads, 0, s>>>(dP, mode);
@@ -558,6 +466,7 @@ cudaError_t launch_col_pass(const Prob* dP, const Prob& hP, int mode, cudaStream
 }
 
 cudaError_t launch_row_pass(const Prob* dP, const Prob& hP, int mode, cudaStream_t s) {
+  if (stream_ok(hP, false)) return launch_stream_pass(dP, hP, false, mode, s);
   dim3 grid(hP.nrowblk, hP.nseg);
   if (hP.m % 4 == 0 && (reinterpret_cast<uintptr_t>(hP.C) & 15u) == 0 && hP.cols_per_seg % 4 == 0)
     row_pass_kernel<4><<<grid, kThreads, 0, s>>>(dP, mode);

@@ -66,6 +66,54 @@ def test_ctransform_parity(pkg, n, m, eps):
     assert np.abs(out.cpu().numpy() - f_true).max() <= 1e-5 * eps + 1e-12
 
 
+# Shapes for the staged stream passes (m % 4 == 0): a single tile, a grid
+# with fewer tiles than CTAs, tall (many contributors per column block), wide
+# (many per row block), ragged in both directions.
+STREAM_SHAPES = [(4, 4), (64, 8), (5003, 260), (40, 9000), (777, 1024)]
+
+
+@pytest.mark.parametrize("n,m", STREAM_SHAPES)
+def test_ctransform_stream_shapes(pkg, n, m):
+    eps = 2e-3
+    prob = W.random_cost(n, m, seed=n + 3 * m)
+    C64 = prob.C.astype(np.float64)
+    rng = np.random.default_rng(n * m)
+    dC = dev(prob.C)
+    f = rng.random(n) * 0.5
+    g_true = O.c_transform_f(f, C64, prob.a, eps)
+    out = torch.zeros(m, dtype=torch.float64, device="cuda")
+    st = pkg.eot_ctransform(pkg.EOT_SIDE_COL, n, m, dC, dev(f), dev(prob.a),
+                            dev(g_true + rng.standard_normal(m) * eps), eps, out, None)
+    assert st == pkg.EOT_OK, pkg.last_error()
+    assert np.abs(out.cpu().numpy() - g_true).max() <= 1e-5 * eps + 1e-12
+    g = rng.random(m) * 0.5
+    f_true = O.c_transform_g(g, C64, prob.b, eps)
+    for off in (2 * eps, -0.3):   # near shift, and one far enough to move the reference
+        out = torch.zeros(n, dtype=torch.float64, device="cuda")
+        st = pkg.eot_ctransform(pkg.EOT_SIDE_ROW, n, m, dC, dev(g), dev(prob.b),
+                                dev(f_true + off), eps, out, None)
+        assert st == pkg.EOT_OK, pkg.last_error()
+        assert np.abs(out.cpu().numpy() - f_true).max() <= 1e-4 * eps
+
+
+def test_ctransform_unaligned_cost_rows(pkg):
+    """A cost whose rows are not 16-byte aligned takes the striped kernels:
+    same results as the aligned copy."""
+    n, m, eps = 300, 256, 1e-2
+    prob = W.random_cost(n, m, seed=11)
+    f = np.linspace(0, 0.3, n)
+    g_true = O.c_transform_f(f, prob.C.astype(np.float64), prob.a, eps)
+    big = torch.zeros(n * m + 1, dtype=torch.float32, device="cuda")
+    big[1:] = torch.as_tensor(prob.C.ravel()).cuda()
+    unaligned = big[1:]
+    assert unaligned.data_ptr() % 16 != 0
+    out = torch.zeros(m, dtype=torch.float64, device="cuda")
+    st = pkg.eot_ctransform(pkg.EOT_SIDE_COL, n, m, unaligned, dev(f), dev(prob.a), None, eps,
+                            out, None)
+    assert st == pkg.EOT_OK, pkg.last_error()
+    assert np.abs(out.cpu().numpy() - g_true).max() <= 1e-5 * eps + 1e-12
+
+
 def test_ctransform_extreme_exponents(pkg):
     """Shifts far from the transform (terms near float32 over/underflow) are
     re-centred by the running log-sum-exp."""
