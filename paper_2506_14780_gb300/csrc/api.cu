@@ -15,6 +15,8 @@
 //               subspace iteration (another graph while loop);
 //   finish      evaluation passes, scores, gauge normalisation, copy-out.
 // The host synchronises once per solve.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -168,6 +170,46 @@ struct Arena {
 };
 
 static int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------------------
+// 2-D tensor map of the cost for the staged stream passes (box 128 columns x
+// 32 rows of float32, no swizzle).  The encoder is the driver's, reached
+// through the runtime's entry-point query (no link against the driver).
+// ---------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+// Encode P.tmC for P.C when the stream passes are in use.
+static eot_status encode_cost_map(Prob& P) {
+  if (P.sk_gcol <= 0 && P.sk_grow <= 0) return EOT_OK;
+  // the striped passes serve costs whose rows are not 16-byte aligned
+  if ((reinterpret_cast<uintptr_t>(P.C) & 15u) != 0 || P.m % 4 != 0) return EOT_OK;
+  auto enc = tensor_map_encoder();
+  if (!enc) return fail(EOT_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+  const cuuint64_t dims[2] = {(cuuint64_t)P.m, (cuuint64_t)P.n};
+  const cuuint64_t strides[1] = {(cuuint64_t)P.m * sizeof(float)};
+  const cuuint32_t box[2] = {128, 32};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(&P.tmC, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(P.C), dims,
+                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return fail(EOT_ECUDA, "cuTensorMapEncodeTiled failed (code " + std::to_string((int)r) + ")");
+  return EOT_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Solver: buffers, tilings and captured graphs for one problem shape.
@@ -817,6 +859,10 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   P.eps = eps0;
   P.k2 = (float)(1.0 / (eps0 * std::log(2.0)));
   P.st = S->dSt;
+  {
+    const eot_status me = encode_cost_map(P);
+    if (me != EOT_OK) return me;
+  }
   CUDA_TRY(cudaMemcpyAsync(S->dP, &P, sizeof(Prob), cudaMemcpyHostToDevice, s));
   // ---- initial state: f = f_init or 0, g shift = 0 ----
   State st0{};
@@ -1136,7 +1182,7 @@ static eot_status standalone_grid(Solver* S, const float* Cdev, const double* p1
   P.k2 = (float)(1.0 / (eps * std::log(2.0)));
   P.st = S->dSt;
   if (cmax_out) *cmax_out = cm;
-  return EOT_OK;
+  return encode_cost_map(P);
 }
 
 static eot_status standalone_solver(int n, int m, int ell, int p, Solver** S, cudaStream_t* s,

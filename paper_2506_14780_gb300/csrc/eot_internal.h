@@ -1,5 +1,6 @@
 // Internal structures shared by the kernels and the host driver.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -93,6 +94,7 @@ struct Prob {
   unsigned* gcnt;          // [4] grid-level arrival counters
   // staged stream passes (stream.cu): grid sizes (0: not used), contributor
   // slots per output block, partial states, arrival counters, block sums
+  CUtensorMap tmC;         // 2-D tensor map of C (box 128 columns x 32 rows), when used
   int sk_gcol, sk_grow;
   int sk_slots_col, sk_slots_row;
   float2* sk_part_col;     // [ceil(m/128)][sk_slots_col][128]

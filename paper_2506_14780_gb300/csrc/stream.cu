@@ -17,9 +17,10 @@
 // block (atomic arrival counter) merges the contributors in a fixed order and
 // finishes the block, so the results do not depend on scheduling.
 //
-// Pipeline.  One producer warp copies each tile row (<= 512 bytes) and the
-// tile's reduction-side coefficients into a ring of four shared-memory stages
-// with cp.async.bulk, completing on the stage's mbarrier; eight consumer warps
+// Pipeline.  One lane of a producer warp loads each tile with one tiled tensor
+// copy (TMA, 2-D map of C) and the tile's reduction-side coefficients with two
+// bulk copies into a ring of four shared-memory stages, completing on the
+// stage's mbarrier; eight consumer warps
 // reduce the tile and release the stage.  Every wait is bounded: a wait that
 // gives up flags a numeric error and the kernel drains its copies and returns.
 //
@@ -33,7 +34,9 @@
 // kept relative to an integer reference (log2 units) that stays 0 while the
 // running maximum lies within 2^+-64 of the output potential's shift (the
 // common case near a fixed point, where the sums are marginal ratios close to
-// one) and is moved with an exact power-of-two rescaling otherwise.
+// one); otherwise it follows the running maximum (see move_ref), with an exact
+// power-of-two rescaling of the sum and the terms re-formed from the raw
+// exponents, so that the reference never costs the dominant terms precision.
 #include "eot_device.cuh"
 #include "eot_internal.h"
 #include "pass_common.cuh"
@@ -52,6 +55,7 @@ constexpr int kStConsumers = 256;
 constexpr int kStThreads = kStConsumers + 32;
 constexpr int kStWait = 1 << 22;
 constexpr float kStWindow = 64.f;
+constexpr int kStPend = 16;
 
 __device__ __forceinline__ void cons_sync() {
   asm volatile("bar.sync 1, 256;" ::: "memory");
@@ -90,55 +94,78 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
       : "memory");
 }
 
+// Tiled tensor copy of the box at (x = column, y = row) of a 2-D tensor map;
+// the whole box is counted on the mbarrier (out-of-range elements read as 0).
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
+      "{%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Arrival counter with acquire-release semantics at GPU scope: the release
+// covers every write of the CTA ordered before it by a barrier (so only the
+// counting thread needs it), the acquire makes the other arrivals' writes
+// visible to the CTA after the next barrier.
+__device__ __forceinline__ unsigned arrive_count(unsigned* p) {
+  unsigned old;
+  asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(old) : "l"(p) : "memory");
+  return old;
+}
+
+// Programmatic dependent launch: wait for the preceding kernel's results /
+// allow the next kernel to start its prologue.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // CTA whose chunk holds tile t (chunks [floor(kT/G), floor((k+1)T/G)), G <= T).
 __device__ __forceinline__ int st_owner(long long t, long long T, int G) {
   return (int)(((t + 1) * (long long)G - 1) / T);
 }
 
-// Sum of three doubles over the 256 consumer threads; valid in thread 0.
-__device__ __forceinline__ void cons_sum3(double v[3], double* sh) {
+// Float64 arithmetic is slow on this GPU (a small fraction of the float32
+// rate), so the reductions below use as few float64 operations as a fixed
+// summation order allows.
+
+// Sum of three doubles held by the first `nact` consumer threads (a multiple
+// of 32, the others hold zeros); valid in thread 0.
+__device__ __forceinline__ void cons_sum3(double v[3], double* sh, int nact) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = nact >> 5;
+  if (wid < nw) {
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const double x = warp_sum_d(v[k]);
-    if (lane == 0) sh[k * 8 + wid] = x;
+    for (int k = 0; k < 3; ++k) {
+      const double x = warp_sum_d(v[k]);
+      if (lane == 0) sh[k * 8 + wid] = x;
+    }
   }
   cons_sync();
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       double t = 0.0;
-      for (int w = 0; w < 8; ++w) t += sh[k * 8 + w];
+      for (int w = 0; w < nw; ++w) t += sh[k * 8 + w];
       v[k] = t;
     }
   }
-  cons_sync();
 }
 
-// Sum of nblk per-block accumulators (stride 4) in a fixed order by the 256
-// consumer threads; result valid in every consumer thread.
-__device__ __forceinline__ void cons_grid_sum3(const double* __restrict__ acc, int nblk,
-                                               double out[3], double* sh) {
+// Sum of nblk per-block accumulators (stride 4) in a fixed order by warp 0;
+// result valid in thread 0.
+__device__ __forceinline__ void warp0_grid_sum3(const double* __restrict__ acc, int nblk,
+                                                double out[3]) {
   double v[3] = {0.0, 0.0, 0.0};
-  for (int b = threadIdx.x; b < nblk; b += kStConsumers) {
+  for (int b = threadIdx.x; b < nblk; b += 32) {
     v[0] += __ldcg(&acc[b * 4 + 0]);
     v[1] += __ldcg(&acc[b * 4 + 1]);
     v[2] += __ldcg(&acc[b * 4 + 2]);
   }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const double x = warp_sum_d(v[k]);
-    if (lane == 0) sh[k * 8 + wid] = x;
-  }
-  cons_sync();
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    double t = 0.0;
-    for (int w = 0; w < 8; ++w) t += sh[k * 8 + w];
-    out[k] = t;
-  }
-  cons_sync();
+  for (int k = 0; k < 3; ++k) out[k] = warp_sum_d(v[k]);
 }
 
 __device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
@@ -147,36 +174,37 @@ __device__ __forceinline__ float2 ex2_2(float2 y) {
   return make_float2(ex2_approx(y.x), ex2_approx(y.y));
 }
 
-// Move the reference of one running sum when its running maximum rr (relative
-// to the reference) left the window; returns the shift d (0 if none).
-__device__ __forceinline__ float recentre(float& rr, float& ref, float& S) {
-  if (fabsf(rr) <= kStWindow || !(rr > -INFINITY)) return 0.f;
-  const float d = rintf(rr);
-  S = scale2(S, -d);
-  ref += d;
-  rr -= d;
-  return d;
+// Reference rule of a running sum (all values in log2 units).  The terms are
+// formed as z = y - ref from the raw exponent y (relative to the output
+// potential's shift), so a reference of exactly 0 keeps them exact.  The
+// reference stays 0 while the running maximum lies within +-kStWindow; when it
+// does not, the reference follows the running maximum (integer, at most 2
+// below it), so that the dominant terms never carry the rounding of a large
+// z.  needs_move says whether the running maximum rr (relative to ref) breaks
+// the rule.
+__device__ __forceinline__ bool needs_move(float rr, float ref) {
+  return ref == 0.f ? !(fabsf(rr) <= kStWindow) : !(rr <= 2.f && rr >= -kStWindow);
+}
+
+// Apply the rule: new reference, exact power-of-two rescaling of the sum.
+__device__ __forceinline__ void move_ref(float& rr, float& ref, float& S) {
+  if (!(rr > -INFINITY) || !needs_move(rr, ref)) return;   // no terms yet, or nothing to do
+  const float ymax = rr + ref;
+  const float nr = fabsf(ymax) <= kStWindow ? 0.f : rintf(ymax);
+  S = scale2(S, ref - nr);
+  rr = ymax - nr;
+  ref = nr;
 }
 
 template <bool COL>
 __global__ void __launch_bounds__(kStThreads, 2)
     stream_pass_kernel(const Prob* __restrict__ PP, int mode) {
+  // PP->tmC is read by the tensor-copy unit: PP points to global memory.  The
+  // problem description (*PP) and the cost are not written by the kernels of
+  // a solve, so they are read before the programmatic-launch wait; the state
+  // and the potentials only after it.
   const Prob& P = *PP;
   State* st = P.st;
-  if (mode != MODE_PLAIN && mode != MODE_EVAL && st->done) return;
-  if (COL && mode == MODE_TRIAL && !st->nr_ok) return;
-  const int cf = st->cur_f, cg = st->cur_g;
-  // buffers (as in the striped passes): a trial column pass reads f' and is
-  // shifted by h = f_k^{C,eps}
-  int src_f = cf, sh_g = cg, dst_g = (cg + 1) % 3;
-  if (COL && mode == MODE_TRIAL) {
-    src_f = 1 - cf;
-    sh_g = (cg + 1) % 3;
-    dst_g = (cg + 2) % 3;
-  }
-  if (mode == MODE_EVAL) dst_g = -1;
-  const Split red = COL ? P.rs[src_f] : P.cs[cg];
-  const Split outs = COL ? P.cs[sh_g] : P.rs[cf];
 
   extern __shared__ __align__(1024) unsigned char st_smem[];
   __shared__ __align__(8) uint64_t full_bar[kStStages];
@@ -187,6 +215,8 @@ __global__ void __launch_bounds__(kStThreads, 2)
   __shared__ double s_red[24];
   __shared__ unsigned s_flag;
   __shared__ int s_err;
+  __shared__ int s_pend[kStPend];   // blocks this CTA finishes after its stream
+  __shared__ int s_npend;
 
   const int n = P.n, m = P.m;
   const int ntr = (n + kStR - 1) / kStR, ntc = (m + kStC - 1) / kStC;
@@ -209,36 +239,89 @@ __global__ void __launch_bounds__(kStThreads, 2)
       mbar_init(smem_addr(&empty_bar[s]), 8);
     }
     s_err = 0;
+    s_npend = 0;
     mbar_init_fence();
   }
   __syncthreads();
 
+  // geometry of tile t of this CTA's chunk
+  auto tile_of = [&](long long t, int& b, int& q, int& r0, int& c0, int& ncoef) {
+    b = (int)(t / nT);
+    q = (int)(t - (long long)b * nT);
+    r0 = COL ? q * kStR : b * kStR;
+    c0 = COL ? b * kStC : q * kStC;
+    const int rows = min(kStR, n - r0), cols = min(kStC, m - c0);
+    // reduction-side coefficients: rows of the tile (column pass, rounded up
+    // to 4 floats: the split arrays are padded) or its columns (row pass)
+    ncoef = COL ? ((rows + 3) & ~3) : cols;
+  };
+  // The first stages of the cost tiles do not depend on the preceding kernel:
+  // start them before waiting for it (they complete when the coefficients
+  // are added below).
+  const int npre = (int)min((long long)kStStages, t1 - t0);
+  if (warp == 8 && lane == 0) {
+    for (int it = 0; it < npre; ++it) {
+      int b, q, r0, c0, ncoef;
+      tile_of(t0 + it, b, q, r0, c0, ncoef);
+      const uint32_t fb = smem_addr(&full_bar[it]);
+      mbar_expect_tx(fb, (uint32_t)(kStTileBytes + 2 * ncoef * 4));
+      // c0 is a multiple of 128 columns: the box starts on a 16-byte boundary
+      tma_load_2d(sbase + (uint32_t)(it * kStStageBytes), &PP->tmC, c0, r0, fb);
+    }
+  }
+  pdl_wait();
+  const bool skip = (mode != MODE_PLAIN && mode != MODE_EVAL && st->done) ||
+                    (COL && mode == MODE_TRIAL && !st->nr_ok);
+  const int cf = st->cur_f, cg = st->cur_g;
+  // buffers (as in the striped passes): a trial column pass reads f' and is
+  // shifted by h = f_k^{C,eps}
+  int src_f = cf, sh_g = cg, dst_g = (cg + 1) % 3;
+  if (COL && mode == MODE_TRIAL) {
+    src_f = 1 - cf;
+    sh_g = (cg + 1) % 3;
+    dst_g = (cg + 2) % 3;
+  }
+  if (mode == MODE_EVAL) dst_g = -1;
+  const Split red = COL ? P.rs[src_f] : P.cs[cg];
+  const Split outs = COL ? P.cs[sh_g] : P.rs[cf];
+  if (warp == 8 && lane == 0) {
+    // coefficients of the prefetched stages
+    for (int it = 0; it < npre; ++it) {
+      int b, q, r0, c0, ncoef;
+      tile_of(t0 + it, b, q, r0, c0, ncoef);
+      const int off = COL ? r0 : c0;
+      const uint32_t fb = smem_addr(&full_bar[it]);
+      const uint32_t dst = sbase + (uint32_t)(it * kStStageBytes);
+      bulk_load(dst + kStTileBytes, red.A + off, (uint32_t)(ncoef * 4), fb);
+      bulk_load(dst + kStTileBytes + kStC * 4, red.AL + off, (uint32_t)(ncoef * 4), fb);
+    }
+  }
+  if (skip) {
+    // nothing to do: let the prefetched copies land before the CTA exits
+    if (warp == 8 && lane == 0)
+      for (int it = 0; it < npre; ++it) mbar_wait(smem_addr(&full_bar[it]), 0, kStWait);
+    return;
+  }
+
   if (warp == 8) {
     // ---------------- producer ----------------
-    int it = 0;
+    int it = npre;
     bool ok = true;
-    for (long long t = t0; t < t1; ++t, ++it) {
+    for (long long t = t0 + npre; t < t1; ++t, ++it) {
       const int s = it % kStStages;
-      if (it >= kStStages &&
-          !mbar_wait(smem_addr(&empty_bar[s]), ((it / kStStages) - 1) & 1, kStWait)) {
+      if (!mbar_wait(smem_addr(&empty_bar[s]), ((it / kStStages) - 1) & 1, kStWait)) {
         ok = false;
         break;
       }
-      const int b = (int)(t / nT), q = (int)(t - (long long)b * nT);
-      const int r0 = COL ? q * kStR : b * kStR;
-      const int c0 = COL ? b * kStC : q * kStC;
-      const int rows = min(kStR, n - r0), cols = min(kStC, m - c0);
-      // reduction-side coefficients: rows of the tile (column pass, rounded up
-      // to 4 floats: the split arrays are padded) or its columns (row pass)
-      const int ncoef = COL ? ((rows + 3) & ~3) : cols;
+      int b, q, r0, c0, ncoef;
+      tile_of(t, b, q, r0, c0, ncoef);
       const uint32_t fb = smem_addr(&full_bar[s]);
       const uint32_t dst = sbase + (uint32_t)(s * kStStageBytes);
-      if (lane == 0) mbar_expect_tx(fb, (uint32_t)(rows * cols * 4 + 2 * ncoef * 4));
-      __syncwarp();
-      if (lane < rows)
-        bulk_load(dst + (uint32_t)(lane * kStC * 4), P.C + (size_t)(r0 + lane) * m + c0,
-                  (uint32_t)(cols * 4), fb);
       if (lane == 0) {
+        // the tile (one tensor copy: c0 is a multiple of 128 columns, so the
+        // box starts on a 16-byte boundary) and the coefficients
+        mbar_expect_tx(fb, (uint32_t)(kStTileBytes + 2 * ncoef * 4));
+        tma_load_2d(dst, &PP->tmC, c0, r0, fb);
         const int off = COL ? r0 : c0;
         bulk_load(dst + kStTileBytes, red.A + off, (uint32_t)(ncoef * 4), fb);
         bulk_load(dst + kStTileBytes + kStC * 4, red.AL + off, (uint32_t)(ncoef * 4), fb);
@@ -251,6 +334,7 @@ __global__ void __launch_bounds__(kStThreads, 2)
         s_err = 1;
       }
     }
+    pdl_trigger();
     // drain: the last copy issued into every stage has landed before exit
     const int issued = it;
     for (int s = 0; s < kStStages && s < issued; ++s) {
@@ -273,12 +357,94 @@ __global__ void __launch_bounds__(kStThreads, 2)
   bool ref0 = true;
   bool werr = false;                  // this warp gave up waiting
 
-  // finish this CTA's piece of output block b
-  auto flush = [&](int b) {
-    const int kf = st_owner((long long)b * nT, T, G);
-    const int kl = st_owner((long long)(b + 1) * nT - 1, T, G);
-    const int nc = kl - kf + 1;
-    const int slot = (int)blockIdx.x - kf;
+  // A CTA's piece of an output block is published (partial state per index
+  // plus an arrival on the block's counter) when the stream leaves the block;
+  // a CTA that arrives last on a block finishes it after its own stream ends,
+  // so that no global round trip stalls the streaming phase.
+  auto contributors = [&](int b, int& kf, int& nc) {
+    kf = st_owner((long long)b * nT, T, G);
+    nc = st_owner((long long)(b + 1) * nT - 1, T, G) - kf + 1;
+  };
+  const int lim = COL ? m : n;
+
+  auto finish_block = [&](int b) {
+    int kf, nc;
+    contributors(b, kf, nc);
+    // the contributors' partials, merged by 256 / width groups in parallel
+    const int c = tid % width, h = tid / width, ng = kStConsumers / width;
+    float Rg = -INFINITY;
+    double Sg = 0.0;
+    if (b * width + c < lim)
+      merge_segments(part + (size_t)b * slots * width, nc, width, c, h, ng, Rg, Sg);
+    s_mr[h][c] = Rg;
+    s_ms[h][c] = Sg;
+    cons_sync();
+    const int idx = b * width + tid;            // output index of thread tid < width
+    float R = -INFINITY;
+    double Sd = 0.0;
+    if (tid < width) {
+      R = s_mr[0][tid];
+      Sd = s_ms[0][tid];
+      for (int g = 1; g < ng; ++g) merge_dd(R, Sd, s_mr[g][tid], s_ms[g][tid]);
+    }
+    if (tid == 0) cnt[b] = 0u;
+    double accv[3] = {0.0, 0.0, 0.0};
+    if (tid < width && idx < lim) {
+      double* out;
+      Split so;
+      if (mode == MODE_PLAIN) {
+        out = P.out_plain;
+        so = Split{nullptr, nullptr, nullptr, nullptr};
+      } else if (mode == MODE_EVAL) {
+        out = nullptr;
+        so = Split{nullptr, nullptr, nullptr, nullptr};
+      } else if (COL) {
+        out = P.g[dst_g];
+        so = P.cs[dst_g];
+      } else {
+        out = P.f[cf];
+        so = P.rs[cf];
+      }
+      if (COL) {
+        finish_index(R, Sd, idx, P, P.g[sh_g], P.b, P.logb, out, so, P.Lcol, accv, &st->numeric);
+        if (mode == MODE_PLAIN && P.logratio_plain) P.logratio_plain[idx] = (double)P.Lcol[idx];
+      } else {
+        finish_index(R, Sd, idx, P, P.f[cf], P.a, P.loga, out, so, P.Lrow, accv, &st->numeric);
+        if (mode == MODE_PLAIN && P.logratio_plain) P.logratio_plain[idx] = (double)P.Lrow[idx];
+      }
+    }
+    cons_sum3(accv, s_red, width < 32 ? 32 : width);
+    if (tid == 0) {
+      double* ab = bacc + b * 4;
+      ab[0] = accv[0];
+      ab[1] = accv[1];
+      ab[2] = accv[2];
+      s_flag = (arrive_count(&P.gcnt[COL ? 0 : 1]) == (unsigned)(nblk - 1)) ? 1u : 0u;
+    }
+    cons_sync();
+    if (!s_flag) return;
+    if (warp == 0) {
+      double tot[3];
+      warp0_grid_sum3(bacc, nblk, tot);
+      if (tid == 0) {
+        P.gcnt[COL ? 0 : 1] = 0u;
+        if (COL) final_step(P, mode, tot, dst_g);
+        else if (mode == MODE_EVAL) st->l1_row = tot[0];
+        else final_step(P, mode == MODE_PLAIN ? MODE_PLAIN : MODE_SK_ROW, tot, cf);
+      }
+    }
+  };
+
+  // finish the blocks this CTA arrived last on (uniform over the consumers)
+  auto finish_pending = [&]() {
+    if (cons_sync_or(*(volatile int*)&s_err)) return;
+    const int np = s_npend;
+    for (int k = 0; k < np; ++k) finish_block(s_pend[k]);
+    cons_sync();
+    if (tid == 0) s_npend = 0;
+  };
+
+  auto publish = [&](int b) {
     if (COL) {
       s_pc[warp][lane * 4 + 0] = f2(ref[0], Sa[0].x);
       s_pc[warp][lane * 4 + 1] = f2(ref[1], Sa[0].y);
@@ -307,11 +473,18 @@ __global__ void __launch_bounds__(kStThreads, 2)
     }
     // s_err may be raised by the producer at any time: take one value for all
     if (cons_sync_or(*(volatile int*)&s_err)) return;
-    float R = -INFINITY;
-    double Sd = 0.0;
-    const int idx = b * width + tid;            // output index of thread tid < width
-    const int lim = COL ? m : n;
+    if (s_npend == kStPend) {
+      // the list is full (tiny blocks): finish now
+      const int np = s_npend;
+      for (int k = 0; k < np; ++k) finish_block(s_pend[k]);
+      if (tid == 0) s_npend = 0;
+    }
+    int kf, nc;
+    contributors(b, kf, nc);
+    const int idx = b * width + tid;
     if (tid < width) {
+      float R = -INFINITY;
+      double Sd = 0.0;
       if (COL) {
 #pragma unroll
         for (int w = 0; w < 8; ++w) merge_d(R, Sd, s_pc[w][tid].x, s_pc[w][tid].y);
@@ -319,77 +492,11 @@ __global__ void __launch_bounds__(kStThreads, 2)
         R = s_mr[0][tid];
         Sd = s_ms[0][tid];
       }
-      if (nc > 1 && idx < lim)
-        part[((size_t)b * slots + slot) * width + tid] = f2(R, (float)Sd);
-    }
-    if (nc > 1) {
-      __threadfence();
-      cons_sync();
-      if (tid == 0) s_flag = (atomicAdd(&cnt[b], 1u) == (unsigned)(nc - 1)) ? 1u : 0u;
-      cons_sync();
-      if (!s_flag) return;
-      __threadfence();
-      // the contributors' partials, merged by 256 / width groups in parallel
-      const int c = tid % width, h = tid / width, ng = kStConsumers / width;
-      float Rg = -INFINITY;
-      double Sg = 0.0;
-      if (b * width + c < lim)
-        merge_segments(part + (size_t)b * slots * width, nc, width, c, h, ng, Rg, Sg);
-      s_mr[h][c] = Rg;
-      s_ms[h][c] = Sg;
-      cons_sync();
-      if (tid < width) {
-        R = s_mr[0][tid];
-        Sd = s_ms[0][tid];
-        for (int g = 1; g < ng; ++g) merge_dd(R, Sd, s_mr[g][tid], s_ms[g][tid]);
-      }
-      if (tid == 0) cnt[b] = 0u;
-    }
-    double accv[3] = {0.0, 0.0, 0.0};
-    if (tid < width && idx < lim) {
-      double* out;
-      Split so;
-      if (mode == MODE_PLAIN) {
-        out = P.out_plain;
-        so = Split{nullptr, nullptr, nullptr, nullptr};
-      } else if (mode == MODE_EVAL) {
-        out = nullptr;
-        so = Split{nullptr, nullptr, nullptr, nullptr};
-      } else if (COL) {
-        out = P.g[dst_g];
-        so = P.cs[dst_g];
-      } else {
-        out = P.f[cf];
-        so = P.rs[cf];
-      }
-      if (COL) {
-        finish_index(R, Sd, idx, P, P.g[sh_g], P.b, P.logb, out, so, P.Lcol, accv, &st->numeric);
-        if (mode == MODE_PLAIN && P.logratio_plain) P.logratio_plain[idx] = (double)P.Lcol[idx];
-      } else {
-        finish_index(R, Sd, idx, P, P.f[cf], P.a, P.loga, out, so, P.Lrow, accv, &st->numeric);
-        if (mode == MODE_PLAIN && P.logratio_plain) P.logratio_plain[idx] = (double)P.Lrow[idx];
-      }
-    }
-    cons_sum3(accv, s_red);
-    if (tid == 0) {
-      double* ab = bacc + b * 4;
-      ab[0] = accv[0];
-      ab[1] = accv[1];
-      ab[2] = accv[2];
-      __threadfence();
-      s_flag = (atomicAdd(&P.gcnt[COL ? 0 : 1], 1u) == (unsigned)(nblk - 1)) ? 1u : 0u;
+      if (idx < lim) part[((size_t)b * slots + ((int)blockIdx.x - kf)) * width + tid] =
+          f2(R, (float)Sd);
     }
     cons_sync();
-    if (!s_flag) return;
-    __threadfence();
-    double tot[3];
-    cons_grid_sum3(bacc, nblk, tot, s_red);
-    if (tid == 0) {
-      P.gcnt[COL ? 0 : 1] = 0u;
-      if (COL) final_step(P, mode, tot, dst_g);
-      else if (mode == MODE_EVAL) st->l1_row = tot[0];
-      else final_step(P, mode == MODE_PLAIN ? MODE_PLAIN : MODE_SK_ROW, tot, cf);
-    }
+    if (tid == 0 && arrive_count(&cnt[b]) == (unsigned)(nc - 1)) s_pend[s_npend++] = b;
   };
 
   auto start_block = [&](int b) {
@@ -427,7 +534,7 @@ __global__ void __launch_bounds__(kStThreads, 2)
   for (long long t = t0; t < t1; ++t, ++it) {
     const int b = (int)(t / nT), q = (int)(t - (long long)b * nT);
     if (b != cur_b) {
-      if (cur_b >= 0) flush(cur_b);
+      if (cur_b >= 0) publish(cur_b);
       cur_b = b;
       start_block(b);
     }
@@ -471,36 +578,39 @@ __global__ void __launch_bounds__(kStThreads, 2)
             yb[u].y = (rv && j + 3 < m) ? yb[u].y : -INFINITY;
           }
         }
-        if (!ref0) {
-          const float2 na = f2(-ref[0], -ref[1]), nb = f2(-ref[2], -ref[3]);
+        // z = y - ref (the raw exponents y are kept for a change of reference)
+        float2 za[4], zb[4];
+        const float2 na = f2(-ref[0], -ref[1]), nb = f2(-ref[2], -ref[3]);
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            ya[u] = __fadd2_rn(ya[u], na);
-            yb[u] = __fadd2_rn(yb[u], nb);
-          }
+        for (int u = 0; u < 4; ++u) {
+          za[u] = ref0 ? ya[u] : __fadd2_rn(ya[u], na);
+          zb[u] = ref0 ? yb[u] : __fadd2_rn(yb[u], nb);
         }
-        rr[0] = fmaxf(rr[0], fmaxf(fmaxf(ya[0].x, ya[1].x), fmaxf(ya[2].x, ya[3].x)));
-        rr[1] = fmaxf(rr[1], fmaxf(fmaxf(ya[0].y, ya[1].y), fmaxf(ya[2].y, ya[3].y)));
-        rr[2] = fmaxf(rr[2], fmaxf(fmaxf(yb[0].x, yb[1].x), fmaxf(yb[2].x, yb[3].x)));
-        rr[3] = fmaxf(rr[3], fmaxf(fmaxf(yb[0].y, yb[1].y), fmaxf(yb[2].y, yb[3].y)));
-        if (!(fabsf(rr[0]) <= kStWindow && fabsf(rr[1]) <= kStWindow &&
-              fabsf(rr[2]) <= kStWindow && fabsf(rr[3]) <= kStWindow)) {
-          const float d0 = recentre(rr[0], ref[0], Sa[0].x);
-          const float d1 = recentre(rr[1], ref[1], Sa[0].y);
-          const float d2 = recentre(rr[2], ref[2], Sa[1].x);
-          const float d3 = recentre(rr[3], ref[3], Sa[1].y);
-          const float2 na = f2(-d0, -d1), nb = f2(-d2, -d3);
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            ya[u] = __fadd2_rn(ya[u], na);
-            yb[u] = __fadd2_rn(yb[u], nb);
-          }
+        rr[0] = fmaxf(rr[0], fmaxf(fmaxf(za[0].x, za[1].x), fmaxf(za[2].x, za[3].x)));
+        rr[1] = fmaxf(rr[1], fmaxf(fmaxf(za[0].y, za[1].y), fmaxf(za[2].y, za[3].y)));
+        rr[2] = fmaxf(rr[2], fmaxf(fmaxf(zb[0].x, zb[1].x), fmaxf(zb[2].x, zb[3].x)));
+        rr[3] = fmaxf(rr[3], fmaxf(fmaxf(zb[0].y, zb[1].y), fmaxf(zb[2].y, zb[3].y)));
+        const bool move = ref0 ? !(fabsf(rr[0]) <= kStWindow && fabsf(rr[1]) <= kStWindow &&
+                                   fabsf(rr[2]) <= kStWindow && fabsf(rr[3]) <= kStWindow)
+                               : (needs_move(rr[0], ref[0]) || needs_move(rr[1], ref[1]) ||
+                                  needs_move(rr[2], ref[2]) || needs_move(rr[3], ref[3]));
+        if (move) {
+          move_ref(rr[0], ref[0], Sa[0].x);
+          move_ref(rr[1], ref[1], Sa[0].y);
+          move_ref(rr[2], ref[2], Sa[1].x);
+          move_ref(rr[3], ref[3], Sa[1].y);
           ref0 = ref[0] == 0.f && ref[1] == 0.f && ref[2] == 0.f && ref[3] == 0.f;
+          const float2 ma = f2(-ref[0], -ref[1]), mb = f2(-ref[2], -ref[3]);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            za[u] = __fadd2_rn(ya[u], ma);
+            zb[u] = __fadd2_rn(yb[u], mb);
+          }
         }
-        Sa[0] = __fadd2_rn(Sa[0], __fadd2_rn(__fadd2_rn(ex2_2(ya[0]), ex2_2(ya[1])),
-                                             __fadd2_rn(ex2_2(ya[2]), ex2_2(ya[3]))));
-        Sa[1] = __fadd2_rn(Sa[1], __fadd2_rn(__fadd2_rn(ex2_2(yb[0]), ex2_2(yb[1])),
-                                             __fadd2_rn(ex2_2(yb[2]), ex2_2(yb[3]))));
+        Sa[0] = __fadd2_rn(Sa[0], __fadd2_rn(__fadd2_rn(ex2_2(za[0]), ex2_2(za[1])),
+                                             __fadd2_rn(ex2_2(za[2]), ex2_2(za[3]))));
+        Sa[1] = __fadd2_rn(Sa[1], __fadd2_rn(__fadd2_rn(ex2_2(zb[0]), ex2_2(zb[1])),
+                                             __fadd2_rn(ex2_2(zb[2]), ex2_2(zb[3]))));
       } else {
         const float4 ca = *reinterpret_cast<const float4*>(cA + lane * 4);
         const float4 cl = *reinterpret_cast<const float4*>(cAL + lane * 4);
@@ -527,44 +637,48 @@ __global__ void __launch_bounds__(kStThreads, 2)
             yb[u].y = (rv && j + 3 < m) ? yb[u].y : -INFINITY;
           }
         }
-        if (!ref0) {
+        float2 za[4], zb[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const float2 nr = f2(-ref[u], -ref[u]);
-            ya[u] = __fadd2_rn(ya[u], nr);
-            yb[u] = __fadd2_rn(yb[u], nr);
-          }
+        for (int u = 0; u < 4; ++u) {
+          const float2 nr = f2(-ref[u], -ref[u]);
+          za[u] = ref0 ? ya[u] : __fadd2_rn(ya[u], nr);
+          zb[u] = ref0 ? yb[u] : __fadd2_rn(yb[u], nr);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          rr[u] = fmaxf(rr[u], fmaxf(fmaxf(ya[u].x, ya[u].y), fmaxf(yb[u].x, yb[u].y)));
-        if (!(fabsf(rr[0]) <= kStWindow && fabsf(rr[1]) <= kStWindow &&
-              fabsf(rr[2]) <= kStWindow && fabsf(rr[3]) <= kStWindow)) {
+          rr[u] = fmaxf(rr[u], fmaxf(fmaxf(za[u].x, za[u].y), fmaxf(zb[u].x, zb[u].y)));
+        const bool move = ref0 ? !(fabsf(rr[0]) <= kStWindow && fabsf(rr[1]) <= kStWindow &&
+                                   fabsf(rr[2]) <= kStWindow && fabsf(rr[3]) <= kStWindow)
+                               : (needs_move(rr[0], ref[0]) || needs_move(rr[1], ref[1]) ||
+                                  needs_move(rr[2], ref[2]) || needs_move(rr[3], ref[3]));
+        if (move) {
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             // the row's running sum is held as a pair: rescale both halves
-            float sx = Sa[u].x, sy = Sa[u].y, rx = ref[u], rry = rr[u];
-            const float d = recentre(rry, rx, sx);
-            if (d != 0.f) {
-              sy = scale2(sy, -d);
-              ya[u] = __fadd2_rn(ya[u], f2(-d, -d));
-              yb[u] = __fadd2_rn(yb[u], f2(-d, -d));
-            }
-            Sa[u] = f2(sx, sy);
+            float sx = Sa[u].x, rx = ref[u], rry = rr[u];
+            const float old = rx;
+            move_ref(rry, rx, sx);
+            Sa[u] = f2(sx, rx != old ? scale2(Sa[u].y, old - rx) : Sa[u].y);
             ref[u] = rx;
             rr[u] = rry;
+            const float2 nr = f2(-rx, -rx);
+            za[u] = __fadd2_rn(ya[u], nr);
+            zb[u] = __fadd2_rn(yb[u], nr);
           }
           ref0 = ref[0] == 0.f && ref[1] == 0.f && ref[2] == 0.f && ref[3] == 0.f;
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          Sa[u] = __fadd2_rn(Sa[u], __fadd2_rn(ex2_2(ya[u]), ex2_2(yb[u])));
+          Sa[u] = __fadd2_rn(Sa[u], __fadd2_rn(ex2_2(za[u]), ex2_2(zb[u])));
       }
     }
     __syncwarp();
     if (lane == 0) mbar_arrive1(smem_addr(&empty_bar[s]));
   }
-  if (cur_b >= 0) flush(cur_b);
+  // the stream is done: the next kernel may start its prologue
+  pdl_trigger();
+  if (cur_b >= 0) publish(cur_b);
+  finish_pending();
 }
 
 // ---------------------------------------------------------------------------
@@ -608,13 +722,23 @@ void stream_plan(int n, int m, bool col, int ctas, int* grid, int* slots) {
   *slots = (int)mx;
 }
 
+// Launched with programmatic stream serialization: the kernel starts while
+// the preceding kernel finishes and waits for it (griddepcontrol.wait) before
+// reading anything that kernel may write.
 cudaError_t launch_stream_pass(const Prob* dP, const Prob& hP, bool col, int mode,
                                cudaStream_t s) {
-  if (col)
-    stream_pass_kernel<true><<<hP.sk_gcol, kStThreads, kStSmem, s>>>(dP, mode);
-  else
-    stream_pass_kernel<false><<<hP.sk_grow, kStThreads, kStSmem, s>>>(dP, mode);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(col ? hP.sk_gcol : hP.sk_grow));
+  cfg.blockDim = dim3(kStThreads);
+  cfg.dynamicSmemBytes = kStSmem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return col ? cudaLaunchKernelEx(&cfg, stream_pass_kernel<true>, dP, mode)
+             : cudaLaunchKernelEx(&cfg, stream_pass_kernel<false>, dP, mode);
 }
 
 }  // namespace eotk
