@@ -62,6 +62,7 @@ void init_mma_attributes();
 void init_stream_attributes();
 int stream_ctas_per_sm();
 void stream_plan(int n, int m, bool col, int ctas, int* grid, int* slots);
+cudaError_t launch_sk_coop(const Prob* dP, const Prob& hP, int max_body, cudaStream_t s);
 
 __global__ void wgram_partial_kernel(const float*, const float*, const double*, int, int, int,
                                      const double*, const float*, double*, double*, const State*,
@@ -372,8 +373,9 @@ struct Solver {
       hP.sk_part_row = A.take<float2>((size_t)sbr * sk_slots_row * 32);
       hP.sk_cnt_col = A.take<unsigned>(sbc);
       hP.sk_cnt_row = A.take<unsigned>(sbr);
-      hP.sk_acc_col = A.take<double>((size_t)sbc * 4);
+      hP.sk_acc_col = A.take<double>((size_t)ceil_div(m, 32) * 4);   // per 32-column unit
       hP.sk_acc_row = A.take<double>((size_t)sbr * 4);
+      hP.gbar = A.take<unsigned>(2 + 32);   // root count, generation, group counts
     }
     hP.out_plain = nullptr;
     hP.logratio_plain = nullptr;
@@ -628,6 +630,26 @@ struct Solver {
 
   // Run a captured loop to completion.  With conditional nodes this is one
   // launch; otherwise the host relaunches the body and polls the state.
+  // Plain Sinkhorn iterations of one level: the cooperative loop (one launch,
+  // grid barriers between the half-steps) when the staged stream passes serve
+  // this cost, else the captured graph.  A cooperative launch the device
+  // refuses falls back to the graph for this solver.
+  bool coop_ok = true;
+  eot_status run_sk(int max_iter, int graph_cap, bool* used_coop) {
+    *used_coop = false;
+    if (coop_ok && !f64 && hP.sk_gcol > 0 && hP.sk_gcol == hP.sk_grow && m % 4 == 0 &&
+        (reinterpret_cast<uintptr_t>(hP.C) & 15u) == 0) {
+      const cudaError_t e = launch_sk_coop(dP, hP, max_iter + 4, ctx->stream);
+      if (e == cudaSuccess) {
+        *used_coop = true;
+        return EOT_OK;
+      }
+      cudaGetLastError();
+      coop_ok = false;
+    }
+    return run_loop(ex_sk, 0, graph_cap);
+  }
+
   eot_status run_loop(cudaGraphExec_t ex, int which, int cap) {
     cudaStream_t s = ctx->stream;
     if (ctx->cond_ok) {
@@ -899,7 +921,8 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   State* hLev = nullptr;
   CUDA_TRY(cudaMallocHost(&hLev, sizeof(State) * (2 * L + 1)));
   std::memset(hLev, 0, sizeof(State) * (2 * L + 1));
-  std::vector<int> lev_nr(L, 0), lev_eig(L, 0);
+  std::vector<int> lev_nr(L, 0), lev_eig(L, 0), lev_coop(L, 0);
+  int resumed_coop = 0;
   bool have_modes = false;
   int eig_iters_total = 0;
   int resumed_iters = 0, resumed_acc = 0, resumed_rej = 0, resumed_bodies = 0, verify_rounds = 0;
@@ -911,13 +934,13 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
     const double eps = levels[t];
     const bool last = t == L - 1;
     // Final-level margins (float32 passes only): the device test and the
-    // verification below evaluate the marginal ratios with float32
-    // exponentials and sums, whose error against a float64 evaluation is a
-    // small fraction of the tolerance (about 0.2% of 1e-6 on the tested
-    // problems).  The device aims at 0.97 tol and the returned pair must
-    // verify below 0.985 tol.
-    const double tol_verify = last ? (S->f64 ? o->tol : 0.985 * o->tol) : 0.0;
-    const double tol = last ? (S->f64 ? o->tol : 0.97 * o->tol)
+    // verification below evaluate the marginal ratios from float32 partial
+    // sums, whose rounding (about 1e-7 relative per sum) leaves the L1
+    // estimate up to ~1e-7 away from a float64 evaluation near a tolerance of
+    // 1e-6.  The device aims at 0.85 tol and the returned pair must verify
+    // below 0.9 tol.
+    const double tol_verify = last ? (S->f64 ? o->tol : 0.9 * o->tol) : 0.0;
+    const double tol = last ? (S->f64 ? o->tol : 0.85 * o->tol)
                             : (o->level_tol > 0.0 ? o->level_tol : o->tol);
     const bool use_nr = ell > 0 && have_modes;
     CUDA_TRY(cudaEventRecord(lev_ev[t], s));
@@ -935,8 +958,10 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
       eot_status e = S->run_loop(S->ex_sknr, 0, body_cap_nr + 1);
       if (e != EOT_OK) return e;
     } else {
-      eot_status e = S->run_loop(S->ex_sk, 0, body_cap_sk + 1);
+      bool coop = false;
+      eot_status e = S->run_sk(o->max_iter, body_cap_sk + 1, &coop);
       if (e != EOT_OK) return e;
+      lev_coop[t] = coop ? 1 : 0;
     }
     if (last) {
       // The device test uses the column term of the L1 marginal error (the row
@@ -960,8 +985,14 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
         resumed_rej += hs.nr_rej;
         level_setup_kernel<<<1, 1, 0, s>>>(S->dP, eps, (float)(1.0 / (eps * std::log(2.0))), tdev,
                                            o->max_iter, use_nr ? body_cap_nr : body_cap_sk);
-        eot_status e = S->run_loop(use_nr ? S->ex_sknr : S->ex_sk, 0,
-                                   (use_nr ? body_cap_nr : body_cap_sk) + 1);
+        eot_status e;
+        if (use_nr) {
+          e = S->run_loop(S->ex_sknr, 0, body_cap_nr + 1);
+        } else {
+          bool coop = false;
+          e = S->run_sk(o->max_iter, body_cap_sk + 1, &coop);
+          if (coop) ++resumed_coop;
+        }
         if (e != EOT_OK) return e;
       }
     }
@@ -1053,6 +1084,7 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   for (int t = 0; t < L; ++t) {
     launches += 1 + 2 + 1 + 2;   // level set-up, splits, first column pass, buffer copy
     if (lev_nr[t]) launches += 4 + (long long)hLev[t].body_runs * (6 * S->unroll_sknr + 1);
+    else if (lev_coop[t]) launches += 1;
     else launches += (long long)hLev[t].body_runs * (2 * S->unroll_sk + 1);
     if (lev_eig[t]) {
       r.eig_iters += hLev[L + t].eig_iter;
@@ -1061,6 +1093,7 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   }
   launches += 5 + 2LL * verify_rounds;
   launches += (long long)resumed_bodies * (lev_nr[L - 1] ? 6 * S->unroll_sknr + 1 : 2 * S->unroll_sk + 1);
+  launches += resumed_coop;
   launches += (verify_rounds > 1 ? (long long)(verify_rounds - 1) : 0);   // level set-up per resume
   r.kernel_launches = launches;
   r.row_l1 = S->hScores[0];

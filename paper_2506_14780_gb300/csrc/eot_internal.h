@@ -101,8 +101,9 @@ struct Prob {
   float2* sk_part_row;     // [ceil(n/32)][sk_slots_row][32]
   unsigned* sk_cnt_col;    // [ceil(m/128)]
   unsigned* sk_cnt_row;    // [ceil(n/32)]
-  double* sk_acc_col;      // [ceil(m/128)][4]
+  double* sk_acc_col;      // [ceil(m/32)][4] (per 128-column block, or per 32-column unit)
   double* sk_acc_row;      // [ceil(n/32)][4]
+  unsigned* gbar;          // [2] grid barrier of the cooperative Sinkhorn loop
   State* st;
   // SK-NR
   int ell;                 // number of modes (0: none)

@@ -8,17 +8,15 @@ namespace eotk {
 
 // ---------------------------------------------------------------------------
 // Finish one index from its merged (R, S): new potential, split arrays, the
-// index's contributions (w |expm1 L|, w L, w out) to the scalars.
+// index's contributions (w |expm1 L|, w L, w out) to the scalars.  The index's
+// shift, weight and log-weight are passed as values (they may be loaded ahead).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void finish_index(float R, double S, int idx, const Prob& P,
-                                             const double* __restrict__ shift,
-                                             const double* __restrict__ w,
-                                             const double* __restrict__ logw,
-                                             double* __restrict__ out, Split so,
-                                             float* __restrict__ Lout, double acc[3],
-                                             int* numeric) {
+__device__ __forceinline__ void finish_index_v(float R, double S, int idx, const Prob& P,
+                                               double sh, double wi, double logwi,
+                                               double* __restrict__ out, Split so,
+                                               float* __restrict__ Lout, double acc[3],
+                                               int* numeric) {
   float L = R * kLn2 + log_sum(S);
-  const double sh = shift[idx];
   double o = sh - P.eps * (double)L;
   if (!isfinite(o) || !(S > 0.0) || fabs(o) > P.pot_bound) {
     atomicAdd(numeric, 1);
@@ -30,17 +28,27 @@ __device__ __forceinline__ void finish_index(float R, double S, int idx, const P
   if (so.A) {
     double hi;
     float lo;
-    split_grid(o + P.eps * logw[idx], P.qscale, P.qinv, hi, lo);
+    split_grid(o + P.eps * logwi, P.qscale, P.qinv, hi, lo);
     so.A[idx] = (float)(hi + (double)P.M);
     so.AL[idx] = lo;
     split_grid(o, P.qscale, P.qinv, hi, lo);
     so.K[idx] = (float)((double)P.M - hi);
     so.KL[idx] = lo;
   }
-  const double wi = w[idx];
   acc[0] = wi * (double)fabsf(expm1f(L));
   acc[1] = wi * (double)L;
   acc[2] = wi * o;
+}
+
+__device__ __forceinline__ void finish_index(float R, double S, int idx, const Prob& P,
+                                             const double* __restrict__ shift,
+                                             const double* __restrict__ w,
+                                             const double* __restrict__ logw,
+                                             double* __restrict__ out, Split so,
+                                             float* __restrict__ Lout, double acc[3],
+                                             int* numeric) {
+  finish_index_v(R, S, idx, P, shift[idx], w[idx], so.A ? logw[idx] : 0.0, out, so, Lout, acc,
+                 numeric);
 }
 
 // Block-wide deterministic sum of 3 doubles; result valid in thread 0.

@@ -212,8 +212,10 @@ __global__ void __launch_bounds__(256) eig_small_kernel(int p, int l, int mode,
                                                         double* __restrict__ theta_out,
                                                         double* __restrict__ resid_out,
                                                         int* __restrict__ fail_out) {
-  __shared__ float A[kMaxP * kMaxP];
-  __shared__ float Q[kMaxP * kMaxP];
+  // A and Q use an odd row stride (pe + 1): the column rotations walk down
+  // columns, and an even stride would put many rows in one shared-memory bank
+  __shared__ float A[kMaxP * (kMaxP + 1)];
+  __shared__ float Q[kMaxP * (kMaxP + 1)];
   __shared__ float G[kMaxP * kMaxP];
   __shared__ float tmp[kMaxP * kMaxP];
   __shared__ float rc[kMaxP], rs[kMaxP], cf[kMaxP], qc[kMaxP];
@@ -224,11 +226,12 @@ __global__ void __launch_bounds__(256) eig_small_kernel(int p, int l, int mode,
   __shared__ int s_stop, s_fail;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int pe = (p + 1) & ~1;   // padded even size for the circle ordering
+  const int ps = pe + 1;         // row stride of A and Q
   for (int e = tid; e < pe * pe; e += nt) {
     const int r = e / pe, q = e - r * pe;
     const bool in = r < p && q < p;
-    A[e] = (mode == 1 && in) ? (float)(0.5 * (T[r * p + q] + T[q * p + r])) : 0.f;
-    Q[e] = (r == q) ? 1.f : 0.f;
+    A[r * ps + q] = (mode == 1 && in) ? (float)(0.5 * (T[r * p + q] + T[q * p + r])) : 0.f;
+    Q[r * ps + q] = (r == q) ? 1.f : 0.f;
   }
   for (int k = tid; k < p; k += nt) cf[k] = (float)c[k];
   if (tid == 0) s_fail = 0;
@@ -238,8 +241,9 @@ __global__ void __launch_bounds__(256) eig_small_kernel(int p, int l, int mode,
       float loc = 0.f, dia = 0.f;
       for (int e = tid; e < pe * pe; e += nt) {
         const int r = e / pe, q = e - r * pe;
-        if (r != q) loc += A[e] * A[e];
-        else dia += A[e] * A[e];
+        const float v = A[r * ps + q];
+        if (r != q) loc += v * v;
+        else dia += v * v;
       }
       loc = warp_sum_f(loc);
       dia = warp_sum_f(dia);
@@ -260,10 +264,10 @@ __global__ void __launch_bounds__(256) eig_small_kernel(int p, int l, int mode,
           const int k = min(a, b), q = max(a, b);
           pairs[2 * tid] = k;
           pairs[2 * tid + 1] = q;
-          const float akq = A[k * pe + q];
+          const float akq = A[k * ps + q];
           float cth = 1.f, sth = 0.f;
           if (fabsf(akq) > 1e-30f) {
-            const float tau = (A[q * pe + q] - A[k * pe + k]) / (2.f * akq);
+            const float tau = (A[q * ps + q] - A[k * ps + k]) / (2.f * akq);
             const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
             cth = rsqrtf(1.f + t * t);
             sth = t * cth;
@@ -276,26 +280,26 @@ __global__ void __launch_bounds__(256) eig_small_kernel(int p, int l, int mode,
           const int pr = e / pe, col = e - pr * pe;
           const int k = pairs[2 * pr], q = pairs[2 * pr + 1];
           const float cth = rc[pr], sth = rs[pr];
-          const float ak = A[k * pe + col], aq = A[q * pe + col];
-          A[k * pe + col] = cth * ak - sth * aq;
-          A[q * pe + col] = sth * ak + cth * aq;
+          const float ak = A[k * ps + col], aq = A[q * ps + col];
+          A[k * ps + col] = cth * ak - sth * aq;
+          A[q * ps + col] = sth * ak + cth * aq;
         }
         __syncthreads();
         for (int e = tid; e < (pe / 2) * pe; e += nt) {     // columns: A <- A J, Q <- Q J
           const int pr = e / pe, row = e - pr * pe;
           const int k = pairs[2 * pr], q = pairs[2 * pr + 1];
           const float cth = rc[pr], sth = rs[pr];
-          const float ak = A[row * pe + k], aq = A[row * pe + q];
-          A[row * pe + k] = cth * ak - sth * aq;
-          A[row * pe + q] = sth * ak + cth * aq;
-          const float qk = Q[row * pe + k], qq = Q[row * pe + q];
-          Q[row * pe + k] = cth * qk - sth * qq;
-          Q[row * pe + q] = sth * qk + cth * qq;
+          const float ak = A[row * ps + k], aq = A[row * ps + q];
+          A[row * ps + k] = cth * ak - sth * aq;
+          A[row * ps + q] = sth * ak + cth * aq;
+          const float qk = Q[row * ps + k], qq = Q[row * ps + q];
+          Q[row * ps + k] = cth * qk - sth * qq;
+          Q[row * ps + q] = sth * qk + cth * qq;
         }
         __syncthreads();
       }
     }
-    for (int k = tid; k < p; k += nt) th[k] = A[k * pe + k];
+    for (int k = tid; k < p; k += nt) th[k] = A[k * ps + k];
     __syncthreads();
     for (int k = tid; k < p; k += nt) {
       int rank = 0;
@@ -305,7 +309,7 @@ __global__ void __launch_bounds__(256) eig_small_kernel(int p, int l, int mode,
     __syncthreads();
     for (int e = tid; e < p * p; e += nt) {
       const int r = e / p, q = e - r * p;
-      tmp[r * p + q] = Q[r * pe + order[q]];
+      tmp[r * p + q] = Q[r * ps + order[q]];
     }
     __syncthreads();
     for (int e = tid; e < p * p; e += nt) Q[e] = tmp[e];

@@ -202,6 +202,24 @@ def test_solve_small_parity(pkg, ell):
     assert abs(res["q_dual"] - ev["q_dual"]) <= 1e-9 + 1e-6 * abs(ev["q_dual"])
 
 
+def test_plain_sinkhorn_many_tiles(pkg):
+    """Plain Sinkhorn over a cost of many tiles with ragged edges (the
+    cooperative iteration loop when the rows are 16-byte aligned): the oracle
+    scores the returned pair, and the iteration count of the last level equals
+    the oracle's Sinkhorn on the same float32 cost from the same start up to
+    the rounding of the last test."""
+    prob = W.gaussian_mixture(640, 804, seed=9, eps=1e-2)
+    f, g, res = pkg.solve(prob, tol=1e-6, ell=0, eps_start=0.0, max_iter=100000)
+    assert res["return_status"] == pkg.EOT_OK, res
+    C, ev = _score(prob, f, g, prob.eps)
+    assert ev["l1"] <= 1e-6, ev
+    ref = O.sinkhorn(C, prob.a, prob.b, prob.eps, tol=1e-6, max_iter=100000)
+    assert abs(res["iters"] - ref.iters) <= max(3, ref.iters // 50), (res["iters"], ref.iters)
+    fr, gr = O.gauge_normalize(ref.f, ref.g, prob.a, prob.b)
+    _, rho2 = O.spectral_modes_dense(ref.f, ref.g, C, prob.a, prob.b, prob.eps, 1)
+    assert np.abs(f - fr).max() <= prob.eps * 2e-6 / (1 - rho2[0]) + 1e-5 * prob.eps
+
+
 def test_solve_sknr_beats_sk_iterations(pkg):
     prob = W.gaussian_mixture(512, 512, seed=0, eps=1e-3)
     _, _, sk = pkg.solve(prob, tol=1e-6, ell=0, eps_start=1e-1, max_iter=100000)
