@@ -58,8 +58,13 @@ typedef enum { EOT_MEM_HOST = 0, EOT_MEM_DEVICE = 1 } eot_mem;
  *  FP32: float32 stored cost; float32 exponentials and sums; potentials kept in
  *        float64 and the exponent f_i + g_j - C_ij formed without rounding error
  *        before the division by eps (so the marginal error can reach ~1e-7).
- *  SPLIT_TC: cost formed on the fly from X, Y on the tensor cores (reserved;
- *        returns EOT_EINVAL in this version). */
+ *  SPLIT_TC: no stored cost: every pass forms C_ij = |x_i|^2 + |y_j|^2 - 2 x_i.y_j
+ *        from X, Y (float32, 1 <= d <= 64) with the Gram products on the tensor
+ *        cores (TF32 high + low parts, three products, float32 accumulation).
+ *        The marginal test is met against this cost, which differs from the
+ *        exact one by the float32 error of a dot product (|dC| ~ 1e-6 for unit
+ *        scale points): potentials within ~1e-3 eps of the exact iterates.
+ *        Plain Sinkhorn only (ell = 0: EOT_EINVAL otherwise). */
 typedef enum { EOT_PREC_FP64 = 0, EOT_PREC_FP32 = 1, EOT_PREC_SPLIT_TC = 2 } eot_prec;
 
 /* Semi-dual Hessian used by the Newton step (Eq. d2Q_semi):

@@ -63,6 +63,12 @@ void init_stream_attributes();
 int stream_ctas_per_sm();
 void stream_plan(int n, int m, bool col, int ctas, int* grid, int* slots);
 cudaError_t launch_sk_coop(const Prob* dP, const Prob& hP, int max_body, cudaStream_t s);
+void init_gram_attributes();
+int gram_smem_bytes();
+void gram_plan(int nO, int nR, int ctas, int* grid, int* slots);
+cudaError_t launch_gram_pass(const Prob* dP, const Prob& hP, bool col, int mode, cudaStream_t s);
+cudaError_t launch_gram_split(const float* X, int n, int d, double scale, float* Xh, float* Xl,
+                              double* nrm, unsigned* bad, cudaStream_t s);
 
 __global__ void wgram_partial_kernel(const float*, const float*, const double*, int, int, int,
                                      const double*, const float*, double*, double*, const State*,
@@ -126,6 +132,7 @@ struct DeviceCtx {
   cudaStream_t stream = nullptr;
   bool cond_ok = true;   // graph conditional nodes usable
   int stream_ctas = 0;   // CTAs of one wave of the staged stream passes
+  int gram_ctas = 0;     // CTAs of one wave of the on-the-fly cost passes
 };
 
 // One context (and stream) per calling thread and device, so that solves issued
@@ -148,6 +155,8 @@ static eot_status get_ctx(DeviceCtx** out) {
   init_mma_attributes();
   init_stream_attributes();
   c->stream_ctas = stream_ctas_per_sm() * c->nsm;
+  init_gram_attributes();
+  c->gram_ctas = c->nsm;   // one CTA per SM (shared memory and TMEM)
   const char* e = getenv("EOT_HOST_LOOP");
   c->cond_ok = !(e && e[0] == '1');
   *out = c.get();
@@ -192,6 +201,24 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
+// 2-D map of an n x 64 float array with boxes of 32 x 128 floats and the
+// 128-byte swizzle (the tensor-core operand layout of the on-the-fly cost).
+static eot_status encode_operand_map(CUtensorMap* map, const float* ptr, int rows) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return fail(EOT_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+  const cuuint64_t dims[2] = {64, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {64 * sizeof(float)};
+  const cuuint32_t box[2] = {32, 128};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(ptr), dims,
+                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return fail(EOT_ECUDA, "cuTensorMapEncodeTiled failed (code " + std::to_string((int)r) + ")");
+  return EOT_OK;
+}
+
 // Encode P.tmC for P.C when the stream passes are in use.
 static eot_status encode_cost_map(Prob& P) {
   if (P.sk_gcol <= 0 && P.sk_grow <= 0) return EOT_OK;
@@ -220,6 +247,10 @@ struct Solver {
   int n = 0, m = 0, ell = 0, p = 0;
   bool own_cost = false;
   bool f64 = false;           // float64 passes (EOT_PREC_FP64)
+  bool gram = false;          // on-the-fly cost on the tensor cores (EOT_PREC_SPLIT_TC)
+  float *Xh = nullptr, *Xl = nullptr, *Yh = nullptr, *Yl = nullptr;   // TF32 parts, x 64
+  double *nX = nullptr, *nY = nullptr;
+  int gm_grow = 0, gm_gcol = 0, gm_slots_row = 1, gm_slots_col = 1;
   // tilings
   int nstripe = 1, rows_per_stripe = 0, ncolblk = 0;
   int nseg = 1, cols_per_seg = 0, nrowblk = 0;
@@ -287,7 +318,10 @@ struct Solver {
     mm_ncolblk = ceil_div(m, 128);
     sk_gcol = sk_grow = 0;
     sk_slots_col = sk_slots_row = 1;
-    if (ctx->stream_ctas > 0 && m % 4 == 0) {
+    if (gram) {
+      gram_plan(n, m, ctx->gram_ctas, &gm_grow, &gm_slots_row);
+      gram_plan(m, n, ctx->gram_ctas, &gm_gcol, &gm_slots_col);
+    } else if (ctx->stream_ctas > 0 && m % 4 == 0) {
       stream_plan(n, m, true, ctx->stream_ctas, &sk_gcol, &sk_slots_col);
       stream_plan(n, m, false, ctx->stream_ctas, &sk_grow, &sk_slots_row);
     }
@@ -332,11 +366,15 @@ struct Solver {
     hP.logb = A.take<double>(m);
     for (int k = 0; k < 2; ++k) {
       hP.f[k] = A.take<double>(n);
-      hP.rs[k] = Split{A.take<float>(n), A.take<float>(n), A.take<float>(n), A.take<float>(n)};
+      const size_t np = (size_t)ceil_div(n, 128) * 128;   // padded: 128-float copies
+      hP.rs[k] = Split{A.take<float>(np), A.take<float>(np), A.take<float>(np), A.take<float>(np),
+                       nullptr};
     }
     for (int k = 0; k < 3; ++k) {
       hP.g[k] = A.take<double>(m);
-      hP.cs[k] = Split{A.take<float>(m), A.take<float>(m), A.take<float>(m), A.take<float>(m)};
+      const size_t mp = (size_t)ceil_div(m, 128) * 128;
+      hP.cs[k] = Split{A.take<float>(mp), A.take<float>(mp), A.take<float>(mp), A.take<float>(mp),
+                       nullptr};
     }
     hP.Lrow = A.take<float>(n);
     hP.Lcol = A.take<float>(m);
@@ -363,6 +401,30 @@ struct Solver {
       hP.part64_row = nullptr;
     }
     hP.gcnt = A.take<unsigned>(4);
+    hP.gram = gram ? 1 : 0;
+    if (gram) {
+      Xh = A.take<float>((size_t)n * 64);
+      Xl = A.take<float>((size_t)n * 64);
+      Yh = A.take<float>((size_t)m * 64);
+      Yl = A.take<float>((size_t)m * 64);
+      nX = A.take<double>(n);
+      nY = A.take<double>(m);
+      hP.nX = nX;
+      hP.nY = nY;
+      for (int k = 0; k < 2; ++k) hP.rs[k].nrm = nX;
+      for (int k = 0; k < 3; ++k) hP.cs[k].nrm = nY;
+      const int tO = ceil_div(n, 128), tR = ceil_div(m, 128);
+      hP.gm_grow = gm_grow;
+      hP.gm_gcol = gm_gcol;
+      hP.gm_slots_row = gm_slots_row;
+      hP.gm_slots_col = gm_slots_col;
+      hP.gm_part_row = A.take<float2>((size_t)tO * gm_slots_row * 128);
+      hP.gm_part_col = A.take<float2>((size_t)tR * gm_slots_col * 128);
+      hP.gm_cnt_row = A.take<unsigned>(tO);
+      hP.gm_cnt_col = A.take<unsigned>(tR);
+      hP.gm_acc_row = A.take<double>((size_t)tO * 4);
+      hP.gm_acc_col = A.take<double>((size_t)tR * 4);
+    }
     hP.sk_gcol = sk_gcol;
     hP.sk_grow = sk_grow;
     hP.sk_slots_col = sk_slots_col;
@@ -419,9 +481,10 @@ struct Solver {
     }
   }
 
-  eot_status init(DeviceCtx* c, int n_, int m_, int d, int ell_, int p_, bool own, bool f64_) {
+  eot_status init(DeviceCtx* c, int n_, int m_, int d, int ell_, int p_, bool own, int prec) {
     ctx = c;
-    f64 = f64_;
+    f64 = prec == EOT_PREC_FP64;
+    gram = prec == EOT_PREC_SPLIT_TC;
     n = n_;
     m = m_;
     ell = ell_;
@@ -524,9 +587,11 @@ struct Solver {
 
   // ---- loop bodies ----
   cudaError_t pass_col(int mode, cudaStream_t s) {
+    if (gram) return launch_gram_pass(dP, hP, true, mode, s);
     return f64 ? launch_col64(dP, hP, mode, s4_args(), s) : launch_col_pass(dP, hP, mode, s);
   }
   cudaError_t pass_row(int mode, cudaStream_t s) {
+    if (gram) return launch_gram_pass(dP, hP, false, mode, s);
     return f64 ? launch_row64(dP, hP, mode, s) : launch_row_pass(dP, hP, mode, s);
   }
   // level-start derived arrays of buffer-0 potentials (float splits; float64
@@ -637,7 +702,7 @@ struct Solver {
   bool coop_ok = true;
   eot_status run_sk(int max_iter, int graph_cap, bool* used_coop) {
     *used_coop = false;
-    if (coop_ok && !f64 && hP.sk_gcol > 0 && hP.sk_gcol == hP.sk_grow && m % 4 == 0 &&
+    if (coop_ok && !f64 && !gram && hP.sk_gcol > 0 && hP.sk_gcol == hP.sk_grow && m % 4 == 0 &&
         (reinterpret_cast<uintptr_t>(hP.C) & 15u) == 0) {
       const cudaError_t e = launch_sk_coop(dP, hP, max_iter + 4, ctx->stream);
       if (e == cudaSuccess) {
@@ -670,10 +735,10 @@ struct Solver {
 // Solver cache: repeated solves of one shape reuse buffers and graphs.
 // ---------------------------------------------------------------------------
 struct CacheKey {
-  int dev, n, m, d, ell, p, own, f64;
+  int dev, n, m, d, ell, p, own, prec;
   bool operator<(const CacheKey& o) const {
-    return std::tie(dev, n, m, d, ell, p, own, f64) <
-           std::tie(o.dev, o.n, o.m, o.d, o.ell, o.p, o.own, o.f64);
+    return std::tie(dev, n, m, d, ell, p, own, prec) <
+           std::tie(o.dev, o.n, o.m, o.d, o.ell, o.p, o.own, o.prec);
   }
 };
 static thread_local std::map<CacheKey, std::unique_ptr<Solver>> t_cache;
@@ -683,8 +748,8 @@ static int mode_block(int n, int ell, int oversample) {
 }
 
 static eot_status get_solver(DeviceCtx* ctx, int n, int m, int d, int ell, int p, bool own,
-                             Solver** out, bool f64 = false) {
-  CacheKey key{ctx->dev, n, m, d, ell, p, own ? 1 : 0, f64 ? 1 : 0};
+                             Solver** out, int prec = EOT_PREC_FP32) {
+  CacheKey key{ctx->dev, n, m, d, ell, p, own ? 1 : 0, prec};
   auto it = t_cache.find(key);
   if (it != t_cache.end()) {
     *out = it->second.get();
@@ -692,7 +757,7 @@ static eot_status get_solver(DeviceCtx* ctx, int n, int m, int d, int ell, int p
   }
   if (t_cache.size() >= 4) t_cache.clear();
   auto s = std::make_unique<Solver>();
-  eot_status st = s->init(ctx, n, m, d, ell, p, own, f64);
+  eot_status st = s->init(ctx, n, m, d, ell, p, own, prec);
   if (st != EOT_OK) return st;
   *out = s.get();
   t_cache[key] = std::move(s);
@@ -701,15 +766,16 @@ static eot_status get_solver(DeviceCtx* ctx, int n, int m, int d, int ell, int p
 
 // Device bytes a solver of this shape allocates (admission control).
 static size_t solver_footprint(DeviceCtx* ctx, int n, int m, int d, int ell, int p,
-                               bool f64 = false) {
+                               int prec = EOT_PREC_FP32) {
   Solver tmp;
   tmp.ctx = ctx;
-  tmp.f64 = f64;
+  tmp.f64 = prec == EOT_PREC_FP64;
+  tmp.gram = prec == EOT_PREC_SPLIT_TC;
   tmp.n = n;
   tmp.m = m;
   tmp.ell = ell;
   tmp.p = p;
-  tmp.own_cost = true;
+  tmp.own_cost = !tmp.gram;
   tmp.plan_tiles();
   Arena A;
   tmp.layout(A, d);
@@ -751,8 +817,14 @@ static eot_status validate(const eot_problem* pr, const eot_options* o) {
   if (hasXY && pr->d < 1) return fail(EOT_EINVAL, "d must be >= 1 with point clouds");
   if (hasC && pr->d != 0) return fail(EOT_EINVAL, "d must be 0 when C is given");
   if (pr->mem != EOT_MEM_HOST && pr->mem != EOT_MEM_DEVICE) return fail(EOT_EINVAL, "bad mem");
-  if (o->prec != EOT_PREC_FP32 && o->prec != EOT_PREC_FP64)
-    return fail(EOT_EINVAL, "EOT_PREC_SPLIT_TC is not implemented in this build");
+  if (o->prec != EOT_PREC_FP32 && o->prec != EOT_PREC_FP64 && o->prec != EOT_PREC_SPLIT_TC)
+    return fail(EOT_EINVAL, "unknown prec");
+  if (o->prec == EOT_PREC_SPLIT_TC) {
+    if (pr->d < 1 || pr->d > 64 || !pr->X || !pr->Y)
+      return fail(EOT_EINVAL, "EOT_PREC_SPLIT_TC needs point clouds X, Y with 1 <= d <= 64");
+    if (o->ell > 0)
+      return fail(EOT_EINVAL, "SK-NR (ell > 0) with the on-the-fly cost is not implemented");
+  }
   if (!(o->tol > 0.0)) return fail(EOT_EINVAL, "tol must be > 0");
   if (o->max_iter < 1) return fail(EOT_EINVAL, "max_iter must be >= 1");
   if (o->ell < 0 || o->ell > kMaxK) return fail(EOT_EINVAL, "ell must be in [0, 64]");
@@ -777,11 +849,12 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   const int n = pr->n, m = pr->m, d = pr->d;
   const bool dev = pr->mem == EOT_MEM_DEVICE;
   const bool f64 = o->prec == EOT_PREC_FP64;
-  const bool borrowC = !f64 && dev && d == 0 && !pr->normalize_cost &&
+  const bool gram = o->prec == EOT_PREC_SPLIT_TC;
+  const bool borrowC = !f64 && !gram && dev && d == 0 && !pr->normalize_cost &&
                        (reinterpret_cast<uintptr_t>(pr->C) & 15u) == 0;
   Solver* S = nullptr;
-  eot_status ss = get_solver(ctx, n, m, d, o->ell, mode_block(n, o->ell, o->oversample), !borrowC,
-                             &S, f64);
+  eot_status ss = get_solver(ctx, n, m, d, o->ell, mode_block(n, o->ell, o->oversample),
+                             !borrowC && !gram, &S, o->prec);
   if (ss != EOT_OK) return ss;
   cudaStream_t s = o->stream ? reinterpret_cast<cudaStream_t>(o->stream) : ctx->stream;
   // the solver's graphs are captured on the context stream; user streams are
@@ -811,7 +884,30 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   const int gb = std::min<long long>(((long long)nm + 255) / 256, 8LL * ctx->nsm);
   const float* Cdev = nullptr;
   double* C64 = const_cast<double*>(S->hP.C64);
-  if (d > 0) {
+  if (gram) {
+    // on-the-fly cost: TF32 parts and squared norms of the (optionally
+    // rescaled, C / max C = |x/s - y/s|^2 with s = sqrt(max C)) points
+    CUDA_TRY(cudaMemcpyAsync(S->X, pr->X, (size_t)n * d * sizeof(float), kin, s));
+    CUDA_TRY(cudaMemcpyAsync(S->Y, pr->Y, (size_t)m * d * sizeof(float), kin, s));
+    double scale = 1.0;
+    if (pr->normalize_cost) {
+      cost_max_kernel<<<gb, 256, 0, s>>>(n, m, d, S->X, S->Y, S->cmax64);
+      unsigned long long bits = 0;
+      CUDA_TRY(cudaMemcpyAsync(&bits, S->cmax64, sizeof(bits), cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaStreamSynchronize(s));
+      double cm;
+      std::memcpy(&cm, &bits, sizeof(cm));
+      if (cm > 0.0 && std::isfinite(cm)) scale = 1.0 / std::sqrt(cm);
+    }
+    CUDA_TRY(launch_gram_split(S->X, n, d, scale, S->Xh, S->Xl, S->nX, S->stats + 1, s));
+    CUDA_TRY(launch_gram_split(S->Y, m, d, scale, S->Yh, S->Yl, S->nY, S->stats + 1, s));
+    // largest squared norm (the grid of the potentials' split, below)
+    CUDA_TRY(cudaMemsetAsync(S->cmax64, 0, sizeof(unsigned long long), s));
+    cost_stats_f64_kernel<<<std::max(1, std::min(ceil_div(std::max(n, m), 256), 4 * ctx->nsm)),
+                            256, 0, s>>>((size_t)n, S->nX, S->cmax64, S->stats + 1);
+    cost_stats_f64_kernel<<<std::max(1, std::min(ceil_div(std::max(n, m), 256), 4 * ctx->nsm)),
+                            256, 0, s>>>((size_t)m, S->nY, S->cmax64, S->stats + 1);
+  } else if (d > 0) {
     CUDA_TRY(cudaMemcpyAsync(S->X, pr->X, (size_t)n * d * sizeof(float), kin, s));
     CUDA_TRY(cudaMemcpyAsync(S->Y, pr->Y, (size_t)m * d * sizeof(float), kin, s));
     if (pr->normalize_cost) cost_max_kernel<<<gb, 256, 0, s>>>(n, m, d, S->X, S->Y, S->cmax64);
@@ -837,7 +933,7 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
     CUDA_TRY(cudaMemcpyAsync(S->Cbuf, pr->C, nm * sizeof(float), kin, s));
     Cdev = S->Cbuf;
   }
-  cost_stats_kernel<<<gb, 256, 0, s>>>(nm, Cdev, S->stats, S->stats + 1);
+  if (!gram) cost_stats_kernel<<<gb, 256, 0, s>>>(nm, Cdev, S->stats, S->stats + 1);
   unsigned hstats[4];
   CUDA_TRY(cudaMemcpyAsync(hstats, S->stats, sizeof(hstats), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
@@ -846,6 +942,13 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   float cmaxf;
   std::memcpy(&cmaxf, &hstats[0], sizeof(float));
   double cmax = cmaxf;
+  double nmax = 0.0;   // on-the-fly cost: largest squared norm
+  if (gram) {
+    unsigned long long bits = 0;
+    CUDA_TRY(cudaMemcpy(&bits, S->cmax64, sizeof(bits), cudaMemcpyDeviceToHost));
+    std::memcpy(&nmax, &bits, sizeof(nmax));
+    cmax = 4.0 * nmax;   // bound of the cost |x - y|^2 <= 2 |x|^2 + 2 |y|^2
+  }
   if (d == 0 && pr->normalize_cost && !f64) {
     if (cmax > 0.0) {
       cost_scale_kernel<<<gb, 256, 0, s>>>(nm, Cdev, cmax, S->Cbuf);
@@ -871,18 +974,29 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   }
   const double R = 4.0 * (cmax + fmax + 40.0 * eps0) + 1e-30;
   int q = 22 - (int)std::ceil(std::log2(R));
+  if (gram) {
+    // grid of k2 (p - |pt|^2) (log2 units) at the smallest eps: the sum of two
+    // grid parts must stay exact, |P| < 2^(22 - q) with room
+    const double k2max = 1.0 / (pr->eps * std::log(2.0));
+    const double Rg = 4.0 * k2max * (cmax + nmax + fmax + 40.0 * eps0) + 1e-30;
+    q = 22 - (int)std::ceil(std::log2(Rg));
+  }
   q = std::max(-100, std::min(q, 60));
   Prob& P = S->hP;
   P.C = Cdev;
   P.qscale = std::ldexp(1.0, q);
   P.qinv = std::ldexp(1.0, -q);
   P.M = (float)(1.5 * std::ldexp(1.0, 23 - q));
-  P.pot_bound = std::ldexp(1.0, 22 - q) / 2.0 - cmax;
+  P.pot_bound = gram ? 1e300 : std::ldexp(1.0, 22 - q) / 2.0 - cmax;
   P.eps = eps0;
   P.k2 = (float)(1.0 / (eps0 * std::log(2.0)));
   P.st = S->dSt;
   {
-    const eot_status me = encode_cost_map(P);
+    eot_status me = encode_cost_map(P);
+    if (me == EOT_OK && gram) me = encode_operand_map(&P.tmXh, S->Xh, n);
+    if (me == EOT_OK && gram) me = encode_operand_map(&P.tmXl, S->Xl, n);
+    if (me == EOT_OK && gram) me = encode_operand_map(&P.tmYh, S->Yh, m);
+    if (me == EOT_OK && gram) me = encode_operand_map(&P.tmYl, S->Yl, m);
     if (me != EOT_OK) return me;
   }
   CUDA_TRY(cudaMemcpyAsync(S->dP, &P, sizeof(Prob), cudaMemcpyHostToDevice, s));
@@ -1716,7 +1830,7 @@ eot_status eot_server_submit(eot_server* srv, const eot_problem* prob, uint64_t 
   if (cs != EOT_OK) return cs;
   r->footprint = eotk::solver_footprint(ctx, n, m, d, srv->opt.ell,
                                         eotk::mode_block(n, srv->opt.ell, srv->opt.oversample),
-                                        srv->opt.prec == EOT_PREC_FP64);
+                                        srv->opt.prec);
   {
     std::lock_guard<std::mutex> lk(srv->mu);
     r->ticket = srv->next++;

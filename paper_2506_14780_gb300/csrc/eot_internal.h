@@ -63,6 +63,11 @@ struct Split {
   float* AL;  // L(p + eps log w)
   float* K;   // M - H(p)                 (output-side shift use)
   float* KL;  // L(p)
+  // On-the-fly cost (EOT_PREC_SPLIT_TC): squared norms |pt|^2 of the side's
+  // points; then K + KL = k2 (p - |pt|^2) split on the 2^-q grid (log2 units,
+  // the same split for both sides, so that K_i + K_j is exact), A = the
+  // side's weight (float) and AL = 0.
+  const double* nrm;
 };
 
 // Everything the pass kernels need for one problem; lives in device memory.
@@ -104,6 +109,20 @@ struct Prob {
   double* sk_acc_col;      // [ceil(m/32)][4] (per 128-column block, or per 32-column unit)
   double* sk_acc_row;      // [ceil(n/32)][4]
   unsigned* gbar;          // [2] grid barrier of the cooperative Sinkhorn loop
+  // on-the-fly cost (EOT_PREC_SPLIT_TC): C_ij = |x_i|^2 + |y_j|^2 - 2 x_i.y_j
+  // with the Gram products on the tensor cores (3xTF32, float32 accumulation)
+  int gram;                // 1 in that mode
+  CUtensorMap tmXh, tmXl;  // TF32 high / low parts of X (n x 64, zero padded)
+  CUtensorMap tmYh, tmYl;  // ... of Y (m x 64)
+  const double* nX;        // |x_i|^2 (n)
+  const double* nY;        // |y_j|^2 (m)
+  int gm_grow, gm_gcol, gm_slots_row, gm_slots_col;
+  float2* gm_part_row;     // [ceil(n/128)][gm_slots_row][128]
+  float2* gm_part_col;     // [ceil(m/128)][gm_slots_col][128]
+  unsigned* gm_cnt_row;    // [ceil(n/128)]
+  unsigned* gm_cnt_col;    // [ceil(m/128)]
+  double* gm_acc_row;      // [ceil(n/128)][4]
+  double* gm_acc_col;      // [ceil(m/128)][4]
   State* st;
   // SK-NR
   int ell;                 // number of modes (0: none)

@@ -25,7 +25,15 @@ __device__ __forceinline__ void finish_index_v(float R, double S, int idx, const
   }
   if (out) out[idx] = o;
   if (Lout) Lout[idx] = L;
-  if (so.A) {
+  if (so.A && so.nrm) {
+    double hi;
+    float lo;
+    split_grid((double)P.k2 * (o - so.nrm[idx]), P.qscale, P.qinv, hi, lo);
+    so.A[idx] = (float)wi;
+    so.AL[idx] = 0.f;
+    so.K[idx] = (float)hi;
+    so.KL[idx] = lo;
+  } else if (so.A) {
     double hi;
     float lo;
     split_grid(o + P.eps * logwi, P.qscale, P.qinv, hi, lo);

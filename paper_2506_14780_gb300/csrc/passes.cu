@@ -431,6 +431,16 @@ __global__ void split_kernel(const Prob* __restrict__ PP, const double* __restri
   const Prob& P = *PP;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < len; i += gridDim.x * blockDim.x) {
     const double v = p[i];
+    if (so.nrm) {   // on-the-fly cost
+      double hi;
+      float lo;
+      split_grid((double)P.k2 * (v - so.nrm[i]), P.qscale, P.qinv, hi, lo);
+      so.A[i] = (float)exp(logw[i]);
+      so.AL[i] = 0.f;
+      so.K[i] = (float)hi;
+      so.KL[i] = lo;
+      continue;
+    }
     double hi;
     float lo;
     split_grid(v + P.eps * logw[i], P.qscale, P.qinv, hi, lo);
