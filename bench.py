@@ -54,6 +54,8 @@ def parse():
                     help="one SK-NR solve per step, no Sinkhorn comparison (for ncu)")
     ap.add_argument("--sk-steps", type=int, default=None)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--quick", action="store_true",
+                    help="skip the additional configurations (on-the-fly cost, batch, serving)")
     return ap.parse_args()
 
 
@@ -246,6 +248,8 @@ def run_ours(args):
         out["e2e"] = {"value": round(statistics.median(e2e), 4), "unit": "ms",
                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(8 * (N + M))}
         out["roofline"] = roofline(pkg, torch, p, f, g, stream)
+        if not args.quick:
+            out["configs_extra"] = extras(pkg, torch, stream)
     if rank == 0 and not args.no_cpu and not args.profile:
         out["cpu_baseline"] = cpu_baseline(prob, last["total_iters"])
     if ws > 1:
@@ -254,21 +258,20 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
 
 
-def roofline(pkg, torch, p, f, g, stream):
-    """Dominant kernel of the solve: the stored-cost log-sum-exp passes.  Their
-    average duration is measured live: two single-level Sinkhorn solves at
-    eps = 1e-3 from the converged potentials with a fixed number of iterations
-    (tolerance unreachable) differ by exactly 2 * (R2 - R1) passes (one row and
-    one column pass per iteration), timed with CUDA events on this stream."""
-    peaks = {}
-    if os.path.exists(PEAKS_FILE):
-        with open(PEAKS_FILE) as fh:
-            peaks = json.load(fh)
-    hbm = peaks.get("hbm_gbs", 6800.0)
+def stage(msg):
+    """Progress note on stderr (the JSON line goes to stdout)."""
+    print(f"[bench] {msg}", file=sys.stderr, flush=True)
+
+
+def per_pass_ms(pkg, torch, p, f, g, stream, r1, r2, **kw):
+    """Average time of one log-sum-exp half-step: two single-level Sinkhorn
+    solves from the same potentials with a fixed number of iterations (the
+    tolerance is unreachable) differ by exactly 2 (r2 - r1) half-steps; CUDA
+    events on this stream, best of three."""
     fi = f.clone()
     ms = {}
-    for R in (100, 400):
-        o = options(pkg, 0, stream.cuda_stream, tol=1e-300, max_iter=R, eps_start=0.0)
+    for R in (r1, r2):
+        o = options(pkg, 0, stream.cuda_stream, tol=1e-300, max_iter=R, eps_start=0.0, **kw)
         p2 = type(p).from_buffer_copy(p)
         p2.f_init = fi.data_ptr()
         best = None
@@ -278,19 +281,154 @@ def roofline(pkg, torch, p, f, g, stream):
             st, res = pkg.eot_solve(p2, o, f, g)
             e1.record()
             torch.cuda.synchronize()
+            if st < 0:
+                raise RuntimeError(pkg.last_error())
             t = e0.elapsed_time(e1)
             best = t if best is None else min(best, t)
         ms[R] = best
-    per_pass_ms = (ms[400] - ms[100]) / (2 * 300)
-    bytes_per_pass = 4.0 * N * M
-    achieved = bytes_per_pass / (per_pass_ms * 1e-3) / 1e9
-    return {"kernel": "col_pass_kernel/row_pass_kernel (stored-cost LSE half-step)",
+    return (ms[r2] - ms[r1]) / (2 * (r2 - r1))
+
+
+def load_peaks():
+    if os.path.exists(PEAKS_FILE):
+        with open(PEAKS_FILE) as fh:
+            return json.load(fh)
+    return {}
+
+
+def roofline(pkg, torch, p, f, g, stream):
+    """Roofline of the stored-cost log-sum-exp half-steps (the Sinkhorn
+    kernels: sk_coop_kernel for plain Sinkhorn, stream_pass_kernel for the
+    half-steps of SK-NR).  A half-step reads the n x m float32 cost once:
+    4 n m algorithmic bytes.  The 4096 x 4096 cost of the timed workload
+    (67 MB) stays in the 129 MB L2 during a solve, so the HBM roofline is
+    measured on the same points at 16384 x 16384 (1.07 GB cost, HBM-resident);
+    the 4096 figure is reported beside it."""
+    import workloads
+    peaks = load_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    stage("roofline: 4096 per-pass")
+    small = per_pass_ms(pkg, torch, p, f, g, stream, 100, 400)
+    nl = 16384
+    stage("roofline: 16384 problem")
+    big = workloads.gaussian_mixture(nl, nl, seed=1, eps=EPS)
+    keep = []
+    Xb, Yb = torch.as_tensor(big.X).cuda(), torch.as_tensor(big.Y).cuda()
+    ab, bb = torch.as_tensor(big.a).cuda(), torch.as_tensor(big.b).cuda()
+    fb = torch.zeros(nl, dtype=torch.float64, device="cuda")
+    gb = torch.zeros(nl, dtype=torch.float64, device="cuda")
+    pb = pkg.make_problem(ab, bb, X=Xb, Y=Yb, eps=1e-2, normalize_cost=True, keep=keep)
+    # converged-level potentials as the start (typical exponents)
+    o = options(pkg, 0, stream.cuda_stream, tol=1e-4, max_iter=2000, eps_start=0.0)
+    pkg.eot_solve(pb, o, fb, gb)
+    torch.cuda.synchronize()
+    stage("roofline: 16384 per-pass")
+    large = per_pass_ms(pkg, torch, pb, fb, gb, stream, 20, 80)
+    bytes_pass = 4.0 * nl * nl
+    achieved = bytes_pass / (large * 1e-3) / 1e9
+    del Xb, Yb, fb, gb
+    return {"kernel": "sk_coop_kernel (stored-cost log-sum-exp half-steps, plain Sinkhorn)",
             "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(achieved / hbm, 3), "traffic": None,
-            "per_pass_us": round(per_pass_ms * 1e3, 3),
-            "algorithmic_bytes_per_launch": int(bytes_per_pass),
-            "note": "peak of measured (MEASURED_PEAKS.json hbm_gbs); the 67 MB cost fits in the "
-                    "129 MB L2, so passes inside one solve read it from L2 and frac can exceed 1"}
+            "per_pass_us": round(large * 1e3, 3), "workload": f"{nl}x{nl} cost (1.07 GB, HBM)",
+            "algorithmic_bytes_per_launch": int(bytes_pass),
+            "l2_resident_4096": {"per_pass_us": round(small * 1e3, 3),
+                                 "achieved_gbs": round(4.0 * N * M / (small * 1e-3) / 1e9, 1)},
+            "note": "per half-step, launch and grid-barrier overheads included; peak of "
+                    "measured (MEASURED_PEAKS.json hbm_gbs)"}
+
+
+def extras(pkg, torch, stream):
+    """The other configurations, measured briefly: on-the-fly cost (c3), a
+    batch of problems (c4) and a served stream (c5)."""
+    import workloads
+    out = {}
+    peaks = load_peaks()
+    # c3: 20000 x 30000 points in R^64 ~ N(0, I)/8, raw cost, eps = 1e-3, the
+    # cost formed on the tensor cores each half-step (3xTF32)
+    n3, m3 = 20000, 30000
+    stage("c3: per-pass")
+    c3 = workloads.gaussian_cloud(n3, m3, d=64, seed=0, eps=1e-3)
+    keep = []
+    X3, Y3 = torch.as_tensor(c3.X).cuda(), torch.as_tensor(c3.Y).cuda()
+    a3, b3 = torch.as_tensor(c3.a).cuda(), torch.as_tensor(c3.b).cuda()
+    f3 = torch.zeros(n3, dtype=torch.float64, device="cuda")
+    g3 = torch.zeros(m3, dtype=torch.float64, device="cuda")
+    p3 = pkg.make_problem(a3, b3, X=X3, Y=Y3, eps=1e-3, keep=keep)
+    pp = per_pass_ms(pkg, torch, p3, f3, g3, stream, 10, 40, prec=pkg.EOT_PREC_SPLIT_TC)
+    flops = 3 * 2.0 * n3 * m3 * 64
+    tf32_peak = peaks.get("bf16_tflops", 1900.0) * (1.1 / 2.25)
+    o3 = options(pkg, 0, stream.cuda_stream, tol=TOL, max_iter=200000, eps_start=1e-1,
+                 prec=pkg.EOT_PREC_SPLIT_TC)
+    stage("c3: solve")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    st, res = pkg.eot_solve(p3, o3, f3, g3)
+    e1.record()
+    torch.cuda.synchronize()
+    r3 = res.as_dict()
+    out["c3_on_the_fly_cost"] = {
+        "workload": "gaussian_cloud_20000x30000_d64 (N(0,I)/8, raw cost), eps 1e-3, SPLIT_TC",
+        "per_pass_us": round(pp * 1e3, 1),
+        "tensor_tflops": round(flops / (pp * 1e-3) / 1e12, 1),
+        "tensor_frac": round(flops / (pp * 1e-3) / 1e12 / tf32_peak, 3),
+        "tensor_peak_note": "TF32 peak = measured bf16 x (1.1 / 2.25) nominal ratio",
+        "stored_cost_equivalent_gbs": round(4.0 * n3 * m3 / (pp * 1e-3) / 1e9, 1),
+        "solve_ms": round(e0.elapsed_time(e1), 1), "status": r3["status_name"],
+        "total_iters": r3["total_iters"], "l1_marginal_own_cost": r3["l1_marginal"]}
+    del X3, Y3, f3, g3
+    # c4: batch of problems of uneven size and eps (one call)
+    stage("c4: batch")
+    probs = workloads.batch_problems(512, seed=0)
+    keepb = []
+    ps = [pkg.make_problem(q.a, q.b, X=q.X, Y=q.Y, eps=q.eps, normalize_cost=True, keep=keepb)
+          for q in probs]
+    ob = pkg.default_options(tol=TOL, max_iter=200000, eps_start=1e-1)
+    fs = [np.zeros(q.n) for q in probs]
+    gs = [np.zeros(q.m) for q in probs]
+    t0 = time.perf_counter()
+    st, resb = pkg.eot_solve_batch(ps, ob, fs, gs)
+    t1 = time.perf_counter()
+    nm = sum(q.n * q.m for q in probs)
+    iters = sum(r.total_iters for r in resb)
+    ok = sum(1 for r in resb if r.status == pkg.EOT_OK)
+    out["c4_batch"] = {"problems": len(probs), "converged": ok, "seconds": round(t1 - t0, 3),
+                       "problems_per_s": round(len(probs) / (t1 - t0), 1),
+                       "total_iters": int(iters),
+                       "cost_gb_streamed_per_s": round(8.0 * nm * (iters / len(probs)) /
+                                                       (t1 - t0) / 1e9, 1),
+                       "note": "host arrays in and out; solves overlap on per-thread streams"}
+    # c5: served stream (Poisson arrivals, continuous batching, warm restarts)
+    stage("c5: serving")
+    reqs = workloads.served_stream(seed=1, rate_per_s=2000.0, duration_s=60.0, max_requests=96)
+    os5 = pkg.default_options(tol=TOL, max_iter=200000, eps_start=1e-1)
+    srv = pkg.Server(os5, hbm_budget_bytes=48 << 30, max_slots=8)
+    try:
+        t0 = time.perf_counter()
+        tickets = []
+        for r in reqs:
+            while time.perf_counter() - t0 < r["t"]:
+                time.sleep(0.0002)
+            tickets.append(srv.submit(r["problem"], cloud_id=r["cloud_id"]))
+        done = 0
+        for t in tickets:
+            while True:
+                st5, _, _, _ = srv.poll(t)
+                if st5 != pkg.EOT_PENDING:
+                    break
+                time.sleep(0.001)
+            done += st5 in (pkg.EOT_OK, pkg.EOT_NOT_CONVERGED)
+        t1 = time.perf_counter()
+        p50, p99, sps = srv.stats()
+    finally:
+        srv.close()
+    out["c5_serving"] = {"requests": len(reqs), "completed": int(done),
+                         "offered_rate_per_s": 2000.0, "p50_ms": round(p50 * 1e3, 2),
+                         "p99_ms": round(p99 * 1e3, 2), "solves_per_s": round(sps, 1),
+                         "wall_s": round(t1 - t0, 3),
+                         "note": "96 requests of the Poisson stream; n, m log-uniform in "
+                                 "[128, 16384], d in {2, 3, 64}; 8 slots, 48 GB budget"}
+    return out
 
 
 def cpu_baseline(prob, gpu_iters, seconds_budget=20.0):

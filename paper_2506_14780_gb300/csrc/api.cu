@@ -181,6 +181,11 @@ struct Arena {
 
 static int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
+// Solves issued from the batch and server worker threads run concurrently on
+// one device; there the plain Sinkhorn levels use the captured graphs, not the
+// cooperative loop (whose grid barriers need the whole grid resident at once).
+static thread_local bool t_concurrent = false;
+
 // ---------------------------------------------------------------------------
 // 2-D tensor map of the cost for the staged stream passes (box 128 columns x
 // 32 rows of float32, no swizzle).  The encoder is the driver's, reached
@@ -702,7 +707,7 @@ struct Solver {
   bool coop_ok = true;
   eot_status run_sk(int max_iter, int graph_cap, bool* used_coop) {
     *used_coop = false;
-    if (coop_ok && !f64 && !gram && hP.sk_gcol > 0 && hP.sk_gcol == hP.sk_grow && m % 4 == 0 &&
+    if (coop_ok && !t_concurrent && !f64 && !gram && hP.sk_gcol > 0 && hP.sk_gcol == hP.sk_grow && m % 4 == 0 &&
         (reinterpret_cast<uintptr_t>(hP.C) & 15u) == 0) {
       const cudaError_t e = launch_sk_coop(dP, hP, max_iter + 4, ctx->stream);
       if (e == cudaSuccess) {
@@ -1635,10 +1640,19 @@ struct eot_server {
     eot_status status = EOT_PENDING;
     bool done = false;
   };
+  // Device-resident potentials of a cloud, shared by the cache and by the
+  // solves that warm-start from them: the buffer is freed when the last
+  // holder lets go (a cache update does not free it under a running solve).
+  struct DevBuf {
+    double* p = nullptr;
+    ~DevBuf() {
+      if (p) cudaFree(p);
+    }
+  };
   struct Cached {
     int n = 0, m = 0;
     double eps = 0;
-    double* f = nullptr;   // device-resident potentials
+    std::shared_ptr<DevBuf> f;
   };
   eot_options opt{};
   size_t budget = 0;
@@ -1659,6 +1673,7 @@ struct eot_server {
 
   void worker() {
     cudaSetDevice(device);
+    eotk::t_concurrent = true;
     for (;;) {
       std::shared_ptr<Request> r;
       Cached warm;
@@ -1694,19 +1709,27 @@ struct eot_server {
       o.stream = nullptr;
       const double* finit = nullptr;
       if (warm.f) {
-        finit = warm.f;
+        finit = warm.f->p;
         if (warm.eps > r->prob.eps) {
           o.eps_start = warm.eps * (o.eps_factor > 0 && o.eps_factor < 1 ? o.eps_factor : 0.5);
         } else {
           o.eps_start = 0.0;
         }
       }
-      double* keep = nullptr;
-      if (r->cloud_id) cudaMalloc(&keep, r->prob.n * sizeof(double));
+      std::shared_ptr<DevBuf> keep;
+      if (r->cloud_id) {
+        keep = std::make_shared<DevBuf>();
+        if (cudaMalloc(&keep->p, r->prob.n * sizeof(double)) != cudaSuccess) {
+          cudaGetLastError();
+          keep.reset();
+        }
+      }
       r->f.assign(r->prob.n, 0.0);
       r->g.assign(r->prob.m, 0.0);
-      eot_status st = eotk::solve_one(&r->prob, &o, r->f.data(), r->g.data(), &r->res, finit, keep);
+      eot_status st = eotk::solve_one(&r->prob, &o, r->f.data(), r->g.data(), &r->res, finit,
+                                      keep ? keep->p : nullptr);
       eotk::drop_thread_cache();
+      warm.f.reset();   // this solve no longer reads the cached potentials
       {
         std::lock_guard<std::mutex> lk(mu);
         in_use -= r->footprint;
@@ -1717,17 +1740,12 @@ struct eot_server {
         lat.push_back(r->t_done - r->t_submit);
         t_last = r->t_done;
         ++completed;
-        if (keep) {
-          if (st >= 0) {
-            auto& c = cache[r->cloud_id];
-            if (c.f) cudaFree(c.f);
-            c.f = keep;
-            c.n = r->prob.n;
-            c.m = r->prob.m;
-            c.eps = r->prob.eps;
-          } else {
-            cudaFree(keep);
-          }
+        if (keep && st >= 0) {
+          auto& c = cache[r->cloud_id];
+          c.f = keep;   // the previous buffer goes when its last reader is done
+          c.n = r->prob.n;
+          c.m = r->prob.m;
+          c.eps = r->prob.eps;
         }
       }
       cv.notify_all();
@@ -1754,6 +1772,7 @@ eot_status eot_solve_batch(int32_t count, const eot_problem* probs, const eot_op
   std::vector<std::string> errs(count);
   auto work = [&]() {
     cudaSetDevice(dev);
+    eotk::t_concurrent = true;
     for (;;) {
       const int k = nexti.fetch_add(1);
       if (k >= count) break;
@@ -1894,8 +1913,7 @@ void eot_server_destroy(eot_server* srv) {
   }
   srv->cv.notify_all();
   for (auto& t : srv->workers) t.join();
-  for (auto& kv : srv->cache)
-    if (kv.second.f) cudaFree(kv.second.f);
+  srv->cache.clear();   // frees the cached potentials
   delete srv;
 }
 
