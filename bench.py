@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--quick", action="store_true",
                     help="skip the additional configurations (on-the-fly cost, batch, serving)")
+    ap.add_argument("--case", default=None, choices=["coop16k", "stream8k", "sknr4k", "gram"],
+                    help="run one small case for a profiler and exit (no timing, no JSON)")
     return ap.parse_args()
 
 
@@ -493,8 +495,53 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def profile_case(name):
+    """Small cases for ncu captures: one plain Sinkhorn launch of two iterations
+    on a 16384 x 16384 cost (coop16k); column and row transforms on an 8192 x
+    8192 cost (stream8k); one SK-NR(30) solve of the 4096 x 4096 workload
+    (sknr4k); ten on-the-fly-cost iterations on 20000 x 30000 points in R^64
+    (gram)."""
+    import torch
+    import workloads
+    import paper_2506_14780_gb300 as pkg
+    pkg.load()
+    if name == "coop16k":
+        prob = workloads.gaussian_mixture(16384, 16384, seed=1, eps=1e-2)
+        _, _, res = pkg.solve(prob, tol=1e-300, ell=0, eps_start=0.0, max_iter=2)
+    elif name == "stream8k":
+        n = 8192
+        prob = workloads.gaussian_mixture(n, n, seed=2, eps=1e-2)
+        X = torch.as_tensor(prob.X).double().cuda()
+        Y = torch.as_tensor(prob.Y).double().cuda()
+        C = torch.cdist(X, Y) ** 2
+        C = (C / C.max()).float().contiguous()
+        a = torch.as_tensor(prob.a).cuda()
+        b = torch.as_tensor(prob.b).cuda()
+        f = torch.zeros(n, dtype=torch.float64, device="cuda")
+        og = torch.zeros(n, dtype=torch.float64, device="cuda")
+        of = torch.zeros(n, dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            if pkg.eot_ctransform(pkg.EOT_SIDE_COL, n, n, C, f, a, None, 1e-2, og, None) != 0:
+                raise RuntimeError(pkg.last_error())
+            if pkg.eot_ctransform(pkg.EOT_SIDE_ROW, n, n, C, og, b, of, 1e-2, of, None) != 0:
+                raise RuntimeError(pkg.last_error())
+        res = {"status_name": "EOT_OK"}
+    elif name == "sknr4k":
+        prob = workloads.gaussian_mixture(N, M, seed=0, eps=EPS)
+        _, _, res = pkg.solve(prob, tol=TOL, ell=ELL, eps_start=1e-1, max_iter=200000)
+    else:
+        prob = workloads.gaussian_cloud(20000, 30000, d=64, seed=0, eps=1e-3)
+        _, _, res = pkg.solve(prob, tol=1e-300, ell=0, eps_start=0.0, max_iter=10,
+                              prec=pkg.EOT_PREC_SPLIT_TC)
+    torch.cuda.synchronize()
+    stage(f"case {name}: {res.get('status_name')}")
+
+
 def main():
     args = parse()
+    if args.case:
+        profile_case(args.case)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
