@@ -54,7 +54,8 @@ int acc_template_k(int k);
 int rowacc_rows(int k);
 void init_acc_attributes();
 cudaError_t launch_wtw_reduce(const AccArgs& a, double* WtW, double* gw, cudaStream_t s);
-cudaError_t launch_colmma(const AccArgs& a, const float* tiles, int ncolblk, cudaStream_t s);
+cudaError_t launch_colmma(const AccArgs& a, const Prob& hP, const float* tiles, int ncolblk,
+                          cudaStream_t s);
 cudaError_t launch_build_tiles(const float* Z, int n, int kk, float* tiles, cudaStream_t s);
 int mma_record(int k);
 size_t mma_tiles_floats(int n, int k);
@@ -226,6 +227,7 @@ static eot_status encode_operand_map(CUtensorMap* map, const float* ptr, int row
 
 // Encode P.tmC for P.C when the stream passes are in use.
 static eot_status encode_cost_map(Prob& P) {
+  P.has_tmC = 0;
   if (P.sk_gcol <= 0 && P.sk_grow <= 0) return EOT_OK;
   // the striped passes serve costs whose rows are not 16-byte aligned
   if ((reinterpret_cast<uintptr_t>(P.C) & 15u) != 0 || P.m % 4 != 0) return EOT_OK;
@@ -241,6 +243,7 @@ static eot_status encode_cost_map(Prob& P) {
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS)
     return fail(EOT_ECUDA, "cuTensorMapEncodeTiled failed (code " + std::to_string((int)r) + ")");
+  P.has_tmC = 1;
   return EOT_OK;
 }
 
@@ -624,7 +627,7 @@ struct Solver {
     for (int u = 0; u < unroll_sknr && e == cudaSuccess; ++u) {
       e = pass_row(MODE_SK_ROW, s);
       if (e == cudaSuccess)
-        e = f64 ? launch_col64(dP, hP, MODE_S4, a, s) : launch_colmma(a, tilesV, mm_ncolblk, s);
+        e = f64 ? launch_col64(dP, hP, MODE_S4, a, s) : launch_colmma(a, hP, tilesV, mm_ncolblk, s);
       if (e != cudaSuccess) break;
       e = launch_wtw_reduce(a, WtW, gw, s);
       if (e != cudaSuccess) break;
@@ -637,7 +640,7 @@ struct Solver {
 
   cudaError_t body_eig(cudaStream_t s, int fb, int gb) {
     cudaError_t e = launch_build_tiles(Zb, n, p, tilesZ, s);
-    if (e == cudaSuccess) e = launch_colmma(kcol_args(fb, gb, Zb, Yb), tilesZ, mm_ncolblk, s);
+    if (e == cudaSuccess) e = launch_colmma(kcol_args(fb, gb, Zb, Yb), hP, tilesZ, mm_ncolblk, s);
     if (e == cudaSuccess) e = launch_rowacc(krow_args(fb, gb, Yb, Xb), kr_nrowblk, s);
     if (e != cudaSuccess) return e;
     // GXX = X^T D_a X (+ c = a^T X), T = Z^T D_a X
@@ -1480,7 +1483,7 @@ eot_status eot_kapply(eot_side side, int32_t n, int32_t m, int32_t k, const floa
   aa.k = k;
   if (side == EOT_SIDE_COL) {
     CUDA_TRY(launch_build_tiles(Z, n, k, S->tilesZ, s));
-    CUDA_TRY(launch_colmma(aa, S->tilesZ, S->mm_ncolblk, s));
+    CUDA_TRY(launch_colmma(aa, S->hP, S->tilesZ, S->mm_ncolblk, s));
   } else {
     CUDA_TRY(launch_rowacc(aa, S->kr_nrowblk, s));
   }

@@ -23,6 +23,7 @@
 #include "eot_internal.h"
 #include "reduce.cuh"
 #include "tc.cuh"
+#include "stream_common.cuh"
 
 namespace eotk {
 
@@ -49,6 +50,153 @@ __global__ void build_tiles_kernel(const float* __restrict__ Z, int n, int kk, i
     const size_t off = sw128_off(r, k >> 2) / 4 + (k & 3);
     tiles[((size_t)c * 2 + 0) * NN * kMmaKC + off] = hi;
     tiles[((size_t)c * 2 + 1) * NN * kMmaKC + off] = lo;
+  }
+}
+
+// Shared state of the segment-combining epilogue.
+struct MmaEpi {
+  double red[24];
+  unsigned last;
+};
+
+// Epilogue of the CTA that arrived last on column block cb: merge the segments'
+// (reference, sum) heads and product rows of its 128 columns, write
+// Op(pi)^T Z (or, in the SK-NR pass, W = pi(f_k, h)^T V with h = f_k^{C,eps},
+// the new potential h and its split arrays, d_j, and the block partials of
+// W^T D_b^{-1} W and d^T W; the last block takes the grid-wide step: L1
+// test, Q_semi(f_k), iteration count).  Run by threads 0..255 (named barrier
+// 1); `smem` is scratch of at least 128 (NN + 3) floats.
+template <int NN>
+__device__ void colmma_finish(const AccArgs& args, const Prob& P, unsigned char* smem,
+                              MmaEpi& epi, int cb, int gb, int dst_g) {
+  State* st = P.st;
+  const bool s4 = args.mode == 1;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int m = P.m, kk = args.k;
+  const int c = tid & (kMmaM - 1);
+  const int j = cb * kMmaM + c;
+  const bool jv = j < m;
+  float* sW = reinterpret_cast<float*>(smem);   // [128][NN + 1]
+  float* sD = sW + kMmaM * (NN + 1);            // [128] d_j
+  float* sB = sD + kMmaM;                       // [128] 1 / b_j
+  double accv[3] = {0.0, 0.0, 0.0};
+  if (tid < kMmaM) {
+    float R = -INFINITY;
+    double Stot = 0.0;
+    if (jv) merge_segments_k(args.part, args.nseg, m, NN + 4, j, R, Stot);
+    double scale = 1.0;
+    if (s4 && jv) scale = P.b[j] / (Stot * ldexp(1.0, (int)R));   // b_j / sum_i 2^{y_ij}
+    // the product rows, 16 columns at a time (segments in a fixed order)
+#pragma unroll 1
+    for (int k0 = 0; k0 < NN; k0 += 16) {
+      float acc[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) acc[k] = 0.f;
+      if (jv) {
+        for (int sg = 0; sg < args.nseg; ++sg) {
+          const float4* src = reinterpret_cast<const float4*>(
+              args.part + ((size_t)sg * m + j) * (NN + 4) + 4 + k0);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float4 v = __ldcg(src + q);
+            acc[4 * q + 0] += v.x;
+            acc[4 * q + 1] += v.y;
+            acc[4 * q + 2] += v.z;
+            acc[4 * q + 3] += v.w;
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        if (k0 + k < kk) {
+          const float wv = (float)(acc[k] * scale);
+          if (jv) args.out[(size_t)j * kk + k0 + k] = wv;
+          if (s4) sW[c * (NN + 1) + k0 + k] = jv ? wv : 0.f;
+        }
+      }
+    }
+    if (s4) {
+      sD[c] = 0.f;
+      sB[c] = 0.f;
+      if (jv) {
+        float L = R * kLn2 + log_sum(Stot);
+        const double sh = P.g[gb][j];
+        double o = sh - P.eps * (double)L;
+        if (!isfinite(o) || !(Stot > 0.0) || fabs(o) > P.pot_bound) {
+          atomicAdd(&st->numeric, 1);
+          o = sh;
+          L = 0.f;
+        }
+        // the products need the exponentials in range: flag a column whose
+        // largest term lies far from 1 (the Newton step is then skipped)
+        if (R > 60.f || R < -60.f) atomicOr(&st->nr_degenerate, 1);
+        P.g[dst_g][j] = o;
+        P.Lcol[j] = L;
+        double hi;
+        float lo;
+        split_grid(o + P.eps * P.logb[j], P.qscale, P.qinv, hi, lo);
+        P.cs[dst_g].A[j] = (float)(hi + (double)P.M);
+        P.cs[dst_g].AL[j] = lo;
+        split_grid(o, P.qscale, P.qinv, hi, lo);
+        P.cs[dst_g].K[j] = (float)((double)P.M - hi);
+        P.cs[dst_g].KL[j] = lo;
+        const double wj = P.b[j];
+        const double dj = -(double)expm1f(L);     // 1 - exp((g_j - h_j)/eps)
+        args.dw[j] = dj;
+        sD[c] = (float)dj;
+        sB[c] = (float)(1.0 / wj);
+        accv[0] = wj * (double)fabsf(expm1f(L));
+        accv[1] = wj * (double)L;
+        accv[2] = wj * o;
+      }
+    }
+  }
+  if (!s4) {
+    if (tid == 0) args.cnt[cb] = 0u;
+    return;
+  }
+  cons_sync();
+  {
+    // block partials of W^T D_b^{-1} W and d^T W over the 128 columns
+    double* dstp = args.wtw_part + (size_t)cb * (kk * kk + kk);
+    // float32 sums over the 128 columns (float64 across blocks)
+    for (int e = tid; e < kk * kk + kk; e += kStConsumers) {
+      float s = 0.f;
+      if (e < kk * kk) {
+        const int r = e / kk, q2 = e - r * kk;
+        for (int q = 0; q < kMmaM; ++q)
+          s = __fmaf_rn(sW[q * (NN + 1) + r] * sB[q], sW[q * (NN + 1) + q2], s);
+      } else {
+        const int r = e - kk * kk;
+        for (int q = 0; q < kMmaM; ++q) s = __fmaf_rn(sD[q], sW[q * (NN + 1) + r], s);
+      }
+      dstp[e] = (double)s;
+    }
+  }
+  // the block's three sums (only the first 128 threads hold nonzero values)
+  cons_sum3(accv, epi.red, kMmaM);
+  if (tid == 0) {
+    args.cnt[cb] = 0u;
+    double* ab = args.blkacc + cb * 4;
+    ab[0] = accv[0];
+    ab[1] = accv[1];
+    ab[2] = accv[2];
+    epi.last = arrive_count(args.gcnt) == (unsigned)(args.nblk - 1);
+  }
+  cons_sync();
+  if (!epi.last || wid != 0) return;
+  double tot[3];
+  warp0_grid_sum3(args.blkacc, args.nblk, tot);
+  if (lane == 0) {
+    *args.gcnt = 0u;
+    st->l1_col = tot[0];
+    st->sum_wL = tot[1];
+    st->qsemi = st->sum_af + tot[2];   // Q_semi(f_k) = <f_k, a> + <h, b>
+    st->iter += 1;
+    st->nr_ok = 0;
+    if (st->numeric > 0) st->done = 3;
+    else if (tot[0] < st->tol) st->done = 1;
+    else if (st->iter >= st->max_iter) st->done = 2;
   }
 }
 
@@ -83,16 +231,15 @@ __global__ void __launch_bounds__(256) colmma_kernel(AccArgs args, const float* 
   __shared__ int s_err;
   __shared__ float s_lr[2][kMmaM];
   __shared__ double s_ls[2][kMmaM];
-  __shared__ double s_red[24];
-  __shared__ unsigned s_last;
+  __shared__ MmaEpi epi;
   const uint32_t raw = smem_addr(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   unsigned char* sbase = smem_raw + (base - raw);
   float2* sRow = reinterpret_cast<float2*>(sbase + SM::row_off);
 
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int tid = threadIdx.x, wid = tid >> 5;
   const int c = tid & (kMmaM - 1), h = tid >> 7;     // column within the tile, row half
-  const int n = P.n, m = P.m, kk = args.k;
+  const int n = P.n, m = P.m;
   const int cb = blockIdx.x, seg = blockIdx.y;
   const int j = cb * kMmaM + c;
   const bool jv = j < m;
@@ -274,150 +421,331 @@ __global__ void __launch_bounds__(256) colmma_kernel(AccArgs args, const float* 
   __syncthreads();
   if (wid == 0) tmem_dealloc(tmem, tcols);
   if (err && tid == 0) atomicAdd(&st->numeric, 1);
-  __threadfence();
+  if (tid == 0) epi.last = arrive_count(&args.cnt[cb]) == (unsigned)(args.nseg - 1);
   __syncthreads();
+  if (!epi.last) return;
+  colmma_finish<NN>(args, P, sbase, epi, cb, gb, dst_g);
+}
+
+// ---------------------------------------------------------------------------
+// Staged variant for costs with 16-byte aligned rows (a 2-D tensor map of C):
+// warp-specialised, A operand in TMEM.
+//   * warp 8 (producer): per chunk of 32 rows, one tiled tensor copy of the
+//     32 x 128 cost tile, one bulk copy of the chunk's B tiles (hi, lo) and
+//     two of the rows' split coefficients into a ring of stages;
+//   * warps 0..7 (consumers): thread (c, h) forms the 16 exponents of column
+//     c, rows 16h..16h+15 of the chunk, from shared memory (two rows at a
+//     time with the packed float32x2 instructions), keeps the column's running
+//     log-sum-exp, and stores the exponentials' TF32 hi / lo parts with
+//     tcgen05.st into TMEM lane c (columns = the chunk's rows): the A operand
+//     of the next MMAs, no shared-memory round trip;
+//   * warp 9 (MMA issuer, TMEM owner): 4 x 3 MMAs per chunk (K = 8; hi*hi,
+//     hi*lo, lo*hi) from the TMEM A buffer and the B tiles in shared memory.
+// Two TMEM A buffers let the consumers form chunk c + 1 while the tensor core
+// multiplies chunk c.  Barriers: full[s] (copies landed), empty[s] (8 consumer
+// warps + the MMA commit), afull[b] (8 consumer warps stored A), aempty[b]
+// (MMA commit), acc (all MMAs done).  Every wait is bounded.
+// ---------------------------------------------------------------------------
+constexpr int kTmThreads = 320;
+constexpr uint32_t kTmTile = kMmaKC * kMmaM * 4;   // 16 KB cost tile
+constexpr uint32_t kTmA = 64;                      // TMEM column of A buffer 0
+constexpr uint32_t kTmCols = 256;
+
+template <int NN>
+struct TmaSmem {
+  static constexpr int stages = NN <= 32 ? 4 : 3;
+  static constexpr uint32_t b_off = kTmTile;                     // B hi, then B lo
+  static constexpr uint32_t coef_off = kTmTile + 2 * NN * 128;   // A[32], AL[32]
+  static constexpr uint32_t stage = (coef_off + 256 + 1023) / 1024 * 1024;
+  static constexpr size_t bytes = (size_t)stages * stage + 1024;
+  static constexpr uint32_t tx = kTmTile + 2 * NN * 128 + 256;
+};
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t v[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+      "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
+      "r"(v[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// D (TMEM) += A (TMEM, M x 8 tf32 at column ta) * B (shared memory descriptor)^T
+__device__ __forceinline__ void mma_tf32_ts(uint32_t tmem_d, uint32_t ta, uint64_t bdesc,
+                                            uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}" ::"r"(tmem_d),
+      "r"(ta), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+// TF32 parts of a non-negative float: hi rounded to 10 fraction bits (half
+// up), lo = x - hi (exact) truncated to 10 fraction bits; hi + lo matches x
+// to 2^-21 relative.
+__device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
+  const uint32_t h = (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
+  hi = h;
+  lo = __float_as_uint(__fsub_rn(x, __uint_as_float(h))) & 0xFFFFE000u;
+}
+
+template <int NN>
+__global__ void __launch_bounds__(kTmThreads, 2)
+    colmma_tma_kernel(AccArgs args, const float* __restrict__ tiles) {
+  const Prob* PP = args.P;
+  const Prob& P = *PP;
+  State* st = P.st;
+  const bool s4 = args.mode == 1;
+  if (s4 && st->done) return;
+  const int fb = s4 ? st->cur_f : args.fbuf;
+  const int gb = s4 ? st->cur_g : args.gbuf;
+  const int dst_g = (st->cur_g + 1) % 3;
+  using SM = TmaSmem<NN>;
+  constexpr int NS = SM::stages;
+
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[NS];
+  __shared__ __align__(8) uint64_t empty_bar[NS];
+  __shared__ __align__(8) uint64_t afull[2];
+  __shared__ __align__(8) uint64_t aempty[2];
+  __shared__ __align__(8) uint64_t accf;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_err;
+  __shared__ float s_lr[2][kMmaM];
+  __shared__ double s_ls[2][kMmaM];
+  __shared__ MmaEpi epi;
+  const uint32_t raw = smem_addr(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char* sbase = smem_raw + (base - raw);
+
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int n = P.n, m = P.m;
+  const int cb = blockIdx.x, seg = blockIdx.y;
+  const int i_beg = seg * args.seg_len;
+  const int i_end = min(n, i_beg + args.seg_len);
+  const int nch = i_end > i_beg ? (i_end - i_beg + kMmaKC - 1) / kMmaKC : 0;
+  constexpr uint32_t idesc = idesc_tf32(kMmaM, NN);
+
   if (tid == 0) {
-    const unsigned prev = atomicAdd(&args.cnt[cb], 1u);
-    s_last = (prev == (unsigned)(args.nseg - 1));
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(smem_addr(&full_bar[s]), 1);
+      mbar_init(smem_addr(&empty_bar[s]), 9);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_addr(&afull[b]), 8);
+      mbar_init(smem_addr(&aempty[b]), 1);
+    }
+    mbar_init(smem_addr(&accf), 1);
+    mbar_init_fence();
+    s_err = 0;
   }
+  if (wid == 9) tmem_alloc(smem_addr(&s_tmem), kTmCols);
+  tc_fence_before();
   __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  // ---- this CTA combines the segments of its 128 columns ----
-  float* sW = reinterpret_cast<float*>(sbase);          // [128][kk + 1], reuses the A tiles
-  float* sD = sW + kMmaM * (NN + 1);    // [128] d_j
-  float* sB = sD + kMmaM;               // [128] 1 / b_j
-  double accv[3] = {0.0, 0.0, 0.0};
-  if (tid < kMmaM) {
-    float R = -INFINITY;
-    double Stot = 0.0;
-    if (jv) merge_segments_k(args.part, args.nseg, m, NN + 4, j, R, Stot);
-    double scale = 1.0;
-    if (s4 && jv) scale = P.b[j] / (Stot * ldexp(1.0, (int)R));   // b_j / sum_i 2^{y_ij}
-    float acc[NN];
-#pragma unroll
-    for (int k = 0; k < NN; ++k) acc[k] = 0.f;
-    if (jv) {
-      for (int sg = 0; sg < args.nseg; ++sg) {
-        const float4* src =
-            reinterpret_cast<const float4*>(args.part + ((size_t)sg * m + j) * (NN + 4) + 4);
-#pragma unroll
-        for (int q = 0; q < NN / 4; ++q) {
-          const float4 v = __ldcg(src + q);
-          acc[4 * q + 0] += v.x;
-          acc[4 * q + 1] += v.y;
-          acc[4 * q + 2] += v.z;
-          acc[4 * q + 3] += v.w;
-        }
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < NN; ++k) {
-      if (k < kk) {
-        const float wv = (float)(acc[k] * scale);
-        if (jv) args.out[(size_t)j * kk + k] = wv;
-        if (s4) sW[c * (NN + 1) + k] = jv ? wv : 0.f;
-      }
-    }
-    if (s4) {
-      sD[c] = 0.f;
-      sB[c] = 0.f;
-      if (jv) {
-        float L = R * kLn2 + log_sum(Stot);
-        const double sh = P.g[gb][j];
-        double o = sh - P.eps * (double)L;
-        if (!isfinite(o) || !(Stot > 0.0) || fabs(o) > P.pot_bound) {
-          atomicAdd(&st->numeric, 1);
-          o = sh;
-          L = 0.f;
-        }
-        // the products need the exponentials in range: flag a column whose
-        // largest term lies far from 1 (the Newton step is then skipped)
-        if (R > 60.f || R < -60.f) atomicOr(&st->nr_degenerate, 1);
-        P.g[dst_g][j] = o;
-        P.Lcol[j] = L;
-        double hi;
-        float lo;
-        split_grid(o + P.eps * P.logb[j], P.qscale, P.qinv, hi, lo);
-        P.cs[dst_g].A[j] = (float)(hi + (double)P.M);
-        P.cs[dst_g].AL[j] = lo;
-        split_grid(o, P.qscale, P.qinv, hi, lo);
-        P.cs[dst_g].K[j] = (float)((double)P.M - hi);
-        P.cs[dst_g].KL[j] = lo;
-        const double wj = P.b[j];
-        const double dj = -(double)expm1f(L);     // 1 - exp((g_j - h_j)/eps)
-        args.dw[j] = dj;
-        sD[c] = (float)dj;
-        sB[c] = (float)(1.0 / wj);
-        accv[0] = wj * (double)fabsf(expm1f(L));
-        accv[1] = wj * (double)L;
-        accv[2] = wj * o;
-      }
-    }
-  }
-  if (!s4) {
-    if (tid == 0) args.cnt[cb] = 0u;
-    return;
-  }
-  __syncthreads();
-  {
-    // block partials of W^T D_b^{-1} W and d^T W over the 128 columns
-    double* dstp = args.wtw_part + (size_t)cb * (kk * kk + kk);
-    // float32 sums over the 128 columns (float64 across blocks)
-    for (int e = tid; e < kk * kk + kk; e += 256) {
-      float s = 0.f;
-      if (e < kk * kk) {
-        const int r = e / kk, q2 = e - r * kk;
-        for (int q = 0; q < kMmaM; ++q)
-          s = __fmaf_rn(sW[q * (NN + 1) + r] * sB[q], sW[q * (NN + 1) + q2], s);
-      } else {
-        const int r = e - kk * kk;
-        for (int q = 0; q < kMmaM; ++q) s = __fmaf_rn(sD[q], sW[q * (NN + 1) + r], s);
-      }
-      dstp[e] = (double)s;
-    }
-  }
-  {
-    double v0 = warp_sum_d(accv[0]), v1 = warp_sum_d(accv[1]), v2 = warp_sum_d(accv[2]);
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+
+  if (wid == 8) {
+    // ---------------- producer ----------------
     if (lane == 0) {
-      s_red[wid] = v0;
-      s_red[8 + wid] = v1;
-      s_red[16 + wid] = v2;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      double t0 = 0.0, t1 = 0.0, t2 = 0.0;
-      for (int w = 0; w < 8; ++w) {
-        t0 += s_red[w];
-        t1 += s_red[8 + w];
-        t2 += s_red[16 + w];
+      const float* rA = P.rs[fb].A;
+      const float* rAL = P.rs[fb].AL;
+      int issued = 0;
+      for (int ch = 0; ch < nch; ++ch) {
+        const int s = ch % NS;
+        if (ch >= NS &&
+            !mbar_wait(smem_addr(&empty_bar[s]), ((ch / NS) - 1) & 1, kMmaWait)) {
+          s_err = 1;
+          break;
+        }
+        const uint32_t fbar = smem_addr(&full_bar[s]);
+        const uint32_t dst = base + (uint32_t)s * SM::stage;
+        const int i0 = i_beg + ch * kMmaKC;   // a multiple of 32 (segments are)
+        mbar_expect_tx(fbar, SM::tx);
+        // column cb * 128: the box starts on a 16-byte boundary
+        tma_load_2d(dst, &PP->tmC, cb * kMmaM, i0, fbar);
+        bulk_load(dst + SM::b_off, tiles + (size_t)(i0 / kMmaKC) * 2 * NN * kMmaKC,
+                  2u * NN * 128u, fbar);
+        // the split arrays are padded to a multiple of 128 floats
+        bulk_load(dst + SM::coef_off, rA + i0, 128u, fbar);
+        bulk_load(dst + SM::coef_off + 128u, rAL + i0, 128u, fbar);
+        ++issued;
       }
-      args.cnt[cb] = 0u;
-      double* ab = args.blkacc + cb * 4;
-      ab[0] = t0;
-      ab[1] = t1;
-      ab[2] = t2;
-      __threadfence();
-      const unsigned prev = atomicAdd(args.gcnt, 1u);
-      s_last = (prev == (unsigned)(args.nblk - 1));
+      // every copy has landed before the CTA may exit
+      for (int s = 0; s < NS && s < issued; ++s) {
+        const int last = s + ((issued - 1 - s) / NS) * NS;
+        if (!mbar_wait(smem_addr(&full_bar[s]), (last / NS) & 1, kMmaWait)) s_err = 1;
+      }
     }
-    __syncthreads();
+  } else if (wid == 9) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      for (int ch = 0; ch < nch; ++ch) {
+        const int s = ch % NS, b = ch & 1;
+        if (!mbar_wait(smem_addr(&full_bar[s]), (ch / NS) & 1, kMmaWait) ||
+            !mbar_wait(smem_addr(&afull[b]), (ch >> 1) & 1, kMmaWait)) {
+          s_err = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t bhi = base + (uint32_t)s * SM::stage + SM::b_off;
+        const uint32_t blo = bhi + (uint32_t)NN * 128u;
+        const uint32_t ahi = tmem + kTmA + 64u * b, alo = ahi + 32u;
+#pragma unroll
+        for (int k = 0; k < kMmaKC / 8; ++k) {
+          const uint32_t ko = k * 32;   // bytes of 8 tf32 in a B row
+          mma_tf32_ts(tmem, ahi + 8 * k, sdesc_sw128(bhi + ko), idesc, (ch > 0 || k > 0) ? 1u : 0u);
+          mma_tf32_ts(tmem, ahi + 8 * k, sdesc_sw128(blo + ko), idesc, 1u);
+          mma_tf32_ts(tmem, alo + 8 * k, sdesc_sw128(bhi + ko), idesc, 1u);
+        }
+        mma_commit(smem_addr(&empty_bar[s]));
+        mma_commit(smem_addr(&aempty[b]));
+      }
+      mma_commit(smem_addr(&accf));   // tracks every MMA issued above
+    }
+  } else {
+    // ---------------- consumers ----------------
+    const int c = tid & (kMmaM - 1), h = tid >> 7;
+    const int j = cb * kMmaM + c;
+    const bool jv = j < m;
+    const float k2 = P.k2;
+    const float2 k2v = f2(k2, k2), m1 = f2(-1.f, -1.f);
+    const float Kj = jv ? P.cs[gb].K[j] : P.M;
+    const float ccj = jv ? P.cs[gb].KL[j] * k2 : 0.f;
+    const float2 nK2 = f2(-Kj, -Kj), cc2 = f2(ccj, ccj);
+    const uint32_t tlane = (uint32_t)((wid & 3) * 32) << 16;
+    float ref = 0.f, rr = -INFINITY, pscale = 1.f;
+    float2 S2 = f2(0.f, 0.f);
+    bool werr = false;
+    for (int ch = 0; ch < nch; ++ch) {
+      const int s = ch % NS, b = ch & 1;
+      if (!__all_sync(0xffffffffu, mbar_wait(smem_addr(&full_bar[s]), (ch / NS) & 1, kMmaWait))) {
+        werr = true;
+        break;
+      }
+      const unsigned char* stg = sbase + (size_t)s * SM::stage;
+      const float* tile = reinterpret_cast<const float*>(stg);
+      const float4* cA = reinterpret_cast<const float4*>(stg + SM::coef_off) + h * 4;
+      const float4* cAL = reinterpret_cast<const float4*>(stg + SM::coef_off + 128) + h * 4;
+      float2 y[8];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 av = cA[q], alv = cAL[q];
+        const int r = h * 16 + 4 * q;
+        const float2 c0 = f2(tile[(r + 0) * kMmaM + c], tile[(r + 1) * kMmaM + c]);
+        const float2 c1 = f2(tile[(r + 2) * kMmaM + c], tile[(r + 3) * kMmaM + c]);
+        const float2 t0 = __ffma2_rn(c0, m1, __fadd2_rn(f2(av.x, av.y), nK2));
+        const float2 t1 = __ffma2_rn(c1, m1, __fadd2_rn(f2(av.z, av.w), nK2));
+        y[2 * q + 0] = __ffma2_rn(t0, k2v, __ffma2_rn(f2(alv.x, alv.y), k2v, cc2));
+        y[2 * q + 1] = __ffma2_rn(t1, k2v, __ffma2_rn(f2(alv.z, alv.w), k2v, cc2));
+      }
+      const int r0 = i_beg + ch * kMmaKC + h * 16;
+      if (!jv || r0 + 16 > i_end) {
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+          y[p].x = (jv && r0 + 2 * p < i_end) ? y[p].x : -INFINITY;
+          y[p].y = (jv && r0 + 2 * p + 1 < i_end) ? y[p].y : -INFINITY;
+        }
+      }
+      // the stage's cost and coefficients are read
+      __syncwarp();
+      if (lane == 0) mbar_arrive1(smem_addr(&empty_bar[s]));
+      float2 z[8];
+      const float2 nr = f2(-ref, -ref);
+#pragma unroll
+      for (int p = 0; p < 8; ++p) z[p] = ref == 0.f ? y[p] : __fadd2_rn(y[p], nr);
+      float mx = fmaxf(fmaxf(fmaxf(z[0].x, z[0].y), fmaxf(z[1].x, z[1].y)),
+                       fmaxf(fmaxf(z[2].x, z[2].y), fmaxf(z[3].x, z[3].y)));
+      mx = fmaxf(mx, fmaxf(fmaxf(fmaxf(z[4].x, z[4].y), fmaxf(z[5].x, z[5].y)),
+                           fmaxf(fmaxf(z[6].x, z[6].y), fmaxf(z[7].x, z[7].y))));
+      rr = fmaxf(rr, mx);
+      if (rr > -INFINITY && needs_move(rr, ref)) {
+        float Ss = S2.x + S2.y;
+        move_ref(rr, ref, Ss);
+        S2 = f2(Ss, 0.f);
+        pscale = scale2(1.f, ref);
+        const float2 nr2 = f2(-ref, -ref);
+#pragma unroll
+        for (int p = 0; p < 8; ++p) z[p] = __fadd2_rn(y[p], nr2);
+      }
+      float2 e[8];
+#pragma unroll
+      for (int p = 0; p < 8; ++p) e[p] = ex2_2(z[p]);
+      S2 = __fadd2_rn(S2, __fadd2_rn(__fadd2_rn(__fadd2_rn(e[0], e[1]), __fadd2_rn(e[2], e[3])),
+                                     __fadd2_rn(__fadd2_rn(e[4], e[5]), __fadd2_rn(e[6], e[7]))));
+      if (ref != 0.f) {   // the product needs the terms at their absolute scale
+        const float2 ps = f2(pscale, pscale);
+#pragma unroll
+        for (int p = 0; p < 8; ++p) e[p] = __fmul2_rn(e[p], ps);
+      }
+      uint32_t hv[16], lv[16];
+#pragma unroll
+      for (int p = 0; p < 8; ++p) {
+        tf32_split(e[p].x, hv[2 * p], lv[2 * p]);
+        tf32_split(e[p].y, hv[2 * p + 1], lv[2 * p + 1]);
+      }
+      // A buffer b is free once the MMAs of chunk ch - 2 are done
+      if (ch >= 2 &&
+          !__all_sync(0xffffffffu, mbar_wait(smem_addr(&aempty[b]), ((ch - 2) >> 1) & 1, kMmaWait))) {
+        werr = true;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t ta = tmem + tlane + kTmA + 64u * b + 16u * h;
+      tmem_st16(ta, hv);
+      tmem_st16(ta + 32u, lv);
+      tmem_st_wait();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive1(smem_addr(&afull[b]));
+    }
+    // all products done (bounded) before the accumulator is read
+    if (!__all_sync(0xffffffffu, mbar_wait(smem_addr(&accf), 0, kMmaWait))) werr = true;
+    if (werr && lane == 0) s_err = 1;
+    tc_fence_after();
+    const float S = S2.x + S2.y;
+    s_lr[h][c] = (S > 0.f) ? ref : -INFINITY;
+    s_ls[h][c] = (double)S;
+    cons_sync();
+    if (tid < kMmaM) {
+      float R = -INFINITY;
+      double Sd = 0.0;
+      merge_d(R, Sd, s_lr[0][c], (float)s_ls[0][c]);
+      merge_d(R, Sd, s_lr[1][c], (float)s_ls[1][c]);
+      float* dst = args.part + ((size_t)seg * m + (jv ? j : 0)) * (NN + 4);
+      // accumulator row c lives in TMEM lane c (warp w reads lanes 32w..32w+31)
+#pragma unroll
+      for (int q = 0; q < NN / 16; ++q) {
+        float v[16];
+        tmem_ld16(tmem + tlane + q * 16, v);
+        if (jv) {
+#pragma unroll
+          for (int u = 0; u < 16; ++u) dst[4 + q * 16 + u] = nch == 0 ? 0.f : v[u];
+        }
+      }
+      if (jv) {
+        dst[0] = R;
+        dst[1] = (float)Sd;
+      }
+    }
   }
-  if (!s_last) return;
-  __threadfence();
-  double tot[3];
-  grid_sum3(args.blkacc, args.nblk, tot, s_red);
+  tc_fence_before();
+  __syncthreads();
+  if (wid == 9) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmCols);
+  }
+  if (wid >= 8) return;
   if (tid == 0) {
-    *args.gcnt = 0u;
-    st->l1_col = tot[0];
-    st->sum_wL = tot[1];
-    st->qsemi = st->sum_af + tot[2];   // Q_semi(f_k) = <f_k, a> + <h, b>
-    st->iter += 1;
-    st->nr_ok = 0;
-    if (st->numeric > 0) st->done = 3;
-    else if (tot[0] < st->tol) st->done = 1;
-    else if (st->iter >= st->max_iter) st->done = 2;
+    if (s_err) atomicAdd(&st->numeric, 1);
+    epi.last = arrive_count(&args.cnt[cb]) == (unsigned)(args.nseg - 1);
   }
+  cons_sync();
+  if (!epi.last) return;
+  colmma_finish<NN>(args, P, sbase, epi, cb, gb, dst_g);
 }
 
 // ---------------------------------------------------------------------------
@@ -430,19 +758,26 @@ size_t mma_tiles_floats(int n, int k) {
 }
 
 template <int NN>
-static cudaError_t launch_colmma_k(const AccArgs& a, const float* tiles, int ncolblk,
+static cudaError_t launch_colmma_k(const AccArgs& a, bool tma, const float* tiles, int ncolblk,
                                    cudaStream_t s) {
   dim3 grid(ncolblk, a.nseg);
-  colmma_kernel<NN><<<grid, 256, MmaSmem<NN>::bytes, s>>>(a, tiles);
+  if (tma)
+    colmma_tma_kernel<NN><<<grid, kTmThreads, TmaSmem<NN>::bytes, s>>>(a, tiles);
+  else
+    colmma_kernel<NN><<<grid, 256, MmaSmem<NN>::bytes, s>>>(a, tiles);
   return cudaGetLastError();
 }
 
-cudaError_t launch_colmma(const AccArgs& a, const float* tiles, int ncolblk, cudaStream_t s) {
+// The staged kernel needs the cost's tensor map (rows 16-byte aligned) and
+// segments of whole 32-row chunks.
+cudaError_t launch_colmma(const AccArgs& a, const Prob& hP, const float* tiles, int ncolblk,
+                          cudaStream_t s) {
+  const bool tma = hP.has_tmC && a.seg_len % kMmaKC == 0;
   switch (mma_width(a.k)) {
-    case 16: return launch_colmma_k<16>(a, tiles, ncolblk, s);
-    case 32: return launch_colmma_k<32>(a, tiles, ncolblk, s);
-    case 48: return launch_colmma_k<48>(a, tiles, ncolblk, s);
-    default: return launch_colmma_k<64>(a, tiles, ncolblk, s);
+    case 16: return launch_colmma_k<16>(a, tma, tiles, ncolblk, s);
+    case 32: return launch_colmma_k<32>(a, tma, tiles, ncolblk, s);
+    case 48: return launch_colmma_k<48>(a, tma, tiles, ncolblk, s);
+    default: return launch_colmma_k<64>(a, tma, tiles, ncolblk, s);
   }
 }
 
@@ -463,6 +798,14 @@ void init_mma_attributes() {
                        (int)MmaSmem<48>::bytes);
   cudaFuncSetAttribute(colmma_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)MmaSmem<64>::bytes);
+  cudaFuncSetAttribute(colmma_tma_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)TmaSmem<16>::bytes);
+  cudaFuncSetAttribute(colmma_tma_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)TmaSmem<32>::bytes);
+  cudaFuncSetAttribute(colmma_tma_kernel<48>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)TmaSmem<48>::bytes);
+  cudaFuncSetAttribute(colmma_tma_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)TmaSmem<64>::bytes);
 }
 
 }  // namespace eotk
