@@ -618,7 +618,7 @@ __global__ void __launch_bounds__(kTmThreads, 2)
     const float2 nK2 = f2(-Kj, -Kj), cc2 = f2(ccj, ccj);
     const uint32_t tlane = (uint32_t)((wid & 3) * 32) << 16;
     float ref = 0.f, rr = -INFINITY, pscale = 1.f;
-    float2 S2 = f2(0.f, 0.f);
+    float2 S2 = f2(0.f, 0.f), C2 = f2(0.f, 0.f);   // running sum, compensation
     bool werr = false;
     for (int ch = 0; ch < nch; ++ch) {
       const int s = ch % NS, b = ch & 1;
@@ -663,6 +663,7 @@ __global__ void __launch_bounds__(kTmThreads, 2)
                            fmaxf(fmaxf(z[6].x, z[6].y), fmaxf(z[7].x, z[7].y))));
       rr = fmaxf(rr, mx);
       if (rr > -INFINITY && needs_move(rr, ref)) {
+        kahan_fold2(S2, C2);
         float Ss = S2.x + S2.y;
         move_ref(rr, ref, Ss);
         S2 = f2(Ss, 0.f);
@@ -674,8 +675,8 @@ __global__ void __launch_bounds__(kTmThreads, 2)
       float2 e[8];
 #pragma unroll
       for (int p = 0; p < 8; ++p) e[p] = ex2_2(z[p]);
-      S2 = __fadd2_rn(S2, __fadd2_rn(__fadd2_rn(__fadd2_rn(e[0], e[1]), __fadd2_rn(e[2], e[3])),
-                                     __fadd2_rn(__fadd2_rn(e[4], e[5]), __fadd2_rn(e[6], e[7]))));
+      kahan_add2(S2, C2, __fadd2_rn(__fadd2_rn(__fadd2_rn(e[0], e[1]), __fadd2_rn(e[2], e[3])),
+                                    __fadd2_rn(__fadd2_rn(e[4], e[5]), __fadd2_rn(e[6], e[7]))));
       if (ref != 0.f) {   // the product needs the terms at their absolute scale
         const float2 ps = f2(pscale, pscale);
 #pragma unroll
@@ -706,15 +707,15 @@ __global__ void __launch_bounds__(kTmThreads, 2)
     if (!__all_sync(0xffffffffu, mbar_wait(smem_addr(&accf), 0, kMmaWait))) werr = true;
     if (werr && lane == 0) s_err = 1;
     tc_fence_after();
-    const float S = S2.x + S2.y;
-    s_lr[h][c] = (S > 0.f) ? ref : -INFINITY;
-    s_ls[h][c] = (double)S;
+    const double S = ((double)S2.x - (double)C2.x) + ((double)S2.y - (double)C2.y);
+    s_lr[h][c] = (S > 0.0) ? ref : -INFINITY;
+    s_ls[h][c] = S;
     cons_sync();
     if (tid < kMmaM) {
       float R = -INFINITY;
       double Sd = 0.0;
-      merge_d(R, Sd, s_lr[0][c], (float)s_ls[0][c]);
-      merge_d(R, Sd, s_lr[1][c], (float)s_ls[1][c]);
+      merge_dd(R, Sd, s_lr[0][c], s_ls[0][c]);
+      merge_dd(R, Sd, s_lr[1][c], s_ls[1][c]);
       float* dst = args.part + ((size_t)seg * m + (jv ? j : 0)) * (NN + 4);
       // accumulator row c lives in TMEM lane c (warp w reads lanes 32w..32w+31)
 #pragma unroll

@@ -284,6 +284,7 @@ __device__ void st_consume(const Prob& P, const StGeom& g, const PassIo& io, StS
   float nKr[4], ccr[4];               // the same per row (row pass)
   float ref[4] = {0.f, 0.f, 0.f, 0.f}, rr[4];
   float2 Sa[4] = {};                  // column pass: Sa[0] = (S0, S1), Sa[1] = (S2, S3)
+  float2 Ca[2] = {};                  // column pass: their compensations
   bool ref0 = true;
   bool werr = false;                  // this warp gave up waiting
 
@@ -296,6 +297,8 @@ __device__ void st_consume(const Prob& P, const StGeom& g, const PassIo& io, StS
 
   auto publish = [&](int b) {
     if (COL) {
+      kahan_fold2(Sa[0], Ca[0]);
+      kahan_fold2(Sa[1], Ca[1]);
       sh.pc[warp][lane * 4 + 0] = f2(ref[0], Sa[0].x);
       sh.pc[warp][lane * 4 + 1] = f2(ref[1], Sa[0].y);
       sh.pc[warp][lane * 4 + 2] = f2(ref[2], Sa[1].x);
@@ -351,6 +354,7 @@ __device__ void st_consume(const Prob& P, const StGeom& g, const PassIo& io, StS
       ref[c] = 0.f;
       rr[c] = -INFINITY;
       Sa[c] = f2(0.f, 0.f);
+      if (c < 2) Ca[c] = f2(0.f, 0.f);
     }
     if (COL) {
       float K[4], KL[4];
@@ -438,6 +442,8 @@ __device__ void st_consume(const Prob& P, const StGeom& g, const PassIo& io, StS
                                : (needs_move(rr[0], ref[0]) || needs_move(rr[1], ref[1]) ||
                                   needs_move(rr[2], ref[2]) || needs_move(rr[3], ref[3]));
         if (move) {
+          kahan_fold2(Sa[0], Ca[0]);
+          kahan_fold2(Sa[1], Ca[1]);
           move_ref(rr[0], ref[0], Sa[0].x);
           move_ref(rr[1], ref[1], Sa[0].y);
           move_ref(rr[2], ref[2], Sa[1].x);
@@ -450,10 +456,10 @@ __device__ void st_consume(const Prob& P, const StGeom& g, const PassIo& io, StS
             zb[u] = __fadd2_rn(yb[u], mb);
           }
         }
-        Sa[0] = __fadd2_rn(Sa[0], __fadd2_rn(__fadd2_rn(ex2_2(za[0]), ex2_2(za[1])),
-                                             __fadd2_rn(ex2_2(za[2]), ex2_2(za[3]))));
-        Sa[1] = __fadd2_rn(Sa[1], __fadd2_rn(__fadd2_rn(ex2_2(zb[0]), ex2_2(zb[1])),
-                                             __fadd2_rn(ex2_2(zb[2]), ex2_2(zb[3]))));
+        kahan_add2(Sa[0], Ca[0], __fadd2_rn(__fadd2_rn(ex2_2(za[0]), ex2_2(za[1])),
+                                            __fadd2_rn(ex2_2(za[2]), ex2_2(za[3]))));
+        kahan_add2(Sa[1], Ca[1], __fadd2_rn(__fadd2_rn(ex2_2(zb[0]), ex2_2(zb[1])),
+                                            __fadd2_rn(ex2_2(zb[2]), ex2_2(zb[3]))));
       } else {
         const float4 ca = *reinterpret_cast<const float4*>(cA + lane * 4);
         const float4 cl = *reinterpret_cast<const float4*>(cAL + lane * 4);

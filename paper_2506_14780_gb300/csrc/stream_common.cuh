@@ -129,6 +129,25 @@ __device__ __forceinline__ void warp0_grid_sum3(const double* __restrict__ acc, 
 
 __device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
 
+// Compensated (Kahan) accumulation of a pair of running sums: S + x with the
+// rounding error carried in c (the sum is S - c).  A long serial float32 sum
+// would otherwise leave a relative error growing with the square root of the
+// number of additions, which the L1 marginal test (a sum of absolute
+// deviations) would read as a floor.
+__device__ __forceinline__ void kahan_add2(float2& S, float2& c, float2 x) {
+  const float2 m1 = f2(-1.f, -1.f);
+  const float2 y = __ffma2_rn(c, m1, x);                 // x - c
+  const float2 t = __fadd2_rn(S, y);
+  c = __ffma2_rn(y, m1, __ffma2_rn(S, m1, t));           // (t - S) - y
+  S = t;
+}
+
+// Fold the carried error into the sum (before a rescaling or a read-out).
+__device__ __forceinline__ void kahan_fold2(float2& S, float2& c) {
+  S = __ffma2_rn(c, f2(-1.f, -1.f), S);
+  c = f2(0.f, 0.f);
+}
+
 __device__ __forceinline__ float2 ex2_2(float2 y) {
   return make_float2(ex2_approx(y.x), ex2_approx(y.y));
 }
