@@ -57,6 +57,7 @@ cudaError_t launch_wtw_reduce(const AccArgs& a, double* WtW, double* gw, cudaStr
 cudaError_t launch_colmma(const AccArgs& a, const Prob& hP, const float* tiles, int ncolblk,
                           cudaStream_t s);
 cudaError_t launch_build_tiles(const float* Z, int n, int kk, float* tiles, cudaStream_t s);
+cudaError_t launch_rowmma(const AccArgs& a, const float* tiles, int nrowblk, cudaStream_t s);
 int mma_record(int k);
 size_t mma_tiles_floats(int n, int k);
 void init_mma_attributes();
@@ -243,6 +244,14 @@ static eot_status encode_cost_map(Prob& P) {
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS)
     return fail(EOT_ECUDA, "cuTensorMapEncodeTiled failed (code " + std::to_string((int)r) + ")");
+  // row-direction tiles of the tensor-core products: 128 rows of 32 columns
+  const cuuint32_t box_r[2] = {32, 128};
+  const CUresult r2 = enc(&P.tmCr, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(P.C),
+                          dims, strides, box_r, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r2 != CUDA_SUCCESS)
+    return fail(EOT_ECUDA, "cuTensorMapEncodeTiled failed (code " + std::to_string((int)r2) + ")");
   P.has_tmC = 1;
   return EOT_OK;
 }
@@ -265,6 +274,7 @@ struct Solver {
   int s4_nseg = 1, s4_seglen = 0, s4_ncolblk = 0, s4_K = 0;
   int ek_K = 0, kc_nseg = 1, kc_seglen = 0, kr_nseg = 1, kr_seglen = 0, kr_nrowblk = 0;
   int mm_ncolblk = 0, mm_nseg = 1, mm_seglen = 0;   // tensor-core column products
+  int rm_nrowblk = 0, rm_nseg = 1, rm_seglen = 0;   // tensor-core row products
   int sk_gcol = 0, sk_grow = 0, sk_slots_col = 1, sk_slots_row = 1;   // stream passes
   // memory
   void* mem = nullptr;
@@ -286,8 +296,8 @@ struct Solver {
          *dw = nullptr;
   // modes
   float *Zb = nullptr, *Xb = nullptr, *Yb = nullptr, *Bm = nullptr, *kcpart = nullptr,
-        *krpart = nullptr;
-  unsigned *kccnt = nullptr, *krcnt = nullptr;
+        *krpart = nullptr, *tilesY = nullptr, *rmpart = nullptr;
+  unsigned *kccnt = nullptr, *krcnt = nullptr, *rmcnt = nullptr;
   double *epart = nullptr, *evpart = nullptr, *GXX = nullptr, *Tm = nullptr, *cvec = nullptr,
          *theta = nullptr, *resid = nullptr;
   int* efail = nullptr;
@@ -351,6 +361,10 @@ struct Solver {
       kr_nseg = std::max(1, std::min(ceil_div(m, 32), (2 * nsm + kr_nrowblk - 1) / kr_nrowblk));
       kr_seglen = ceil_div(ceil_div(m, kr_nseg), 32) * 32;
       kr_nseg = ceil_div(m, kr_seglen);
+      rm_nrowblk = ceil_div(n, 128);
+      rm_nseg = std::max(1, std::min(ceil_div(m, 32), (2 * nsm) / rm_nrowblk));
+      rm_seglen = ceil_div(ceil_div(m, rm_nseg), 32) * 32;
+      rm_nseg = ceil_div(m, rm_seglen);
     }
   }
 
@@ -478,6 +492,9 @@ struct Solver {
       krpart = A.take<float>((size_t)kr_nseg * n * (ek_K + 2));
       kccnt = A.take<unsigned>(mm_ncolblk);
       krcnt = A.take<unsigned>(kr_nrowblk);
+      tilesY = A.take<float>(mma_tiles_floats(m, p));
+      rmpart = A.take<float>((size_t)rm_nseg * n * mma_record(p));
+      rmcnt = A.take<unsigned>(rm_nrowblk);
       epart = A.take<double>((size_t)nch * p * p);
       evpart = A.take<double>((size_t)nch * p);
       GXX = A.take<double>((size_t)p * p);
@@ -577,6 +594,47 @@ struct Solver {
     return a;
   }
 
+  AccArgs rmma_args(int fb, int gb, const float* Z, float* out) const {
+    AccArgs a{};
+    a.P = dP;
+    a.mode = 2;  // ACC_KROW
+    a.k = p;
+    a.Z = Z;
+    a.out = out;
+    a.part = rmpart;
+    a.cnt = rmcnt;
+    a.nseg = rm_nseg;
+    a.seg_len = rm_seglen;
+    a.nblk = rm_nrowblk;
+    a.fbuf = fb;
+    a.gbuf = gb;
+    return a;
+  }
+  // Op(pi) Z: on the tensor cores when the cost has its tensor maps, else on
+  // the CUDA cores
+  cudaError_t kapply_row(int fb, int gb, const float* Z, float* out, cudaStream_t s) {
+    if (!hP.has_tmC) return launch_rowacc(krow_args(fb, gb, Z, out), kr_nrowblk, s);
+    cudaError_t e = launch_build_tiles(Z, m, p, tilesY, s);
+    if (e == cudaSuccess) e = launch_rowmma(rmma_args(fb, gb, Z, out), tilesY, rm_nrowblk, s);
+    return e;
+  }
+  // The captured graphs bake in the choice between the staged (tensor-map)
+  // kernels and the others: drop them when that choice changes.
+  int graph_tma = -1;
+  void match_graphs_to_cost() {
+    const int want = hP.has_tmC ? 1 : 0;
+    if (graph_tma == want) return;
+    if (ex_sk) cudaGraphExecDestroy(ex_sk);
+    if (ex_sknr) cudaGraphExecDestroy(ex_sknr);
+    if (ex_eig) cudaGraphExecDestroy(ex_eig);
+    if (gr_sk) cudaGraphDestroy(gr_sk);
+    if (gr_sknr) cudaGraphDestroy(gr_sknr);
+    if (gr_eig) cudaGraphDestroy(gr_eig);
+    ex_sk = ex_sknr = ex_eig = nullptr;
+    gr_sk = gr_sknr = gr_eig = nullptr;
+    graph_tma = want;
+  }
+
   // weighted Gram  out = A^T diag(w or 1/w) B  (+ vout = sum_i vw_i A_i)
   cudaError_t wgram(const float* Am, const float* Bm_, const double* w, int wmode, int len, int q,
                     const double* vw, const float* vsrc, double* part, double* vpart, double* out,
@@ -641,7 +699,7 @@ struct Solver {
   cudaError_t body_eig(cudaStream_t s, int fb, int gb) {
     cudaError_t e = launch_build_tiles(Zb, n, p, tilesZ, s);
     if (e == cudaSuccess) e = launch_colmma(kcol_args(fb, gb, Zb, Yb), hP, tilesZ, mm_ncolblk, s);
-    if (e == cudaSuccess) e = launch_rowacc(krow_args(fb, gb, Yb, Xb), kr_nrowblk, s);
+    if (e == cudaSuccess) e = kapply_row(fb, gb, Yb, Xb, s);
     if (e != cudaSuccess) return e;
     // GXX = X^T D_a X (+ c = a^T X), T = Z^T D_a X
     e = wgram(Xb, Xb, hP.a, 0, n, p, hP.a, Xb, epart, evpart, GXX, cvec, 0, s);
@@ -710,8 +768,8 @@ struct Solver {
   bool coop_ok = true;
   eot_status run_sk(int max_iter, int graph_cap, bool* used_coop) {
     *used_coop = false;
-    if (coop_ok && !t_concurrent && !f64 && !gram && hP.sk_gcol > 0 && hP.sk_gcol == hP.sk_grow && m % 4 == 0 &&
-        (reinterpret_cast<uintptr_t>(hP.C) & 15u) == 0) {
+    if (coop_ok && !t_concurrent && !f64 && !gram && hP.sk_gcol > 0 &&
+        hP.sk_gcol == hP.sk_grow && hP.has_tmC) {
       const cudaError_t e = launch_sk_coop(dP, hP, max_iter + 4, ctx->stream);
       if (e == cudaSuccess) {
         *used_coop = true;
@@ -1020,7 +1078,8 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
     CUDA_TRY(cudaMemsetAsync(P.f[0], 0, n * sizeof(double), s));
   }
   CUDA_TRY(cudaMemsetAsync(P.g[0], 0, m * sizeof(double), s));
-  // ---- graphs (captured once per solver) ----
+  // ---- graphs (captured once per solver and kernel choice) ----
+  S->match_graphs_to_cost();
   if (!S->ex_sk) {
     eot_status e = S->build_loop([&](cudaStream_t cs_) { return S->body_sk(cs_); }, 0, &S->gr_sk,
                                  &S->ex_sk);
@@ -1484,6 +1543,11 @@ eot_status eot_kapply(eot_side side, int32_t n, int32_t m, int32_t k, const floa
   if (side == EOT_SIDE_COL) {
     CUDA_TRY(launch_build_tiles(Z, n, k, S->tilesZ, s));
     CUDA_TRY(launch_colmma(aa, S->hP, S->tilesZ, S->mm_ncolblk, s));
+  } else if (S->hP.has_tmC) {
+    AccArgs ar = S->rmma_args(0, 0, Z, out);
+    ar.k = k;
+    CUDA_TRY(launch_build_tiles(Z, m, k, S->tilesY, s));
+    CUDA_TRY(launch_rowmma(ar, S->tilesY, S->rm_nrowblk, s));
   } else {
     CUDA_TRY(launch_rowacc(aa, S->kr_nrowblk, s));
   }
@@ -1558,15 +1622,16 @@ eot_status eot_spectral_modes(int32_t n, int32_t m, const float* C, const double
   cudaStream_t s;
   eot_status st = standalone_solver(n, m, ell, p, &S, &s, stream);
   if (st != EOT_OK) return st;
+  st = load_weights(S, a, b, s, 0);
+  if (st != EOT_OK) return st;
+  st = standalone_grid(S, C, f, n, g, m, eps, s, nullptr);
+  if (st != EOT_OK) return st;
+  S->match_graphs_to_cost();
   if (!S->ex_eig) {
     st = S->build_loop([&](cudaStream_t cs_) { return S->body_eig(cs_, 0, 0); }, 1, &S->gr_eig,
                        &S->ex_eig);
     if (st != EOT_OK) return st;
   }
-  st = load_weights(S, a, b, s, 0);
-  if (st != EOT_OK) return st;
-  st = standalone_grid(S, C, f, n, g, m, eps, s, nullptr);
-  if (st != EOT_OK) return st;
   Prob& P = S->hP;
   CUDA_TRY(cudaMemcpyAsync(P.f[0], f, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(P.g[0], g, m * sizeof(double), cudaMemcpyDeviceToDevice, s));

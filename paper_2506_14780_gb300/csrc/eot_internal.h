@@ -100,6 +100,7 @@ struct Prob {
   // staged stream passes (stream.cu): grid sizes (0: not used), contributor
   // slots per output block, partial states, arrival counters, block sums
   CUtensorMap tmC;         // 2-D tensor map of C (box 128 columns x 32 rows), when used
+  CUtensorMap tmCr;        // the same, box 32 columns x 128 rows, 128-byte swizzle
   int has_tmC;             // tmC encoded for this C
   int sk_gcol, sk_grow;
   int sk_slots_col, sk_slots_row;

@@ -59,20 +59,21 @@ struct MmaEpi {
   unsigned last;
 };
 
-// Epilogue of the CTA that arrived last on column block cb: merge the segments'
-// (reference, sum) heads and product rows of its 128 columns, write
-// Op(pi)^T Z (or, in the SK-NR pass, W = pi(f_k, h)^T V with h = f_k^{C,eps},
+// Epilogue of the CTA that arrived last on output block cb (128 columns, or
+// 128 rows for the row-direction product; `len` = m or n): merge the
+// segments' (reference, sum) heads and product rows of its 128 indices, write
+// the product (or, in the SK-NR pass, W = pi(f_k, h)^T V with h = f_k^{C,eps},
 // the new potential h and its split arrays, d_j, and the block partials of
 // W^T D_b^{-1} W and d^T W; the last block takes the grid-wide step: L1
 // test, Q_semi(f_k), iteration count).  Run by threads 0..255 (named barrier
 // 1); `smem` is scratch of at least 128 (NN + 3) floats.
 template <int NN>
 __device__ void colmma_finish(const AccArgs& args, const Prob& P, unsigned char* smem,
-                              MmaEpi& epi, int cb, int gb, int dst_g) {
+                              MmaEpi& epi, int cb, int gb, int dst_g, int len) {
   State* st = P.st;
   const bool s4 = args.mode == 1;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int m = P.m, kk = args.k;
+  const int m = len, kk = args.k;
   const int c = tid & (kMmaM - 1);
   const int j = cb * kMmaM + c;
   const bool jv = j < m;
@@ -424,7 +425,7 @@ __global__ void __launch_bounds__(256) colmma_kernel(AccArgs args, const float* 
   if (tid == 0) epi.last = arrive_count(&args.cnt[cb]) == (unsigned)(args.nseg - 1);
   __syncthreads();
   if (!epi.last) return;
-  colmma_finish<NN>(args, P, sbase, epi, cb, gb, dst_g);
+  colmma_finish<NN>(args, P, sbase, epi, cb, gb, dst_g, m);
 }
 
 // ---------------------------------------------------------------------------
@@ -492,13 +493,20 @@ __device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) 
   lo = __float_as_uint(__fsub_rn(x, __uint_as_float(h))) & 0xFFFFE000u;
 }
 
-template <int NN>
+// ROW = false: column direction (output index j over 128-column blocks,
+// reduction over rows i; the cost tile is 32 rows x 128 columns).  ROW = true:
+// the row-direction product Op(pi) Z, out_i = sum_j 2^{y_ij} Z_j at absolute
+// scale (Eq. def_Op_pi); output index i over 128-row blocks, reduction over
+// columns j, the cost tile 128 rows x 32 columns from a second tensor map with
+// 128-byte swizzle (16-byte chunk q of row r at chunk q ^ (r & 7)), so that a
+// thread reads its row's 16 values with four conflict-free 16-byte loads.
+template <int NN, bool ROW>
 __global__ void __launch_bounds__(kTmThreads, 2)
-    colmma_tma_kernel(AccArgs args, const float* __restrict__ tiles) {
+    mma_tma_kernel(AccArgs args, const float* __restrict__ tiles) {
   const Prob* PP = args.P;
   const Prob& P = *PP;
   State* st = P.st;
-  const bool s4 = args.mode == 1;
+  const bool s4 = !ROW && args.mode == 1;
   if (s4 && st->done) return;
   const int fb = s4 ? st->cur_f : args.fbuf;
   const int gb = s4 ? st->cur_g : args.gbuf;
@@ -523,9 +531,11 @@ __global__ void __launch_bounds__(kTmThreads, 2)
 
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int n = P.n, m = P.m;
+  const int olen = ROW ? n : m;     // output indices
+  const int rlen = ROW ? m : n;     // reduction indices
   const int cb = blockIdx.x, seg = blockIdx.y;
-  const int i_beg = seg * args.seg_len;
-  const int i_end = min(n, i_beg + args.seg_len);
+  const int i_beg = seg * args.seg_len;   // reduction range of this segment
+  const int i_end = min(rlen, i_beg + args.seg_len);
   const int nch = i_end > i_beg ? (i_end - i_beg + kMmaKC - 1) / kMmaKC : 0;
   constexpr uint32_t idesc = idesc_tf32(kMmaM, NN);
 
@@ -551,8 +561,8 @@ __global__ void __launch_bounds__(kTmThreads, 2)
   if (wid == 8) {
     // ---------------- producer ----------------
     if (lane == 0) {
-      const float* rA = P.rs[fb].A;
-      const float* rAL = P.rs[fb].AL;
+      const float* rA = ROW ? P.cs[gb].A : P.rs[fb].A;
+      const float* rAL = ROW ? P.cs[gb].AL : P.rs[fb].AL;
       int issued = 0;
       for (int ch = 0; ch < nch; ++ch) {
         const int s = ch % NS;
@@ -565,8 +575,11 @@ __global__ void __launch_bounds__(kTmThreads, 2)
         const uint32_t dst = base + (uint32_t)s * SM::stage;
         const int i0 = i_beg + ch * kMmaKC;   // a multiple of 32 (segments are)
         mbar_expect_tx(fbar, SM::tx);
-        // column cb * 128: the box starts on a 16-byte boundary
-        tma_load_2d(dst, &PP->tmC, cb * kMmaM, i0, fbar);
+        // the box's first column (cb * 128, or i0) starts on a 16-byte boundary
+        if (ROW)
+          tma_load_2d(dst, &PP->tmCr, i0, cb * kMmaM, fbar);
+        else
+          tma_load_2d(dst, &PP->tmC, cb * kMmaM, i0, fbar);
         bulk_load(dst + SM::b_off, tiles + (size_t)(i0 / kMmaKC) * 2 * NN * kMmaKC,
                   2u * NN * 128u, fbar);
         // the split arrays are padded to a multiple of 128 floats
@@ -609,12 +622,13 @@ __global__ void __launch_bounds__(kTmThreads, 2)
   } else {
     // ---------------- consumers ----------------
     const int c = tid & (kMmaM - 1), h = tid >> 7;
-    const int j = cb * kMmaM + c;
-    const bool jv = j < m;
+    const int j = cb * kMmaM + c;       // output index (column, or row for ROW)
+    const bool jv = j < olen;
     const float k2 = P.k2;
     const float2 k2v = f2(k2, k2), m1 = f2(-1.f, -1.f);
-    const float Kj = jv ? P.cs[gb].K[j] : P.M;
-    const float ccj = jv ? P.cs[gb].KL[j] * k2 : 0.f;
+    const Split& os = ROW ? P.rs[fb] : P.cs[gb];
+    const float Kj = jv ? os.K[j] : P.M;
+    const float ccj = jv ? os.KL[j] * k2 : 0.f;
     const float2 nK2 = f2(-Kj, -Kj), cc2 = f2(ccj, ccj);
     const uint32_t tlane = (uint32_t)((wid & 3) * 32) << 16;
     float ref = 0.f, rr = -INFINITY, pscale = 1.f;
@@ -634,9 +648,16 @@ __global__ void __launch_bounds__(kTmThreads, 2)
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const float4 av = cA[q], alv = cAL[q];
-        const int r = h * 16 + 4 * q;
-        const float2 c0 = f2(tile[(r + 0) * kMmaM + c], tile[(r + 1) * kMmaM + c]);
-        const float2 c1 = f2(tile[(r + 2) * kMmaM + c], tile[(r + 3) * kMmaM + c]);
+        float2 c0, c1;
+        if (ROW) {
+          const float4 cv = reinterpret_cast<const float4*>(tile)[c * 8 + ((h * 4 + q) ^ (c & 7))];
+          c0 = f2(cv.x, cv.y);
+          c1 = f2(cv.z, cv.w);
+        } else {
+          const int r = h * 16 + 4 * q;
+          c0 = f2(tile[(r + 0) * kMmaM + c], tile[(r + 1) * kMmaM + c]);
+          c1 = f2(tile[(r + 2) * kMmaM + c], tile[(r + 3) * kMmaM + c]);
+        }
         const float2 t0 = __ffma2_rn(c0, m1, __fadd2_rn(f2(av.x, av.y), nK2));
         const float2 t1 = __ffma2_rn(c1, m1, __fadd2_rn(f2(av.z, av.w), nK2));
         y[2 * q + 0] = __ffma2_rn(t0, k2v, __ffma2_rn(f2(alv.x, alv.y), k2v, cc2));
@@ -716,7 +737,7 @@ __global__ void __launch_bounds__(kTmThreads, 2)
       double Sd = 0.0;
       merge_dd(R, Sd, s_lr[0][c], s_ls[0][c]);
       merge_dd(R, Sd, s_lr[1][c], s_ls[1][c]);
-      float* dst = args.part + ((size_t)seg * m + (jv ? j : 0)) * (NN + 4);
+      float* dst = args.part + ((size_t)seg * olen + (jv ? j : 0)) * (NN + 4);
       // accumulator row c lives in TMEM lane c (warp w reads lanes 32w..32w+31)
 #pragma unroll
       for (int q = 0; q < NN / 16; ++q) {
@@ -746,7 +767,7 @@ __global__ void __launch_bounds__(kTmThreads, 2)
   }
   cons_sync();
   if (!epi.last) return;
-  colmma_finish<NN>(args, P, sbase, epi, cb, gb, dst_g);
+  colmma_finish<NN>(args, P, sbase, epi, cb, gb, dst_g, olen);
 }
 
 // ---------------------------------------------------------------------------
@@ -763,7 +784,7 @@ static cudaError_t launch_colmma_k(const AccArgs& a, bool tma, const float* tile
                                    cudaStream_t s) {
   dim3 grid(ncolblk, a.nseg);
   if (tma)
-    colmma_tma_kernel<NN><<<grid, kTmThreads, TmaSmem<NN>::bytes, s>>>(a, tiles);
+    mma_tma_kernel<NN, false><<<grid, kTmThreads, TmaSmem<NN>::bytes, s>>>(a, tiles);
   else
     colmma_kernel<NN><<<grid, 256, MmaSmem<NN>::bytes, s>>>(a, tiles);
   return cudaGetLastError();
@@ -782,12 +803,34 @@ cudaError_t launch_colmma(const AccArgs& a, const Prob& hP, const float* tiles, 
   }
 }
 
+// Row-direction product on the tensor cores (needs the cost's tensor maps;
+// segments of whole 32-column chunks, output blocks of 128 rows).
+cudaError_t launch_rowmma(const AccArgs& a, const float* tiles, int nrowblk, cudaStream_t s) {
+  dim3 grid(nrowblk, a.nseg);
+  if (a.seg_len % kMmaKC != 0) return cudaErrorInvalidValue;
+  switch (mma_width(a.k)) {
+    case 16: mma_tma_kernel<16, true><<<grid, kTmThreads, TmaSmem<16>::bytes, s>>>(a, tiles); break;
+    case 32: mma_tma_kernel<32, true><<<grid, kTmThreads, TmaSmem<32>::bytes, s>>>(a, tiles); break;
+    case 48: mma_tma_kernel<48, true><<<grid, kTmThreads, TmaSmem<48>::bytes, s>>>(a, tiles); break;
+    default: mma_tma_kernel<64, true><<<grid, kTmThreads, TmaSmem<64>::bytes, s>>>(a, tiles); break;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_build_tiles(const float* Z, int n, int kk, float* tiles, cudaStream_t s) {
   const int NN = mma_width(kk);
   const long total = (long)((n + kMmaKC - 1) / kMmaKC) * NN * kMmaKC;
   const int blocks = (int)((total + 255) / 256);
   build_tiles_kernel<<<blocks < 4096 ? blocks : 4096, 256, 0, s>>>(Z, n, kk, NN, tiles);
   return cudaGetLastError();
+}
+
+template <int NN>
+static void set_tma_attr() {
+  cudaFuncSetAttribute(mma_tma_kernel<NN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)TmaSmem<NN>::bytes);
+  cudaFuncSetAttribute(mma_tma_kernel<NN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)TmaSmem<NN>::bytes);
 }
 
 void init_mma_attributes() {
@@ -799,14 +842,10 @@ void init_mma_attributes() {
                        (int)MmaSmem<48>::bytes);
   cudaFuncSetAttribute(colmma_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)MmaSmem<64>::bytes);
-  cudaFuncSetAttribute(colmma_tma_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)TmaSmem<16>::bytes);
-  cudaFuncSetAttribute(colmma_tma_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)TmaSmem<32>::bytes);
-  cudaFuncSetAttribute(colmma_tma_kernel<48>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)TmaSmem<48>::bytes);
-  cudaFuncSetAttribute(colmma_tma_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)TmaSmem<64>::bytes);
+  set_tma_attr<16>();
+  set_tma_attr<32>();
+  set_tma_attr<48>();
+  set_tma_attr<64>();
 }
 
 }  // namespace eotk

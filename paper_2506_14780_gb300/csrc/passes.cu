@@ -461,8 +461,7 @@ cudaError_t launch_stream_pass(const Prob* dP, const Prob& hP, bool col, int mod
 // The staged stream kernels (stream.cu) take every pass whose cost rows are
 // 16-byte aligned; the striped kernels below serve the rest.
 static bool stream_ok(const Prob& hP, bool col) {
-  return (col ? hP.sk_gcol : hP.sk_grow) > 0 && hP.m % 4 == 0 &&
-         (reinterpret_cast<uintptr_t>(hP.C) & 15u) == 0;
+  return (col ? hP.sk_gcol : hP.sk_grow) > 0 && hP.has_tmC;
 }
 
 cudaError_t launch_col_pass(const Prob* dP, const Prob& hP, int mode, cudaStream_t s) {
