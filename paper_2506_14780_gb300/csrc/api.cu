@@ -78,8 +78,9 @@ __global__ void wgram_partial_kernel(const float*, const float*, const double*, 
 __global__ void wgram_reduce_kernel(const double*, int, int, double*, const State*, int);
 __global__ void newton_kernel(const Prob*, const double*, const double*, const double*);
 __global__ void fprime_kernel(const Prob*);
-__global__ void eig_small_kernel(int, int, int, const double*, const double*, const double*,
-                                 float*, double*, double*, int*);
+void launch_eig_small(int p, int l, int mode, const double* GXX, const double* T,
+                      const double* c, float* B, double* theta, double* resid, int* fail,
+                      cudaStream_t s);
 __global__ void apply_kernel(const float*, const double*, const float*, int, int, float*);
 __global__ void init_block_kernel(float*, int, int, unsigned long long, const float*, int);
 __global__ void take_cols_kernel(const float*, int, int, int, float*);
@@ -689,7 +690,7 @@ struct Solver {
       if (e != cudaSuccess) break;
       e = launch_wtw_reduce(a, WtW, gw, s);
       if (e != cudaSuccess) break;
-      newton_kernel<<<1, 32, 0, s>>>(dP, WtW, gw, nullptr);
+      newton_kernel<<<1, 256, 0, s>>>(dP, WtW, gw, nullptr);
       fprime_kernel<<<std::min(ceil_div(n, 256), 4 * ctx->nsm), 256, 0, s>>>(dP);
       e = pass_col(MODE_TRIAL, s);
     }
@@ -706,7 +707,7 @@ struct Solver {
     if (e == cudaSuccess) e = wgram(Zb, Xb, hP.a, 0, n, p, nullptr, nullptr, epart, nullptr, Tm,
                                     nullptr, 0, s);
     if (e != cudaSuccess) return e;
-    eig_small_kernel<<<1, 256, 0, s>>>(p, ell, 1, GXX, Tm, cvec, Bm, theta, resid, efail);
+    launch_eig_small(p, ell, 1, GXX, Tm, cvec, Bm, theta, resid, efail, s);
     apply_kernel<<<ceil_div(n, 64), 256, (size_t)(p * p + 64 * p) * 4, s>>>(Xb, cvec, Bm, n, p,
                                                                            Zb);
     eig_ctl_kernel<<<1, 1, 0, s>>>(dSt, resid, efail);
@@ -1200,8 +1201,7 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
       // orthonormalise the start block: Z = (X0 - 1 c^T) L^{-T}
       CUDA_TRY(S->wgram(S->Xb, S->Xb, P.a, 0, n, S->p, P.a, S->Xb, S->epart, S->evpart, S->GXX,
                         S->cvec, 0, s));
-      eig_small_kernel<<<1, 256, 0, s>>>(S->p, ell, 0, S->GXX, S->Tm, S->cvec, S->Bm, S->theta,
-                                         S->resid, S->efail);
+      launch_eig_small(S->p, ell, 0, S->GXX, S->Tm, S->cvec, S->Bm, S->theta, S->resid, S->efail, s);
       apply_kernel<<<ceil_div(n, 64), 256, (size_t)(S->p * S->p + 64 * S->p) * 4, s>>>(
           S->Xb, S->cvec, S->Bm, n, S->p, S->Zb);
       eig_setup_kernel<<<1, 1, 0, s>>>(S->dSt, o->eig_tol, o->eig_max_iter,
@@ -1651,8 +1651,7 @@ eot_status eot_spectral_modes(int32_t n, int32_t m, const float* C, const double
       S->Xb, n, p, 0x5EEDull, use_V_as_start ? S->V : nullptr, use_V_as_start ? ell : 0);
   CUDA_TRY(S->wgram(S->Xb, S->Xb, P.a, 0, n, p, P.a, S->Xb, S->epart, S->evpart, S->GXX, S->cvec,
                     0, s));
-  eig_small_kernel<<<1, 256, 0, s>>>(p, ell, 0, S->GXX, S->Tm, S->cvec, S->Bm, S->theta, S->resid,
-                                     S->efail);
+  launch_eig_small(p, ell, 0, S->GXX, S->Tm, S->cvec, S->Bm, S->theta, S->resid, S->efail, s);
   apply_kernel<<<ceil_div(n, 64), 256, (size_t)(p * p + 64 * p) * 4, s>>>(S->Xb, S->cvec, S->Bm, n,
                                                                          p, S->Zb);
   eig_setup_kernel<<<1, 1, 0, s>>>(S->dSt, tol, max_iter, max_iter + 4);

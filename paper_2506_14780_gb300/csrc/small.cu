@@ -78,75 +78,76 @@ __global__ void wgram_reduce_kernel(const double* __restrict__ part, int nchunk,
 }
 
 // ---------------------------------------------------------------------------
-// Newton step on V (one warp, float64).  GV = V^T D_a V (or V^T D_r V),
-// WtW = sum_j W_j W_j^T / b_j, gw = sum_j d_j W_j (d_j = -expm1(L_j)),
-// Va = V^T a.  -H_V = (GV - WtW)/eps is factorised by a right-looking Cholesky
-// with lanes over rows; Delta = (-H_V)^{-1} grad_V, grad_V = -gw.
+// Newton step on V (one CTA of 256 threads, float64).  GV = V^T D_a V (or
+// V^T D_r V), WtW = sum_j W_j W_j^T / b_j, gw = sum_j d_j W_j
+// (d_j = -expm1(L_j)), Va = V^T a.  -H_V = (GV - WtW)/eps is factorised as
+// L D L^T (outer-product elimination without square roots, one barrier per
+// pivot), the forward substitution of grad_V = -gw riding along with the
+// elimination; Delta = (-H_V)^{-1} grad_V.  A pivot that is not positive (the
+// restricted Hessian is not negative definite) rejects the step.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(32) newton_kernel(const Prob* __restrict__ PP,
-                                                    const double* __restrict__ WtW,
-                                                    const double* __restrict__ gw,
-                                                    const double* __restrict__ Dr) {
+__global__ void __launch_bounds__(256) newton_kernel(const Prob* __restrict__ PP,
+                                                     const double* __restrict__ WtW,
+                                                     const double* __restrict__ gw,
+                                                     const double* __restrict__ Dr) {
   const Prob& P = *PP;
   State* st = P.st;
   if (st->done) return;
   const int l = P.ell;
-  const int lane = threadIdx.x;
-  // the matrix is assembled in float64 (the difference GV - WtW cancels), the
-  // factorisation and solves run in float32 (relative error ~1e-7 x cond)
-  __shared__ float H[kMaxK * kMaxK];
-  __shared__ float g[kMaxK];
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int ty = tid >> 4, tx = tid & 15;          // 16 x 16 tiling of the trailing matrix
+  constexpr int kS = kMaxK + 1;                    // odd row stride
+  __shared__ double H[kMaxK * kS];
+  __shared__ double g[kMaxK];
+  __shared__ int s_fail;
   const double inv_eps = 1.0 / P.eps;
-  for (int e = lane; e < l * l; e += 32) {
-    const int r = e / l, c = e - r * l;
-    const double gv = Dr ? 0.5 * (Dr[r * l + c] + Dr[c * l + r]) : 0.5 * (P.GV[r * l + c] + P.GV[c * l + r]);
-    const double wt = 0.5 * (WtW[r * l + c] + WtW[c * l + r]);
-    H[e] = (float)(inv_eps * (gv - wt));
-  }
-  for (int k = lane; k < l; k += 32) g[k] = (float)(-gw[k]);
-  __syncwarp();
-  bool fail = false;
-  for (int k = 0; k < l; ++k) {
-    const float d = H[k * l + k];
-    if (!(d > 0.f) || !isfinite(d)) fail = true;
-    const float dk = d > 0.f ? sqrtf(d) : 1.f;
-    __syncwarp();
-    if (lane == 0) H[k * l + k] = dk;
-    for (int r = k + 1 + lane; r < l; r += 32) H[r * l + k] /= dk;
-    __syncwarp();
-    for (int r = k + 1 + lane; r < l; r += 32) {
-      const float hrk = H[r * l + k];
-      for (int c = k + 1; c <= r; ++c) H[r * l + c] -= hrk * H[c * l + k];
+  const double* __restrict__ G0 = Dr ? Dr : P.GV;
+  for (int r = ty; r < l; r += 16)
+    for (int c = tx; c <= r; c += 16) {
+      const double gv = 0.5 * (G0[r * l + c] + G0[c * l + r]);
+      const double wt = 0.5 * (WtW[r * l + c] + WtW[c * l + r]);
+      H[r * kS + c] = inv_eps * (gv - wt);
     }
-    __syncwarp();
+  for (int k = tid; k < l; k += 256) g[k] = -gw[k];
+  if (tid == 0) s_fail = 0;
+  __syncthreads();
+  // elimination: after pivot k, H[r][k] = L_rk D_k (r > k), H[k][k] = D_k, and
+  // g holds the forward-substituted right-hand side
+  for (int k = 0; k < l; ++k) {
+    const double dk = H[k * kS + k];
+    const bool ok = dk > 0.0 && isfinite(dk);
+    if (!ok && tid == 0) s_fail = 1;
+    const double inv = ok ? 1.0 / dk : 0.0;
+    for (int r = k + 1 + ty; r < l; r += 16) {
+      const double hr = H[r * kS + k] * inv;
+      for (int c = k + 1 + tx; c <= r; c += 16) H[r * kS + c] -= hr * H[c * kS + k];
+    }
+    if (tid >= 128) {
+      const int i = k + 1 + (tid - 128);
+      if (i < l) g[i] -= H[i * kS + k] * inv * g[k];
+    }
+    __syncthreads();
   }
-  // L y = g (column oriented), then L^T x = y
-  for (int r = 0; r < l; ++r) {
-    const float yr = g[r] / H[r * l + r];
-    __syncwarp();
-    if (lane == 0) g[r] = yr;
-    for (int i = r + 1 + lane; i < l; i += 32) g[i] -= H[i * l + r] * yr;
-    __syncwarp();
-  }
-  for (int r = l - 1; r >= 0; --r) {
-    const float xr = g[r] / H[r * l + r];
-    __syncwarp();
-    if (lane == 0) g[r] = xr;
-    for (int i = lane; i < r; i += 32) g[i] -= H[r * l + i] * xr;
+  if (tid >= 32) return;
+  // D z = y, then L^T x = z (column oriented, lanes over rows)
+  for (int k = lane; k < l; k += 32) g[k] = s_fail ? 0.0 : g[k] / H[k * kS + k];
+  __syncwarp();
+  for (int k = l - 1; k >= 0; --k) {
+    const double xk = g[k];
+    for (int i = lane; i < k; i += 32) g[i] -= H[k * kS + i] / H[i * kS + i] * xk;
     __syncwarp();
   }
   double dva = 0.0;
   bool finite = true;
   for (int k = lane; k < l; k += 32) {
-    P.delta[k] = (double)g[k];
-    dva += (double)g[k] * P.Va[k];
+    P.delta[k] = g[k];
+    dva += g[k] * P.Va[k];
     finite = finite && isfinite(g[k]);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) dva += __shfl_xor_sync(0xffffffffu, dva, o);
   finite = __all_sync(0xffffffffu, finite);
-  fail = __any_sync(0xffffffffu, fail) || st->nr_degenerate != 0;
-  __syncwarp();
+  const bool fail = s_fail != 0 || st->nr_degenerate != 0;
   if (lane == 0) {
     st->nr_degenerate = 0;
     if (fail || !finite) {
@@ -203,199 +204,221 @@ __global__ void fprime_kernel(const Prob* __restrict__ PP) {
 //           residual_k^2 = (Q^T GXX Q)_kk - theta_k^2, then
 //           L L^T = Q^T (GXX - c c^T) Q and B = Q L^{-T}.
 //   outputs B (p x p float32), theta (p), max residual over the first l.
+// Launched as one CTA of kMaxP/2 x kMaxP/2 threads (launch_eig_small).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) eig_small_kernel(int p, int l, int mode,
-                                                        const double* __restrict__ GXX,
-                                                        const double* __restrict__ T,
-                                                        const double* __restrict__ c,
-                                                        float* __restrict__ Bout,
-                                                        double* __restrict__ theta_out,
-                                                        double* __restrict__ resid_out,
-                                                        int* __restrict__ fail_out) {
-  // A and Q use an odd row stride (pe + 1): the column rotations walk down
-  // columns, and an even stride would put many rows in one shared-memory bank
-  __shared__ float A[kMaxP * (kMaxP + 1)];
-  __shared__ float Q[kMaxP * (kMaxP + 1)];
-  __shared__ float G[kMaxP * kMaxP];
-  __shared__ float tmp[kMaxP * kMaxP];
-  __shared__ float rc[kMaxP], rs[kMaxP], cf[kMaxP], qc[kMaxP];
-  __shared__ int pairs[kMaxP];
-  __shared__ float th[kMaxP];
-  __shared__ int order[kMaxP];
-  __shared__ float s_w[16];
-  __shared__ int s_stop, s_fail;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int pe = (p + 1) & ~1;   // padded even size for the circle ordering
-  const int ps = pe + 1;         // row stride of A and Q
-  for (int e = tid; e < pe * pe; e += nt) {
-    const int r = e / pe, q = e - r * pe;
-    const bool in = r < p && q < p;
-    A[r * ps + q] = (mode == 1 && in) ? (float)(0.5 * (T[r * p + q] + T[q * p + r])) : 0.f;
-    Q[r * ps + q] = (r == q) ? 1.f : 0.f;
+constexpr int kEH = kMaxP / 2;   // the block is kEH x kEH threads: one per pair of pairs
+constexpr int kES = kMaxP + 1;   // odd row stride of the shared matrices
+
+// Block-wide sum of two floats over the kEH x kEH threads; valid in thread 0.
+__device__ __forceinline__ void eig_sum2(float& a, float& b, float* red) {
+  const int tid = threadIdx.y * kEH + threadIdx.x, lane = tid & 31, w = tid >> 5;
+  a = warp_sum_f(a);
+  b = warp_sum_f(b);
+  if (lane == 0) {
+    red[w] = a;
+    red[32 + w] = b;
   }
-  for (int k = tid; k < p; k += nt) cf[k] = (float)c[k];
+  __syncthreads();
+  if (tid == 0) {
+    a = b = 0.f;
+    for (int k = 0; k < (kEH * kEH + 31) / 32; ++k) {
+      a += red[k];
+      b += red[32 + k];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kEH * kEH) eig_small_kernel(int p, int l, int mode,
+                                                              const double* __restrict__ GXX,
+                                                              const double* __restrict__ T,
+                                                              const double* __restrict__ c,
+                                                              float* __restrict__ Bout,
+                                                              double* __restrict__ theta_out,
+                                                              double* __restrict__ resid_out,
+                                                              int* __restrict__ fail_out) {
+  __shared__ float A[kMaxP * kES];
+  __shared__ float Q[kMaxP * kES];
+  __shared__ float G[kMaxP * kES];
+  __shared__ float W[kMaxP * kES];
+  __shared__ float rc[kEH], rs[kEH], sq[kMaxP];
+  __shared__ int pk[kEH], pq[kEH];
+  __shared__ float th[kMaxP], cf[kMaxP], qc[kMaxP];
+  __shared__ int order[kMaxP];
+  __shared__ float red[64];
+  __shared__ int s_stop, s_fail;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kEH + tx;
+  const int pe = (p + 1) & ~1;   // padded even size for the circle ordering
+  const int half = pe / 2;
+  for (int r = ty; r < pe; r += kEH)
+    for (int q = tx; q < pe; q += kEH) {
+      const bool in = r < p && q < p;
+      A[r * kES + q] = (mode == 1 && in) ? (float)(0.5 * (T[r * p + q] + T[q * p + r])) : 0.f;
+      Q[r * kES + q] = (r == q) ? 1.f : 0.f;
+    }
+  for (int k = tid; k < p; k += kEH * kEH) cf[k] = (float)c[k];
   if (tid == 0) s_fail = 0;
   __syncthreads();
   if (mode == 1) {
+    // cyclic Jacobi, circle ordering: in each round the pe/2 disjoint pairs
+    // rotate at once; thread (ty, tx) applies A <- R A R^T to the 2 x 2 block
+    // of pairs (ty, tx) and Q <- Q R^T to two rows of pair tx
     for (int sweep = 0; sweep < 12; ++sweep) {
       float loc = 0.f, dia = 0.f;
-      for (int e = tid; e < pe * pe; e += nt) {
-        const int r = e / pe, q = e - r * pe;
-        const float v = A[r * ps + q];
-        if (r != q) loc += v * v;
-        else dia += v * v;
-      }
-      loc = warp_sum_f(loc);
-      dia = warp_sum_f(dia);
-      if ((tid & 31) == 0) { s_w[tid >> 5] = loc; s_w[8 + (tid >> 5)] = dia; }
-      __syncthreads();
-      if (tid == 0) {
-        float o = 0.f, d = 0.f;
-        for (int w = 0; w < (nt >> 5); ++w) { o += s_w[w]; d += s_w[8 + w]; }
-        s_stop = (o <= 1e-10f * (d + 1e-30f)) ? 1 : 0;
-      }
+      for (int r = ty; r < pe; r += kEH)
+        for (int q = tx; q < pe; q += kEH) {
+          const float v = A[r * kES + q];
+          if (r != q) loc += v * v;
+          else dia += v * v;
+        }
+      eig_sum2(loc, dia, red);
+      if (tid == 0) s_stop = (loc <= 1e-10f * (dia + 1e-30f)) ? 1 : 0;
       __syncthreads();
       if (s_stop) break;
       for (int round = 0; round < pe - 1; ++round) {
-        if (tid < pe / 2) {
-          const int pa = tid, pb = pe - 1 - tid;
+        if (ty == 0 && tx < half) {
+          const int pa = tx, pb = pe - 1 - tx;
           const int a = pa == 0 ? 0 : 1 + (pa - 1 + round) % (pe - 1);
           const int b = 1 + (pb - 1 + round) % (pe - 1);
           const int k = min(a, b), q = max(a, b);
-          pairs[2 * tid] = k;
-          pairs[2 * tid + 1] = q;
-          const float akq = A[k * ps + q];
+          pk[tx] = k;
+          pq[tx] = q;
+          const float akq = A[k * kES + q];
           float cth = 1.f, sth = 0.f;
           if (fabsf(akq) > 1e-30f) {
-            const float tau = (A[q * ps + q] - A[k * ps + k]) / (2.f * akq);
+            const float tau = (A[q * kES + q] - A[k * kES + k]) / (2.f * akq);
             const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
             cth = rsqrtf(1.f + t * t);
             sth = t * cth;
           }
-          rc[tid] = cth;
-          rs[tid] = sth;
+          rc[tx] = cth;
+          rs[tx] = sth;
         }
         __syncthreads();
-        for (int e = tid; e < (pe / 2) * pe; e += nt) {     // rows: A <- J^T A
-          const int pr = e / pe, col = e - pr * pe;
-          const int k = pairs[2 * pr], q = pairs[2 * pr + 1];
-          const float cth = rc[pr], sth = rs[pr];
-          const float ak = A[k * ps + col], aq = A[q * ps + col];
-          A[k * ps + col] = cth * ak - sth * aq;
-          A[q * ps + col] = sth * ak + cth * aq;
+        if (ty < half && tx < half) {
+          const int k1 = pk[ty], q1 = pq[ty], k2 = pk[tx], q2 = pq[tx];
+          const float c1 = rc[ty], s1 = rs[ty], c2 = rc[tx], s2 = rs[tx];
+          const float a = A[k1 * kES + k2], b = A[k1 * kES + q2];
+          const float e = A[q1 * kES + k2], d = A[q1 * kES + q2];
+          const float u11 = c1 * a - s1 * e, u12 = c1 * b - s1 * d;
+          const float u21 = s1 * a + c1 * e, u22 = s1 * b + c1 * d;
+          A[k1 * kES + k2] = u11 * c2 - u12 * s2;
+          A[k1 * kES + q2] = u11 * s2 + u12 * c2;
+          A[q1 * kES + k2] = u21 * c2 - u22 * s2;
+          A[q1 * kES + q2] = u21 * s2 + u22 * c2;
         }
-        __syncthreads();
-        for (int e = tid; e < (pe / 2) * pe; e += nt) {     // columns: A <- A J, Q <- Q J
-          const int pr = e / pe, row = e - pr * pe;
-          const int k = pairs[2 * pr], q = pairs[2 * pr + 1];
-          const float cth = rc[pr], sth = rs[pr];
-          const float ak = A[row * ps + k], aq = A[row * ps + q];
-          A[row * ps + k] = cth * ak - sth * aq;
-          A[row * ps + q] = sth * ak + cth * aq;
-          const float qk = Q[row * ps + k], qq = Q[row * ps + q];
-          Q[row * ps + k] = cth * qk - sth * qq;
-          Q[row * ps + q] = sth * qk + cth * qq;
+        if (tx < half) {
+          const int k = pk[tx], q = pq[tx];
+          const float cth = rc[tx], sth = rs[tx];
+          for (int r = ty; r < pe; r += kEH) {
+            const float qk = Q[r * kES + k], qq = Q[r * kES + q];
+            Q[r * kES + k] = cth * qk - sth * qq;
+            Q[r * kES + q] = sth * qk + cth * qq;
+          }
         }
         __syncthreads();
       }
     }
-    for (int k = tid; k < p; k += nt) th[k] = A[k * ps + k];
+    for (int k = tid; k < p; k += kEH * kEH) th[k] = A[k * kES + k];
     __syncthreads();
-    for (int k = tid; k < p; k += nt) {
+    for (int k = tid; k < p; k += kEH * kEH) {
       int rank = 0;
       for (int q = 0; q < p; ++q) rank += (th[q] > th[k]) || (th[q] == th[k] && q < k);
       order[rank] = k;
     }
     __syncthreads();
-    for (int e = tid; e < p * p; e += nt) {
-      const int r = e / p, q = e - r * p;
-      tmp[r * p + q] = Q[r * ps + order[q]];
-    }
-    __syncthreads();
-    for (int e = tid; e < p * p; e += nt) Q[e] = tmp[e];
+    for (int r = ty; r < p; r += kEH)     // W = Q with the columns in descending order
+      for (int q = tx; q < p; q += kEH) W[r * kES + q] = Q[r * kES + order[q]];
     if (tid < p) theta_out[tid] = (double)th[order[tid]];
     __syncthreads();
+    for (int r = ty; r < p; r += kEH)
+      for (int q = tx; q < p; q += kEH) Q[r * kES + q] = W[r * kES + q];
   } else {
-    for (int e = tid; e < p * p; e += nt) {
-      const int r = e / p, q = e - r * p;
-      Q[e] = (r == q) ? 1.f : 0.f;
-    }
-    __syncthreads();
+    for (int r = ty; r < p; r += kEH)
+      for (int q = tx; q < p; q += kEH) Q[r * kES + q] = (r == q) ? 1.f : 0.f;
   }
   // G = GXX - c c^T (float), then (mode 1) G <- Q^T G Q
-  for (int e = tid; e < p * p; e += nt) {
-    const int r = e / p, q = e - r * p;
-    G[e] = (float)(GXX[e] - c[r] * c[q]);
-  }
+  for (int r = ty; r < p; r += kEH)
+    for (int q = tx; q < p; q += kEH) G[r * kES + q] = (float)(GXX[r * p + q] - c[r] * c[q]);
   __syncthreads();
   if (mode == 1) {
-    for (int e = tid; e < p * p; e += nt) {     // tmp = G Q
-      const int r = e / p, q = e - r * p;
-      float acc = 0.f;
-      for (int k = 0; k < p; ++k) acc = __fmaf_rn(G[r * p + k], Q[k * p + q], acc);
-      tmp[e] = acc;
-    }
+    for (int r = ty; r < p; r += kEH)     // W = G Q
+      for (int q = tx; q < p; q += kEH) {
+        float acc = 0.f;
+        for (int k = 0; k < p; ++k) acc = __fmaf_rn(G[r * kES + k], Q[k * kES + q], acc);
+        W[r * kES + q] = acc;
+      }
+    if (ty == 0)                          // (Q^T c)_k
+      for (int k = tx; k < p; k += kEH) {
+        float acc = 0.f;
+        for (int r = 0; r < p; ++r) acc = __fmaf_rn(Q[r * kES + k], cf[r], acc);
+        qc[k] = acc;
+      }
     __syncthreads();
-    for (int e = tid; e < p * p; e += nt) {     // A = Q^T tmp (stride p)
-      const int r = e / p, q = e - r * p;
-      float acc = 0.f;
-      for (int k = 0; k < p; ++k) acc = __fmaf_rn(Q[k * p + r], tmp[k * p + q], acc);
-      A[e] = acc;
-    }
-    for (int k = tid; k < p; k += nt) {         // (Q^T c)_k
-      float acc = 0.f;
-      for (int r = 0; r < p; ++r) acc = __fmaf_rn(Q[r * p + k], cf[r], acc);
-      qc[k] = acc;
-    }
+    for (int r = ty; r < p; r += kEH)     // A = Q^T W
+      for (int q = tx; q < p; q += kEH) {
+        float acc = 0.f;
+        for (int k = 0; k < p; ++k) acc = __fmaf_rn(Q[k * kES + r], W[k * kES + q], acc);
+        A[r * kES + q] = acc;
+      }
     __syncthreads();
     // residual_k^2 = (Q^T GXX Q)_kk - theta_k^2 = G'_kk + (Q^T c)_k^2 - theta_k^2
     float rmax = 0.f;
-    for (int k = tid; k < l && k < p; k += nt) {
+    for (int k = tid; k < l && k < p; k += kEH * kEH) {
       const float t = (float)theta_out[k];
-      const float r2 = A[k * p + k] + qc[k] * qc[k] - t * t;
+      const float r2 = A[k * kES + k] + qc[k] * qc[k] - t * t;
       rmax = fmaxf(rmax, r2 > 0.f ? sqrtf(r2) : 0.f);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-    if ((tid & 31) == 0) s_w[tid >> 5] = rmax;
+    if ((tid & 31) == 0) red[tid >> 5] = rmax;
     __syncthreads();
     if (tid == 0) {
       float mx = 0.f;
-      for (int w = 0; w < (nt >> 5); ++w) mx = fmaxf(mx, s_w[w]);
+      for (int w = 0; w < (kEH * kEH + 31) / 32; ++w) mx = fmaxf(mx, red[w]);
       *resid_out = (double)mx;
     }
-    for (int e = tid; e < p * p; e += nt) G[e] = A[e];
+    for (int r = ty; r < p; r += kEH)
+      for (int q = tx; q < p; q += kEH) G[r * kES + q] = A[r * kES + q];
     __syncthreads();
   }
-  // Cholesky of G (lower, in place)
+  // G = L D L^T by outer products (one barrier per pivot); L = L1 D^(1/2)
   for (int k = 0; k < p; ++k) {
-    const float d = G[k * p + k];
-    const float dk = d > 0.f ? sqrtf(d) : 1.f;
-    if (tid == 0 && !(d > 0.f)) s_fail = 1;
-    __syncthreads();
-    if (tid == 0) G[k * p + k] = dk;
-    for (int r = k + 1 + tid; r < p; r += nt) G[r * p + k] /= dk;
-    __syncthreads();
-    for (int e = tid; e < (p - k - 1) * (p - k - 1); e += nt) {
-      const int r = k + 1 + e / (p - k - 1), q = k + 1 + e % (p - k - 1);
-      if (q <= r) G[r * p + q] -= G[r * p + k] * G[q * p + k];
+    const float dk = G[k * kES + k];
+    if (tid == 0 && !(dk > 0.f)) s_fail = 1;
+    const float inv = dk > 0.f ? 1.f / dk : 0.f;
+    for (int r = k + 1 + ty; r < p; r += kEH) {
+      const float hr = G[r * kES + k] * inv;
+      for (int q = k + 1 + tx; q <= r; q += kEH) G[r * kES + q] -= hr * G[q * kES + k];
     }
     __syncthreads();
   }
-  // B = Q L^{-T}: row r of B solves  B_r L^T = Q_r  (thread r, in place in tmp)
-  for (int e = tid; e < p * p; e += nt) tmp[e] = Q[e];
-  __syncthreads();
-  for (int r = tid; r < p; r += nt) {
-    float* row = tmp + r * p;
-    for (int q = 0; q < p; ++q) {
-      float acc = row[q];
-      for (int k = 0; k < q; ++k) acc -= row[k] * G[q * p + k];
-      row[q] = acc / G[q * p + q];
-    }
+  for (int k = tid; k < p; k += kEH * kEH) {
+    const float dk = G[k * kES + k];
+    sq[k] = dk > 0.f ? sqrtf(dk) : 1.f;
   }
+  for (int r = ty; r < p; r += kEH)       // W = Q (right-hand sides)
+    for (int q = tx; q < p; q += kEH) W[r * kES + q] = Q[r * kES + q];
   __syncthreads();
-  for (int e = tid; e < p * p; e += nt) Bout[e] = tmp[e];
+  // B L^T = Q, column by column: after step q, column q of W is final
+  // (L_cq = G_cq / sqrt(D_q) for c > q, L_qq = sqrt(D_q))
+  for (int q = 0; q < p; ++q) {
+    const float lqq = sq[q];
+    for (int r = ty; r < p; r += kEH) {
+      const float b = W[r * kES + q] / lqq;
+      for (int cc = q + 1 + tx; cc < p; cc += kEH)
+        W[r * kES + cc] -= b * (G[cc * kES + q] / lqq);
+    }
+    __syncthreads();
+  }
+  for (int r = ty; r < p; r += kEH)
+    for (int q = tx; q < p; q += kEH) Bout[r * p + q] = W[r * kES + q] / sq[q];
   if (tid == 0 && fail_out) *fail_out = s_fail;
+}
+
+void launch_eig_small(int p, int l, int mode, const double* GXX, const double* T,
+                      const double* c, float* B, double* theta, double* resid, int* fail,
+                      cudaStream_t s) {
+  eig_small_kernel<<<1, dim3(kEH, kEH), 0, s>>>(p, l, mode, GXX, T, c, B, theta, resid, fail);
 }
 
 // Z_i <- (X_i - c) B   (len x p, float32), c float64 (deflation of the constant).
