@@ -78,13 +78,15 @@ __global__ void wgram_reduce_kernel(const double* __restrict__ part, int nchunk,
 }
 
 // ---------------------------------------------------------------------------
-// Newton step on V (one CTA of 256 threads, float64).  GV = V^T D_a V (or
-// V^T D_r V), WtW = sum_j W_j W_j^T / b_j, gw = sum_j d_j W_j
-// (d_j = -expm1(L_j)), Va = V^T a.  -H_V = (GV - WtW)/eps is factorised as
-// L D L^T (outer-product elimination without square roots, one barrier per
-// pivot), the forward substitution of grad_V = -gw riding along with the
-// elimination; Delta = (-H_V)^{-1} grad_V.  A pivot that is not positive (the
-// restricted Hessian is not negative definite) rejects the step.
+// Newton step on V (one CTA of 256 threads).  GV = V^T D_a V (or V^T D_r V),
+// WtW = sum_j W_j W_j^T / b_j, gw = sum_j d_j W_j (d_j = -expm1(L_j)),
+// Va = V^T a.  -eps H_V = GV - WtW is assembled in float64 (the difference
+// cancels) and factorised in float32 as L D L^T (outer-product elimination
+// without square roots, one barrier per pivot; float64 arithmetic is a small
+// fraction of the float32 rate on this GPU), the forward substitution of
+// grad_V = -gw riding along with the elimination;
+// Delta = (-H_V)^{-1} grad_V = eps (GV - WtW)^{-1} grad_V.  A pivot that is not
+// positive (the restricted Hessian is not negative definite) rejects the step.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) newton_kernel(const Prob* __restrict__ PP,
                                                      const double* __restrict__ WtW,
@@ -97,52 +99,60 @@ __global__ void __launch_bounds__(256) newton_kernel(const Prob* __restrict__ PP
   const int tid = threadIdx.x, lane = tid & 31;
   const int ty = tid >> 4, tx = tid & 15;          // 16 x 16 tiling of the trailing matrix
   constexpr int kS = kMaxK + 1;                    // odd row stride
-  __shared__ double H[kMaxK * kS];
-  __shared__ double g[kMaxK];
+  __shared__ float H[kMaxK * kS];
+  __shared__ float g[kMaxK];
+  __shared__ float s_inv[kMaxK];   // 1 / D_k, formed by the thread owning the pivot
   __shared__ int s_fail;
-  const double inv_eps = 1.0 / P.eps;
   const double* __restrict__ G0 = Dr ? Dr : P.GV;
+  if (tid == 0) s_fail = 0;
+  auto pivot = [&](int k) {        // thread 0 owns element (k, k) of every update
+    const float d = H[k * kS + k];
+    const bool ok = d > 0.f && isfinite(d);
+    if (!ok) s_fail = 1;
+    s_inv[k] = ok ? 1.f / d : 0.f;
+  };
   for (int r = ty; r < l; r += 16)
     for (int c = tx; c <= r; c += 16) {
       const double gv = 0.5 * (G0[r * l + c] + G0[c * l + r]);
       const double wt = 0.5 * (WtW[r * l + c] + WtW[c * l + r]);
-      H[r * kS + c] = inv_eps * (gv - wt);
+      H[r * kS + c] = (float)(gv - wt);
+      if (r == 0) pivot(0);
     }
-  for (int k = tid; k < l; k += 256) g[k] = -gw[k];
-  if (tid == 0) s_fail = 0;
+  for (int k = tid; k < l; k += 256) g[k] = (float)(-gw[k]);
   __syncthreads();
   // elimination: after pivot k, H[r][k] = L_rk D_k (r > k), H[k][k] = D_k, and
   // g holds the forward-substituted right-hand side
   for (int k = 0; k < l; ++k) {
-    const double dk = H[k * kS + k];
-    const bool ok = dk > 0.0 && isfinite(dk);
-    if (!ok && tid == 0) s_fail = 1;
-    const double inv = ok ? 1.0 / dk : 0.0;
+    const float inv = s_inv[k];
     for (int r = k + 1 + ty; r < l; r += 16) {
-      const double hr = H[r * kS + k] * inv;
-      for (int c = k + 1 + tx; c <= r; c += 16) H[r * kS + c] -= hr * H[c * kS + k];
+      const float hr = H[r * kS + k] * inv;
+      for (int c = k + 1 + tx; c <= r; c += 16) {
+        H[r * kS + c] = __fmaf_rn(-hr, H[c * kS + k], H[r * kS + c]);
+        if (c == k + 1 && r == k + 1) pivot(k + 1);
+      }
     }
     if (tid >= 128) {
       const int i = k + 1 + (tid - 128);
-      if (i < l) g[i] -= H[i * kS + k] * inv * g[k];
+      if (i < l) g[i] = __fmaf_rn(-H[i * kS + k] * inv, g[k], g[i]);
     }
     __syncthreads();
   }
   if (tid >= 32) return;
   // D z = y, then L^T x = z (column oriented, lanes over rows)
-  for (int k = lane; k < l; k += 32) g[k] = s_fail ? 0.0 : g[k] / H[k * kS + k];
+  for (int k = lane; k < l; k += 32) g[k] = s_fail ? 0.f : g[k] * s_inv[k];
   __syncwarp();
   for (int k = l - 1; k >= 0; --k) {
-    const double xk = g[k];
-    for (int i = lane; i < k; i += 32) g[i] -= H[k * kS + i] / H[i * kS + i] * xk;
+    const float xk = g[k];
+    for (int i = lane; i < k; i += 32) g[i] = __fmaf_rn(-H[k * kS + i] * s_inv[i], xk, g[i]);
     __syncwarp();
   }
   double dva = 0.0;
   bool finite = true;
   for (int k = lane; k < l; k += 32) {
-    P.delta[k] = g[k];
-    dva += g[k] * P.Va[k];
-    finite = finite && isfinite(g[k]);
+    const double dk = P.eps * (double)g[k];
+    P.delta[k] = dk;
+    dva += dk * P.Va[k];
+    finite = finite && isfinite(dk);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) dva += __shfl_xor_sync(0xffffffffu, dva, o);
