@@ -66,59 +66,32 @@ struct MmaEpi {
 // the new potential h and its split arrays, d_j, and the block partials of
 // W^T D_b^{-1} W and d^T W; the last block takes the grid-wide step: L1
 // test, Q_semi(f_k), iteration count).  Run by threads 0..255 (named barrier
-// 1); `smem` is scratch of at least 128 (NN + 3) floats.
+// 1); `smem` is scratch of at least 2 * 128 (NN + 1) + 256 + 4608 floats.
 template <int NN>
-__device__ void colmma_finish(const AccArgs& args, const Prob& P, unsigned char* smem,
+__device__ __noinline__ void colmma_finish(const AccArgs& args, const Prob& P, unsigned char* smem,
                               MmaEpi& epi, int cb, int gb, int dst_g, int len) {
   State* st = P.st;
   const bool s4 = args.mode == 1;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int m = len, kk = args.k;
-  const int c = tid & (kMmaM - 1);
+  const int c = tid & (kMmaM - 1), h = tid >> 7;
   const int j = cb * kMmaM + c;
   const bool jv = j < m;
-  float* sW = reinterpret_cast<float*>(smem);   // [128][NN + 1]
-  float* sD = sW + kMmaM * (NN + 1);            // [128] d_j
-  float* sB = sD + kMmaM;                       // [128] 1 / b_j
+  constexpr int WS = NN + 1;                    // odd row stride
+  float* sW = reinterpret_cast<float*>(smem);   // [128][NN + 1]  W_j
+  float* sWb = sW + kMmaM * WS;                 // [128][NN + 1]  W_j / b_j
+  float* sD = sWb + kMmaM * WS;                 // [128] d_j
+  float* sS = sD + kMmaM;                       // [128] scale of the product row
+  float* sP = sS + kMmaM;                       // [4][16 * 64] partial 4 x 4 blocks
   double accv[3] = {0.0, 0.0, 0.0};
   if (tid < kMmaM) {
     float R = -INFINITY;
     double Stot = 0.0;
     if (jv) merge_segments_k(args.part, args.nseg, m, NN + 4, j, R, Stot);
-    double scale = 1.0;
-    if (s4 && jv) scale = P.b[j] / (Stot * ldexp(1.0, (int)R));   // b_j / sum_i 2^{y_ij}
-    // the product rows, 16 columns at a time (segments in a fixed order)
-#pragma unroll 1
-    for (int k0 = 0; k0 < NN; k0 += 16) {
-      float acc[16];
-#pragma unroll
-      for (int k = 0; k < 16; ++k) acc[k] = 0.f;
-      if (jv) {
-        for (int sg = 0; sg < args.nseg; ++sg) {
-          const float4* src = reinterpret_cast<const float4*>(
-              args.part + ((size_t)sg * m + j) * (NN + 4) + 4 + k0);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float4 v = __ldcg(src + q);
-            acc[4 * q + 0] += v.x;
-            acc[4 * q + 1] += v.y;
-            acc[4 * q + 2] += v.z;
-            acc[4 * q + 3] += v.w;
-          }
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        if (k0 + k < kk) {
-          const float wv = (float)(acc[k] * scale);
-          if (jv) args.out[(size_t)j * kk + k0 + k] = wv;
-          if (s4) sW[c * (NN + 1) + k0 + k] = jv ? wv : 0.f;
-        }
-      }
-    }
+    // pi(f_k, h)^T V: the product rows times b_j / sum_i 2^{y_ij}
+    sS[c] = (s4 && jv) ? (float)(P.b[j] / (Stot * ldexp(1.0, (int)R))) : 1.f;
     if (s4) {
       sD[c] = 0.f;
-      sB[c] = 0.f;
       if (jv) {
         float L = R * kLn2 + log_sum(Stot);
         const double sh = P.g[gb][j];
@@ -142,13 +115,51 @@ __device__ void colmma_finish(const AccArgs& args, const Prob& P, unsigned char*
         P.cs[dst_g].K[j] = (float)((double)P.M - hi);
         P.cs[dst_g].KL[j] = lo;
         const double wj = P.b[j];
-        const double dj = -(double)expm1f(L);     // 1 - exp((g_j - h_j)/eps)
+        const float em = expm1f(L);
+        const double dj = -(double)em;          // 1 - exp((g_j - h_j)/eps)
         args.dw[j] = dj;
         sD[c] = (float)dj;
-        sB[c] = (float)(1.0 / wj);
-        accv[0] = wj * (double)fabsf(expm1f(L));
+        accv[0] = wj * (double)fabsf(em);
         accv[1] = wj * (double)L;
         accv[2] = wj * o;
+      }
+    }
+  }
+  cons_sync();
+  // the product rows: thread (c, h) sums the segments of 16-value pieces
+  // h, h + 2, ... of row c (segments in a fixed order)
+  {
+    const float scale = sS[c];
+    const float binv = (s4 && jv) ? (float)(1.0 / P.b[j]) : 0.f;
+#pragma unroll 1
+    for (int k0 = 16 * h; k0 < NN; k0 += 32) {
+      float acc[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) acc[k] = 0.f;
+      if (jv) {
+#pragma unroll 3
+        for (int sg = 0; sg < args.nseg; ++sg) {
+          const float4* src = reinterpret_cast<const float4*>(
+              args.part + ((size_t)sg * m + j) * (NN + 4) + 4 + k0);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float4 v = __ldcg(src + q);
+            acc[4 * q + 0] += v.x;
+            acc[4 * q + 1] += v.y;
+            acc[4 * q + 2] += v.z;
+            acc[4 * q + 3] += v.w;
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const float wv = acc[k] * scale;
+        if (k0 + k < kk && jv) args.out[(size_t)j * kk + k0 + k] = wv;
+        if (s4) {
+          const bool live = jv && k0 + k < kk;
+          sW[c * WS + k0 + k] = live ? wv : 0.f;
+          sWb[c * WS + k0 + k] = live ? wv * binv : 0.f;
+        }
       }
     }
   }
@@ -158,20 +169,53 @@ __device__ void colmma_finish(const AccArgs& args, const Prob& P, unsigned char*
   }
   cons_sync();
   {
-    // block partials of W^T D_b^{-1} W and d^T W over the 128 columns
+    // block partials of W^T D_b^{-1} W (4 x 4 register blocks; the 128
+    // columns split among 256 / nb^2 thread groups) and d^T W, float32 sums
+    // over the block's columns, float64 across blocks
     double* dstp = args.wtw_part + (size_t)cb * (kk * kk + kk);
-    // float32 sums over the 128 columns (float64 across blocks)
-    for (int e = tid; e < kk * kk + kk; e += kStConsumers) {
-      float s = 0.f;
-      if (e < kk * kk) {
-        const int r = e / kk, q2 = e - r * kk;
-        for (int q = 0; q < kMmaM; ++q)
-          s = __fmaf_rn(sW[q * (NN + 1) + r] * sB[q], sW[q * (NN + 1) + q2], s);
-      } else {
-        const int r = e - kk * kk;
-        for (int q = 0; q < kMmaM; ++q) s = __fmaf_rn(sD[q], sW[q * (NN + 1) + r], s);
+    const int nb = (kk + 3) >> 2, nb2 = nb * nb;    // nb <= 12
+    const int groups = nb2 <= 64 ? 4 : 2;           // each thread owns at most two blocks
+    const int gsz = kStConsumers / groups;
+    const int grp = tid / gsz, t = tid - grp * gsz;
+    const int q0 = grp * (kMmaM / groups), q1 = q0 + kMmaM / groups;
+    for (int blk = t; blk < nb2; blk += gsz) {
+      const int br = blk / nb, bc = blk - br * nb;
+      float o4[4][4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) o4[x][y] = 0.f;
+      for (int q = q0; q < q1; ++q) {
+        float u[4], v[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          u[x] = sWb[q * WS + min(4 * br + x, NN - 1)];
+          v[x] = sW[q * WS + min(4 * bc + x, NN - 1)];
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) o4[x][y] = __fmaf_rn(u[x], v[y], o4[x][y]);
       }
-      dstp[e] = (double)s;
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) sP[(grp * nb2 + blk) * 16 + x * 4 + y] = o4[x][y];
+    }
+    // d^T W
+    for (int r = tid; r < kk; r += kStConsumers) {
+      float sdw = 0.f;
+      for (int q = 0; q < kMmaM; ++q) sdw = __fmaf_rn(sD[q], sW[q * WS + r], sdw);
+      dstp[kk * kk + r] = (double)sdw;
+    }
+    cons_sync();
+    for (int e = tid; e < nb2 * 16; e += kStConsumers) {
+      const int blk = e >> 4, x = (e >> 2) & 3, y = e & 3;
+      const int br = blk / nb, bc = blk - br * nb;
+      const int r = 4 * br + x, cc = 4 * bc + y;
+      float sum = 0.f;
+      for (int g2 = 0; g2 < groups; ++g2) sum += sP[(g2 * nb2 + blk) * 16 + x * 4 + y];
+      if (r < kk && cc < kk) dstp[r * kk + cc] = (double)sum;
     }
   }
   // the block's three sums (only the first 128 threads hold nonzero values)
@@ -442,24 +486,32 @@ __global__ void __launch_bounds__(256) colmma_kernel(AccArgs args, const float* 
 //     of the next MMAs, no shared-memory round trip;
 //   * warp 9 (MMA issuer, TMEM owner): 4 x 3 MMAs per chunk (K = 8; hi*hi,
 //     hi*lo, lo*hi) from the TMEM A buffer and the B tiles in shared memory.
-// Two TMEM A buffers let the consumers form chunk c + 1 while the tensor core
-// multiplies chunk c.  Barriers: full[s] (copies landed), empty[s] (8 consumer
-// warps + the MMA commit), afull[b] (8 consumer warps stored A), aempty[b]
-// (MMA commit), acc (all MMAs done).  Every wait is bounded.
+// Three TMEM A buffers let the consumers run up to two chunks ahead of the
+// tensor core.  Barriers: full[s] / empty[s] of the cost ring (copies landed;
+// 8 consumer warps read them), bfull[t] / bempty[t] of the operand ring
+// (copy landed; MMA commit), afull[b] (8 consumer warps stored A), aempty[b]
+// (MMA commit), acc (all MMAs done).  The producer warp feeds the cost ring,
+// the MMA thread the operand ring.  Every wait is bounded.
 // ---------------------------------------------------------------------------
 constexpr int kTmThreads = 320;
 constexpr uint32_t kTmTile = kMmaKC * kMmaM * 4;   // 16 KB cost tile
 constexpr uint32_t kTmA = 64;                      // TMEM column of A buffer 0
+constexpr int kTmNA = 3;                           // TMEM A buffers (64 columns each)
 constexpr uint32_t kTmCols = 256;
 
+// Two rings: cost stages (tile + the rows' coefficients), released by the
+// consumers as soon as they have read them, and operand stages (B hi, B lo),
+// released by the MMA commit.
 template <int NN>
 struct TmaSmem {
-  static constexpr int stages = NN <= 32 ? 4 : 3;
-  static constexpr uint32_t b_off = kTmTile;                     // B hi, then B lo
-  static constexpr uint32_t coef_off = kTmTile + 2 * NN * 128;   // A[32], AL[32]
-  static constexpr uint32_t stage = (coef_off + 256 + 1023) / 1024 * 1024;
-  static constexpr size_t bytes = (size_t)stages * stage + 1024;
-  static constexpr uint32_t tx = kTmTile + 2 * NN * 128 + 256;
+  static constexpr int cstages = 4;
+  static constexpr int bstages = NN <= 48 ? 3 : 2;
+  static constexpr uint32_t coef_off = kTmTile;                     // A[32], AL[32]
+  static constexpr uint32_t cstage = (kTmTile + 256 + 1023) / 1024 * 1024;
+  static constexpr uint32_t bstage = 2 * NN * 128;                  // a multiple of 1024
+  static constexpr uint32_t b_base = cstages * cstage;
+  static constexpr size_t bytes = (size_t)b_base + (size_t)bstages * bstage + 1024;
+  static constexpr uint32_t ctx = kTmTile + 256;
 };
 
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t v[16]) {
@@ -484,13 +536,18 @@ __device__ __forceinline__ void mma_tf32_ts(uint32_t tmem_d, uint32_t ta, uint64
       "r"(ta), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
-// TF32 parts of a non-negative float: hi rounded to 10 fraction bits (half
-// up), lo = x - hi (exact) truncated to 10 fraction bits; hi + lo matches x
-// to 2^-21 relative.
-__device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
-  const uint32_t h = (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
-  hi = h;
-  lo = __float_as_uint(__fsub_rn(x, __uint_as_float(h))) & 0xFFFFE000u;
+// TF32 parts of a pair of non-negative floats: hi = x with the 13 low fraction
+// bits cleared, lo = x - hi (exact in float32).  The tensor core reads a tf32
+// operand from the high 19 bits of its 32-bit register, so lo is passed whole
+// and enters with its leading 11 bits: hi + lo as multiplied matches x to
+// 2^-21 relative.
+__device__ __forceinline__ void tf32_split2(float2 x, uint32_t& h0, uint32_t& h1, uint32_t& l0,
+                                            uint32_t& l1) {
+  h0 = __float_as_uint(x.x) & 0xFFFFE000u;
+  h1 = __float_as_uint(x.y) & 0xFFFFE000u;
+  const float2 lo = __ffma2_rn(f2(__uint_as_float(h0), __uint_as_float(h1)), f2(-1.f, -1.f), x);
+  l0 = __float_as_uint(lo.x);
+  l1 = __float_as_uint(lo.y);
 }
 
 // ROW = false: column direction (output index j over 128-column blocks,
@@ -512,13 +569,15 @@ __global__ void __launch_bounds__(kTmThreads, 2)
   const int gb = s4 ? st->cur_g : args.gbuf;
   const int dst_g = (st->cur_g + 1) % 3;
   using SM = TmaSmem<NN>;
-  constexpr int NS = SM::stages;
+  constexpr int NS = SM::cstages, NB = SM::bstages;
 
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[NS];
   __shared__ __align__(8) uint64_t empty_bar[NS];
-  __shared__ __align__(8) uint64_t afull[2];
-  __shared__ __align__(8) uint64_t aempty[2];
+  __shared__ __align__(8) uint64_t bfull[NB];
+  __shared__ __align__(8) uint64_t bempty[NB];
+  __shared__ __align__(8) uint64_t afull[kTmNA];
+  __shared__ __align__(8) uint64_t aempty[kTmNA];
   __shared__ __align__(8) uint64_t accf;
   __shared__ uint32_t s_tmem;
   __shared__ int s_err;
@@ -542,9 +601,13 @@ __global__ void __launch_bounds__(kTmThreads, 2)
   if (tid == 0) {
     for (int s = 0; s < NS; ++s) {
       mbar_init(smem_addr(&full_bar[s]), 1);
-      mbar_init(smem_addr(&empty_bar[s]), 9);
+      mbar_init(smem_addr(&empty_bar[s]), 8);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int t = 0; t < NB; ++t) {
+      mbar_init(smem_addr(&bfull[t]), 1);
+      mbar_init(smem_addr(&bempty[t]), 1);
+    }
+    for (int b = 0; b < kTmNA; ++b) {
       mbar_init(smem_addr(&afull[b]), 8);
       mbar_init(smem_addr(&aempty[b]), 1);
     }
@@ -561,6 +624,7 @@ __global__ void __launch_bounds__(kTmThreads, 2)
   if (wid == 8) {
     // ---------------- producer ----------------
     if (lane == 0) {
+      // cost ring
       const float* rA = ROW ? P.cs[gb].A : P.rs[fb].A;
       const float* rAL = ROW ? P.cs[gb].AL : P.rs[fb].AL;
       int issued = 0;
@@ -572,16 +636,14 @@ __global__ void __launch_bounds__(kTmThreads, 2)
           break;
         }
         const uint32_t fbar = smem_addr(&full_bar[s]);
-        const uint32_t dst = base + (uint32_t)s * SM::stage;
+        const uint32_t dst = base + (uint32_t)s * SM::cstage;
         const int i0 = i_beg + ch * kMmaKC;   // a multiple of 32 (segments are)
-        mbar_expect_tx(fbar, SM::tx);
+        mbar_expect_tx(fbar, SM::ctx);
         // the box's first column (cb * 128, or i0) starts on a 16-byte boundary
         if (ROW)
           tma_load_2d(dst, &PP->tmCr, i0, cb * kMmaM, fbar);
         else
           tma_load_2d(dst, &PP->tmC, cb * kMmaM, i0, fbar);
-        bulk_load(dst + SM::b_off, tiles + (size_t)(i0 / kMmaKC) * 2 * NN * kMmaKC,
-                  2u * NN * 128u, fbar);
         // the split arrays are padded to a multiple of 128 floats
         bulk_load(dst + SM::coef_off, rA + i0, 128u, fbar);
         bulk_load(dst + SM::coef_off + 128u, rAL + i0, 128u, fbar);
@@ -596,15 +658,27 @@ __global__ void __launch_bounds__(kTmThreads, 2)
   } else if (wid == 9) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
+      // operand ring: the MMA thread refills a stage once its own products
+      // that read it are done (the consumers run well behind the tensor core)
+      auto load_b = [&](int ch) {
+        const int t = ch % NB;
+        const uint32_t bbar = smem_addr(&bfull[t]);
+        mbar_expect_tx(bbar, SM::bstage);
+        bulk_load(base + SM::b_base + (uint32_t)t * SM::bstage,
+                  tiles + (size_t)((i_beg + ch * kMmaKC) / kMmaKC) * 2 * NN * kMmaKC, SM::bstage,
+                  bbar);
+      };
+      int bissued = 0;
+      for (; bissued < NB && bissued < nch; ++bissued) load_b(bissued);
       for (int ch = 0; ch < nch; ++ch) {
-        const int s = ch % NS, b = ch & 1;
-        if (!mbar_wait(smem_addr(&full_bar[s]), (ch / NS) & 1, kMmaWait) ||
-            !mbar_wait(smem_addr(&afull[b]), (ch >> 1) & 1, kMmaWait)) {
+        const int t = ch % NB, b = ch % kTmNA;
+        if (!mbar_wait(smem_addr(&bfull[t]), (ch / NB) & 1, kMmaWait) ||
+            !mbar_wait(smem_addr(&afull[b]), (ch / kTmNA) & 1, kMmaWait)) {
           s_err = 1;
           break;
         }
         tc_fence_after();
-        const uint32_t bhi = base + (uint32_t)s * SM::stage + SM::b_off;
+        const uint32_t bhi = base + SM::b_base + (uint32_t)t * SM::bstage;
         const uint32_t blo = bhi + (uint32_t)NN * 128u;
         const uint32_t ahi = tmem + kTmA + 64u * b, alo = ahi + 32u;
 #pragma unroll
@@ -614,10 +688,22 @@ __global__ void __launch_bounds__(kTmThreads, 2)
           mma_tf32_ts(tmem, ahi + 8 * k, sdesc_sw128(blo + ko), idesc, 1u);
           mma_tf32_ts(tmem, alo + 8 * k, sdesc_sw128(bhi + ko), idesc, 1u);
         }
-        mma_commit(smem_addr(&empty_bar[s]));
+        mma_commit(smem_addr(&bempty[t]));
         mma_commit(smem_addr(&aempty[b]));
+        if (bissued < nch) {
+          if (!mbar_wait(smem_addr(&bempty[t]), (ch / NB) & 1, kMmaWait)) {
+            s_err = 1;
+            break;
+          }
+          load_b(bissued++);
+        }
       }
       mma_commit(smem_addr(&accf));   // tracks every MMA issued above
+      // every operand copy has landed before the CTA may exit
+      for (int t = 0; t < NB && t < bissued; ++t) {
+        const int last = t + ((bissued - 1 - t) / NB) * NB;
+        if (!mbar_wait(smem_addr(&bfull[t]), (last / NB) & 1, kMmaWait)) s_err = 1;
+      }
     }
   } else {
     // ---------------- consumers ----------------
@@ -635,12 +721,12 @@ __global__ void __launch_bounds__(kTmThreads, 2)
     float2 S2 = f2(0.f, 0.f), C2 = f2(0.f, 0.f);   // running sum, compensation
     bool werr = false;
     for (int ch = 0; ch < nch; ++ch) {
-      const int s = ch % NS, b = ch & 1;
+      const int s = ch % NS, b = ch % kTmNA;
       if (!__all_sync(0xffffffffu, mbar_wait(smem_addr(&full_bar[s]), (ch / NS) & 1, kMmaWait))) {
         werr = true;
         break;
       }
-      const unsigned char* stg = sbase + (size_t)s * SM::stage;
+      const unsigned char* stg = sbase + (size_t)s * SM::cstage;
       const float* tile = reinterpret_cast<const float*>(stg);
       const float4* cA = reinterpret_cast<const float4*>(stg + SM::coef_off) + h * 4;
       const float4* cAL = reinterpret_cast<const float4*>(stg + SM::coef_off + 128) + h * 4;
@@ -705,13 +791,11 @@ __global__ void __launch_bounds__(kTmThreads, 2)
       }
       uint32_t hv[16], lv[16];
 #pragma unroll
-      for (int p = 0; p < 8; ++p) {
-        tf32_split(e[p].x, hv[2 * p], lv[2 * p]);
-        tf32_split(e[p].y, hv[2 * p + 1], lv[2 * p + 1]);
-      }
-      // A buffer b is free once the MMAs of chunk ch - 2 are done
-      if (ch >= 2 &&
-          !__all_sync(0xffffffffu, mbar_wait(smem_addr(&aempty[b]), ((ch - 2) >> 1) & 1, kMmaWait))) {
+      for (int p = 0; p < 8; ++p) tf32_split2(e[p], hv[2 * p], hv[2 * p + 1], lv[2 * p], lv[2 * p + 1]);
+      // A buffer b is free once the MMAs of chunk ch - kTmNA are done
+      if (ch >= kTmNA &&
+          !__all_sync(0xffffffffu,
+                      mbar_wait(smem_addr(&aempty[b]), ((ch - kTmNA) / kTmNA) & 1, kMmaWait))) {
         werr = true;
         break;
       }
@@ -779,14 +863,20 @@ size_t mma_tiles_floats(int n, int k) {
   return (size_t)((n + kMmaKC - 1) / kMmaKC) * 2 * mma_width(k) * kMmaKC;
 }
 
+// (A programmatic dependent launch of this kernel measured slower: its CTAs
+// then hold shared memory and TMEM while the preceding pass finishes.)
+template <int NN, bool ROW>
+static cudaError_t launch_tma(const AccArgs& a, const float* tiles, dim3 grid, cudaStream_t s) {
+  mma_tma_kernel<NN, ROW><<<grid, kTmThreads, TmaSmem<NN>::bytes, s>>>(a, tiles);
+  return cudaGetLastError();
+}
+
 template <int NN>
 static cudaError_t launch_colmma_k(const AccArgs& a, bool tma, const float* tiles, int ncolblk,
                                    cudaStream_t s) {
   dim3 grid(ncolblk, a.nseg);
-  if (tma)
-    mma_tma_kernel<NN, false><<<grid, kTmThreads, TmaSmem<NN>::bytes, s>>>(a, tiles);
-  else
-    colmma_kernel<NN><<<grid, 256, MmaSmem<NN>::bytes, s>>>(a, tiles);
+  if (tma) return launch_tma<NN, false>(a, tiles, grid, s);
+  colmma_kernel<NN><<<grid, 256, MmaSmem<NN>::bytes, s>>>(a, tiles);
   return cudaGetLastError();
 }
 
@@ -809,12 +899,11 @@ cudaError_t launch_rowmma(const AccArgs& a, const float* tiles, int nrowblk, cud
   dim3 grid(nrowblk, a.nseg);
   if (a.seg_len % kMmaKC != 0) return cudaErrorInvalidValue;
   switch (mma_width(a.k)) {
-    case 16: mma_tma_kernel<16, true><<<grid, kTmThreads, TmaSmem<16>::bytes, s>>>(a, tiles); break;
-    case 32: mma_tma_kernel<32, true><<<grid, kTmThreads, TmaSmem<32>::bytes, s>>>(a, tiles); break;
-    case 48: mma_tma_kernel<48, true><<<grid, kTmThreads, TmaSmem<48>::bytes, s>>>(a, tiles); break;
-    default: mma_tma_kernel<64, true><<<grid, kTmThreads, TmaSmem<64>::bytes, s>>>(a, tiles); break;
+    case 16: return launch_tma<16, true>(a, tiles, grid, s);
+    case 32: return launch_tma<32, true>(a, tiles, grid, s);
+    case 48: return launch_tma<48, true>(a, tiles, grid, s);
+    default: return launch_tma<64, true>(a, tiles, grid, s);
   }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_build_tiles(const float* Z, int n, int kk, float* tiles, cudaStream_t s) {

@@ -13,6 +13,7 @@
 //  * eig_small_kernel (one CTA, float32 Jacobi): Rayleigh-Ritz of the block
 //    subspace iteration and the Cholesky-QR transform of the next block;
 //  * apply_kernel: Z <- (X - 1 c^T) B.
+#include <algorithm>
 #include "eot_device.cuh"
 #include "eot_internal.h"
 
@@ -216,12 +217,13 @@ __global__ void fprime_kernel(const Prob* __restrict__ PP) {
 //   outputs B (p x p float32), theta (p), max residual over the first l.
 // Launched as one CTA of kMaxP/2 x kMaxP/2 threads (launch_eig_small).
 // ---------------------------------------------------------------------------
-constexpr int kEH = kMaxP / 2;   // the block is kEH x kEH threads: one per pair of pairs
+constexpr int kEH = kMaxP / 2;   // at most kEH x kEH threads: one per pair of pairs
 constexpr int kES = kMaxP + 1;   // odd row stride of the shared matrices
 
-// Block-wide sum of two floats over the kEH x kEH threads; valid in thread 0.
+// Block-wide sum of two floats; valid in thread 0.
 __device__ __forceinline__ void eig_sum2(float& a, float& b, float* red) {
-  const int tid = threadIdx.y * kEH + threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int nt = blockDim.x * blockDim.y;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, lane = tid & 31, w = tid >> 5;
   a = warp_sum_f(a);
   b = warp_sum_f(b);
   if (lane == 0) {
@@ -231,10 +233,32 @@ __device__ __forceinline__ void eig_sum2(float& a, float& b, float* red) {
   __syncthreads();
   if (tid == 0) {
     a = b = 0.f;
-    for (int k = 0; k < (kEH * kEH + 31) / 32; ++k) {
+    for (int k = 0; k < (nt + 31) / 32; ++k) {
       a += red[k];
       b += red[32 + k];
     }
+  }
+}
+
+// Entry (x, y) of R1 B R2^T for a 2 x 2 block B (b00, b01, b10, b11) and
+// rotations R = [[c, -s], [s, c]].
+__device__ __forceinline__ float rot_entry(int x, int y, float c1, float s1, float c2, float s2,
+                                           float b00, float b01, float b10, float b11) {
+  const float u0 = x ? s1 : c1, u1 = x ? c1 : -s1;   // row x of R1
+  const float v0 = y ? s2 : c2, v1 = y ? c2 : -s2;   // row y of R2
+  return u0 * (b00 * v0 + b01 * v1) + u1 * (b10 * v0 + b11 * v1);
+}
+
+// Jacobi rotation annihilating a_kq of the symmetric 2 x 2 problem.
+__device__ __forceinline__ void jacobi_rot(float akk, float aqq, float akq, float& cth,
+                                           float& sth) {
+  cth = 1.f;
+  sth = 0.f;
+  if (fabsf(akq) > 1e-30f) {
+    const float tau = (aqq - akk) / (2.f * akq);
+    const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+    cth = rsqrtf(1.f + t * t);
+    sth = t * cth;
   }
 }
 
@@ -246,36 +270,64 @@ __global__ void __launch_bounds__(kEH * kEH) eig_small_kernel(int p, int l, int 
                                                               double* __restrict__ theta_out,
                                                               double* __restrict__ resid_out,
                                                               int* __restrict__ fail_out) {
-  __shared__ float A[kMaxP * kES];
+  __shared__ float A0[kMaxP * kES];
   __shared__ float Q[kMaxP * kES];
   __shared__ float G[kMaxP * kES];
-  __shared__ float W[kMaxP * kES];
-  __shared__ float rc[kEH], rs[kEH], sq[kMaxP];
-  __shared__ int pk[kEH], pq[kEH];
+  __shared__ float W[kMaxP * kES];        // scratch; the second Jacobi buffer
+  __shared__ float rc[2][kEH], rs[2][kEH], sq[kMaxP];
+  __shared__ int pk[2][kEH], pq[2][kEH];
+  __shared__ unsigned short sched[(kMaxP - 1) * kEH];   // round r, slot t: k | q << 8
+  __shared__ unsigned char slot_of[(kMaxP - 1) * kMaxP]; // round r, index: slot << 1 | (is q)
   __shared__ float th[kMaxP], cf[kMaxP], qc[kMaxP];
   __shared__ int order[kMaxP];
   __shared__ float red[64];
   __shared__ int s_stop, s_fail;
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kEH + tx;
-  const int pe = (p + 1) & ~1;   // padded even size for the circle ordering
-  const int half = pe / 2;
-  for (int r = ty; r < pe; r += kEH)
-    for (int q = tx; q < pe; q += kEH) {
+  const int nx = blockDim.x;              // blockDim = (nx, nx), nx >= half
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * nx + tx, nt = nx * nx;
+  const int pe = (p + 1) & ~1;            // padded even size for the circle ordering
+  const int half = pe / 2, nr = pe - 1;   // pairs per round, rounds per sweep
+  float* A = A0;
+  for (int r = ty; r < pe; r += nx)
+    for (int q = tx; q < pe; q += nx) {
       const bool in = r < p && q < p;
       A[r * kES + q] = (mode == 1 && in) ? (float)(0.5 * (T[r * p + q] + T[q * p + r])) : 0.f;
       Q[r * kES + q] = (r == q) ? 1.f : 0.f;
     }
-  for (int k = tid; k < p; k += kEH * kEH) cf[k] = (float)c[k];
+  for (int k = tid; k < p; k += nt) cf[k] = (float)c[k];
+  if (mode == 1) {
+    // circle ordering: index 0 fixed, the others rotate by one place per round
+    for (int e = tid; e < nr * half; e += nt) {
+      const int r = e / half, t = e - r * half;
+      const int pa = t, pb = pe - 1 - t;
+      const int a = pa == 0 ? 0 : 1 + (pa - 1 + r) % nr;
+      const int b = 1 + (pb - 1 + r) % nr;
+      const int k = min(a, b), q = max(a, b);
+      sched[e] = (unsigned short)(k | (q << 8));
+      slot_of[r * pe + k] = (unsigned char)(t << 1);
+      slot_of[r * pe + q] = (unsigned char)((t << 1) | 1);
+    }
+  }
   if (tid == 0) s_fail = 0;
   __syncthreads();
   if (mode == 1) {
-    // cyclic Jacobi, circle ordering: in each round the pe/2 disjoint pairs
-    // rotate at once; thread (ty, tx) applies A <- R A R^T to the 2 x 2 block
-    // of pairs (ty, tx) and Q <- Q R^T to two rows of pair tx
+    // cyclic Jacobi: in each round the pe/2 disjoint pairs rotate at once;
+    // thread (ty, tx) maps the 2 x 2 block of pairs (ty, tx) from A to the
+    // other buffer (A' = R A R^T), applies the rotations of pair tx to rows ty
+    // and ty + half of Q, and (ty == 0) forms the rotation of slot tx of the
+    // next round from the current values: one barrier per round
+    float* An = W;
+    if (ty == 0 && tx < half) {
+      const int kq = sched[tx], k = kq & 255, q = kq >> 8;
+      pk[0][tx] = k;
+      pq[0][tx] = q;
+      jacobi_rot(A[k * kES + k], A[q * kES + q], A[k * kES + q], rc[0][tx], rs[0][tx]);
+    }
+    __syncthreads();
+    int cur = 0;
     for (int sweep = 0; sweep < 12; ++sweep) {
       float loc = 0.f, dia = 0.f;
-      for (int r = ty; r < pe; r += kEH)
-        for (int q = tx; q < pe; q += kEH) {
+      for (int r = ty; r < pe; r += nx)
+        for (int q = tx; q < pe; q += nx) {
           const float v = A[r * kES + q];
           if (r != q) loc += v * v;
           else dia += v * v;
@@ -284,88 +336,93 @@ __global__ void __launch_bounds__(kEH * kEH) eig_small_kernel(int p, int l, int 
       if (tid == 0) s_stop = (loc <= 1e-10f * (dia + 1e-30f)) ? 1 : 0;
       __syncthreads();
       if (s_stop) break;
-      for (int round = 0; round < pe - 1; ++round) {
-        if (ty == 0 && tx < half) {
-          const int pa = tx, pb = pe - 1 - tx;
-          const int a = pa == 0 ? 0 : 1 + (pa - 1 + round) % (pe - 1);
-          const int b = 1 + (pb - 1 + round) % (pe - 1);
-          const int k = min(a, b), q = max(a, b);
-          pk[tx] = k;
-          pq[tx] = q;
-          const float akq = A[k * kES + q];
-          float cth = 1.f, sth = 0.f;
-          if (fabsf(akq) > 1e-30f) {
-            const float tau = (A[q * kES + q] - A[k * kES + k]) / (2.f * akq);
-            const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-            cth = rsqrtf(1.f + t * t);
-            sth = t * cth;
-          }
-          rc[tx] = cth;
-          rs[tx] = sth;
-        }
-        __syncthreads();
+      for (int round = 0; round < nr; ++round) {
         if (ty < half && tx < half) {
-          const int k1 = pk[ty], q1 = pq[ty], k2 = pk[tx], q2 = pq[tx];
-          const float c1 = rc[ty], s1 = rs[ty], c2 = rc[tx], s2 = rs[tx];
+          const int k1 = pk[cur][ty], q1 = pq[cur][ty], k2 = pk[cur][tx], q2 = pq[cur][tx];
+          const float c1 = rc[cur][ty], s1 = rs[cur][ty], c2 = rc[cur][tx], s2 = rs[cur][tx];
           const float a = A[k1 * kES + k2], b = A[k1 * kES + q2];
           const float e = A[q1 * kES + k2], d = A[q1 * kES + q2];
           const float u11 = c1 * a - s1 * e, u12 = c1 * b - s1 * d;
           const float u21 = s1 * a + c1 * e, u22 = s1 * b + c1 * d;
-          A[k1 * kES + k2] = u11 * c2 - u12 * s2;
-          A[k1 * kES + q2] = u11 * s2 + u12 * c2;
-          A[q1 * kES + k2] = u21 * c2 - u22 * s2;
-          A[q1 * kES + q2] = u21 * s2 + u22 * c2;
+          An[k1 * kES + k2] = u11 * c2 - u12 * s2;
+          An[k1 * kES + q2] = u11 * s2 + u12 * c2;
+          An[q1 * kES + k2] = u21 * c2 - u22 * s2;
+          An[q1 * kES + q2] = u21 * s2 + u22 * c2;
         }
         if (tx < half) {
-          const int k = pk[tx], q = pq[tx];
-          const float cth = rc[tx], sth = rs[tx];
-          for (int r = ty; r < pe; r += kEH) {
+          const int k = pk[cur][tx], q = pq[cur][tx];
+          const float cth = rc[cur][tx], sth = rs[cur][tx];
+          for (int r = ty; r < pe; r += nx) {
             const float qk = Q[r * kES + k], qq = Q[r * kES + q];
             Q[r * kES + k] = cth * qk - sth * qq;
             Q[r * kES + q] = sth * qk + cth * qq;
           }
         }
+        if (ty == 0 && tx < half) {
+          // slot tx of the next round (round 0 of the next sweep after the last)
+          const int rn = round + 1 < nr ? round + 1 : 0;
+          const int kq = sched[rn * half + tx], k = kq & 255, q = kq >> 8;
+          const int ok_ = slot_of[round * pe + k], oq_ = slot_of[round * pe + q];
+          const int ta = ok_ >> 1, xa = ok_ & 1, tb = oq_ >> 1, xb = oq_ & 1;
+          const float ca = rc[cur][ta], sa = rs[cur][ta], cb = rc[cur][tb], sb = rs[cur][tb];
+          const int ka = pk[cur][ta], qa = pq[cur][ta], kb = pk[cur][tb], qb = pq[cur][tb];
+          const float akk = rot_entry(xa, xa, ca, sa, ca, sa, A[ka * kES + ka], A[ka * kES + qa],
+                                      A[qa * kES + ka], A[qa * kES + qa]);
+          const float aqq = rot_entry(xb, xb, cb, sb, cb, sb, A[kb * kES + kb], A[kb * kES + qb],
+                                      A[qb * kES + kb], A[qb * kES + qb]);
+          const float akq = rot_entry(xa, xb, ca, sa, cb, sb, A[ka * kES + kb], A[ka * kES + qb],
+                                      A[qa * kES + kb], A[qa * kES + qb]);
+          pk[cur ^ 1][tx] = k;
+          pq[cur ^ 1][tx] = q;
+          jacobi_rot(akk, aqq, akq, rc[cur ^ 1][tx], rs[cur ^ 1][tx]);
+        }
         __syncthreads();
+        float* t2 = A;
+        A = An;
+        An = t2;
+        cur ^= 1;
       }
     }
-    for (int k = tid; k < p; k += kEH * kEH) th[k] = A[k * kES + k];
+    for (int k = tid; k < p; k += nt) th[k] = A[k * kES + k];
     __syncthreads();
-    for (int k = tid; k < p; k += kEH * kEH) {
+    for (int k = tid; k < p; k += nt) {
       int rank = 0;
       for (int q = 0; q < p; ++q) rank += (th[q] > th[k]) || (th[q] == th[k] && q < k);
       order[rank] = k;
     }
     __syncthreads();
-    for (int r = ty; r < p; r += kEH)     // W = Q with the columns in descending order
-      for (int q = tx; q < p; q += kEH) W[r * kES + q] = Q[r * kES + order[q]];
+    for (int r = ty; r < p; r += nx)      // G = Q with the columns in descending order
+      for (int q = tx; q < p; q += nx) G[r * kES + q] = Q[r * kES + order[q]];
     if (tid < p) theta_out[tid] = (double)th[order[tid]];
     __syncthreads();
-    for (int r = ty; r < p; r += kEH)
-      for (int q = tx; q < p; q += kEH) Q[r * kES + q] = W[r * kES + q];
+    for (int r = ty; r < p; r += nx)
+      for (int q = tx; q < p; q += nx) Q[r * kES + q] = G[r * kES + q];
   } else {
-    for (int r = ty; r < p; r += kEH)
-      for (int q = tx; q < p; q += kEH) Q[r * kES + q] = (r == q) ? 1.f : 0.f;
+    for (int r = ty; r < p; r += nx)
+      for (int q = tx; q < p; q += nx) Q[r * kES + q] = (r == q) ? 1.f : 0.f;
   }
+  __syncthreads();
+  A = A0;
   // G = GXX - c c^T (float), then (mode 1) G <- Q^T G Q
-  for (int r = ty; r < p; r += kEH)
-    for (int q = tx; q < p; q += kEH) G[r * kES + q] = (float)(GXX[r * p + q] - c[r] * c[q]);
+  for (int r = ty; r < p; r += nx)
+    for (int q = tx; q < p; q += nx) G[r * kES + q] = (float)(GXX[r * p + q] - c[r] * c[q]);
   __syncthreads();
   if (mode == 1) {
-    for (int r = ty; r < p; r += kEH)     // W = G Q
-      for (int q = tx; q < p; q += kEH) {
+    for (int r = ty; r < p; r += nx)      // W = G Q
+      for (int q = tx; q < p; q += nx) {
         float acc = 0.f;
         for (int k = 0; k < p; ++k) acc = __fmaf_rn(G[r * kES + k], Q[k * kES + q], acc);
         W[r * kES + q] = acc;
       }
     if (ty == 0)                          // (Q^T c)_k
-      for (int k = tx; k < p; k += kEH) {
+      for (int k = tx; k < p; k += nx) {
         float acc = 0.f;
         for (int r = 0; r < p; ++r) acc = __fmaf_rn(Q[r * kES + k], cf[r], acc);
         qc[k] = acc;
       }
     __syncthreads();
-    for (int r = ty; r < p; r += kEH)     // A = Q^T W
-      for (int q = tx; q < p; q += kEH) {
+    for (int r = ty; r < p; r += nx)      // A = Q^T W
+      for (int q = tx; q < p; q += nx) {
         float acc = 0.f;
         for (int k = 0; k < p; ++k) acc = __fmaf_rn(Q[k * kES + r], W[k * kES + q], acc);
         A[r * kES + q] = acc;
@@ -373,7 +430,7 @@ __global__ void __launch_bounds__(kEH * kEH) eig_small_kernel(int p, int l, int 
     __syncthreads();
     // residual_k^2 = (Q^T GXX Q)_kk - theta_k^2 = G'_kk + (Q^T c)_k^2 - theta_k^2
     float rmax = 0.f;
-    for (int k = tid; k < l && k < p; k += kEH * kEH) {
+    for (int k = tid; k < l && k < p; k += nt) {
       const float t = (float)theta_out[k];
       const float r2 = A[k * kES + k] + qc[k] * qc[k] - t * t;
       rmax = fmaxf(rmax, r2 > 0.f ? sqrtf(r2) : 0.f);
@@ -384,11 +441,11 @@ __global__ void __launch_bounds__(kEH * kEH) eig_small_kernel(int p, int l, int 
     __syncthreads();
     if (tid == 0) {
       float mx = 0.f;
-      for (int w = 0; w < (kEH * kEH + 31) / 32; ++w) mx = fmaxf(mx, red[w]);
+      for (int w = 0; w < (nt + 31) / 32; ++w) mx = fmaxf(mx, red[w]);
       *resid_out = (double)mx;
     }
-    for (int r = ty; r < p; r += kEH)
-      for (int q = tx; q < p; q += kEH) G[r * kES + q] = A[r * kES + q];
+    for (int r = ty; r < p; r += nx)
+      for (int q = tx; q < p; q += nx) G[r * kES + q] = A[r * kES + q];
     __syncthreads();
   }
   // G = L D L^T by outer products (one barrier per pivot); L = L1 D^(1/2)
@@ -396,39 +453,40 @@ __global__ void __launch_bounds__(kEH * kEH) eig_small_kernel(int p, int l, int 
     const float dk = G[k * kES + k];
     if (tid == 0 && !(dk > 0.f)) s_fail = 1;
     const float inv = dk > 0.f ? 1.f / dk : 0.f;
-    for (int r = k + 1 + ty; r < p; r += kEH) {
+    for (int r = k + 1 + ty; r < p; r += nx) {
       const float hr = G[r * kES + k] * inv;
-      for (int q = k + 1 + tx; q <= r; q += kEH) G[r * kES + q] -= hr * G[q * kES + k];
+      for (int q = k + 1 + tx; q <= r; q += nx) G[r * kES + q] -= hr * G[q * kES + k];
     }
     __syncthreads();
   }
-  for (int k = tid; k < p; k += kEH * kEH) {
+  for (int k = tid; k < p; k += nt) {
     const float dk = G[k * kES + k];
     sq[k] = dk > 0.f ? sqrtf(dk) : 1.f;
   }
-  for (int r = ty; r < p; r += kEH)       // W = Q (right-hand sides)
-    for (int q = tx; q < p; q += kEH) W[r * kES + q] = Q[r * kES + q];
+  for (int r = ty; r < p; r += nx)        // W = Q (right-hand sides)
+    for (int q = tx; q < p; q += nx) W[r * kES + q] = Q[r * kES + q];
   __syncthreads();
   // B L^T = Q, column by column: after step q, column q of W is final
   // (L_cq = G_cq / sqrt(D_q) for c > q, L_qq = sqrt(D_q))
   for (int q = 0; q < p; ++q) {
     const float lqq = sq[q];
-    for (int r = ty; r < p; r += kEH) {
+    for (int r = ty; r < p; r += nx) {
       const float b = W[r * kES + q] / lqq;
-      for (int cc = q + 1 + tx; cc < p; cc += kEH)
+      for (int cc = q + 1 + tx; cc < p; cc += nx)
         W[r * kES + cc] -= b * (G[cc * kES + q] / lqq);
     }
     __syncthreads();
   }
-  for (int r = ty; r < p; r += kEH)
-    for (int q = tx; q < p; q += kEH) Bout[r * p + q] = W[r * kES + q] / sq[q];
+  for (int r = ty; r < p; r += nx)
+    for (int q = tx; q < p; q += nx) Bout[r * p + q] = W[r * kES + q] / sq[q];
   if (tid == 0 && fail_out) *fail_out = s_fail;
 }
 
 void launch_eig_small(int p, int l, int mode, const double* GXX, const double* T,
                       const double* c, float* B, double* theta, double* resid, int* fail,
                       cudaStream_t s) {
-  eig_small_kernel<<<1, dim3(kEH, kEH), 0, s>>>(p, l, mode, GXX, T, c, B, theta, resid, fail);
+  const int half = std::max(4, ((p + 1) & ~1) / 2);   // one thread per pair of pairs
+  eig_small_kernel<<<1, dim3(half, half), 0, s>>>(p, l, mode, GXX, T, c, B, theta, resid, fail);
 }
 
 // Z_i <- (X_i - c) B   (len x p, float32), c float64 (deflation of the constant).
