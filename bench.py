@@ -399,7 +399,9 @@ def extras(pkg, torch, stream):
                        "total_iters": int(iters),
                        "cost_gb_streamed_per_s": round(8.0 * nm * (iters / len(probs)) /
                                                        (t1 - t0) / 1e9, 1),
-                       "note": "host arrays in and out; solves overlap on per-thread streams"}
+                       "note": "host arrays in and out; one persistent cooperative launch "
+                               "(graph-captured) runs every problem, gang sizes from a "
+                               "calibrated cost model"}
     # c5: served stream (Poisson arrivals, continuous batching, warm restarts)
     stage("c5: serving")
     reqs = workloads.served_stream(seed=1, rate_per_s=2000.0, duration_s=60.0, max_requests=96)

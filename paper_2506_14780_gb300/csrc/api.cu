@@ -34,6 +34,7 @@
 
 #include "eot.h"
 #include "eot_internal.h"
+#include "batch.h"
 
 namespace eotk {
 
@@ -1311,6 +1312,504 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   return status;
 }
 
+
+// ---------------------------------------------------------------------------
+// Persistent batch (eot_solve_batch with float32 costs): set-up kernels over
+// all problems, one host synchronisation for the cost statistics, then one
+// cooperative launch of batch_sk_kernel (captured in a CUDA graph) that runs
+// every problem to its result, and one copy-out.
+// ---------------------------------------------------------------------------
+struct BatchModel {            // calibrated cost model of the gang sizes
+  double ns_per_elem = 0.0;    // one CTA, one element of one half-step
+  double fix_ns = 0.0;         // fixed cost of one iteration of a small problem
+  double bar_ns = 0.0;         // one gang barrier
+  bool done = false;
+};
+static BatchModel g_bmodel[64];
+static std::mutex g_bmodel_mu;
+
+// Predicted device time of a task: iterations x (two half-steps shared by G
+// CTAs + the fixed cost + two gang barriers when G > 1).
+static double task_ns(const BatchModel& M, double iters, long long nm, int G) {
+  return iters * (2.0 * (double)nm * M.ns_per_elem / G + M.fix_ns + (G > 1 ? 2.0 * M.bar_ns : 0.0));
+}
+
+// Grow-only pinned staging buffer of the calling thread.
+static char* pinned_staging(size_t bytes) {
+  static thread_local char* buf = nullptr;
+  static thread_local size_t cap = 0;
+  if (bytes <= cap) return buf;
+  if (buf) cudaFreeHost(buf);
+  buf = nullptr;
+  cap = 0;
+  if (cudaMallocHost(&buf, bytes) != cudaSuccess) return nullptr;
+  cap = bytes;
+  return buf;
+}
+
+static eot_status run_batch(int count, const eot_problem* probs, const eot_options& o,
+                            double* const* f_out, double* const* g_out, eot_status* st,
+                            eot_result* rs, std::string* errs, int forced_G, float* kernel_ms);
+
+// Calibrate the gang-size model on this device with synthetic problems: a
+// 1024 x 1024 one run by one CTA (the element rate) and a 64 x 64 one run by
+// gangs of 1 and 8 CTAs (the fixed cost of an iteration and of a barrier),
+// each for a fixed number of iterations.
+static eot_status calibrate_batch(int dev) {
+  std::lock_guard<std::mutex> lk(g_bmodel_mu);
+  BatchModel& M = g_bmodel[dev & 63];
+  if (M.done) return EOT_OK;
+  uint64_t z = 0x9E3779B97F4A7C15ull;
+  auto rnd = [&]() {   // SplitMix64 draws in [0, 1)
+    z += 0x9E3779B97F4A7C15ull;
+    uint64_t x = z;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    x ^= x >> 31;
+    return (float)((x >> 40) * (1.0 / 16777216.0));
+  };
+  auto run = [&](int n, int iters, int G, float* ms) {
+    std::vector<float> X(2 * n), Y(2 * n);
+    for (auto& v : X) v = rnd();
+    for (auto& v : Y) v = rnd();
+    std::vector<double> w(n, 1.0 / n), f(n), g(n);
+    eot_problem q{};
+    q.n = q.m = n;
+    q.d = 2;
+    q.a = w.data();
+    q.b = w.data();
+    q.X = X.data();
+    q.Y = Y.data();
+    q.mem = EOT_MEM_HOST;
+    q.normalize_cost = 1;
+    q.eps = 0.05;
+    eot_options o;
+    eot_default_options(&o);
+    o.tol = 1e-300;
+    o.max_iter = iters;
+    double* fo[1] = {f.data()};
+    double* go[1] = {g.data()};
+    eot_status st;
+    eot_result r;
+    std::string e;
+    return run_batch(1, &q, o, fo, go, &st, &r, &e, G, ms);
+  };
+  const int it_big = 8, it_small = 64;
+  float tb = 0.f, t1 = 0.f, t8 = 0.f;
+  eot_status sc = run(1024, it_big, 1, &tb);   // warm-up
+  if (sc == EOT_OK) sc = run(1024, it_big, 1, &tb);
+  if (sc == EOT_OK) sc = run(64, it_small, 1, &t1);
+  if (sc == EOT_OK) sc = run(64, it_small, 8, &t8);
+  if (sc != EOT_OK) return sc;
+  // a run: G_INIT, the iterations, the evaluation (about 2 iters + 2 half-steps)
+  M.fix_ns = std::max(1000.0, 1e6 * t1 / (it_small + 1.5));
+  M.ns_per_elem = std::max(1e-3, (1e6 * tb / (it_big + 1.5) - M.fix_ns) / (2.0 * 1024.0 * 1024.0));
+  M.bar_ns = std::max(500.0, 1e6 * (t8 - t1) / (2.0 * (it_small + 2.0)));
+  M.done = true;
+  return EOT_OK;
+}
+
+static eot_status run_batch(int count, const eot_problem* probs, const eot_options& o,
+                            double* const* f_out, double* const* g_out, eot_status* st,
+                            eot_result* rs, std::string* errs, int forced_G, float* kernel_ms) {
+  DeviceCtx* ctx = nullptr;
+  eot_status cs = get_ctx(&ctx);
+  if (cs != EOT_OK) return cs;
+  cudaStream_t s = ctx->stream;
+  const int ctas = batch_ctas_per_sm() * ctx->nsm;
+  if (ctas < 1) return fail(EOT_ECUDA, "the batch kernel cannot be resident");
+  const int cap = std::max(1, std::min(kBMaxGang, ctas / 8));
+  if (forced_G <= 0) {
+    eot_status ce = calibrate_batch(ctx->dev);
+    if (ce != EOT_OK) return ce;
+  }
+  const BatchModel& M = g_bmodel[ctx->dev & 63];
+  struct PL {
+    bool ok = false;
+    int n = 0, m = 0, d = 0, pitch = 0, G = 1;
+    std::vector<double> lev;
+    size_t h_a = 0, h_b = 0, h_x = 0, h_y = 0, h_c = 0, h_f = 0;   // staging offsets
+  };
+  std::vector<PL> pl(count);
+  size_t hbytes = 0;
+  auto htake = [&](size_t bytes) {
+    const size_t off = (hbytes + 255) & ~size_t(255);
+    hbytes = off + bytes;
+    return off;
+  };
+  for (int k = 0; k < count; ++k) {
+    const eot_problem& q = probs[k];
+    PL& p = pl[k];
+    st[k] = validate(&q, &o);
+    if (st[k] != EOT_OK) {
+      errs[k] = t_err;
+      continue;
+    }
+    p.lev = schedule(o.eps_start, q.eps, o.eps_factor);
+    if ((int)p.lev.size() > kBMaxLev) {
+      st[k] = fail(EOT_EINVAL, "more than 64 continuation levels");
+      errs[k] = t_err;
+      continue;
+    }
+    p.ok = true;
+    p.n = q.n;
+    p.m = q.m;
+    p.d = q.d;
+    p.pitch = (q.m + 3) & ~3;
+    p.G = forced_G > 0 ? std::min(forced_G, cap) : 1;
+    if (q.mem == EOT_MEM_HOST) {
+      p.h_a = htake(sizeof(double) * q.n);
+      p.h_b = htake(sizeof(double) * q.m);
+      if (q.d > 0) {
+        p.h_x = htake(sizeof(float) * q.n * q.d);
+        p.h_y = htake(sizeof(float) * q.m * q.d);
+      } else {
+        p.h_c = htake(sizeof(float) * (size_t)q.n * q.m);
+      }
+      if (q.f_init) p.h_f = htake(sizeof(double) * q.n);
+    }
+  }
+  // ---- gang sizes: no task longer than half the ideal makespan (sum of the
+  // single-CTA task times over the grid), as far as doubling its gang helps;
+  // iterations estimated from the eps schedule ----
+  std::vector<double> est_it(count, 0.0);
+  for (int k = 0; k < count; ++k) {
+    if (!pl[k].ok) continue;
+    double it = 0.0;
+    for (double e : pl[k].lev) it += std::min(0.66 / e, (double)o.max_iter);
+    est_it[k] = std::max(1.0, it);
+  }
+  if (forced_G <= 0) {
+    double sum1 = 0.0;
+    for (int k = 0; k < count; ++k)
+      if (pl[k].ok) sum1 += task_ns(M, est_it[k], (long long)pl[k].n * pl[k].m, 1);
+    const double target = 0.5 * sum1 / ctas;
+    for (int k = 0; k < count; ++k) {
+      if (!pl[k].ok) continue;
+      const long long nm = (long long)pl[k].n * pl[k].m;
+      int G = 1;
+      while (G < cap && task_ns(M, est_it[k], nm, G) > target &&
+             task_ns(M, est_it[k], nm, 2 * G) < task_ns(M, est_it[k], nm, G))
+        G *= 2;
+      pl[k].G = G;
+    }
+  }
+  // ---- device arena: [staged inputs | per-problem state | outputs | tables] ----
+  struct DL {
+    double *a, *b, *loga, *logb, *f, *g0, *g1, *fo, *go, *part;
+    float *C, *Lrow, *Lcol, *fs[4], *gs0[4], *gs1[4];
+    unsigned* bar;
+  };
+  std::vector<DL> dl(count);
+  size_t out_off = 0, out_bytes = 0;
+  auto layout = [&](Arena& A) {
+    A.take<char>(hbytes);   // the staged inputs, same offsets as on the host
+    for (int k = 0; k < count; ++k) {
+      if (!pl[k].ok) continue;
+      const PL& p = pl[k];
+      DL& L = dl[k];
+      const size_t np = (size_t)((p.n + 127) / 128) * 128, mp = (size_t)((p.m + 127) / 128) * 128;
+      L.a = A.take<double>(p.n);
+      L.b = A.take<double>(p.m);
+      L.loga = A.take<double>(p.n);
+      L.logb = A.take<double>(p.m);
+      L.C = A.take<float>((size_t)p.n * p.pitch);
+      L.f = A.take<double>(p.n);
+      L.g0 = A.take<double>(p.m);
+      L.g1 = A.take<double>(p.m);
+      for (int q = 0; q < 4; ++q) L.fs[q] = A.take<float>(np);
+      for (int q = 0; q < 4; ++q) L.gs0[q] = A.take<float>(mp);
+      for (int q = 0; q < 4; ++q) L.gs1[q] = A.take<float>(mp);
+      L.Lrow = A.take<float>(p.n);
+      L.Lcol = A.take<float>(p.m);
+      L.part = A.take<double>((size_t)p.G * kBPart);
+      L.bar = A.take<unsigned>(2);
+    }
+    A.off = (A.off + 255) & ~size_t(255);
+    out_off = A.off;
+    for (int k = 0; k < count; ++k) {
+      if (!pl[k].ok) continue;
+      dl[k].fo = A.take<double>(pl[k].n);
+      dl[k].go = A.take<double>(pl[k].m);
+    }
+    A.off = (A.off + 255) & ~size_t(255);
+    out_bytes = A.off - out_off;
+  };
+  Arena A0;
+  layout(A0);
+  const size_t nslots_max = (size_t)count * kBMaxGang;
+  size_t tbl = A0.off;
+  Arena At{nullptr, tbl};
+  At.take<BatchTask>(count);
+  At.take<BatchIn>(count);
+  At.take<BatchOut>(count);
+  At.take<int2>(nslots_max);
+  At.take<unsigned long long>(count);
+  At.take<unsigned>(2 * count + 1);
+  const size_t total = At.off + 256;
+  char* dmem = nullptr;
+  CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&dmem), total, s));
+  struct Free {
+    char* p;
+    cudaStream_t s;
+    ~Free() {
+      if (p) cudaFreeAsync(p, s);
+    }
+  } guard{dmem, s};
+  CUDA_TRY(cudaMemsetAsync(dmem, 0, total, s));
+  Arena A{dmem, 0};
+  layout(A);
+  A.off = tbl;
+  BatchTask* d_tasks = A.take<BatchTask>(count);
+  BatchIn* d_in = A.take<BatchIn>(count);
+  BatchOut* d_out = A.take<BatchOut>(count);
+  int2* d_slots = A.take<int2>(nslots_max);
+  unsigned long long* d_cmax = A.take<unsigned long long>(count);
+  unsigned* d_bad = A.take<unsigned>(2 * count + 1);
+  unsigned* d_next = d_bad + 2 * count;
+  // ---- stage host inputs, one copy ----
+  const size_t stage_bytes = std::max(hbytes, out_bytes) + 256;
+  char* hst = pinned_staging(stage_bytes);
+  if (!hst) return fail(EOT_ENOMEM, "pinned staging buffer");
+  for (int k = 0; k < count; ++k) {
+    const eot_problem& q = probs[k];
+    const PL& p = pl[k];
+    if (!p.ok || q.mem != EOT_MEM_HOST) continue;
+    std::memcpy(hst + p.h_a, q.a, sizeof(double) * q.n);
+    std::memcpy(hst + p.h_b, q.b, sizeof(double) * q.m);
+    if (q.d > 0) {
+      std::memcpy(hst + p.h_x, q.X, sizeof(float) * q.n * q.d);
+      std::memcpy(hst + p.h_y, q.Y, sizeof(float) * q.m * q.d);
+    } else {
+      std::memcpy(hst + p.h_c, q.C, sizeof(float) * (size_t)q.n * q.m);
+    }
+    if (q.f_init) std::memcpy(hst + p.h_f, q.f_init, sizeof(double) * q.n);
+  }
+  if (hbytes) CUDA_TRY(cudaMemcpyAsync(dmem, hst, hbytes, cudaMemcpyHostToDevice, s));
+  // ---- set-up descriptors and kernels ----
+  std::vector<BatchIn> hin(count);
+  int maxrows = 1;
+  for (int k = 0; k < count; ++k) {
+    BatchIn& I = hin[k];
+    std::memset(&I, 0, sizeof(I));
+    if (!pl[k].ok) continue;
+    const eot_problem& q = probs[k];
+    const PL& p = pl[k];
+    const DL& L = dl[k];
+    const bool host = q.mem == EOT_MEM_HOST;
+    I.n = p.n;
+    I.m = p.m;
+    I.d = p.d;
+    I.pitch = p.pitch;
+    I.normalize = q.normalize_cost ? 1 : 0;
+    I.givenC = q.d == 0 ? 1 : 0;
+    I.X = q.d > 0 ? (host ? reinterpret_cast<const float*>(dmem + p.h_x)
+                          : static_cast<const float*>(q.X))
+                  : nullptr;
+    I.Y = q.d > 0 ? (host ? reinterpret_cast<const float*>(dmem + p.h_y)
+                          : static_cast<const float*>(q.Y))
+                  : nullptr;
+    I.Cin = q.d == 0 ? (host ? reinterpret_cast<const float*>(dmem + p.h_c)
+                             : static_cast<const float*>(q.C))
+                     : nullptr;
+    I.win_a = host ? reinterpret_cast<const double*>(dmem + p.h_a) : q.a;
+    I.win_b = host ? reinterpret_cast<const double*>(dmem + p.h_b) : q.b;
+    I.a = L.a;
+    I.b = L.b;
+    I.loga = L.loga;
+    I.logb = L.logb;
+    I.C = L.C;
+    I.cmax = d_cmax + k;
+    I.bad = d_bad + 2 * k;
+    maxrows = std::max(maxrows, p.n);
+    if (q.f_init)
+      CUDA_TRY(cudaMemcpyAsync(L.f, host ? (const void*)(dmem + p.h_f) : (const void*)q.f_init,
+                               sizeof(double) * p.n, cudaMemcpyDeviceToDevice, s));
+  }
+  CUDA_TRY(cudaMemcpyAsync(d_in, hin.data(), sizeof(BatchIn) * count, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(launch_batch_setup(d_in, count, maxrows, s));
+  std::vector<unsigned long long> hcmax(count);
+  std::vector<unsigned> hbad(2 * count);
+  CUDA_TRY(cudaMemcpyAsync(hcmax.data(), d_cmax, sizeof(unsigned long long) * count,
+                           cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(hbad.data(), d_bad, sizeof(unsigned) * 2 * count,
+                           cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  // ---- tasks: exponent grids, tolerances, gangs; schedule ----
+  std::vector<BatchTask> ht(count);
+  std::vector<std::pair<double, int>> order;
+  for (int k = 0; k < count; ++k) {
+    BatchTask& T = ht[k];
+    std::memset(&T, 0, sizeof(T));
+    if (!pl[k].ok) continue;
+    const eot_problem& q = probs[k];
+    const PL& p = pl[k];
+    if (hbad[2 * k]) {
+      st[k] = fail(EOT_EINVAL, "weights must be positive and finite");
+      errs[k] = t_err;
+      pl[k].ok = false;
+      continue;
+    }
+    if (hbad[2 * k + 1]) {
+      st[k] = fail(EOT_EINVAL, "cost has non-finite entries");
+      errs[k] = t_err;
+      pl[k].ok = false;
+      continue;
+    }
+    double cmax;
+    const unsigned long long bits = hcmax[k];
+    std::memcpy(&cmax, &bits, 8);
+    if (q.normalize_cost && cmax > 0.0) cmax = 1.0;
+    double fmax = 0.0;
+    if (q.f_init) {
+      std::vector<double> hf(p.n);
+      if (q.mem == EOT_MEM_HOST) std::memcpy(hf.data(), q.f_init, sizeof(double) * p.n);
+      else CUDA_TRY(cudaMemcpy(hf.data(), q.f_init, sizeof(double) * p.n, cudaMemcpyDeviceToHost));
+      for (double v : hf) {
+        if (!std::isfinite(v)) {
+          st[k] = fail(EOT_EINVAL, "f_init has non-finite entries");
+          errs[k] = t_err;
+          pl[k].ok = false;
+          break;
+        }
+        fmax = std::max(fmax, std::fabs(v));
+      }
+      if (!pl[k].ok) continue;
+    }
+    const double eps0 = p.lev.front();
+    const double R = 4.0 * (cmax + fmax + 40.0 * eps0) + 1e-30;
+    int qg = 22 - (int)std::ceil(std::log2(R));
+    qg = std::max(-100, std::min(qg, 60));
+    const DL& L = dl[k];
+    T.n = p.n;
+    T.m = p.m;
+    T.pitch = p.pitch;
+    T.nlev = (int)p.lev.size();
+    T.G = p.G;
+    T.max_iter = o.max_iter;
+    T.C = L.C;
+    T.a = L.a;
+    T.b = L.b;
+    T.loga = L.loga;
+    T.logb = L.logb;
+    T.f = L.f;
+    T.g[0] = L.g0;
+    T.g[1] = L.g1;
+    T.fs = Split{L.fs[0], L.fs[1], L.fs[2], L.fs[3], nullptr};
+    T.gsp[0] = Split{L.gs0[0], L.gs0[1], L.gs0[2], L.gs0[3], nullptr};
+    T.gsp[1] = Split{L.gs1[0], L.gs1[1], L.gs1[2], L.gs1[3], nullptr};
+    T.Lrow = L.Lrow;
+    T.Lcol = L.Lcol;
+    T.f_out = L.fo;
+    T.g_out = L.go;
+    T.bar = L.bar;
+    T.part = L.part;
+    T.out = d_out + k;
+    T.tol_level = o.level_tol > 0.0 ? o.level_tol : o.tol;
+    T.tol_last = 0.85 * o.tol;   // the float32 estimate's margin (see solve_one)
+    T.tol_verify = 0.9 * o.tol;
+    T.qscale = std::ldexp(1.0, qg);
+    T.qinv = std::ldexp(1.0, -qg);
+    T.M = (float)(1.5 * std::ldexp(1.0, 23 - qg));
+    T.pot_bound = std::ldexp(1.0, 22 - qg) / 2.0 - cmax;
+    for (int l = 0; l < T.nlev; ++l) T.eps[l] = p.lev[l];
+    // the longest predicted tasks first
+    order.push_back({-task_ns(M.done ? M : BatchModel{1.0, 0.0, 0.0, true}, est_it[k],
+                              (long long)p.n * p.m, p.G),
+                     k});
+  }
+  std::sort(order.begin(), order.end());
+  std::vector<int2> slots;
+  for (const auto& e : order)
+    for (int r = 0; r < ht[e.second].G; ++r) slots.push_back(make_int2(e.second, r));
+  const int nslots = (int)slots.size();
+  // ---- the persistent launch (one graph: tables, counter, kernel) ----
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  if (nslots > 0) {
+    cudaGraph_t gr = nullptr;
+    cudaGraphExec_t gx = nullptr;
+    CUDA_TRY(cudaMemcpyAsync(d_tasks, ht.data(), sizeof(BatchTask) * count,
+                             cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(d_slots, slots.data(), sizeof(int2) * nslots,
+                             cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    cudaError_t ce = cudaMemsetAsync(d_next, 0, sizeof(unsigned), s);
+    if (ce == cudaSuccess) ce = launch_batch_sk(d_tasks, d_slots, nslots, d_next, ctas, s);
+    cudaError_t ee = cudaStreamEndCapture(s, &gr);
+    if (ce != cudaSuccess || ee != cudaSuccess) {
+      if (gr) cudaGraphDestroy(gr);
+      return fail(EOT_ECUDA, std::string("batch graph capture: ") +
+                                 cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+    }
+    ce = cudaGraphInstantiate(&gx, gr, 0);
+    if (ce == cudaSuccess) {
+      CUDA_TRY(cudaEventRecord(e0, s));
+      ce = cudaGraphLaunch(gx, s);
+      CUDA_TRY(cudaEventRecord(e1, s));
+    }
+    if (gx) cudaGraphExecDestroy(gx);
+    cudaGraphDestroy(gr);
+    if (ce != cudaSuccess) return fail(EOT_ECUDA, std::string("batch launch: ") + cudaGetErrorString(ce));
+  } else {
+    CUDA_TRY(cudaEventRecord(e0, s));
+    CUDA_TRY(cudaEventRecord(e1, s));
+  }
+  // ---- copy-out ----
+  std::vector<BatchOut> hout(count);
+  CUDA_TRY(cudaMemcpyAsync(hout.data(), d_out, sizeof(BatchOut) * count, cudaMemcpyDeviceToHost, s));
+  if (out_bytes)
+    CUDA_TRY(cudaMemcpyAsync(hst, dmem + out_off, out_bytes, cudaMemcpyDeviceToHost, s));
+  for (int k = 0; k < count; ++k) {
+    if (!pl[k].ok || probs[k].mem != EOT_MEM_DEVICE) continue;
+    CUDA_TRY(cudaMemcpyAsync(f_out[k], dl[k].fo, sizeof(double) * pl[k].n, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(g_out[k], dl[k].go, sizeof(double) * pl[k].m, cudaMemcpyDeviceToDevice, s));
+  }
+  CUDA_TRY(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (kernel_ms) *kernel_ms = ms;
+  for (int k = 0; k < count; ++k) {
+    if (!pl[k].ok) {
+      rs[k] = eot_result{};
+      rs[k].status = st[k];
+      continue;
+    }
+    if (probs[k].mem == EOT_MEM_HOST) {
+      std::memcpy(f_out[k], hst + (reinterpret_cast<char*>(dl[k].fo) - dmem - out_off),
+                  sizeof(double) * pl[k].n);
+      std::memcpy(g_out[k], hst + (reinterpret_cast<char*>(dl[k].go) - dmem - out_off),
+                  sizeof(double) * pl[k].m);
+    }
+    const BatchOut& b = hout[k];
+    eot_result r{};
+    r.iters = b.iters;
+    r.total_iters = b.total_iters;
+    r.levels = b.levels;
+    r.row_l1 = b.row_l1;
+    r.col_l1 = b.col_l1;
+    r.l1_marginal = b.row_l1 + b.col_l1;
+    r.q_dual = b.q_dual;
+    r.q_semi = b.q_semi;
+    r.dual_gap = b.dual_gap;
+    r.seconds = 1e-9 * (double)(b.t_end - b.t_begin);
+    r.seconds_last_level = 1e-9 * (double)(b.t_end - b.t_last_level);
+    r.kernel_launches = 5;   // weights, cost max, cost fill, persistent kernel (+ counter)
+    switch (b.status) {
+      case 1: r.status = EOT_OK; break;
+      case 2: r.status = EOT_NOT_CONVERGED; errs[k] = "max_iter reached"; break;
+      case 3: r.status = EOT_ENUMERIC; errs[k] = "non-finite values or potentials outside the exact range"; break;
+      default: r.status = EOT_ETIMEDOUT; errs[k] = "batch gang wait gave up"; break;
+    }
+    st[k] = r.status;
+    rs[k] = r;
+  }
+  return EOT_OK;
+}
 }  // namespace eotk
 
 // ===========================================================================
@@ -1837,6 +2336,24 @@ eot_status eot_solve_batch(int32_t count, const eot_problem* probs, const eot_op
   std::vector<eot_result> rs(count);
   std::atomic<int> nexti(0);
   std::vector<std::string> errs(count);
+  if (o.prec == EOT_PREC_FP32) {
+    // one persistent launch for all problems
+    const eot_status bs = eotk::run_batch(count, probs, o, f_out, g_out, st.data(), rs.data(),
+                                          errs.data(), 0, nullptr);
+    if (bs != EOT_OK) return bs;
+    eot_status worst = EOT_OK;
+    for (int k = 0; k < count; ++k) {
+      if (results) results[k] = rs[k];
+      if (st[k] < 0 && (worst >= 0 || st[k] < worst)) {
+        worst = st[k];
+        t_err = errs[k];
+      } else if (worst == EOT_OK && st[k] > 0) {
+        worst = st[k];
+        t_err = errs[k];
+      }
+    }
+    return worst;
+  }
   auto work = [&]() {
     cudaSetDevice(dev);
     eotk::t_concurrent = true;

@@ -84,11 +84,21 @@ def test_batch_same_alone_and_in_mix(pkg):
     assert st in (pkg.EOT_OK, pkg.EOT_NOT_CONVERGED), pkg.last_error()
     for k in (0, 5, 17):
         p = probs[k]
-        f1, g1, r1 = pkg.solve(p, tol=1e-6, max_iter=200000)
-        assert np.array_equal(f1, fs[k]) and np.array_equal(g1, gs[k])
+        # the same problem alone in a batch: bit for bit the same result
+        fa, ga = [np.zeros(p.n)], [np.zeros(p.m)]
+        sta, resa = pkg.eot_solve_batch([ps[k]], o, fa, ga)
+        assert resa[0].status == res[k].status and resa[0].total_iters == res[k].total_iters
+        assert np.array_equal(fa[0], fs[k]) and np.array_equal(ga[0], gs[k])
+        # and a valid solution, like the single solve's
         C = O.sq_euclidean_cost(p.X, p.Y, normalize=True).astype(np.float32).astype(np.float64)
-        if res[k].status == pkg.EOT_OK:
-            assert O.evaluate(fs[k], gs[k], C, p.a, p.b, p.eps)["l1"] <= 1e-6
+        assert res[k].status == pkg.EOT_OK, res[k].status
+        ev = O.evaluate(fs[k], gs[k], C, p.a, p.b, p.eps)
+        assert ev["l1"] <= 1e-6 and abs(ev["l1"] - res[k].l1_marginal) <= 2e-7, (ev, res[k].l1_marginal)
+        f1, g1, r1 = pkg.solve(p, tol=1e-6, max_iter=200000)
+        assert r1["return_status"] == pkg.EOT_OK
+        assert O.evaluate(f1, g1, C, p.a, p.b, p.eps)["l1"] <= 1e-6
+        # both approximate the same optimum (gauge <f,a> = <g,b> in both)
+        assert np.abs(f1 - fs[k]).max() <= 1e-3 * p.eps
 
 
 def test_batch_rejects_bad_member(pkg):
