@@ -91,6 +91,9 @@ __global__ void eig_ctl_kernel(State*, const double*, const int*);
 __global__ void level_setup_kernel(Prob*, double, float, double, int, int);
 __global__ void eig_setup_kernel(State*, double, int, int);
 __global__ void cost_max_kernel(int, int, int, const float*, const float*, unsigned long long*);
+cudaError_t launch_cost_points(int n, int m, int d, const float* X, const float* Y, bool want_max,
+                               int normalize, float* C, unsigned* fmax_bits,
+                               unsigned long long* cmax64, cudaStream_t s);
 __global__ void cost_fill_kernel(int, int, int, const float*, const float*,
                                  const unsigned long long*, int, float*);
 __global__ void cost_scale_kernel(size_t, const float*, double, float*);
@@ -380,7 +383,7 @@ struct Solver {
     f_out = A.take<double>(n);
     g_out = A.take<double>(m);
     scores = A.take<double>(16);
-    stats = A.take<unsigned>(4);
+    stats = A.take<unsigned>(8);   // [4] float32 bits of the approximate max of C
     cmax64 = A.take<unsigned long long>(1);
     X = d > 0 ? A.take<float>((size_t)n * d) : nullptr;
     Y = d > 0 ? A.take<float>((size_t)m * d) : nullptr;
@@ -959,7 +962,7 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
     CUDA_TRY(cudaMemcpyAsync(S->Y, pr->Y, (size_t)m * d * sizeof(float), kin, s));
     double scale = 1.0;
     if (pr->normalize_cost) {
-      cost_max_kernel<<<gb, 256, 0, s>>>(n, m, d, S->X, S->Y, S->cmax64);
+      CUDA_TRY(launch_cost_points(n, m, d, S->X, S->Y, true, 0, nullptr, S->stats + 4, S->cmax64, s));
       unsigned long long bits = 0;
       CUDA_TRY(cudaMemcpyAsync(&bits, S->cmax64, sizeof(bits), cudaMemcpyDeviceToHost, s));
       CUDA_TRY(cudaStreamSynchronize(s));
@@ -978,14 +981,14 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   } else if (d > 0) {
     CUDA_TRY(cudaMemcpyAsync(S->X, pr->X, (size_t)n * d * sizeof(float), kin, s));
     CUDA_TRY(cudaMemcpyAsync(S->Y, pr->Y, (size_t)m * d * sizeof(float), kin, s));
-    if (pr->normalize_cost) cost_max_kernel<<<gb, 256, 0, s>>>(n, m, d, S->X, S->Y, S->cmax64);
+    if (pr->normalize_cost && f64) cost_max_kernel<<<gb, 256, 0, s>>>(n, m, d, S->X, S->Y, S->cmax64);
     if (f64) {
       cost_fill64_kernel<<<gb, 256, 0, s>>>(n, m, d, S->X, S->Y, S->cmax64, pr->normalize_cost,
                                             C64);
       cost64_finish_kernel<<<gb, 256, 0, s>>>(nm, C64, S->cmax64, 0, S->Cbuf);
     } else {
-      cost_fill_kernel<<<gb, 256, 0, s>>>(n, m, d, S->X, S->Y, S->cmax64, pr->normalize_cost,
-                                          S->Cbuf);
+      CUDA_TRY(launch_cost_points(n, m, d, S->X, S->Y, pr->normalize_cost != 0,
+                                  pr->normalize_cost, S->Cbuf, S->stats + 4, S->cmax64, s));
     }
     Cdev = S->Cbuf;
   } else if (f64) {
@@ -2061,13 +2064,11 @@ eot_status eot_cost(int32_t n, int32_t m, int32_t d, const float* X, const float
   eot_status cs = get_ctx(&ctx);
   if (cs != EOT_OK) return cs;
   cudaStream_t s = stream ? reinterpret_cast<cudaStream_t>(stream) : ctx->stream;
-  unsigned long long* tmp = nullptr;
-  CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&tmp), sizeof(unsigned long long), s));
-  CUDA_TRY(cudaMemsetAsync(tmp, 0, sizeof(unsigned long long), s));
-  const size_t nm = (size_t)n * m;
-  const int gb = std::min<long long>(((long long)nm + 255) / 256, 8LL * ctx->nsm);
-  cost_max_kernel<<<gb, 256, 0, s>>>(n, m, d, X, Y, tmp);
-  cost_fill_kernel<<<gb, 256, 0, s>>>(n, m, d, X, Y, tmp, normalize, C);
+  unsigned long long* tmp = nullptr;   // [0] float64 max, [1] float32 approximate max
+  CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&tmp), 2 * sizeof(unsigned long long), s));
+  CUDA_TRY(cudaMemsetAsync(tmp, 0, 2 * sizeof(unsigned long long), s));
+  CUDA_TRY(launch_cost_points(n, m, d, X, Y, true, normalize, C,
+                              reinterpret_cast<unsigned*>(tmp + 1), tmp, s));
   if (cmax_out)
     CUDA_TRY(cudaMemcpyAsync(cmax_out, tmp, sizeof(double), cudaMemcpyDeviceToDevice, s));
   CUDA_TRY(cudaFreeAsync(tmp, s));

@@ -7,6 +7,7 @@
 //  * final_eval: the scores of the returned potentials (marginal errors, Eq.
 //    def_Q value, duality gap) and the gauge normalisation <f,a> = <g,b>
 //    (Sec. 2: the dual is invariant under (f, g) + c (1, -1)).
+#include <algorithm>
 #include "eot_device.cuh"
 #include "eot_internal.h"
 
@@ -50,6 +51,126 @@ __global__ void cost_fill_kernel(int n, int m, int d, const float* __restrict__ 
     if (normalize && cmax > 0.0) v = __ddiv_rn(v, cmax);
     C[e] = __double2float_rn(v);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Tiled cost construction from points (rows of a tile staged in shared
+// memory, threads over columns: no per-element index division).
+// ---------------------------------------------------------------------------
+constexpr int kCostRows = 32;
+
+// float32 approximation of ||x_i - y_j||^2: relative error below
+// (d + 3) 2^-24 (every term is non-negative).
+__device__ __forceinline__ float sqdist_f(const float* __restrict__ x, const float* __restrict__ y,
+                                          int d) {
+  float s = 0.f;
+  for (int k = 0; k < d; ++k) {
+    const float t = x[k] - y[k];
+    s = __fmaf_rn(t, t, s);
+  }
+  return s;
+}
+
+// Pass A of the exact maximum: max over the float32 approximations
+// (non-negative floats compare like their bit patterns).
+__global__ void __launch_bounds__(256) cost_maxf_kernel(int n, int m, int d,
+                                                        const float* __restrict__ X,
+                                                        const float* __restrict__ Y,
+                                                        unsigned* __restrict__ fmax_bits) {
+  extern __shared__ float sx[];   // [kCostRows][d]
+  const int i0 = blockIdx.x * kCostRows, nr = min(kCostRows, n - i0);
+  for (int e = threadIdx.x; e < nr * d; e += blockDim.x) sx[e] = X[(size_t)i0 * d + e];
+  __syncthreads();
+  float mx = 0.f;
+  for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < m; j += gridDim.y * blockDim.x) {
+    const float* y = Y + (size_t)j * d;
+    for (int r = 0; r < nr; ++r) mx = fmaxf(mx, sqdist_f(sx + r * d, y, d));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(fmax_bits, __float_as_uint(mx));
+}
+
+// Pass B: the exact float64 distance of every candidate pair, those whose
+// approximation lies within twice the approximation's error of the
+// approximate maximum (the exact maximum is among them).
+__global__ void __launch_bounds__(256) cost_maxx_kernel(int n, int m, int d,
+                                                        const float* __restrict__ X,
+                                                        const float* __restrict__ Y,
+                                                        const unsigned* __restrict__ fmax_bits,
+                                                        unsigned long long* __restrict__ out) {
+  extern __shared__ float sx[];   // [kCostRows][d]
+  const int i0 = blockIdx.x * kCostRows, nr = min(kCostRows, n - i0);
+  for (int e = threadIdx.x; e < nr * d; e += blockDim.x) sx[e] = X[(size_t)i0 * d + e];
+  __syncthreads();
+  const float fm = __uint_as_float(*fmax_bits);
+  const float thr = fm * (1.f - 2.f * (float)(d + 4) * 1.1920929e-7f);
+  double mx = 0.0;
+  for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < m; j += gridDim.y * blockDim.x) {
+    const float* y = Y + (size_t)j * d;
+    for (int r = 0; r < nr; ++r)
+      if (sqdist_f(sx + r * d, y, d) >= thr) mx = fmax(mx, sqdist(sx + r * d, y, d));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx > 0.0)
+    atomicMax(out, (unsigned long long)__double_as_longlong(mx));
+}
+
+// C_ij in float64, optionally divided by the maximum, rounded once to float32.
+// The quotient is formed from the correctly rounded reciprocal with one
+// residual correction (Markstein's theorem: q = RN(a r), e = a - b q exact by
+// FMA, RN(q + e r) is the correctly rounded a / b), which replaces a full
+// float64 division per element.
+__global__ void __launch_bounds__(256) cost_fill2_kernel(int n, int m, int d,
+                                                         const float* __restrict__ X,
+                                                         const float* __restrict__ Y,
+                                                         const unsigned long long* __restrict__ cmax_bits,
+                                                         int normalize, float* __restrict__ C) {
+  extern __shared__ float sx[];   // [kCostRows][d]
+  const int i0 = blockIdx.x * kCostRows, nr = min(kCostRows, n - i0);
+  for (int e = threadIdx.x; e < nr * d; e += blockDim.x) sx[e] = X[(size_t)i0 * d + e];
+  __syncthreads();
+  const double cmax = __longlong_as_double((long long)*cmax_bits);
+  const bool norm = normalize && cmax > 0.0;
+  const double rc = norm ? 1.0 / cmax : 1.0;
+  for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < m; j += gridDim.y * blockDim.x) {
+    const float* y = Y + (size_t)j * d;
+    for (int r = 0; r < nr; ++r) {
+      double v = sqdist(sx + r * d, y, d);
+      if (norm) {
+        const double q = v * rc;
+        const double e = fma(-q, cmax, v);
+        v = fma(e, rc, q);
+      }
+      C[(size_t)(i0 + r) * m + j] = __double2float_rn(v);
+    }
+  }
+}
+
+// Cost from points: the exact maximum (when wanted; into *cmax64, which the
+// caller zeroed) and the cost (when C is given).  Wide points (more than 384
+// coordinates) take the untiled kernels.
+cudaError_t launch_cost_points(int n, int m, int d, const float* X, const float* Y, bool want_max,
+                               int normalize, float* C, unsigned* fmax_bits,
+                               unsigned long long* cmax64, cudaStream_t s) {
+  const size_t sm = (size_t)kCostRows * d * sizeof(float);
+  if (sm > 48 * 1024) {
+    const size_t nm = (size_t)n * m;
+    const int gb = (int)std::min<size_t>((nm + 255) / 256, 2048);
+    if (want_max) cost_max_kernel<<<gb, 256, 0, s>>>(n, m, d, X, Y, cmax64);
+    if (C) cost_fill_kernel<<<gb, 256, 0, s>>>(n, m, d, X, Y, cmax64, normalize, C);
+    return cudaGetLastError();
+  }
+  const dim3 grid((n + kCostRows - 1) / kCostRows, std::min(16, (m + 255) / 256));
+  if (want_max) {
+    cudaError_t e = cudaMemsetAsync(fmax_bits, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    cost_maxf_kernel<<<grid, 256, sm, s>>>(n, m, d, X, Y, fmax_bits);
+    cost_maxx_kernel<<<grid, 256, sm, s>>>(n, m, d, X, Y, fmax_bits, cmax64);
+  }
+  if (C) cost_fill2_kernel<<<grid, 256, sm, s>>>(n, m, d, X, Y, cmax64, normalize, C);
+  return cudaGetLastError();
 }
 
 // Scale a given cost by 1 / max (normalisation of a user-supplied C).

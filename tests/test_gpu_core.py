@@ -156,11 +156,19 @@ def test_kapply_parity(pkg, n, m, k):
     assert np.abs(outr.cpu().numpy() - er).max() <= 2e-5 * sr
 
 
-@pytest.mark.parametrize("n,m,d,norm", [(7, 9, 2, True), (300, 257, 3, True), (64, 100, 64, False)])
+@pytest.mark.parametrize("n,m,d,norm", [(7, 9, 2, True), (300, 257, 3, True), (64, 100, 64, False),
+                                        (2048, 1500, 3, True), (1000, 777, 16, True),
+                                        (40, 3000, 500, True), (33, 65, 1, True)])
 def test_cost_bit_exact(pkg, n, m, d, norm):
+    """C = ||x - y||^2 in float64, divided by its float64 maximum, rounded once:
+    bit for bit the float32 rounding of the float64 definition (many tied
+    maxima on the 1-D grid; 500 coordinates take the untiled kernels)."""
     rng = np.random.default_rng(d)
     X = rng.random((n, d)).astype(np.float32)
     Y = rng.random((m, d)).astype(np.float32)
+    if d == 1:
+        X = (np.arange(n, dtype=np.float32) / 8).reshape(n, 1)
+        Y = (np.arange(m, dtype=np.float32) / 8)[::-1].copy().reshape(m, 1)
     out = torch.zeros((n, m), dtype=torch.float32, device="cuda")
     cmax = torch.zeros(1, dtype=torch.float64, device="cuda")
     assert pkg.eot_cost(n, m, d, dev(X), dev(Y), norm, out, cmax) == pkg.EOT_OK
