@@ -56,7 +56,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--quick", action="store_true",
                     help="skip the additional configurations (on-the-fly cost, batch, serving)")
-    ap.add_argument("--case", default=None, choices=["coop16k", "stream8k", "sknr4k", "gram"],
+    ap.add_argument("--case", default=None,
+                    choices=["coop16k", "stream8k", "sknr4k", "gram", "batch"],
                     help="run one small case for a profiler and exit (no timing, no JSON)")
     return ap.parse_args()
 
@@ -502,7 +503,7 @@ def profile_case(name):
     on a 16384 x 16384 cost (coop16k); column and row transforms on an 8192 x
     8192 cost (stream8k); one SK-NR(30) solve of the 4096 x 4096 workload
     (sknr4k); ten on-the-fly-cost iterations on 20000 x 30000 points in R^64
-    (gram)."""
+    (gram); the batch of 512 problems (batch)."""
     import torch
     import workloads
     import paper_2506_14780_gb300 as pkg
@@ -531,6 +532,15 @@ def profile_case(name):
     elif name == "sknr4k":
         prob = workloads.gaussian_mixture(N, M, seed=0, eps=EPS)
         _, _, res = pkg.solve(prob, tol=TOL, ell=ELL, eps_start=1e-1, max_iter=200000)
+    elif name == "batch":
+        probs = workloads.batch_problems(512, seed=0)
+        keepb = []
+        ps = [pkg.make_problem(q.a, q.b, X=q.X, Y=q.Y, eps=q.eps, normalize_cost=True, keep=keepb)
+              for q in probs]
+        ob = pkg.default_options(tol=TOL, max_iter=200000, eps_start=1e-1)
+        st, _ = pkg.eot_solve_batch(ps, ob, [np.zeros(q.n) for q in probs],
+                                    [np.zeros(q.m) for q in probs])
+        res = {"status_name": "EOT_OK" if st == pkg.EOT_OK else str(st)}
     else:
         prob = workloads.gaussian_cloud(20000, 30000, d=64, seed=0, eps=1e-3)
         _, _, res = pkg.solve(prob, tol=1e-300, ell=0, eps_start=0.0, max_iter=10,

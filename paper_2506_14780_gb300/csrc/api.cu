@@ -73,12 +73,10 @@ cudaError_t launch_gram_pass(const Prob* dP, const Prob& hP, bool col, int mode,
 cudaError_t launch_gram_split(const float* X, int n, int d, double scale, float* Xh, float* Xl,
                               double* nrm, unsigned* bad, cudaStream_t s);
 
-__global__ void wgram_partial_kernel(const float*, const float*, const double*, int, int, int,
-                                     const double*, const float*, double*, double*, const State*,
-                                     int);
-__global__ void wgram_reduce_kernel(const double*, int, int, double*, const State*, int);
 __global__ void newton_kernel(const Prob*, const double*, const double*, const double*);
 __global__ void fprime_kernel(const Prob*);
+void launch_eig_gram(const float* X, const float* Z, const double* w, int len, int p,
+                     float* part, double* G, double* T, double* c, cudaStream_t s);
 void launch_eig_small(int p, int l, int mode, const double* GXX, const double* T,
                       const double* c, float* B, double* theta, double* resid, int* fail,
                       cudaStream_t s);
@@ -107,7 +105,6 @@ __global__ void cost_fill64_kernel(int, int, int, const float*, const float*,
 __global__ void cost64_finish_kernel(size_t, double*, const unsigned long long*, int, float*);
 __global__ void reset_buffers_kernel(State*);
 
-constexpr int kGChunkHost = 64;
 
 // ---------------------------------------------------------------------------
 // Errors
@@ -297,13 +294,14 @@ struct Solver {
   // SK-NR
   float *V = nullptr, *W = nullptr, *s4part = nullptr, *tilesV = nullptr, *tilesZ = nullptr;
   unsigned *s4cnt = nullptr, *s4gcnt = nullptr;
-  double *s4blk = nullptr, *wtw_part = nullptr, *gpart = nullptr, *gvpart = nullptr, *WtW = nullptr, *gw = nullptr,
+  double *s4blk = nullptr, *wtw_part = nullptr, *WtW = nullptr, *gw = nullptr,
          *dw = nullptr;
   // modes
+  float *egpart = nullptr, *eppart = nullptr;   // fused Gram partials (modes V, block X)
   float *Zb = nullptr, *Xb = nullptr, *Yb = nullptr, *Bm = nullptr, *kcpart = nullptr,
         *krpart = nullptr, *tilesY = nullptr, *rmpart = nullptr;
   unsigned *kccnt = nullptr, *krcnt = nullptr, *rmcnt = nullptr;
-  double *epart = nullptr, *evpart = nullptr, *GXX = nullptr, *Tm = nullptr, *cvec = nullptr,
+  double *GXX = nullptr, *Tm = nullptr, *cvec = nullptr,
          *theta = nullptr, *resid = nullptr;
   int* efail = nullptr;
   // host mirrors
@@ -468,7 +466,6 @@ struct Solver {
     }
     hP.out_plain = nullptr;
     hP.logratio_plain = nullptr;
-    const int nch = ceil_div(std::max(n, m), kGChunkHost);
     if (ell > 0) {
       V = A.take<float>((size_t)n * ell);
       W = A.take<float>((size_t)m * ell);
@@ -478,8 +475,7 @@ struct Solver {
       s4blk = A.take<double>((size_t)mm_ncolblk * 4);
       wtw_part = A.take<double>((size_t)mm_ncolblk * (ell * ell + ell));
       tilesV = A.take<float>(mma_tiles_floats(n, ell));
-      gpart = A.take<double>((size_t)nch * ell * ell);
-      gvpart = A.take<double>((size_t)nch * ell);
+      egpart = A.take<float>((size_t)128 * (2 * ell * ell + ell));
       WtW = A.take<double>((size_t)ell * ell);
       gw = A.take<double>(ell);
       dw = A.take<double>(m);
@@ -500,8 +496,7 @@ struct Solver {
       tilesY = A.take<float>(mma_tiles_floats(m, p));
       rmpart = A.take<float>((size_t)rm_nseg * n * mma_record(p));
       rmcnt = A.take<unsigned>(rm_nrowblk);
-      epart = A.take<double>((size_t)nch * p * p);
-      evpart = A.take<double>((size_t)nch * p);
+      eppart = A.take<float>((size_t)128 * (2 * p * p + p));
       GXX = A.take<double>((size_t)p * p);
       Tm = A.take<double>((size_t)p * p);
       cvec = A.take<double>(p);
@@ -640,22 +635,6 @@ struct Solver {
     graph_tma = want;
   }
 
-  // weighted Gram  out = A^T diag(w or 1/w) B  (+ vout = sum_i vw_i A_i)
-  cudaError_t wgram(const float* Am, const float* Bm_, const double* w, int wmode, int len, int q,
-                    const double* vw, const float* vsrc, double* part, double* vpart, double* out,
-                    double* vout, int respect_done, cudaStream_t s) {
-    const int nch = ceil_div(len, kGChunkHost);
-    const size_t sm = ((size_t)2 * kGChunkHost * q + 2 * kGChunkHost) * sizeof(float);
-    wgram_partial_kernel<<<nch, 256, sm, s>>>(Am, Bm_, w, wmode, len, q, vw, vsrc, part,
-                                              vout ? vpart : nullptr, dSt, respect_done);
-    wgram_reduce_kernel<<<ceil_div(q * q, 256), 256, 0, s>>>(part, nch, q * q, out, dSt,
-                                                              respect_done);
-    if (vout)
-      wgram_reduce_kernel<<<ceil_div(q, 256), 256, 0, s>>>(vpart, nch, q, vout, dSt,
-                                                            respect_done);
-    return cudaGetLastError();
-  }
-
   // ---- loop bodies ----
   cudaError_t pass_col(int mode, cudaStream_t s) {
     if (gram) return launch_gram_pass(dP, hP, true, mode, s);
@@ -707,9 +686,8 @@ struct Solver {
     if (e == cudaSuccess) e = kapply_row(fb, gb, Yb, Xb, s);
     if (e != cudaSuccess) return e;
     // GXX = X^T D_a X (+ c = a^T X), T = Z^T D_a X
-    e = wgram(Xb, Xb, hP.a, 0, n, p, hP.a, Xb, epart, evpart, GXX, cvec, 0, s);
-    if (e == cudaSuccess) e = wgram(Zb, Xb, hP.a, 0, n, p, nullptr, nullptr, epart, nullptr, Tm,
-                                    nullptr, 0, s);
+    launch_eig_gram(Xb, Zb, hP.a, n, p, eppart, GXX, Tm, cvec, s);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     launch_eig_small(p, ell, 1, GXX, Tm, cvec, Bm, theta, resid, efail, s);
     apply_kernel<<<ceil_div(n, 64), 256, (size_t)(p * p + 64 * p) * 4, s>>>(Xb, cvec, Bm, n, p,
@@ -1138,8 +1116,8 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
     CUDA_TRY(S->pass_col(MODE_G_INIT, s));
     if (use_nr) {
       // V^T D_a V and V^T a for this level's modes
-      CUDA_TRY(S->wgram(S->V, S->V, P.a, 0, n, ell, P.a, S->V, S->gpart, S->gvpart, P.GV, P.Va, 0,
-                        s));
+      launch_eig_gram(S->V, nullptr, P.a, n, ell, S->egpart, P.GV, nullptr, P.Va, s);
+      CUDA_TRY(cudaGetLastError());
       CUDA_TRY(launch_build_tiles(S->V, n, ell, S->tilesV, s));
       eot_status e = S->run_loop(S->ex_sknr, 0, body_cap_nr + 1);
       if (e != EOT_OK) return e;
@@ -1203,8 +1181,8 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
           S->Xb, n, S->p, 0x5EEDull + 977ull * (unsigned long long)t, have_modes ? S->V : nullptr,
           keep);
       // orthonormalise the start block: Z = (X0 - 1 c^T) L^{-T}
-      CUDA_TRY(S->wgram(S->Xb, S->Xb, P.a, 0, n, S->p, P.a, S->Xb, S->epart, S->evpart, S->GXX,
-                        S->cvec, 0, s));
+      launch_eig_gram(S->Xb, nullptr, P.a, n, S->p, S->eppart, S->GXX, nullptr, S->cvec, s);
+      CUDA_TRY(cudaGetLastError());
       launch_eig_small(S->p, ell, 0, S->GXX, S->Tm, S->cvec, S->Bm, S->theta, S->resid, S->efail, s);
       apply_kernel<<<ceil_div(n, 64), 256, (size_t)(S->p * S->p + 64 * S->p) * 4, s>>>(
           S->Xb, S->cvec, S->Bm, n, S->p, S->Zb);
@@ -2149,8 +2127,8 @@ eot_status eot_spectral_modes(int32_t n, int32_t m, const float* C, const double
   }
   init_block_kernel<<<std::min(ceil_div((long long)n * p, 256), 8 * S->ctx->nsm), 256, 0, s>>>(
       S->Xb, n, p, 0x5EEDull, use_V_as_start ? S->V : nullptr, use_V_as_start ? ell : 0);
-  CUDA_TRY(S->wgram(S->Xb, S->Xb, P.a, 0, n, p, P.a, S->Xb, S->epart, S->evpart, S->GXX, S->cvec,
-                    0, s));
+  launch_eig_gram(S->Xb, nullptr, P.a, n, p, S->eppart, S->GXX, nullptr, S->cvec, s);
+  CUDA_TRY(cudaGetLastError());
   launch_eig_small(p, ell, 0, S->GXX, S->Tm, S->cvec, S->Bm, S->theta, S->resid, S->efail, s);
   apply_kernel<<<ceil_div(n, 64), 256, (size_t)(p * p + 64 * p) * 4, s>>>(S->Xb, S->cvec, S->Bm, n,
                                                                          p, S->Zb);

@@ -1,9 +1,9 @@
 // Small dense algebra on the device for SK-NR(l) (Algorithm 4.1) and the mode
 // computation (Sec. 4), plus the O(n l) vector updates.
 //
-//  * weighted Gram partials/reduction:  G = A^T diag(w) B (+ w^T A), float32
-//    products summed in float32 over 64-row chunks, float64 across chunks;
-//  * newton_kernel (one CTA, float64): H_V = -(1/eps) [V^T D_a V - W^T D_b^{-1} W]
+//  * eig_gram_kernel: the fused weighted Gram sums X^T D_w X, Z^T D_w X, X^T w
+//    (float32 register blocks, compensated float32 sums across row ranges);
+//  * newton_kernel (one CTA): H_V = -(1/eps) [V^T D_a V - W^T D_b^{-1} W]
 //    (Eq. d2Q_semi restricted to V_l with D_r ~ D_a, or exact with D_r),
 //    grad_V = -sum_j d_j W_j with d_j = 1 - exp((g_j - h_j)/eps) (the semi-dual
 //    gradient a - pi(f_k, h) 1 of Eq. dQ_semi projected on V; the row marginals
@@ -19,63 +19,156 @@
 
 namespace eotk {
 
-constexpr int kGChunk = 64;
+// ---------------------------------------------------------------------------
+// Fused weighted Gram sums of the subspace iteration and the Newton set-up:
+//   G = X^T D_w X,  T = Z^T D_w X (when Z is given),  c = X^T w.
+// eig_gram_kernel: each CTA sums a contiguous range of rows with 4 x 4
+// register blocks (float32) into a partial record; eig_gram_reduce_kernel:
+// one thread per output element adds the records in range order with a
+// compensated float32 sum and writes the float64 result (deterministic).
+// ---------------------------------------------------------------------------
+constexpr int kEGMaxChunks = 128;
+constexpr int kEGRows = 64;      // rows staged in shared memory at a time
 
-// part[chunk][p*p] (+ vpart[chunk][p] = sum_i vw_i A_i) partial sums over the
-// rows of one chunk.
-__global__ void __launch_bounds__(256) wgram_partial_kernel(
-    const float* __restrict__ A, const float* __restrict__ B, const double* __restrict__ w,
-    int wmode /*0: w, 1: 1/w*/, int len, int p, const double* __restrict__ vw,
-    const float* __restrict__ vsrc, double* __restrict__ part, double* __restrict__ vpart,
-    const State* st, int respect_done) {
-  if (respect_done && st->done) return;
+__global__ void __launch_bounds__(256) eig_gram_kernel(const float* __restrict__ X,
+                                                       const float* __restrict__ Z,
+                                                       const double* __restrict__ w, int len,
+                                                       int p, float* __restrict__ part) {
   extern __shared__ float sm[];
-  float* sA = sm;                       // [kGChunk][p]
-  float* sB = sA + kGChunk * p;         // [kGChunk][p]
-  float* sw = sB + kGChunk * p;         // [kGChunk]
-  float* svw = sw + kGChunk;            // [kGChunk]
-  const int chunk = blockIdx.x;
-  const int r0 = chunk * kGChunk;
-  const int nr = min(kGChunk, len - r0);
-  for (int t = threadIdx.x; t < kGChunk * p; t += blockDim.x) {
-    const int r = t / p;
-    sA[t] = r < nr ? A[(size_t)r0 * p + t] : 0.f;
-    sB[t] = r < nr ? B[(size_t)r0 * p + t] : 0.f;
-  }
-  for (int r = threadIdx.x; r < kGChunk; r += blockDim.x) {
-    float wv = 0.f, vv = 0.f;
-    if (r < nr) {
-      const double x = w[r0 + r];
-      wv = (float)(wmode ? 1.0 / x : x);
-      vv = vw ? (float)vw[r0 + r] : 0.f;
+  float* sX = sm;                         // [kEGRows][p]
+  float* sZ = sX + kEGRows * p;           // [kEGRows][p]
+  float* sw = sZ + kEGRows * p;           // [kEGRows]
+  const int tid = threadIdx.x;
+  const int nb = (p + 3) >> 2, nb2 = nb * nb;
+  const int ngt = (Z ? 2 : 1) * nb2;               // G and T blocks
+  const int nblk = ngt + nb;                       // + c groups
+  const int rec = 2 * p * p + p;                   // floats per partial record
+  const long long r_beg = (long long)len * blockIdx.x / gridDim.x;
+  const long long r_end = (long long)len * (blockIdx.x + 1) / gridDim.x;
+  float o[2][4][4];
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) o[q][x][y] = 0.f;
+  int ua[2][4], va[2][4];                          // clamped column indices of the blocks
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int blk = tid + 256 * q;
+    int br = 0, bc = 0;
+    if (blk < ngt) {
+      const int b = blk >= nb2 ? blk - nb2 : blk;
+      br = b / nb;
+      bc = b - br * nb;
+    } else if (blk < nblk) {
+      br = blk - ngt;
     }
-    sw[r] = wv;
-    svw[r] = vv;
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      ua[q][x] = min(4 * br + x, p - 1);
+      va[q][x] = min(4 * bc + x, p - 1);
+    }
   }
-  __syncthreads();
-  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
-    const int k = e / p, l = e - k * p;
-    float s = 0.f;
-    for (int r = 0; r < nr; ++r) s = __fmaf_rn(sw[r] * sA[r * p + k], sB[r * p + l], s);
-    part[(size_t)chunk * p * p + e] = (double)s;
+  for (long long r0 = r_beg; r0 < r_end; r0 += kEGRows) {
+    const int nr = (int)min((long long)kEGRows, r_end - r0);
+    __syncthreads();
+    for (int e = tid; e < nr * p; e += 256) {
+      sX[e] = X[(size_t)r0 * p + e];
+      if (Z) sZ[e] = Z[(size_t)r0 * p + e];
+    }
+    for (int r = tid; r < nr; r += 256) sw[r] = (float)w[r0 + r];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int blk = tid + 256 * q;
+      if (blk >= nblk) continue;
+      if (blk < ngt) {
+        const float* U = blk >= nb2 ? sZ : sX;
+        for (int r = 0; r < nr; ++r) {
+          const float wr = sw[r];
+          float u[4], v[4];
+#pragma unroll
+          for (int x = 0; x < 4; ++x) {
+            u[x] = wr * U[r * p + ua[q][x]];
+            v[x] = sX[r * p + va[q][x]];
+          }
+#pragma unroll
+          for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) o[q][x][y] = __fmaf_rn(u[x], v[y], o[q][x][y]);
+        }
+      } else {
+        for (int r = 0; r < nr; ++r) {
+          const float wr = sw[r];
+#pragma unroll
+          for (int x = 0; x < 4; ++x) o[q][0][x] = __fmaf_rn(wr, sX[r * p + ua[q][x]], o[q][0][x]);
+        }
+      }
+    }
   }
-  if (vpart) {
-    for (int k = threadIdx.x; k < p; k += blockDim.x) {
-      float s = 0.f;
-      for (int r = 0; r < nr; ++r) s = __fmaf_rn(svw[r], sA[r * p + k], s);
-      vpart[(size_t)chunk * p + k] = (double)s;
+  // partial record of this range: [G p*p | T p*p | c p]
+  float* my = part + (size_t)blockIdx.x * rec;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int blk = tid + 256 * q;
+    if (blk >= nblk) continue;
+    if (blk < ngt) {
+      const bool isT = blk >= nb2;
+      const int b = isT ? blk - nb2 : blk;
+      const int br = b / nb, bc = b - br * nb;
+      float* dst = my + (isT ? p * p : 0);
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          const int r = 4 * br + x, cc = 4 * bc + y;
+          if (r < p && cc < p) dst[r * p + cc] = o[q][x][y];
+        }
+    } else {
+      const int b = blk - ngt;
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+        if (4 * b + x < p) my[2 * p * p + 4 * b + x] = o[q][0][x];
     }
   }
 }
 
-__global__ void wgram_reduce_kernel(const double* __restrict__ part, int nchunk, int cnt,
-                                    double* __restrict__ out, const State* st, int respect_done) {
-  if (respect_done && st->done) return;
+__global__ void __launch_bounds__(64) eig_gram_reduce_kernel(const float* __restrict__ part,
+                                                             int nch, int p, int withT,
+                                                             double* __restrict__ G,
+                                                             double* __restrict__ T,
+                                                             double* __restrict__ c) {
+  const int rec = 2 * p * p + p;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= cnt) return;
-  double s = 0.0;
-  for (int c = 0; c < nchunk; ++c) s += part[(size_t)c * cnt + e];
-  out[e] = s;
+  if (e >= rec) return;
+  const bool isT = e >= p * p && e < 2 * p * p;
+  if (isT && !withT) return;
+  float sum = 0.f, comp = 0.f;
+  for (int k0 = 0; k0 < nch; k0 += 8) {
+    float v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = k0 + k < nch ? __ldg(part + (size_t)(k0 + k) * rec + e) : 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float y = v[k] - comp;
+      const float t = sum + y;
+      comp = (t - sum) - y;
+      sum = t;
+    }
+  }
+  if (e < p * p) G[e] = (double)sum;
+  else if (isT) T[e - p * p] = (double)sum;
+  else c[e - 2 * p * p] = (double)sum;
+}
+
+void launch_eig_gram(const float* X, const float* Z, const double* w, int len, int p,
+                     float* part, double* G, double* T, double* c, cudaStream_t s) {
+  const int nch = std::max(1, std::min(kEGMaxChunks, (len + kEGRows - 1) / kEGRows));
+  const size_t sm = ((size_t)2 * kEGRows * p + kEGRows) * sizeof(float);
+  eig_gram_kernel<<<nch, 256, sm, s>>>(X, Z, w, len, p, part);
+  const int rec = 2 * p * p + p;
+  eig_gram_reduce_kernel<<<(rec + 63) / 64, 64, 0, s>>>(part, nch, p, Z ? 1 : 0, G, T, c);
 }
 
 // ---------------------------------------------------------------------------
