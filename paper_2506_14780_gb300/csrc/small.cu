@@ -348,8 +348,8 @@ __device__ __forceinline__ void jacobi_rot(float akk, float aqq, float akq, floa
   cth = 1.f;
   sth = 0.f;
   if (fabsf(akq) > 1e-30f) {
-    const float tau = (aqq - akk) / (2.f * akq);
-    const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+    const float tau = __fdividef(aqq - akk, 2.f * akq);
+    const float t = __fdividef(tau >= 0.f ? 1.f : -1.f, fabsf(tau) + sqrtf(1.f + tau * tau));
     cth = rsqrtf(1.f + t * t);
     sth = t * cth;
   }
@@ -365,12 +365,10 @@ __global__ void __launch_bounds__(kEH * kEH) eig_small_kernel(int p, int l, int 
                                                               int* __restrict__ fail_out) {
   __shared__ float A0[kMaxP * kES];
   __shared__ float Q[kMaxP * kES];
-  __shared__ float G[kMaxP * kES];
+  __shared__ __align__(16) float G[kMaxP * kES];
   __shared__ float W[kMaxP * kES];        // scratch; the second Jacobi buffer
   __shared__ float rc[2][kEH], rs[2][kEH], sq[kMaxP];
   __shared__ int pk[2][kEH], pq[2][kEH];
-  __shared__ unsigned short sched[(kMaxP - 1) * kEH];   // round r, slot t: k | q << 8
-  __shared__ unsigned char slot_of[(kMaxP - 1) * kMaxP]; // round r, index: slot << 1 | (is q)
   __shared__ float th[kMaxP], cf[kMaxP], qc[kMaxP];
   __shared__ int order[kMaxP];
   __shared__ float red[64];
@@ -387,17 +385,45 @@ __global__ void __launch_bounds__(kEH * kEH) eig_small_kernel(int p, int l, int 
       Q[r * kES + q] = (r == q) ? 1.f : 0.f;
     }
   for (int k = tid; k < p; k += nt) cf[k] = (float)c[k];
+  // circle ordering: index 0 fixed, the others rotate by one place per round;
+  // pair (k, q), k < q, of slot t in round r
+  auto pair_of = [&](int r, int t, int& k, int& q) {
+    const int pa = t, pb = pe - 1 - t;
+    const int a = pa == 0 ? 0 : 1 + (pa - 1 + r) % nr;
+    const int b = 1 + (pb - 1 + r) % nr;
+    k = min(a, b);
+    q = max(a, b);
+  };
+  // Table of the Jacobi rounds (in G, unused until the Jacobi ends): for round
+  // r and slot t of round r + 1 (round 0 after the last), its pair (k, q) and
+  // where k and q sit in round r: slots ta, tb with pairs (ka, qa), (kb, qb)
+  // and sides xa, xb.  Packed: k | q << 6 | ka << 12 | qa << 18 | xa << 24 |
+  // xb << 25, and kb | qb << 6 | ta << 12 | tb << 17.
+  uint2* nxt = reinterpret_cast<uint2*>(G);
   if (mode == 1) {
-    // circle ordering: index 0 fixed, the others rotate by one place per round
     for (int e = tid; e < nr * half; e += nt) {
       const int r = e / half, t = e - r * half;
-      const int pa = t, pb = pe - 1 - t;
-      const int a = pa == 0 ? 0 : 1 + (pa - 1 + r) % nr;
-      const int b = 1 + (pb - 1 + r) % nr;
-      const int k = min(a, b), q = max(a, b);
-      sched[e] = (unsigned short)(k | (q << 8));
-      slot_of[r * pe + k] = (unsigned char)(t << 1);
-      slot_of[r * pe + q] = (unsigned char)((t << 1) | 1);
+      int k, q;
+      pair_of(r + 1 < nr ? r + 1 : 0, t, k, q);
+      int ta = 0, tb = 0, xa = 0, xb = 0, ka = 0, qa = 0, kb = 0, qb = 0;
+      for (int u = 0; u < half; ++u) {
+        int k2, q2;
+        pair_of(r, u, k2, q2);
+        if (k2 == k || q2 == k) {
+          ta = u;
+          xa = q2 == k;
+          ka = k2;
+          qa = q2;
+        }
+        if (k2 == q || q2 == q) {
+          tb = u;
+          xb = q2 == q;
+          kb = k2;
+          qb = q2;
+        }
+      }
+      nxt[e] = make_uint2((unsigned)(k | (q << 6) | (ka << 12) | (qa << 18) | (xa << 24) | (xb << 25)),
+                          (unsigned)(kb | (qb << 6) | (ta << 12) | (tb << 17)));
     }
   }
   if (tid == 0) s_fail = 0;
@@ -410,7 +436,8 @@ __global__ void __launch_bounds__(kEH * kEH) eig_small_kernel(int p, int l, int 
     // next round from the current values: one barrier per round
     float* An = W;
     if (ty == 0 && tx < half) {
-      const int kq = sched[tx], k = kq & 255, q = kq >> 8;
+      int k, q;
+      pair_of(0, tx, k, q);
       pk[0][tx] = k;
       pq[0][tx] = q;
       jacobi_rot(A[k * kES + k], A[q * kES + q], A[k * kES + q], rc[0][tx], rs[0][tx]);
@@ -426,7 +453,10 @@ __global__ void __launch_bounds__(kEH * kEH) eig_small_kernel(int p, int l, int 
           else dia += v * v;
         }
       eig_sum2(loc, dia, red);
-      if (tid == 0) s_stop = (loc <= 1e-10f * (dia + 1e-30f)) ? 1 : 0;
+      // off-diagonal below 1e-4 of the diagonal (Frobenius): the Ritz
+      // vectors then carry errors far below the subspace iteration's residual
+      // tolerance, and the next iteration refines them anyway
+      if (tid == 0) s_stop = (loc <= 1e-8f * (dia + 1e-30f)) ? 1 : 0;
       __syncthreads();
       if (s_stop) break;
       for (int round = 0; round < nr; ++round) {
@@ -453,12 +483,12 @@ __global__ void __launch_bounds__(kEH * kEH) eig_small_kernel(int p, int l, int 
         }
         if (ty == 0 && tx < half) {
           // slot tx of the next round (round 0 of the next sweep after the last)
-          const int rn = round + 1 < nr ? round + 1 : 0;
-          const int kq = sched[rn * half + tx], k = kq & 255, q = kq >> 8;
-          const int ok_ = slot_of[round * pe + k], oq_ = slot_of[round * pe + q];
-          const int ta = ok_ >> 1, xa = ok_ & 1, tb = oq_ >> 1, xb = oq_ & 1;
+          const uint2 tb2 = nxt[round * half + tx];
+          const int k = tb2.x & 63, q = (tb2.x >> 6) & 63, ka = (tb2.x >> 12) & 63;
+          const int qa = (tb2.x >> 18) & 63, xa = (tb2.x >> 24) & 1, xb = (tb2.x >> 25) & 1;
+          const int kb = tb2.y & 63, qb = (tb2.y >> 6) & 63, ta = (tb2.y >> 12) & 31;
+          const int tb = (tb2.y >> 17) & 31;
           const float ca = rc[cur][ta], sa = rs[cur][ta], cb = rc[cur][tb], sb = rs[cur][tb];
-          const int ka = pk[cur][ta], qa = pq[cur][ta], kb = pk[cur][tb], qb = pq[cur][tb];
           const float akk = rot_entry(xa, xa, ca, sa, ca, sa, A[ka * kES + ka], A[ka * kES + qa],
                                       A[qa * kES + ka], A[qa * kES + qa]);
           const float aqq = rot_entry(xb, xb, cb, sb, cb, sb, A[kb * kES + kb], A[kb * kES + qb],
@@ -554,24 +584,26 @@ __global__ void __launch_bounds__(kEH * kEH) eig_small_kernel(int p, int l, int 
   }
   for (int k = tid; k < p; k += nt) {
     const float dk = G[k * kES + k];
-    sq[k] = dk > 0.f ? sqrtf(dk) : 1.f;
+    sq[k] = dk > 0.f ? rsqrtf(dk) : 1.f;   // 1 / L_kk
   }
+  __syncthreads();
+  // L below the diagonal: L_cq = G_cq / sqrt(D_q) (one product per element)
+  for (int r = ty; r < p; r += nx)
+    for (int q = tx; q < r; q += nx) G[r * kES + q] *= sq[q];
   for (int r = ty; r < p; r += nx)        // W = Q (right-hand sides)
     for (int q = tx; q < p; q += nx) W[r * kES + q] = Q[r * kES + q];
   __syncthreads();
   // B L^T = Q, column by column: after step q, column q of W is final
-  // (L_cq = G_cq / sqrt(D_q) for c > q, L_qq = sqrt(D_q))
   for (int q = 0; q < p; ++q) {
-    const float lqq = sq[q];
+    const float il = sq[q];
     for (int r = ty; r < p; r += nx) {
-      const float b = W[r * kES + q] / lqq;
-      for (int cc = q + 1 + tx; cc < p; cc += nx)
-        W[r * kES + cc] -= b * (G[cc * kES + q] / lqq);
+      const float b = W[r * kES + q] * il;
+      for (int cc = q + 1 + tx; cc < p; cc += nx) W[r * kES + cc] -= b * G[cc * kES + q];
     }
     __syncthreads();
   }
   for (int r = ty; r < p; r += nx)
-    for (int q = tx; q < p; q += nx) Bout[r * p + q] = W[r * kES + q] / sq[q];
+    for (int q = tx; q < p; q += nx) Bout[r * p + q] = W[r * kES + q] * sq[q];
   if (tid == 0 && fail_out) *fail_out = s_fail;
 }
 
