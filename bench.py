@@ -16,6 +16,7 @@ oracle instead (bounded sample, scaled to one solve).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -332,13 +333,36 @@ def roofline(pkg, torch, p, f, g, stream):
     del Xb, Yb, fb, gb
     return {"kernel": "sk_coop_kernel (stored-cost log-sum-exp half-steps, plain Sinkhorn)",
             "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-            "frac": round(achieved / hbm, 3), "traffic": None,
+            "frac": round(achieved / hbm, 3), "traffic": coop_traffic(),
             "per_pass_us": round(large * 1e3, 3), "workload": f"{nl}x{nl} cost (1.07 GB, HBM)",
             "algorithmic_bytes_per_launch": int(bytes_pass),
             "l2_resident_4096": {"per_pass_us": round(small * 1e3, 3),
                                  "achieved_gbs": round(4.0 * N * M / (small * 1e-3) / 1e9, 1)},
             "note": "per half-step, launch and grid-barrier overheads included; peak of "
                     "measured (MEASURED_PEAKS.json hbm_gbs)"}
+
+
+# DRAM traffic of one sk_coop_kernel half-step at 16384^2 (dram__bytes_read.sum +
+# dram__bytes_write.sum of one launch of four half-steps, divided by four; ncu capture
+# summarised in profiles/sk_coop_kernel_16384_traffic.md).  It describes the kernel
+# built from the sources it was taken on, identified by their SHA-256: after any change
+# to them the bench reports no traffic until the capture is taken again.
+COOP_TRAFFIC_BYTES = 1082074816
+COOP_TRAFFIC_SOURCES = ("stream.cu", "stream_common.cuh", "eot_device.cuh", "eot_internal.h",
+                        "pass_common.cuh", "reduce.cuh", "tc.cuh")
+COOP_TRAFFIC_SHA256 = "32e1fef245c6f90a201e747fb2bcca04238352e6b1755253323fc921c36100f8"
+
+
+def coop_traffic():
+    h = hashlib.sha256()
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2506_14780_gb300", "csrc")
+    try:
+        for f in COOP_TRAFFIC_SOURCES:
+            with open(os.path.join(src, f), "rb") as fh:
+                h.update(fh.read())
+    except OSError:
+        return None
+    return COOP_TRAFFIC_BYTES if h.hexdigest() == COOP_TRAFFIC_SHA256 else None
 
 
 def extras(pkg, torch, stream):

@@ -1039,6 +1039,7 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   P.pot_bound = gram ? 1e300 : std::ldexp(1.0, 22 - q) / 2.0 - cmax;
   P.eps = eps0;
   P.k2 = (float)(1.0 / (eps0 * std::log(2.0)));
+  P.k2lo = (float)(1.0 / (eps0 * std::log(2.0)) - (double)P.k2);
   P.st = S->dSt;
   {
     eot_status me = encode_cost_map(P);
@@ -1097,14 +1098,15 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   for (int t = 0; t < L; ++t) {
     const double eps = levels[t];
     const bool last = t == L - 1;
-    // Final-level margins (float32 passes only): the device test and the
-    // verification below evaluate the marginal ratios from float32 partial
-    // sums, whose rounding (about 1e-7 relative per sum) leaves the L1
-    // estimate up to ~1e-7 away from a float64 evaluation near a tolerance of
-    // 1e-6.  The device aims at 0.85 tol and the returned pair must verify
-    // below 0.9 tol.
+    // Final-level margins (float32 passes only): the device test estimates
+    // the column term from the iteration's own arithmetic (the hardware
+    // exponential, biased by a few 1e-8 relative, and k2 rounded to float32,
+    // i.e. eps' instead of eps), which cannot see a uniform marginal error of
+    // about 1e-7; the verification below evaluates both terms at eps with the
+    // unbiased exponential.  The device aims at 0.75 tol and the returned pair
+    // must verify below 0.9 tol.
     const double tol_verify = last ? (S->f64 ? o->tol : 0.9 * o->tol) : 0.0;
-    const double tol = last ? (S->f64 ? o->tol : 0.85 * o->tol)
+    const double tol = last ? (S->f64 ? o->tol : 0.75 * o->tol)
                             : (o->level_tol > 0.0 ? o->level_tol : o->tol);
     const bool use_nr = ell > 0 && have_modes;
     CUDA_TRY(cudaEventRecord(lev_ev[t], s));
@@ -1301,7 +1303,7 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
 // every problem to its result, and one copy-out.
 // ---------------------------------------------------------------------------
 struct BatchModel {            // calibrated cost model of the gang sizes
-  double ns_per_elem = 0.0;    // one CTA, one element of one half-step
+  double step_ns = 0.0;        // one load-and-reduce step of a CTA (8192 elements when full)
   double fix_ns = 0.0;         // fixed cost of one iteration of a small problem
   double bar_ns = 0.0;         // one gang barrier
   bool done = false;
@@ -1309,10 +1311,24 @@ struct BatchModel {            // calibrated cost model of the gang sizes
 static BatchModel g_bmodel[64];
 static std::mutex g_bmodel_mu;
 
-// Predicted device time of a task: iterations x (two half-steps shared by G
-// CTAs + the fixed cost + two gang barriers when G > 1).
-static double task_ns(const BatchModel& M, double iters, long long nm, int G) {
-  return iters * (2.0 * (double)nm * M.ns_per_elem / G + M.fix_ns + (G > 1 ? 2.0 * M.bar_ns : 0.0));
+// Predicted device time of a task: iterations x (the steps of a rank's two
+// half-steps + the fixed cost + two gang barriers when G > 1).  A step is one
+// round of cost loads and reductions of the whole CTA (eight 16-byte loads a
+// thread); the counts follow the kernel's work units: chunks of rows in the
+// row pass, blocks of 128 columns times 8-row blocks per warp in the column
+// pass.  Calibrated on a single CTA, a step's time includes the latency of its
+// loads, which is what bounds the passes of small problems.
+static double batch_steps(int n, int m, int G) {
+  const int lpr = eotk::batch_lpr(m), rpw = 32 / lpr, rpwc = std::max(rpw, 4), cr = 8 * rpwc;
+  const double ng = (m + 3) / 4;
+  const double rows = std::ceil((double)n / G);
+  const double row_steps = std::ceil(rows / cr) * (rpwc / rpw) * std::ceil(ng / (8.0 * lpr));
+  const double w = 4.0 * std::ceil(ng / G);
+  const double col_steps = std::ceil(w / 128.0) * std::ceil(std::ceil(n / 8.0) / 8.0);
+  return row_steps + col_steps;
+}
+static double task_ns(const BatchModel& M, double iters, int n, int m, int G) {
+  return iters * (batch_steps(n, m, G) * M.step_ns + M.fix_ns + (G > 1 ? 2.0 * M.bar_ns : 0.0));
 }
 
 // Grow-only pinned staging buffer of the calling thread.
@@ -1382,9 +1398,12 @@ static eot_status calibrate_batch(int dev) {
   if (sc == EOT_OK) sc = run(64, it_small, 1, &t1);
   if (sc == EOT_OK) sc = run(64, it_small, 8, &t8);
   if (sc != EOT_OK) return sc;
-  // a run: G_INIT, the iterations, the evaluation (about 2 iters + 2 half-steps)
-  M.fix_ns = std::max(1000.0, 1e6 * t1 / (it_small + 1.5));
-  M.ns_per_elem = std::max(1e-3, (1e6 * tb / (it_big + 1.5) - M.fix_ns) / (2.0 * 1024.0 * 1024.0));
+  // a run: G_INIT, the iterations, the evaluation (about 1.5 iterations more);
+  // per iteration: fix + steps x step_ns, solved from the small and the large run
+  const double tsm = 1e6 * t1 / (it_small + 1.5), tbg = 1e6 * tb / (it_big + 1.5);
+  const double ssm = batch_steps(64, 64, 1), sbg = batch_steps(1024, 1024, 1);
+  M.step_ns = std::max(10.0, (tbg - tsm) / (sbg - ssm));
+  M.fix_ns = std::max(500.0, tsm - ssm * M.step_ns);
   M.bar_ns = std::max(500.0, 1e6 * (t8 - t1) / (2.0 * (it_small + 2.0)));
   M.done = true;
   return EOT_OK;
@@ -1401,12 +1420,19 @@ static eot_status run_batch(int count, const eot_problem* probs, const eot_optio
   if (ctas < 1) return fail(EOT_ECUDA, "the batch kernel cannot be resident");
   const int cap = std::max(1, std::min(kBMaxGang, ctas / 8));
   if (forced_G <= 0) {
+    // EOT_BATCH_GANG=G: every problem runs on a gang of G CTAs (no cost model;
+    // results are the same for any G)
+    const char* ge = getenv("EOT_BATCH_GANG");
+    if (ge && atoi(ge) > 0) forced_G = atoi(ge);
+  }
+  if (forced_G <= 0) {
     eot_status ce = calibrate_batch(ctx->dev);
     if (ce != EOT_OK) return ce;
   }
   const BatchModel& M = g_bmodel[ctx->dev & 63];
   struct PL {
     bool ok = false;
+    bool trans = false;   // run as the transposed problem (rows = the shorter side)
     int n = 0, m = 0, d = 0, pitch = 0, G = 1;
     std::vector<double> lev;
     size_t h_a = 0, h_b = 0, h_x = 0, h_y = 0, h_c = 0, h_f = 0;   // staging offsets
@@ -1433,10 +1459,14 @@ static eot_status run_batch(int count, const eot_problem* probs, const eot_optio
       continue;
     }
     p.ok = true;
-    p.n = q.n;
-    p.m = q.m;
+    // plain Sinkhorn is symmetric in the two sides: with more rows than
+    // columns the problem runs transposed, so that the column half-step (one
+    // CTA streams all rows of its columns) has the short side to stream
+    p.trans = q.n > q.m && !q.f_init;
+    p.n = p.trans ? q.m : q.n;
+    p.m = p.trans ? q.n : q.m;
     p.d = q.d;
-    p.pitch = (q.m + 3) & ~3;
+    p.pitch = (p.m + 3) & ~3;
     p.G = forced_G > 0 ? std::min(forced_G, cap) : 1;
     if (q.mem == EOT_MEM_HOST) {
       p.h_a = htake(sizeof(double) * q.n);
@@ -1463,23 +1493,23 @@ static eot_status run_batch(int count, const eot_problem* probs, const eot_optio
   if (forced_G <= 0) {
     double sum1 = 0.0;
     for (int k = 0; k < count; ++k)
-      if (pl[k].ok) sum1 += task_ns(M, est_it[k], (long long)pl[k].n * pl[k].m, 1);
+      if (pl[k].ok) sum1 += task_ns(M, est_it[k], pl[k].n, pl[k].m, 1);
     const double target = 0.5 * sum1 / ctas;
     for (int k = 0; k < count; ++k) {
       if (!pl[k].ok) continue;
-      const long long nm = (long long)pl[k].n * pl[k].m;
+      const int n = pl[k].n, m = pl[k].m;
       int G = 1;
-      while (G < cap && task_ns(M, est_it[k], nm, G) > target &&
-             task_ns(M, est_it[k], nm, 2 * G) < task_ns(M, est_it[k], nm, G))
+      while (G < cap && task_ns(M, est_it[k], n, m, G) > target &&
+             task_ns(M, est_it[k], n, m, 2 * G) < task_ns(M, est_it[k], n, m, G))
         G *= 2;
       pl[k].G = G;
     }
   }
   // ---- device arena: [staged inputs | per-problem state | outputs | tables] ----
   struct DL {
-    double *a, *b, *loga, *logb, *f, *g0, *g1, *fo, *go, *part;
-    float *C, *Lrow, *Lcol, *fs[4], *gs0[4], *gs1[4];
-    unsigned* bar;
+    double *a, *b, *loga, *logb, *f, *g0, *g1, *fo, *go;
+    float *af, *bf, *C, *Lrow, *Lcol, *fs[4], *gs0[4], *gs1[4];
+    unsigned *bar, *flag;
   };
   std::vector<DL> dl(count);
   size_t out_off = 0, out_bytes = 0;
@@ -1501,17 +1531,19 @@ static eot_status run_batch(int count, const eot_problem* probs, const eot_optio
       for (int q = 0; q < 4; ++q) L.fs[q] = A.take<float>(np);
       for (int q = 0; q < 4; ++q) L.gs0[q] = A.take<float>(mp);
       for (int q = 0; q < 4; ++q) L.gs1[q] = A.take<float>(mp);
+      L.af = A.take<float>(p.n);
+      L.bf = A.take<float>(p.m);
       L.Lrow = A.take<float>(p.n);
       L.Lcol = A.take<float>(p.m);
-      L.part = A.take<double>((size_t)p.G * kBPart);
       L.bar = A.take<unsigned>(2);
+      L.flag = A.take<unsigned>(1);
     }
     A.off = (A.off + 255) & ~size_t(255);
     out_off = A.off;
     for (int k = 0; k < count; ++k) {
       if (!pl[k].ok) continue;
-      dl[k].fo = A.take<double>(pl[k].n);
-      dl[k].go = A.take<double>(pl[k].m);
+      dl[k].fo = A.take<double>(probs[k].n);
+      dl[k].go = A.take<double>(probs[k].m);
     }
     A.off = (A.off + 255) & ~size_t(255);
     out_bytes = A.off - out_off;
@@ -1584,21 +1616,28 @@ static eot_status run_batch(int count, const eot_problem* probs, const eot_optio
     I.pitch = p.pitch;
     I.normalize = q.normalize_cost ? 1 : 0;
     I.givenC = q.d == 0 ? 1 : 0;
-    I.X = q.d > 0 ? (host ? reinterpret_cast<const float*>(dmem + p.h_x)
-                          : static_cast<const float*>(q.X))
-                  : nullptr;
-    I.Y = q.d > 0 ? (host ? reinterpret_cast<const float*>(dmem + p.h_y)
-                          : static_cast<const float*>(q.Y))
-                  : nullptr;
+    const float* Xs = q.d > 0 ? (host ? reinterpret_cast<const float*>(dmem + p.h_x)
+                                      : static_cast<const float*>(q.X))
+                              : nullptr;
+    const float* Ys = q.d > 0 ? (host ? reinterpret_cast<const float*>(dmem + p.h_y)
+                                      : static_cast<const float*>(q.Y))
+                              : nullptr;
+    I.X = p.trans ? Ys : Xs;
+    I.Y = p.trans ? Xs : Ys;
+    I.trans = p.trans ? 1 : 0;
     I.Cin = q.d == 0 ? (host ? reinterpret_cast<const float*>(dmem + p.h_c)
                              : static_cast<const float*>(q.C))
                      : nullptr;
-    I.win_a = host ? reinterpret_cast<const double*>(dmem + p.h_a) : q.a;
-    I.win_b = host ? reinterpret_cast<const double*>(dmem + p.h_b) : q.b;
+    const double* was = host ? reinterpret_cast<const double*>(dmem + p.h_a) : q.a;
+    const double* wbs = host ? reinterpret_cast<const double*>(dmem + p.h_b) : q.b;
+    I.win_a = p.trans ? wbs : was;
+    I.win_b = p.trans ? was : wbs;
     I.a = L.a;
     I.b = L.b;
     I.loga = L.loga;
     I.logb = L.logb;
+    I.af = L.af;
+    I.bf = L.bf;
     I.C = L.C;
     I.cmax = d_cmax + k;
     I.bad = d_bad + 2 * k;
@@ -1668,7 +1707,10 @@ static eot_status run_batch(int count, const eot_problem* probs, const eot_optio
     T.nlev = (int)p.lev.size();
     T.G = p.G;
     T.max_iter = o.max_iter;
+    T.lpr = batch_lpr(p.n > 0 ? p.m : 1);
     T.C = L.C;
+    T.af = L.af;
+    T.bf = L.bf;
     T.a = L.a;
     T.b = L.b;
     T.loga = L.loga;
@@ -1681,10 +1723,10 @@ static eot_status run_batch(int count, const eot_problem* probs, const eot_optio
     T.gsp[1] = Split{L.gs1[0], L.gs1[1], L.gs1[2], L.gs1[3], nullptr};
     T.Lrow = L.Lrow;
     T.Lcol = L.Lcol;
-    T.f_out = L.fo;
-    T.g_out = L.go;
+    T.f_out = p.trans ? L.go : L.fo;
+    T.g_out = p.trans ? L.fo : L.go;
     T.bar = L.bar;
-    T.part = L.part;
+    T.flag = L.flag;
     T.out = d_out + k;
     T.tol_level = o.level_tol > 0.0 ? o.level_tol : o.tol;
     T.tol_last = 0.85 * o.tol;   // the float32 estimate's margin (see solve_one)
@@ -1695,8 +1737,8 @@ static eot_status run_batch(int count, const eot_problem* probs, const eot_optio
     T.pot_bound = std::ldexp(1.0, 22 - qg) / 2.0 - cmax;
     for (int l = 0; l < T.nlev; ++l) T.eps[l] = p.lev[l];
     // the longest predicted tasks first
-    order.push_back({-task_ns(M.done ? M : BatchModel{1.0, 0.0, 0.0, true}, est_it[k],
-                              (long long)p.n * p.m, p.G),
+    order.push_back({-task_ns(M.done ? M : BatchModel{1.0, 0.0, 0.0, true}, est_it[k], p.n, p.m,
+                              p.G),
                      k});
   }
   std::sort(order.begin(), order.end());
@@ -1745,8 +1787,8 @@ static eot_status run_batch(int count, const eot_problem* probs, const eot_optio
     CUDA_TRY(cudaMemcpyAsync(hst, dmem + out_off, out_bytes, cudaMemcpyDeviceToHost, s));
   for (int k = 0; k < count; ++k) {
     if (!pl[k].ok || probs[k].mem != EOT_MEM_DEVICE) continue;
-    CUDA_TRY(cudaMemcpyAsync(f_out[k], dl[k].fo, sizeof(double) * pl[k].n, cudaMemcpyDeviceToDevice, s));
-    CUDA_TRY(cudaMemcpyAsync(g_out[k], dl[k].go, sizeof(double) * pl[k].m, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(f_out[k], dl[k].fo, sizeof(double) * probs[k].n, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(g_out[k], dl[k].go, sizeof(double) * probs[k].m, cudaMemcpyDeviceToDevice, s));
   }
   CUDA_TRY(cudaStreamSynchronize(s));
   float ms = 0.f;
@@ -1762,20 +1804,20 @@ static eot_status run_batch(int count, const eot_problem* probs, const eot_optio
     }
     if (probs[k].mem == EOT_MEM_HOST) {
       std::memcpy(f_out[k], hst + (reinterpret_cast<char*>(dl[k].fo) - dmem - out_off),
-                  sizeof(double) * pl[k].n);
+                  sizeof(double) * probs[k].n);
       std::memcpy(g_out[k], hst + (reinterpret_cast<char*>(dl[k].go) - dmem - out_off),
-                  sizeof(double) * pl[k].m);
+                  sizeof(double) * probs[k].m);
     }
     const BatchOut& b = hout[k];
     eot_result r{};
     r.iters = b.iters;
     r.total_iters = b.total_iters;
     r.levels = b.levels;
-    r.row_l1 = b.row_l1;
-    r.col_l1 = b.col_l1;
+    r.row_l1 = pl[k].trans ? b.col_l1 : b.row_l1;
+    r.col_l1 = pl[k].trans ? b.row_l1 : b.col_l1;
     r.l1_marginal = b.row_l1 + b.col_l1;
     r.q_dual = b.q_dual;
-    r.q_semi = b.q_semi;
+    r.q_semi = b.q_semi;   // a transposed run reports the semi-dual in g
     r.dual_gap = b.dual_gap;
     r.seconds = 1e-9 * (double)(b.t_end - b.t_begin);
     r.seconds_last_level = 1e-9 * (double)(b.t_end - b.t_last_level);
@@ -1874,6 +1916,7 @@ static eot_status standalone_grid(Solver* S, const float* Cdev, const double* p1
   P.pot_bound = std::ldexp(1.0, 22 - q) / 2.0 - cm;
   P.eps = eps;
   P.k2 = (float)(1.0 / (eps * std::log(2.0)));
+  P.k2lo = (float)(1.0 / (eps * std::log(2.0)) - (double)P.k2);
   P.st = S->dSt;
   if (cmax_out) *cmax_out = cm;
   return encode_cost_map(P);

@@ -18,13 +18,21 @@
 //
 // Within a task the gang splits the rows (row half-step) and the columns
 // (column half-step) into contiguous ranges: every output potential is
-// computed whole by one CTA, so no partial log-sum-exp states cross CTAs.
-// Gang barriers (global counters, acquire/release, time-bounded waits)
-// separate the half-steps; per-rank partial sums, added in rank order, give
-// the L1 test and the scores, so the results do not depend on scheduling.
+// computed whole by one CTA, so no partial log-sum-exp states cross CTAs, and
+// the order of every sum depends on the problem's shape alone.  Gang barriers
+// (global counters, acquire/release, time-bounded waits) separate the
+// half-steps; the L1 test and the scores are summed by every rank over the
+// whole problem in one fixed order, so a result does not depend on the gang
+// size, on the schedule or on the other problems of the batch.
 // The column half-step writes the new g into the other of two buffers and the
 // gang commits it only when the test fails, so that the returned pair is
 // (f_k, g_k) of the stopping iteration (as in the single solves).
+//
+// Inner loops: the cost is read with 16-byte loads, eight per lane issued
+// before the arithmetic (enough bytes in flight per SM to stream from HBM);
+// exponents are formed two at a time with the packed float32x2 instructions;
+// the float64 finish of each output (log, delta update, grid splits) runs in
+// whole warps, batched per chunk of rows or columns.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -81,269 +89,411 @@ __device__ bool gang_sync(unsigned* bar, int G, int* s_flag) {
   return *s_flag == 0;
 }
 
-// Running log-sum-exp of one output index over a thread's terms (log2 units,
-// windowed integer reference as in the staged passes).
-struct BLse {
-  float ref, rr, S;
-};
-
-__device__ __forceinline__ void blse_add4(BLse& s, float y0, float y1, float y2, float y3) {
-  float z0 = y0, z1 = y1, z2 = y2, z3 = y3;
-  if (s.ref != 0.f) {
-    z0 -= s.ref;
-    z1 -= s.ref;
-    z2 -= s.ref;
-    z3 -= s.ref;
-  }
-  s.rr = fmaxf(s.rr, fmaxf(fmaxf(z0, z1), fmaxf(z2, z3)));
-  if (s.rr > -INFINITY && needs_move(s.rr, s.ref)) {
-    move_ref(s.rr, s.ref, s.S);
-    z0 = y0 - s.ref;
-    z1 = y1 - s.ref;
-    z2 = y2 - s.ref;
-    z3 = y3 - s.ref;
-  }
-  s.S += (ex2_approx(z0) + ex2_approx(z1)) + (ex2_approx(z2) + ex2_approx(z3));
-}
-
-// Split of a potential value into the four exponent arrays (eot_device.cuh).
-__device__ __forceinline__ void bsplit(const BatchTask& T, double o, double eps_logw, Split s,
-                                       int idx) {
+// Split of a potential value into the four exponent arrays (eot_device.cuh);
+// the low parts are stored times k2 = 1/(eps ln 2) of the current level, so
+// that an exponent is one fused multiply-add away from the exact part.
+__device__ __forceinline__ void bsplit(const BatchTask& T, double o, double eps_logw, float k2,
+                                       Split s, int idx) {
   double hi;
   float lo;
   split_grid(o + eps_logw, T.qscale, T.qinv, hi, lo);
   s.A[idx] = (float)(hi + (double)T.M);
-  s.AL[idx] = lo;
+  s.AL[idx] = lo * k2;
   split_grid(o, T.qscale, T.qinv, hi, lo);
   s.K[idx] = (float)((double)T.M - hi);
-  s.KL[idx] = lo;
+  s.KL[idx] = lo * k2;
 }
 
-// Finish one output index from its merged (R, S) (log2 units): the new value
-// (delta form: out = shift - eps L), its splits (unless eval), and, in float
-// (the test needs a few digits of a sum of positive terms), its L1 term
-// w |expm1 L| and a numeric flag.  Float64 work here is kept to the splits:
-// it runs at a small fraction of the float32 rate on this GPU.
-__device__ __forceinline__ void bfinish(const BatchTask& T, float R, float S, double shift,
-                                        double w, double eps_logw, double eps, double* out,
-                                        Split so, float* Lout, int idx, bool eval,
-                                        float acc[2]) {
-  float L = R * kLn2 + log_sum((double)S);
-  double o = shift - eps * (double)L;
+// Finish one output index from its merged state (reference R and sum S in
+// log2 units, without the output side's low part kl, which enters here): the
+// new value (delta form: out = shift - eps L, Eq. foc_f / foc_g), its splits
+// (unless eval) and L.  A non-finite or out-of-range value raises the
+// problem's numeric flag and keeps the old value.
+__device__ __forceinline__ void bfinish(const BatchTask& T, float R, float S, float kl,
+                                        double shift, double eps_logw, double eps, float k2,
+                                        double* out, Split so, float* Lout, int idx, bool eval) {
+  double L = ((double)R + (double)kl) * 0.6931471805599453 + (double)log_sum((double)S);
+  double o = shift - eps * L;
   if (!isfinite(o) || !(S > 0.f) || fabs(o) > T.pot_bound) {
-    acc[1] += 1.f;
+    atomicOr(T.flag, 1u);
     o = shift;
-    L = 0.f;
+    L = 0.0;
   }
-  Lout[idx] = L;
+  Lout[idx] = (float)L;
   if (!eval) {
     out[idx] = o;
-    bsplit(T, o, eps_logw, so, idx);
+    bsplit(T, o, eps_logw, k2, so, idx);
   }
-  acc[0] += (float)w * fabsf(expm1f(L));
 }
 
-// Sum of two floats over the CTA; valid in thread 0.
-__device__ __forceinline__ void bsum2f(float v[2], float* sh /*[2][8]*/) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const float a = warp_sum_f(v[0]), b = warp_sum_f(v[1]);
-  if (lane == 0) {
-    sh[wid] = a;
-    sh[8 + wid] = b;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float x = 0.f, y = 0.f;
-    for (int w = 0; w < kBThreads / 32; ++w) {
-      x += sh[w];
-      y += sh[8 + w];
-    }
-    v[0] = x;
-    v[1] = y;
-  }
-  __syncthreads();
-}
-
-// Sum of four doubles over the CTA; valid in thread 0.
-__device__ __forceinline__ void bsum4(double v[4], double* sh /*[4][8]*/) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const double x = warp_sum_d(v[k]);
-    if (lane == 0) sh[k * 8 + wid] = x;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      double t = 0.0;
-      for (int w = 0; w < kBThreads / 32; ++w) t += sh[k * 8 + w];
-      v[k] = t;
-    }
-  }
-  __syncthreads();
+// Rescale a pair of partial sums that share one reference.
+__device__ __forceinline__ void move_ref2(float& rr, float& ref, float2& S) {
+  const float old = ref;
+  move_ref(rr, ref, S.x);
+  if (ref != old) S.y = scale2(S.y, old - ref);
 }
 
 struct BShared {
-  float mr[kBThreads];
-  float ms[kBThreads];
-  double red[32];
-  float redf[16];
+  float4 cref[2][8][32];   // column pass: [buffer][row group][lane], 4 columns a lane
+  float4 csum[2][8][32];
+  float rref[2][256];      // row pass: [buffer][row of the chunk]
+  float rsum[2][256];
+  double red[8][8];        // block sums: [value][warp]
   int flag;
   int slot;
 };
 
-// Row half-step over rows [r0, r1): f_i <- f_i - eps L_i (Eq. foc_f, delta
-// form), g from buffer gi.  eval: log-ratios and sums only.  A row is reduced
-// by a group of LPR lanes (a power of two sized so that a lane streams about
-// four 4-column groups), so a warp finishes 32 / LPR rows at once.
-__device__ void brow_pass(const BatchTask& T, int r0, int r1, int gi, double eps, float k2,
-                          bool eval, float acc[2]) {
+// Sum over the CTA of NV values per thread in a fixed order (warp butterflies,
+// then the warps in index order); every thread receives the sums.
+template <int NV, class V>
+__device__ __forceinline__ void bsum_all(V v[NV], BShared& sh) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int m = T.m;
-  const Split cs = T.gsp[gi];
-  int LPR = 1;
-  while (LPR < 32 && LPR * 16 < m) LPR *= 2;
-  const int sub = lane & (LPR - 1), grp = lane / LPR, rpw = 32 / LPR;
-  for (int i0 = r0 + wid * rpw; i0 < r1; i0 += (kBThreads / 32) * rpw) {
-    const int i = i0 + grp;
-    const bool iv = i < r1;
-    float rf = -INFINITY, ss = 0.f;
-    if (iv) {
-      const float Ki = T.fs.K[i], cci = T.fs.KL[i] * k2;
-      const float* Ci = T.C + (size_t)i * T.pitch;
-      BLse s{0.f, -INFINITY, 0.f};
-      // two 4-column groups per step, all loads issued before the arithmetic
-      // (the cost rows are padded to a multiple of 4 floats and the split
-      // arrays to a multiple of 128, so the 16-byte loads stay in bounds)
-      auto terms = [&](int j, float4 c, float4 av, float4 al, float y[4]) {
-        const float cv[4] = {c.x, c.y, c.z, c.w};
-        const float aa[4] = {av.x, av.y, av.z, av.w};
-        const float ll[4] = {al.x, al.y, al.z, al.w};
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float t = __fsub_rn(__fsub_rn(aa[q], Ki), cv[q]);
-          y[q] = (j + q < m) ? __fmaf_rn(t, k2, __fmaf_rn(ll[q], k2, cci)) : -INFINITY;
-        }
-      };
-      const int step = LPR * 4;
-      int j = sub * 4;
-      for (; j + step < m; j += 2 * step) {
-        const float4 c0 = *reinterpret_cast<const float4*>(Ci + j);
-        const float4 c1 = *reinterpret_cast<const float4*>(Ci + j + step);
-        const float4 a0 = __ldg(reinterpret_cast<const float4*>(cs.A + j));
-        const float4 a1 = __ldg(reinterpret_cast<const float4*>(cs.A + j + step));
-        const float4 l0 = __ldg(reinterpret_cast<const float4*>(cs.AL + j));
-        const float4 l1 = __ldg(reinterpret_cast<const float4*>(cs.AL + j + step));
-        float y0[4], y1[4];
-        terms(j, c0, a0, l0, y0);
-        terms(j + step, c1, a1, l1, y1);
-        blse_add4(s, y0[0], y0[1], y0[2], y0[3]);
-        blse_add4(s, y1[0], y1[1], y1[2], y1[3]);
-      }
-      if (j < m) {
-        float y0[4];
-        terms(j, *reinterpret_cast<const float4*>(Ci + j),
-              __ldg(reinterpret_cast<const float4*>(cs.A + j)),
-              __ldg(reinterpret_cast<const float4*>(cs.AL + j)), y0);
-        blse_add4(s, y0[0], y0[1], y0[2], y0[3]);
-      }
-      rf = (s.S > 0.f) ? s.ref : -INFINITY;
-      ss = s.S;
+  for (int k = 0; k < NV; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    if (lane == 0) sh.red[k][wid] = (double)v[k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    V t = V(0);
+    for (int w = 0; w < kBThreads / 32; ++w) t += (V)sh.red[k][w];
+    v[k] = t;
+  }
+  __syncthreads();
+}
+
+// Partial log-sum-exp of row i over one lane's 4-column groups g = sub,
+// sub + LPR, ... (eight groups per step, all cost loads issued first):
+// exponents y_j = ((A_j - K_i) - C_ij) k2 + AL_j k2 in log2 units, summed in
+// a pair of float32 sums under one windowed reference.
+template <bool ACC>
+__device__ __forceinline__ void brow_stream(const BatchTask& T, const Split& cs, int i, int sub,
+                                            int LPR, float k2, float k2lo, float& rf, float& ss) {
+  const int m = T.m, ng = (m + 3) >> 2;
+  const float4* Ci = reinterpret_cast<const float4*>(T.C + (size_t)i * T.pitch);
+  const float4* A4 = reinterpret_cast<const float4*>(cs.A);
+  const float4* L4 = reinterpret_cast<const float4*>(cs.AL);
+  const float Ki = T.fs.K[i];
+  const float2 nk = f2(-Ki, -Ki), k2v = f2(k2, k2), k2l = f2(k2lo, k2lo), m1 = f2(-1.f, -1.f);
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  float ref = 0.f, rr = -INFINITY;
+  float2 S = f2(0.f, 0.f);
+  for (int g0 = sub; g0 < ng; g0 += kBRowU * LPR) {
+    float4 c[kBRowU];
+#pragma unroll
+    for (int u = 0; u < kBRowU; ++u) {
+      const int g = g0 + u * LPR;
+      c[u] = g < ng ? __ldcg(Ci + g) : z4;
     }
-    // merge the group's lanes (every lane of the warp takes part in the shuffles)
-    for (int o = LPR >> 1; o > 0; o >>= 1) {
-      const float r2 = __shfl_xor_sync(0xffffffffu, rf, o);
-      const float s2 = __shfl_xor_sync(0xffffffffu, ss, o);
-      lse2_merge(rf, ss, r2, s2);
+    // exponents: the iteration rounds y = t k2 + AL once; an evaluation pass
+    // (ACC) keeps t and forms y as p + q at the term, p = t k2 rounded and q
+    // its exact rounding error plus AL (ex2_pq)
+    float2 ya[kBRowU], yb[kBRowU];
+#pragma unroll
+    for (int u = 0; u < kBRowU; ++u) {
+      const int g = g0 + u * LPR;
+      const float4 a = g < ng ? A4[g] : z4;
+      const float4 l = g < ng ? L4[g] : z4;
+      const float2 ta = __ffma2_rn(f2(c[u].x, c[u].y), m1, __fadd2_rn(f2(a.x, a.y), nk));
+      const float2 tb = __ffma2_rn(f2(c[u].z, c[u].w), m1, __fadd2_rn(f2(a.z, a.w), nk));
+      if constexpr (ACC) {
+        ya[u] = ta;
+        yb[u] = tb;
+      } else {
+        ya[u] = __ffma2_rn(ta, k2v, __ffma2_rn(ta, k2l, f2(l.x, l.y)));
+        yb[u] = __ffma2_rn(tb, k2v, __ffma2_rn(tb, k2l, f2(l.z, l.w)));
+      }
+      const int j = 4 * g;
+      if (j + 3 >= m) {   // the ragged last group, or past the end of the row
+        ya[u].x = j + 0 < m ? ya[u].x : -INFINITY;
+        ya[u].y = j + 1 < m ? ya[u].y : -INFINITY;
+        yb[u].x = j + 2 < m ? yb[u].x : -INFINITY;
+        yb[u].y = j + 3 < m ? yb[u].y : -INFINITY;
+      }
     }
-    if (iv && sub == 0)
-      bfinish(T, rf, ss, T.f[i], T.a[i], eps * T.loga[i], eps, T.f, T.fs, T.Lrow, i, eval, acc);
+    // the running maximum from the raw exponents (subtracting the reference
+    // is monotone, so max(y) - ref = max(y - ref) exactly), then the terms
+    float my = -INFINITY;
+#pragma unroll
+    for (int u = 0; u < kBRowU; ++u) {
+      if constexpr (ACC) {
+        const float2 pa = __fmul2_rn(ya[u], k2v), pb = __fmul2_rn(yb[u], k2v);
+        my = fmaxf(my, fmaxf(fmaxf(pa.x, pa.y), fmaxf(pb.x, pb.y)));
+      } else {
+        my = fmaxf(my, fmaxf(fmaxf(ya[u].x, ya[u].y), fmaxf(yb[u].x, yb[u].y)));
+      }
+    }
+    rr = fmaxf(rr, ref == 0.f ? my : my - ref);
+    if (rr > -INFINITY && needs_move(rr, ref)) move_ref2(rr, ref, S);
+    const bool r0 = ref == 0.f;
+    const float2 nr = f2(-ref, -ref);
+    if constexpr (ACC) {
+      // evaluation: terms 2^(p + q) added one group after another (few live
+      // registers; the order is fixed by the row's layout)
+      float2 e = f2(0.f, 0.f);
+#pragma unroll 2
+      for (int u = 0; u < kBRowU; ++u) {
+        const int g = g0 + u * LPR;
+        const float4 l = g < ng ? L4[g] : z4;
+        const float2 pa = __fmul2_rn(ya[u], k2v), pb = __fmul2_rn(yb[u], k2v);
+        const float2 qa = __fadd2_rn(__ffma2_rn(ya[u], k2v, f2(-pa.x, -pa.y)),
+                                     __ffma2_rn(ya[u], k2l, f2(l.x, l.y)));
+        const float2 qb = __fadd2_rn(__ffma2_rn(yb[u], k2v, f2(-pb.x, -pb.y)),
+                                     __ffma2_rn(yb[u], k2l, f2(l.z, l.w)));
+        e = __fadd2_rn(e, f2(ex2_pq(__fsub_rn(pa.x, ref), qa.x) + ex2_pq(__fsub_rn(pb.x, ref), qb.x),
+                             ex2_pq(__fsub_rn(pa.y, ref), qa.y) + ex2_pq(__fsub_rn(pb.y, ref), qb.y)));
+      }
+      S = __fadd2_rn(S, e);
+    } else {
+      float2 e[kBRowU];
+#pragma unroll
+      for (int u = 0; u < kBRowU; ++u)
+        e[u] = r0 ? __fadd2_rn(ex2_2(ya[u]), ex2_2(yb[u]))
+                  : __fadd2_rn(ex2_2(__fadd2_rn(ya[u], nr)), ex2_2(__fadd2_rn(yb[u], nr)));
+#pragma unroll
+      for (int w = 1; w < kBRowU; w *= 2)
+#pragma unroll
+        for (int u = 0; u + w < kBRowU; u += 2 * w) e[u] = __fadd2_rn(e[u], e[u + w]);
+      S = __fadd2_rn(S, e[0]);
+    }
+  }
+  ss = S.x + S.y;
+  rf = ref;
+}
+
+// Row half-step over rows [r0, r1): f_i <- f_i - eps L_i (Eq. foc_f, delta
+// form), g from buffer gi; eval: L only.  A row is reduced by a group of LPR
+// lanes (a function of m alone, so every row sums in the same order whatever
+// the gang); the rows go in chunks whose states pass through shared memory to
+// warp 0, which finishes a whole chunk with full warps (the finish is float64
+// work, slow on this GPU) while the other warps stream the next chunk.
+__device__ void brow_pass(const BatchTask& T, int r0, int r1, int gi, double eps, float k2,
+                          float k2lo, bool eval, BShared& sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int LPR = T.lpr, rpw = 32 / LPR, sub = lane & (LPR - 1), grp = lane / LPR;
+  const int rpwc = max(rpw, 4), CR = (kBThreads / 32) * rpwc;
+  const Split cs = T.gsp[gi];
+  int k = 0;
+  for (int q0 = r0; q0 < r1; q0 += CR, ++k) {
+    const int buf = k & 1;
+    for (int s = 0; s < rpwc; s += rpw) {
+      const int lr = wid * rpwc + s + grp;
+      const int i = q0 + lr;
+      float rf = 0.f, ss = 0.f;
+      if (i < r1) {
+        if (eval) brow_stream<true>(T, cs, i, sub, LPR, k2, k2lo, rf, ss);
+        else brow_stream<false>(T, cs, i, sub, LPR, k2, k2lo, rf, ss);
+      }
+      for (int o = LPR >> 1; o > 0; o >>= 1) {
+        const float r2 = __shfl_xor_sync(0xffffffffu, rf, o);
+        const float s2 = __shfl_xor_sync(0xffffffffu, ss, o);
+        lse2_merge(rf, ss, r2, s2);
+      }
+      if (sub == 0) {
+        sh.rref[buf][lr] = rf;
+        sh.rsum[buf][lr] = ss;
+      }
+    }
+    __syncthreads();
+    if (wid == 0) {
+      for (int lr = lane; lr < CR; lr += 32) {
+        const int i = q0 + lr;
+        if (i < r1)
+          bfinish(T, sh.rref[buf][lr], sh.rsum[buf][lr], T.fs.KL[i], T.f[i], eps * T.loga[i], eps,
+                  k2, T.f, T.fs, T.Lrow, i, eval);
+      }
+    }
   }
 }
 
-// Column half-step over columns [c0, c1): g'_j = g_j - eps L_j (Eq. foc_g,
-// delta form) from buffer gi into buffer 1 - gi (unless eval).  Threads over
-// columns (coalesced row segments); a range narrower than the CTA splits the
-// rows among R groups whose states merge in shared memory.
-__device__ void bcol_pass(const BatchTask& T, int c0, int c1, int gi, double eps, float k2,
-                          bool eval, float acc[2], BShared& sh) {
-  const int tid = threadIdx.x;
-  const int n = T.n, w = c1 - c0;
-  if (w <= 0) return;
-  // W columns x R row groups: the fewest terms per thread (each block of W
-  // columns adds a merge of R states), ties to the wider layout
-  int W = 32;
-  {
-    long long best = -1;
-    for (int Wc = 32; Wc <= kBThreads; Wc *= 2) {
-      const int Rc = kBThreads / Wc;
-      const long long blocks = (w + Wc - 1) / Wc;
-      const long long cost = blocks * (((long long)n + Rc - 1) / Rc + 8 * Rc);
-      if (best < 0 || cost <= best) {
-        best = cost;
-        W = Wc;
+// Partial log-sum-exp of the four columns j..j+3 over the 8-row blocks
+// b = rg, rg + 8, ... (rg: the warp's row group): exponents
+// ((A_i - K_j) - C_ij) k2 + AL_i k2, windowed references per column and
+// compensated pair sums (one compensated add per block of eight rows).
+template <bool ACC>
+__device__ __forceinline__ void bcol_stream(const BatchTask& T, const Split& os, int j, int c1,
+                                            int rg, float k2, float k2lo, float4& Rout,
+                                            float4& Sout) {
+  const int n = T.n;
+  const size_t pitch = (size_t)T.pitch;
+  const float4 K = *reinterpret_cast<const float4*>(os.K + j);
+  const float2 nK01 = f2(-K.x, -K.y), nK23 = f2(-K.z, -K.w), k2v = f2(k2, k2),
+               k2l = f2(k2lo, k2lo), m1 = f2(-1.f, -1.f);
+  const bool fullc = j + 4 <= c1;
+  const float* Cj = T.C + j;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  float ref[4] = {0.f, 0.f, 0.f, 0.f};
+  float rr[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
+  bool ref0 = true;
+  float2 Sa[2] = {f2(0.f, 0.f), f2(0.f, 0.f)}, Ca[2] = {f2(0.f, 0.f), f2(0.f, 0.f)};
+  for (int b = rg; 8 * b < n; b += kBThreads / 32) {
+    const int i0 = 8 * b;
+    const bool fullr = i0 + 8 <= n;
+    float4 c[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      c[u] = (fullr || i0 + u < n) ? __ldcg(reinterpret_cast<const float4*>(Cj + (size_t)(i0 + u) * pitch))
+                                   : z4;
+    const float4 a0 = *reinterpret_cast<const float4*>(T.fs.A + i0);
+    const float4 a1 = *reinterpret_cast<const float4*>(T.fs.A + i0 + 4);
+    const float4 l0 = *reinterpret_cast<const float4*>(T.fs.AL + i0);
+    const float4 l1 = *reinterpret_cast<const float4*>(T.fs.AL + i0 + 4);
+    const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const float lv[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+    // exponents as in the row pass: rounded once, or t kept for ACC
+    float2 ya[8], yb[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const float2 arr = f2(av[u], av[u]), alr = f2(lv[u], lv[u]);
+      const float2 ta = __ffma2_rn(f2(c[u].x, c[u].y), m1, __fadd2_rn(arr, nK01));
+      const float2 tb = __ffma2_rn(f2(c[u].z, c[u].w), m1, __fadd2_rn(arr, nK23));
+      if constexpr (ACC) {
+        ya[u] = ta;
+        yb[u] = tb;
+      } else {
+        ya[u] = __ffma2_rn(ta, k2v, __ffma2_rn(ta, k2l, alr));
+        yb[u] = __ffma2_rn(tb, k2v, __ffma2_rn(tb, k2l, alr));
       }
     }
+    if (!(fullr && fullc)) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const bool rv = i0 + u < n;
+        ya[u].x = (rv && j + 0 < c1) ? ya[u].x : -INFINITY;
+        ya[u].y = (rv && j + 1 < c1) ? ya[u].y : -INFINITY;
+        yb[u].x = (rv && j + 2 < c1) ? yb[u].x : -INFINITY;
+        yb[u].y = (rv && j + 3 < c1) ? yb[u].y : -INFINITY;
+      }
+    }
+    // running maxima from the raw exponents (max(y) - ref = max(y - ref))
+    float my[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      float2 pa = ya[u], pb = yb[u];
+      if constexpr (ACC) {
+        pa = __fmul2_rn(pa, k2v);
+        pb = __fmul2_rn(pb, k2v);
+      }
+      my[0] = fmaxf(my[0], pa.x);
+      my[1] = fmaxf(my[1], pa.y);
+      my[2] = fmaxf(my[2], pb.x);
+      my[3] = fmaxf(my[3], pb.y);
+    }
+    bool move = false;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      rr[q] = fmaxf(rr[q], ref0 ? my[q] : my[q] - ref[q]);
+      move |= rr[q] > -INFINITY && needs_move(rr[q], ref[q]);
+    }
+    if (move) {
+      kahan_fold2(Sa[0], Ca[0]);
+      kahan_fold2(Sa[1], Ca[1]);
+      move_ref(rr[0], ref[0], Sa[0].x);
+      move_ref(rr[1], ref[1], Sa[0].y);
+      move_ref(rr[2], ref[2], Sa[1].x);
+      move_ref(rr[3], ref[3], Sa[1].y);
+      ref0 = ref[0] == 0.f && ref[1] == 0.f && ref[2] == 0.f && ref[3] == 0.f;
+    }
+    const float2 na = f2(-ref[0], -ref[1]), nb = f2(-ref[2], -ref[3]);
+    if constexpr (ACC) {
+      // evaluation: terms 2^(p + q), one row after another
+      float2 ea = f2(0.f, 0.f), eb = f2(0.f, 0.f);
+#pragma unroll 2
+      for (int u = 0; u < 8; ++u) {
+        const float2 alr = f2(lv[u], lv[u]);
+        const float2 pa = __fmul2_rn(ya[u], k2v), pb = __fmul2_rn(yb[u], k2v);
+        const float2 qa = __fadd2_rn(__ffma2_rn(ya[u], k2v, f2(-pa.x, -pa.y)),
+                                     __ffma2_rn(ya[u], k2l, alr));
+        const float2 qb = __fadd2_rn(__ffma2_rn(yb[u], k2v, f2(-pb.x, -pb.y)),
+                                     __ffma2_rn(yb[u], k2l, alr));
+        ea = __fadd2_rn(ea, f2(ex2_pq(__fsub_rn(pa.x, ref[0]), qa.x), ex2_pq(__fsub_rn(pa.y, ref[1]), qa.y)));
+        eb = __fadd2_rn(eb, f2(ex2_pq(__fsub_rn(pb.x, ref[2]), qb.x), ex2_pq(__fsub_rn(pb.y, ref[3]), qb.y)));
+      }
+      kahan_add2(Sa[0], Ca[0], ea);
+      kahan_add2(Sa[1], Ca[1], eb);
+    } else {
+      float2 ea[8], eb[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        ea[u] = ex2_2(ref0 ? ya[u] : __fadd2_rn(ya[u], na));
+        eb[u] = ex2_2(ref0 ? yb[u] : __fadd2_rn(yb[u], nb));
+      }
+#pragma unroll
+      for (int w = 1; w < 8; w *= 2)
+#pragma unroll
+        for (int u = 0; u + w < 8; u += 2 * w) {
+          ea[u] = __fadd2_rn(ea[u], ea[u + w]);
+          eb[u] = __fadd2_rn(eb[u], eb[u + w]);
+        }
+      kahan_add2(Sa[0], Ca[0], ea[0]);
+      kahan_add2(Sa[1], Ca[1], eb[0]);
+    }
   }
-  const int R = kBThreads / W;
-  const int col = tid % W, rg = tid / W;
+  kahan_fold2(Sa[0], Ca[0]);
+  kahan_fold2(Sa[1], Ca[1]);
+  Rout = make_float4(ref[0], ref[1], ref[2], ref[3]);
+  Sout = make_float4(Sa[0].x, Sa[0].y, Sa[1].x, Sa[1].y);
+}
+
+__device__ __forceinline__ void lse_merge4(float4& R, float4& S, float4 r, float4 s) {
+  lse2_merge(R.x, S.x, r.x, s.x);
+  lse2_merge(R.y, S.y, r.y, s.y);
+  lse2_merge(R.z, S.z, r.z, s.z);
+  lse2_merge(R.w, S.w, r.w, s.w);
+}
+
+// Column half-step over columns [c0, c1) (c0 a multiple of 4): g'_j = g_j -
+// eps L_j (Eq. foc_g, delta form) from buffer gi into buffer 1 - gi.  Blocks
+// of 128 columns, four a lane; each warp is one of eight row groups (8-row
+// blocks, interleaved), whose states warp 0 merges in group order and
+// finishes while the others stream the next block.  The order of every sum
+// depends on n alone, not on the gang.
+__device__ void bcol_pass(const BatchTask& T, int c0, int c1, int gi, double eps, float k2,
+                          float k2lo, bool eval, BShared& sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const Split os = T.gsp[gi];
   const Split ns = T.gsp[1 - gi];
   const double* gcur = T.g[gi];
   double* gnew = T.g[1 - gi];
-  for (int jb = c0; jb < c1; jb += W) {
-    const int j = jb + col;
-    const bool jv = j < c1 && rg < R;
-    BLse s{0.f, -INFINITY, 0.f};
-    if (jv) {
-      const float Kj = os.K[j], ccj = os.KL[j] * k2;
-      const float* Cj = T.C + j;
-      int i = rg;
-      // eight rows per step, all loads issued before the arithmetic
-      for (; i + 7 * R < n; i += 8 * R) {
-        float c[8], av[8], al[8];
+  int k = 0;
+  for (int cb = c0; cb < c1; cb += 128, ++k) {
+    const int buf = k & 1;
+    const int j = cb + 4 * lane;
+    float4 R = make_float4(0.f, 0.f, 0.f, 0.f), S = R;
+    if (j < c1) {
+      if (eval) bcol_stream<true>(T, os, j, c1, wid, k2, k2lo, R, S);
+      else bcol_stream<false>(T, os, j, c1, wid, k2, k2lo, R, S);
+    }
+    sh.cref[buf][wid][lane] = R;
+    sh.csum[buf][wid][lane] = S;
+    __syncthreads();
+    if (wid == 0 && j < c1) {
+      R = sh.cref[buf][0][lane];
+      S = sh.csum[buf][0][lane];
+      for (int g2 = 1; g2 < kBThreads / 32; ++g2) lse_merge4(R, S, sh.cref[buf][g2][lane], sh.csum[buf][g2][lane]);
+      const float rv[4] = {R.x, R.y, R.z, R.w}, sv[4] = {S.x, S.y, S.z, S.w};
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int ii = i + u * R;
-          c[u] = Cj[(size_t)ii * T.pitch];
-          av[u] = __ldg(T.fs.A + ii);
-          al[u] = __ldg(T.fs.AL + ii);
-        }
-        float y[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const float t = __fsub_rn(__fsub_rn(av[u], Kj), c[u]);
-          y[u] = __fmaf_rn(t, k2, __fmaf_rn(al[u], k2, ccj));
-        }
-        blse_add4(s, y[0], y[1], y[2], y[3]);
-        blse_add4(s, y[4], y[5], y[6], y[7]);
-      }
-      for (; i < n; i += R) {
-        const float c = Cj[(size_t)i * T.pitch];
-        const float t = __fsub_rn(__fsub_rn(__ldg(T.fs.A + i), Kj), c);
-        const float y = __fmaf_rn(t, k2, __fmaf_rn(__ldg(T.fs.AL + i), k2, ccj));
-        blse_add4(s, y, -INFINITY, -INFINITY, -INFINITY);
+      for (int q = 0; q < 4; ++q) {
+        const int jj = j + q;
+        if (jj < c1)
+          bfinish(T, rv[q], sv[q], os.KL[jj], gcur[jj], eps * T.logb[jj], eps, k2, gnew, ns,
+                  T.Lcol, jj, eval);
       }
     }
-    sh.mr[tid] = (s.S > 0.f) ? s.ref : -INFINITY;
-    sh.ms[tid] = s.S;
-    __syncthreads();
-    if (rg == 0 && jv) {
-      float rf = sh.mr[col], ss = sh.ms[col];
-      for (int g2 = 1; g2 < R; ++g2) lse2_merge(rf, ss, sh.mr[g2 * W + col], sh.ms[g2 * W + col]);
-      bfinish(T, rf, ss, gcur[j], T.b[j], eps * T.logb[j], eps, gnew, ns, T.Lcol, j, eval, acc);
-    }
-    __syncthreads();
   }
 }
 
-// One task (problem) run by rank `rank` of its gang.
+// One task (problem) run by rank `rank` of its gang.  Gang-wide sums (the L1
+// test, the scores) are formed by every rank from the per-index arrays in one
+// fixed order, so they, and with them every decision, do not depend on G.
 __device__ void brun_task(const BatchTask& T, int rank, BShared& sh) {
   const int G = T.G, n = T.n, m = T.m;
   const int r0 = (int)((long long)n * rank / G), r1 = (int)((long long)n * (rank + 1) / G);
-  const int c0 = (int)((long long)m * rank / G), c1 = (int)((long long)m * (rank + 1) / G);
-  double* my = T.part + (size_t)rank * kBPart;
+  const int nq = (m + 3) >> 2;
+  const int c0 = 4 * (int)((long long)nq * rank / G);
+  const int c1 = min(m, 4 * (int)((long long)nq * (rank + 1) / G));
   int gi = 0, total = 0, iter = 0, status = 0, verify_rounds = 0, lev = 0;
   double row_l1 = 0.0, col_l1 = 0.0;
   bool have_row = false;
@@ -354,77 +504,65 @@ __device__ void brun_task(const BatchTask& T, int rank, BShared& sh) {
     status = 4;
     return false;
   };
-  // gang-wide sums of the partials (rank order)
-  auto gsum = [&](int k) {
-    double t = 0.0;
-    for (int q = 0; q < G; ++q) t += __ldcg(T.part + (size_t)q * kBPart + k);
-    return t;
-  };
-  auto publish = [&](double v[4], int base) {
-    bsum4(v, sh.red);
-    if (threadIdx.x == 0)
-      for (int k = 0; k < 4; ++k) my[base + k] = v[k];
-  };
-  auto publishf = [&](float v[2], int base) {
-    bsum2f(v, sh.redf);
-    if (threadIdx.x == 0) {
-      my[base] = (double)v[0];
-      my[base + 1] = (double)v[1];
-    }
+  auto numeric = [&]() { return *(volatile const unsigned*)T.flag != 0u; };
+  // sum_k w_k |expm1 L_k| over a whole side, in float (the test needs a few digits)
+  auto l1_side = [&](const float* L, const float* w, int len) -> double {
+    float v[1] = {0.f};
+    for (int k = threadIdx.x; k < len; k += kBThreads) v[0] += w[k] * fabsf(expm1f(L[k]));
+    bsum_all<1>(v, sh);
+    return (double)v[0];
   };
   for (lev = 0; lev < T.nlev && status == 0; ++lev) {
     const bool last = lev == T.nlev - 1;
     const double eps = T.eps[lev];
-    const float k2 = (float)(1.0 / (eps * 0.6931471805599453));
+    const double k2d = 1.0 / (eps * 0.6931471805599453);
+    const float k2 = (float)k2d, k2lo = (float)(k2d - (double)k2);
     if (last) t_last = gtime_ns();
     // splits of the carried potentials at this eps
-    for (int i = r0 + threadIdx.x; i < r1; i += kBThreads) bsplit(T, T.f[i], eps * T.loga[i], T.fs, i);
+    for (int i = r0 + threadIdx.x; i < r1; i += kBThreads) bsplit(T, T.f[i], eps * T.loga[i], k2, T.fs, i);
     for (int j = c0 + threadIdx.x; j < c1; j += kBThreads)
-      bsplit(T, T.g[gi][j], eps * T.logb[j], T.gsp[gi], j);
+      bsplit(T, T.g[gi][j], eps * T.logb[j], k2, T.gsp[gi], j);
     if (!sync()) break;
     // g_1 = f_0^{C,eps} (Algorithm 4.1 line 3 at the first iteration)
-    {
-      float v[2] = {0.f, 0.f};
-      bcol_pass(T, c0, c1, gi, eps, k2, false, v, sh);
-      publishf(v, 0);
-      if (!sync()) break;
-      if (gsum(1) > 0.0) {
-        status = 3;
-        break;
-      }
-      gi ^= 1;
+    bcol_pass(T, c0, c1, gi, eps, k2, k2lo, false, sh);
+    if (!sync()) break;
+    if (numeric()) {
+      status = 3;
+      break;
     }
+    gi ^= 1;
     double tol = last ? T.tol_last : T.tol_level;
     iter = 0;
     for (;;) {
-      float u[2] = {0.f, 0.f};
-      brow_pass(T, r0, r1, gi, eps, k2, false, u);   // f_k = g_k^{C,eps} (its numeric flags)
-      u[0] = 0.f;
+      brow_pass(T, r0, r1, gi, eps, k2, k2lo, false, sh);   // f_k = g_k^{C,eps}
       if (!sync()) break;
-      bcol_pass(T, c0, c1, gi, eps, k2, false, u, sh);   // f_k^{C,eps} and the L1 test
-      publishf(u, 0);
+      bcol_pass(T, c0, c1, gi, eps, k2, k2lo, false, sh);   // f_k^{C,eps}: the L1 test
       if (!sync()) break;
-      const double l1 = gsum(0);
+      const double l1 = l1_side(T.Lcol, T.bf, m);
       ++iter;
       ++total;
-      if (gsum(1) > 0.0) {
+      if (numeric()) {
         status = 3;
         break;
       }
       col_l1 = l1;
       if (l1 < tol) {
         if (!last) break;
-        // verify the pair (f_k, g_k): the row term of the L1 error
-        float e[2] = {0.f, 0.f};
-        brow_pass(T, r0, r1, gi, eps, k2, true, e);
-        publishf(e, 8);
+        // verify the pair (f_k, g_k): both terms of the L1 error with the
+        // unbiased exponential (the two passes read f_k, g_k and write
+        // different arrays: one barrier after both)
+        brow_pass(T, r0, r1, gi, eps, k2, k2lo, true, sh);
+        bcol_pass(T, c0, c1, gi, eps, k2, k2lo, true, sh);
         if (!sync()) break;
-        row_l1 = gsum(8);
+        row_l1 = l1_side(T.Lrow, T.af, n);
+        col_l1 = l1_side(T.Lcol, T.bf, m);
         have_row = true;
         ++verify_rounds;
         if (row_l1 + col_l1 < T.tol_verify || verify_rounds >= 4) break;
-        tol = 0.9 * (T.tol_verify - row_l1);
-        if (!(tol > 0.0)) tol = 0.1 * T.tol_verify;
+        // continue with the fast test's threshold scaled to what the
+        // verification found
+        tol = 0.9 * (T.tol_verify - row_l1) * (l1 / fmax(col_l1, 1e-300));
+        if (!(tol > 0.0) || tol > l1) tol = 0.5 * l1;
         have_row = false;
         continue;
       }
@@ -438,42 +576,43 @@ __device__ void brun_task(const BatchTask& T, int rank, BShared& sh) {
   const int levels = lev;
   if (status == 0) status = 1;
   if (status != 4) {
-    // scores of the returned pair (f, g[gi]) at the last eps (the column
-    // log-ratios are those of the last column pass)
+    // scores of the returned pair (f, g[gi]) at the last eps, from the
+    // log-ratios of the verification passes (unbiased exponential)
     const double eps = T.eps[max(0, min(levels, T.nlev) - 1)];
-    const float k2 = (float)(1.0 / (eps * 0.6931471805599453));
+    const double k2d = 1.0 / (eps * 0.6931471805599453);
+    const float k2 = (float)k2d, k2lo = (float)(k2d - (double)k2);
+    bool ok = true;
     if (!have_row) {
-      float e[2] = {0.f, 0.f};
-      brow_pass(T, r0, r1, gi, eps, k2, true, e);
-      publishf(e, 8);
-      if (sync()) row_l1 = gsum(8);
+      brow_pass(T, r0, r1, gi, eps, k2, k2lo, true, sh);
+      bcol_pass(T, c0, c1, gi, eps, k2, k2lo, true, sh);
+      ok = sync();
+      if (ok) row_l1 = l1_side(T.Lrow, T.af, n);
     }
-    // float64 sums: <f,a>, sum pi, <pi1-a,f> | <g,b>, <pi^T1-b,g>, column L1,
-    // <h,b> with h = f^{C,eps} from the last column half-step (other buffer)
-    double v[4] = {0.0, 0.0, 0.0, 0.0}, u[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int i = r0 + threadIdx.x; i < r1; i += kBThreads) {
-      const double e = (double)expm1f(T.Lrow[i]), ai = T.a[i], fi = T.f[i];
-      v[0] += ai * fi;
-      v[1] += ai * (1.0 + e);
-      v[2] += ai * e * fi;
-    }
-    for (int j = c0 + threadIdx.x; j < c1; j += kBThreads) {
-      const double e = (double)expm1f(T.Lcol[j]), bj = T.b[j], gj = T.g[gi][j];
-      u[0] += bj * gj;
-      u[1] += bj * e * gj;
-      u[2] += bj * fabs(e);
-      u[3] += bj * T.g[1 - gi][j];
-    }
-    if (status != 4 && sync()) {   // every rank has read the partials above
-      publish(v, 0);
-      publish(u, 12);
-    }
-    if (status != 4 && sync()) {
-      const double fa = gsum(0), sumpi = gsum(1), gap_f = gsum(2);
-      const double gb = gsum(12), gap_g = gsum(13), cl1 = gsum(14), sum_bh = gsum(15);
+    if (ok) {
+      // float64 sums, whole problem, fixed order: <f,a>, sum pi, <pi1-a,f>,
+      // <g,b>, <pi^T1-b,g>, column L1, <h,b> with h = f^{C,eps} from the
+      // last column half-step (the other buffer)
+      double v[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      for (int i = threadIdx.x; i < n; i += kBThreads) {
+        const double e = (double)expm1f(T.Lrow[i]), ai = T.a[i], fi = T.f[i];
+        v[0] += ai * fi;
+        v[1] += ai * (1.0 + e);
+        v[2] += ai * e * fi;
+      }
+      const double *gc = T.g[gi], *gh = T.g[1 - gi];
+      for (int j = threadIdx.x; j < m; j += kBThreads) {
+        const double e = (double)expm1f(T.Lcol[j]), bj = T.b[j], gj = gc[j];
+        v[3] += bj * gj;
+        v[4] += bj * e * gj;
+        v[5] += bj * fabs(e);
+        v[6] += bj * gh[j];
+      }
+      bsum_all<7>(v, sh);
+      const double fa = v[0], sumpi = v[1], gap_f = v[2];
+      const double gb = v[3], gap_g = v[4], cl1 = v[5], sum_bh = v[6];
       const double c = 0.5 * (gb - fa);
       for (int i = r0 + threadIdx.x; i < r1; i += kBThreads) T.f_out[i] = T.f[i] + c;
-      for (int j = c0 + threadIdx.x; j < c1; j += kBThreads) T.g_out[j] = T.g[gi][j] - c;
+      for (int j = c0 + threadIdx.x; j < c1; j += kBThreads) T.g_out[j] = gc[j] - c;
       if (rank == 0 && threadIdx.x == 0) {
         BatchOut* o = T.out;
         o->row_l1 = row_l1;
@@ -483,6 +622,8 @@ __device__ void brun_task(const BatchTask& T, int rank, BShared& sh) {
         o->dual_gap = gap_f + gap_g + eps * (sumpi - 1.0);
         o->gauge = c;
       }
+    } else {
+      status = 4;
     }
   }
   if (rank == 0 && threadIdx.x == 0) {
@@ -524,6 +665,7 @@ __global__ void __launch_bounds__(256) batch_weights_kernel(const BatchIn* __res
   const double* win = side_b ? P.win_b : P.win_a;
   double* w = side_b ? P.b : P.a;
   double* lw = side_b ? P.logb : P.loga;
+  float* wf = side_b ? P.bf : P.af;
   __shared__ double sh[8];
   double s = 0.0;
   unsigned nb = 0;
@@ -544,6 +686,7 @@ __global__ void __launch_bounds__(256) batch_weights_kernel(const BatchIn* __res
   for (int i = threadIdx.x; i < len; i += 256) {
     const double v = win[i] / tot;
     w[i] = v;
+    wf[i] = (float)v;
     lw[i] = v > 0.0 ? log(v) : -INFINITY;
   }
 }
@@ -600,7 +743,7 @@ __global__ void __launch_bounds__(256) batch_cost_fill_kernel(const BatchIn* __r
     for (int j = lane; j < P.pitch; j += 32) {
       float out = 0.f;
       if (j < P.m) {
-        double v = P.givenC ? (double)P.Cin[(size_t)i * P.m + j]
+        double v = P.givenC ? (double)P.Cin[P.trans ? (size_t)j * P.n + i : (size_t)i * P.m + j]
                             : bsqdist(P.X + (size_t)i * P.d, P.Y + (size_t)j * P.d, P.d);
         if (norm) v = __ddiv_rn(v, cmax);
         out = __double2float_rn(v);

@@ -8,9 +8,8 @@ namespace eotk {
 
 constexpr int kBThreads = 256;
 constexpr int kBMaxLev = 64;
-constexpr int kBPart = 16;                // partial sums per rank: [0..3] column pass,
-                                          // [8..11] row evaluation, [12..15] scores
 constexpr int kBMaxGang = 32;
+constexpr int kBRowU = 8;                 // 4-column groups a lane loads per step (row pass)
 constexpr unsigned long long kBWaitNs = 30000000000ull;   // 30 s bound of a gang wait
 
 struct BatchOut {
@@ -22,8 +21,10 @@ struct BatchOut {
 
 struct BatchTask {
   int n, m, pitch, nlev, G, max_iter;
+  int lpr;                        // lanes per row of the row pass (batch_lpr(m))
   const float* C;                 // n x pitch
   const double *a, *b, *loga, *logb;
+  const float *af, *bf;           // the weights in float32 (L1 sums)
   double* f;                      // n
   double* g[2];                   // m, double-buffered
   Split fs;                       // split arrays of f
@@ -31,7 +32,7 @@ struct BatchTask {
   float *Lrow, *Lcol;
   double *f_out, *g_out;
   unsigned* bar;                  // [2]: arrivals, generation
-  double* part;                   // [G][kBPart]
+  unsigned* flag;                 // numeric flag of the problem (0 / 1)
   BatchOut* out;
   double tol_level, tol_last, tol_verify;
   double qscale, qinv, pot_bound;
@@ -41,15 +42,28 @@ struct BatchTask {
 
 struct BatchIn {
   int n, m, d, pitch, normalize, givenC;
+  int trans;                   // given cost read transposed (Cin is m x n)
   const float *X, *Y;          // points (d > 0)
   const float* Cin;            // given cost, n x m (d == 0)
   const double *win_a, *win_b; // weights as given
   double *a, *b, *loga, *logb; // normalised weights and their logs
+  float *af, *bf;              // the normalised weights in float32
   float* C;                    // n x pitch
   unsigned long long* cmax;    // float64 bits of max C (or max |C|)
   unsigned* bad;               // [0] weights, [1] cost
 };
 
+
+// Lanes that reduce one row in the row pass: the smallest power of two (at
+// most 32) for which a lane holds at most kBRowU of the row's 4-column groups
+// per step.  A function of m alone: every row sums in the same order whatever
+// the gang.
+inline __host__ __device__ int batch_lpr(int m) {
+  const int ng = (m + 3) >> 2;
+  int L = 1;
+  while (L < 32 && L * kBRowU < ng) L *= 2;
+  return L;
+}
 
 int batch_ctas_per_sm();
 cudaError_t launch_batch_setup(const BatchIn* d_in, int count, int maxrows, cudaStream_t s);

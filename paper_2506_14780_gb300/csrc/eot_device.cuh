@@ -37,6 +37,32 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
+// 2^(p + q) for the evaluation passes that verify a result: p a float32
+// exponent (log2 units), q a small correction carried beside it (|q| < 1/4;
+// the rounding error of p and the low parts of the potentials).  Range
+// reduction p = n + f with n = rint(p) (f exact), x = (f + q) ln 2, and the
+// Taylor series of e^x to degree 7 (|x| < 0.53: truncation below 1e-7, mostly
+// below 1e-8), Horner in float32 with round-to-nearest, so that its rounding
+// errors average out over a sum.  Two reasons for not using the iteration's
+// arithmetic here: the hardware approximation ex2.approx is biased by a few
+// 1e-8 relative with the same sign for every term (measured: -2e-8 to -5e-8
+// for p in [-1, 0] to [-30, 0]), and an evaluation that repeated the
+// iteration's rounding of each exponent would not see that rounding's effect
+// on the marginals; either blind spot hides ~1e-7 of L1, a tenth of 1e-6.
+__device__ __forceinline__ float ex2_pq(float p, float q) {
+  if (!(p >= -126.f)) return 0.f;   // -inf (masked terms) and results below the normal range
+  const float n = fminf(rintf(p), 127.f), x = ((p - n) + q) * 0.6931471805599453f;
+  float r = 1.f / 5040.f;
+  r = fmaf(r, x, 1.f / 720.f);
+  r = fmaf(r, x, 1.f / 120.f);
+  r = fmaf(r, x, 1.f / 24.f);
+  r = fmaf(r, x, 1.f / 6.f);
+  r = fmaf(r, x, 0.5f);
+  r = fmaf(r, x, 1.f);
+  r = fmaf(r, x, 1.f);
+  return r * __int_as_float(((int)n + 127) << 23);   // exact scaling by 2^n
+}
+
 // The exact part of the exponent (see the header comment).
 //   C: cost, K: M - sH (output-side shift), A: uH + M (reduction-side), returns
 //   tH - l ; the caller adds uL and scales.

@@ -77,7 +77,12 @@ struct Prob {
   const double *a, *b;     // weights
   const double *loga, *logb;
   double eps;
-  float k2;                // log2(e) / eps
+  float k2;                // log2(e) / eps, rounded to float32
+  float k2lo;              // log2(e) / eps - k2.  The iteration's passes use k2 alone: they
+                           // solve the problem at eps' = 1/(k2 ln 2), within 6e-8 relative
+                           // of eps (a marginal error at eps of that relative size times a
+                           // row's entropy).  The evaluation passes that verify a result
+                           // add t k2lo, so the verification is at eps itself.
   float M;                 // magic constant 1.5 * 2^(23-q)
   double qscale, qinv;     // 2^q, 2^-q
   double* f[2];

@@ -38,6 +38,7 @@ __global__ void level_setup_kernel(Prob* P, double eps, float k2, double tol, in
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   P->eps = eps;
   P->k2 = k2;
+  P->k2lo = (float)(1.0 / (eps * 0.6931471805599453) - (double)k2);
   State* st = P->st;
   st->iter = 0;
   st->done = 0;

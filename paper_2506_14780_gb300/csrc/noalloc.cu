@@ -211,6 +211,7 @@ extern "C" eot_status eot_ctransform_noalloc(eot_side side, int32_t n, int32_t m
   P.pot_bound = std::ldexp(1.0, 22 - q) / 2.0 - cm;
   P.eps = eps;
   P.k2 = (float)(1.0 / (eps * std::log(2.0)));
+  P.k2lo = (float)(1.0 / (eps * std::log(2.0)) - (double)P.k2);
   double* redbuf = col ? P.f[0] : P.g[0];
   double* outbuf = col ? P.g[0] : P.f[0];
   NA_TRY(cudaMemcpyAsync(redbuf, pot, nred * sizeof(double), cudaMemcpyDeviceToDevice, s));

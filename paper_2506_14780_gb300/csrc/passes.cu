@@ -34,7 +34,7 @@ namespace eotk {
 // Column pass.  VEC = 4: m % 4 == 0 (16-byte aligned rows), float4 loads;
 // VEC = 1: scalar loads with column bounds checks.
 // ---------------------------------------------------------------------------
-template <int VEC>
+template <int VEC, bool ACC>
 __global__ void __launch_bounds__(kThreads) col_pass_kernel(const Prob* __restrict__ PP, int mode) {
   const Prob& P = *PP;
   State* st = P.st;
@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kThreads) col_pass_kernel(const Prob* __restri
   const int j0 = cb * kColTile + lane * 4;
   const int i_beg = stripe * P.rows_per_stripe;
   const int nrows = min(n, i_beg + P.rows_per_stripe) - i_beg;
-  const float k2 = P.k2;
+  const float k2 = P.k2, k2lo = P.k2lo;
 
   float K[4], cc0[4], cc[4], ref[4], run[4], S[4];
   bool valid[4];
@@ -118,7 +118,9 @@ __global__ void __launch_bounds__(kThreads) col_pass_kernel(const Prob* __restri
         const bool rvalid = r0 + 8 * u < nrows;
 #pragma unroll
         for (int c = 0; c < 4; ++c)
-          t[u][c] = rvalid ? __fadd_rn(split_exponent(cv[u][c], K[c], av[u]), alv[u]) : -INFINITY;
+          t[u][c] = rvalid ? (ACC ? split_exponent(cv[u][c], K[c], av[u])
+                                  : __fadd_rn(split_exponent(cv[u][c], K[c], av[u]), alv[u]))
+                           : -INFINITY;
       }
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
@@ -136,7 +138,19 @@ __global__ void __launch_bounds__(kThreads) col_pass_kernel(const Prob* __restri
 #pragma unroll
           for (int u = 0; u < 4; ++u) y[u] = __fmaf_rn(t[u][c], k2, cc[c]);
         }
-        S[c] += (ex2_approx(y[0]) + ex2_approx(y[1])) + (ex2_approx(y[2]) + ex2_approx(y[3]));
+        if (ACC) {
+          // evaluation: the exponent as p + q (ex2_pq), p = t k2 rounded, q its
+          // exact rounding error plus the low parts
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float pz = __fmul_rn(t[u][c], k2);   // not contracted with its uses
+            const float qz = __fmaf_rn(t[u][c], k2, -pz) +
+                             __fmaf_rn(t[u][c], k2lo, __fmaf_rn(alv[u], k2, cc0[c]));
+            S[c] += ex2_pq(__fsub_rn(pz, ref[c]), qz);
+          }
+        } else {
+          S[c] += (ex2_approx(y[0]) + ex2_approx(y[1])) + (ex2_approx(y[2]) + ex2_approx(y[3]));
+        }
       }
     }
   }
@@ -224,7 +238,7 @@ __global__ void __launch_bounds__(kThreads) col_pass_kernel(const Prob* __restri
 // ---------------------------------------------------------------------------
 // Row pass.
 // ---------------------------------------------------------------------------
-template <int VEC>
+template <int VEC, bool ACC>
 __global__ void __launch_bounds__(kThreads) row_pass_kernel(const Prob* __restrict__ PP, int mode) {
   const Prob& P = *PP;
   State* st = P.st;
@@ -247,7 +261,7 @@ __global__ void __launch_bounds__(kThreads) row_pass_kernel(const Prob* __restri
   const int i0 = rb * kRowTile + wid * kRowsPerWarp;
   const int c_beg = seg * P.cols_per_seg;
   const int c_end = min(m, c_beg + P.cols_per_seg);
-  const float k2 = P.k2;
+  const float k2 = P.k2, k2lo = P.k2lo;
 
   float K[kRowsPerWarp], cc0[kRowsPerWarp], cc[kRowsPerWarp], ref[kRowsPerWarp],
       run[kRowsPerWarp], S[kRowsPerWarp];
@@ -315,7 +329,8 @@ __global__ void __launch_bounds__(kThreads) row_pass_kernel(const Prob* __restri
         float t[4], y[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          t[c] = (cvld[c] && rv[r]) ? __fadd_rn(split_exponent(cv[r][c], K[r], ca[c]), cal[c])
+          t[c] = (cvld[c] && rv[r]) ? (ACC ? split_exponent(cv[r][c], K[r], ca[c])
+                                           : __fadd_rn(split_exponent(cv[r][c], K[r], ca[c]), cal[c]))
                                     : -INFINITY;
           y[c] = __fmaf_rn(t[c], k2, cc[r]);
         }
@@ -330,7 +345,18 @@ __global__ void __launch_bounds__(kThreads) row_pass_kernel(const Prob* __restri
 #pragma unroll
           for (int c = 0; c < 4; ++c) y[c] = __fmaf_rn(t[c], k2, cc[r]);
         }
-        S[r] += (ex2_approx(y[0]) + ex2_approx(y[1])) + (ex2_approx(y[2]) + ex2_approx(y[3]));
+        if (ACC) {
+          // evaluation: p + q as in the column pass
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const float pz = __fmul_rn(t[c], k2);
+            const float qz = __fmaf_rn(t[c], k2, -pz) +
+                             __fmaf_rn(t[c], k2lo, __fmaf_rn(cal[c], k2, cc0[r]));
+            S[r] += ex2_pq(__fsub_rn(pz, ref[r]), qz);
+          }
+        } else {
+          S[r] += (ex2_approx(y[0]) + ex2_approx(y[1])) + (ex2_approx(y[2]) + ex2_approx(y[3]));
+        }
       }
     }
   }
@@ -464,23 +490,30 @@ static bool stream_ok(const Prob& hP, bool col) {
   return (col ? hP.sk_gcol : hP.sk_grow) > 0 && hP.has_tmC;
 }
 
+// The evaluation passes (MODE_EVAL: the verification of a returned pair and
+// its scores) run on the striped kernels with the unbiased exponential.
 cudaError_t launch_col_pass(const Prob* dP, const Prob& hP, int mode, cudaStream_t s) {
-  if (stream_ok(hP, true)) return launch_stream_pass(dP, hP, true, mode, s);
+  const bool acc = mode == MODE_EVAL;
+  if (!acc && stream_ok(hP, true)) return launch_stream_pass(dP, hP, true, mode, s);
   dim3 grid(hP.ncolblk, hP.nstripe);
-  if (hP.m % 4 == 0 && (reinterpret_cast<uintptr_t>(hP.C) & 15u) == 0)
-    col_pass_kernel<4><<<grid, kThreads, 0, s>>>(dP, mode);
-  else
-    col_pass_kernel<1><<<grid, kThreads, 0, s>>>(dP, mode);
+  const bool v4 = hP.m % 4 == 0 && (reinterpret_cast<uintptr_t>(hP.C) & 15u) == 0;
+  if (v4 && acc) col_pass_kernel<4, true><<<grid, kThreads, 0, s>>>(dP, mode);
+  else if (v4) col_pass_kernel<4, false><<<grid, kThreads, 0, s>>>(dP, mode);
+  else if (acc) col_pass_kernel<1, true><<<grid, kThreads, 0, s>>>(dP, mode);
+  else col_pass_kernel<1, false><<<grid, kThreads, 0, s>>>(dP, mode);
   return cudaGetLastError();
 }
 
 cudaError_t launch_row_pass(const Prob* dP, const Prob& hP, int mode, cudaStream_t s) {
-  if (stream_ok(hP, false)) return launch_stream_pass(dP, hP, false, mode, s);
+  const bool acc = mode == MODE_EVAL;
+  if (!acc && stream_ok(hP, false)) return launch_stream_pass(dP, hP, false, mode, s);
   dim3 grid(hP.nrowblk, hP.nseg);
-  if (hP.m % 4 == 0 && (reinterpret_cast<uintptr_t>(hP.C) & 15u) == 0 && hP.cols_per_seg % 4 == 0)
-    row_pass_kernel<4><<<grid, kThreads, 0, s>>>(dP, mode);
-  else
-    row_pass_kernel<1><<<grid, kThreads, 0, s>>>(dP, mode);
+  const bool v4 = hP.m % 4 == 0 && (reinterpret_cast<uintptr_t>(hP.C) & 15u) == 0 &&
+                  hP.cols_per_seg % 4 == 0;
+  if (v4 && acc) row_pass_kernel<4, true><<<grid, kThreads, 0, s>>>(dP, mode);
+  else if (v4) row_pass_kernel<4, false><<<grid, kThreads, 0, s>>>(dP, mode);
+  else if (acc) row_pass_kernel<1, true><<<grid, kThreads, 0, s>>>(dP, mode);
+  else row_pass_kernel<1, false><<<grid, kThreads, 0, s>>>(dP, mode);
   return cudaGetLastError();
 }
 

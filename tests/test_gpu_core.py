@@ -210,7 +210,11 @@ def test_solve_small_parity(pkg, ell):
     ref = O.continuation(C, prob.a, prob.b, prob.eps, tol=1e-13, eps_start=1e-1, ell=0)
     fr, gr = O.gauge_normalize(ref.f, ref.g, prob.a, prob.b)
     assert np.abs(f - fr).max() <= 1e-5 * prob.eps * 50
-    assert abs(res["l1_marginal"] - ev["l1"]) <= 2e-7 + 0.1 * ev["l1"]
+    # the reported L1 comes from evaluation passes at eps itself with an
+    # unbiased exponential: it agrees with the float64 evaluation up to the
+    # float32 rounding noise of the terms (no systematic part)
+    d = res["l1_marginal"] - ev["l1"]
+    assert abs(d) <= 3e-8 + 0.25 * ev["l1"], (res["l1_marginal"], ev["l1"])
     assert abs(res["q_dual"] - ev["q_dual"]) <= 1e-9 + 1e-6 * abs(ev["q_dual"])
 
 
@@ -218,14 +222,15 @@ def test_plain_sinkhorn_many_tiles(pkg):
     """Plain Sinkhorn over a cost of many tiles with ragged edges (the
     cooperative iteration loop when the rows are 16-byte aligned): the oracle
     scores the returned pair, and the iteration count of the last level equals
-    the oracle's Sinkhorn on the same float32 cost from the same start up to
-    the rounding of the last test."""
+    the oracle's Sinkhorn on the same float32 cost from the same start, run to
+    the device's stop target on the last level (0.75 tol, the margin for the
+    float32 test), up to the rounding of the last test."""
     prob = W.gaussian_mixture(640, 804, seed=9, eps=1e-2)
     f, g, res = pkg.solve(prob, tol=1e-6, ell=0, eps_start=0.0, max_iter=100000)
     assert res["return_status"] == pkg.EOT_OK, res
     C, ev = _score(prob, f, g, prob.eps)
     assert ev["l1"] <= 1e-6, ev
-    ref = O.sinkhorn(C, prob.a, prob.b, prob.eps, tol=1e-6, max_iter=100000)
+    ref = O.sinkhorn(C, prob.a, prob.b, prob.eps, tol=0.75e-6, max_iter=100000)
     assert abs(res["iters"] - ref.iters) <= max(3, ref.iters // 50), (res["iters"], ref.iters)
     fr, gr = O.gauge_normalize(ref.f, ref.g, prob.a, prob.b)
     _, rho2 = O.spectral_modes_dense(ref.f, ref.g, C, prob.a, prob.b, prob.eps, 1)

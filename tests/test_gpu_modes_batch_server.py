@@ -93,12 +93,78 @@ def test_batch_same_alone_and_in_mix(pkg):
         C = O.sq_euclidean_cost(p.X, p.Y, normalize=True).astype(np.float32).astype(np.float64)
         assert res[k].status == pkg.EOT_OK, res[k].status
         ev = O.evaluate(fs[k], gs[k], C, p.a, p.b, p.eps)
-        assert ev["l1"] <= 1e-6 and abs(ev["l1"] - res[k].l1_marginal) <= 2e-7, (ev, res[k].l1_marginal)
+        assert ev["l1"] <= 1e-6 and -(1e-8 + 0.03 * ev["l1"]) <= (
+            res[k].l1_marginal - ev["l1"]) <= 1e-7 + 0.3 * ev["l1"], (ev, res[k].l1_marginal)
         f1, g1, r1 = pkg.solve(p, tol=1e-6, max_iter=200000)
         assert r1["return_status"] == pkg.EOT_OK
         assert O.evaluate(f1, g1, C, p.a, p.b, p.eps)["l1"] <= 1e-6
         # both approximate the same optimum (gauge <f,a> = <g,b> in both)
         assert np.abs(f1 - fs[k]).max() <= 1e-3 * p.eps
+
+
+def test_batch_result_independent_of_gang_size(pkg, monkeypatch):
+    """Every output is computed whole by one CTA in an order set by the problem's
+    shape, and the gang-wide sums are formed in one fixed order: a problem's
+    result is bit for bit the same on any number of CTAs.  Shapes: rows not a
+    multiple of 8, columns not a multiple of 4, narrow (m < 128) and wide rows,
+    tall and short problems."""
+    shapes = [(77, 61), (300, 1030), (1203, 207), (96, 700), (513, 129)]
+    probs = [W.uniform_square(n, m, d=2, seed=20 + k, eps=[2e-2, 5e-3, 1e-2, 3e-3, 8e-3][k])
+             for k, (n, m) in enumerate(shapes)]
+    keep = []
+    ps = [pkg.make_problem(p.a, p.b, X=p.X, Y=p.Y, eps=p.eps, normalize_cost=True, keep=keep)
+          for p in probs]
+    o = pkg.default_options(tol=1e-6, max_iter=200000, eps_start=1e-1)
+    outs = []
+    for gang in ("1", "2", "8", "32", None):
+        if gang is None:
+            monkeypatch.delenv("EOT_BATCH_GANG", raising=False)
+        else:
+            monkeypatch.setenv("EOT_BATCH_GANG", gang)
+        fs = [np.zeros(p.n) for p in probs]
+        gs = [np.zeros(p.m) for p in probs]
+        st, res = pkg.eot_solve_batch(ps, o, fs, gs)
+        assert st == pkg.EOT_OK, (gang, pkg.last_error(), [r.status for r in res])
+        outs.append((fs, gs, [r.total_iters for r in res], [r.l1_marginal for r in res]))
+    f0, g0, it0, l10 = outs[0]
+    for fs, gs, its, l1s in outs[1:]:
+        assert its == it0 and l1s == l10
+        for k in range(len(probs)):
+            assert np.array_equal(fs[k], f0[k]) and np.array_equal(gs[k], g0[k]), k
+    for k, p in enumerate(probs):
+        C = O.sq_euclidean_cost(p.X, p.Y, normalize=True).astype(np.float32).astype(np.float64)
+        assert O.evaluate(f0[k], g0[k], C, p.a, p.b, p.eps)["l1"] <= 1e-6
+
+
+def test_batch_tall_problems_given_cost(pkg):
+    """Problems with more rows than columns run transposed inside the batch
+    (given cost read transposed, points and weights swapped): the returned
+    potentials are in the caller's roles and solve the problem."""
+    rng = np.random.default_rng(5)
+    n, m, eps = 150, 41, 1e-2
+    C = rng.random((n, m)).astype(np.float32)
+    a = rng.dirichlet(np.ones(n))
+    b = rng.dirichlet(np.ones(m))
+    pts = W.uniform_square(333, 70, d=3, seed=9, eps=4e-3)
+    keep = []
+    ps = [pkg.make_problem(a, b, C=C, eps=eps, keep=keep),
+          pkg.make_problem(pts.a, pts.b, X=pts.X, Y=pts.Y, eps=pts.eps, normalize_cost=True,
+                           keep=keep)]
+    o = pkg.default_options(tol=1e-6, max_iter=200000, eps_start=1e-1)
+    fs = [np.zeros(n), np.zeros(pts.n)]
+    gs = [np.zeros(m), np.zeros(pts.m)]
+    st, res = pkg.eot_solve_batch(ps, o, fs, gs)
+    assert st == pkg.EOT_OK, pkg.last_error()
+    Cp = O.sq_euclidean_cost(pts.X, pts.Y, normalize=True).astype(np.float32).astype(np.float64)
+    for (f, g, Ck, ak, bk, ek, r) in ((fs[0], gs[0], C.astype(np.float64), a, b, eps, res[0]),
+                                       (fs[1], gs[1], Cp, pts.a, pts.b, pts.eps, res[1])):
+        ev = O.evaluate(f, g, Ck, ak, bk, ek)
+        assert ev["l1"] <= 1e-6 and -(1e-8 + 0.03 * ev["l1"]) <= (
+            r.l1_marginal - ev["l1"]) <= 1e-7 + 0.3 * ev["l1"], (ev, r.l1_marginal)
+        assert abs(f @ ak - g @ bk) <= 1e-9 * max(1.0, abs(f @ ak))   # gauge <f,a> = <g,b>
+        ref = O.sinkhorn(Ck, ak, bk, ek, tol=1e-12, max_iter=200000)
+        fr, gr = O.gauge_normalize(ref.f, ref.g, ak, bk)
+        assert np.abs(f - fr).max() <= 1e-3 * ek and np.abs(g - gr).max() <= 1e-3 * ek
 
 
 def test_batch_rejects_bad_member(pkg):
