@@ -1502,6 +1502,11 @@ static eot_status run_batch(int count, const eot_problem* probs, const eot_optio
       while (G < cap && task_ns(M, est_it[k], n, m, G) > target &&
              task_ns(M, est_it[k], n, m, 2 * G) < task_ns(M, est_it[k], n, m, G))
         G *= 2;
+      // and at most 1.25 MB of a cost per CTA: more of a problem's cost stays
+      // in L2 between its half-steps (the mixed 512-problem batch: 0.49 s per
+      // call without this floor, 0.46 s with it; 0.53 s at 160 KB, where the
+      // gang barriers cost more than the reuse gains)
+      while (G < cap && (double)G * kBCostPerCta < 4.0 * (double)n * (double)m) G *= 2;
       pl[k].G = G;
     }
   }

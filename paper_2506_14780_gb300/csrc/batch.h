@@ -10,6 +10,7 @@ constexpr int kBThreads = 256;
 constexpr int kBMaxLev = 64;
 constexpr int kBMaxGang = 32;
 constexpr int kBRowU = 8;                 // 4-column groups a lane loads per step (row pass)
+constexpr double kBCostPerCta = 1.25 * 1024 * 1024;   // floor of the gang sizes: cost bytes per CTA
 constexpr unsigned long long kBWaitNs = 30000000000ull;   // 30 s bound of a gang wait
 
 struct BatchOut {
