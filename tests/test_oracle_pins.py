@@ -401,3 +401,42 @@ def test_continuation_sknr_beats_sk_iterations():
     f1, g1 = O.gauge_normalize(sk.f, sk.g, p.a, p.b)
     f2, g2 = O.gauge_normalize(nr.f, nr.g, p.a, p.b)
     assert np.abs(f1 - f2).max() < 1e-5 * 2e-3 * 1e3
+
+
+def test_transposed_problem_has_the_transposed_coupling():
+    """Sinkhorn is symmetric in the two sides (Eq. foc_f / foc_g): the problem
+    (C^T, b, a) has the coupling pi^T and the potentials (g, f) up to the gauge.
+    The batched solver runs problems with more rows than columns this way."""
+    p = W.gaussian_mixture(60, 45, seed=3, eps=5e-2)
+    C = O.sq_euclidean_cost(p.X, p.Y, normalize=True)
+    r1 = O.sinkhorn(C, p.a, p.b, p.eps, tol=1e-13, max_iter=200000)
+    r2 = O.sinkhorn(C.T, p.b, p.a, p.eps, tol=1e-13, max_iter=200000)
+    P1 = O.plan(r1.f, r1.g, C, p.a, p.b, p.eps)
+    P2 = O.plan(r2.f, r2.g, C.T, p.b, p.a, p.eps)
+    assert np.abs(P1 - P2.T).max() <= 1e-12
+    f1, g1 = O.gauge_normalize(r1.f, r1.g, p.a, p.b)
+    g2, f2 = O.gauge_normalize(r2.f, r2.g, p.b, p.a)
+    assert np.abs(f1 - f2).max() <= 1e-9 * p.eps and np.abs(g1 - g2).max() <= 1e-9 * p.eps
+
+
+def test_rounded_inverse_eps_solves_a_nearby_problem():
+    """A float32 iteration forms every exponent as (f + g + eps log w - C) k2 with
+    k2 = 1/(eps ln 2) rounded, k2 = (1 + d)/(eps ln 2): it iterates Sinkhorn for
+    the weights w^(1+d) at eps' = eps/(1 + d).  At eps the row marginals of its
+    pair are off by d times the entropy of each row's conditional coupling (to
+    first order in d), and the columns by the same total: the size of the error
+    that the iteration's own test cannot see."""
+    p = W.uniform_square(120, 90, seed=3, eps=2e-2)
+    C = O.sq_euclidean_cost(p.X, p.Y, normalize=True)
+    eps, d = 2e-2, 1e-5
+    a2, b2 = p.a ** (1 + d), p.b ** (1 + d)
+    # the raised weights do not balance (sum a^(1+d) != sum b^(1+d)): the
+    # iteration settles to the balance error, far below what is measured here
+    r = O.sinkhorn(C, a2, b2, eps / (1 + d), tol=1e-11, max_iter=3000)
+    ev = O.evaluate(r.f, r.g, C, p.a, p.b, eps)
+    P = O.plan(r.f, r.g, C, a2, b2, eps / (1 + d))
+    rows = P / P.sum(1, keepdims=True)
+    H = -(rows * np.log(np.where(rows > 0, rows, 1.0))).sum(1)
+    pred = d * (p.a @ H)
+    assert abs(ev["row_l1"] - pred) <= 1e-3 * pred
+    assert abs(ev["col_l1"] - ev["row_l1"]) <= 1e-3 * pred
