@@ -138,7 +138,11 @@ eot_status eot_solve(const eot_problem *prob, const eot_options *opt,
 /* Solve count independent problems of uneven sizes in one persistent launch
  * (plain Sinkhorn; opt->ell must be 0).  Arrays of count pointers; results[k]
  * (host) holds each problem's status; the call returns the worst status.  Each
- * problem's result does not depend on which others share the batch. */
+ * problem's result does not depend on which others share the batch, nor on how
+ * many CTAs the scheduler gives it (bit for bit).  A problem with n > m and no
+ * f_init runs transposed internally (Sinkhorn is symmetric in the two sides):
+ * f_out, g_out, row_l1 and col_l1 are returned in the caller's roles, and its
+ * q_semi is the semi-dual in g. */
 eot_status eot_solve_batch(int32_t count, const eot_problem *probs, const eot_options *opt,
                            double *const *f_out, double *const *g_out, eot_result *results);
 
