@@ -91,7 +91,7 @@ __device__ bool gang_sync(unsigned* bar, int G, int* s_flag) {
 
 // Split of a potential value into the four exponent arrays (eot_device.cuh);
 // the low parts are stored times k2 = 1/(eps ln 2) of the current level, so
-// that an exponent is one fused multiply-add away from the exact part.
+// that an exponent needs no further product for them.
 __device__ __forceinline__ void bsplit(const BatchTask& T, double o, double eps_logw, float k2,
                                        Split s, int idx) {
   double hi;
@@ -166,8 +166,10 @@ __device__ __forceinline__ void bsum_all(V v[NV], BShared& sh) {
 
 // Partial log-sum-exp of row i over one lane's 4-column groups g = sub,
 // sub + LPR, ... (eight groups per step, all cost loads issued first):
-// exponents y_j = ((A_j - K_i) - C_ij) k2 + AL_j k2 in log2 units, summed in
-// a pair of float32 sums under one windowed reference.
+// exponents y_j = t (k2 + k2lo) + AL_j k2 in log2 units with the exact
+// t = (A_j - K_i) - C_ij (k2lo: the float32 remainder of 1/(eps ln 2), so
+// that the iteration is at eps itself), summed in a pair of float32 sums
+// under one windowed reference.
 template <bool ACC>
 __device__ __forceinline__ void brow_stream(const BatchTask& T, const Split& cs, int i, int sub,
                                             int LPR, float k2, float k2lo, float& rf, float& ss) {
@@ -310,8 +312,9 @@ __device__ void brow_pass(const BatchTask& T, int r0, int r1, int gi, double eps
 
 // Partial log-sum-exp of the four columns j..j+3 over the 8-row blocks
 // b = rg, rg + 8, ... (rg: the warp's row group): exponents
-// ((A_i - K_j) - C_ij) k2 + AL_i k2, windowed references per column and
-// compensated pair sums (one compensated add per block of eight rows).
+// t (k2 + k2lo) + AL_i k2 with the exact t = (A_i - K_j) - C_ij, windowed
+// references per column and compensated pair sums (one compensated add per
+// block of eight rows).
 template <bool ACC>
 __device__ __forceinline__ void bcol_stream(const BatchTask& T, const Split& os, int j, int c1,
                                             int rg, float k2, float k2lo, float4& Rout,
