@@ -189,6 +189,11 @@ __device__ __forceinline__ void brow_stream(const BatchTask& T, const Split& cs,
       const int g = g0 + u * LPR;
       c[u] = g < ng ? __ldcg(Ci + g) : z4;
     }
+#pragma unroll
+    for (int u = 0; u < kBRowU; ++u) {   // the lane's next step into L2
+      const int g = g0 + (kBRowU + u) * LPR;
+      if (g < ng) asm volatile("prefetch.global.L2 [%0];" ::"l"(Ci + g));
+    }
     // exponents: the iteration rounds y = t k2 + AL once; an evaluation pass
     // (ACC) keeps t and forms y as p + q at the term, p = t k2 rounded and q
     // its exact rounding error plus AL (ex2_pq)
@@ -339,6 +344,14 @@ __device__ __forceinline__ void bcol_stream(const BatchTask& T, const Split& os,
     for (int u = 0; u < 8; ++u)
       c[u] = (fullr || i0 + u < n) ? __ldcg(reinterpret_cast<const float4*>(Cj + (size_t)(i0 + u) * pitch))
                                    : z4;
+    // the warp's next block into L2 while this one is reduced (measured on
+    // the mixed 512-problem batch, with the row pass's prefetch: 0.45 -> 0.42 s)
+    {
+      const int in = i0 + 8 * (kBThreads / 32);
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (in + u < n) asm volatile("prefetch.global.L2 [%0];" ::"l"(Cj + (size_t)(in + u) * pitch));
+    }
     const float4 a0 = *reinterpret_cast<const float4*>(T.fs.A + i0);
     const float4 a1 = *reinterpret_cast<const float4*>(T.fs.A + i0 + 4);
     const float4 l0 = *reinterpret_cast<const float4*>(T.fs.AL + i0);
