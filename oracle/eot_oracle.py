@@ -22,6 +22,9 @@ Pins (what fixes each function independently of this file; the tests live in
                               ascent of the semi-dual (Thm 4.2, step 1).
 * ``grad_semi`` / ``hess_semi`` central finite differences of ``q_semi``;
                               H 1 = 0.
+* ``newton_cg``               numpy.linalg.solve on SPD systems (exact in k
+                              steps up to rounding); breakdown on indefinite
+                              ones; SK-NR with it repeats the direct solve.
 * ``operator_K`` / ``spectral_modes_*``  Thm 3.1 invariants (spectrum in
                               [-1, 1], symmetric, rho_0 = 1 with eigenvector
                               1 + 1), Hermitization (singular values of R),
@@ -57,7 +60,7 @@ __all__ = [
     "q_dual", "q_semi", "primal_value", "duality_gap", "evaluate", "gauge_normalize",
     "grad_semi", "hess_semi", "hess_dual",
     "op_pi", "op_pi_T", "operator_K", "R_matrix", "semidual_operator_M",
-    "splitmix64_uniform", "spectral_modes_dense", "spectral_modes_subspace",
+    "splitmix64_uniform", "spectral_modes_dense", "spectral_modes_subspace", "newton_cg",
     "SolveResult", "sinkhorn", "sknr", "eps_schedule", "continuation",
     "bruteforce_ot", "dense_newton",
 ]
@@ -384,8 +387,41 @@ class SolveResult:
     nr_rejected: int = 0
 
 
+def newton_cg(A, rhs, tol: float = 1e-14, max_iter: Optional[int] = None):
+    """Conjugate gradients (Hestenes-Stiefel) for A x = rhs, A symmetric
+    (Sec. 4, remarks on the design: the Newton system of the NR step solved
+    iteratively, the form that parallelises over many problems).  Stops at a
+    relative residual ``tol`` or after ``max_iter`` steps (default 10 k: in
+    floating point CG needs more than the k steps of exact arithmetic on an
+    ill-conditioned system).  Returns (x, ok): ok is False when a search
+    direction has non-positive curvature p^T A p <= 0 (A is not positive
+    definite along it), in which case the step is rejected like a failed
+    Cholesky factorisation."""
+    A, rhs = _f64(A), _f64(rhs)
+    k = rhs.shape[0]
+    x = np.zeros(k)
+    r = rhs.copy()
+    p = r.copy()
+    rr = float(r @ r)
+    stop = tol * tol * max(rr, 1e-300)
+    for _ in range(10 * k if max_iter is None else max_iter):
+        if rr <= stop:
+            break
+        Ap = A @ p
+        curv = float(p @ Ap)
+        if not curv > 0.0:
+            return x, False
+        alpha = rr / curv
+        x = x + alpha * p
+        r = r - alpha * Ap
+        rr_new = float(r @ r)
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+    return x, True
+
+
 def sknr(C, a, b, eps, V=None, tol: float = 1e-6, max_iter: int = 10000, f0=None,
-         hessian: str = "exact", record: bool = False) -> SolveResult:
+         hessian: str = "exact", record: bool = False, newton: str = "direct") -> SolveResult:
     """Algorithm 4.1, SK-NR(l).  With V None (or l = 0) it is log-domain Sinkhorn.
 
     Iteration k (the algorithm's order):
@@ -397,6 +433,8 @@ def sknr(C, a, b, eps, V=None, tol: float = 1e-6, max_iter: int = 10000, f0=None
       Q_semi(f') > Q_semi(f_k).
     ``hessian="exact"`` uses D_r with r = pi(f_k, f_k^{C,eps}) 1 (Eq. d2Q_semi);
     ``hessian="diag_alpha"`` replaces D_r by D_a (equal at the optimum).
+    ``newton="direct"`` solves for Delta by Cholesky; ``newton="cg"`` by
+    conjugate gradients (``newton_cg``), rejecting on non-positive curvature.
     Returns (f_k, g_k) of the stopping iteration.
     """
     C, a, b = _f64(C), _f64(a), _f64(b)
@@ -427,12 +465,18 @@ def sknr(C, a, b, eps, V=None, tol: float = 1e-6, max_iter: int = 10000, f0=None
             d = r if hessian == "exact" else a
             H = -(1.0 / eps) * (V.T @ (d[:, None] * V) - W.T @ (W / b[:, None]))
             negH = 0.5 * (-H - H.T)
-            try:
-                np.linalg.cholesky(negH)
-            except np.linalg.LinAlgError:
-                res.nr_rejected += 1
-                continue
-            delta = np.linalg.solve(negH, grad)
+            if newton == "cg":
+                delta, ok = newton_cg(negH, grad)
+                if not ok:
+                    res.nr_rejected += 1
+                    continue
+            else:
+                try:
+                    np.linalg.cholesky(negH)
+                except np.linalg.LinAlgError:
+                    res.nr_rejected += 1
+                    continue
+                delta = np.linalg.solve(negH, grad)
             f_new = f + V @ delta
             if q_semi(f_new, C, a, b, eps) > q_k:
                 f = f_new

@@ -440,3 +440,43 @@ def test_rounded_inverse_eps_solves_a_nearby_problem():
     pred = d * (p.a @ H)
     assert abs(ev["row_l1"] - pred) <= 1e-3 * pred
     assert abs(ev["col_l1"] - ev["row_l1"]) <= 1e-3 * pred
+
+
+def test_newton_cg_matches_direct_solve():
+    """The iterative Newton solve (Sec. 4, remarks on the design) against
+    numpy.linalg.solve on SPD systems of the projected Hessian's size (to the
+    conditioning times the residual tolerance), and a breakdown (step
+    rejected) on an indefinite one, like a failed Cholesky factorisation."""
+    rng = np.random.default_rng(11)
+    for k in (1, 5, 30, 40):
+        Q, _ = np.linalg.qr(rng.standard_normal((k, k)))
+        lam = np.geomspace(1.0, 1e-4, k)             # condition number 1e4
+        A = (Q * lam) @ Q.T
+        rhs = rng.standard_normal(k)
+        x, ok = O.newton_cg(A, rhs)
+        xd = np.linalg.solve(A, rhs)
+        assert ok and np.abs(x - xd).max() <= 1e-8 * np.abs(xd).max()
+    A = np.diag([1.0, 2.0, -0.5])
+    _, ok = O.newton_cg(A, np.array([1.0, 1.0, 1.0]))
+    assert not ok
+
+
+def test_sknr_with_cg_repeats_the_direct_newton():
+    """SK-NR(l) with the Newton system solved by conjugate gradients takes the
+    same steps as with the direct solve: same iterations, same accepted and
+    rejected steps, the same potentials to rounding.  The tolerance stops the
+    run while the semi-dual increase of a step is still well above the float64
+    rounding of Q_semi: on this instance it falls to one unit in the last place
+    of Q_semi (3e-18) near L1 = 5e-7, where the strict accept test of
+    Algorithm 4.1 is decided by rounding whichever way Delta is computed."""
+    p = W.gaussian_mixture(150, 130, seed=4)
+    C = O.sq_euclidean_cost(p.X, p.Y, normalize=True)
+    eps = 5e-3
+    start = O.sinkhorn(C, p.a, p.b, 2 * eps, tol=1e-8, max_iter=100000)
+    V, _ = O.spectral_modes_dense(start.f, start.g, C, p.a, p.b, 2 * eps, 12)
+    r1 = O.sknr(C, p.a, p.b, eps, V, tol=2e-6, max_iter=20000, f0=start.f, hessian="diag_alpha")
+    r2 = O.sknr(C, p.a, p.b, eps, V, tol=2e-6, max_iter=20000, f0=start.f, hessian="diag_alpha",
+                newton="cg")
+    assert r1.converged and r2.converged
+    assert (r1.iters, r1.nr_accepted, r1.nr_rejected) == (r2.iters, r2.nr_accepted, r2.nr_rejected)
+    assert np.abs(r1.f - r2.f).max() <= 1e-9 * eps
