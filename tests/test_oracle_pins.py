@@ -480,3 +480,34 @@ def test_sknr_with_cg_repeats_the_direct_newton():
     assert r1.converged and r2.converged
     assert (r1.iters, r1.nr_accepted, r1.nr_rejected) == (r2.iters, r2.nr_accepted, r2.nr_rejected)
     assert np.abs(r1.f - r2.f).max() <= 1e-9 * eps
+
+
+def test_chebyshev_filtered_subspace_iteration():
+    """The Chebyshev-filtered spectral step against numpy.linalg.eigh (same
+    Ritz values and subspace as the dense eigendecomposition), and its reason
+    to exist: on a clustered spectrum (rho_1^2 near 1) it reaches the same
+    residual with fewer applications of M and far fewer Rayleigh-Ritz steps
+    than plain subspace iteration."""
+    C, a, b, eps, f, g = _solved(n=60, m=70, eps=0.05, seed=12)
+    ell = 5
+    Vd, rd = O.spectral_modes_dense(f, g, C, a, b, eps, ell)
+    Vc, rc, steps, res, apps = O.spectral_modes_chebyshev(f, g, C, a, b, eps, ell, oversample=8,
+                                                          degree=4, tol=1e-10, max_iter=2000)
+    assert res <= 1e-10 and np.allclose(rc, rd, atol=1e-9)
+    assert np.allclose(Vc.T @ (a[:, None] * Vc), np.eye(ell), atol=1e-10)
+    assert np.abs(a @ Vc).max() < 1e-10
+    Pd = Vd @ Vd.T @ np.diag(a)
+    assert np.allclose(Pd @ Vc, Vc, atol=1e-6)
+    p = W.gaussian_mixture(200, 180, seed=1, eps=5e-3)
+    C2 = O.sq_euclidean_cost(p.X, p.Y, normalize=True)
+    r = O.sinkhorn(C2, p.a, p.b, p.eps, tol=1e-10, max_iter=400000)
+    _, rho2 = O.spectral_modes_dense(r.f, r.g, C2, p.a, p.b, p.eps, 10)
+    assert rho2[0] > 0.99
+    _, r_s, it_s, res_s = O.spectral_modes_subspace(r.f, r.g, C2, p.a, p.b, p.eps, 10,
+                                                    oversample=10, tol=1e-8, max_iter=20000)
+    _, r_c, st_c, res_c, apps_c = O.spectral_modes_chebyshev(r.f, r.g, C2, p.a, p.b, p.eps, 10,
+                                                             oversample=10, degree=4, tol=1e-8,
+                                                             max_iter=20000)
+    assert res_s <= 1e-8 and res_c <= 1e-8
+    assert np.abs(r_c - rho2).max() <= 1e-8 and np.abs(r_s - rho2).max() <= 1e-8
+    assert apps_c < it_s and 3 * st_c < it_s
