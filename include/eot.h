@@ -219,6 +219,23 @@ eot_status eot_spectral_modes(int32_t n, int32_t m, const float *C, const double
                               int32_t use_V_as_start, double *V, double *rho2,
                               int32_t *iters_out, double *resid_out, void *stream);
 
+/* The schedule eot_solve_batch would use, computed on the host only (no
+ * device work, no GPU needed): for count problems of sizes n[k] x m[k] at
+ * eps[k] (has_f_init[k] != 0 if the problem carries a warm start; NULL: none
+ * does), the options' eps schedule and max_iter, a grid of grid_ctas resident
+ * CTAs and a cost model (step_ns: one load-and-reduce step of a CTA; fix_ns:
+ * the fixed cost of an iteration; bar_ns: one gang barrier; the library
+ * calibrates these on the device before its first batch), gang_out[k]
+ * receives the number of CTAs of problem k (a power of two, at most 32 and an
+ * eighth of the grid) and transposed_out[k] 1 if it runs as the transposed
+ * problem (n > m without a warm start).  Host arrays of count entries.
+ * Returns EOT_EINVAL on a member with n, m < 1 or eps <= 0, or a model with
+ * step_ns <= 0. */
+eot_status eot_batch_plan(int32_t count, const int32_t *n, const int32_t *m, const double *eps,
+                          const int32_t *has_f_init, const eot_options *opt, int32_t grid_ctas,
+                          double step_ns, double fix_ns, double bar_ns, int32_t *gang_out,
+                          int32_t *transposed_out);
+
 /* Marginal errors of pi(f, g) computed on the device (float32 exponentials,
  * float64 sums): row_l1 = ||pi1 - a||_1, col_l1 = ||pi^T1 - b||_1 (host outputs). */
 eot_status eot_marginal_error(int32_t n, int32_t m, const float *C, const double *f,

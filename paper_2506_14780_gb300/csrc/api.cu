@@ -1331,6 +1331,51 @@ static double task_ns(const BatchModel& M, double iters, int n, int m, int G) {
   return iters * (batch_steps(n, m, G) * M.step_ns + M.fix_ns + (G > 1 ? 2.0 * M.bar_ns : 0.0));
 }
 
+// Whether a batch member runs as the transposed problem: plain Sinkhorn is
+// symmetric in the two sides, and with more rows than columns the column
+// half-step (one CTA streams every row of its columns) gets the short side to
+// stream.  A warm start f_init fixes the roles.
+static bool batch_transposed(int n, int m, bool has_f_init) { return n > m && !has_f_init; }
+
+// Predicted iterations of a batch member: the sum over its eps levels of
+// min(0.66 / eps, max_iter), at least 1.
+static double batch_est_iters(const std::vector<double>& levels, int max_iter) {
+  double it = 0.0;
+  for (double e : levels) it += std::min(0.66 / e, (double)max_iter);
+  return std::max(1.0, it);
+}
+
+// Gang sizes of a batch (host logic): no task longer than half the ideal
+// makespan (the sum of the single-CTA task times over the grid), as far as
+// doubling its gang helps, and at most kBCostPerCta bytes of a problem's cost
+// per CTA (more of it stays in L2 between half-steps; the mixed 512-problem
+// batch: 0.49 s per call without this floor, 0.46 s with it, 0.53 s at
+// 160 KB, where the gang barriers cost more than the reuse gains).  n, m are
+// the dimensions the kernel runs (after transposition); members with ok[k]
+// false get no gang.
+static void plan_gangs(const BatchModel& M, int count, const int* n, const int* m,
+                       const double* est_it, const bool* ok, int ctas, int cap, int* G_out) {
+  double sum1 = 0.0;
+  for (int k = 0; k < count; ++k)
+    if (ok[k]) sum1 += task_ns(M, est_it[k], n[k], m[k], 1);
+  const double target = 0.5 * sum1 / ctas;
+  for (int k = 0; k < count; ++k) {
+    if (!ok[k]) {
+      G_out[k] = 0;
+      continue;
+    }
+    int G = 1;
+    while (G < cap && task_ns(M, est_it[k], n[k], m[k], G) > target &&
+           task_ns(M, est_it[k], n[k], m[k], 2 * G) < task_ns(M, est_it[k], n[k], m[k], G))
+      G *= 2;
+    while (G < cap && (double)G * kBCostPerCta < 4.0 * (double)n[k] * (double)m[k]) G *= 2;
+    G_out[k] = G;
+  }
+}
+
+// Largest gang: 32 CTAs, and no more than an eighth of the grid.
+static int batch_gang_cap(int ctas) { return std::max(1, std::min(kBMaxGang, ctas / 8)); }
+
 // Grow-only pinned staging buffer of the calling thread.
 static char* pinned_staging(size_t bytes) {
   static thread_local char* buf = nullptr;
@@ -1418,7 +1463,7 @@ static eot_status run_batch(int count, const eot_problem* probs, const eot_optio
   cudaStream_t s = ctx->stream;
   const int ctas = batch_ctas_per_sm() * ctx->nsm;
   if (ctas < 1) return fail(EOT_ECUDA, "the batch kernel cannot be resident");
-  const int cap = std::max(1, std::min(kBMaxGang, ctas / 8));
+  const int cap = batch_gang_cap(ctas);
   if (forced_G <= 0) {
     // EOT_BATCH_GANG=G: every problem runs on a gang of G CTAs (no cost model;
     // results are the same for any G)
@@ -1462,7 +1507,7 @@ static eot_status run_batch(int count, const eot_problem* probs, const eot_optio
     // plain Sinkhorn is symmetric in the two sides: with more rows than
     // columns the problem runs transposed, so that the column half-step (one
     // CTA streams all rows of its columns) has the short side to stream
-    p.trans = q.n > q.m && !q.f_init;
+    p.trans = batch_transposed(q.n, q.m, q.f_init != nullptr);
     p.n = p.trans ? q.m : q.n;
     p.m = p.trans ? q.n : q.m;
     p.d = q.d;
@@ -1480,35 +1525,21 @@ static eot_status run_batch(int count, const eot_problem* probs, const eot_optio
       if (q.f_init) p.h_f = htake(sizeof(double) * q.n);
     }
   }
-  // ---- gang sizes: no task longer than half the ideal makespan (sum of the
-  // single-CTA task times over the grid), as far as doubling its gang helps;
-  // iterations estimated from the eps schedule ----
+  // ---- gang sizes (plan_gangs), iterations estimated from the eps schedule ----
   std::vector<double> est_it(count, 0.0);
-  for (int k = 0; k < count; ++k) {
-    if (!pl[k].ok) continue;
-    double it = 0.0;
-    for (double e : pl[k].lev) it += std::min(0.66 / e, (double)o.max_iter);
-    est_it[k] = std::max(1.0, it);
-  }
+  for (int k = 0; k < count; ++k)
+    if (pl[k].ok) est_it[k] = batch_est_iters(pl[k].lev, o.max_iter);
   if (forced_G <= 0) {
-    double sum1 = 0.0;
-    for (int k = 0; k < count; ++k)
-      if (pl[k].ok) sum1 += task_ns(M, est_it[k], pl[k].n, pl[k].m, 1);
-    const double target = 0.5 * sum1 / ctas;
+    std::vector<int> nn(count), mm(count), GG(count);
+    std::unique_ptr<bool[]> okk(new bool[count]);
     for (int k = 0; k < count; ++k) {
-      if (!pl[k].ok) continue;
-      const int n = pl[k].n, m = pl[k].m;
-      int G = 1;
-      while (G < cap && task_ns(M, est_it[k], n, m, G) > target &&
-             task_ns(M, est_it[k], n, m, 2 * G) < task_ns(M, est_it[k], n, m, G))
-        G *= 2;
-      // and at most 1.25 MB of a cost per CTA: more of a problem's cost stays
-      // in L2 between its half-steps (the mixed 512-problem batch: 0.49 s per
-      // call without this floor, 0.46 s with it; 0.53 s at 160 KB, where the
-      // gang barriers cost more than the reuse gains)
-      while (G < cap && (double)G * kBCostPerCta < 4.0 * (double)n * (double)m) G *= 2;
-      pl[k].G = G;
+      nn[k] = pl[k].n;
+      mm[k] = pl[k].m;
+      okk[k] = pl[k].ok;
     }
+    plan_gangs(M, count, nn.data(), mm.data(), est_it.data(), okk.get(), ctas, cap, GG.data());
+    for (int k = 0; k < count; ++k)
+      if (pl[k].ok) pl[k].G = GG[k];
   }
   // ---- device arena: [staged inputs | per-problem state | outputs | tables] ----
   struct DL {
@@ -2100,6 +2131,38 @@ eot_status eot_cost(int32_t n, int32_t m, int32_t d, const float* X, const float
   CUDA_TRY(cudaFreeAsync(tmp, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   CUDA_TRY(cudaGetLastError());
+  return EOT_OK;
+}
+
+eot_status eot_batch_plan(int32_t count, const int32_t* n, const int32_t* m, const double* eps,
+                          const int32_t* has_f_init, const eot_options* opt, int32_t grid_ctas,
+                          double step_ns, double fix_ns, double bar_ns, int32_t* gang_out,
+                          int32_t* transposed_out) {
+  if (count < 0 || (count > 0 && (!n || !m || !eps || !gang_out || !transposed_out)) || !opt)
+    return fail(EOT_EINVAL, "count >= 0, n, m, eps, opt, gang_out and transposed_out are required");
+  if (grid_ctas < 1) return fail(EOT_EINVAL, "grid_ctas must be >= 1");
+  if (!(step_ns > 0.0) || !(fix_ns >= 0.0) || !(bar_ns >= 0.0))
+    return fail(EOT_EINVAL, "the cost model needs step_ns > 0, fix_ns >= 0, bar_ns >= 0");
+  BatchModel M;
+  M.step_ns = step_ns;
+  M.fix_ns = fix_ns;
+  M.bar_ns = bar_ns;
+  M.done = true;
+  std::vector<int> nn(count), mm(count), GG(count);
+  std::vector<double> it(count);
+  std::unique_ptr<bool[]> ok(new bool[count]);
+  for (int k = 0; k < count; ++k) {
+    if (n[k] < 1 || m[k] < 1 || !finite_pos(eps[k])) return fail(EOT_EINVAL, "member with n, m < 1 or eps <= 0");
+    const bool tr = batch_transposed(n[k], m[k], has_f_init && has_f_init[k]);
+    transposed_out[k] = tr ? 1 : 0;
+    nn[k] = tr ? m[k] : n[k];
+    mm[k] = tr ? n[k] : m[k];
+    it[k] = batch_est_iters(schedule(opt->eps_start, eps[k], opt->eps_factor), opt->max_iter);
+    ok[k] = true;
+  }
+  plan_gangs(M, count, nn.data(), mm.data(), it.data(), ok.get(), grid_ctas,
+             batch_gang_cap(grid_ctas), GG.data());
+  for (int k = 0; k < count; ++k) gang_out[k] = GG[k];
   return EOT_OK;
 }
 

@@ -88,6 +88,8 @@ _SIGNATURES = {
     "eot_marginal_error": (C.c_int, [C.c_int32, C.c_int32, _PTR, _PTR, _PTR, _PTR, _PTR,
                                      C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                      _PTR]),
+    "eot_batch_plan": (C.c_int, [C.c_int32, _PTR, _PTR, _PTR, _PTR, C.POINTER(eot_options),
+                                 C.c_int32, C.c_double, C.c_double, C.c_double, _PTR, _PTR]),
     "eot_last_error": (C.c_char_p, []),
     "eot_version": (C.c_char_p, []),
 }
@@ -260,6 +262,25 @@ def eot_spectral_modes(n, m, Cdev, f, g, a, b, eps, ell, oversample, tol, max_it
                                    V.data_ptr(), None if rho2 is None else rho2.data_ptr(),
                                    C.byref(it), C.byref(rs), stream)
     return st, it.value, rs.value
+
+
+def eot_batch_plan(n, m, eps, options: eot_options, grid_ctas: int, step_ns: float,
+                   fix_ns: float, bar_ns: float, has_f_init=None):
+    """Host-only schedule of eot_solve_batch: (status, gangs, transposed) for the
+    problem sizes n, m and eps (sequences) under the given cost model."""
+    import numpy as np
+    n = np.ascontiguousarray(n, dtype=np.int32)
+    m = np.ascontiguousarray(m, dtype=np.int32)
+    eps = np.ascontiguousarray(eps, dtype=np.float64)
+    k = int(n.shape[0])
+    fi = None if has_f_init is None else np.ascontiguousarray(has_f_init, dtype=np.int32)
+    gang = np.zeros(k, dtype=np.int32)
+    tr = np.zeros(k, dtype=np.int32)
+    st = load().eot_batch_plan(k, n.ctypes.data, m.ctypes.data, eps.ctypes.data,
+                               None if fi is None else fi.ctypes.data, C.byref(options),
+                               int(grid_ctas), float(step_ns), float(fix_ns), float(bar_ns),
+                               gang.ctypes.data, tr.ctypes.data)
+    return st, gang, tr
 
 
 def eot_marginal_error(n, m, Cdev, f, g, a, b, eps, stream=None):
