@@ -511,3 +511,27 @@ def test_chebyshev_filtered_subspace_iteration():
     assert res_s <= 1e-8 and res_c <= 1e-8
     assert np.abs(r_c - rho2).max() <= 1e-8 and np.abs(r_s - rho2).max() <= 1e-8
     assert apps_c < it_s and 3 * st_c < it_s
+
+
+def test_spectrum_concentrates_as_eps_decreases():
+    """Sec. 3, spectral stability (the paper's figure of the ten smallest
+    eigenvalues of Id + K_eps, square against annulus): as eps decreases every
+    one of the ten leading rho_k^2 grows towards 1, while the leading
+    eigenvectors move little."""
+    p = W.square_annulus(160, 160, seed=0)
+    C = O.sq_euclidean_cost(p.X, p.Y)
+    rho, modes = [], []
+    for eps in (0.256, 0.128, 0.064, 0.032, 0.016):
+        s = O.sinkhorn(C, p.a, p.b, eps, tol=1e-11, max_iter=200000)
+        V, rho2 = O.spectral_modes_dense(s.f, s.g, C, p.a, p.b, eps, 10)
+        rho.append(rho2)
+        modes.append(V)
+    rho = np.array(rho)
+    assert np.all(np.diff(rho, axis=0) > 0)          # each rho_k^2 grows as eps halves
+    assert rho[-1, 0] > 0.9 and rho[0, 0] < 0.5
+    sa = np.sqrt(p.a)[:, None]
+    Qu, _ = np.linalg.qr(sa * modes[0][:, :3])
+    Qv, _ = np.linalg.qr(sa * modes[2][:, :3])
+    # smallest cosine of the principal angles between the leading 3-mode
+    # subspaces at eps = 0.256 and eps = 0.064
+    assert np.linalg.svd(Qu.T @ Qv, compute_uv=False).min() > 0.95

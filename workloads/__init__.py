@@ -138,6 +138,20 @@ def gaussians_2d(n: int = 200, seed: int = 0, eps: float = 1e-1) -> Problem:
                    normalize_cost=False, name=f"gaussians_2d_{n}x{2 * n}")
 
 
+def square_annulus(n: int = 200, m: int = 200, seed: int = 0, eps: float = 0.064) -> Problem:
+    """Sec. 3 (spectral stability): uniform measure on the unit square against
+    the uniform measure on an annulus (radii 0.25 and 0.5, centred at
+    (0.5, 0.5)); uniform weights; squared Euclidean cost, not normalised."""
+    rng = np.random.default_rng(seed)
+    X = rng.random((n, 2))
+    r = np.sqrt(rng.uniform(0.25 ** 2, 0.5 ** 2, m))     # uniform in area
+    th = rng.uniform(0.0, 2.0 * np.pi, m)
+    Y = np.stack([0.5 + r * np.cos(th), 0.5 + r * np.sin(th)], axis=1)
+    return Problem(a=_simplex_uniform(n), b=_simplex_uniform(m), X=X.astype(np.float32),
+                   Y=Y.astype(np.float32), eps=eps, normalize_cost=False,
+                   name=f"square_annulus_{n}x{m}")
+
+
 def random_cost(n: int, m: int, seed: int = 0, scale: float = 1.0,
                 dirichlet: bool = True) -> Problem:
     """A dense cost with entries uniform in [0, scale), float32, plus weights."""
