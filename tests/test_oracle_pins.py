@@ -535,3 +535,34 @@ def test_spectrum_concentrates_as_eps_decreases():
     # smallest cosine of the principal angles between the leading 3-mode
     # subspaces at eps = 0.256 and eps = 0.064
     assert np.linalg.svd(Qu.T @ Qv, compute_uv=False).min() > 0.95
+
+
+def test_two_gaussians_protocols_of_section_5():
+    """Sec. 5, the 2-D Gaussian experiment (n = 200 against 2n = 400 points,
+    uniform weights, raw squared Euclidean cost), its three protocols in
+    float64: (1) sequential warm start from eps = 1, halving: with l = 10 modes
+    refreshed at every level, every level after the first needs at least 2x
+    fewer iterations than Sinkhorn's; (2) static modes computed once at
+    eps' = 1: still fewer iterations than Sinkhorn on the first transitions;
+    (3) more modes, fewer iterations: at eps = 0.25 from the eps = 1 solution
+    with its modes, the count falls strictly with l in {0, 2, 5, 10, 20}."""
+    p = W.gaussians_2d(200, seed=0)
+    C = O.sq_euclidean_cost(p.X, p.Y)
+    _, hs = O.continuation(C, p.a, p.b, 0.25, tol=1e-6, eps_start=1.0, ell=0, return_levels=True)
+    _, hn = O.continuation(C, p.a, p.b, 0.25, tol=1e-6, eps_start=1.0, ell=10, return_levels=True)
+    _, hst = O.continuation(C, p.a, p.b, 0.25, tol=1e-6, eps_start=1.0, ell=10, sequential=False,
+                            return_levels=True)
+    sk = [h["iters"] for h in hs]
+    seq = [h["iters"] for h in hn]
+    static = [h["iters"] for h in hst]
+    assert seq[0] == sk[0] == static[0]              # the first level has no modes yet
+    assert all(2 * q <= s for q, s in zip(seq[1:], sk[1:])), (seq, sk)
+    assert all(q < s for q, s in zip(static[1:], sk[1:])), (static, sk)
+    s1 = O.sinkhorn(C, p.a, p.b, 1.0, tol=1e-10, max_iter=100000)
+    counts = []
+    for ell in (0, 2, 5, 10, 20):
+        V = None
+        if ell:
+            V, _ = O.spectral_modes_dense(s1.f, s1.g, C, p.a, p.b, 1.0, ell)
+        counts.append(O.sknr(C, p.a, p.b, 0.25, V, tol=1e-6, max_iter=200000, f0=s1.f).iters)
+    assert all(b < a for a, b in zip(counts, counts[1:])), counts
