@@ -566,3 +566,30 @@ def test_two_gaussians_protocols_of_section_5():
             V, _ = O.spectral_modes_dense(s1.f, s1.g, C, p.a, p.b, 1.0, ell)
         counts.append(O.sknr(C, p.a, p.b, 0.25, V, tol=1e-6, max_iter=200000, f0=s1.f).iters)
     assert all(b < a for a, b in zip(counts, counts[1:])), counts
+
+
+def test_gradient_on_modes_delta_form():
+    """The device forms the semi-dual gradient on V (Eq. dQ_semi at f_k, with
+    g = h = f_k^{C,eps}) as -sum_j d_j W_j, W = pi(f_k, h)^T V and
+    d_j = 1 - exp((g_j - h_j)/eps).  Since V^T a = V^T pi(f_k, g_k) 1 when the
+    rows of pi(f_k, g_k) sum to a (after the row half-step f_k = g_k^{C,eps}),
+    this equals V^T (a - pi(f_k, h) 1) exactly; it does not when the rows do
+    not match."""
+    C, a, b, eps, f_opt, g_opt = _solved(n=70, m=50, eps=0.05, seed=21)
+    V, _ = O.spectral_modes_dense(f_opt, g_opt, C, a, b, eps, 6)
+    rng = np.random.default_rng(2)
+    g = g_opt + 0.3 * eps * rng.standard_normal(b.shape)     # an iterate away from the optimum
+    f = O.c_transform_g(g, C, b, eps)                         # row half-step: rows of pi(f, g) = a
+    h = O.c_transform_f(f, C, a, eps)
+    P = O.plan(f, h, C, a, b, eps)
+    grad = V.T @ (a - P.sum(axis=1))
+    W = P.T @ V
+    d = 1.0 - np.exp((g - h) / eps)
+    delta_form = -(d[:, None] * W).sum(axis=0)
+    assert np.abs(grad - delta_form).max() <= 1e-12 * max(1.0, np.abs(grad).max())
+    assert np.abs(grad).max() > 1e-6                          # a non-trivial gradient
+    f_off = f + 0.1 * eps * rng.standard_normal(a.shape)      # rows no longer match a
+    h2 = O.c_transform_f(f_off, C, a, eps)
+    P2 = O.plan(f_off, h2, C, a, b, eps)
+    d2 = 1.0 - np.exp((g - h2) / eps)
+    assert np.abs(V.T @ (a - P2.sum(axis=1)) + (d2[:, None] * (P2.T @ V)).sum(axis=0)).max() > 1e-6
