@@ -593,3 +593,25 @@ def test_gradient_on_modes_delta_form():
     P2 = O.plan(f_off, h2, C, a, b, eps)
     d2 = 1.0 - np.exp((g - h2) / eps)
     assert np.abs(V.T @ (a - P2.sum(axis=1)) + (d2[:, None] * (P2.T @ V)).sum(axis=0)).max() > 1e-6
+
+
+def test_diag_alpha_hessian_equals_exact_at_the_optimum():
+    """Reading R6: the device's projected Hessian replaces D_r, r = pi(f, h) 1
+    (Eq. d2Q_semi), by D_a.  At the optimum r = a, so both agree on V; away
+    from it they differ by V^T diag(r - a) V / eps."""
+    C, a, b, eps, f_opt, g_opt = _solved(n=60, m=45, eps=0.05, seed=8)
+    V, _ = O.spectral_modes_dense(f_opt, g_opt, C, a, b, eps, 5)
+
+    def h_diag_alpha(f):
+        h = O.c_transform_f(f, C, a, eps)
+        W = O.plan(f, h, C, a, b, eps).T @ V
+        return -(1.0 / eps) * (V.T @ (a[:, None] * V) - W.T @ (W / b[:, None]))
+
+    exact = V.T @ O.hess_semi(f_opt, C, a, b, eps) @ V
+    assert np.abs(exact - h_diag_alpha(f_opt)).max() <= 1e-8 * np.abs(exact).max()
+    f = f_opt + 0.5 * eps * np.random.default_rng(1).standard_normal(a.shape)
+    h = O.c_transform_f(f, C, a, eps)
+    r = O.plan(f, h, C, a, b, eps).sum(axis=1)
+    diff = V.T @ O.hess_semi(f, C, a, b, eps) @ V - h_diag_alpha(f)
+    assert np.allclose(diff, -(1.0 / eps) * V.T @ ((r - a)[:, None] * V), atol=1e-10)
+    assert np.abs(diff).max() > 1e-4
