@@ -2290,6 +2290,7 @@ struct eot_server {
     std::vector<double> a, b;
     std::vector<float> C, X, Y;
     size_t footprint = 0;
+    double work = 0;   // predicted cost: n m x the iterations its eps schedule predicts
     double t_submit = 0, t_done = 0;
     std::vector<double> f, g;
     eot_result res{};
@@ -2316,7 +2317,8 @@ struct eot_server {
   int device = 0;
   std::mutex mu;
   std::condition_variable cv;
-  std::deque<std::shared_ptr<Request>> queue;
+  std::deque<std::shared_ptr<Request>> queue;   // submission order
+  static constexpr double kMaxWaitS = 1.0;      // after this, a request goes first
   std::map<uint64_t, std::shared_ptr<Request>> all;
   std::map<uint64_t, Cached> cache;
   size_t in_use = 0;
@@ -2337,21 +2339,36 @@ struct eot_server {
         std::unique_lock<std::mutex> lk(mu);
         for (;;) {
           if (stop) return;
-          for (auto it = queue.begin(); it != queue.end(); ++it) {
-            if ((*it)->footprint <= budget - std::min(budget, in_use)) {
-              r = *it;
-              queue.erase(it);
-              break;
-            }
-            if ((*it)->footprint > budget) {   // can never fit
+          // a request that can never fit is refused at once
+          for (auto it = queue.begin(); it != queue.end();) {
+            if ((*it)->footprint > budget) {
               (*it)->status = EOT_ENOMEM;
               (*it)->res.status = EOT_ENOMEM;
               (*it)->done = true;
-              queue.erase(it);
-              break;
+              it = queue.erase(it);
+            } else {
+              ++it;
             }
           }
-          if (r) break;
+          // of the requests that fit now: one that has waited longer than
+          // kMaxWaitS (oldest first), else the least predicted work, so that
+          // the small requests of a burst do not queue behind the large ones
+          const size_t room = budget - std::min(budget, in_use);
+          const double now = eotk::now_s();
+          auto pick = queue.end();
+          for (auto it = queue.begin(); it != queue.end(); ++it) {
+            if ((*it)->footprint > room) continue;
+            if (now - (*it)->t_submit > kMaxWaitS) {
+              pick = it;
+              break;
+            }
+            if (pick == queue.end() || (*it)->work < (*pick)->work) pick = it;
+          }
+          if (pick != queue.end()) {
+            r = *pick;
+            queue.erase(pick);
+            break;
+          }
           cv.wait(lk);
         }
         in_use += r->footprint;
@@ -2524,6 +2541,9 @@ eot_status eot_server_submit(eot_server* srv, const eot_problem* prob, uint64_t 
   r->footprint = eotk::solver_footprint(ctx, n, m, d, srv->opt.ell,
                                         eotk::mode_block(n, srv->opt.ell, srv->opt.oversample),
                                         srv->opt.prec);
+  r->work = (double)n * (double)m *
+            eotk::batch_est_iters(eotk::schedule(srv->opt.eps_start, prob->eps, srv->opt.eps_factor),
+                                  srv->opt.max_iter);
   {
     std::lock_guard<std::mutex> lk(srv->mu);
     r->ticket = srv->next++;
