@@ -31,7 +31,9 @@ Pins (what fixes each function independently of this file; the tests live in
                               the semi-dual Hessian identity of App. A.4,
                               subspace iteration (plain and Chebyshev-filtered)
                               against ``numpy.linalg.eigh``.
-* ``evaluate``                the duality gap vanishes at the fixed point.
+* ``duality_gap`` / ``evaluate``  a hand-worked 2 x 2 value away from the
+                              optimum; primal_value(pi(f,g)) - q_dual(f,g) at
+                              random (f, g); zero at the fixed point.
 
 Readings of the paper that this file adopts (each is also recorded in the
 design notes of the repository):

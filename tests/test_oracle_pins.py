@@ -381,6 +381,44 @@ def test_gap_vanishes_and_gauge():
     assert np.allclose(O.plan(fn, gn, C, a, b, eps), P, rtol=1e-10)
 
 
+def test_duality_gap_by_hand_off_the_optimum():
+    """A 2 x 2 pair away from the optimum, worked by hand from Eq. primal_EOT
+    and Eq. def_Q.  a = b = (1/2, 1/2), eps = 1, C = [[0, ln 2], [ln 2, 0]],
+    f = (0, ln 2), g = 0 give pi = [[1/4, 1/8], [1/4, 1/2]], so pi 1 =
+    (3/8, 3/4), pi^T 1 = (1/2, 5/8), sum pi = 9/8, and the gap
+    <pi 1 - a, f> + <pi^T 1 - b, g> + eps (sum pi - 1) = ln(2)/4 + 1/8."""
+    ln2 = math.log(2.0)
+    a = b = np.array([0.5, 0.5])
+    C = np.array([[0.0, ln2], [ln2, 0.0]])
+    f, g = np.array([0.0, ln2]), np.zeros(2)
+    P = O.plan(f, g, C, a, b, 1.0)
+    assert np.allclose(P, [[0.25, 0.125], [0.25, 0.5]], rtol=0, atol=1e-15)
+    assert O.duality_gap(f, g, C, a, b, 1.0) == pytest.approx(ln2 / 4 + 0.125, rel=1e-14)
+    # the same value as the primal value of pi minus the dual value, by hand
+    primal = float((P * C).sum() + (P * np.log(P / np.outer(a, b))).sum())
+    dual = float(f @ a + g @ b - (P.sum() - 1.0))
+    assert primal - dual == pytest.approx(ln2 / 4 + 0.125, rel=1e-13)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_duality_gap_is_primal_minus_dual_anywhere(seed):
+    """At any (f, g), not only at the optimum, the gap equals the primal value
+    of pi(f, g) (Eq. primal_EOT, pinned at the optimum against the dual) minus
+    Q_eps(f, g) (Eq. def_Q): log(pi / (a b)) = (f + g - C)/eps turns the KL
+    term into <pi1, f> + <pi^T 1, g> - <pi, C>.  The value is far from zero
+    here, so a sign error or swapped marginal in the gap would show."""
+    rng = _rng(100 + seed)
+    n, m, eps = 7, 11, 0.3
+    C = rng.random((n, m))
+    a, b = _simplex(rng, n), _simplex(rng, m)
+    f, g = rng.standard_normal(n) * 0.2, rng.standard_normal(m) * 0.2
+    P = O.plan(f, g, C, a, b, eps)
+    gap = O.duality_gap(f, g, C, a, b, eps)
+    assert abs(gap) > 1e-3
+    assert gap == pytest.approx(O.primal_value(P, C, a, b, eps) - O.q_dual(f, g, C, a, b, eps),
+                                rel=1e-12, abs=1e-14)
+
+
 def test_eps_schedule():
     lv = O.eps_schedule(1e-1, 1e-3, 0.5)
     assert len(lv) == 8 and lv[0] == 1e-1 and lv[-1] == 1e-3
