@@ -102,6 +102,11 @@ typedef struct {
     eot_hessian hessian;
     int32_t poll_every;     /* iterations between host convergence polls (0: auto)    */
     void *stream;           /* cudaStream_t to run on; NULL: the library's own stream */
+    double wait_limit_s;    /* bound of every device-side wait of one CTA on others
+                               (the grid barriers of the cooperative Sinkhorn loop, the
+                               gang barriers of eot_solve_batch); a wait that exceeds it
+                               gives up and the solve returns EOT_ETIMEDOUT (the device
+                               stays usable).  <= 0 or not finite: 30 s               */
 } eot_options;
 
 typedef struct {
@@ -124,7 +129,7 @@ typedef struct {
 
 /* Fill *opt with defaults: tol 1e-6, max_iter 100000, ell 0, single level,
  * eps_factor 0.5, sequential modes, oversample 10, eig_tol 1e-2, eig_max_iter 100,
- * FP32, Hessian with D_a, automatic polling, library stream. */
+ * FP32, Hessian with D_a, automatic polling, library stream, 30 s wait limit. */
 void eot_default_options(eot_options *opt);
 
 /* Solve one problem (Algorithm 4.1 with eps continuation).  f_out (n) and
@@ -255,11 +260,28 @@ eot_status eot_marginal_error(int32_t n, int32_t m, const float *C, const double
  * up the array's address, so make that first call before any stream capture.
  * All calls share the array and it keeps the last call's contents: calls that
  * overlap on the GPU (other streams or threads without ordering) race.  Runs
- * on `stream` (NULL: the legacy default stream) and returns after it has
- * synchronised. */
+ * on `stream` (NULL: the legacy default stream); every call synchronises that
+ * stream before it returns, on success and on failure alike (it reads the
+ * cost's range back to the host, and a failed call leaves no work of its own
+ * running on the shared array). */
 eot_status eot_ctransform_noalloc(eot_side side, int32_t n, int32_t m, const float *C,
                                   const double *pot, const double *w, const double *shift,
                                   double eps, double *out, double *log_ratio, void *stream);
+
+/* The two exponentials of the float32 passes, elementwise, so that callers can
+ * check their accuracy (not a step of the method; Sec. 2 only needs exp):
+ *   variant 0: out_i = 2^(p_i + q_i) as the evaluation passes that verify a
+ *              result form it: p a float32 exponent, q a small correction
+ *              (|q| < 1/4) carried beside it; range reduction and a degree-7
+ *              Taylor series in float32, unbiased (mean relative error below
+ *              1e-9 over a range of arguments).
+ *   variant 1: out_i = the hardware approximation ex2.approx of the float32 sum
+ *              p_i + q_i, as the iterations form their terms (biased by a few
+ *              1e-8 relative, the same sign for every term).
+ * count >= 0 elements; p, q, out float32 device pointers.  Runs on `stream`
+ * (NULL: the legacy default stream) and returns once enqueued. */
+eot_status eot_exp2(int32_t count, const float *p, const float *q, int32_t variant, float *out,
+                    void *stream);
 
 /* Thread-local description of the last non-OK status returned on this thread. */
 const char *eot_last_error(void);

@@ -248,14 +248,15 @@ __global__ void __launch_bounds__(kThreads) colacc_kernel(AccArgs args) {
       }
       if (s4 && sl == 0) {
         // column transform h and the marginal test, as in the Sinkhorn column pass
-        float L = R * kLn2 + log_sum(Stot);
+        double Ld = (double)R * 0.6931471805599453 + (double)log_sum(Stot);
         const double sh = P.g[gb][jj];
-        double o = sh - P.eps * (double)L;
+        double o = sh - P.eps * Ld;
         if (!isfinite(o) || !(Stot > 0.0) || fabs(o) > P.pot_bound) {
           atomicAdd(&st->numeric, 1);
           o = sh;
-          L = 0.f;
+          Ld = 0.0;
         }
+        const float L = (float)Ld;
         P.g[dst_g][jj] = o;
         P.Lcol[jj] = L;
         double hi;
@@ -272,7 +273,7 @@ __global__ void __launch_bounds__(kThreads) colacc_kernel(AccArgs args) {
         sD[col] = dj;
         sB[col] = 1.0 / wj;
         accv[0] = wj * (double)fabsf(expm1f(L));
-        accv[1] = wj * (double)L;
+        accv[1] = wj * Ld;
         accv[2] = wj * o;
       }
     } else if (s4) {

@@ -66,6 +66,8 @@ void init_stream_attributes();
 int stream_ctas_per_sm();
 void stream_plan(int n, int m, bool col, int ctas, int* grid, int* slots);
 cudaError_t launch_sk_coop(const Prob* dP, const Prob& hP, int max_body, cudaStream_t s);
+cudaError_t launch_exp2_check(int count, const float* p, const float* q, int variant, float* out,
+                              cudaStream_t s);
 void init_gram_attributes();
 int gram_smem_bytes();
 void gram_plan(int nO, int nR, int ctas, int* grid, int* slots);
@@ -833,6 +835,15 @@ static size_t solver_footprint(DeviceCtx* ctx, int n, int m, int d, int ell, int
 
 static void drop_thread_cache() { t_cache.clear(); }
 
+static void evict_solver(Solver* S) {
+  for (auto it = t_cache.begin(); it != t_cache.end(); ++it) {
+    if (it->second.get() == S) {
+      t_cache.erase(it);
+      return;
+    }
+  }
+}
+
 static double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
@@ -854,6 +865,13 @@ static std::vector<double> schedule(double eps_start, double eps, double factor)
 }
 
 static bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+// Bound of a device wait on other CTAs, in globaltimer nanoseconds.
+static unsigned long long wait_ns(const eot_options* o) {
+  const double s = o->wait_limit_s;
+  if (!(s > 0.0) || !std::isfinite(s) || s >= 1e9) return kWaitNsDefault;
+  return std::max(1ull, (unsigned long long)(s * 1e9));
+}
 
 // Validate a problem's scalar fields (array contents are checked on the device).
 static eot_status validate(const eot_problem* pr, const eot_options* o) {
@@ -1037,6 +1055,7 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   P.qinv = std::ldexp(1.0, -q);
   P.M = (float)(1.5 * std::ldexp(1.0, 23 - q));
   P.pot_bound = gram ? 1e300 : std::ldexp(1.0, 22 - q) / 2.0 - cmax;
+  P.wait_ns = wait_ns(o);
   P.eps = eps0;
   P.k2 = (float)(1.0 / (eps0 * std::log(2.0)));
   P.k2lo = (float)(1.0 / (eps0 * std::log(2.0)) - (double)P.k2);
@@ -1274,11 +1293,14 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   if (fin.done == 1) status = EOT_OK;
   else if (fin.done == 2) status = EOT_NOT_CONVERGED;
   else if (fin.done == 3) status = EOT_ENUMERIC;
-  else if (fin.done == 4) status = EOT_ETIMEDOUT;
+  else if (fin.done == 4 || fin.done == 5) status = EOT_ETIMEDOUT;
   else status = EOT_NOT_CONVERGED;
+  bool wait_gave_up = fin.done == 5;
   for (int t = 0; t < L - 1 && status == EOT_OK; ++t) {
     if (hLev[t].done == 3) status = EOT_ENUMERIC;
+    if (hLev[t].done == 5) status = EOT_ETIMEDOUT;
   }
+  for (int t = 0; t < L; ++t) wait_gave_up = wait_gave_up || hLev[t].done == 5;
   r.status = status;
   if (res) *res = r;
   for (auto& e : lev_ev) cudaEventDestroy(e);
@@ -1290,7 +1312,13 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   (void)eig_ev0;
   (void)eig_ev1;
   if (status == EOT_ENUMERIC) t_err = "non-finite values or potentials outside the exact range";
-  if (status == EOT_ETIMEDOUT) t_err = "device loop reached its body cap";
+  if (status == EOT_ETIMEDOUT)
+    t_err = wait_gave_up ? "a grid-barrier wait gave up (wait_limit_s)"
+                         : "device loop reached its body cap";
+  // a cooperative launch that gave up left some passes unfinished (their
+  // arrival counters reset only when a pass completes): drop this solver so
+  // that the next solve of the shape starts from a fresh, zeroed arena
+  if (wait_gave_up) evict_solver(S);
   if (status == EOT_NOT_CONVERGED) t_err = "max_iter reached";
   return status;
 }
@@ -1762,6 +1790,7 @@ static eot_status run_batch(int count, const eot_problem* probs, const eot_optio
     T.f_out = p.trans ? L.go : L.fo;
     T.g_out = p.trans ? L.fo : L.go;
     T.bar = L.bar;
+    T.wait_ns = wait_ns(&o);
     T.flag = L.flag;
     T.out = d_out + k;
     T.tol_level = o.level_tol > 0.0 ? o.level_tol : o.tol;
@@ -1895,6 +1924,7 @@ void eot_default_options(eot_options* o) {
   o->hessian = EOT_HESS_DIAG_ALPHA;
   o->poll_every = 0;
   o->stream = nullptr;
+  o->wait_limit_s = 30.0;
 }
 
 eot_status eot_solve(const eot_problem* prob, const eot_options* opt, double* f_out,
@@ -2194,6 +2224,18 @@ eot_status eot_marginal_error(int32_t n, int32_t m, const float* C, const double
   if (st != EOT_OK) return st;
   if (row_l1) *row_l1 = S->hScores[0];
   if (col_l1) *col_l1 = S->hScores[1];
+  return EOT_OK;
+}
+
+eot_status eot_exp2(int32_t count, const float* p, const float* q, int32_t variant, float* out,
+                    void* stream) {
+  if (count < 0) return fail(EOT_EINVAL, "count must be >= 0");
+  if (count > 0 && (!p || !q || !out)) return fail(EOT_EINVAL, "null pointer");
+  if (variant != 0 && variant != 1) return fail(EOT_EINVAL, "variant must be 0 or 1");
+  DeviceCtx* ctx = nullptr;
+  eot_status cs = get_ctx(&ctx);
+  if (cs != EOT_OK) return cs;
+  CUDA_TRY(launch_exp2_check(count, p, q, variant, out, reinterpret_cast<cudaStream_t>(stream)));
   return EOT_OK;
 }
 

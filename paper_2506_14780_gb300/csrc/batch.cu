@@ -62,8 +62,8 @@ __device__ __forceinline__ void st_rel(unsigned* p, unsigned v) {
 }
 
 // Barrier of the G CTAs of a gang (G == 1: the CTA barrier).  Returns false
-// (in every thread) if the wait gave up.
-__device__ bool gang_sync(unsigned* bar, int G, int* s_flag) {
+// (in every thread) if the wait exceeded wait_ns and gave up.
+__device__ bool gang_sync(unsigned* bar, int G, unsigned long long wait_ns, int* s_flag) {
   __syncthreads();
   if (G > 1 && threadIdx.x == 0) {
     bool ok = true;
@@ -74,7 +74,7 @@ __device__ bool gang_sync(unsigned* bar, int G, int* s_flag) {
     } else {
       const unsigned long long t0 = gtime_ns();
       while (ld_acq(&bar[1]) == gen) {
-        if (gtime_ns() - t0 > kBWaitNs) {
+        if (gtime_ns() - t0 > wait_ns) {
           ok = false;
           break;
         }
@@ -516,7 +516,7 @@ __device__ void brun_task(const BatchTask& T, int rank, BShared& sh) {
   const unsigned long long t_begin = gtime_ns();
   unsigned long long t_last = t_begin;
   auto sync = [&]() -> bool {
-    if (gang_sync(T.bar, G, &sh.flag)) return true;
+    if (gang_sync(T.bar, G, T.wait_ns, &sh.flag)) return true;
     status = 4;
     return false;
   };

@@ -11,7 +11,7 @@ constexpr int kBMaxLev = 64;
 constexpr int kBMaxGang = 32;
 constexpr int kBRowU = 8;                 // 4-column groups a lane loads per step (row pass)
 constexpr double kBCostPerCta = 1.25 * 1024 * 1024;   // floor of the gang sizes: cost bytes per CTA
-constexpr unsigned long long kBWaitNs = 30000000000ull;   // 30 s bound of a gang wait
+constexpr unsigned long long kWaitNsDefault = 30000000000ull;   // 30 s bound of a device wait
 
 struct BatchOut {
   int status;        // 1 converged, 2 iteration cap, 3 numeric, 4 gang wait gave up
@@ -33,6 +33,7 @@ struct BatchTask {
   float *Lrow, *Lcol;
   double *f_out, *g_out;
   unsigned* bar;                  // [2]: arrivals, generation
+  unsigned long long wait_ns;     // bound of a gang-barrier wait (globaltimer ns)
   unsigned* flag;                 // numeric flag of the problem (0 / 1)
   BatchOut* out;
   double tol_level, tol_last, tol_verify;

@@ -32,7 +32,8 @@ enum PassMode : int {
 // Device-resident solver state (one per problem).
 struct State {
   int iter;        // Algorithm 4.1 iterations done at the current level
-  int done;        // 0 running, 1 converged, 2 max_iter, 3 numeric error
+  int done;        // 0 running, 1 converged, 2 max_iter, 3 numeric error,
+                   // 4 loop body cap, 5 a grid-barrier wait gave up
   int cur_f;       // index of the current f buffer (0/1)
   int cur_g;       // index of the current g buffer (0..2)
   int nr_acc, nr_rej;
@@ -116,6 +117,7 @@ struct Prob {
   double* sk_acc_col;      // [ceil(m/32)][4] (per 128-column block, or per 32-column unit)
   double* sk_acc_row;      // [ceil(n/32)][4]
   unsigned* gbar;          // [2] grid barrier of the cooperative Sinkhorn loop
+  unsigned long long wait_ns;   // bound of a grid-barrier wait (globaltimer ns)
   // on-the-fly cost (EOT_PREC_SPLIT_TC): C_ij = |x_i|^2 + |y_j|^2 - 2 x_i.y_j
   // with the Gram products on the tensor cores (3xTF32, float32 accumulation)
   int gram;                // 1 in that mode

@@ -93,14 +93,15 @@ __device__ __noinline__ void colmma_finish(const AccArgs& args, const Prob& P, u
     if (s4) {
       sD[c] = 0.f;
       if (jv) {
-        float L = R * kLn2 + log_sum(Stot);
+        double Ld = (double)R * 0.6931471805599453 + (double)log_sum(Stot);
         const double sh = P.g[gb][j];
-        double o = sh - P.eps * (double)L;
+        double o = sh - P.eps * Ld;
         if (!isfinite(o) || !(Stot > 0.0) || fabs(o) > P.pot_bound) {
           atomicAdd(&st->numeric, 1);
           o = sh;
-          L = 0.f;
+          Ld = 0.0;
         }
+        const float L = (float)Ld;
         // the products need the exponentials in range: flag a column whose
         // largest term lies far from 1 (the Newton step is then skipped)
         if (R > 60.f || R < -60.f) atomicOr(&st->nr_degenerate, 1);
@@ -120,7 +121,7 @@ __device__ __noinline__ void colmma_finish(const AccArgs& args, const Prob& P, u
         args.dw[j] = dj;
         sD[c] = (float)dj;
         accv[0] = wj * (double)fabsf(em);
-        accv[1] = wj * (double)L;
+        accv[1] = wj * Ld;
         accv[2] = wj * o;
       }
     }

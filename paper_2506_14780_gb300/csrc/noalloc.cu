@@ -17,9 +17,12 @@
 // fit the array; larger sizes return EOT_EINVAL before any device work.
 // The first call on a device looks up the array's device address
 // (cudaGetSymbolAddress) with that device current; make that first call before
-// any stream capture.  All calls share the one array and it keeps the last
-// call's contents: calls that overlap on the GPU (on different streams or
-// threads without ordering) race and corrupt each other.
+// any stream capture.  Every call synchronises the caller's stream before it
+// returns (it reads the cost's range back to the host to place the exponent
+// grid), also when it fails after enqueueing work.  All calls share the one
+// array and it keeps the last call's contents: calls that overlap on the GPU
+// (on different streams or threads without ordering) race and corrupt each
+// other.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -152,10 +155,16 @@ extern "C" eot_status eot_ctransform_noalloc(eot_side side, int32_t n, int32_t m
     return na_fail(EOT_EINVAL, "eot_ctransform_noalloc: problem too large for the static scratch");
   P.st = dSt;
 
+  // On a failure after work was enqueued, wait for that work before
+  // returning: a retry (on any stream) must not overlap kernels that still
+  // use the shared array.  The wait's own status is not needed.
 #define NA_TRY(expr)                                                                  \
   do {                                                                                \
     cudaError_t _e = (expr);                                                          \
-    if (_e != cudaSuccess) return na_fail(EOT_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+    if (_e != cudaSuccess) {                                                          \
+      (void)cudaStreamSynchronize(s);                                                 \
+      return na_fail(EOT_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(_e));  \
+    }                                                                                 \
   } while (0)
 
   // everything that must start at zero: state, counters, the unused weights

@@ -16,13 +16,16 @@ __device__ __forceinline__ void finish_index_v(float R, double S, int idx, const
                                                double* __restrict__ out, Split so,
                                                float* __restrict__ Lout, double acc[3],
                                                int* numeric) {
-  float L = R * kLn2 + log_sum(S);
-  double o = sh - P.eps * (double)L;
+  // the log-ratio in float64: far from the shift (|L| large) a float32 L
+  // would move the output by eps |L| 2^-24
+  double Ld = (double)R * 0.6931471805599453 + (double)log_sum(S);
+  double o = sh - P.eps * Ld;
   if (!isfinite(o) || !(S > 0.0) || fabs(o) > P.pot_bound) {
     atomicAdd(numeric, 1);
     o = sh;
-    L = 0.f;
+    Ld = 0.0;
   }
+  const float L = (float)Ld;
   if (out) out[idx] = o;
   if (Lout) Lout[idx] = L;
   if (so.A && so.nrm) {
@@ -44,7 +47,7 @@ __device__ __forceinline__ void finish_index_v(float R, double S, int idx, const
     so.KL[idx] = lo;
   }
   acc[0] = wi * (double)fabsf(expm1f(L));
-  acc[1] = wi * (double)L;
+  acc[1] = wi * Ld;
   acc[2] = wi * o;
 }
 

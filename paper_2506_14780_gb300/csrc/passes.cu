@@ -23,6 +23,8 @@
 // arrival counter) merges the segments in parallel and in a fixed order, so
 // results are deterministic; the last index block then runs the mode-specific
 // grid-wide step.
+#include <algorithm>
+
 #include "eot_device.cuh"
 #include "eot_internal.h"
 #include "reduce.cuh"
@@ -852,6 +854,25 @@ cudaError_t launch_shift64(const Prob* dP, const double* p, const double* logw, 
                            double* out, cudaStream_t s) {
   const int blocks = (len + 255) / 256;
   shift64_kernel<<<blocks < 1024 ? blocks : 1024, 256, 0, s>>>(dP, p, logw, len, out);
+  return cudaGetLastError();
+}
+
+// The two exponentials of the float32 passes, elementwise, for accuracy
+// checks: variant 0 is 2^(p + q) of the evaluation passes that verify a
+// result (ex2_pq), variant 1 the hardware approximation of the iterations
+// applied to the float32 sum p + q.
+__global__ void exp2_check_kernel(int count, const float* __restrict__ p,
+                                  const float* __restrict__ q, int variant,
+                                  float* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+    out[i] = variant == 0 ? ex2_pq(p[i], q[i]) : ex2_approx(__fadd_rn(p[i], q[i]));
+}
+
+cudaError_t launch_exp2_check(int count, const float* p, const float* q, int variant, float* out,
+                              cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const int grid = (int)std::min<long long>(((long long)count + 255) / 256, 4096);
+  exp2_check_kernel<<<grid, 256, 0, s>>>(count, p, q, variant, out);
   return cudaGetLastError();
 }
 

@@ -61,7 +61,6 @@ constexpr int kStSmem = kStStages * kStStageBytes;
 constexpr int kStThreads = kStConsumers + 32;
 constexpr int kStWait = 1 << 22;
 constexpr int kStPend = 16;
-constexpr int kGridWait = 1 << 24;
 
 // Static shared state of a stream CTA.
 struct StShared {
@@ -620,7 +619,7 @@ __device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
 // returned.  Returns that code to every thread of every CTA, or -1 after a
 // wait that gave up.
 template <class F>
-__device__ int grid_sync(unsigned* bar, StShared& sh, F on_release) {
+__device__ int grid_sync(unsigned* bar, unsigned long long wait_ns, StShared& sh, F on_release) {
   __syncthreads();
   const int lane = threadIdx.x & 31;
   if ((threadIdx.x >> 5) == 0) {
@@ -645,10 +644,13 @@ __device__ int grid_sync(unsigned* bar, StShared& sh, F on_release) {
         st_release(&bar[1], (gen & ~3u) + 4u + (unsigned)code);
       }
     } else if (lane == 0) {
-      int k = 0;
+      unsigned long long t0;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
       unsigned now;
       while ((now = ld_acquire(&bar[1])) == gen) {
-        if (++k > kGridWait) break;
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > wait_ns) break;
         __nanosleep(32);
       }
       code = now == gen ? -1 : (int)(now & 3u);
@@ -707,7 +709,7 @@ __global__ void __launch_bounds__(kStThreads, 2)
       }
       it += chunk;
       // the releaser takes the row sums (the row step of the mode)
-      code = grid_sync(bar, sh, [&]() -> int {
+      code = grid_sync(bar, P.wait_ns, sh, [&]() -> int {
         double tot[3];
         warp0_grid_sum3(P.sk_acc_row, g.ntr, tot);
         if ((threadIdx.x & 31) == 0) {
@@ -739,7 +741,7 @@ __global__ void __launch_bounds__(kStThreads, 2)
       it += chunk;
       ++iter;
       // the releaser takes the decision of Algorithm 4.1 (L1 test) for all
-      code = grid_sync(bar, sh, [&]() -> int {
+      code = grid_sync(bar, P.wait_ns, sh, [&]() -> int {
         double tot[3];
         warp0_grid_sum3(P.sk_acc_col, g.ntc, tot);
         int done = 0;
@@ -762,10 +764,11 @@ __global__ void __launch_bounds__(kStThreads, 2)
       cg = io.dst_g;
     }
   }
+  // a barrier wait or a pipeline wait of this CTA that gave up: the loop
+  // stops with the timeout state (the host reports EOT_ETIMEDOUT)
   const bool failed = code < 0 || sh.err;
   if (failed) {
-    if (tid == 0) atomicAdd(&st->numeric, 1);
-    if (blockIdx.x == 0 && tid == 0) st->done = 3;
+    if (tid == 0) st->done = 5;
   } else if (code == 0 && body >= max_body && blockIdx.x == 0 && tid == 0) {
     st->done = 4;   // iteration cap of this launch
   }

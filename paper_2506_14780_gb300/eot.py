@@ -41,7 +41,8 @@ class eot_options(C.Structure):
                 ("eps_start", C.c_double), ("eps_factor", C.c_double), ("level_tol", C.c_double),
                 ("sequential_modes", C.c_int32), ("oversample", C.c_int32),
                 ("eig_tol", C.c_double), ("eig_max_iter", C.c_int32), ("prec", C.c_int32),
-                ("hessian", C.c_int32), ("poll_every", C.c_int32), ("stream", C.c_void_p)]
+                ("hessian", C.c_int32), ("poll_every", C.c_int32), ("stream", C.c_void_p),
+                ("wait_limit_s", C.c_double)]
 
 
 class eot_result(C.Structure):
@@ -90,6 +91,7 @@ _SIGNATURES = {
                                      _PTR]),
     "eot_batch_plan": (C.c_int, [C.c_int32, _PTR, _PTR, _PTR, _PTR, C.POINTER(eot_options),
                                  C.c_int32, C.c_double, C.c_double, C.c_double, _PTR, _PTR]),
+    "eot_exp2": (C.c_int, [C.c_int32, _PTR, _PTR, C.c_int32, _PTR, _PTR]),
     "eot_last_error": (C.c_char_p, []),
     "eot_version": (C.c_char_p, []),
 }
@@ -281,6 +283,12 @@ def eot_batch_plan(n, m, eps, options: eot_options, grid_ctas: int, step_ns: flo
                                int(grid_ctas), float(step_ns), float(fix_ns), float(bar_ns),
                                gang.ctypes.data, tr.ctypes.data)
     return st, gang, tr
+
+
+def eot_exp2(p, q, variant: int, out, stream=None) -> int:
+    """Elementwise 2^(p + q) of the float32 passes (device float32 tensors)."""
+    return load().eot_exp2(int(p.numel()), p.data_ptr(), q.data_ptr(), int(variant),
+                           out.data_ptr(), stream)
 
 
 def eot_marginal_error(n, m, Cdev, f, g, a, b, eps, stream=None):

@@ -1,0 +1,66 @@
+"""Write ``c2_oracle_counts.json``: the float64 oracle's own iteration counts on
+the benchmark workload, so that the timed CPU baseline (a bounded sample of
+oracle iterations) scales by the oracle's counts, not by the GPU's.
+
+Workload: ``workloads.gaussian_mixture(4096, 4096, seed=0)`` (4 components,
+sigma 0.1, Dirichlet(1) weights), squared Euclidean cost normalised to max 1
+and rounded to float32 (the device input), promoted to float64.  Solves: eps
+continuation 1e-1 -> 1e-3 by halving (Sec. 5), L1 marginal tolerance 1e-6 at
+every level (Algorithm 4.1's stopping test); SK-NR(30) with the D_a Hessian,
+modes refreshed at every level by block subspace iteration (block 40, Ritz
+residual 1e-2, at most 100 steps, started from the previous level's modes);
+plain Sinkhorn on the same schedule.
+
+Calls only ``oracle`` and ``workloads``.  Run from the repository root:
+``python tests/golden/make_c2_oracle_counts.py`` (about an hour on one core).
+"""
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import oracle as O  # noqa: E402
+import workloads as W  # noqa: E402
+
+OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "c2_oracle_counts.json")
+
+
+def main():
+    prob = W.gaussian_mixture(4096, 4096, seed=0, eps=1e-3)
+    C = O.sq_euclidean_cost(prob.X, prob.Y, normalize=True).astype(np.float32).astype(np.float64)
+    levels = O.eps_schedule(1e-1, 1e-3, 0.5)
+    out = {"workload": "gaussian_mixture_4096x4096_d3 seed 0, float32 cost normalised to max 1",
+           "levels": levels, "tol": 1e-6}
+    for name, ell in (("sknr30", 30), ("sinkhorn", 0)):
+        f = np.zeros(4096)
+        V = None
+        rows = []
+        t0 = time.perf_counter()
+        for t, e in enumerate(levels):
+            res = O.sknr(C, prob.a, prob.b, e, V if ell else None, tol=1e-6, max_iter=100000,
+                         f0=f, hessian="diag_alpha")
+            f = res.f
+            row = {"eps": e, "iters": res.iters, "converged": res.converged,
+                   "nr_accepted": res.nr_accepted, "nr_rejected": res.nr_rejected,
+                   "eig_iters": 0}
+            if ell and t < len(levels) - 1:
+                V, _, it, _ = O.spectral_modes_subspace(res.f, res.g, C, prob.a, prob.b, e, ell,
+                                                        oversample=10, tol=1e-2, max_iter=100,
+                                                        seed=t, V0=V)
+                row["eig_iters"] = it
+            rows.append(row)
+            print(name, row, f"{time.perf_counter() - t0:.0f} s", flush=True)
+        out[name] = {"per_level": rows,
+                     "total_iters": int(sum(r["iters"] for r in rows)),
+                     "eig_iters": int(sum(r["eig_iters"] for r in rows))}
+        with open(OUT, "w") as fh:
+            json.dump(out, fh, indent=1)
+
+
+if __name__ == "__main__":
+    main()

@@ -57,6 +57,59 @@ def test_noalloc_matches_allocating_transform(pkg):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("side", ["col", "row"])
+def test_noalloc_without_shift(pkg, side):
+    """shift = NULL: the call runs two passes (the first one places the
+    reference) through the same static array; same results as eot_ctransform
+    and as the oracle, on two calls in a row."""
+    eps = 2e-3
+    n, m = (1500, 1003) if side == "col" else (901, 2052)
+    prob = W.random_cost(n, m, seed=21 + n)
+    C64 = prob.C.astype(np.float64)
+    rng = np.random.default_rng(n)
+    s = pkg.EOT_SIDE_COL if side == "col" else pkg.EOT_SIDE_ROW
+    if side == "col":
+        pot, w, nout = rng.random(n) * 0.5, prob.a, m
+        ref = O.c_transform_f(pot, C64, prob.a, eps)
+    else:
+        pot, w, nout = rng.random(m) * 0.5, prob.b, n
+        ref = O.c_transform_g(pot, C64, prob.b, eps)
+    dC, dpot, dw = _dev(prob.C), _dev(pot), _dev(w)
+    for _ in range(2):
+        outs = []
+        for fn in (pkg.eot_ctransform, pkg.eot_ctransform_noalloc):
+            out = torch.zeros(nout, dtype=torch.float64, device="cuda")
+            assert fn(s, n, m, dC, dpot, dw, None, eps, out, None) == pkg.EOT_OK, pkg.last_error()
+            outs.append(out.cpu().numpy())
+        assert np.abs(outs[1] - outs[0]).max() <= 1e-5 * eps
+        assert np.abs(outs[1] - ref).max() <= 1e-5 * eps
+
+
+@pytest.mark.gpu
+def test_noalloc_at_its_size_limit(pkg):
+    """n = m = 16384, the largest size the static array serves: the carve-out
+    fits on this device and the result equals the allocating transform's; the
+    oracle checks a sample of output columns (each column's transform needs
+    only that column of the cost)."""
+    eps = 5e-3
+    n = m = 16384
+    prob = W.random_cost(n, m, seed=5)
+    rng = np.random.default_rng(6)
+    pot = rng.random(n) * 0.5
+    dC, dpot, dw = _dev(prob.C), _dev(pot), _dev(prob.a)
+    outs = []
+    for fn in (pkg.eot_ctransform, pkg.eot_ctransform_noalloc):
+        out = torch.zeros(m, dtype=torch.float64, device="cuda")
+        st = fn(pkg.EOT_SIDE_COL, n, m, dC, dpot, dw, None, eps, out, None)
+        assert st == pkg.EOT_OK, pkg.last_error()
+        outs.append(out.cpu().numpy())
+    assert np.abs(outs[1] - outs[0]).max() <= 1e-5 * eps
+    cols = rng.choice(m, 64, replace=False)
+    ref = O.c_transform_f(pot, prob.C[:, cols].astype(np.float64), prob.a, eps)
+    assert np.abs(outs[1][cols] - ref).max() <= 1e-5 * eps
+
+
+@pytest.mark.gpu
 def test_noalloc_rejects_sizes_beyond_its_scratch(pkg):
     C = torch.zeros(1, dtype=torch.float32, device="cuda")
     v = torch.zeros(1, dtype=torch.float64, device="cuda")
