@@ -224,6 +224,48 @@ eot_status eot_spectral_modes(int32_t n, int32_t m, const float *C, const double
                               int32_t use_V_as_start, double *V, double *rho2,
                               int32_t *iters_out, double *resid_out, void *stream);
 
+/* Scalars of one SK-NR iteration (eot_sknr_step). */
+typedef struct {
+    double col_l1;      /* sum_j b_j |exp((g_j - h_j)/eps) - 1|: the column term of the
+                           L1 test of Algorithm 4.1 at (f_k, g_k)                      */
+    double q_semi;      /* Q_semi(f_k) = <f_k, a> + <h, b>  (Eq. def_Q_semi)            */
+    double dq;          /* Q_semi(f') - Q_semi(f_k), summed as <V Delta, a> + <h' - h, b> */
+    int32_t newton_ok;  /* 0: -H_V not positive definite (or the products saw
+                           exponentials out of range): no trial, the step is rejected */
+    int32_t accepted;   /* 1: dq > 0, (f', h') is the next iterate; 0: (f_k, h) is     */
+    double stage_seconds[4]; /* device time (CUDA events on the call's stream) of the
+                           row half-step that forms f_k, the S4 pass (h, W, test),
+                           the Newton solve (W^T D_b^-1 W reduction, factorisation,
+                           f'), and the trial column pass                          */
+} eot_sknr_info;
+
+/* One iteration of Algorithm 4.1 (lines 4-16) from g_k with the caller's modes
+ * V, on a float32 cost, exposing every intermediate of the Newton step:
+ *   f_k   = g_k^{C,eps}                                  (Eq. foc_f, line 4)
+ *   h     = f_k^{C,eps}                                  (Eq. foc_g)
+ *   W     = pi(f_k, h)^T V   (m x ell, float32)
+ *   grad  = V^T (a - pi(f_k, h) 1), formed as -sum_j d_j W_j with
+ *           d_j = 1 - exp((g_j - h_j)/eps)               (Eq. dQ_semi on V)
+ *   GV    = V^T D_a V,  WtDW = W^T D_b^-1 W,  -H_V = (GV - WtDW)/eps
+ *                                                        (Eq. d2Q_semi, D_r ~ D_a)
+ *   delta = (-H_V)^-1 grad                               (lines 12-13)
+ *   f'    = f_k + V delta,  h' = f'^{C,eps}               (lines 14-16)
+ * and the scalars in *info.  The float32 passes, tensor-core products and
+ * float32 factorisation are those of eot_solve's SK-NR iterations.
+ * Arguments: n >= 3, m >= 1, 1 <= ell <= 47, ell < n.  C (n x m, float32),
+ * a (n), b (m) (used as given), g (m), V (n x ell, float64 row-major; the
+ * library rounds it to float32 as eot_solve stores its modes; it should be
+ * a-orthonormal and a-orthogonal to the constants, Sec. 4): device pointers.
+ * Outputs (device pointers, each optional): f_k (n), h (m), W (m x ell,
+ * float32), grad (ell), GV (ell x ell), WtDW (ell x ell), delta (ell),
+ * f_trial (n) and h_trial (m) (left untouched when newton_ok is 0); info
+ * (host, optional).  Synchronises `stream` before it returns. */
+eot_status eot_sknr_step(int32_t n, int32_t m, int32_t ell, const float *C, const double *a,
+                         const double *b, double eps, const double *g, const double *V,
+                         double *f_k, double *h, float *W, double *grad, double *GV,
+                         double *WtDW, double *delta, double *f_trial, double *h_trial,
+                         eot_sknr_info *info, void *stream);
+
 /* The schedule eot_solve_batch would use, computed on the host only (no
  * device work, no GPU needed): for count problems of sizes n[k] x m[k] at
  * eps[k] (has_f_init[k] != 0 if the problem carries a warm start; NULL: none

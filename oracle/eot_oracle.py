@@ -13,6 +13,7 @@ Pins (what fixes each function independently of this file; the tests live in
 ``tests/test_oracle_*.py``):
 
 * ``sq_euclidean_cost``       brute-force per-entry loop; translation invariance.
+* ``sq_euclidean_cost_gram``  the per-entry loop, to float64 cancellation.
 * ``c_transform_f`` / ``_g``  separable cost closed form, m = 1 closed form,
                               eps -> infinity limit, permutation equivariance,
                               log-sum-exp against direct summation at safe scales.
@@ -57,14 +58,14 @@ from typing import Optional
 import numpy as np
 
 __all__ = [
-    "sq_euclidean_cost", "cost_entries",
+    "sq_euclidean_cost", "sq_euclidean_cost_gram", "cost_entries",
     "lse", "c_transform_f", "c_transform_g",
     "plan", "marginals", "marginal_errors",
     "q_dual", "q_semi", "primal_value", "duality_gap", "evaluate", "gauge_normalize",
     "grad_semi", "hess_semi", "hess_dual",
     "op_pi", "op_pi_T", "operator_K", "R_matrix", "semidual_operator_M",
     "splitmix64_uniform", "spectral_modes_dense", "spectral_modes_subspace",
-    "spectral_modes_chebyshev", "newton_cg",
+    "spectral_modes_chebyshev", "newton_cg", "newton_step",
     "SolveResult", "sinkhorn", "sknr", "eps_schedule", "continuation",
     "bruteforce_ot", "dense_newton",
 ]
@@ -92,6 +93,16 @@ def sq_euclidean_cost(X, Y, normalize: bool = False) -> np.ndarray:
         if cmax > 0:
             C = C / cmax
     return C
+
+
+def sq_euclidean_cost_gram(X, Y) -> np.ndarray:
+    """C_ij = |x_i|^2 + |y_j|^2 - 2 x_i . y_j in float64, the same cost with
+    the cross term as one matrix product (a library routine); for large clouds
+    where the per-coordinate loop of ``sq_euclidean_cost`` is slow.  The
+    cancellation loses at most a few float64 ulps of |x_i|^2 + |y_j|^2."""
+    X = _f64(X)
+    Y = _f64(Y)
+    return (X * X).sum(axis=1)[:, None] + (Y * Y).sum(axis=1)[None, :] - 2.0 * (X @ Y.T)
 
 
 def cost_entries(X, Y, rows, cols, scale: float = 1.0) -> np.ndarray:
@@ -493,6 +504,58 @@ def newton_cg(A, rhs, tol: float = 1e-14, max_iter: Optional[int] = None):
     return x, True
 
 
+def newton_step(f, C, a, b, eps, V, hessian: str = "exact", newton: str = "direct") -> dict:
+    """The Newton part of one iteration of Algorithm 4.1 at f = f_k (after the
+    row half-step), with every intermediate returned:
+
+      h = f_k^{C,eps} (Eq. foc_g) and Q_semi(f_k) = <f_k, a> + <h, b>;
+      pi = pi(f_k, h), r = pi 1, W = pi^T V;
+      grad = V^T (a - r)                              (Eq. dQ_semi on V);
+      GV = V^T D V with D = D_r (exact) or D_a (``diag_alpha``), WtDW = W^T D_b^-1 W,
+      H = -(1/eps) [GV - WtDW]                        (Eq. d2Q_semi on V);
+      ok = -H positive definite (Cholesky), Delta = (-H)^-1 grad;
+      f' = f_k + V Delta, h' = f'^{C,eps}, Q_semi(f') = <f', a> + <h', b>;
+      accepted = Q_semi(f') > Q_semi(f_k) (strict), dq = Q_semi(f') - Q_semi(f_k),
+      dq_diff = <V Delta, a> + <h' - h, b> (the same difference, summed as one).
+    With ``newton="cg"`` Delta comes from ``newton_cg``; ok is then its
+    curvature test.  When ok is False the trial entries are None.
+    """
+    f, C, a, b, V = map(_f64, (f, C, a, b, V))
+    h = c_transform_f(f, C, a, eps)
+    q_k = float(f @ a + h @ b)
+    P = plan(f, h, C, a, b, eps)
+    r = P.sum(axis=1)
+    grad = V.T @ (a - r)
+    W = P.T @ V
+    d = r if hessian == "exact" else a
+    GV = V.T @ (d[:, None] * V)
+    WtDW = W.T @ (W / b[:, None])
+    H = -(1.0 / eps) * (GV - WtDW)
+    negH = 0.5 * (-H - H.T)
+    out = {"h": h, "q_semi": q_k, "r": r, "W": W, "grad": grad, "GV": GV, "WtDW": WtDW,
+           "H": H, "ok": True, "delta": None, "f_trial": None, "h_trial": None,
+           "q_trial": None, "dq": None, "dq_diff": None, "accepted": False}
+    if newton == "cg":
+        delta, ok = newton_cg(negH, grad)
+        if not ok:
+            out["ok"] = False
+            return out
+    else:
+        try:
+            np.linalg.cholesky(negH)
+        except np.linalg.LinAlgError:
+            out["ok"] = False
+            return out
+        delta = np.linalg.solve(negH, grad)
+    step = V @ delta
+    f_new = f + step
+    h_new = c_transform_f(f_new, C, a, eps)
+    q_new = float(f_new @ a + h_new @ b)
+    out.update(delta=delta, f_trial=f_new, h_trial=h_new, q_trial=q_new, dq=q_new - q_k,
+               dq_diff=float(step @ a + (h_new - h) @ b), accepted=q_new > q_k)
+    return out
+
+
 def sknr(C, a, b, eps, V=None, tol: float = 1e-6, max_iter: int = 10000, f0=None,
          hessian: str = "exact", record: bool = False, newton: str = "direct") -> SolveResult:
     """Algorithm 4.1, SK-NR(l).  With V None (or l = 0) it is log-domain Sinkhorn.
@@ -529,30 +592,12 @@ def sknr(C, a, b, eps, V=None, tol: float = 1e-6, max_iter: int = 10000, f0=None
             res.converged = True
             break
         if ell > 0:
-            h = c_transform_f(f, C, a, eps)
-            q_k = float(f @ a + h @ b)
-            P = plan(f, h, C, a, b, eps)
-            r = P.sum(axis=1)
-            grad = V.T @ (a - r)
-            W = P.T @ V
-            d = r if hessian == "exact" else a
-            H = -(1.0 / eps) * (V.T @ (d[:, None] * V) - W.T @ (W / b[:, None]))
-            negH = 0.5 * (-H - H.T)
-            if newton == "cg":
-                delta, ok = newton_cg(negH, grad)
-                if not ok:
-                    res.nr_rejected += 1
-                    continue
-            else:
-                try:
-                    np.linalg.cholesky(negH)
-                except np.linalg.LinAlgError:
-                    res.nr_rejected += 1
-                    continue
-                delta = np.linalg.solve(negH, grad)
-            f_new = f + V @ delta
-            if q_semi(f_new, C, a, b, eps) > q_k:
-                f = f_new
+            step = newton_step(f, C, a, b, eps, V, hessian=hessian, newton=newton)
+            if not step["ok"]:
+                res.nr_rejected += 1
+                continue
+            if step["accepted"]:
+                f = step["f_trial"]
                 res.nr_accepted += 1
             else:
                 res.nr_rejected += 1

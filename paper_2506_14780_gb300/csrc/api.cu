@@ -1949,6 +1949,16 @@ const char* eot_version(void) { return "eot-gb300 0.1 (sm_103a)"; }
 // ===========================================================================
 namespace eotk {
 
+__global__ void cast_f32_kernel(const double* __restrict__ x, long long len, float* __restrict__ y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+
+__global__ void neg_copy_kernel(const double* __restrict__ x, int len, double* __restrict__ y) {
+  for (int i = threadIdx.x; i < len; i += blockDim.x) y[i] = -x[i];
+}
+
 // Pick the exponent grid for a standalone call from max|C| and the potentials.
 static eot_status standalone_grid(Solver* S, const float* Cdev, const double* p1, int l1,
                                   const double* p2, int l2, double eps, cudaStream_t s,
@@ -2304,6 +2314,99 @@ eot_status eot_spectral_modes(int32_t n, int32_t m, const float* C, const double
   if (resid_out) *resid_out = S->hSt->eig_resid;
   if (S->hSt->eig_done == 4) return fail(EOT_ETIMEDOUT, "mode loop reached its body cap");
   return S->hSt->eig_done == 1 ? EOT_OK : EOT_NOT_CONVERGED;
+}
+
+eot_status eot_sknr_step(int32_t n, int32_t m, int32_t ell, const float* C, const double* a,
+                         const double* b, double eps, const double* g, const double* V,
+                         double* f_k, double* h, float* W, double* grad, double* GV,
+                         double* WtDW, double* delta, double* f_trial, double* h_trial,
+                         eot_sknr_info* info, void* stream) {
+  if (!C || !a || !b || !g || !V) return fail(EOT_EINVAL, "C, a, b, g and V are required");
+  if (n < 3 || m < 1) return fail(EOT_EINVAL, "need n >= 3 and m >= 1");
+  if (ell < 1 || ell + 1 > kMaxP || ell >= n) return fail(EOT_EINVAL, "need 1 <= ell <= 47, ell < n");
+  if (!finite_pos(eps)) return fail(EOT_EINVAL, "eps must be finite and > 0");
+  const int p = mode_block(n, ell, 0);
+  Solver* S = nullptr;
+  cudaStream_t s;
+  eot_status st = standalone_solver(n, m, ell, p, &S, &s, stream);
+  if (st != EOT_OK) return st;
+  st = load_weights(S, a, b, s, 0);
+  if (st != EOT_OK) return st;
+  st = standalone_grid(S, C, g, m, nullptr, 0, eps, s, nullptr);
+  if (st != EOT_OK) return st;
+  Prob& P = S->hP;
+  // modes: float32 copy, their tensor-core tiles, V^T D_a V and V^T a
+  cast_f32_kernel<<<std::min(ceil_div((long long)n * ell, 256), 8 * S->ctx->nsm), 256, 0, s>>>(
+      V, (long long)n * ell, S->V);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(P.g[0], g, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemsetAsync(P.f[0], 0, n * sizeof(double), s));
+  State st0{};
+  st0.max_iter = 1 << 30;
+  st0.tol = -1.0;   // no convergence stop: the step runs whole
+  CUDA_TRY(cudaMemcpyAsync(S->dSt, &st0, sizeof(State), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(S->dP, &P, sizeof(Prob), cudaMemcpyHostToDevice, s));
+  launch_eig_gram(S->V, nullptr, P.a, n, ell, S->egpart, P.GV, nullptr, P.Va, s);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(launch_build_tiles(S->V, n, ell, S->tilesV, s));
+  CUDA_TRY(S->prep_level(s));
+  // line 4: f_k = g_k^{C,eps}.  The first row pass, from the zero shift,
+  // places the reference; the second one forms f_k in delta form from it.
+  CUDA_TRY(S->pass_row(MODE_SK_ROW, s));
+  cudaEvent_t ev[5];
+  for (auto& e : ev) CUDA_TRY(cudaEventCreate(&e));
+  struct EvGuard {
+    cudaEvent_t* e;
+    ~EvGuard() {
+      for (int k = 0; k < 5; ++k) cudaEventDestroy(e[k]);
+    }
+  } ev_guard{ev};
+  CUDA_TRY(cudaEventRecord(ev[0], s));
+  CUDA_TRY(S->pass_row(MODE_SK_ROW, s));
+  CUDA_TRY(cudaEventRecord(ev[1], s));
+  // S4 (h, W, the L1 test, Q_semi), S5 (Newton), S6 (trial and acceptance):
+  // the kernels of one SK-NR loop body
+  const AccArgs acc = S->s4_args();
+  CUDA_TRY(launch_colmma(acc, P, S->tilesV, S->mm_ncolblk, s));
+  CUDA_TRY(cudaEventRecord(ev[2], s));
+  CUDA_TRY(launch_wtw_reduce(acc, S->WtW, S->gw, s));
+  newton_kernel<<<1, 256, 0, s>>>(S->dP, S->WtW, S->gw, nullptr);
+  fprime_kernel<<<std::min(ceil_div(n, 256), 4 * S->ctx->nsm), 256, 0, s>>>(S->dP);
+  CUDA_TRY(cudaEventRecord(ev[3], s));
+  CUDA_TRY(S->pass_col(MODE_TRIAL, s));
+  CUDA_TRY(cudaEventRecord(ev[4], s));
+  CUDA_TRY(cudaMemcpyAsync(S->hSt, S->dSt, sizeof(State), cudaMemcpyDeviceToHost, s));
+  // buffers: f_k in f[0], h in g[1], f' in f[1], h' in g[2] (start cur_f = cur_g = 0)
+  const cudaMemcpyKind dd = cudaMemcpyDeviceToDevice;
+  if (f_k) CUDA_TRY(cudaMemcpyAsync(f_k, P.f[0], n * sizeof(double), dd, s));
+  if (h) CUDA_TRY(cudaMemcpyAsync(h, P.g[1], m * sizeof(double), dd, s));
+  if (W) CUDA_TRY(cudaMemcpyAsync(W, S->W, (size_t)m * ell * sizeof(float), dd, s));
+  if (grad) neg_copy_kernel<<<1, 64, 0, s>>>(S->gw, ell, grad);
+  if (GV) CUDA_TRY(cudaMemcpyAsync(GV, P.GV, (size_t)ell * ell * sizeof(double), dd, s));
+  if (WtDW) CUDA_TRY(cudaMemcpyAsync(WtDW, S->WtW, (size_t)ell * ell * sizeof(double), dd, s));
+  if (delta) CUDA_TRY(cudaMemcpyAsync(delta, P.delta, ell * sizeof(double), dd, s));
+  st = standalone_finish(s, stream);
+  if (st != EOT_OK) return st;
+  const State hs = *S->hSt;
+  if (hs.numeric > 0 || hs.done == 3)
+    return fail(EOT_ENUMERIC, "non-finite values or potentials outside the exact range");
+  if (hs.nr_ok) {
+    if (f_trial) CUDA_TRY(cudaMemcpy(f_trial, P.f[1], n * sizeof(double), dd));
+    if (h_trial) CUDA_TRY(cudaMemcpy(h_trial, P.g[2], m * sizeof(double), dd));
+  }
+  if (info) {
+    info->col_l1 = hs.l1_col;
+    info->q_semi = hs.qsemi;
+    info->dq = hs.nr_ok ? hs.dq : 0.0;
+    info->newton_ok = hs.nr_ok;
+    info->accepted = hs.nr_ok && hs.nr_acc > 0 ? 1 : 0;
+    for (int k = 0; k < 4; ++k) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+      info->stage_seconds[k] = 1e-3 * ms;
+    }
+  }
+  return EOT_OK;
 }
 
 }  // extern "C"

@@ -59,6 +59,12 @@ class eot_result(C.Structure):
         return d
 
 
+class eot_sknr_info(C.Structure):
+    _fields_ = [("col_l1", C.c_double), ("q_semi", C.c_double), ("dq", C.c_double),
+                ("newton_ok", C.c_int32), ("accepted", C.c_int32),
+                ("stage_seconds", C.c_double * 4)]
+
+
 _PTR = C.c_void_p
 _SIGNATURES = {
     "eot_default_options": (None, [C.POINTER(eot_options)]),
@@ -92,6 +98,9 @@ _SIGNATURES = {
     "eot_batch_plan": (C.c_int, [C.c_int32, _PTR, _PTR, _PTR, _PTR, C.POINTER(eot_options),
                                  C.c_int32, C.c_double, C.c_double, C.c_double, _PTR, _PTR]),
     "eot_exp2": (C.c_int, [C.c_int32, _PTR, _PTR, C.c_int32, _PTR, _PTR]),
+    "eot_sknr_step": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, _PTR, _PTR, _PTR, C.c_double,
+                                _PTR, _PTR, _PTR, _PTR, _PTR, _PTR, _PTR, _PTR, _PTR, _PTR,
+                                _PTR, C.POINTER(eot_sknr_info), _PTR]),
     "eot_last_error": (C.c_char_p, []),
     "eot_version": (C.c_char_p, []),
 }
@@ -289,6 +298,24 @@ def eot_exp2(p, q, variant: int, out, stream=None) -> int:
     """Elementwise 2^(p + q) of the float32 passes (device float32 tensors)."""
     return load().eot_exp2(int(p.numel()), p.data_ptr(), q.data_ptr(), int(variant),
                            out.data_ptr(), stream)
+
+
+def eot_sknr_step(n, m, ell, Cdev, a, b, eps, g, V, f_k=None, h=None, W=None, grad=None,
+                  GV=None, WtDW=None, delta=None, f_trial=None, h_trial=None, stream=None):
+    """One SK-NR iteration from g with modes V (device tensors; outputs are
+    optional device tensors).  Returns (status, info dict)."""
+    info = eot_sknr_info()
+
+    def ptr(x):
+        return None if x is None else x.data_ptr()
+
+    st = load().eot_sknr_step(n, m, ell, Cdev.data_ptr(), a.data_ptr(), b.data_ptr(),
+                              float(eps), g.data_ptr(), V.data_ptr(), ptr(f_k), ptr(h), ptr(W),
+                              ptr(grad), ptr(GV), ptr(WtDW), ptr(delta), ptr(f_trial),
+                              ptr(h_trial), C.byref(info), stream)
+    d = {k: getattr(info, k) for k, _ in info._fields_}
+    d["stage_seconds"] = list(info.stage_seconds)
+    return st, d
 
 
 def eot_marginal_error(n, m, Cdev, f, g, a, b, eps, stream=None):

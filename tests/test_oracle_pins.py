@@ -653,3 +653,44 @@ def test_diag_alpha_hessian_equals_exact_at_the_optimum():
     diff = V.T @ O.hess_semi(f, C, a, b, eps) @ V - h_diag_alpha(f)
     assert np.allclose(diff, -(1.0 / eps) * V.T @ ((r - a)[:, None] * V), atol=1e-10)
     assert np.abs(diff).max() > 1e-4
+
+
+def test_newton_step_intermediates():
+    """The Newton part of Algorithm 4.1 (``newton_step``): its gradient and
+    Hessian on V are the full semi-dual gradient and Hessian (pinned by finite
+    differences above) restricted to V; Delta solves the Newton system; the
+    two forms of the objective change agree; the exact Hessian's step
+    increases Q_semi here."""
+    rng = _rng(31)
+    n, m, eps, ell = 12, 15, 0.1, 4
+    C = rng.random((n, m))
+    a, b = _simplex(rng, n), _simplex(rng, m)
+    g = rng.standard_normal(m) * 0.05
+    f = O.c_transform_g(g, C, b, eps)
+    V = rng.standard_normal((n, ell))
+    st = O.newton_step(f, C, a, b, eps, V, hessian="exact")
+    Vg = V.T @ O.grad_semi(f, C, a, b, eps)
+    VHV = V.T @ O.hess_semi(f, C, a, b, eps) @ V
+    assert np.allclose(st["grad"], Vg, rtol=1e-12, atol=1e-14)
+    assert np.allclose(st["H"], VHV, rtol=1e-10, atol=1e-12)
+    assert st["ok"]
+    assert np.allclose(-st["H"] @ st["delta"], st["grad"], rtol=1e-10, atol=1e-13)
+    assert np.allclose(st["f_trial"], f + V @ st["delta"], rtol=0, atol=1e-15)
+    assert st["dq"] == pytest.approx(st["dq_diff"], rel=1e-9, abs=1e-15)
+    assert st["accepted"] and st["dq"] > 0
+    # the D_a variant differs by V^T diag(r - a) V / eps
+    sa = O.newton_step(f, C, a, b, eps, V, hessian="diag_alpha")
+    r = O.plan(f, st["h"], C, a, b, eps).sum(axis=1)
+    assert np.allclose(sa["H"] - st["H"], -(V.T @ ((a - r)[:, None] * V)) / eps, rtol=1e-9,
+                       atol=1e-12)
+
+
+def test_gram_form_of_the_cost_matches_entrywise_loop():
+    """|x|^2 + |y|^2 - 2 x.y (one matrix product) against ||x - y||^2 entry by
+    entry, for the on-the-fly workload's clouds (N(0, I)/8 in R^64)."""
+    prob = W.gaussian_cloud(40, 50, d=64, seed=3)
+    Cg = O.sq_euclidean_cost_gram(prob.X, prob.Y)
+    for i in range(0, 40, 7):
+        for j in range(0, 50, 9):
+            d = prob.X[i].astype(np.float64) - prob.Y[j].astype(np.float64)
+            assert Cg[i, j] == pytest.approx(float(d @ d), rel=0, abs=1e-14)
