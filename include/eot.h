@@ -125,6 +125,9 @@ typedef struct {
     double seconds_eig;     /* part of it spent computing modes                        */
     double seconds_last_level; /* device time of the final eps level incl. its modes   */
     int64_t kernel_launches; /* device kernels this solve launched (all levels)        */
+    int64_t device_t_begin_ns, device_t_end_ns; /* the device clock (globaltimer, ns) at
+                               the solve's first and last kernel: solves whose
+                               intervals intersect ran on the device at once         */
 } eot_result;
 
 /* Fill *opt with defaults: tol 1e-6, max_iter 100000, ell 0, single level,
@@ -161,9 +164,22 @@ typedef struct eot_server eot_server;
  * warm-start later requests on the same cloud.  Ownership: *srv until destroy. */
 eot_status eot_server_create(const eot_options *opt, size_t hbm_budget_bytes,
                              int32_t max_slots, eot_server **srv);
-/* Deep-copies the problem (host memory only) and returns a ticket. */
+/* Deep-copies the problem (host memory only) and returns a ticket.  The
+ * request runs with the server's options, except that a request whose stored
+ * float32 cost would exceed 256 MB (4 n m bytes) and that gives points with
+ * d <= 64 and plain Sinkhorn runs with the on-the-fly cost (EOT_PREC_SPLIT_TC).
+ * Scheduling: a request is admitted when a slot is free and its device
+ * footprint fits the free budget; among those that fit, the one with the
+ * least predicted work (n m times the iterations of its eps schedule) goes
+ * first; a request that has waited more than 1 s goes before all others, and
+ * while it does not fit no other request is admitted (no starvation); one
+ * that can never fit the budget fails with EOT_ENOMEM. */
 eot_status eot_server_submit(eot_server *srv, const eot_problem *prob, uint64_t cloud_id,
                              uint64_t *ticket);
+/* eot_server_submit with the request's own options (eps schedule, ell,
+ * tolerance, precision; its stream field is ignored); NULL: the server's. */
+eot_status eot_server_submit_opts(eot_server *srv, const eot_problem *prob, uint64_t cloud_id,
+                                  const eot_options *opt, uint64_t *ticket);
 /* EOT_PENDING until done; then copies f (n), g (m) to host memory and fills res
  * (which may be NULL), returns the request's status and forgets the ticket.
  * Unknown tickets give EOT_ENOTFOUND. */
@@ -173,7 +189,22 @@ eot_status eot_server_poll(eot_server *srv, uint64_t ticket, double *f_out, doub
  * second since creation. */
 eot_status eot_server_stats(eot_server *srv, double *p50_s, double *p99_s,
                             double *solves_per_s);
+/* Current load (host outputs, each optional): requests waiting, requests
+ * being solved, device bytes admitted (their footprints), completed solves. */
+eot_status eot_server_status(eot_server *srv, int32_t *queued, int32_t *running,
+                             uint64_t *hbm_in_use, uint64_t *completed);
 void eot_server_destroy(eot_server *srv);
+
+/* The server's scheduling policy replayed on the host (no device work): count
+ * requests arriving at t_arrive[k] (seconds) with device footprints
+ * footprint[k] (bytes), predicted work work[k] and service times service_s[k],
+ * served by `slots` workers within `budget` bytes, a request that has waited
+ * more than max_wait_s going first (the server uses 1 s).  t_start[k] and
+ * t_done[k] receive the dispatch and completion times (-1 for a request that
+ * can never fit).  Host arrays of count entries. */
+eot_status eot_server_simulate(int32_t count, const double *t_arrive, const uint64_t *footprint,
+                               const double *work, const double *service_s, uint64_t budget,
+                               int32_t slots, double max_wait_s, double *t_start, double *t_done);
 
 /* --------------------------------------------------- single hot-path steps
  * Device-pointer entry points for the individual passes.  They run on `stream`

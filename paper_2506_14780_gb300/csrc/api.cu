@@ -139,7 +139,14 @@ struct DeviceCtx {
   bool cond_ok = true;   // graph conditional nodes usable
   int stream_ctas = 0;   // CTAs of one wave of the staged stream passes
   int gram_ctas = 0;     // CTAs of one wave of the on-the-fly cost passes
+  // pinned host mirrors of the device state, allocated once per thread and
+  // device (a cudaFreeHost synchronises the whole device: never per solve)
+  State* hSt = nullptr;           // one State
+  double* hScores = nullptr;      // 16 scores
+  State* hLev = nullptr;          // per-level states: 2 kMaxLevels + 1
+  unsigned long long* hStamp = nullptr;   // device timestamps of a solve [2]
 };
+constexpr int kMaxLevels = 256;   // bound of the eps continuation levels of one solve
 
 // One context (and stream) per calling thread and device, so that solves issued
 // from different threads (the server's workers) overlap on the device.
@@ -165,6 +172,10 @@ static eot_status get_ctx(DeviceCtx** out) {
   c->gram_ctas = c->nsm;   // one CTA per SM (shared memory and TMEM)
   const char* e = getenv("EOT_HOST_LOOP");
   c->cond_ok = !(e && e[0] == '1');
+  CUDA_TRY(cudaMallocHost(&c->hSt, sizeof(State)));
+  CUDA_TRY(cudaMallocHost(&c->hScores, 16 * sizeof(double)));
+  CUDA_TRY(cudaMallocHost(&c->hLev, sizeof(State) * (2 * kMaxLevels + 1)));
+  CUDA_TRY(cudaMallocHost(&c->hStamp, 2 * sizeof(unsigned long long)));
   *out = c.get();
   g_ctx[dev] = std::move(c);
   return EOT_OK;
@@ -289,6 +300,7 @@ struct Solver {
   float* Cbuf = nullptr;
   double *a_in = nullptr, *b_in = nullptr, *f_init = nullptr;
   double *f_out = nullptr, *g_out = nullptr, *scores = nullptr;
+  unsigned long long* stamps = nullptr;  // globaltimer at a solve's first and last kernel
   unsigned* stats = nullptr;             // [0] max|C| bits, [1] bad C, [2] bad a/b
   unsigned long long* cmax64 = nullptr;
   float* X = nullptr;
@@ -321,9 +333,8 @@ struct Solver {
     if (gr_sk) cudaGraphDestroy(gr_sk);
     if (gr_sknr) cudaGraphDestroy(gr_sknr);
     if (gr_eig) cudaGraphDestroy(gr_eig);
-    if (mem) cudaFree(mem);
-    if (hSt) cudaFreeHost(hSt);
-    if (hScores) cudaFreeHost(hScores);
+    // stream-ordered: after the solver's last work, without a device-wide sync
+    if (mem) cudaFreeAsync(mem, ctx->stream);
   }
 
   void plan_tiles() {
@@ -383,6 +394,7 @@ struct Solver {
     f_out = A.take<double>(n);
     g_out = A.take<double>(m);
     scores = A.take<double>(16);
+    stamps = A.take<unsigned long long>(2);
     stats = A.take<unsigned>(8);   // [4] float32 bits of the approximate max of C
     cmax64 = A.take<unsigned long long>(1);
     X = d > 0 ? A.take<float>((size_t)n * d) : nullptr;
@@ -522,13 +534,13 @@ struct Solver {
     Arena A;
     layout(A, d);
     bytes = A.off + 256;
-    CUDA_TRY(cudaMalloc(&mem, bytes));
+    CUDA_TRY(cudaMallocAsync(&mem, bytes, ctx->stream));
     CUDA_TRY(cudaMemsetAsync(mem, 0, bytes, ctx->stream));
     Arena B;
     B.base = reinterpret_cast<char*>(mem);
     layout(B, d);
-    CUDA_TRY(cudaMallocHost(&hSt, sizeof(State)));
-    CUDA_TRY(cudaMallocHost(&hScores, 16 * sizeof(double)));
+    hSt = ctx->hSt;
+    hScores = ctx->hScores;
     hP.n = n;
     hP.m = m;
     hP.nstripe = nstripe;
@@ -902,6 +914,14 @@ static eot_status validate(const eot_problem* pr, const eot_options* o) {
   return EOT_OK;
 }
 
+// Device timestamp (globaltimer, ns): brackets a solve's work on the device,
+// so that the overlap of concurrent solves can be observed.
+__global__ void stamp_kernel(unsigned long long* t) {
+  unsigned long long v;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(v));
+  *t = v;
+}
+
 // ---------------------------------------------------------------------------
 // One solve.
 // ---------------------------------------------------------------------------
@@ -937,6 +957,7 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   s = ctx->stream;
   const double t_host0 = now_s();
   CUDA_TRY(cudaEventRecord(ev0, s));
+  stamp_kernel<<<1, 1, 0, s>>>(S->stamps);
   const cudaMemcpyKind kin = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   // ---- inputs ----
   CUDA_TRY(cudaMemsetAsync(S->stats, 0, 4 * sizeof(unsigned), s));
@@ -1102,8 +1123,8 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   std::vector<cudaEvent_t> lev_ev(L + 1);
   for (auto& e : lev_ev) CUDA_TRY(cudaEventCreate(&e));
   std::vector<State> lev_state(L);
-  State* hLev = nullptr;
-  CUDA_TRY(cudaMallocHost(&hLev, sizeof(State) * (2 * L + 1)));
+  if (L > kMaxLevels) return fail(EOT_EINVAL, "too many continuation levels");
+  State* hLev = ctx->hLev;
   std::memset(hLev, 0, sizeof(State) * (2 * L + 1));
   std::vector<int> lev_nr(L, 0), lev_eig(L, 0), lev_coop(L, 0);
   int resumed_coop = 0;
@@ -1231,7 +1252,10 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   CUDA_TRY(cudaMemcpyAsync(g_out, S->g_out, m * sizeof(double), kout, s));
   if (f_keep_dev)
     CUDA_TRY(cudaMemcpyAsync(f_keep_dev, S->f_out, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  stamp_kernel<<<1, 1, 0, s>>>(S->stamps + 1);
   CUDA_TRY(cudaMemcpyAsync(S->hScores, S->scores, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(ctx->hStamp, S->stamps, 2 * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaEventRecord(ev1, s));
   if (o->stream && reinterpret_cast<cudaStream_t>(o->stream) != ctx->stream) {
     CUDA_TRY(cudaStreamWaitEvent(reinterpret_cast<cudaStream_t>(o->stream), ev1, 0));
@@ -1279,7 +1303,9 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   launches += (long long)resumed_bodies * (lev_nr[L - 1] ? 6 * S->unroll_sknr + 1 : 2 * S->unroll_sk + 1);
   launches += resumed_coop;
   launches += (verify_rounds > 1 ? (long long)(verify_rounds - 1) : 0);   // level set-up per resume
-  r.kernel_launches = launches;
+  r.kernel_launches = launches + 2;   // + the two timestamps
+  r.device_t_begin_ns = (int64_t)ctx->hStamp[0];
+  r.device_t_end_ns = (int64_t)ctx->hStamp[1];
   r.row_l1 = S->hScores[0];
   r.col_l1 = S->hScores[1];
   r.l1_marginal = r.row_l1 + r.col_l1;
@@ -1307,7 +1333,6 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   cudaEventDestroy(ev0);
   cudaEventDestroy(ev1);
   cudaEventDestroy(evj);
-  cudaFreeHost(hLev);
   (void)t_host0;
   (void)eig_ev0;
   (void)eig_ev1;
@@ -1887,6 +1912,8 @@ static eot_status run_batch(int count, const eot_problem* probs, const eot_optio
     r.seconds = 1e-9 * (double)(b.t_end - b.t_begin);
     r.seconds_last_level = 1e-9 * (double)(b.t_end - b.t_last_level);
     r.kernel_launches = 5;   // weights, cost max, cost fill, persistent kernel (+ counter)
+    r.device_t_begin_ns = (int64_t)b.t_begin;
+    r.device_t_end_ns = (int64_t)b.t_end;
     switch (b.status) {
       case 1: r.status = EOT_OK; break;
       case 2: r.status = EOT_NOT_CONVERGED; errs[k] = "max_iter reached"; break;
@@ -2428,10 +2455,48 @@ static int batch_threads(int count) {
 
 }  // namespace eotk
 
+namespace eotk {
+
+// The server's choice of the next request, shared with eot_server_simulate.
+// A request that has waited longer than max_wait goes next, the oldest
+// first; while it does not fit in the free memory nothing else is admitted,
+// so the memory that running solves release goes to it (a stream of small
+// requests cannot starve a large one).  Otherwise, among the requests that
+// fit, the one with the least predicted work (shortest job first: the small
+// requests of a burst do not wait behind the large ones).  Returns the index
+// of the pick, or -1 to wait.
+struct QueuedReq {
+  double t_submit;
+  size_t footprint;
+  double work;
+};
+
+static int server_pick(const QueuedReq* q, int count, size_t room, double now, double max_wait) {
+  int oldest = -1;
+  for (int k = 0; k < count; ++k)
+    if (oldest < 0 || q[k].t_submit < q[oldest].t_submit) oldest = k;
+  if (oldest >= 0 && now - q[oldest].t_submit > max_wait)
+    return q[oldest].footprint <= room ? oldest : -1;
+  int pick = -1;
+  for (int k = 0; k < count; ++k) {
+    if (q[k].footprint > room) continue;
+    if (pick < 0 || q[k].work < q[pick].work) pick = k;
+  }
+  return pick;
+}
+
+// Requests of a served stream whose stored cost would exceed this take the
+// on-the-fly cost (EOT_PREC_SPLIT_TC) when they can (points with d <= 64,
+// plain Sinkhorn).
+constexpr double kServeStoredCostMax = 256.0 * 1024 * 1024;
+
+}  // namespace eotk
+
 struct eot_server {
   struct Request {
     uint64_t ticket = 0, cloud_id = 0;
     eot_problem prob{};
+    eot_options opt{};   // the request's own options (the server's unless given)
     std::vector<double> a, b;
     std::vector<float> C, X, Y;
     size_t footprint = 0;
@@ -2448,7 +2513,9 @@ struct eot_server {
   struct DevBuf {
     double* p = nullptr;
     ~DevBuf() {
-      if (p) cudaFree(p);
+      // stream-ordered: every solve that read it has completed (a holder lets
+      // go only after its solve synchronised), and no device-wide sync
+      if (p) cudaFreeAsync(p, nullptr);
     }
   };
   struct Cached {
@@ -2467,6 +2534,7 @@ struct eot_server {
   std::map<uint64_t, std::shared_ptr<Request>> all;
   std::map<uint64_t, Cached> cache;
   size_t in_use = 0;
+  int running = 0;
   bool stop = false;
   uint64_t next = 1;
   std::vector<std::thread> workers;
@@ -2495,35 +2563,29 @@ struct eot_server {
               ++it;
             }
           }
-          // of the requests that fit now: one that has waited longer than
-          // kMaxWaitS (oldest first), else the least predicted work, so that
-          // the small requests of a burst do not queue behind the large ones
           const size_t room = budget - std::min(budget, in_use);
-          const double now = eotk::now_s();
-          auto pick = queue.end();
-          for (auto it = queue.begin(); it != queue.end(); ++it) {
-            if ((*it)->footprint > room) continue;
-            if (now - (*it)->t_submit > kMaxWaitS) {
-              pick = it;
-              break;
-            }
-            if (pick == queue.end() || (*it)->work < (*pick)->work) pick = it;
-          }
-          if (pick != queue.end()) {
-            r = *pick;
-            queue.erase(pick);
+          std::vector<eotk::QueuedReq> q;
+          q.reserve(queue.size());
+          for (const auto& x : queue) q.push_back({x->t_submit, x->footprint, x->work});
+          const int k = eotk::server_pick(q.data(), (int)q.size(), room, eotk::now_s(), kMaxWaitS);
+          if (k >= 0) {
+            r = queue[k];
+            queue.erase(queue.begin() + k);
             break;
           }
-          cv.wait(lk);
+          // re-evaluate when a request arrives or a solve ends, and at least
+          // every 20 ms (a queued request's age crosses the threshold)
+          cv.wait_for(lk, std::chrono::milliseconds(20));
         }
         in_use += r->footprint;
+        ++running;
         if (r->cloud_id) {
           auto it = cache.find(r->cloud_id);
           if (it != cache.end() && it->second.n == r->prob.n && it->second.m == r->prob.m)
             warm = it->second;
         }
       }
-      eot_options o = opt;
+      eot_options o = r->opt;
       o.stream = nullptr;
       const double* finit = nullptr;
       if (warm.f) {
@@ -2535,10 +2597,13 @@ struct eot_server {
         }
       }
       std::shared_ptr<DevBuf> keep;
-      if (r->cloud_id) {
+      eotk::DeviceCtx* wctx = nullptr;
+      if (r->cloud_id && eotk::get_ctx(&wctx) == EOT_OK) {
         keep = std::make_shared<DevBuf>();
-        if (cudaMalloc(&keep->p, r->prob.n * sizeof(double)) != cudaSuccess) {
+        if (cudaMallocAsync(reinterpret_cast<void**>(&keep->p), r->prob.n * sizeof(double),
+                            wctx->stream) != cudaSuccess) {
           cudaGetLastError();
+          keep->p = nullptr;
           keep.reset();
         }
       }
@@ -2551,6 +2616,7 @@ struct eot_server {
       {
         std::lock_guard<std::mutex> lk(mu);
         in_use -= r->footprint;
+        --running;
         r->status = st;
         r->res.status = st;
         r->t_done = eotk::now_s();
@@ -2659,9 +2725,21 @@ eot_status eot_server_create(const eot_options* opt, size_t hbm_budget_bytes, in
 
 eot_status eot_server_submit(eot_server* srv, const eot_problem* prob, uint64_t cloud_id,
                              uint64_t* ticket) {
+  return eot_server_submit_opts(srv, prob, cloud_id, nullptr, ticket);
+}
+
+eot_status eot_server_submit_opts(eot_server* srv, const eot_problem* prob, uint64_t cloud_id,
+                                  const eot_options* opt, uint64_t* ticket) {
   if (!srv || !prob || !ticket) return fail(EOT_EINVAL, "null argument");
   if (prob->mem != EOT_MEM_HOST) return fail(EOT_EINVAL, "server requests use host memory");
-  eot_status vs = eotk::validate(prob, &srv->opt);
+  eot_options ro = opt ? *opt : srv->opt;
+  ro.stream = nullptr;
+  // a large stored cost is replaced by the on-the-fly cost where that path
+  // serves the request (float32 points with d <= 64, plain Sinkhorn)
+  if (ro.prec == EOT_PREC_FP32 && prob->X && prob->Y && prob->d >= 1 && prob->d <= 64 &&
+      ro.ell == 0 && 4.0 * (double)prob->n * (double)prob->m > eotk::kServeStoredCostMax)
+    ro.prec = EOT_PREC_SPLIT_TC;
+  eot_status vs = eotk::validate(prob, &ro);
   if (vs != EOT_OK) return vs;
   auto r = std::make_shared<eot_server::Request>();
   const int n = prob->n, m = prob->m, d = prob->d;
@@ -2680,15 +2758,15 @@ eot_status eot_server_submit(eot_server* srv, const eot_problem* prob, uint64_t 
   r->prob.Y = prob->X ? r->Y.data() : nullptr;
   r->prob.f_init = nullptr;
   r->cloud_id = cloud_id;
+  r->opt = ro;
   eotk::DeviceCtx* ctx = nullptr;
   eot_status cs = eotk::get_ctx(&ctx);
   if (cs != EOT_OK) return cs;
-  r->footprint = eotk::solver_footprint(ctx, n, m, d, srv->opt.ell,
-                                        eotk::mode_block(n, srv->opt.ell, srv->opt.oversample),
-                                        srv->opt.prec);
+  r->footprint = eotk::solver_footprint(ctx, n, m, d, ro.ell,
+                                        eotk::mode_block(n, ro.ell, ro.oversample), ro.prec);
   r->work = (double)n * (double)m *
-            eotk::batch_est_iters(eotk::schedule(srv->opt.eps_start, prob->eps, srv->opt.eps_factor),
-                                  srv->opt.max_iter);
+            eotk::batch_est_iters(eotk::schedule(ro.eps_start, prob->eps, ro.eps_factor),
+                                  ro.max_iter);
   {
     std::lock_guard<std::mutex> lk(srv->mu);
     r->ticket = srv->next++;
@@ -2741,6 +2819,85 @@ eot_status eot_server_stats(eot_server* srv, double* p50_s, double* p99_s, doubl
   if (p50_s) *p50_s = pct(0.5);
   if (p99_s) *p99_s = pct(0.99);
   if (solves_per_s) *solves_per_s = (done > 0 && t1 > t0) ? done / (t1 - t0) : 0.0;
+  return EOT_OK;
+}
+
+eot_status eot_server_status(eot_server* srv, int32_t* queued, int32_t* running,
+                             uint64_t* hbm_in_use, uint64_t* completed) {
+  if (!srv) return fail(EOT_EINVAL, "null server");
+  std::lock_guard<std::mutex> lk(srv->mu);
+  if (queued) *queued = (int32_t)srv->queue.size();
+  if (running) *running = srv->running;
+  if (hbm_in_use) *hbm_in_use = (uint64_t)srv->in_use;
+  if (completed) *completed = (uint64_t)srv->completed;
+  return EOT_OK;
+}
+
+eot_status eot_server_simulate(int32_t count, const double* t_arrive, const uint64_t* footprint,
+                               const double* work, const double* service_s, uint64_t budget,
+                               int32_t slots, double max_wait_s, double* t_start, double* t_done) {
+  if (count < 0 || slots < 1 || budget == 0) return fail(EOT_EINVAL, "bad simulation arguments");
+  if (count > 0 && (!t_arrive || !footprint || !work || !service_s || !t_start || !t_done))
+    return fail(EOT_EINVAL, "null argument");
+  for (int k = 0; k < count; ++k) {
+    if (!std::isfinite(t_arrive[k]) || !(service_s[k] >= 0.0)) return fail(EOT_EINVAL, "bad request");
+    t_start[k] = t_done[k] = -1.0;
+  }
+  // event-driven replay of the worker loop: arrivals in time order, slots
+  // and memory taken at dispatch and returned at completion
+  std::vector<int> order(count);
+  for (int k = 0; k < count; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return t_arrive[x] < t_arrive[y]; });
+  std::vector<int> queue;                       // request indices waiting
+  std::vector<std::pair<double, int>> active;   // (completion time, index)
+  size_t in_use = 0;
+  double now = count ? t_arrive[order[0]] : 0.0;
+  size_t next = 0;
+  int guard = 0;
+  while ((next < order.size() || !queue.empty() || !active.empty()) && guard++ < 100000000) {
+    // admit everything that has arrived by now; refuse what never fits
+    while (next < order.size() && t_arrive[order[next]] <= now) {
+      const int k = order[next++];
+      if (footprint[k] > budget) continue;
+      queue.push_back(k);
+    }
+    // complete what has finished by now
+    for (size_t i = 0; i < active.size();) {
+      if (active[i].first <= now) {
+        in_use -= footprint[active[i].second];
+        active.erase(active.begin() + i);
+      } else {
+        ++i;
+      }
+    }
+    // dispatch while a slot is free and the policy picks a request
+    bool dispatched = true;
+    while (dispatched && (int)active.size() < slots && !queue.empty()) {
+      dispatched = false;
+      std::vector<eotk::QueuedReq> q;
+      for (int k : queue) q.push_back({t_arrive[k], (size_t)footprint[k], work[k]});
+      const int pick = eotk::server_pick(q.data(), (int)q.size(), budget - std::min<size_t>(budget, in_use),
+                                         now, max_wait_s);
+      if (pick >= 0) {
+        const int k = queue[pick];
+        queue.erase(queue.begin() + pick);
+        in_use += footprint[k];
+        t_start[k] = now;
+        t_done[k] = now + service_s[k];
+        active.push_back({t_done[k], k});
+        dispatched = true;
+      }
+    }
+    // next event: an arrival, a completion or a queued request's age crossing
+    double t = INFINITY;
+    if (next < order.size()) t = std::min(t, t_arrive[order[next]]);
+    for (const auto& a : active) t = std::min(t, a.first);
+    for (int k : queue)
+      if (t_arrive[k] + max_wait_s > now) t = std::min(t, t_arrive[k] + max_wait_s + 1e-9);
+    if (!std::isfinite(t)) break;   // nothing can ever change
+    now = std::max(now, t);
+  }
   return EOT_OK;
 }
 

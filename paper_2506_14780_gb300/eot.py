@@ -51,7 +51,8 @@ class eot_result(C.Structure):
                 ("eig_iters", C.c_int32), ("l1_marginal", C.c_double), ("row_l1", C.c_double),
                 ("col_l1", C.c_double), ("q_dual", C.c_double), ("q_semi", C.c_double),
                 ("dual_gap", C.c_double), ("seconds", C.c_double), ("seconds_eig", C.c_double),
-                ("seconds_last_level", C.c_double), ("kernel_launches", C.c_int64)]
+                ("seconds_last_level", C.c_double), ("kernel_launches", C.c_int64),
+                ("device_t_begin_ns", C.c_int64), ("device_t_end_ns", C.c_int64)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -80,6 +81,12 @@ _SIGNATURES = {
     "eot_server_stats": (C.c_int, [_PTR, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                    C.POINTER(C.c_double)]),
     "eot_server_destroy": (None, [_PTR]),
+    "eot_server_submit_opts": (C.c_int, [_PTR, C.POINTER(eot_problem), C.c_uint64,
+                                         C.POINTER(eot_options), C.POINTER(C.c_uint64)]),
+    "eot_server_status": (C.c_int, [_PTR, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                    C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
+    "eot_server_simulate": (C.c_int, [C.c_int32, _PTR, _PTR, _PTR, _PTR, C.c_uint64, C.c_int32,
+                                      C.c_double, _PTR, _PTR]),
     "eot_ctransform": (C.c_int, [C.c_int, C.c_int32, C.c_int32, _PTR, _PTR, _PTR, _PTR,
                                  C.c_double, _PTR, _PTR, _PTR]),
     "eot_ctransform_noalloc": (C.c_int, [C.c_int, C.c_int32, C.c_int32, _PTR, _PTR, _PTR, _PTR,
@@ -327,6 +334,23 @@ def eot_marginal_error(n, m, Cdev, f, g, a, b, eps, stream=None):
     return st, r.value, c.value
 
 
+def eot_server_simulate(t_arrive, footprint, work, service_s, budget: int, slots: int,
+                        max_wait_s: float = 1.0):
+    """Host replay of the server's scheduling policy.  Returns (status,
+    t_start, t_done) as NumPy arrays."""
+    ta = np.ascontiguousarray(t_arrive, dtype=np.float64)
+    fp = np.ascontiguousarray(footprint, dtype=np.uint64)
+    wk = np.ascontiguousarray(work, dtype=np.float64)
+    sv = np.ascontiguousarray(service_s, dtype=np.float64)
+    k = int(ta.shape[0])
+    t0 = np.zeros(k)
+    t1 = np.zeros(k)
+    st = load().eot_server_simulate(k, ta.ctypes.data, fp.ctypes.data, wk.ctypes.data,
+                                    sv.ctypes.data, int(budget), int(slots), float(max_wait_s),
+                                    t0.ctypes.data, t1.ctypes.data)
+    return st, t0, t1
+
+
 class Server:
     """eot_server_* wrapper (host arrays)."""
 
@@ -339,12 +363,14 @@ class Server:
         self.h = h
         self._keep = {}
 
-    def submit(self, prob, cloud_id: int = 0) -> int:
+    def submit(self, prob, cloud_id: int = 0, options: Optional[eot_options] = None) -> int:
         keep = []
         p = make_problem(prob.a, prob.b, C=prob.C, X=prob.X, Y=prob.Y, eps=prob.eps,
                          normalize_cost=prob.normalize_cost, keep=keep)
         t = C.c_uint64(0)
-        st = load().eot_server_submit(self.h, C.byref(p), C.c_uint64(cloud_id), C.byref(t))
+        st = load().eot_server_submit_opts(self.h, C.byref(p), C.c_uint64(cloud_id),
+                                           None if options is None else C.byref(options),
+                                           C.byref(t))
         if st != EOT_OK:
             raise RuntimeError(f"eot_server_submit: {STATUS_NAMES.get(st)} {last_error()}")
         self._keep[t.value] = (prob.n, prob.m)
@@ -365,6 +391,13 @@ class Server:
         p50, p99, sps = C.c_double(), C.c_double(), C.c_double()
         load().eot_server_stats(self.h, C.byref(p50), C.byref(p99), C.byref(sps))
         return p50.value, p99.value, sps.value
+
+    def status(self) -> dict:
+        q, r = C.c_int32(), C.c_int32()
+        hb, done = C.c_uint64(), C.c_uint64()
+        load().eot_server_status(self.h, C.byref(q), C.byref(r), C.byref(hb), C.byref(done))
+        return {"queued": q.value, "running": r.value, "hbm_in_use": hb.value,
+                "completed": done.value}
 
     def close(self):
         if self.h:

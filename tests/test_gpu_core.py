@@ -1,7 +1,10 @@
 """Parity of the CUDA hot path with the float64 oracle, through the C ABI.
 
 Tolerances (float32 exponentials and sums, exponents formed exactly, float64
-potentials): a single (C, eps)-transform matches the oracle to 1e-5 * eps;
+potentials): a single (C, eps)-transform matches the oracle to 1e-5 * eps when
+its shift (the current potential on the output side) is within a few eps of
+the result, as in the iterations; a shift |off| away adds the float32 rounding
+of exponents of size |off| / eps, |off| 2^-22;
 products Op(pi) Z and Op(pi)^T Z to 2e-5 relative; the cost is bit-exact
 (same float64 operations, one rounding).  Solves are scored by the oracle's
 float64 evaluation of the returned potentials: L1 marginal error <= 1e-6.
@@ -93,7 +96,9 @@ def test_ctransform_stream_shapes(pkg, n, m):
         st = pkg.eot_ctransform(pkg.EOT_SIDE_ROW, n, m, dC, dev(g), dev(prob.b),
                                 dev(f_true + off), eps, out, None)
         assert st == pkg.EOT_OK, pkg.last_error()
-        assert np.abs(out.cpu().numpy() - f_true).max() <= 1e-5 * eps
+        # the exponents are float32 values of size |off| / eps: their rounding
+        # adds |off| 2^-22 to the 1e-5 eps of a transform near its shift
+        assert np.abs(out.cpu().numpy() - f_true).max() <= 1e-5 * eps + abs(off) * 2.0 ** -22
 
 
 def test_ctransform_unaligned_cost_rows(pkg):
@@ -127,7 +132,8 @@ def test_ctransform_extreme_exponents(pkg):
         st = pkg.eot_ctransform(pkg.EOT_SIDE_COL, n, m, dev(prob.C), dev(f), dev(prob.a),
                                 dev(g_true + off), eps, out, None)
         assert st == pkg.EOT_OK
-        assert np.abs(out.cpu().numpy() - g_true).max() <= 1e-5 * eps
+        # float32 exponents of size |off| / eps: rounding |off| 2^-22 beyond 1e-5 eps
+        assert np.abs(out.cpu().numpy() - g_true).max() <= 1e-5 * eps + abs(off) * 2.0 ** -22
 
 
 # m % 4 != 0 takes the CUDA-core kernels, m % 4 == 0 the staged tensor-core

@@ -225,6 +225,84 @@ def test_server_continuous_batching(pkg):
         srv.close()
 
 
+def test_server_solves_overlap_on_the_device(pkg):
+    """Requests admitted together run on the device at the same time: their
+    device intervals (the device clock at each solve's first and last kernel)
+    intersect; the status call sees them running; each result equals the
+    same problem solved alone, bit for bit."""
+    probs = [W.gaussian_mixture(1200, 1300 + 4 * k, seed=40 + k, eps=5e-3) for k in range(4)]
+    o = pkg.default_options(tol=1e-6, max_iter=200000, eps_start=1e-1)
+    srv = pkg.Server(o, hbm_budget_bytes=8 << 30, max_slots=4)
+    try:
+        tickets = [srv.submit(p) for p in probs]
+        peak_running = 0
+        results = {}
+        deadline = time.time() + 120
+        while len(results) < len(tickets):
+            peak_running = max(peak_running, srv.status()["running"])
+            for t in tickets:
+                if t in results:
+                    continue
+                st, f, g, res = srv.poll(t)
+                if st != pkg.EOT_PENDING:
+                    assert st == pkg.EOT_OK, res
+                    results[t] = (f, g, res)
+            assert time.time() < deadline
+            time.sleep(0.0005)
+        assert srv.status()["completed"] == len(tickets)
+        iv = [(results[t][2]["device_t_begin_ns"], results[t][2]["device_t_end_ns"])
+              for t in tickets]
+        assert all(0 < b < e for b, e in iv)
+        pairs = [(i, j) for i in range(len(iv)) for j in range(i + 1, len(iv))
+                 if max(iv[i][0], iv[j][0]) < min(iv[i][1], iv[j][1])]
+        print(f"device intervals (ms from the first): "
+              f"{[(round((b - iv[0][0]) / 1e6, 2), round((e - iv[0][0]) / 1e6, 2)) for b, e in iv]}"
+              f"; overlapping pairs {pairs}; peak running {peak_running}")
+        assert pairs, iv
+        for t, p in zip(tickets, probs):
+            f1, g1, _ = pkg.solve(p, tol=1e-6, max_iter=200000, eps_start=1e-1)
+            assert np.array_equal(results[t][0], f1) and np.array_equal(results[t][1], g1)
+    finally:
+        srv.close()
+
+
+def test_server_request_options_and_on_the_fly_cost(pkg):
+    """Per-request options (an SK-NR request among plain ones), and a request
+    whose stored cost would exceed 256 MB served with the on-the-fly cost."""
+    o = pkg.default_options(tol=1e-6, max_iter=200000, eps_start=1e-1)
+    srv = pkg.Server(o, hbm_budget_bytes=16 << 30, max_slots=2)
+    try:
+        small = W.gaussian_mixture(300, 280, seed=3, eps=5e-3)
+        t1 = srv.submit(small, options=pkg.default_options(tol=1e-6, max_iter=200000,
+                                                           eps_start=1e-1, ell=10))
+        big = W.gaussian_cloud(8200, 8300, d=64, seed=4, eps=1e-2)
+        big.normalize_cost = True
+        t2 = srv.submit(big)
+        out = {}
+        deadline = time.time() + 300
+        while len(out) < 2:
+            for t in (t1, t2):
+                if t not in out:
+                    st, f, g, res = srv.poll(t)
+                    if st != pkg.EOT_PENDING:
+                        out[t] = (st, f, g, res)
+            assert time.time() < deadline
+            time.sleep(0.002)
+        st, f, g, res = out[t1]
+        assert st == pkg.EOT_OK and res["nr_accepted"] >= 1, res
+        C = O.sq_euclidean_cost(small.X, small.Y, normalize=True).astype(np.float32)
+        assert O.evaluate(f, g, C.astype(np.float64), small.a, small.b, small.eps)["l1"] <= 1e-6
+        st, f, g, res = out[t2]
+        assert st == pkg.EOT_OK, res
+        # the same request solved directly with the on-the-fly cost: the same result
+        f2, g2, r2 = pkg.solve(big, tol=1e-6, max_iter=200000, eps_start=1e-1,
+                               prec=pkg.EOT_PREC_SPLIT_TC)
+        assert r2["return_status"] == pkg.EOT_OK
+        assert np.array_equal(f, f2) and np.array_equal(g, g2)
+    finally:
+        srv.close()
+
+
 def test_server_admission_budget(pkg):
     o = pkg.default_options()
     srv = pkg.Server(o, hbm_budget_bytes=1 << 16, max_slots=1)
