@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--oracle-sample", action="store_true",
                     help="time the bounded oracle sample of the CPU baseline and print it (JSON)")
     ap.add_argument("--case", default=None,
-                    choices=["coop16k", "stream8k", "sknr4k", "gram", "batch"],
+                    choices=["coop16k", "stream8k", "sknr4k", "gram", "batch", "s4_8k"],
                     help="run one small case for a profiler and exit (no timing, no JSON)")
     return ap.parse_args()
 
@@ -772,6 +772,13 @@ def profile_case(name):
             if pkg.eot_ctransform(pkg.EOT_SIDE_ROW, n, n, C, og, b, of, 1e-2, of, None) != 0:
                 raise RuntimeError(pkg.last_error())
         res = {"status_name": "EOT_OK"}
+    elif name == "s4_8k":
+        # three single SK-NR iterations (eot_sknr_step) on the 8192^2 mixture
+        # (268 MB cost, beyond L2) from a Sinkhorn state with 30 modes
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        st4 = sknr_stage_times(pkg, torch, 8192, 2, 1e-2, flush, torch.cuda.current_stream(),
+                               reps=1)
+        res = {"status_name": f"stage us {[round(x * 1e6, 1) for x in st4]}"}
     elif name == "sknr4k":
         prob = workloads.gaussian_mixture(N, M, seed=0, eps=EPS)
         _, _, res = pkg.solve(prob, tol=TOL, ell=ELL, eps_start=1e-1, max_iter=200000)

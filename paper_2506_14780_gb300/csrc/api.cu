@@ -55,6 +55,8 @@ int acc_template_k(int k);
 int rowacc_rows(int k);
 void init_acc_attributes();
 cudaError_t launch_wtw_reduce(const AccArgs& a, double* WtW, double* gw, cudaStream_t s);
+cudaError_t launch_newton(const Prob* dP, const AccArgs& a, double* WtW, double* gw,
+                          cudaStream_t s);
 cudaError_t launch_colmma(const AccArgs& a, const Prob& hP, const float* tiles, int ncolblk,
                           cudaStream_t s);
 cudaError_t launch_build_tiles(const float* Z, int n, int kk, float* tiles, cudaStream_t s);
@@ -197,6 +199,26 @@ struct Arena {
 };
 
 static int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Segments per output block of the tensor-core products (grid = nblk x nseg
+// CTAs, `slots` resident at once): the fewest segments, from one wave's worth
+// upwards, whose CTAs fill their waves to at least 90% (the CTAs of a block
+// do equal work; a partly empty last wave idles SMs), at most max_seg.
+static int wave_nseg(int nblk, int max_seg, int slots) {
+  const int base = std::max(1, std::min(max_seg, slots / std::max(1, nblk)));
+  int best = base;
+  double best_eff = 0.0;
+  for (int s = base; s <= std::min(max_seg, 4 * base); ++s) {
+    const long long t = (long long)nblk * s;
+    const double eff = (double)t / (double)(ceil_div(t, slots) * (long long)slots);
+    if (eff > best_eff + 1e-9) {
+      best = s;
+      best_eff = eff;
+    }
+    if (eff >= 0.9) return s;
+  }
+  return best;
+}
 
 // Solves issued from the batch and server worker threads run concurrently on
 // one device; there the plain Sinkhorn levels use the captured graphs, not the
@@ -359,7 +381,7 @@ struct Solver {
       stream_plan(n, m, true, ctx->stream_ctas, &sk_gcol, &sk_slots_col);
       stream_plan(n, m, false, ctx->stream_ctas, &sk_grow, &sk_slots_row);
     }
-    mm_nseg = std::max(1, std::min(ceil_div(n, 32), (2 * nsm) / std::max(1, mm_ncolblk)));
+    mm_nseg = wave_nseg(mm_ncolblk, ceil_div(n, 32), 2 * nsm);
     mm_seglen = ceil_div(ceil_div(n, mm_nseg), 32) * 32;
     mm_nseg = ceil_div(n, mm_seglen);
     if (ell > 0) {
@@ -378,7 +400,7 @@ struct Solver {
       kr_seglen = ceil_div(ceil_div(m, kr_nseg), 32) * 32;
       kr_nseg = ceil_div(m, kr_seglen);
       rm_nrowblk = ceil_div(n, 128);
-      rm_nseg = std::max(1, std::min(ceil_div(m, 32), (2 * nsm) / rm_nrowblk));
+      rm_nseg = wave_nseg(rm_nrowblk, ceil_div(m, 32), 2 * nsm);
       rm_seglen = ceil_div(ceil_div(m, rm_nseg), 32) * 32;
       rm_nseg = ceil_div(m, rm_seglen);
     }
@@ -685,9 +707,8 @@ struct Solver {
       if (e == cudaSuccess)
         e = f64 ? launch_col64(dP, hP, MODE_S4, a, s) : launch_colmma(a, hP, tilesV, mm_ncolblk, s);
       if (e != cudaSuccess) break;
-      e = launch_wtw_reduce(a, WtW, gw, s);
+      e = launch_newton(dP, a, WtW, gw, s);
       if (e != cudaSuccess) break;
-      newton_kernel<<<1, 256, 0, s>>>(dP, WtW, gw, nullptr);
       fprime_kernel<<<std::min(ceil_div(n, 256), 4 * ctx->nsm), 256, 0, s>>>(dP);
       e = pass_col(MODE_TRIAL, s);
     }
@@ -1287,11 +1308,13 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   r.levels = L;
   eig_iters_total = 0;
   r.eig_iters = 0;
-  // kernel launches (fixed per phase + loop bodies as counted on the device)
+  // kernel launches (fixed per phase + loop bodies as counted on the device);
+  // an SK-NR body: row pass, S4, Newton (one fused kernel for l <= 32), f', trial
+  const long long nr_body = ell <= 32 ? 5 : 6;
   long long launches = 2 + 1 + (d > 0 ? (pr->normalize_cost ? 2 : 1) : (pr->normalize_cost ? 1 : 0));
   for (int t = 0; t < L; ++t) {
     launches += 1 + 2 + 1 + 2;   // level set-up, splits, first column pass, buffer copy
-    if (lev_nr[t]) launches += 4 + (long long)hLev[t].body_runs * (6 * S->unroll_sknr + 1);
+    if (lev_nr[t]) launches += 4 + (long long)hLev[t].body_runs * (nr_body * S->unroll_sknr + 1);
     else if (lev_coop[t]) launches += 1;
     else launches += (long long)hLev[t].body_runs * (2 * S->unroll_sk + 1);
     if (lev_eig[t]) {
@@ -1300,7 +1323,7 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
     }
   }
   launches += 5 + 2LL * verify_rounds;
-  launches += (long long)resumed_bodies * (lev_nr[L - 1] ? 6 * S->unroll_sknr + 1 : 2 * S->unroll_sk + 1);
+  launches += (long long)resumed_bodies * (lev_nr[L - 1] ? nr_body * S->unroll_sknr + 1 : 2 * S->unroll_sk + 1);
   launches += resumed_coop;
   launches += (verify_rounds > 1 ? (long long)(verify_rounds - 1) : 0);   // level set-up per resume
   r.kernel_launches = launches + 2;   // + the two timestamps
@@ -2396,8 +2419,7 @@ eot_status eot_sknr_step(int32_t n, int32_t m, int32_t ell, const float* C, cons
   const AccArgs acc = S->s4_args();
   CUDA_TRY(launch_colmma(acc, P, S->tilesV, S->mm_ncolblk, s));
   CUDA_TRY(cudaEventRecord(ev[2], s));
-  CUDA_TRY(launch_wtw_reduce(acc, S->WtW, S->gw, s));
-  newton_kernel<<<1, 256, 0, s>>>(S->dP, S->WtW, S->gw, nullptr);
+  CUDA_TRY(launch_newton(S->dP, acc, S->WtW, S->gw, s));
   fprime_kernel<<<std::min(ceil_div(n, 256), 4 * S->ctx->nsm), 256, 0, s>>>(S->dP);
   CUDA_TRY(cudaEventRecord(ev[3], s));
   CUDA_TRY(S->pass_col(MODE_TRIAL, s));

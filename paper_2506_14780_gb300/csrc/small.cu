@@ -19,6 +19,8 @@
 
 namespace eotk {
 
+cudaError_t launch_wtw_reduce(const AccArgs& a, double* WtW, double* gw, cudaStream_t s);
+
 // ---------------------------------------------------------------------------
 // Fused weighted Gram sums of the subspace iteration and the Newton set-up:
 //   G = X^T D_w X,  T = Z^T D_w X (when Z is given),  c = X^T w.
@@ -263,6 +265,137 @@ __global__ void __launch_bounds__(256) newton_kernel(const Prob* __restrict__ PP
       st->dot_vd_a = dva;
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Fused Newton step for l <= 32 (one CTA): the reduction of the per-block
+// partials of W^T D_b^{-1} W and d^T W (what wtw_reduce_kernel does) by all
+// 256 threads into shared memory, then one warp factorises GV - WtW as
+// L D L^T with lane j holding row j in registers (right-looking elimination:
+// at pivot k every lane j > k forms L_jk = H_jk / D_k from its own row and
+// updates its row with H_ki broadcast from lane k), solves L z = grad,
+// y = z / D, L^T x = y (x_k = y_k - sum_{i>k} L_ik x_i as a warp sum), and
+// sets Delta = eps x.  Same arithmetic precision as newton_kernel (float64
+// assembly, float32 factorisation), no block barrier inside the elimination.
+// WtW and gw are also written out (the single-step entry point reports them).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) newton32_kernel(const Prob* __restrict__ PP,
+                                                       const double* __restrict__ part, int nblk,
+                                                       double* __restrict__ WtW,
+                                                       double* __restrict__ gw,
+                                                       const double* __restrict__ Dr) {
+  const Prob& P = *PP;
+  State* st = P.st;
+  if (st->done) return;
+  const int l = P.ell, cnt = l * l + l;
+  __shared__ double red[32 * 32 + 32];
+  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int b = 0;
+    for (; b + 4 <= nblk; b += 4) {
+      s0 += __ldcg(&part[(size_t)(b + 0) * cnt + e]);
+      s1 += __ldcg(&part[(size_t)(b + 1) * cnt + e]);
+      s2 += __ldcg(&part[(size_t)(b + 2) * cnt + e]);
+      s3 += __ldcg(&part[(size_t)(b + 3) * cnt + e]);
+    }
+    for (; b < nblk; ++b) s0 += __ldcg(&part[(size_t)b * cnt + e]);
+    const double t = (s0 + s1) + (s2 + s3);
+    red[e] = t;
+    if (e < l * l) WtW[e] = t;
+    else gw[e - l * l] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  const unsigned FULL = 0xffffffffu;
+  const double* __restrict__ G0 = Dr ? Dr : P.GV;
+  float row[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    float v = 0.f;
+    if (lane < l && i < l) {
+      const double gv = 0.5 * (G0[lane * l + i] + G0[i * l + lane]);
+      const double wt = 0.5 * (red[lane * l + i] + red[i * l + lane]);
+      v = (float)(gv - wt);
+    }
+    row[i] = v;
+  }
+  float z = lane < l ? (float)(-red[l * l + lane]) : 0.f;   // grad_V = -sum_j d_j W_j
+  float dk = 1.f;
+  bool fail = false;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    if (k < l) {
+      const float d = __shfl_sync(FULL, row[k], k);
+      const bool ok = d > 0.f && isfinite(d);
+      fail = fail || !ok;
+      const float inv = ok ? 1.f / d : 0.f;
+      if (lane == k) dk = d;
+      const float lj = lane > k ? row[k] * inv : 0.f;
+#pragma unroll
+      for (int i = k + 1; i < 32; ++i) {
+        if (i < l) {
+          const float hki = __shfl_sync(FULL, row[i], k);
+          row[i] = __fmaf_rn(-hki, lj, row[i]);
+        }
+      }
+      if (lane > k) row[k] = lj;
+    }
+  }
+  // L z = grad (unit lower, row k of L in lane k), then D and L^T
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    if (k < l) {
+      const float zk = __shfl_sync(FULL, z, k);
+      if (lane > k) z = __fmaf_rn(-row[k], zk, z);
+    }
+  }
+  const float y = (!fail && lane < l) ? z / dk : 0.f;
+  float x = y;
+#pragma unroll
+  for (int k = 31; k >= 0; --k) {
+    if (k < l) {
+      float t = (lane > k && lane < l) ? row[k] * x : 0.f;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
+      if (lane == k) x = y - t;
+    }
+  }
+  double dva = 0.0;
+  bool finite = true;
+  if (lane < l) {
+    const double dkd = P.eps * (double)x;
+    P.delta[lane] = dkd;
+    dva = dkd * P.Va[lane];
+    finite = isfinite(dkd);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dva += __shfl_xor_sync(FULL, dva, o);
+  finite = __all_sync(FULL, finite);
+  if (lane == 0) {
+    const bool bad = fail || st->nr_degenerate != 0 || !finite;
+    st->nr_degenerate = 0;
+    if (bad) {
+      st->nr_ok = 0;
+      st->nr_rej += 1;
+      st->cur_g = (st->cur_g + 1) % 3;   // keep the Sinkhorn step: g_{k+1} = h
+    } else {
+      st->nr_ok = 1;
+      st->dot_vd_a = dva;
+    }
+  }
+}
+
+cudaError_t launch_newton(const Prob* dP, const AccArgs& a, double* WtW, double* gw,
+                          cudaStream_t s) {
+  if (a.k <= 32) {
+    newton32_kernel<<<1, 256, 0, s>>>(dP, a.wtw_part, a.nblk, WtW, gw, nullptr);
+    return cudaGetLastError();
+  }
+  cudaError_t e = launch_wtw_reduce(a, WtW, gw, s);
+  if (e != cudaSuccess) return e;
+  newton_kernel<<<1, 256, 0, s>>>(dP, WtW, gw, nullptr);
+  return cudaGetLastError();
 }
 
 // f' = f_k + V Delta (float64 accumulation of float32 V), into the other f buffer.
