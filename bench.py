@@ -530,36 +530,40 @@ def extras(pkg, torch, stream):
                                "(graph-captured) runs every problem, gang sizes from a "
                                "calibrated cost model; median of 3 calls after a first call "
                                "that also calibrates the model (first_call_seconds)"}
-    # c5: served stream (Poisson arrivals, continuous batching, warm restarts)
-    stage("c5: serving")
-    reqs = workloads.served_stream(seed=1, rate_per_s=2000.0, duration_s=60.0, max_requests=96)
+    # the same batch with SK-NR(30): every problem a whole solve on one of the
+    # worker threads (own stream), the longest predicted first
+    stage("c4: batch, SK-NR(30)")
+    obn = pkg.default_options(tol=TOL, max_iter=200000, eps_start=1e-1, ell=ELL)
+    t0 = time.perf_counter()
+    stn, resn = pkg.eot_solve_batch(ps, obn, [np.zeros(q.n) for q in probs],
+                                    [np.zeros(q.m) for q in probs])
+    tn = time.perf_counter() - t0
+    out["c4_batch"]["sknr30"] = {
+        "seconds": round(tn, 3), "problems_per_s": round(len(probs) / tn, 1),
+        "converged": sum(1 for r in resn if r.status == pkg.EOT_OK),
+        "total_iters": int(sum(r.total_iters for r in resn)),
+        "note": "ell = 30: whole SK-NR solves (modes, Newton steps) on 8 host worker threads "
+                "with their own streams, overlapping on the device; one call"}
+    # c5: served stream (Poisson arrivals, continuous batching, warm restarts):
+    # at the offered 2000 requests/s (its first requests: far beyond capacity,
+    # latency is queueing) and at ~70% of the rate measured there
+    stage("c5: serving at 2000/s")
     os5 = pkg.default_options(tol=TOL, max_iter=200000, eps_start=1e-1)
-    srv = pkg.Server(os5, hbm_budget_bytes=48 << 30, max_slots=8)
-    try:
-        t0 = time.perf_counter()
-        tickets = []
-        for r in reqs:
-            while time.perf_counter() - t0 < r["t"]:
-                time.sleep(0.0002)
-            tickets.append(srv.submit(r["problem"], cloud_id=r["cloud_id"]))
-        done = 0
-        for t in tickets:
-            while True:
-                st5, _, _, _ = srv.poll(t)
-                if st5 != pkg.EOT_PENDING:
-                    break
-                time.sleep(0.001)
-            done += st5 in (pkg.EOT_OK, pkg.EOT_NOT_CONVERGED)
-        t1 = time.perf_counter()
-        p50, p99, sps = srv.stats()
-    finally:
-        srv.close()
-    out["c5_serving"] = {"requests": len(reqs), "completed": int(done),
-                         "offered_rate_per_s": 2000.0, "p50_ms": round(p50 * 1e3, 2),
-                         "p99_ms": round(p99 * 1e3, 2), "solves_per_s": round(sps, 1),
-                         "wall_s": round(t1 - t0, 3),
-                         "note": "96 requests of the Poisson stream; n, m log-uniform in "
-                                 "[128, 16384], d in {2, 3, 64}; 8 slots, 48 GB budget"}
+    reqs = workloads.served_stream(seed=1, rate_per_s=2000.0, duration_s=60.0, max_requests=200)
+    hi = serve(pkg, reqs, os5)
+    rate = max(1.0, 0.7 * hi["solves_per_s"])
+    stage(f"c5: serving at {rate:.1f}/s")
+    reqs2 = workloads.served_stream(seed=3, rate_per_s=rate, duration_s=20.0, max_requests=2000)
+    lo = serve(pkg, reqs2, os5)
+    out["c5_serving"] = {
+        "offered_2000_per_s": dict(hi, offered_rate_per_s=2000.0,
+                                   note="the first 200 requests of the 2000/s stream"),
+        "sustainable": dict(lo, offered_rate_per_s=round(rate, 1),
+                            note="20 s Poisson stream at 0.7 x the solves/s measured at 2000/s"),
+        "note": "n, m log-uniform in [128, 16384], d in {2, 3, 64}, eps in {1e-1, 1e-2, 1e-3}, "
+                "half the requests re-use an earlier cloud (warm start from its resident "
+                "potentials); stored costs above 256 MB run with the on-the-fly cost; 8 slots, "
+                "48 GB budget; admitted solves overlap on the device (own streams)"}
     return out, c3_pair
 
 
@@ -630,6 +634,42 @@ def _sample_in_child(threads):
     if r.returncode != 0:
         raise RuntimeError(f"oracle sample failed: {r.stderr[-2000:]}")
     return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def serve(pkg, reqs, opts, slots=8, budget=48 << 30):
+    """Play a request stream into a server in real time; latencies are
+    submit -> completion.  Samples the queue depth and admitted bytes."""
+    srv = pkg.Server(opts, hbm_budget_bytes=budget, max_slots=slots)
+    qmax, hbm_max = 0, 0
+    try:
+        t0 = time.perf_counter()
+        tickets = []
+        for r in reqs:
+            while time.perf_counter() - t0 < r["t"]:
+                time.sleep(0.0002)
+            tickets.append(srv.submit(r["problem"], cloud_id=r["cloud_id"]))
+            s5 = srv.status()
+            qmax = max(qmax, s5["queued"])
+            hbm_max = max(hbm_max, s5["hbm_in_use"])
+        done = 0
+        for t in tickets:
+            while True:
+                st5, _, _, _ = srv.poll(t)
+                if st5 != pkg.EOT_PENDING:
+                    break
+                s5 = srv.status()
+                qmax = max(qmax, s5["queued"])
+                hbm_max = max(hbm_max, s5["hbm_in_use"])
+                time.sleep(0.001)
+            done += st5 in (pkg.EOT_OK, pkg.EOT_NOT_CONVERGED)
+        t1 = time.perf_counter()
+        p50, p99, sps = srv.stats()
+    finally:
+        srv.close()
+    return {"requests": len(reqs), "completed": int(done), "p50_ms": round(p50 * 1e3, 2),
+            "p99_ms": round(p99 * 1e3, 2), "solves_per_s": round(sps, 1),
+            "wall_s": round(t1 - t0, 3), "max_queue_depth": qmax,
+            "max_hbm_admitted_gb": round(hbm_max / 2 ** 30, 2)}
 
 
 def cpu_baseline():

@@ -143,8 +143,12 @@ void eot_default_options(eot_options *opt);
 eot_status eot_solve(const eot_problem *prob, const eot_options *opt,
                      double *f_out, double *g_out, eot_result *res);
 
-/* Solve count independent problems of uneven sizes in one persistent launch
- * (plain Sinkhorn; opt->ell must be 0).  Arrays of count pointers; results[k]
+/* Solve count independent problems of uneven sizes.  Plain Sinkhorn on float32
+ * costs (opt->ell == 0, FP32) runs every problem in one persistent launch;
+ * SK-NR (ell > 0) and the other precisions run each problem as a whole solve
+ * (eot_solve's path) on a pool of host worker threads, each with its own
+ * stream, so that the solves overlap on the device, the problems with the
+ * most predicted work first.  Arrays of count pointers; results[k]
  * (host) holds each problem's status; the call returns the worst status.  Each
  * problem's result does not depend on which others share the batch, nor on how
  * many CTAs the scheduler gives it (bit for bit).  A problem with n > m and no

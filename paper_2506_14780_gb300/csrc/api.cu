@@ -1309,8 +1309,8 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   eig_iters_total = 0;
   r.eig_iters = 0;
   // kernel launches (fixed per phase + loop bodies as counted on the device);
-  // an SK-NR body: row pass, S4, Newton (one fused kernel for l <= 32), f', trial
-  const long long nr_body = ell <= 32 ? 5 : 6;
+  // an SK-NR body: row pass, S4, W^T D_b^-1 W reduction, Newton, f', trial
+  const long long nr_body = 6;
   long long launches = 2 + 1 + (d > 0 ? (pr->normalize_cost ? 2 : 1) : (pr->normalize_cost ? 1 : 0));
   for (int t = 0; t < L; ++t) {
     launches += 1 + 2 + 1 + 2;   // level set-up, splits, first column pass, buffer copy
@@ -2669,14 +2669,13 @@ eot_status eot_solve_batch(int32_t count, const eot_problem* probs, const eot_op
   eot_options o;
   if (opt) o = *opt;
   else eot_default_options(&o);
-  if (o.ell != 0) return fail(EOT_EINVAL, "eot_solve_batch runs plain Sinkhorn (ell = 0)");
   int dev = 0;
   CUDA_TRY(cudaGetDevice(&dev));
   std::vector<eot_status> st(count, EOT_OK);
   std::vector<eot_result> rs(count);
   std::atomic<int> nexti(0);
   std::vector<std::string> errs(count);
-  if (o.prec == EOT_PREC_FP32) {
+  if (o.prec == EOT_PREC_FP32 && o.ell == 0) {
     // one persistent launch for all problems
     const eot_status bs = eotk::run_batch(count, probs, o, f_out, g_out, st.data(), rs.data(),
                                           errs.data(), 0, nullptr);
@@ -2694,12 +2693,27 @@ eot_status eot_solve_batch(int32_t count, const eot_problem* probs, const eot_op
     }
     return worst;
   }
+  // SK-NR (ell > 0) and the float64 / on-the-fly-cost passes: every problem
+  // is a whole solve on one of the worker threads, each with its own stream,
+  // so that the solves overlap on the device; the problems with the most
+  // predicted work (n m times the iterations of the eps schedule) go first
+  std::vector<std::pair<double, int>> order(count);
+  for (int k = 0; k < count; ++k) {
+    const eot_problem& q = probs[k];
+    const double it = (q.eps > 0.0 && std::isfinite(q.eps))
+                          ? eotk::batch_est_iters(eotk::schedule(o.eps_start, q.eps, o.eps_factor),
+                                                  o.max_iter)
+                          : 1.0;
+    order[k] = {-(double)q.n * (double)q.m * it, k};
+  }
+  std::stable_sort(order.begin(), order.end());
   auto work = [&]() {
     cudaSetDevice(dev);
     eotk::t_concurrent = true;
     for (;;) {
-      const int k = nexti.fetch_add(1);
-      if (k >= count) break;
+      const int i = nexti.fetch_add(1);
+      if (i >= count) break;
+      const int k = order[i].second;
       eot_options ok = o;
       ok.stream = nullptr;
       st[k] = eotk::solve_one(&probs[k], &ok, f_out[k], g_out[k], &rs[k]);

@@ -268,44 +268,22 @@ __global__ void __launch_bounds__(256) newton_kernel(const Prob* __restrict__ PP
 }
 
 // ---------------------------------------------------------------------------
-// Fused Newton step for l <= 32 (one CTA): the reduction of the per-block
-// partials of W^T D_b^{-1} W and d^T W (what wtw_reduce_kernel does) by all
-// 256 threads into shared memory, then one warp factorises GV - WtW as
-// L D L^T with lane j holding row j in registers (right-looking elimination:
-// at pivot k every lane j > k forms L_jk = H_jk / D_k from its own row and
-// updates its row with H_ki broadcast from lane k), solves L z = grad,
-// y = z / D, L^T x = y (x_k = y_k - sum_{i>k} L_ik x_i as a warp sum), and
-// sets Delta = eps x.  Same arithmetic precision as newton_kernel (float64
-// assembly, float32 factorisation), no block barrier inside the elimination.
-// WtW and gw are also written out (the single-step entry point reports them).
+// Newton step for l <= 32 (one warp): GV - WtW (WtW and gw from
+// wtw_reduce_kernel) factorised as L D L^T with lane j holding row j in
+// registers (right-looking elimination: at pivot k every lane j > k forms
+// L_jk = H_jk / D_k from its own row and updates its row with H_ki broadcast
+// from lane k), then L z = grad, y = z / D, L^T x = y (x_k = y_k -
+// sum_{i>k} L_ik x_i as a warp sum), Delta = eps x.  Same precision as
+// newton_kernel (float64 assembly, float32 factorisation), no block barrier.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) newton32_kernel(const Prob* __restrict__ PP,
-                                                       const double* __restrict__ part, int nblk,
-                                                       double* __restrict__ WtW,
-                                                       double* __restrict__ gw,
-                                                       const double* __restrict__ Dr) {
+__global__ void __launch_bounds__(32) newton32_kernel(const Prob* __restrict__ PP,
+                                                      const double* __restrict__ red,
+                                                      const double* __restrict__ gw,
+                                                      const double* __restrict__ Dr) {
   const Prob& P = *PP;
   State* st = P.st;
   if (st->done) return;
-  const int l = P.ell, cnt = l * l + l;
-  __shared__ double red[32 * 32 + 32];
-  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    int b = 0;
-    for (; b + 4 <= nblk; b += 4) {
-      s0 += __ldcg(&part[(size_t)(b + 0) * cnt + e]);
-      s1 += __ldcg(&part[(size_t)(b + 1) * cnt + e]);
-      s2 += __ldcg(&part[(size_t)(b + 2) * cnt + e]);
-      s3 += __ldcg(&part[(size_t)(b + 3) * cnt + e]);
-    }
-    for (; b < nblk; ++b) s0 += __ldcg(&part[(size_t)b * cnt + e]);
-    const double t = (s0 + s1) + (s2 + s3);
-    red[e] = t;
-    if (e < l * l) WtW[e] = t;
-    else gw[e - l * l] = t;
-  }
-  __syncthreads();
-  if (threadIdx.x >= 32) return;
+  const int l = P.ell;
   const int lane = threadIdx.x;
   const unsigned FULL = 0xffffffffu;
   const double* __restrict__ G0 = Dr ? Dr : P.GV;
@@ -320,7 +298,7 @@ __global__ void __launch_bounds__(256) newton32_kernel(const Prob* __restrict__ 
     }
     row[i] = v;
   }
-  float z = lane < l ? (float)(-red[l * l + lane]) : 0.f;   // grad_V = -sum_j d_j W_j
+  float z = lane < l ? (float)(-gw[lane]) : 0.f;   // grad_V = -sum_j d_j W_j
   float dk = 1.f;
   bool fail = false;
 #pragma unroll
@@ -388,13 +366,10 @@ __global__ void __launch_bounds__(256) newton32_kernel(const Prob* __restrict__ 
 
 cudaError_t launch_newton(const Prob* dP, const AccArgs& a, double* WtW, double* gw,
                           cudaStream_t s) {
-  if (a.k <= 32) {
-    newton32_kernel<<<1, 256, 0, s>>>(dP, a.wtw_part, a.nblk, WtW, gw, nullptr);
-    return cudaGetLastError();
-  }
   cudaError_t e = launch_wtw_reduce(a, WtW, gw, s);
   if (e != cudaSuccess) return e;
-  newton_kernel<<<1, 256, 0, s>>>(dP, WtW, gw, nullptr);
+  if (a.k <= 32) newton32_kernel<<<1, 32, 0, s>>>(dP, WtW, gw, nullptr);
+  else newton_kernel<<<1, 256, 0, s>>>(dP, WtW, gw, nullptr);
   return cudaGetLastError();
 }
 

@@ -175,6 +175,41 @@ def test_batch_tall_problems_given_cost(pkg):
         assert np.abs(f - fr).max() <= 1e-3 * ek and np.abs(g - gr).max() <= 1e-3 * ek
 
 
+def test_batch_sknr_members(pkg):
+    """SK-NR(l) through eot_solve_batch (concurrent whole solves on worker
+    streams): every member meets L1 1e-6 in the oracle's evaluation, equals
+    the same problem solved alone (in a batch of one and through eot_solve),
+    bit for bit, with the same iteration count, and takes fewer iterations
+    than Sinkhorn at the small eps of the batch recipe."""
+    probs = W.batch_problems(10, seed=8, n_lo=100, n_hi=900, eps_lo=2e-3, eps_hi=2e-2)
+    keep = []
+    ps = [pkg.make_problem(p.a, p.b, X=p.X, Y=p.Y, eps=p.eps, normalize_cost=True, keep=keep)
+          for p in probs]
+    o = pkg.default_options(tol=1e-6, max_iter=200000, eps_start=1e-1, ell=12)
+    fs = [np.zeros(p.n) for p in probs]
+    gs = [np.zeros(p.m) for p in probs]
+    st, res = pkg.eot_solve_batch(ps, o, fs, gs)
+    assert st == pkg.EOT_OK, pkg.last_error()
+    osk = pkg.default_options(tol=1e-6, max_iter=200000, eps_start=1e-1)
+    _, res_sk = pkg.eot_solve_batch(ps, osk, [np.zeros(p.n) for p in probs],
+                                    [np.zeros(p.m) for p in probs])
+    fewer = 0
+    for k, p in enumerate(probs):
+        C = O.sq_euclidean_cost(p.X, p.Y, normalize=True).astype(np.float32).astype(np.float64)
+        assert O.evaluate(fs[k], gs[k], C, p.a, p.b, p.eps)["l1"] <= 1e-6
+        fewer += res[k].total_iters < res_sk[k].total_iters
+    for k in (0, 4, 9):
+        p = probs[k]
+        fa, ga = [np.zeros(p.n)], [np.zeros(p.m)]
+        sta, resa = pkg.eot_solve_batch([ps[k]], o, fa, ga)
+        assert sta == pkg.EOT_OK and resa[0].total_iters == res[k].total_iters
+        assert np.array_equal(fa[0], fs[k]) and np.array_equal(ga[0], gs[k])
+        f1, g1, r1 = pkg.solve(p, tol=1e-6, max_iter=200000, eps_start=1e-1, ell=12)
+        assert r1["total_iters"] == res[k].total_iters
+        assert np.array_equal(f1, fs[k]) and np.array_equal(g1, gs[k])
+    assert fewer >= 8, [(r.total_iters, q.total_iters) for r, q in zip(res, res_sk)]
+
+
 def test_batch_rejects_bad_member(pkg):
     good = W.uniform_square(40, 50, seed=1, eps=0.05)
     keep = []
