@@ -220,6 +220,17 @@ static int wave_nseg(int nblk, int max_seg, int slots) {
   return best;
 }
 
+// Segments of the staged tensor-core products: at most 8 (one thread-block
+// cluster per output block, segments merged in distributed shared memory)
+// when that still fills at least 80% of its waves, else the plain rule
+// (segments merged through global records).
+static int mma_nseg(int nblk, int max_seg, int slots) {
+  const int capped = wave_nseg(nblk, std::min(max_seg, 8), slots);
+  const long long t = (long long)nblk * capped;
+  const double eff = (double)t / (double)(ceil_div(t, slots) * (long long)slots);
+  return eff >= 0.8 ? capped : wave_nseg(nblk, max_seg, slots);
+}
+
 // Solves issued from the batch and server worker threads run concurrently on
 // one device; there the plain Sinkhorn levels use the captured graphs, not the
 // cooperative loop (whose grid barriers need the whole grid resident at once).
@@ -381,7 +392,7 @@ struct Solver {
       stream_plan(n, m, true, ctx->stream_ctas, &sk_gcol, &sk_slots_col);
       stream_plan(n, m, false, ctx->stream_ctas, &sk_grow, &sk_slots_row);
     }
-    mm_nseg = wave_nseg(mm_ncolblk, ceil_div(n, 32), 2 * nsm);
+    mm_nseg = mma_nseg(mm_ncolblk, ceil_div(n, 32), 2 * nsm);
     mm_seglen = ceil_div(ceil_div(n, mm_nseg), 32) * 32;
     mm_nseg = ceil_div(n, mm_seglen);
     if (ell > 0) {
@@ -400,7 +411,7 @@ struct Solver {
       kr_seglen = ceil_div(ceil_div(m, kr_nseg), 32) * 32;
       kr_nseg = ceil_div(m, kr_seglen);
       rm_nrowblk = ceil_div(n, 128);
-      rm_nseg = wave_nseg(rm_nrowblk, ceil_div(m, 32), 2 * nsm);
+      rm_nseg = mma_nseg(rm_nrowblk, ceil_div(m, 32), 2 * nsm);
       rm_seglen = ceil_div(ceil_div(m, rm_nseg), 32) * 32;
       rm_nseg = ceil_div(m, rm_seglen);
     }

@@ -30,6 +30,7 @@ namespace eotk {
 constexpr int kMmaM = 128;      // columns per CTA
 constexpr int kMmaKC = 32;      // rows per chunk
 constexpr int kMmaWait = 1 << 22;
+constexpr int kMmaMaxCluster = 8;   // segments per output block merged in one cluster
 
 // Swizzled tiles of Z^T: for chunk c of 32 rows, tile (c, part) holds NN rows
 // (the k index, padded with zeros) of 32 floats (the chunk's rows of Z), part 0
@@ -244,6 +245,228 @@ __device__ __noinline__ void colmma_finish(const AccArgs& args, const Prob& P, u
     else if (tot[0] < st->tol) st->done = 1;
     else if (st->iter >= st->max_iter) st->done = 2;
   }
+}
+
+// ---------------------------------------------------------------------------
+// Cluster epilogue of the staged kernel: the nseg segment CTAs of an output
+// block form one thread-block cluster.  Each CTA leaves its record (per
+// output index: the (reference, sum) head of its log-sum-exp and its product
+// row) in its own shared memory; after a cluster barrier, CTA rank r merges
+// the records of all segments for its slice of the block's 128 indices by
+// distributed shared-memory loads (segments in rank order: deterministic),
+// finishes those indices (the product or W = pi(f_k, h)^T V, and in the SK-NR
+// pass h = f_k^{C,eps}, its splits, d_j) and, in the SK-NR pass, the slice's
+// partials of W^T D_b^{-1} W, d^T W and the three scalar sums; after a second
+// barrier rank 0 adds the slices' partials (rank order) into the block's
+// record and takes the grid-wide step as the last block to arrive.  No
+// global round trip between the segments' streams and the merge.
+// Shared memory (from the 1024-aligned base; the cost and operand rings are
+// idle by then): records [128][NN + 4] floats (R, -, S as a double, the
+// product row), then the slice rows and the partials.
+// ---------------------------------------------------------------------------
+template <int NN>
+struct ClusterEpi {
+  static constexpr int RW = NN + 4;                               // record floats
+  static constexpr int WS = NN + 1;                               // slice row stride
+  static constexpr uint32_t rec = 128u * RW * 4u;
+  static constexpr uint32_t scr = rec;                            // sW, sWb [128][WS]
+  static constexpr uint32_t vec = scr + 2u * 128u * WS * 4u;      // sD, sS, sBi [128]
+  static constexpr uint32_t part = (vec + 3u * 128u * 4u + 15u) & ~15u;   // doubles
+  static constexpr uint32_t bytes_s4 = part + (uint32_t)(NN * NN + NN + 4) * 8u;
+  static constexpr uint32_t bytes_prod = scr + 3u * 128u * 4u + 128u * NN * 4u;
+};
+
+template <int NN>
+__device__ __noinline__ void cluster_finish(const AccArgs& args, const Prob& P,
+                                            unsigned char* sbase, uint32_t sb, MmaEpi& epi,
+                                            int cb, int gb, int dst_g, int len, bool s4) {
+  using CE = ClusterEpi<NN>;
+  State* st = P.st;
+  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, wid = tid >> 5;
+  const int kk = args.k;
+  const int cs = (int)gridDim.y;
+  const int rank = (int)cluster_rank();
+  const int c0 = rank * kMmaM / cs, c1 = (rank + 1) * kMmaM / cs, w = c1 - c0;
+  float* sW = reinterpret_cast<float*>(sbase + CE::scr);
+  float* sWb = sW + kMmaM * CE::WS;
+  float* sD = reinterpret_cast<float*>(sbase + (s4 ? CE::vec : CE::scr));
+  float* sS = sD + kMmaM;
+  float* sBi = sS + kMmaM;
+  double accv[3] = {0.0, 0.0, 0.0};
+  // heads: one thread per index of the slice, every segment's head in flight
+  if (tid < w) {
+    const int cc = c0 + tid, j = cb * kMmaM + cc;
+    const bool jv = j < len;
+    float rr[8];
+    double ss[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      if (r < cs) {
+        const uint32_t a = peer_addr(sb + (uint32_t)(cc * CE::RW) * 4u, (uint32_t)r);
+        rr[r] = ld_peer_f(a);
+        ss[r] = ld_peer_d(a + 8u);
+      }
+    }
+    float R = -INFINITY;
+    double Stot = 0.0;
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+      if (r < cs) merge_dd(R, Stot, rr[r], ss[r]);
+    sS[tid] = (s4 && jv) ? (float)(P.b[j] / (Stot * ldexp(1.0, (int)R))) : 1.f;
+    sBi[tid] = (s4 && jv) ? (float)(1.0 / P.b[j]) : 0.f;
+    if (s4) {
+      sD[tid] = 0.f;
+      if (jv) {
+        double Ld = (double)R * 0.6931471805599453 + (double)log_sum(Stot);
+        const double sh = P.g[gb][j];
+        double o = sh - P.eps * Ld;
+        if (!isfinite(o) || !(Stot > 0.0) || fabs(o) > P.pot_bound) {
+          atomicAdd(&st->numeric, 1);
+          o = sh;
+          Ld = 0.0;
+        }
+        const float L = (float)Ld;
+        // the products need the exponentials in range: flag a column whose
+        // largest term lies far from 1 (the Newton step is then skipped)
+        if (R > 60.f || R < -60.f) atomicOr(&st->nr_degenerate, 1);
+        P.g[dst_g][j] = o;
+        P.Lcol[j] = L;
+        double hi;
+        float lo;
+        split_grid(o + P.eps * P.logb[j], P.qscale, P.qinv, hi, lo);
+        P.cs[dst_g].A[j] = (float)(hi + (double)P.M);
+        P.cs[dst_g].AL[j] = lo;
+        split_grid(o, P.qscale, P.qinv, hi, lo);
+        P.cs[dst_g].K[j] = (float)((double)P.M - hi);
+        P.cs[dst_g].KL[j] = lo;
+        const double wj = P.b[j];
+        const float em = expm1f(L);
+        const double dj = -(double)em;          // 1 - exp((g_j - h_j)/eps)
+        args.dw[j] = dj;
+        sD[tid] = (float)dj;
+        accv[0] = wj * (double)fabsf(em);
+        accv[1] = wj * Ld;
+        accv[2] = wj * o;
+      }
+    }
+  }
+  // product rows of the slice: float4 pieces, segments in rank order
+  {
+    constexpr int Q4 = NN / 4;
+    float* raw = s4 ? sW : reinterpret_cast<float*>(sbase + CE::scr + 3u * 128u * 4u);
+    for (int e = tid; e < w * Q4; e += nthr) {
+      const int t = e / Q4, q = e - t * Q4;
+      const uint32_t off = sb + (uint32_t)((c0 + t) * CE::RW + 4 + 4 * q) * 4u;
+      float4 v[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+        if (r < cs) v[r] = ld_peer4(peer_addr(off, (uint32_t)r));
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        if (r < cs) {
+          acc.x += v[r].x;
+          acc.y += v[r].y;
+          acc.z += v[r].z;
+          acc.w += v[r].w;
+        }
+      }
+      if (s4) {
+        float* dstw = sW + t * CE::WS + 4 * q;
+        dstw[0] = acc.x;
+        dstw[1] = acc.y;
+        dstw[2] = acc.z;
+        dstw[3] = acc.w;
+      } else {
+        reinterpret_cast<float4*>(raw)[t * Q4 + q] = acc;
+      }
+    }
+  }
+  __syncthreads();
+  // scale the rows: W_j (SK-NR: times b_j / sum_i 2^{y_ij}; products: absolute)
+  {
+    const float* raw = s4 ? sW : reinterpret_cast<const float*>(sbase + CE::scr + 3u * 128u * 4u);
+    for (int e = tid; e < w * NN; e += nthr) {
+      const int t = e / NN, k = e - t * NN;
+      const int j = cb * kMmaM + c0 + t;
+      const bool live = j < len && k < kk;
+      const float wv = (s4 ? raw[t * CE::WS + k] : raw[t * NN + k]) * sS[t];
+      if (live) args.out[(size_t)j * kk + k] = wv;
+      if (s4) {
+        sW[t * CE::WS + k] = live ? wv : 0.f;
+        sWb[t * CE::WS + k] = live ? wv * sBi[t] : 0.f;
+      }
+    }
+  }
+  if (!s4) {
+    // every peer has read this CTA's records before any CTA leaves
+    cluster_sync_all();
+    return;
+  }
+  __syncthreads();
+  // the slice's partials: W^T D_b^{-1} W and d^T W (float32 over the slice's
+  // indices, in index order) and the three scalar sums (float64)
+  double* part = reinterpret_cast<double*>(sbase + CE::part);
+  const int cnt = kk * kk + kk;
+  for (int e = tid; e < kk * kk; e += nthr) {
+    const int r = e / kk, c2 = e - r * kk;
+    float sum = 0.f;
+    for (int t = 0; t < w; ++t) sum = __fmaf_rn(sWb[t * CE::WS + r], sW[t * CE::WS + c2], sum);
+    part[e] = (double)sum;
+  }
+  for (int e = tid; e < kk; e += nthr) {
+    float sum = 0.f;
+    for (int t = 0; t < w; ++t) sum = __fmaf_rn(sD[t], sW[t * CE::WS + e], sum);
+    part[kk * kk + e] = (double)sum;
+  }
+  if (wid < 4) {   // the slice's indices live in threads 0..w-1 (w <= 128)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double x = warp_sum_d(accv[k]);
+      if (lane == 0) epi.red[k * 8 + wid] = x;
+    }
+  }
+  __syncthreads();
+  if (tid < 3) part[cnt + tid] = (epi.red[tid * 8] + epi.red[tid * 8 + 1]) +
+                                 (epi.red[tid * 8 + 2] + epi.red[tid * 8 + 3]);
+  // every slice's partials are in place, and every record has been read
+  cluster_sync_all();
+  if (rank == 0) {
+    const uint32_t pa = sb + CE::part;
+    double* dstp = args.wtw_part + (size_t)cb * cnt;
+    for (int e = tid; e < cnt + 3; e += nthr) {
+      double v[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+        if (r < cs) v[r] = ld_peer_d(peer_addr(pa + (uint32_t)e * 8u, (uint32_t)r));
+      double sum = 0.0;
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+        if (r < cs) sum += v[r];
+      if (e < cnt) dstp[e] = sum;
+      else args.blkacc[cb * 4 + (e - cnt)] = sum;
+    }
+    __syncthreads();
+    if (tid == 0) epi.last = arrive_count(args.gcnt) == (unsigned)(args.nblk - 1);
+    __syncthreads();
+    if (epi.last && wid == 0) {
+      double tot[3];
+      warp0_grid_sum3(args.blkacc, args.nblk, tot);
+      if (lane == 0) {
+        *args.gcnt = 0u;
+        st->l1_col = tot[0];
+        st->sum_wL = tot[1];
+        st->qsemi = st->sum_af + tot[2];   // Q_semi(f_k) = <f_k, a> + <h, b>
+        st->iter += 1;
+        st->nr_ok = 0;
+        if (st->numeric > 0) st->done = 3;
+        else if (tot[0] < st->tol) st->done = 1;
+        else if (st->iter >= st->max_iter) st->done = 2;
+      }
+    }
+  }
+  // rank 0 has read every slice's partials before any CTA leaves
+  cluster_sync_all();
 }
 
 template <int NN>
@@ -558,9 +781,11 @@ __device__ __forceinline__ void tf32_split2(float2 x, uint32_t& h0, uint32_t& h1
 // columns j, the cost tile 128 rows x 32 columns from a second tensor map with
 // 128-byte swizzle (16-byte chunk q of row r at chunk q ^ (r & 7)), so that a
 // thread reads its row's 16 values with four conflict-free 16-byte loads.
-template <int NN, bool ROW>
+template <int NN, bool ROW, bool CL>
 __global__ void __launch_bounds__(kTmThreads, 2)
     mma_tma_kernel(AccArgs args, const float* __restrict__ tiles) {
+  static_assert(ClusterEpi<NN>::bytes_prod + 1024 <= TmaSmem<NN>::bytes, "epilogue smem");
+  static_assert(NN > 48 || ClusterEpi<NN>::bytes_s4 + 1024 <= TmaSmem<NN>::bytes, "epilogue smem");
   const Prob* PP = args.P;
   const Prob& P = *PP;
   State* st = P.st;
@@ -822,20 +1047,36 @@ __global__ void __launch_bounds__(kTmThreads, 2)
       double Sd = 0.0;
       merge_dd(R, Sd, s_lr[0][c], s_ls[0][c]);
       merge_dd(R, Sd, s_lr[1][c], s_ls[1][c]);
+      if (CL) {
+        // the record stays in this CTA's shared memory (the rings are idle:
+        // every copy has landed and been consumed, every product is done)
+        float* rec = reinterpret_cast<float*>(sbase) + c * (NN + 4);
+#pragma unroll
+        for (int q = 0; q < NN / 16; ++q) {
+          float v[16];
+          tmem_ld16(tmem + tlane + q * 16, v);
+#pragma unroll
+          for (int u = 0; u < 16; ++u) rec[4 + q * 16 + u] = (!jv || nch == 0) ? 0.f : v[u];
+        }
+        rec[0] = jv ? R : -INFINITY;
+        *reinterpret_cast<double*>(rec + 2) = jv ? Sd : 0.0;
+      }
       float* dst = args.part + ((size_t)seg * olen + (jv ? j : 0)) * (NN + 4);
       // accumulator row c lives in TMEM lane c (warp w reads lanes 32w..32w+31)
+      if (!CL) {
 #pragma unroll
-      for (int q = 0; q < NN / 16; ++q) {
-        float v[16];
-        tmem_ld16(tmem + tlane + q * 16, v);
-        if (jv) {
+        for (int q = 0; q < NN / 16; ++q) {
+          float v[16];
+          tmem_ld16(tmem + tlane + q * 16, v);
+          if (jv) {
 #pragma unroll
-          for (int u = 0; u < 16; ++u) dst[4 + q * 16 + u] = nch == 0 ? 0.f : v[u];
+            for (int u = 0; u < 16; ++u) dst[4 + q * 16 + u] = nch == 0 ? 0.f : v[u];
+          }
         }
-      }
-      if (jv) {
-        dst[0] = R;
-        dst[1] = (float)Sd;
+        if (jv) {
+          dst[0] = R;
+          dst[1] = (float)Sd;
+        }
       }
     }
   }
@@ -844,6 +1085,13 @@ __global__ void __launch_bounds__(kTmThreads, 2)
   if (wid == 9) {
     tc_fence_after();
     tmem_dealloc(tmem, kTmCols);
+  }
+  if (CL) {
+    // every warp of every CTA of the cluster takes the barriers below
+    if (tid == 0 && s_err) atomicAdd(&st->numeric, 1);
+    cluster_sync_all();   // every segment's record is in place
+    cluster_finish<NN>(args, P, sbase, base, epi, cb, gb, dst_g, olen, s4);
+    return;
   }
   if (wid >= 8) return;
   if (tid == 0) {
@@ -864,12 +1112,32 @@ size_t mma_tiles_floats(int n, int k) {
   return (size_t)((n + kMmaKC - 1) / kMmaKC) * 2 * mma_width(k) * kMmaKC;
 }
 
+// Segments merged through a thread-block cluster when an output block has at
+// most 8 of them (the portable cluster size); otherwise through global
+// records and the block's last-arriving CTA.
+bool mma_cluster_merge(int nseg) { return nseg >= 1 && nseg <= kMmaMaxCluster; }
+
 // (A programmatic dependent launch of this kernel measured slower: its CTAs
 // then hold shared memory and TMEM while the preceding pass finishes.)
 template <int NN, bool ROW>
 static cudaError_t launch_tma(const AccArgs& a, const float* tiles, dim3 grid, cudaStream_t s) {
-  mma_tma_kernel<NN, ROW><<<grid, kTmThreads, TmaSmem<NN>::bytes, s>>>(a, tiles);
-  return cudaGetLastError();
+  if (!mma_cluster_merge((int)grid.y)) {
+    mma_tma_kernel<NN, ROW, false><<<grid, kTmThreads, TmaSmem<NN>::bytes, s>>>(a, tiles);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(kTmThreads);
+  cfg.dynamicSmemBytes = TmaSmem<NN>::bytes;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 1;
+  attr[0].val.clusterDim.y = grid.y;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, mma_tma_kernel<NN, ROW, true>, a, tiles);
 }
 
 template <int NN>
@@ -917,10 +1185,14 @@ cudaError_t launch_build_tiles(const float* Z, int n, int kk, float* tiles, cuda
 
 template <int NN>
 static void set_tma_attr() {
-  cudaFuncSetAttribute(mma_tma_kernel<NN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)TmaSmem<NN>::bytes);
-  cudaFuncSetAttribute(mma_tma_kernel<NN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)TmaSmem<NN>::bytes);
+  cudaFuncSetAttribute(mma_tma_kernel<NN, false, false>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TmaSmem<NN>::bytes);
+  cudaFuncSetAttribute(mma_tma_kernel<NN, true, false>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TmaSmem<NN>::bytes);
+  cudaFuncSetAttribute(mma_tma_kernel<NN, false, true>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TmaSmem<NN>::bytes);
+  cudaFuncSetAttribute(mma_tma_kernel<NN, true, true>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TmaSmem<NN>::bytes);
 }
 
 void init_mma_attributes() {
