@@ -68,6 +68,7 @@ void init_stream_attributes();
 int stream_ctas_per_sm();
 void stream_plan(int n, int m, bool col, int ctas, int* grid, int* slots);
 cudaError_t launch_sk_coop(const Prob* dP, const Prob& hP, int max_body, cudaStream_t s);
+int mma_active_clusters(int cs);
 cudaError_t launch_exp2_check(int count, const float* p, const float* q, int variant, float* out,
                               cudaStream_t s);
 void init_gram_attributes();
@@ -220,15 +221,38 @@ static int wave_nseg(int nblk, int max_seg, int slots) {
   return best;
 }
 
-// Segments of the staged tensor-core products: at most 8 (one thread-block
-// cluster per output block, segments merged in distributed shared memory)
-// when that still fills at least 80% of its waves, else the plain rule
-// (segments merged through global records).
-static int mma_nseg(int nblk, int max_seg, int slots) {
-  const int capped = wave_nseg(nblk, std::min(max_seg, 8), slots);
-  const long long t = (long long)nblk * capped;
-  const double eff = (double)t / (double)(ceil_div(t, slots) * (long long)slots);
-  return eff >= 0.8 ? capped : wave_nseg(nblk, max_seg, slots);
+// Segments of the staged tensor-core products over `len` reduction indices.
+// Two ways to merge a block's segments: in a thread-block cluster of up to 8
+// CTAs (distributed shared memory) or through global records and the block's
+// last CTA; clusters pack the SMs less densely (a cluster stays within one
+// GPC).  Each choice is costed as its waves times the rows a CTA streams
+// plus the merge's cost in row-equivalents (measured on the 4096^2 workload:
+// about 60 rows a segment for the global merge, 260 for the cluster's), and
+// the cheapest segment count and merge are taken.
+static int mma_nseg(int nblk, int len, int slots, bool* cluster) {
+  const int max_seg = ceil_div(len, 32);
+  int best = -1;
+  double best_cost = 0.0;
+  *cluster = false;
+  for (int s = 1; s <= std::min(max_seg, 64); ++s) {   // global merge: ~60 rows a segment
+    const double cost =
+        (double)ceil_div((long long)nblk * s, slots) * ceil_div(len, s) + 60.0 * s;
+    if (best < 0 || cost < best_cost) {
+      best = s;
+      best_cost = cost;
+    }
+  }
+  for (int cs = 1; cs <= std::min(8, max_seg); ++cs) {
+    const int active = mma_active_clusters(cs);
+    if (active < 1) continue;
+    const double cost = (double)ceil_div(nblk, active) * ceil_div(len, cs) + 260.0;
+    if (cost < best_cost) {
+      best = cs;
+      best_cost = cost;
+      *cluster = true;
+    }
+  }
+  return best;
 }
 
 // Solves issued from the batch and server worker threads run concurrently on
@@ -323,6 +347,7 @@ struct Solver {
   int ek_K = 0, kc_nseg = 1, kc_seglen = 0, kr_nseg = 1, kr_seglen = 0, kr_nrowblk = 0;
   int mm_ncolblk = 0, mm_nseg = 1, mm_seglen = 0;   // tensor-core column products
   int rm_nrowblk = 0, rm_nseg = 1, rm_seglen = 0;   // tensor-core row products
+  bool mm_cluster = false, rm_cluster = false;      // segments merged in a cluster
   int sk_gcol = 0, sk_grow = 0, sk_slots_col = 1, sk_slots_row = 1;   // stream passes
   // memory
   void* mem = nullptr;
@@ -392,7 +417,7 @@ struct Solver {
       stream_plan(n, m, true, ctx->stream_ctas, &sk_gcol, &sk_slots_col);
       stream_plan(n, m, false, ctx->stream_ctas, &sk_grow, &sk_slots_row);
     }
-    mm_nseg = mma_nseg(mm_ncolblk, ceil_div(n, 32), 2 * nsm);
+    mm_nseg = mma_nseg(mm_ncolblk, n, 2 * nsm, &mm_cluster);
     mm_seglen = ceil_div(ceil_div(n, mm_nseg), 32) * 32;
     mm_nseg = ceil_div(n, mm_seglen);
     if (ell > 0) {
@@ -411,7 +436,7 @@ struct Solver {
       kr_seglen = ceil_div(ceil_div(m, kr_nseg), 32) * 32;
       kr_nseg = ceil_div(m, kr_seglen);
       rm_nrowblk = ceil_div(n, 128);
-      rm_nseg = mma_nseg(rm_nrowblk, ceil_div(m, 32), 2 * nsm);
+      rm_nseg = mma_nseg(rm_nrowblk, m, 2 * nsm, &rm_cluster);
       rm_seglen = ceil_div(ceil_div(m, rm_nseg), 32) * 32;
       rm_nseg = ceil_div(m, rm_seglen);
     }
@@ -606,6 +631,7 @@ struct Solver {
     a.gcnt = s4gcnt;
     a.dw = dw;
     a.wtw_part = wtw_part;
+    a.cluster = mm_cluster ? 1 : 0;
     return a;
   }
   AccArgs kcol_args(int fb, int gb, const float* Z, float* out) const {
@@ -622,6 +648,7 @@ struct Solver {
     a.nblk = mm_ncolblk;
     a.fbuf = fb;
     a.gbuf = gb;
+    a.cluster = mm_cluster ? 1 : 0;
     return a;
   }
   AccArgs krow_args(int fb, int gb, const float* Z, float* out) const {
@@ -655,6 +682,7 @@ struct Solver {
     a.nblk = rm_nrowblk;
     a.fbuf = fb;
     a.gbuf = gb;
+    a.cluster = rm_cluster ? 1 : 0;
     return a;
   }
   // Op(pi) Z: on the tensor cores when the cost has its tensor maps, else on

@@ -172,6 +172,7 @@ struct AccArgs {
   unsigned* gcnt;
   double* dw;            // (m) gradient weights d_j (SK-NR)
   double* wtw_part;      // [nblk][k*k + k] block partials (SK-NR)
+  int cluster;           // staged kernel: merge a block's segments in a cluster (nseg <= 8)
 };
 
 }  // namespace eotk

@@ -1112,16 +1112,48 @@ size_t mma_tiles_floats(int n, int k) {
   return (size_t)((n + kMmaKC - 1) / kMmaKC) * 2 * mma_width(k) * kMmaKC;
 }
 
-// Segments merged through a thread-block cluster when an output block has at
-// most 8 of them (the portable cluster size); otherwise through global
-// records and the block's last-arriving CTA.
-bool mma_cluster_merge(int nseg) { return nseg >= 1 && nseg <= kMmaMaxCluster; }
+// Segments merged through a thread-block cluster when the plan asks for it
+// and an output block has at most 8 of them (the portable cluster size);
+// otherwise through global records and the block's last-arriving CTA.
+static bool mma_cluster_merge(const AccArgs& a, int nseg) {
+  return a.cluster && nseg >= 1 && nseg <= kMmaMaxCluster;
+}
+
+// Clusters of cs CTAs of the staged kernel that fit on the current device at
+// once (clusters live within one GPC, so this is below the CTA slots / cs);
+// 0 if such a cluster cannot be launched.  Queried once per device and size.
+int mma_active_clusters(int cs) {
+  static int cache[64][kMmaMaxCluster + 1];
+  static bool done[64][kMmaMaxCluster + 1];
+  int dev = 0;
+  if (cs < 1 || cs > kMmaMaxCluster || cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return 0;
+  if (done[dev][cs]) return cache[dev][cs];
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(1, cs, 1);
+  cfg.blockDim = dim3(kTmThreads);
+  cfg.dynamicSmemBytes = TmaSmem<48>::bytes;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 1;
+  attr[0].val.clusterDim.y = cs;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int num = 0;
+  if (cudaOccupancyMaxActiveClusters(&num, mma_tma_kernel<48, false, true>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    num = 0;
+  }
+  cache[dev][cs] = num;
+  done[dev][cs] = true;
+  return num;
+}
 
 // (A programmatic dependent launch of this kernel measured slower: its CTAs
 // then hold shared memory and TMEM while the preceding pass finishes.)
 template <int NN, bool ROW>
 static cudaError_t launch_tma(const AccArgs& a, const float* tiles, dim3 grid, cudaStream_t s) {
-  if (!mma_cluster_merge((int)grid.y)) {
+  if (!mma_cluster_merge(a, (int)grid.y)) {
     mma_tma_kernel<NN, ROW, false><<<grid, kTmThreads, TmaSmem<NN>::bytes, s>>>(a, tiles);
     return cudaGetLastError();
   }

@@ -138,12 +138,14 @@ def test_ctransform_extreme_exponents(pkg):
 
 # m % 4 != 0 takes the CUDA-core kernels, m % 4 == 0 the staged tensor-core
 # kernels (ragged row and column blocks, every template width); the last two
-# shapes merge their segments in thread-block clusters (both directions at
-# 4096^2, the row direction at 6507 x 3816), the others through global records
+# the staged kernels merge the segments of an output block either in a
+# thread-block cluster or through global records, whichever the plan costs
+# lower: most of these shapes take clusters; the tall 16384 x 256 cost
+# merges its many column segments through global records
 @pytest.mark.parametrize("n,m,k", [(50, 70, 8), (257, 129, 33), (1024, 900, 40),
                                    (300, 260, 17), (130, 516, 48), (2049, 1028, 30),
                                    (33, 4, 5), (4100, 132, 48), (4096, 4096, 40),
-                                   (6507, 3816, 30)])
+                                   (6507, 3816, 30), (16384, 256, 30)])
 def test_kapply_parity(pkg, n, m, k):
     prob = W.uniform_square(n, m, seed=11, eps=0.05)
     C = O.sq_euclidean_cost(prob.X, prob.Y, normalize=True).astype(np.float32)
