@@ -68,7 +68,6 @@ void init_stream_attributes();
 int stream_ctas_per_sm();
 void stream_plan(int n, int m, bool col, int ctas, int* grid, int* slots);
 cudaError_t launch_sk_coop(const Prob* dP, const Prob& hP, int max_body, cudaStream_t s);
-int mma_active_clusters(int cs);
 cudaError_t launch_exp2_check(int count, const float* p, const float* q, int variant, float* out,
                               cudaStream_t s);
 void init_gram_attributes();
@@ -225,7 +224,7 @@ static int wave_nseg(int nblk, int max_seg, int slots) {
 // Two ways to merge a block's segments: in a thread-block cluster of up to 8
 // CTAs (distributed shared memory) or through global records and the block's
 // last CTA; clusters pack the SMs less densely (a cluster stays within one
-// GPC).  Each choice is costed as its waves times the rows a CTA streams
+// GPC: counted as 85% of the two-per-SM CTA slots).  Each choice is costed as its waves times the rows a CTA streams
 // plus the merge's cost in row-equivalents (measured on the 4096^2 workload:
 // about 60 rows a segment for the global merge, 260 for the cluster's), and
 // the cheapest segment count and merge are taken.
@@ -243,8 +242,7 @@ static int mma_nseg(int nblk, int len, int slots, bool* cluster) {
     }
   }
   for (int cs = 1; cs <= std::min(8, max_seg); ++cs) {
-    const int active = mma_active_clusters(cs);
-    if (active < 1) continue;
+    const int active = std::max(1, (int)(0.85 * slots / cs));
     const double cost = (double)ceil_div(nblk, active) * ceil_div(len, cs) + 260.0;
     if (cost < best_cost) {
       best = cs;

@@ -19,6 +19,8 @@
 // MMAs; two buffers let the tensor core work on chunk c while the threads form
 // chunk c + 1; completion is tracked with tcgen05.commit on an mbarrier whose
 // waits are bounded.
+#include <algorithm>
+
 #include "eot_device.cuh"
 #include "eot_internal.h"
 #include "reduce.cuh"
@@ -1119,36 +1121,6 @@ static bool mma_cluster_merge(const AccArgs& a, int nseg) {
   return a.cluster && nseg >= 1 && nseg <= kMmaMaxCluster;
 }
 
-// Clusters of cs CTAs of the staged kernel that fit on the current device at
-// once (clusters live within one GPC, so this is below the CTA slots / cs);
-// 0 if such a cluster cannot be launched.  Queried once per device and size.
-int mma_active_clusters(int cs) {
-  static int cache[64][kMmaMaxCluster + 1];
-  static bool done[64][kMmaMaxCluster + 1];
-  int dev = 0;
-  if (cs < 1 || cs > kMmaMaxCluster || cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return 0;
-  if (done[dev][cs]) return cache[dev][cs];
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(1, cs, 1);
-  cfg.blockDim = dim3(kTmThreads);
-  cfg.dynamicSmemBytes = TmaSmem<48>::bytes;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = 1;
-  attr[0].val.clusterDim.y = cs;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  int num = 0;
-  if (cudaOccupancyMaxActiveClusters(&num, mma_tma_kernel<48, false, true>, &cfg) != cudaSuccess) {
-    cudaGetLastError();
-    num = 0;
-  }
-  cache[dev][cs] = num;
-  done[dev][cs] = true;
-  return num;
-}
-
 // (A programmatic dependent launch of this kernel measured slower: its CTAs
 // then hold shared memory and TMEM while the preceding pass finishes.)
 template <int NN, bool ROW>
@@ -1217,6 +1189,15 @@ cudaError_t launch_build_tiles(const float* Z, int n, int kk, float* tiles, cuda
 
 template <int NN>
 static void set_tma_attr() {
+  // two CTAs per SM need most of the SM's shared memory
+  cudaFuncSetAttribute(mma_tma_kernel<NN, false, false>,
+                       cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  cudaFuncSetAttribute(mma_tma_kernel<NN, true, false>,
+                       cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  cudaFuncSetAttribute(mma_tma_kernel<NN, false, true>,
+                       cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  cudaFuncSetAttribute(mma_tma_kernel<NN, true, true>,
+                       cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   cudaFuncSetAttribute(mma_tma_kernel<NN, false, false>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TmaSmem<NN>::bytes);
   cudaFuncSetAttribute(mma_tma_kernel<NN, true, false>,
