@@ -267,102 +267,11 @@ __global__ void __launch_bounds__(256) newton_kernel(const Prob* __restrict__ PP
   }
 }
 
-// ---------------------------------------------------------------------------
-// Newton step for l <= 32 (one warp; WtW and gw from wtw_reduce_kernel):
-// GV - WtW, assembled in float64 and rounded once, is factorised in shared
-// memory as L D L^T with lane j owning column j (at pivot k every lane j > k
-// forms L_jk = H_kj / D_k and updates its column below the pivot), then
-// L z = grad (forward, one z_k broadcast per step), y = z / D and
-// L^T x = y (x_k = y_k - sum_{i>k} L_ik x_i as a warp sum), Delta = eps x.
-// Compact loops (a long unrolled elimination runs once per launch and is
-// fetched cold); no block barrier.  Same precision as newton_kernel.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(32) newton32_kernel(const Prob* __restrict__ PP,
-                                                      const double* __restrict__ WtW,
-                                                      const double* __restrict__ gw,
-                                                      const double* __restrict__ Dr) {
-  const Prob& P = *PP;
-  State* st = P.st;
-  if (st->done) return;
-  const int l = P.ell;
-  const int lane = threadIdx.x;
-  const unsigned FULL = 0xffffffffu;
-  const double* __restrict__ G0 = Dr ? Dr : P.GV;
-  __shared__ float H[32][33];   // H[i][j]: row i, column j (column j owned by lane j)
-  __shared__ float Lm[32][33];  // Lm[k][i] = L_ik (i > k)
-  if (lane < l) {
-#pragma unroll 4
-    for (int i = 0; i < l; ++i) {
-      const double gv = 0.5 * (G0[i * l + lane] + G0[lane * l + i]);
-      const double wt = 0.5 * (WtW[i * l + lane] + WtW[lane * l + i]);
-      H[i][lane] = (float)(gv - wt);
-    }
-  }
-  float z = lane < l ? (float)(-gw[lane]) : 0.f;   // grad_V = -sum_j d_j W_j
-  __syncwarp();
-  float dk = 1.f;
-  bool fail = false;
-#pragma unroll 1
-  for (int k = 0; k < l; ++k) {
-    const float d = H[k][k];
-    const bool ok = d > 0.f && isfinite(d);
-    fail = fail || !ok;
-    const float inv = ok ? __frcp_rn(d) : 0.f;
-    if (lane == k) dk = d;
-    const bool mine = lane > k && lane < l;
-    const float lj = mine ? H[k][lane] * inv : 0.f;
-    if (mine) {
-#pragma unroll 4
-      for (int i = k + 1; i < l; ++i) H[i][lane] = __fmaf_rn(-H[i][k], lj, H[i][lane]);
-      Lm[k][lane] = lj;
-    }
-    __syncwarp();
-  }
-#pragma unroll 1
-  for (int k = 0; k < l; ++k) {
-    const float zk = __shfl_sync(FULL, z, k);
-    if (lane > k && lane < l) z = __fmaf_rn(-Lm[k][lane], zk, z);
-  }
-  const float y = (!fail && lane < l) ? z * __frcp_rn(dk) : 0.f;
-  float x = y;
-#pragma unroll 1
-  for (int k = l - 1; k >= 0; --k) {
-    float t = (lane > k && lane < l) ? Lm[k][lane] * x : 0.f;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
-    if (lane == k) x = y - t;
-  }
-  double dva = 0.0;
-  bool finite = true;
-  if (lane < l) {
-    const double dkd = P.eps * (double)x;
-    P.delta[lane] = dkd;
-    dva = dkd * P.Va[lane];
-    finite = isfinite(dkd);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) dva += __shfl_xor_sync(FULL, dva, o);
-  finite = __all_sync(FULL, finite);
-  if (lane == 0) {
-    const bool bad = fail || st->nr_degenerate != 0 || !finite;
-    st->nr_degenerate = 0;
-    if (bad) {
-      st->nr_ok = 0;
-      st->nr_rej += 1;
-      st->cur_g = (st->cur_g + 1) % 3;   // keep the Sinkhorn step: g_{k+1} = h
-    } else {
-      st->nr_ok = 1;
-      st->dot_vd_a = dva;
-    }
-  }
-}
-
 cudaError_t launch_newton(const Prob* dP, const AccArgs& a, double* WtW, double* gw,
                           cudaStream_t s) {
   cudaError_t e = launch_wtw_reduce(a, WtW, gw, s);
   if (e != cudaSuccess) return e;
-  if (a.k <= 32) newton32_kernel<<<1, 32, 0, s>>>(dP, WtW, gw, nullptr);
-  else newton_kernel<<<1, 256, 0, s>>>(dP, WtW, gw, nullptr);
+  newton_kernel<<<1, 256, 0, s>>>(dP, WtW, gw, nullptr);
   return cudaGetLastError();
 }
 
@@ -672,28 +581,14 @@ __global__ void __launch_bounds__(kEH * kEH) eig_small_kernel(int p, int l, int 
       for (int q = tx; q < p; q += nx) G[r * kES + q] = A[r * kES + q];
     __syncthreads();
   }
-  // G = L D L^T, right-looking: thread q of the first one or two warps owns
-  // column q and updates it below the diagonal at every pivot (no two threads
-  // write the same element); one warp (p <= 32) or a 64-thread named barrier
-  // per pivot instead of a block barrier.  L = L1 D^(1/2) below.
-  {
-    const int nw = p > 32 ? 2 : 1;   // p > 32 implies nt >= 289 threads
-    const unsigned wmask = nt >= 32 ? 0xffffffffu : ((1u << nt) - 1u);
-    if (tid < 32 * nw) {
-      const int q = tid;
-#pragma unroll 1
-      for (int k = 0; k < p; ++k) {
-        const float dk = G[k * kES + k];
-        if (tid == 0 && !(dk > 0.f)) s_fail = 1;
-        const float inv = dk > 0.f ? __frcp_rn(dk) : 0.f;
-        if (q > k && q < p) {
-          const float lq = G[q * kES + k] * inv;
-#pragma unroll 4
-          for (int r = q; r < p; ++r) G[r * kES + q] = __fmaf_rn(-G[r * kES + k], lq, G[r * kES + q]);
-        }
-        if (nw == 2) asm volatile("bar.sync 1, 64;" ::: "memory");
-        else __syncwarp(wmask);
-      }
+  // G = L D L^T by outer products (one barrier per pivot); L = L1 D^(1/2)
+  for (int k = 0; k < p; ++k) {
+    const float dk = G[k * kES + k];
+    if (tid == 0 && !(dk > 0.f)) s_fail = 1;
+    const float inv = dk > 0.f ? 1.f / dk : 0.f;
+    for (int r = k + 1 + ty; r < p; r += nx) {
+      const float hr = G[r * kES + k] * inv;
+      for (int q = k + 1 + tx; q <= r; q += nx) G[r * kES + q] -= hr * G[q * kES + k];
     }
     __syncthreads();
   }
@@ -708,17 +603,15 @@ __global__ void __launch_bounds__(kEH * kEH) eig_small_kernel(int p, int l, int 
   for (int r = ty; r < p; r += nx)        // W = Q (right-hand sides)
     for (int q = tx; q < p; q += nx) W[r * kES + q] = Q[r * kES + q];
   __syncthreads();
-  // B L^T = Q: the rows are independent, one thread a row (forward
-  // substitution: after step q, element q of the row is final)
-  for (int r = tid; r < p; r += nt) {
-#pragma unroll 1
-    for (int q = 0; q < p; ++q) {
-      const float b = W[r * kES + q] * sq[q];
-#pragma unroll 4
-      for (int cc = q + 1; cc < p; ++cc) W[r * kES + cc] -= b * G[cc * kES + q];
+  // B L^T = Q, column by column: after step q, column q of W is final
+  for (int q = 0; q < p; ++q) {
+    const float il = sq[q];
+    for (int r = ty; r < p; r += nx) {
+      const float b = W[r * kES + q] * il;
+      for (int cc = q + 1 + tx; cc < p; cc += nx) W[r * kES + cc] -= b * G[cc * kES + q];
     }
+    __syncthreads();
   }
-  __syncthreads();
   for (int r = ty; r < p; r += nx)
     for (int q = tx; q < p; q += nx) Bout[r * p + q] = W[r * kES + q] * sq[q];
   if (tid == 0 && fail_out) *fail_out = s_fail;
