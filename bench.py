@@ -35,8 +35,10 @@ if ROOT not in sys.path:
 N = M = 4096
 EPS = 1e-3
 TOL = 1e-6
+LEVEL_TOL = 1e-4   # intermediate continuation levels (warm starts): L1 1e-4
 ELL = 30
-METRIC = "time-to-L1-marginal 1e-6 at eps=1e-3 (SK-NR(30), eps continuation 1e-1->1e-3)"
+METRIC = ("time-to-L1-marginal 1e-6 at eps=1e-3 (SK-NR(30), eps continuation 1e-1->1e-3, "
+          "intermediate levels to 1e-4)")
 WORKLOAD = "gaussian_mixture_4096x4096_d3_stored_fp32_cost"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
@@ -70,7 +72,7 @@ def dist_info():
 
 def options(pkg, ell, stream=None, **kw):
     o = pkg.default_options(tol=TOL, max_iter=200000, ell=ell, eps_start=1e-1, eps_factor=0.5,
-                            oversample=10, eig_tol=1e-2, eig_max_iter=100)
+                            level_tol=LEVEL_TOL, oversample=10, eig_tol=1e-2, eig_max_iter=100)
     for k, v in kw.items():
         setattr(o, k, v)
     if stream is not None:
@@ -207,6 +209,7 @@ def run_ours(args):
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": WORKLOAD, "n": N, "m": M, "d": 3, "eps": EPS, "tol": TOL,
                       "ell": ELL, "eps_schedule": "1e-1 x 0.5^k -> 1e-3 (8 levels)",
+                      "level_tol": LEVEL_TOL,
                       "potentials": "f64 (exponents formed exactly, f32 exp/sums)",
                       "l2": "flushed between steps (512 MB write)",
                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"}}
@@ -548,7 +551,8 @@ def extras(pkg, torch, stream):
     # at the offered 2000 requests/s (its first requests: far beyond capacity,
     # latency is queueing) and at ~70% of the rate measured there
     stage("c5: serving at 2000/s")
-    os5 = pkg.default_options(tol=TOL, max_iter=200000, eps_start=1e-1)
+    os5 = pkg.default_options(tol=TOL, max_iter=200000, eps_start=1e-1, level_tol=LEVEL_TOL,
+                              ell=ELL)
     reqs = workloads.served_stream(seed=1, rate_per_s=2000.0, duration_s=60.0, max_requests=200)
     hi = serve(pkg, reqs, os5)
     rate = max(1.0, 0.7 * hi["solves_per_s"])
@@ -562,8 +566,9 @@ def extras(pkg, torch, stream):
                             note="20 s Poisson stream at 0.7 x the solves/s measured at 2000/s"),
         "note": "n, m log-uniform in [128, 16384], d in {2, 3, 64}, eps in {1e-1, 1e-2, 1e-3}, "
                 "half the requests re-use an earlier cloud (warm start from its resident "
-                "potentials); stored costs above 256 MB run with the on-the-fly cost; 8 slots, "
-                "48 GB budget; admitted solves overlap on the device (own streams)"}
+                "potentials); every request SK-NR(30) on a stored float32 cost, continuation "
+                "from 1e-1 (intermediate levels to 1e-4); 8 slots, 48 GB budget; admitted "
+                "solves overlap on the device (own streams)"}
     return out, c3_pair
 
 
@@ -775,7 +780,7 @@ def run_reference(args):
            "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "n": N, "m": M, "d": 3, "eps": EPS, "tol": TOL,
-                      "ell": ELL}, "impl": "reference",
+                      "ell": ELL, "level_tol": LEVEL_TOL}, "impl": "reference",
            "cpu_baseline": cb,
            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)

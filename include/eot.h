@@ -69,8 +69,10 @@ typedef enum { EOT_PREC_FP64 = 0, EOT_PREC_FP32 = 1, EOT_PREC_SPLIT_TC = 2 } eot
 
 /* Semi-dual Hessian used by the Newton step (Eq. d2Q_semi):
  *  EOT_HESS_DIAG_ALPHA: -(1/eps) [V^T D_a V - W^T D_b^{-1} W], W = pi^T V
- *                       (D_r replaced by D_a; equal at the optimum; 3 passes).
- *  EOT_HESS_EXACT:      D_r with r = pi(f, f^{C,eps}) 1 (one extra row pass). */
+ *                       (D_r replaced by D_a; equal at the optimum; 3 passes per
+ *                       iteration).  The device implements this form only.
+ *  EOT_HESS_EXACT:      D_r with r = pi(f, f^{C,eps}) 1 (it would need one extra
+ *                       row pass per iteration); rejected with EOT_EINVAL. */
 typedef enum { EOT_HESS_DIAG_ALPHA = 0, EOT_HESS_EXACT = 1 } eot_hessian;
 
 typedef struct {

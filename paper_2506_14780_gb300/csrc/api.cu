@@ -962,6 +962,8 @@ static eot_status validate(const eot_problem* pr, const eot_options* o) {
     if (o->ell > 0)
       return fail(EOT_EINVAL, "SK-NR (ell > 0) with the on-the-fly cost is not implemented");
   }
+  if (o->hessian != EOT_HESS_DIAG_ALPHA)
+    return fail(EOT_EINVAL, "the device Newton step uses the D_a Hessian (EOT_HESS_DIAG_ALPHA) only");
   if (!(o->tol > 0.0)) return fail(EOT_EINVAL, "tol must be > 0");
   if (o->max_iter < 1) return fail(EOT_EINVAL, "max_iter must be >= 1");
   if (o->ell < 0 || o->ell > kMaxK) return fail(EOT_EINVAL, "ell must be in [0, 64]");

@@ -54,3 +54,15 @@ def test_version_and_error_without_device(lib):
     st, _ = eot.eot_solve(p, o, np.zeros(3), np.zeros(2))
     assert st == eot.EOT_EINVAL
     assert "eps" in eot.last_error()
+
+
+def test_unimplemented_hessian_is_rejected(lib):
+    """The device Newton step uses the D_a form of the Hessian (Eq. d2Q_semi
+    with D_r replaced by D_a); asking for the exact form fails on the host."""
+    import numpy as np
+    from paper_2506_14780_gb300 import eot
+    o = eot.default_options(ell=2, hessian=eot.EOT_HESS_EXACT)
+    p = eot.make_problem(np.ones(5) / 5, np.ones(4) / 4, C=np.zeros((5, 4), np.float32), eps=0.1)
+    st, _ = eot.eot_solve(p, o, np.zeros(5), np.zeros(4))
+    assert st == eot.EOT_EINVAL
+    assert "D_a" in eot.last_error()

@@ -5,7 +5,8 @@
   and stored in float32, eps continuation 1e-1 -> 1e-3, SK-NR with l = 30 and
   plain Sinkhorn): the returned pair is evaluated by the oracle in float64 on
   the same float32 cost and must meet the L1 marginal target 1e-6
-  (Algorithm 4.1's stopping test).
+  (Algorithm 4.1's stopping test); intermediate levels solved to 1e-4 as the
+  benchmark does, and to 1e-6 as well.
 * The on-the-fly cost (EOT_PREC_SPLIT_TC) at the target eps = 1e-3 on a reduced
   instance of the 20000 x 30000 x 64 workload (2000 x 3000, same recipe):
   fixed-iteration iterates within 1e-3 eps of the oracle's on the exact cost,
@@ -38,14 +39,15 @@ def c2():
     return prob, C
 
 
-@pytest.mark.parametrize("ell", [30, 0])
-def test_benchmark_workload_scored_by_oracle(pkg, c2, ell):
+@pytest.mark.parametrize("ell,level_tol", [(30, 1e-4), (0, 1e-4), (30, 0.0)])
+def test_benchmark_workload_scored_by_oracle(pkg, c2, ell, level_tol):
     """The benchmark's solve (same options) returns a pair whose float64 L1
     marginal error on the float32 cost is below the 1e-6 target; the reported
     L1, dual value and duality gap agree with the oracle's evaluation."""
     prob, C = c2
     f, g, res = pkg.solve(prob, tol=1e-6, ell=ell, eps_start=1e-1, eps_factor=0.5,
-                          oversample=10, eig_tol=1e-2, eig_max_iter=100, max_iter=200000)
+                          level_tol=level_tol, oversample=10, eig_tol=1e-2, eig_max_iter=100,
+                          max_iter=200000)
     assert res["return_status"] == pkg.EOT_OK, res
     ev = O.evaluate(f, g, C, prob.a, prob.b, prob.eps)
     print(f"ell={ell}: oracle L1 {ev['l1']:.3e} (row {ev['row_l1']:.2e}, col {ev['col_l1']:.2e}),"
