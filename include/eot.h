@@ -109,6 +109,13 @@ typedef struct {
                                gang barriers of eot_solve_batch); a wait that exceeds it
                                gives up and the solve returns EOT_ETIMEDOUT (the device
                                stays usable).  <= 0 or not finite: 30 s               */
+    int32_t stall_window;   /* iterations between stall checkpoints of a level: when the
+                               L1 marginal error has not fallen below 0.99 times its
+                               value at the previous checkpoint the level stops (float32
+                               rounding floors the error); the solve then returns
+                               EOT_OK if the returned pair meets tol, else
+                               EOT_NOT_CONVERGED, with eot_result.stalled = 1.
+                               0: no check.  Default 1000.                            */
 } eot_options;
 
 typedef struct {
@@ -130,6 +137,7 @@ typedef struct {
     int64_t device_t_begin_ns, device_t_end_ns; /* the device clock (globaltimer, ns) at
                                the solve's first and last kernel: solves whose
                                intervals intersect ran on the device at once         */
+    int32_t stalled;        /* 1: the final level stopped on the stall check           */
 } eot_result;
 
 /* Fill *opt with defaults: tol 1e-6, max_iter 100000, ell 0, single level,
@@ -270,6 +278,9 @@ typedef struct {
     int32_t newton_ok;  /* 0: -H_V not positive definite (or the products saw
                            exponentials out of range): no trial, the step is rejected */
     int32_t accepted;   /* 1: dq > 0, (f', h') is the next iterate; 0: (f_k, h) is     */
+    int32_t products_in_range; /* 0: the S4 pass saw a column whose largest term lies
+                           more than 2^60 from 1 (W would lose range): the step is
+                           then skipped, newton_ok = 0                              */
     double stage_seconds[4]; /* device time (CUDA events on the call's stream) of the
                            row half-step that forms f_k, the S4 pass (h, W, test),
                            the Newton solve (W^T D_b^-1 W reduction, factorisation,

@@ -332,8 +332,7 @@ __global__ void __launch_bounds__(kThreads) colacc_kernel(AccArgs args) {
     st->iter += 1;
     st->nr_ok = 0;
     if (st->numeric > 0) st->done = 3;
-    else if (tot[0] < st->tol) st->done = 1;
-    else if (st->iter >= st->max_iter) st->done = 2;
+    else st->done = stop_code(st, tot[0], st->iter, st->tol, st->max_iter, P.stall_window);
   }
 }
 

@@ -970,6 +970,7 @@ static eot_status validate(const eot_problem* pr, const eot_options* o) {
   if (o->ell > 0 && pr->n < 3) return fail(EOT_EINVAL, "SK-NR needs n >= 3");
   if (o->ell > 0 && o->ell + 1 > kMaxP) return fail(EOT_EINVAL, "ell must be <= 47");
   if (o->oversample < 0) return fail(EOT_EINVAL, "oversample must be >= 0");
+  if (o->stall_window < 0) return fail(EOT_EINVAL, "stall_window must be >= 0");
   if ((long long)pr->n * pr->m > (1ll << 34)) return fail(EOT_EINVAL, "n*m too large");
   return EOT_OK;
 }
@@ -1137,6 +1138,7 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   P.M = (float)(1.5 * std::ldexp(1.0, 23 - q));
   P.pot_bound = gram ? 1e300 : std::ldexp(1.0, 22 - q) / 2.0 - cmax;
   P.wait_ns = wait_ns(o);
+  P.stall_window = o->stall_window;
   P.eps = eps0;
   P.k2 = (float)(1.0 / (eps0 * std::log(2.0)));
   P.k2lo = (float)(1.0 / (eps0 * std::log(2.0)) - (double)P.k2);
@@ -1382,7 +1384,9 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   else if (fin.done == 2) status = EOT_NOT_CONVERGED;
   else if (fin.done == 3) status = EOT_ENUMERIC;
   else if (fin.done == 4 || fin.done == 5) status = EOT_ETIMEDOUT;
+  else if (fin.done == 6) status = r.l1_marginal < o->tol ? EOT_OK : EOT_NOT_CONVERGED;
   else status = EOT_NOT_CONVERGED;
+  r.stalled = fin.done == 6 ? 1 : 0;
   bool wait_gave_up = fin.done == 5;
   for (int t = 0; t < L - 1 && status == EOT_OK; ++t) {
     if (hLev[t].done == 3) status = EOT_ENUMERIC;
@@ -1406,7 +1410,9 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   // arrival counters reset only when a pass completes): drop this solver so
   // that the next solve of the shape starts from a fresh, zeroed arena
   if (wait_gave_up) evict_solver(S);
-  if (status == EOT_NOT_CONVERGED) t_err = "max_iter reached";
+  if (status == EOT_NOT_CONVERGED)
+    t_err = fin.done == 6 ? "the L1 marginal error stalled above tol (stall_window)"
+                          : "max_iter reached";
   return status;
 }
 
@@ -1878,6 +1884,7 @@ static eot_status run_batch(int count, const eot_problem* probs, const eot_optio
     T.g_out = p.trans ? L.fo : L.go;
     T.bar = L.bar;
     T.wait_ns = wait_ns(&o);
+    T.stall_window = o.stall_window;
     T.flag = L.flag;
     T.out = d_out + k;
     T.tol_level = o.level_tol > 0.0 ? o.level_tol : o.tol;
@@ -1976,9 +1983,14 @@ static eot_status run_batch(int count, const eot_problem* probs, const eot_optio
     r.kernel_launches = 5;   // weights, cost max, cost fill, persistent kernel (+ counter)
     r.device_t_begin_ns = (int64_t)b.t_begin;
     r.device_t_end_ns = (int64_t)b.t_end;
+    r.stalled = b.status == 6 ? 1 : 0;
     switch (b.status) {
       case 1: r.status = EOT_OK; break;
       case 2: r.status = EOT_NOT_CONVERGED; errs[k] = "max_iter reached"; break;
+      case 6:
+        r.status = r.l1_marginal < o.tol ? EOT_OK : EOT_NOT_CONVERGED;
+        if (r.status != EOT_OK) errs[k] = "the L1 marginal error stalled above tol (stall_window)";
+        break;
       case 3: r.status = EOT_ENUMERIC; errs[k] = "non-finite values or potentials outside the exact range"; break;
       default: r.status = EOT_ETIMEDOUT; errs[k] = "batch gang wait gave up"; break;
     }
@@ -2014,6 +2026,7 @@ void eot_default_options(eot_options* o) {
   o->poll_every = 0;
   o->stream = nullptr;
   o->wait_limit_s = 30.0;
+  o->stall_window = 1000;
 }
 
 eot_status eot_solve(const eot_problem* prob, const eot_options* opt, double* f_out,
@@ -2457,6 +2470,9 @@ eot_status eot_sknr_step(int32_t n, int32_t m, int32_t ell, const float* C, cons
   // the kernels of one SK-NR loop body
   const AccArgs acc = S->s4_args();
   CUDA_TRY(launch_colmma(acc, P, S->tilesV, S->mm_ncolblk, s));
+  // the S4 pass's range flag, before the Newton kernel consumes it
+  CUDA_TRY(cudaMemcpyAsync(S->stats + 6, &S->dSt->nr_degenerate, sizeof(int),
+                           cudaMemcpyDeviceToDevice, s));
   CUDA_TRY(cudaEventRecord(ev[2], s));
   CUDA_TRY(launch_newton(S->dP, acc, S->WtW, S->gw, s));
   fprime_kernel<<<std::min(ceil_div(n, 256), 4 * S->ctx->nsm), 256, 0, s>>>(S->dP);
@@ -2478,6 +2494,8 @@ eot_status eot_sknr_step(int32_t n, int32_t m, int32_t ell, const float* C, cons
   const State hs = *S->hSt;
   if (hs.numeric > 0 || hs.done == 3)
     return fail(EOT_ENUMERIC, "non-finite values or potentials outside the exact range");
+  int degenerate = 0;
+  CUDA_TRY(cudaMemcpy(&degenerate, S->stats + 6, sizeof(int), cudaMemcpyDeviceToHost));
   if (hs.nr_ok) {
     if (f_trial) CUDA_TRY(cudaMemcpy(f_trial, P.f[1], n * sizeof(double), dd));
     if (h_trial) CUDA_TRY(cudaMemcpy(h_trial, P.g[2], m * sizeof(double), dd));
@@ -2488,6 +2506,7 @@ eot_status eot_sknr_step(int32_t n, int32_t m, int32_t ell, const float* C, cons
     info->dq = hs.nr_ok ? hs.dq : 0.0;
     info->newton_ok = hs.nr_ok;
     info->accepted = hs.nr_ok && hs.nr_acc > 0 ? 1 : 0;
+    info->products_in_range = degenerate ? 0 : 1;
     for (int k = 0; k < 4; ++k) {
       float ms = 0.f;
       cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);

@@ -549,6 +549,10 @@ __device__ void brun_task(const BatchTask& T, int rank, BShared& sh) {
     gi ^= 1;
     double tol = last ? T.tol_last : T.tol_level;
     iter = 0;
+    // the stall check of stop_code, in local state (every CTA of the gang
+    // computes the same l1 and takes the same decision)
+    double stall_l1 = 1e300;
+    int stall_at = T.stall_window;
     for (;;) {
       brow_pass(T, r0, r1, gi, eps, k2, k2lo, false, sh);   // f_k = g_k^{C,eps}
       if (!sync()) break;
@@ -585,6 +589,15 @@ __device__ void brun_task(const BatchTask& T, int rank, BShared& sh) {
       if (iter >= T.max_iter) {
         status = 2;
         break;
+      }
+      if (T.stall_window > 0 && iter >= stall_at) {
+        const bool stalled = !(l1 < 0.99 * stall_l1);
+        stall_l1 = l1;
+        stall_at = iter + T.stall_window;
+        if (stalled) {   // an intermediate level goes on to the next eps
+          if (last) status = 6;
+          break;
+        }
       }
       gi ^= 1;   // commit g_{k+1} = f_k^{C,eps}
     }

@@ -14,7 +14,8 @@ constexpr double kBCostPerCta = 1.25 * 1024 * 1024;   // floor of the gang sizes
 constexpr unsigned long long kWaitNsDefault = 30000000000ull;   // 30 s bound of a device wait
 
 struct BatchOut {
-  int status;        // 1 converged, 2 iteration cap, 3 numeric, 4 gang wait gave up
+  int status;        // 1 converged, 2 iteration cap, 3 numeric, 4 gang wait gave up,
+                     // 6 the last level's L1 error stalled
   int iters, total_iters, levels, verify_rounds, pad;
   double row_l1, col_l1, q_dual, q_semi, dual_gap, gauge;
   unsigned long long t_begin, t_end, t_last_level;
@@ -34,6 +35,7 @@ struct BatchTask {
   double *f_out, *g_out;
   unsigned* bar;                  // [2]: arrivals, generation
   unsigned long long wait_ns;     // bound of a gang-barrier wait (globaltimer ns)
+  int stall_window;               // iterations between stall checkpoints (0: none)
   unsigned* flag;                 // numeric flag of the problem (0 / 1)
   BatchOut* out;
   double tol_level, tol_last, tol_verify;

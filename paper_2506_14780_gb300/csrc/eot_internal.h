@@ -33,7 +33,8 @@ enum PassMode : int {
 struct State {
   int iter;        // Algorithm 4.1 iterations done at the current level
   int done;        // 0 running, 1 converged, 2 max_iter, 3 numeric error,
-                   // 4 loop body cap, 5 a grid-barrier wait gave up
+                   // 4 loop body cap, 5 a grid-barrier wait gave up,
+                   // 6 the L1 error stalled (see stop_code)
   int cur_f;       // index of the current f buffer (0/1)
   int cur_g;       // index of the current g buffer (0..2)
   int nr_acc, nr_rej;
@@ -56,6 +57,8 @@ struct State {
   double eig_tol, eig_resid;
   int total_iters;
   int nr_degenerate;   // set when the SK-NR products saw exponentials out of range
+  double stall_l1;     // L1 error at the last stall checkpoint of this level
+  int stall_at;        // iteration of the next stall checkpoint
 };
 
 // Split arrays of one potential buffer (see eot_device.cuh).
@@ -118,6 +121,7 @@ struct Prob {
   double* sk_acc_row;      // [ceil(n/32)][4]
   unsigned* gbar;          // [2] grid barrier of the cooperative Sinkhorn loop
   unsigned long long wait_ns;   // bound of a grid-barrier wait (globaltimer ns)
+  int stall_window;        // iterations between stall checkpoints (0: none)
   // on-the-fly cost (EOT_PREC_SPLIT_TC): C_ij = |x_i|^2 + |y_j|^2 - 2 x_i.y_j
   // with the Gram products on the tensor cores (3xTF32, float32 accumulation)
   int gram;                // 1 in that mode
@@ -174,5 +178,28 @@ struct AccArgs {
   double* wtw_part;      // [nblk][k*k + k] block partials (SK-NR)
   int cluster;           // staged kernel: merge a block's segments in a cluster (nseg <= 8)
 };
+
+#ifdef __CUDACC__
+// Stop test of Algorithm 4.1 after iteration `iter` of a level with L1 marginal
+// error l1 (one thread): 1 converged (l1 < tol), 2 iteration cap, 6 stalled,
+// 0 go on.  Every `window` iterations l1 is compared with its value at the
+// previous checkpoint; when it has not fallen below kStallRatio times that
+// value the level stops (the float32 passes floor the error, and a level that
+// gains less than 1% per window would need far more than any iteration cap
+// to gain a decade).  window 0 turns the check off.
+constexpr double kStallRatio = 0.99;
+__device__ inline int stop_code(State* st, double l1, int iter, double tol, int max_iter,
+                                int window) {
+  if (l1 < tol) return 1;
+  if (iter >= max_iter) return 2;
+  if (window > 0 && iter >= st->stall_at) {
+    const bool stalled = !(l1 < kStallRatio * st->stall_l1);
+    st->stall_l1 = l1;
+    st->stall_at = iter + window;
+    if (stalled) return 6;
+  }
+  return 0;
+}
+#endif
 
 }  // namespace eotk

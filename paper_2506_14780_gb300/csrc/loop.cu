@@ -50,6 +50,8 @@ __global__ void level_setup_kernel(Prob* P, double eps, float k2, double tol, in
   st->numeric = 0;
   st->body_runs = 0;
   st->body_cap = body_cap;
+  st->stall_l1 = 1e300;
+  st->stall_at = P->stall_window;
 }
 
 __global__ void eig_setup_kernel(State* st, double tol, int max_iter, int body_cap) {

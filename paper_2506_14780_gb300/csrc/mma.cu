@@ -33,6 +33,7 @@ constexpr int kMmaM = 128;      // columns per CTA
 constexpr int kMmaKC = 32;      // rows per chunk
 constexpr int kMmaWait = 1 << 22;
 constexpr int kMmaMaxCluster = 8;   // segments per output block merged in one cluster
+constexpr double kNrRangeLn = 60.0 * 0.6931471805599453;   // |ln column sum| bound for the products
 
 // Swizzled tiles of Z^T: for chunk c of 32 rows, tile (c, part) holds NN rows
 // (the k index, padded with zeros) of 32 floats (the chunk's rows of Z), part 0
@@ -97,6 +98,13 @@ __device__ __noinline__ void colmma_finish(const AccArgs& args, const Prob& P, u
       sD[c] = 0.f;
       if (jv) {
         double Ld = (double)R * 0.6931471805599453 + (double)log_sum(Stot);
+        // The products hold the terms at their absolute scale 2^{y_ij}.  The
+        // column's sum 2^R Stot lies between its largest term and n times it,
+        // so a sum within 2^{+-60} keeps every term that matters inside the
+        // float32 range; otherwise the Newton step is skipped.  (R itself is
+        // the log-sum-exp reference, which may sit up to 64 below the largest
+        // term, and says nothing about the range.)
+        if (!(fabs(Ld) <= kNrRangeLn)) atomicOr(&st->nr_degenerate, 1);
         const double sh = P.g[gb][j];
         double o = sh - P.eps * Ld;
         if (!isfinite(o) || !(Stot > 0.0) || fabs(o) > P.pot_bound) {
@@ -105,9 +113,6 @@ __device__ __noinline__ void colmma_finish(const AccArgs& args, const Prob& P, u
           Ld = 0.0;
         }
         const float L = (float)Ld;
-        // the products need the exponentials in range: flag a column whose
-        // largest term lies far from 1 (the Newton step is then skipped)
-        if (R > 60.f || R < -60.f) atomicOr(&st->nr_degenerate, 1);
         P.g[dst_g][j] = o;
         P.Lcol[j] = L;
         double hi;
@@ -244,8 +249,7 @@ __device__ __noinline__ void colmma_finish(const AccArgs& args, const Prob& P, u
     st->iter += 1;
     st->nr_ok = 0;
     if (st->numeric > 0) st->done = 3;
-    else if (tot[0] < st->tol) st->done = 1;
-    else if (st->iter >= st->max_iter) st->done = 2;
+    else st->done = stop_code(st, tot[0], st->iter, st->tol, st->max_iter, P.stall_window);
   }
 }
 
@@ -320,6 +324,13 @@ __device__ __noinline__ void cluster_finish(const AccArgs& args, const Prob& P,
       sD[tid] = 0.f;
       if (jv) {
         double Ld = (double)R * 0.6931471805599453 + (double)log_sum(Stot);
+        // The products hold the terms at their absolute scale 2^{y_ij}.  The
+        // column's sum 2^R Stot lies between its largest term and n times it,
+        // so a sum within 2^{+-60} keeps every term that matters inside the
+        // float32 range; otherwise the Newton step is skipped.  (R itself is
+        // the log-sum-exp reference, which may sit up to 64 below the largest
+        // term, and says nothing about the range.)
+        if (!(fabs(Ld) <= kNrRangeLn)) atomicOr(&st->nr_degenerate, 1);
         const double sh = P.g[gb][j];
         double o = sh - P.eps * Ld;
         if (!isfinite(o) || !(Stot > 0.0) || fabs(o) > P.pot_bound) {
@@ -328,9 +339,6 @@ __device__ __noinline__ void cluster_finish(const AccArgs& args, const Prob& P,
           Ld = 0.0;
         }
         const float L = (float)Ld;
-        // the products need the exponentials in range: flag a column whose
-        // largest term lies far from 1 (the Newton step is then skipped)
-        if (R > 60.f || R < -60.f) atomicOr(&st->nr_degenerate, 1);
         P.g[dst_g][j] = o;
         P.Lcol[j] = L;
         double hi;
@@ -462,8 +470,7 @@ __device__ __noinline__ void cluster_finish(const AccArgs& args, const Prob& P,
         st->iter += 1;
         st->nr_ok = 0;
         if (st->numeric > 0) st->done = 3;
-        else if (tot[0] < st->tol) st->done = 1;
-        else if (st->iter >= st->max_iter) st->done = 2;
+        else st->done = stop_code(st, tot[0], st->iter, st->tol, st->max_iter, P.stall_window);
       }
     }
   }

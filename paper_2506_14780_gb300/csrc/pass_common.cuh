@@ -113,9 +113,8 @@ __device__ inline void final_step(const Prob& P, int mode, const double t[3], in
       st->l1_col = t[0];
       st->qsemi = st->sum_af + t[2];   // Q_semi(f_k) = <f_k, a> + <f_k^{C,eps}, b>
       st->iter += 1;
-      if (t[0] < st->tol) st->done = 1;
-      else if (st->iter >= st->max_iter) st->done = 2;
-      else st->cur_g = dst;
+      st->done = stop_code(st, t[0], st->iter, st->tol, st->max_iter, P.stall_window);
+      if (!st->done) st->cur_g = dst;
       break;
     case MODE_EVAL:
       st->l1_col = t[0];

@@ -748,8 +748,7 @@ __global__ void __launch_bounds__(kStThreads, 2)
         if ((threadIdx.x & 31) == 0) {
           const int numeric = *(volatile int*)&st->numeric;
           if (numeric > 0) done = 3;
-          else if (tot[0] < tol) done = 1;
-          else if (iter >= max_iter) done = 2;
+          else done = stop_code(st, tot[0], iter, tol, max_iter, P.stall_window);
           st->l1_col = tot[0];
           st->qsemi = st->sum_af + tot[2];   // Q_semi(f_k) = <f_k, a> + <f_k^{C,eps}, b>
           st->sum_wL = tot[1];

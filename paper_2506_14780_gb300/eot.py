@@ -42,7 +42,7 @@ class eot_options(C.Structure):
                 ("sequential_modes", C.c_int32), ("oversample", C.c_int32),
                 ("eig_tol", C.c_double), ("eig_max_iter", C.c_int32), ("prec", C.c_int32),
                 ("hessian", C.c_int32), ("poll_every", C.c_int32), ("stream", C.c_void_p),
-                ("wait_limit_s", C.c_double)]
+                ("wait_limit_s", C.c_double), ("stall_window", C.c_int32)]
 
 
 class eot_result(C.Structure):
@@ -52,7 +52,8 @@ class eot_result(C.Structure):
                 ("col_l1", C.c_double), ("q_dual", C.c_double), ("q_semi", C.c_double),
                 ("dual_gap", C.c_double), ("seconds", C.c_double), ("seconds_eig", C.c_double),
                 ("seconds_last_level", C.c_double), ("kernel_launches", C.c_int64),
-                ("device_t_begin_ns", C.c_int64), ("device_t_end_ns", C.c_int64)]
+                ("device_t_begin_ns", C.c_int64), ("device_t_end_ns", C.c_int64),
+                ("stalled", C.c_int32)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -63,6 +64,7 @@ class eot_result(C.Structure):
 class eot_sknr_info(C.Structure):
     _fields_ = [("col_l1", C.c_double), ("q_semi", C.c_double), ("dq", C.c_double),
                 ("newton_ok", C.c_int32), ("accepted", C.c_int32),
+                ("products_in_range", C.c_int32),
                 ("stage_seconds", C.c_double * 4)]
 
 
