@@ -111,10 +111,11 @@ typedef struct {
                                stays usable).  <= 0 or not finite: 30 s               */
     int32_t stall_window;   /* iterations between stall checkpoints of a level: when the
                                L1 marginal error has not fallen below 0.99 times its
-                               value at the previous checkpoint the level stops (float32
-                               rounding floors the error); the solve then returns
-                               EOT_OK if the returned pair meets tol, else
-                               EOT_NOT_CONVERGED, with eot_result.stalled = 1.
+                               value at the previous checkpoint the level stops (the
+                               error has reached the float32 rounding floor, or falls
+                               so slowly that a decade would take > 200 windows); the
+                               solve then returns EOT_OK if the returned pair meets
+                               tol, else EOT_NOT_CONVERGED, with eot_result.stalled = 1.
                                0: no check.  Default 1000.                            */
 } eot_options;
 

@@ -1,47 +1,24 @@
-// Passes that accumulate a block of k vectors weighted by the coupling:
+// Row-direction product on the CUDA cores, for costs without a tensor map (a
+// row pitch that is not a multiple of 16 bytes):
 //
-//  * Op(pi)^T Z (column direction, Eq. def_Op_pi_T):
-//        out_j = sum_i exp((f_i + g_j - C_ij)/eps) a_i Z_i          (Z: n x k)
-//  * Op(pi) Z (row direction, Eq. def_Op_pi):
+//  * Op(pi) Z (Eq. def_Op_pi):
 //        out_i = sum_j exp((f_i + g_j - C_ij)/eps) b_j Z_j          (Z: m x k)
-//  * the fused SK-NR column pass at f_k (Algorithm 4.1, value / gradient /
-//    Hessian on V_l): with h = f_k^{C,eps} (the column transform, computed in
-//    the same pass as a log-sum-exp),
-//        W_j = sum_i pi(f_k, h)_ij V_i = b_j * softmax_i(x_ij) . V,
-//    the semi-dual coupling of Eq. (dQ_semi) applied to the modes; plus the
-//    marginal test of the iteration, the new column potential h, the gradient
-//    weights d_j = 1 - exp((g_j - h_j)/eps) and, per block of 32 columns, the
-//    partial sums of W_j W_j^T / b_j and d_j W_j (Eq. d2Q_semi, dQ_semi on V).
 //
-// Exponents are formed exactly as in the Sinkhorn passes (eot_device.cuh).
-// Column direction: one thread per column (warp = 32 consecutive columns, one
-// 128-byte line per row), 8 warps interleaved over a segment of rows; the
-// segment is walked in chunks of 64 rows whose rows of Z are staged in shared
-// memory (double buffered) while the next chunk's cost entries and Z rows are
-// already in flight.  Row direction: a warp owns one or two rows, lanes stride
-// along the columns, chunks of 128 columns of Z are staged in shared memory
-// (double buffered, conflict-free padding) and shared by the CTA's warps.
-// Partial (reference, sum, k accumulators) per segment are merged in parallel
-// and in fixed order by the last-arriving CTA of each index block.
+// Exponents are formed exactly as in the Sinkhorn passes (eot_device.cuh).  A
+// warp owns one or two rows, lanes stride along the columns, chunks of 128
+// columns of Z are staged in shared memory (double buffered, conflict-free
+// padding) and shared by the CTA's warps.  Partial (reference, sum, k
+// accumulators) per segment are merged in parallel and in fixed order by the
+// last-arriving CTA of each row block.  Also here: the reduction of the SK-NR
+// column pass's per-block partials of W^T D_b^{-1} W and d^T W (Eq. d2Q_semi,
+// dQ_semi on V), whose column pass itself runs on the tensor cores (mma.cu).
 #include "eot_device.cuh"
 #include "eot_internal.h"
 #include "reduce.cuh"
 
 namespace eotk {
 
-enum AccMode : int { ACC_KCOL = 0, ACC_S4 = 1, ACC_KROW = 2 };
-
-constexpr int kCH = 64;   // rows per chunk (column direction)
 constexpr int kCC = 128;  // columns per chunk (row direction)
-
-template <int K>
-struct ColAccSmem {
-  static constexpr int KS = K + 4;
-  static constexpr size_t tiles = (size_t)2 * (kCH * KS + 2 * kCH) * 4;
-  static constexpr size_t red = (size_t)8 * 32 * (K + 2) * 4;
-  static constexpr size_t extra = (size_t)32 * (K + 1) * 4 + 32 * 8 * 2;
-  static constexpr size_t bytes = (tiles > red ? tiles : red) + extra;
-};
 
 template <int K>
 struct RowAccSmem {
@@ -51,290 +28,6 @@ struct RowAccSmem {
   static constexpr size_t red = (size_t)8 * 32 * (RW * (K + 2) + 1) * 4;
   static constexpr size_t bytes = tiles > red ? tiles : red;
 };
-
-// ---------------------------------------------------------------------------
-// Column direction (K-apply col, S4).
-// ---------------------------------------------------------------------------
-template <int K>
-__global__ void __launch_bounds__(kThreads) colacc_kernel(AccArgs args) {
-  const Prob& P = *args.P;
-  State* st = P.st;
-  const bool s4 = args.mode == ACC_S4;
-  if (s4 && st->done) return;
-  const int fb = s4 ? st->cur_f : args.fbuf;
-  const int gb = s4 ? st->cur_g : args.gbuf;
-  const int dst_g = (st->cur_g + 1) % 3;
-  const float* __restrict__ rA = P.rs[fb].A;
-  const float* __restrict__ rAL = P.rs[fb].AL;
-  const float* __restrict__ cK = P.cs[gb].K;
-  const float* __restrict__ cKL = P.cs[gb].KL;
-  using SM = ColAccSmem<K>;
-  constexpr int KS = SM::KS;
-  constexpr int VPT = (kCH * K) / kThreads;   // staged Z values per thread per chunk
-
-  extern __shared__ __align__(16) float smem[];
-  float* sZ = smem;                                     // [2][kCH][KS]
-  float2* sRow = reinterpret_cast<float2*>(smem + 2 * kCH * KS);   // [2][kCH]
-  float* sRed = smem;                                   // reused after the loop
-  float* sW = smem + (SM::tiles > SM::red ? SM::tiles : SM::red) / 4;   // [32][K+1]
-  double* sD = reinterpret_cast<double*>(sW + 32 * (K + 1));          // [32] d_j
-  double* sB = sD + 32;                                               // [32] 1/b_j
-  __shared__ double s_red[24];
-  __shared__ unsigned s_last;
-
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int n = P.n, m = P.m, kk = args.k;
-  const int cb = blockIdx.x, seg = blockIdx.y;
-  const int j = cb * 32 + lane;
-  const bool jv = j < m;
-  const int i_beg = seg * args.seg_len;
-  const int i_end = min(n, i_beg + args.seg_len);
-  const int nchunks = (i_end - i_beg + kCH - 1) / kCH;
-  const float k2 = P.k2;
-  const float Kj = jv ? cK[j] : P.M;
-  const float cc0 = jv ? cKL[j] * k2 : 0.f;
-  float cc = cc0;
-  float ref = 0.f, run = -INFINITY, S = 0.f;
-  float acc[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) acc[k] = 0.f;
-
-  float zn[VPT];
-  float2 rn = make_float2(0.f, 0.f);
-  float cn[8];
-  auto fetch = [&](int ch) {
-    const int base = i_beg + ch * kCH;
-    const int nr = min(kCH, i_end - base);
-#pragma unroll
-    for (int q = 0; q < VPT; ++q) {
-      const int t = threadIdx.x + q * kThreads;
-      const int r = t / K, k = t - r * K;
-      zn[q] = (r < nr && k < kk) ? __ldg(args.Z + (size_t)(base + r) * kk + k) : 0.f;
-    }
-    if ((int)threadIdx.x < nr) rn = make_float2(__ldg(rA + base + threadIdx.x), __ldg(rAL + base + threadIdx.x));
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int r = wid + 8 * u;
-      cn[u] = (jv && r < nr) ? __ldg(P.C + (size_t)(base + r) * m + j) : 0.f;
-    }
-  };
-  auto publish = [&](int buf) {
-#pragma unroll
-    for (int q = 0; q < VPT; ++q) {
-      const int t = threadIdx.x + q * kThreads;
-      const int r = t / K, k = t - r * K;
-      sZ[(buf * kCH + r) * KS + k] = zn[q];
-    }
-    if ((int)threadIdx.x < kCH) sRow[buf * kCH + threadIdx.x] = rn;
-  };
-  if (nchunks > 0) {
-    fetch(0);
-    publish(0);
-  }
-  __syncthreads();
-  for (int ch = 0; ch < nchunks; ++ch) {
-    const int buf = ch & 1;
-    const int nr = min(kCH, i_end - (i_beg + ch * kCH));
-    float cv[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) cv[u] = cn[u];
-    if (ch + 1 < nchunks) fetch(ch + 1);
-    if (jv) {
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int r = wid + 8 * u;
-        if (r < nr) {
-          const float2 ra = sRow[buf * kCH + r];
-          const float t = __fadd_rn(split_exponent(cv[u], Kj, ra.x), ra.y);
-          float y = __fmaf_rn(t, k2, cc);
-          if (y > run) {
-            run = y;
-            if (run > kRecenter || (run < -kRecenter && run > -INFINITY)) {
-              const float d = rintf(run);
-              S = scale2(S, -d);
-#pragma unroll
-              for (int k = 0; k < K; ++k) acc[k] = scale2(acc[k], -d);
-              ref += d;
-              cc = __fsub_rn(cc0, ref);
-              run -= d;
-              y = __fmaf_rn(t, k2, cc);
-            }
-          }
-          const float e = ex2_approx(y);
-          S += e;
-          const float4* z4 = reinterpret_cast<const float4*>(sZ + (buf * kCH + r) * KS);
-#pragma unroll
-          for (int k4 = 0; k4 < K / 4; ++k4) {
-            const float4 z = z4[k4];
-            acc[4 * k4 + 0] = __fmaf_rn(e, z.x, acc[4 * k4 + 0]);
-            acc[4 * k4 + 1] = __fmaf_rn(e, z.y, acc[4 * k4 + 1]);
-            acc[4 * k4 + 2] = __fmaf_rn(e, z.z, acc[4 * k4 + 2]);
-            acc[4 * k4 + 3] = __fmaf_rn(e, z.w, acc[4 * k4 + 3]);
-          }
-        }
-      }
-    }
-    if (ch + 1 < nchunks) publish(buf ^ 1);
-    __syncthreads();
-  }
-  // intra-CTA combine over the 8 warps: rescale to the CTA maximum reference
-  {
-    float* my = sRed + (wid * 32 + lane) * (K + 2);
-    my[0] = (S > 0.f) ? ref : -INFINITY;
-    my[1] = S;
-#pragma unroll
-    for (int k = 0; k < K; ++k) my[2 + k] = acc[k];
-  }
-  __syncthreads();
-  {
-    const int col = threadIdx.x & 31, sl = threadIdx.x >> 5;
-    float R = -INFINITY;
-    for (int w = 0; w < 8; ++w) R = fmaxf(R, sRed[(w * 32 + col) * (K + 2)]);
-    const int jj = cb * 32 + col;
-    for (int e = sl; e < K + 2; e += 8) {
-      float v = 0.f;
-      if (e == 0) {
-        v = R;
-      } else {
-        for (int w = 0; w < 8; ++w) {
-          const float* src = sRed + (w * 32 + col) * (K + 2);
-          const float rw = src[0];
-          if (rw == -INFINITY) continue;
-          v += (rw == R) ? src[e] : scale2(src[e], rw - R);
-        }
-      }
-      if (jj < m) args.part[((size_t)seg * m + jj) * (K + 2) + e] = v;
-    }
-  }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned prev = atomicAdd(&args.cnt[cb], 1u);
-    s_last = (prev == (unsigned)(args.nseg - 1));
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  // --- combine the segments of the 32 columns of this block ---
-  double accv[3] = {0.0, 0.0, 0.0};
-  {
-    const int col = threadIdx.x & 31, sl = threadIdx.x >> 5;
-    const int jj = cb * 32 + col;
-    if (jj < m) {
-      float R = -INFINITY;
-      double Stot = 0.0;
-      merge_segments_k(args.part, args.nseg, m, K + 2, jj, R, Stot);
-      float scale;
-      if (s4) scale = (float)(P.b[jj] / Stot);          // b_j * softmax normalisation
-      else scale = scale2(1.f, R);                       // un-normalised product
-      for (int k = sl; k < kk; k += 8) {
-        float v = 0.f;
-        for (int s0 = 0; s0 < args.nseg; s0 += 4) {
-          float pr[4], pv[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int s = s0 + q;
-            const float* src = args.part + ((size_t)s * m + jj) * (K + 2);
-            pr[q] = s < args.nseg ? __ldcg(src) : -INFINITY;
-            pv[q] = s < args.nseg ? __ldcg(src + 2 + k) : 0.f;
-          }
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-            if (pr[q] > -INFINITY) v += (pr[q] == R) ? pv[q] : scale2(pv[q], pr[q] - R);
-        }
-        const float wv = v * scale;
-        args.out[(size_t)jj * kk + k] = wv;
-        if (s4) sW[col * (K + 1) + k] = wv;
-      }
-      if (s4 && sl == 0) {
-        // column transform h and the marginal test, as in the Sinkhorn column pass
-        double Ld = (double)R * 0.6931471805599453 + (double)log_sum(Stot);
-        const double sh = P.g[gb][jj];
-        double o = sh - P.eps * Ld;
-        if (!isfinite(o) || !(Stot > 0.0) || fabs(o) > P.pot_bound) {
-          atomicAdd(&st->numeric, 1);
-          o = sh;
-          Ld = 0.0;
-        }
-        const float L = (float)Ld;
-        P.g[dst_g][jj] = o;
-        P.Lcol[jj] = L;
-        double hi;
-        float lo;
-        split_grid(o + P.eps * P.logb[jj], P.qscale, P.qinv, hi, lo);
-        P.cs[dst_g].A[jj] = (float)(hi + (double)P.M);
-        P.cs[dst_g].AL[jj] = lo;
-        split_grid(o, P.qscale, P.qinv, hi, lo);
-        P.cs[dst_g].K[jj] = (float)((double)P.M - hi);
-        P.cs[dst_g].KL[jj] = lo;
-        const double wj = P.b[jj];
-        const double dj = -(double)expm1f(L);     // 1 - exp((g_j - h_j)/eps)
-        args.dw[jj] = dj;
-        sD[col] = dj;
-        sB[col] = 1.0 / wj;
-        accv[0] = wj * (double)fabsf(expm1f(L));
-        accv[1] = wj * Ld;
-        accv[2] = wj * o;
-      }
-    } else if (s4) {
-      for (int k = sl; k < kk; k += 8) sW[col * (K + 1) + k] = 0.f;
-      if (sl == 0) {
-        sD[col] = 0.0;
-        sB[col] = 0.0;
-      }
-    }
-  }
-  if (!s4) {
-    if (threadIdx.x == 0) args.cnt[cb] = 0u;
-    return;
-  }
-  __syncthreads();
-  // block partials of W^T D_b^{-1} W (kk x kk) and of sum_j d_j W_j (kk)
-  {
-    double* dst = args.wtw_part + (size_t)cb * (kk * kk + kk);
-    for (int e = threadIdx.x; e < kk * kk + kk; e += kThreads) {
-      double s = 0.0;
-      if (e < kk * kk) {
-        const int r = e / kk, c = e - r * kk;
-        for (int q = 0; q < 32; ++q)
-          s += (double)(sW[q * (K + 1) + r] * sW[q * (K + 1) + c]) * sB[q];
-      } else {
-        const int r = e - kk * kk;
-        for (int q = 0; q < 32; ++q) s += sD[q] * (double)sW[q * (K + 1) + r];
-      }
-      dst[e] = s;
-    }
-  }
-  // block sums and the grid-final step
-  {
-    double v0 = warp_sum_d(accv[0]), v1 = warp_sum_d(accv[1]), v2 = warp_sum_d(accv[2]);
-    if (threadIdx.x == 0) {
-      args.cnt[cb] = 0u;
-      double* ab = args.blkacc + cb * 4;
-      ab[0] = v0;
-      ab[1] = v1;
-      ab[2] = v2;
-      __threadfence();
-      const unsigned prev = atomicAdd(args.gcnt, 1u);
-      s_last = (prev == (unsigned)(args.nblk - 1));
-    }
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  double tot[3];
-  grid_sum3(args.blkacc, args.nblk, tot, s_red);
-  if (threadIdx.x == 0) {
-    *args.gcnt = 0u;
-    st->l1_col = tot[0];
-    st->sum_wL = tot[1];
-    st->qsemi = st->sum_af + tot[2];   // Q_semi(f_k) = <f_k, a> + <h, b>
-    st->iter += 1;
-    st->nr_ok = 0;
-    if (st->numeric > 0) st->done = 3;
-    else st->done = stop_code(st, tot[0], st->iter, st->tol, st->max_iter, P.stall_window);
-  }
-}
 
 // Sum of the per-block partials of W^T D_b^{-1} W and sum_j d_j W_j: a CTA owns
 // 32 entries, its 8 warps take interleaved blocks, the warps' sums are added in
@@ -578,13 +271,6 @@ __global__ void __launch_bounds__(kThreads) rowacc_kernel(AccArgs args) {
 
 // ---------------------------------------------------------------------------
 template <int K>
-static cudaError_t launch_colacc_k(const AccArgs& a, int ncolblk, cudaStream_t s) {
-  dim3 grid(ncolblk, a.nseg);
-  colacc_kernel<K><<<grid, kThreads, ColAccSmem<K>::bytes, s>>>(a);
-  return cudaGetLastError();
-}
-
-template <int K>
 static cudaError_t launch_rowacc_k(const AccArgs& a, int nrowblk, cudaStream_t s) {
   dim3 grid(nrowblk, a.nseg);
   rowacc_kernel<K><<<grid, kThreads, RowAccSmem<K>::bytes, s>>>(a);
@@ -593,8 +279,6 @@ static cudaError_t launch_rowacc_k(const AccArgs& a, int nrowblk, cudaStream_t s
 
 template <int K>
 static void set_acc_attr() {
-  cudaFuncSetAttribute(colacc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)ColAccSmem<K>::bytes);
   cudaFuncSetAttribute(rowacc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)RowAccSmem<K>::bytes);
 }
@@ -612,15 +296,6 @@ int acc_template_k(int k) { return k <= 16 ? 16 : k <= 32 ? 32 : k <= 48 ? 48 : 
 
 // Rows per CTA of the row-direction product for a given width.
 int rowacc_rows(int k) { return acc_template_k(k) <= 32 ? 16 : 8; }
-
-cudaError_t launch_colacc(const AccArgs& a, int ncolblk, cudaStream_t s) {
-  switch (acc_template_k(a.k)) {
-    case 16: return launch_colacc_k<16>(a, ncolblk, s);
-    case 32: return launch_colacc_k<32>(a, ncolblk, s);
-    case 48: return launch_colacc_k<48>(a, ncolblk, s);
-    default: return launch_colacc_k<64>(a, ncolblk, s);
-  }
-}
 
 cudaError_t launch_rowacc(const AccArgs& a, int nrowblk, cudaStream_t s) {
   switch (acc_template_k(a.k)) {

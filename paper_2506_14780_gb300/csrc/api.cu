@@ -49,7 +49,6 @@ cudaError_t launch_row64(const Prob* dP, const Prob& hP, int mode, cudaStream_t 
 cudaError_t launch_shift64(const Prob* dP, const double* p, const double* logw, int len,
                            double* out, cudaStream_t s);
 
-cudaError_t launch_colacc(const AccArgs& a, int ncolblk, cudaStream_t s);
 cudaError_t launch_rowacc(const AccArgs& a, int nrowblk, cudaStream_t s);
 int acc_template_k(int k);
 int rowacc_rows(int k);
@@ -616,7 +615,7 @@ struct Solver {
   AccArgs s4_args() const {
     AccArgs a{};
     a.P = dP;
-    a.mode = 1;  // ACC_S4
+    a.mode = ACC_S4;
     a.k = ell;
     a.Z = V;
     a.out = W;
@@ -635,7 +634,7 @@ struct Solver {
   AccArgs kcol_args(int fb, int gb, const float* Z, float* out) const {
     AccArgs a{};
     a.P = dP;
-    a.mode = 0;  // ACC_KCOL
+    a.mode = ACC_KCOL;
     a.k = p;
     a.Z = Z;
     a.out = out;
@@ -652,7 +651,7 @@ struct Solver {
   AccArgs krow_args(int fb, int gb, const float* Z, float* out) const {
     AccArgs a{};
     a.P = dP;
-    a.mode = 2;  // ACC_KROW
+    a.mode = ACC_KROW;
     a.k = p;
     a.Z = Z;
     a.out = out;
@@ -669,7 +668,7 @@ struct Solver {
   AccArgs rmma_args(int fb, int gb, const float* Z, float* out) const {
     AccArgs a{};
     a.P = dP;
-    a.mode = 2;  // ACC_KROW
+    a.mode = ACC_KROW;
     a.k = p;
     a.Z = Z;
     a.out = out;

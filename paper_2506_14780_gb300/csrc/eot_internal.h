@@ -29,6 +29,10 @@ enum PassMode : int {
   MODE_S4 = 7         // float64 SK-NR column pass (h, W)
 };
 
+// What a coupling-product pass computes (AccArgs::mode): the column product
+// Op(pi)^T Z, the fused SK-NR column pass S4, the row product Op(pi) Z.
+enum AccMode : int { ACC_KCOL = 0, ACC_S4 = 1, ACC_KROW = 2 };
+
 // Device-resident solver state (one per problem).
 struct State {
   int iter;        // Algorithm 4.1 iterations done at the current level
@@ -184,9 +188,10 @@ struct AccArgs {
 // error l1 (one thread): 1 converged (l1 < tol), 2 iteration cap, 6 stalled,
 // 0 go on.  Every `window` iterations l1 is compared with its value at the
 // previous checkpoint; when it has not fallen below kStallRatio times that
-// value the level stops (the float32 passes floor the error, and a level that
-// gains less than 1% per window would need far more than any iteration cap
-// to gain a decade).  window 0 turns the check off.
+// value the level stops: the error has reached the float32 passes' rounding
+// floor, or falls so slowly (under 1% per window, over 200 windows per decade)
+// that no practical iteration cap would reach the tolerance.  window 0 turns
+// the check off.
 constexpr double kStallRatio = 0.99;
 __device__ inline int stop_code(State* st, double l1, int iter, double tol, int max_iter,
                                 int window) {

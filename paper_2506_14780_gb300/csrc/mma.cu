@@ -75,7 +75,7 @@ template <int NN>
 __device__ __noinline__ void colmma_finish(const AccArgs& args, const Prob& P, unsigned char* smem,
                               MmaEpi& epi, int cb, int gb, int dst_g, int len) {
   State* st = P.st;
-  const bool s4 = args.mode == 1;
+  const bool s4 = args.mode == ACC_S4;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int m = len, kk = args.k;
   const int c = tid & (kMmaM - 1), h = tid >> 7;
@@ -492,7 +492,7 @@ template <int NN>
 __global__ void __launch_bounds__(256) colmma_kernel(AccArgs args, const float* __restrict__ tiles) {
   const Prob& P = *args.P;
   State* st = P.st;
-  const bool s4 = args.mode == 1;
+  const bool s4 = args.mode == ACC_S4;
   if (s4 && st->done) return;
   const int fb = s4 ? st->cur_f : args.fbuf;
   const int gb = s4 ? st->cur_g : args.gbuf;
@@ -528,7 +528,7 @@ __global__ void __launch_bounds__(256) colmma_kernel(AccArgs args, const float* 
   const float k2 = P.k2;
   const float Kj = jv ? cK[j] : P.M;
   const float cc0 = jv ? cKL[j] * k2 : 0.f;
-  float cc = cc0, ref = 0.f, run = -INFINITY, S = 0.f;
+  float ref = 0.f, run = -INFINITY, S = 0.f, Sc = 0.f;   // run: maximum of y - ref
   constexpr uint32_t idesc = idesc_tf32(kMmaM, NN);
   constexpr uint32_t tcols = NN <= 32 ? 32 : (NN <= 64 ? 64 : 128);
   constexpr int BV = (2 * NN * kMmaKC) / (4 * 256);  // float4 of B tiles per thread per chunk
@@ -588,6 +588,7 @@ __global__ void __launch_bounds__(256) colmma_kernel(AccArgs args, const float* 
     const int base_i = i_beg + ch * kMmaKC;
     // exponentials of this thread's 16 rows, written as A (hi and lo tiles)
     float ew[16];
+    float part = 0.f;   // the current group of 4 terms, added to S compensated
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
       const int r = h * 16 + u;
@@ -595,21 +596,34 @@ __global__ void __launch_bounds__(256) colmma_kernel(AccArgs args, const float* 
       if (jv && base_i + r < i_end) {
         const float2 ra = sRow[buf * kMmaKC + r];
         const float t = __fadd_rn(split_exponent(cv[u], Kj, ra.x), ra.y);
-        float y = __fmaf_rn(t, k2, cc);
-        if (y > run) {
-          run = y;
-          if (run > kRecenter || (run < -kRecenter && run > -INFINITY)) {
-            const float d = rintf(run);
-            S = scale2(S, -d);
-            ref += d;
-            cc = __fsub_rn(cc0, ref);
-            run -= d;
-            y = __fmaf_rn(t, k2, cc);
+        const float y = __fmaf_rn(t, k2, cc0);   // relative to the column's shift
+        float z = ref == 0.f ? y : __fsub_rn(y, ref);
+        if (z > run) {
+          run = z;
+          if (needs_move(run, ref)) {
+            // the Sinkhorn passes' reference rule (exact power-of-two
+            // rescaling; the reference returns to 0 once the maximum is
+            // within the window), so that the dominant terms carry no
+            // rounding of a large exponent
+            S = __fadd_rn(__fsub_rn(S, Sc), part);
+            Sc = 0.f;
+            part = 0.f;
+            move_ref(run, ref, S);
+            z = ref == 0.f ? y : __fsub_rn(y, ref);
           }
         }
-        const float e = ex2_approx(y);
-        S += e;
+        const float e = ex2_approx(z);
+        part += e;
         ew[u] = (ref == 0.f) ? e : scale2(e, ref);   // absolute scale for the product
+      }
+      if ((u & 3) == 3) {
+        // Kahan: a serial float32 sum over a long segment would floor the
+        // L1 marginal test
+        const float yk = __fsub_rn(part, Sc);
+        const float tk = __fadd_rn(S, yk);
+        Sc = __fsub_rn(__fsub_rn(tk, S), yk);
+        S = tk;
+        part = 0.f;
       }
     }
     {
@@ -669,6 +683,7 @@ __global__ void __launch_bounds__(256) colmma_kernel(AccArgs args, const float* 
   }
   if (!ok) s_err = 1;
   tc_fence_after();
+  S = __fsub_rn(S, Sc);
   // LSE halves -> one state per column
   s_lr[h][c] = (S > 0.f) ? ref : -INFINITY;
   s_ls[h][c] = (double)S;
@@ -798,7 +813,7 @@ __global__ void __launch_bounds__(kTmThreads, 2)
   const Prob* PP = args.P;
   const Prob& P = *PP;
   State* st = P.st;
-  const bool s4 = !ROW && args.mode == 1;
+  const bool s4 = !ROW && args.mode == ACC_S4;
   if (s4 && st->done) return;
   const int fb = s4 ? st->cur_f : args.fbuf;
   const int gb = s4 ? st->cur_g : args.gbuf;

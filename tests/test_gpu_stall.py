@@ -77,3 +77,19 @@ def test_batch_members_stop_on_stall(pkg):
         assert r.status == pkg.EOT_NOT_CONVERGED and r.stalled == 1, r.as_dict()
         assert r.iters <= 20 * WINDOW, r.as_dict()
         assert O.evaluate(f, g, _cost(q), q.a, q.b, q.eps)["l1"] < 1e-5
+
+
+def test_sknr_on_an_unaligned_cost_pitch_reaches_tol(pkg):
+    """m = 15482: the cost rows are not 16-byte aligned, so the SK-NR column
+    pass runs its non-TMA variant over segments of thousands of rows; its
+    column sums are compensated, so the L1 test reaches 1e-6 about as soon as
+    Sinkhorn's does (an uncompensated float32 sum floored the estimate above
+    the tolerance and the level ran to its stall check)."""
+    p = W.gaussian_cloud(12511, 15482, d=64, seed=11, eps=1e-2)
+    p.normalize_cost = True
+    _, _, sk = pkg.solve(p, tol=1e-6, max_iter=20000, eps_start=1e-1, level_tol=1e-4, ell=0)
+    f, g, nr = pkg.solve(p, tol=1e-6, max_iter=20000, eps_start=1e-1, level_tol=1e-4, ell=30)
+    assert sk["return_status"] == pkg.EOT_OK and nr["return_status"] == pkg.EOT_OK, (sk, nr)
+    assert nr["stalled"] == 0, nr
+    assert nr["iters"] <= sk["iters"] + 10, (nr["iters"], sk["iters"])
+    assert O.evaluate(f, g, _cost(p), p.a, p.b, p.eps)["l1"] <= 1e-6
