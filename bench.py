@@ -549,26 +549,29 @@ def extras(pkg, torch, stream):
                 "with their own streams, overlapping on the device; one call"}
     # c5: served stream (Poisson arrivals, continuous batching, warm restarts):
     # at the offered 2000 requests/s (its first requests: far beyond capacity,
-    # latency is queueing) and at ~70% of the rate measured there
+    # latency is queueing) and at half the rate measured there
     stage("c5: serving at 2000/s")
     os5 = pkg.default_options(tol=TOL, max_iter=200000, eps_start=1e-1, level_tol=LEVEL_TOL,
                               ell=ELL)
     reqs = workloads.served_stream(seed=1, rate_per_s=2000.0, duration_s=60.0, max_requests=200)
     hi = serve(pkg, reqs, os5)
-    rate = max(1.0, 0.7 * hi["solves_per_s"])
+    rate = max(1.0, 0.5 * hi["solves_per_s"])
     stage(f"c5: serving at {rate:.1f}/s")
-    reqs2 = workloads.served_stream(seed=3, rate_per_s=rate, duration_s=20.0, max_requests=2000)
+    # the same seed: the same sequence of problems (arrival gaps scale with the
+    # rate), so its first 200 requests are the ones measured above
+    reqs2 = workloads.served_stream(seed=1, rate_per_s=rate, duration_s=20.0, max_requests=2000)
     lo = serve(pkg, reqs2, os5)
     out["c5_serving"] = {
         "offered_2000_per_s": dict(hi, offered_rate_per_s=2000.0,
                                    note="the first 200 requests of the 2000/s stream"),
         "sustainable": dict(lo, offered_rate_per_s=round(rate, 1),
-                            note="20 s Poisson stream at 0.7 x the solves/s measured at 2000/s"),
+                            note="20 s Poisson stream at 0.5 x the solves/s measured at 2000/s"),
         "note": "n, m log-uniform in [128, 16384], d in {2, 3, 64}, eps in {1e-1, 1e-2, 1e-3}, "
                 "half the requests re-use an earlier cloud (warm start from its resident "
                 "potentials); every request SK-NR(30) on a stored float32 cost, continuation "
-                "from 1e-1 (intermediate levels to 1e-4); 8 slots, 48 GB budget; admitted "
-                "solves overlap on the device (own streams)"}
+                "from 1e-1 (intermediate levels to 1e-4), a level stops on a stall (under 1% "
+                "gain per 1000 iterations); 8 slots, 48 GB budget; admitted solves overlap on "
+                "the device (own streams); converged = EOT_OK (the returned pair meets 1e-6)"}
     return out, c3_pair
 
 
@@ -656,7 +659,7 @@ def serve(pkg, reqs, opts, slots=8, budget=48 << 30):
             s5 = srv.status()
             qmax = max(qmax, s5["queued"])
             hbm_max = max(hbm_max, s5["hbm_in_use"])
-        done = 0
+        done = conv = 0
         for t in tickets:
             while True:
                 st5, _, _, _ = srv.poll(t)
@@ -667,11 +670,13 @@ def serve(pkg, reqs, opts, slots=8, budget=48 << 30):
                 hbm_max = max(hbm_max, s5["hbm_in_use"])
                 time.sleep(0.001)
             done += st5 in (pkg.EOT_OK, pkg.EOT_NOT_CONVERGED)
+            conv += st5 == pkg.EOT_OK
         t1 = time.perf_counter()
         p50, p99, sps = srv.stats()
     finally:
         srv.close()
-    return {"requests": len(reqs), "completed": int(done), "p50_ms": round(p50 * 1e3, 2),
+    return {"requests": len(reqs), "completed": int(done), "converged": int(conv),
+            "p50_ms": round(p50 * 1e3, 2),
             "p99_ms": round(p99 * 1e3, 2), "solves_per_s": round(sps, 1),
             "wall_s": round(t1 - t0, 3), "max_queue_depth": qmax,
             "max_hbm_admitted_gb": round(hbm_max / 2 ** 30, 2)}
@@ -790,7 +795,7 @@ def profile_case(name):
     """Small cases for ncu captures: one plain Sinkhorn launch of two iterations
     on a 16384 x 16384 cost (coop16k); column and row transforms on an 8192 x
     8192 cost (stream8k); one SK-NR(30) solve of the 4096 x 4096 workload
-    (sknr4k); ten on-the-fly-cost iterations on 20000 x 30000 points in R^64
+    (sknr4k, two solves); ten on-the-fly-cost iterations on 20000 x 30000 points in R^64
     (gram); the batch of 512 problems (batch)."""
     import torch
     import workloads
@@ -825,8 +830,11 @@ def profile_case(name):
                                reps=1)
         res = {"status_name": f"stage us {[round(x * 1e6, 1) for x in st4]}"}
     elif name == "sknr4k":
+        # two solves (the first also builds the solver) under the benchmark's protocol
         prob = workloads.gaussian_mixture(N, M, seed=0, eps=EPS)
-        _, _, res = pkg.solve(prob, tol=TOL, ell=ELL, eps_start=1e-1, max_iter=200000)
+        for _ in range(2):
+            _, _, res = pkg.solve(prob, tol=TOL, ell=ELL, eps_start=1e-1, max_iter=200000,
+                                  level_tol=LEVEL_TOL)
     elif name == "batch":
         probs = workloads.batch_problems(512, seed=0)
         keepb = []
