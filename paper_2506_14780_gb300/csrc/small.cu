@@ -365,6 +365,31 @@ __device__ __forceinline__ void jacobi_rot(float akk, float aqq, float akq, floa
   }
 }
 
+// Out = X Y (or X^T Y) for p x p shared matrices of row stride kES, p <= 2 nx:
+// thread (ty, tx) forms the 2 x 2 block of rows ty, ty + nx and columns tx,
+// tx + nx.
+__device__ __forceinline__ void block2_product(const float* X, const float* Y, float* Out, int p,
+                                               int ty, int tx, int nx, bool transX) {
+  const int r0 = ty, r1 = ty + nx, q0 = tx, q1 = tx + nx;
+  if (r0 >= p || q0 >= p) return;
+  const bool vr = r1 < p, vq = q1 < p;
+  float a00 = 0.f, a01 = 0.f, a10 = 0.f, a11 = 0.f;
+  for (int k = 0; k < p; ++k) {
+    const float x0 = transX ? X[k * kES + r0] : X[r0 * kES + k];
+    const float x1 = vr ? (transX ? X[k * kES + r1] : X[r1 * kES + k]) : 0.f;
+    const float y0 = Y[k * kES + q0];
+    const float y1 = vq ? Y[k * kES + q1] : 0.f;
+    a00 = __fmaf_rn(x0, y0, a00);
+    a01 = __fmaf_rn(x0, y1, a01);
+    a10 = __fmaf_rn(x1, y0, a10);
+    a11 = __fmaf_rn(x1, y1, a11);
+  }
+  Out[r0 * kES + q0] = a00;
+  if (vq) Out[r0 * kES + q1] = a01;
+  if (vr) Out[r1 * kES + q0] = a10;
+  if (vr && vq) Out[r1 * kES + q1] = a11;
+}
+
 __global__ void __launch_bounds__(kEH * kEH) eig_small_kernel(int p, int l, int mode,
                                                               const double* __restrict__ GXX,
                                                               const double* __restrict__ T,
@@ -410,28 +435,28 @@ __global__ void __launch_bounds__(kEH * kEH) eig_small_kernel(int p, int l, int 
   // and sides xa, xb.  Packed: k | q << 6 | ka << 12 | qa << 18 | xa << 24 |
   // xb << 25, and kb | qb << 6 | ta << 12 | tb << 17.
   uint2* nxt = reinterpret_cast<uint2*>(G);
+  // slot of index idx in round r (inverse of pair_of): index 0 sits in slot 0;
+  // any other index sits at position pos = 1 + (idx - 1 - r mod nr) of the
+  // rotating ring, on the first side of slot pos if pos < half, else on the
+  // second side of slot pe - 1 - pos
+  auto slot_of = [&](int r, int idx, int& t, int& x, int& k2, int& q2) {
+    if (idx == 0) {
+      t = 0;
+    } else {
+      const int pos = 1 + ((idx - 1 - r) % nr + nr) % nr;
+      t = pos <= half - 1 ? pos : pe - 1 - pos;
+    }
+    pair_of(r, t, k2, q2);
+    x = q2 == idx;
+  };
   if (mode == 1) {
     for (int e = tid; e < nr * half; e += nt) {
       const int r = e / half, t = e - r * half;
       int k, q;
       pair_of(r + 1 < nr ? r + 1 : 0, t, k, q);
-      int ta = 0, tb = 0, xa = 0, xb = 0, ka = 0, qa = 0, kb = 0, qb = 0;
-      for (int u = 0; u < half; ++u) {
-        int k2, q2;
-        pair_of(r, u, k2, q2);
-        if (k2 == k || q2 == k) {
-          ta = u;
-          xa = q2 == k;
-          ka = k2;
-          qa = q2;
-        }
-        if (k2 == q || q2 == q) {
-          tb = u;
-          xb = q2 == q;
-          kb = k2;
-          qb = q2;
-        }
-      }
+      int ta, tb, xa, xb, ka, qa, kb, qb;
+      slot_of(r, k, ta, xa, ka, qa);
+      slot_of(r, q, tb, xb, kb, qb);
       nxt[e] = make_uint2((unsigned)(k | (q << 6) | (ka << 12) | (qa << 18) | (xa << 24) | (xb << 25)),
                           (unsigned)(kb | (qb << 6) | (ta << 12) | (tb << 17)));
     }
@@ -541,12 +566,9 @@ __global__ void __launch_bounds__(kEH * kEH) eig_small_kernel(int p, int l, int 
     for (int q = tx; q < p; q += nx) G[r * kES + q] = (float)(GXX[r * p + q] - c[r] * c[q]);
   __syncthreads();
   if (mode == 1) {
-    for (int r = ty; r < p; r += nx)      // W = G Q
-      for (int q = tx; q < p; q += nx) {
-        float acc = 0.f;
-        for (int k = 0; k < p; ++k) acc = __fmaf_rn(G[r * kES + k], Q[k * kES + q], acc);
-        W[r * kES + q] = acc;
-      }
+    // W = G Q: thread (ty, tx) forms rows ty, ty + nx and columns tx, tx + nx
+    // (p <= 2 nx), each loaded value used twice
+    block2_product(G, Q, W, p, ty, tx, nx, false);
     if (ty == 0)                          // (Q^T c)_k
       for (int k = tx; k < p; k += nx) {
         float acc = 0.f;
@@ -554,12 +576,7 @@ __global__ void __launch_bounds__(kEH * kEH) eig_small_kernel(int p, int l, int 
         qc[k] = acc;
       }
     __syncthreads();
-    for (int r = ty; r < p; r += nx)      // A = Q^T W
-      for (int q = tx; q < p; q += nx) {
-        float acc = 0.f;
-        for (int k = 0; k < p; ++k) acc = __fmaf_rn(Q[k * kES + r], W[k * kES + q], acc);
-        A[r * kES + q] = acc;
-      }
+    block2_product(Q, W, A, p, ty, tx, nx, true);   // A = Q^T W
     __syncthreads();
     // residual_k^2 = (Q^T GXX Q)_kk - theta_k^2 = G'_kk + (Q^T c)_k^2 - theta_k^2
     float rmax = 0.f;
