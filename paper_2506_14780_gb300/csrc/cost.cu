@@ -117,45 +117,79 @@ __global__ void __launch_bounds__(256) cost_maxx_kernel(int n, int m, int d,
     atomicMax(out, (unsigned long long)__double_as_longlong(mx));
 }
 
+// RN32(RN64(v / cmax)) from rc = RN64(1 / cmax).  q = RN64(v rc) lies within
+// 2 units in the last place of RN64(v / cmax) (|q - v / cmax| < 2 ulp); both
+// round to the same float32 unless a float32 rounding midpoint is that close,
+// i.e. unless the 29 bits of q below float32 precision are within 2 of
+// 2^28 (or q is below the float32 normal range).  Only then is the quotient
+// corrected once (Markstein's theorem: e = v - cmax q is exact by FMA and
+// RN64(q + e rc) is the correctly rounded v / cmax).
+__device__ __forceinline__ float round_quotient(double v, double cmax, double rc) {
+  const double q = __dmul_rn(v, rc);
+  const unsigned long long b = (unsigned long long)__double_as_longlong(q);
+  const unsigned low = (unsigned)(b & 0x1FFFFFFFull);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex > 1023 - 126 && low - ((1u << 28) - 2u) > 4u) return __double2float_rn(q);
+  const double e = fma(-q, cmax, v);
+  return __double2float_rn(fma(e, rc, q));
+}
+
 // C_ij in float64, optionally divided by the maximum, rounded once to float32.
-// The quotient is formed from the correctly rounded reciprocal with one
-// residual correction (Markstein's theorem: q = RN(a r), e = a - b q exact by
-// FMA, RN(q + e r) is the correctly rounded a / b), which replaces a full
-// float64 division per element.
+// The tile's rows are converted to float64 once (shared memory); points of up
+// to 4 coordinates keep the column's point in float64 registers.
 __global__ void __launch_bounds__(256) cost_fill2_kernel(int n, int m, int d,
                                                          const float* __restrict__ X,
                                                          const float* __restrict__ Y,
                                                          const unsigned long long* __restrict__ cmax_bits,
                                                          int normalize, float* __restrict__ C) {
-  extern __shared__ float sx[];   // [kCostRows][d]
+  extern __shared__ double sxd[];   // [kCostRows][d]
   const int i0 = blockIdx.x * kCostRows, nr = min(kCostRows, n - i0);
-  for (int e = threadIdx.x; e < nr * d; e += blockDim.x) sx[e] = X[(size_t)i0 * d + e];
+  for (int e = threadIdx.x; e < nr * d; e += blockDim.x) sxd[e] = (double)X[(size_t)i0 * d + e];
   __syncthreads();
   const double cmax = __longlong_as_double((long long)*cmax_bits);
   const bool norm = normalize && cmax > 0.0;
   const double rc = norm ? 1.0 / cmax : 1.0;
+  const bool small = d <= 4;
   for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < m; j += gridDim.y * blockDim.x) {
     const float* y = Y + (size_t)j * d;
+    double yd[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) yd[k] = (small && k < d) ? (double)y[k] : 0.0;
     for (int r = 0; r < nr; ++r) {
-      double v = sqdist(sx + r * d, y, d);
-      if (norm) {
-        const double q = v * rc;
-        const double e = fma(-q, cmax, v);
-        v = fma(e, rc, q);
+      const double* x = sxd + r * d;
+      double v;
+      if (small) {
+        // the same operations, in the same order, as sqdist
+        const double t0 = __dsub_rn(x[0], yd[0]);
+        v = __dmul_rn(t0, t0);
+#pragma unroll
+        for (int k = 1; k < 4; ++k) {
+          if (k < d) {
+            const double t = __dsub_rn(x[k], yd[k]);
+            v = __dadd_rn(v, __dmul_rn(t, t));
+          }
+        }
+      } else {
+        v = 0.0;
+        for (int k = 0; k < d; ++k) {
+          const double t = __dsub_rn(x[k], (double)y[k]);
+          v = __dadd_rn(v, __dmul_rn(t, t));
+        }
       }
-      C[(size_t)(i0 + r) * m + j] = __double2float_rn(v);
+      C[(size_t)(i0 + r) * m + j] = norm ? round_quotient(v, cmax, rc) : __double2float_rn(v);
     }
   }
 }
 
 // Cost from points: the exact maximum (when wanted; into *cmax64, which the
-// caller zeroed) and the cost (when C is given).  Wide points (more than 384
+// caller zeroed) and the cost (when C is given).  Wide points (more than 192
 // coordinates) take the untiled kernels.
 cudaError_t launch_cost_points(int n, int m, int d, const float* X, const float* Y, bool want_max,
                                int normalize, float* C, unsigned* fmax_bits,
                                unsigned long long* cmax64, cudaStream_t s) {
   const size_t sm = (size_t)kCostRows * d * sizeof(float);
-  if (sm > 48 * 1024) {
+  const size_t sm64 = (size_t)kCostRows * d * sizeof(double);   // the fill kernel's rows
+  if (sm64 > 48 * 1024) {
     const size_t nm = (size_t)n * m;
     const int gb = (int)std::min<size_t>((nm + 255) / 256, 2048);
     if (want_max) cost_max_kernel<<<gb, 256, 0, s>>>(n, m, d, X, Y, cmax64);
@@ -169,7 +203,7 @@ cudaError_t launch_cost_points(int n, int m, int d, const float* X, const float*
     cost_maxf_kernel<<<grid, 256, sm, s>>>(n, m, d, X, Y, fmax_bits);
     cost_maxx_kernel<<<grid, 256, sm, s>>>(n, m, d, X, Y, fmax_bits, cmax64);
   }
-  if (C) cost_fill2_kernel<<<grid, 256, sm, s>>>(n, m, d, X, Y, cmax64, normalize, C);
+  if (C) cost_fill2_kernel<<<grid, 256, sm64, s>>>(n, m, d, X, Y, cmax64, normalize, C);
   return cudaGetLastError();
 }
 

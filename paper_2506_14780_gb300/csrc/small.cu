@@ -174,13 +174,107 @@ void launch_eig_gram(const float* X, const float* Z, const double* w, int len, i
 }
 
 // ---------------------------------------------------------------------------
+// In-place L1 D L1^T of the symmetric matrix H in shared memory (row stride S,
+// lower triangle read), pivots 0..p-1, NB pivots at a time (right-looking,
+// outer products, no square roots).  Rows p..rows-1 are right-hand sides that
+// ride along as extra rows: their first p entries end as L1^{-1} b.  On
+// return H[r][j] = L1_rj D_j (r > j), H[j][j] = D_j, inv[j] = 1 / D_j, and
+// *fail = 1 if a pivot was not positive and finite (its inv is then 0).
+// Every thread factors the NB x NB diagonal block in registers from shared
+// memory (no barrier for it); the panel below it and the trailing update take
+// one barrier each, NB pivots per pair of barriers instead of one barrier per
+// pivot.  Each entry receives the same updates, in the same order and with the
+// same products (L1_ru D_u / D_u) x (L1_qu D_u), as in the one-pivot-at-a-time
+// elimination.  Called by every thread of the CTA.
+// ---------------------------------------------------------------------------
+template <int NB>
+__device__ void ldlt_blocked(float* H, int S, int p, int rows, float* inv, int* fail) {
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+  const int NY = nt >> 4, ty = tid >> 4, tx = tid & 15;   // 16-wide tiling of the update
+  for (int k0 = 0; k0 < p; k0 += NB) {
+    const int nb = min(NB, p - k0), k1 = k0 + nb;
+    // (a) the diagonal block: w[j][i] = L1_ji D_i (i < j), d[j] = D_j
+    float w[NB][NB], d[NB], di[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      d[j] = 1.f;
+      di[j] = 0.f;
+#pragma unroll
+      for (int i = 0; i < NB; ++i) w[j][i] = 0.f;
+      if (j < nb) {
+#pragma unroll
+        for (int i = 0; i < j; ++i) {
+          float t = H[(k0 + j) * S + k0 + i];
+#pragma unroll
+          for (int u = 0; u < i; ++u) t = __fmaf_rn(-(w[j][u] * di[u]), w[i][u], t);
+          w[j][i] = t;
+        }
+        float t = H[(k0 + j) * S + k0 + j];
+#pragma unroll
+        for (int u = 0; u < j; ++u) t = __fmaf_rn(-(w[j][u] * di[u]), w[j][u], t);
+        d[j] = t;
+        const bool ok = t > 0.f && isfinite(t);
+        di[j] = ok ? 1.f / t : 0.f;
+      }
+    }
+    // (b) the panel below the block: rows k1..rows-1, one thread per row
+    for (int r = k1 + tid; r < rows; r += nt) {
+      float x[NB];
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        x[j] = 0.f;
+        if (j < nb) {
+          float t = H[r * S + k0 + j];
+#pragma unroll
+          for (int u = 0; u < j; ++u) t = __fmaf_rn(-(x[u] * di[u]), w[j][u], t);
+          x[j] = t;
+          H[r * S + k0 + j] = t;
+        }
+      }
+    }
+    __syncthreads();
+    // (c) the trailing update of rows k1.. and columns k1..min(r, p - 1)
+    if (ty < NY) {
+      for (int r = k1 + ty; r < rows; r += NY) {
+        float hr[NB];
+#pragma unroll
+        for (int j = 0; j < NB; ++j) hr[j] = j < nb ? H[r * S + k0 + j] * di[j] : 0.f;
+        const int qe = min(r, p - 1);
+        for (int q = k1 + tx; q <= qe; q += 16) {
+          float t = H[r * S + q];
+#pragma unroll
+          for (int j = 0; j < NB; ++j)
+            if (j < nb) t = __fmaf_rn(-hr[j], H[q * S + k0 + j], t);
+          H[r * S + q] = t;
+        }
+      }
+    }
+    // the block's own rows (read by every thread in (a), so written after the
+    // barrier) and its pivots
+    if (tid == 0) {
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        if (j < nb) {
+#pragma unroll
+          for (int i = 0; i < j; ++i) H[(k0 + j) * S + k0 + i] = w[j][i];
+          H[(k0 + j) * S + k0 + j] = d[j];
+          inv[k0 + j] = di[j];
+          if (!(d[j] > 0.f && isfinite(d[j]))) *fail = 1;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Newton step on V (one CTA of 256 threads).  GV = V^T D_a V (or V^T D_r V),
 // WtW = sum_j W_j W_j^T / b_j, gw = sum_j d_j W_j (d_j = -expm1(L_j)),
 // Va = V^T a.  -eps H_V = GV - WtW is assembled in float64 (the difference
 // cancels) and factorised in float32 as L D L^T (outer-product elimination
-// without square roots, one barrier per pivot; float64 arithmetic is a small
-// fraction of the float32 rate on this GPU), the forward substitution of
-// grad_V = -gw riding along with the elimination;
+// without square roots, 8 pivots per pair of barriers: ldlt_blocked; float64
+// arithmetic is a small fraction of the float32 rate on this GPU), the forward
+// substitution of grad_V = -gw riding along as an extra row;
 // Delta = (-H_V)^{-1} grad_V = eps (GV - WtW)^{-1} grad_V.  A pivot that is not
 // positive (the restricted Hessian is not negative definite) rejects the step.
 // ---------------------------------------------------------------------------
@@ -193,47 +287,28 @@ __global__ void __launch_bounds__(256) newton_kernel(const Prob* __restrict__ PP
   if (st->done) return;
   const int l = P.ell;
   const int tid = threadIdx.x, lane = tid & 31;
-  const int ty = tid >> 4, tx = tid & 15;          // 16 x 16 tiling of the trailing matrix
+  const int ty = tid >> 4, tx = tid & 15;          // 16 x 16 tiling of the assembly
   constexpr int kS = kMaxK + 1;                    // odd row stride
-  __shared__ float H[kMaxK * kS];
+  __shared__ float H[(kMaxK + 1) * kS];            // row l: the right-hand side
   __shared__ float g[kMaxK];
-  __shared__ float s_inv[kMaxK];   // 1 / D_k, formed by the thread owning the pivot
+  __shared__ float s_inv[kMaxK];   // 1 / D_k
   __shared__ int s_fail;
   const double* __restrict__ G0 = Dr ? Dr : P.GV;
   if (tid == 0) s_fail = 0;
-  auto pivot = [&](int k) {        // thread 0 owns element (k, k) of every update
-    const float d = H[k * kS + k];
-    const bool ok = d > 0.f && isfinite(d);
-    if (!ok) s_fail = 1;
-    s_inv[k] = ok ? 1.f / d : 0.f;
-  };
   for (int r = ty; r < l; r += 16)
     for (int c = tx; c <= r; c += 16) {
       const double gv = 0.5 * (G0[r * l + c] + G0[c * l + r]);
       const double wt = 0.5 * (WtW[r * l + c] + WtW[c * l + r]);
       H[r * kS + c] = (float)(gv - wt);
-      if (r == 0) pivot(0);
     }
-  for (int k = tid; k < l; k += 256) g[k] = (float)(-gw[k]);
+  for (int k = tid; k < l; k += 256) H[l * kS + k] = (float)(-gw[k]);
   __syncthreads();
-  // elimination: after pivot k, H[r][k] = L_rk D_k (r > k), H[k][k] = D_k, and
-  // g holds the forward-substituted right-hand side
-  for (int k = 0; k < l; ++k) {
-    const float inv = s_inv[k];
-    for (int r = k + 1 + ty; r < l; r += 16) {
-      const float hr = H[r * kS + k] * inv;
-      for (int c = k + 1 + tx; c <= r; c += 16) {
-        H[r * kS + c] = __fmaf_rn(-hr, H[c * kS + k], H[r * kS + c]);
-        if (c == k + 1 && r == k + 1) pivot(k + 1);
-      }
-    }
-    if (tid >= 128) {
-      const int i = k + 1 + (tid - 128);
-      if (i < l) g[i] = __fmaf_rn(-H[i * kS + k] * inv, g[k], g[i]);
-    }
-    __syncthreads();
-  }
+  // elimination (8 pivots per pair of barriers): H[r][k] = L_rk D_k (r > k),
+  // H[k][k] = D_k, and row l holds the forward-substituted right-hand side
+  ldlt_blocked<8>(H, kS, l, l + 1, s_inv, &s_fail);
   if (tid >= 32) return;
+  for (int k = lane; k < l; k += 32) g[k] = H[l * kS + k];
+  __syncwarp();
   // D z = y, then L^T x = z (column oriented, lanes over rows)
   for (int k = lane; k < l; k += 32) g[k] = s_fail ? 0.f : g[k] * s_inv[k];
   __syncwarp();
@@ -598,17 +673,9 @@ __global__ void __launch_bounds__(kEH * kEH) eig_small_kernel(int p, int l, int 
       for (int q = tx; q < p; q += nx) G[r * kES + q] = A[r * kES + q];
     __syncthreads();
   }
-  // G = L D L^T by outer products (one barrier per pivot); L = L1 D^(1/2)
-  for (int k = 0; k < p; ++k) {
-    const float dk = G[k * kES + k];
-    if (tid == 0 && !(dk > 0.f)) s_fail = 1;
-    const float inv = dk > 0.f ? 1.f / dk : 0.f;
-    for (int r = k + 1 + ty; r < p; r += nx) {
-      const float hr = G[r * kES + k] * inv;
-      for (int q = k + 1 + tx; q <= r; q += nx) G[r * kES + q] -= hr * G[q * kES + k];
-    }
-    __syncthreads();
-  }
+  // G = L1 D L1^T (8 pivots per pair of barriers; th: scratch for 1 / D,
+  // the Ritz values are written out); L = L1 D^(1/2)
+  ldlt_blocked<8>(G, kES, p, p, th, &s_fail);
   for (int k = tid; k < p; k += nt) {
     const float dk = G[k * kES + k];
     sq[k] = dk > 0.f ? rsqrtf(dk) : 1.f;   // 1 / L_kk
@@ -620,14 +687,45 @@ __global__ void __launch_bounds__(kEH * kEH) eig_small_kernel(int p, int l, int 
   for (int r = ty; r < p; r += nx)        // W = Q (right-hand sides)
     for (int q = tx; q < p; q += nx) W[r * kES + q] = Q[r * kES + q];
   __syncthreads();
-  // B L^T = Q, column by column: after step q, column q of W is final
-  for (int q = 0; q < p; ++q) {
-    const float il = sq[q];
-    for (int r = ty; r < p; r += nx) {
-      const float b = W[r * kES + q] * il;
-      for (int cc = q + 1 + tx; cc < p; cc += nx) W[r * kES + cc] -= b * G[cc * kES + q];
+  // B L^T = Q by blocks of 8 columns, B_rq = W_rq sq_q: (a) one thread per
+  // row finishes the block's columns (updates from the block's earlier
+  // columns), (b) the later columns receive the block's updates; every entry
+  // gets its updates in increasing column order, as column by column
+  {
+    const int NY = nt >> 4, y16 = tid >> 4, x16 = tid & 15;
+    for (int c0 = 0; c0 < p; c0 += 8) {
+      const int nb = min(8, p - c0), c1 = c0 + nb;
+      for (int r = tid; r < p; r += nt) {
+        float b[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          b[j] = 0.f;
+          if (j < nb) {
+            float t = W[r * kES + c0 + j];
+#pragma unroll
+            for (int u = 0; u < j; ++u) t = __fmaf_rn(-b[u], G[(c0 + j) * kES + c0 + u], t);
+            W[r * kES + c0 + j] = t;
+            b[j] = t * sq[c0 + j];
+          }
+        }
+      }
+      __syncthreads();
+      if (y16 < NY) {
+        for (int r = y16; r < p; r += NY) {
+          float b[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) b[j] = j < nb ? W[r * kES + c0 + j] * sq[c0 + j] : 0.f;
+          for (int cc = c1 + x16; cc < p; cc += 16) {
+            float t = W[r * kES + cc];
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              if (j < nb) t = __fmaf_rn(-b[j], G[cc * kES + c0 + j], t);
+            W[r * kES + cc] = t;
+          }
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
   for (int r = ty; r < p; r += nx)
     for (int q = tx; q < p; q += nx) Bout[r * p + q] = W[r * kES + q] * sq[q];

@@ -189,6 +189,24 @@ def test_cost_bit_exact(pkg, n, m, d, norm):
     assert cmax.item() == O.sq_euclidean_cost(X, Y).max()
 
 
+def test_cost_rounding_at_float32_midpoints(pkg):
+    """Normalised costs whose float64 value sits exactly on, or one float64
+    unit above, a float32 rounding midpoint (1.5625 + 2^-24 has the bit just
+    below float32 precision set and nothing under it; 2^-52 more is one unit
+    above): the kernel's fast quotient path hands these to the corrected
+    quotient, and the result is still the float32 rounding of the float64
+    definition, bit for bit."""
+    X = np.zeros((2, 3), dtype=np.float32)
+    X[1] = [0.5, 0.0, 0.0]
+    Y = np.array([[1.25, 2.0 ** -12, 0.0], [1.25, 2.0 ** -12, 2.0 ** -26], [2.0, 0.0, 0.0],
+                  [1.25, 0.0, 2.0 ** -12], [0.75, 2.0 ** -13, 2.0 ** -27]], dtype=np.float32)
+    n, m = X.shape[0], Y.shape[0]
+    out = torch.zeros((n, m), dtype=torch.float32, device="cuda")
+    assert pkg.eot_cost(n, m, 3, dev(X), dev(Y), True, out) == pkg.EOT_OK
+    ref = O.sq_euclidean_cost(X, Y, normalize=True).astype(np.float32)
+    assert np.array_equal(out.cpu().numpy(), ref)
+
+
 def test_marginal_error_parity(pkg):
     prob = W.random_cost(333, 211, seed=9)
     C64 = prob.C.astype(np.float64)
