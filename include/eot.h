@@ -117,6 +117,14 @@ typedef struct {
                                solve then returns EOT_OK if the returned pair meets
                                tol, else EOT_NOT_CONVERGED, with eot_result.stalled = 1.
                                0: no check.  Default 1000.                            */
+    int32_t eig_degree;     /* mode computation (Sec. 3-4): 0 or 1, block subspace
+                               iteration with a Rayleigh-Ritz step per application of
+                               Op(pi) o Op(pi)^T; 2..8, Chebyshev-filtered subspace
+                               iteration: between two Rayleigh-Ritz steps the Ritz
+                               vectors are multiplied by the Chebyshev polynomial of
+                               this degree that damps the spectrum below the block's
+                               smallest Ritz value (eig_degree applications per step;
+                               eig_max_iter counts Rayleigh-Ritz steps).  Default 0.  */
 } eot_options;
 
 typedef struct {
@@ -269,6 +277,23 @@ eot_status eot_spectral_modes(int32_t n, int32_t m, const float *C, const double
                               int32_t ell, int32_t oversample, double tol, int32_t max_iter,
                               int32_t use_V_as_start, double *V, double *rho2,
                               int32_t *iters_out, double *resid_out, void *stream);
+
+/* The same modes by Chebyshev-filtered block subspace iteration (a faster
+ * spectral step where the rho_k^2 cluster near 1, Sec. 3): after each
+ * Rayleigh-Ritz step that misses tol, the Ritz vectors are multiplied by
+ * T_degree((M - c)/e), [c - e, c + e] = [0, smallest Ritz value of the block]
+ * (scaled three-term recurrence, every product deflated of the constants),
+ * and the filtered block is orthonormalised in L2(a) by a Cholesky-QR of its
+ * column-scaled Gram matrix.  degree 0 or 1: eot_spectral_modes; 2..8 otherwise
+ * (EOT_EINVAL beyond).  iters_out counts Rayleigh-Ritz steps; each but the
+ * last costs degree applications of Op(pi) o Op(pi)^T.  Other arguments as
+ * eot_spectral_modes. */
+eot_status eot_spectral_modes_filtered(int32_t n, int32_t m, const float *C, const double *f,
+                                       const double *g, const double *a, const double *b,
+                                       double eps, int32_t ell, int32_t oversample,
+                                       int32_t degree, double tol, int32_t max_iter,
+                                       int32_t use_V_as_start, double *V, double *rho2,
+                                       int32_t *iters_out, double *resid_out, void *stream);
 
 /* Scalars of one SK-NR iteration (eot_sknr_step). */
 typedef struct {

@@ -69,6 +69,7 @@ __global__ void __launch_bounds__(256) wtw_reduce_kernel(const AccArgs args,
 // ---------------------------------------------------------------------------
 template <int K>
 __global__ void __launch_bounds__(kThreads) rowacc_kernel(AccArgs args) {
+  if (args.skip && *args.skip) return;
   const Prob& P = *args.P;
   const float* __restrict__ cA = P.cs[args.gbuf].A;
   const float* __restrict__ cAL = P.cs[args.gbuf].AL;

@@ -58,7 +58,8 @@ cudaError_t launch_newton(const Prob* dP, const AccArgs& a, double* WtW, double*
                           cudaStream_t s);
 cudaError_t launch_colmma(const AccArgs& a, const Prob& hP, const float* tiles, int ncolblk,
                           cudaStream_t s);
-cudaError_t launch_build_tiles(const float* Z, int n, int kk, float* tiles, cudaStream_t s);
+cudaError_t launch_build_tiles(const float* Z, int n, int kk, float* tiles, cudaStream_t s,
+                               const int* skip = nullptr);
 cudaError_t launch_rowmma(const AccArgs& a, const float* tiles, int nrowblk, cudaStream_t s);
 int mma_record(int k);
 size_t mma_tiles_floats(int n, int k);
@@ -79,11 +80,18 @@ cudaError_t launch_gram_split(const float* X, int n, int d, double scale, float*
 __global__ void newton_kernel(const Prob*, const double*, const double*, const double*);
 __global__ void fprime_kernel(const Prob*);
 void launch_eig_gram(const float* X, const float* Z, const double* w, int len, int p,
-                     float* part, double* G, double* T, double* c, cudaStream_t s);
+                     float* part, double* G, double* T, double* c, cudaStream_t s,
+                     const int* skip = nullptr);
 void launch_eig_small(int p, int l, int mode, const double* GXX, const double* T,
                       const double* c, float* B, double* theta, double* resid, int* fail,
-                      cudaStream_t s);
-__global__ void apply_kernel(const float*, const double*, const float*, int, int, float*);
+                      cudaStream_t s, float* Qout = nullptr, const int* skip = nullptr);
+__global__ void apply_kernel(const float*, const double*, const float*, int, int, float*,
+                             const int*);
+void launch_ritz(const float* Z, const float* X, const double* cx, const float* Q,
+                 const double* theta, const double* a, int len, int p, int l, float* part,
+                 float* Y0, float* Y1, double* sig, double* resid, int nsm, cudaStream_t s);
+void launch_cheb_step(const float* X, const double* a, const float* Yc, float* Yp, int len, int p,
+                      int k, double* sig, float* part, int nsm, const int* skip, cudaStream_t s);
 __global__ void init_block_kernel(float*, int, int, unsigned long long, const float*, int);
 __global__ void take_cols_kernel(const float*, int, int, int, float*);
 __global__ void grad_weights_kernel(const Prob*, double*);
@@ -373,6 +381,11 @@ struct Solver {
   double *GXX = nullptr, *Tm = nullptr, *cvec = nullptr,
          *theta = nullptr, *resid = nullptr;
   int* efail = nullptr;
+  // Chebyshev filter of the mode computation: the two recurrence blocks, the
+  // Ritz rotation and the filter's scalars
+  float *F0 = nullptr, *F1 = nullptr, *Qm = nullptr;
+  double* csig = nullptr;
+  int eig_graph_degree = -1;   // filter degree the mode loop's graph was captured with
   // host mirrors
   State* hSt = nullptr;
   double* hScores = nullptr;
@@ -572,6 +585,10 @@ struct Solver {
       theta = A.take<double>(p);
       resid = A.take<double>(1);
       efail = A.take<int>(1);
+      F0 = A.take<float>((size_t)n * p);
+      F1 = A.take<float>((size_t)n * p);
+      Qm = A.take<float>((size_t)p * p);
+      csig = A.take<double>(kChebSigDoubles);
     }
   }
 
@@ -684,10 +701,17 @@ struct Solver {
   }
   // Op(pi) Z: on the tensor cores when the cost has its tensor maps, else on
   // the CUDA cores
-  cudaError_t kapply_row(int fb, int gb, const float* Z, float* out, cudaStream_t s) {
-    if (!hP.has_tmC) return launch_rowacc(krow_args(fb, gb, Z, out), kr_nrowblk, s);
-    cudaError_t e = launch_build_tiles(Z, m, p, tilesY, s);
-    if (e == cudaSuccess) e = launch_rowmma(rmma_args(fb, gb, Z, out), tilesY, rm_nrowblk, s);
+  cudaError_t kapply_row(int fb, int gb, const float* Z, float* out, cudaStream_t s,
+                         const int* skip = nullptr) {
+    if (!hP.has_tmC) {
+      AccArgs a = krow_args(fb, gb, Z, out);
+      a.skip = skip;
+      return launch_rowacc(a, kr_nrowblk, s);
+    }
+    cudaError_t e = launch_build_tiles(Z, m, p, tilesY, s, skip);
+    AccArgs a = rmma_args(fb, gb, Z, out);
+    a.skip = skip;
+    if (e == cudaSuccess) e = launch_rowmma(a, tilesY, rm_nrowblk, s);
     return e;
   }
   // The captured graphs bake in the choice between the staged (tensor-map)
@@ -760,11 +784,79 @@ struct Solver {
     launch_eig_gram(Xb, Zb, hP.a, n, p, eppart, GXX, Tm, cvec, s);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    launch_eig_small(p, ell, 1, GXX, Tm, cvec, Bm, theta, resid, efail, s);
+    launch_eig_small(p, ell, 1, GXX, Tm, cvec, Bm, theta, resid, efail, s, Qm);
+    // the residuals of the Ritz pairs, formed from the residual vectors
+    launch_ritz(Zb, Xb, cvec, Qm, theta, hP.a, n, p, ell, eppart, nullptr, nullptr, csig, resid,
+                ctx->nsm, s);
     apply_kernel<<<ceil_div(n, 64), 256, (size_t)(p * p + 64 * p) * 4, s>>>(Xb, cvec, Bm, n, p,
-                                                                           Zb);
+                                                                           Zb, nullptr);
     eig_ctl_kernel<<<1, 1, 0, s>>>(dSt, resid, efail);
     return cudaGetLastError();
+  }
+
+  // One step of the Chebyshev-filtered mode computation (filter degree d >= 2):
+  // the Rayleigh-Ritz step of body_eig on the block Z, then, unless that step
+  // met the stopping test, the filter T_d on the Ritz vectors (d - 1 more
+  // products, the scaled recurrence of cheb_step_kernel) and the
+  // column-scaled Cholesky-QR of the result into Z.  The
+  // kernels after the test are given the loop's done flag and return at once
+  // when it is set, so that Z then keeps the plain step's block.
+  cudaError_t body_cheb(cudaStream_t s, int fb, int gb, int degree) {
+    const int* done = &dSt->eig_done;
+    cudaError_t e = launch_build_tiles(Zb, n, p, tilesZ, s);
+    if (e == cudaSuccess) e = launch_colmma(kcol_args(fb, gb, Zb, Yb), hP, tilesZ, mm_ncolblk, s);
+    if (e == cudaSuccess) e = kapply_row(fb, gb, Yb, Xb, s);
+    if (e != cudaSuccess) return e;
+    launch_eig_gram(Xb, Zb, hP.a, n, p, eppart, GXX, Tm, cvec, s);
+    launch_eig_small(p, ell, 1, GXX, Tm, cvec, Bm, theta, resid, efail, s, Qm);
+    // the Ritz residuals, and Y_0 = Z Q, Y_1 from the product already formed
+    // (before the power step below overwrites Z)
+    launch_ritz(Zb, Xb, cvec, Qm, theta, hP.a, n, p, ell, eppart, F0, F1, csig, resid, ctx->nsm,
+                s);
+    eig_ctl_kernel<<<1, 1, 0, s>>>(dSt, resid, efail);
+    apply_kernel<<<ceil_div(n, 64), 256, (size_t)(p * p + 64 * p) * 4, s>>>(Xb, cvec, Bm, n, p,
+                                                                           Zb, nullptr);
+    float* Yp = F0;
+    float* Yc = F1;
+    for (int k = 2; k <= degree; ++k) {
+      AccArgs ka = kcol_args(fb, gb, Yc, Yb);
+      ka.skip = done;
+      e = launch_build_tiles(Yc, n, p, tilesZ, s, done);
+      if (e == cudaSuccess) e = launch_colmma(ka, hP, tilesZ, mm_ncolblk, s);
+      if (e == cudaSuccess) e = kapply_row(fb, gb, Yb, Xb, s, done);
+      if (e != cudaSuccess) return e;
+      launch_cheb_step(Xb, hP.a, Yc, Yp, n, p, k, csig, eppart, ctx->nsm, done, s);
+      std::swap(Yp, Yc);   // Yc holds Y_k
+    }
+    // the filtered block's Cholesky-QR (columns scaled first) into Z
+    launch_eig_gram(Yc, nullptr, hP.a, n, p, eppart, GXX, nullptr, cvec, s, done);
+    launch_eig_small(p, ell, 2, GXX, Tm, cvec, Bm, theta, resid, efail, s, nullptr, done);
+    apply_kernel<<<ceil_div(n, 64), 256, (size_t)(p * p + 64 * p) * 4, s>>>(Yc, cvec, Bm, n, p,
+                                                                           Zb, done);
+    return cudaGetLastError();
+  }
+
+  // Kernel launches of one body of the mode loop (the loop control included).
+  int eig_body_launches() const {
+    const int plain = 14;   // tiles, two products (3), Gram (2), RR, residual (2), apply, ctl, loop
+    const int dg = eig_graph_degree >= 2 ? eig_graph_degree : 0;
+    return dg ? plain + (dg - 1) * 6 + 4 : plain;
+  }
+
+  // The mode loop's graph for a filter degree (captured again when it changes;
+  // degrees 0 and 1 are the plain subspace iteration).
+  eot_status ensure_eig_graph(int degree) {
+    const int dg = degree >= 2 ? degree : 0;
+    if (ex_eig && eig_graph_degree == dg) return EOT_OK;
+    if (ex_eig) cudaGraphExecDestroy(ex_eig);
+    if (gr_eig) cudaGraphDestroy(gr_eig);
+    ex_eig = nullptr;
+    gr_eig = nullptr;
+    eot_status e = build_loop(
+        [&](cudaStream_t cs_) { return dg ? body_cheb(cs_, 0, 0, dg) : body_eig(cs_, 0, 0); }, 1,
+        &gr_eig, &ex_eig);
+    if (e == EOT_OK) eig_graph_degree = dg;
+    return e;
   }
 
   // Capture `body` into a graph; with conditional nodes, wrap it in a while loop.
@@ -970,6 +1062,8 @@ static eot_status validate(const eot_problem* pr, const eot_options* o) {
   if (o->ell > 0 && o->ell + 1 > kMaxP) return fail(EOT_EINVAL, "ell must be <= 47");
   if (o->oversample < 0) return fail(EOT_EINVAL, "oversample must be >= 0");
   if (o->stall_window < 0) return fail(EOT_EINVAL, "stall_window must be >= 0");
+  if (o->eig_degree < 0 || o->eig_degree > kMaxChebDegree)
+    return fail(EOT_EINVAL, "eig_degree must be in [0, 8]");
   if ((long long)pr->n * pr->m > (1ll << 34)) return fail(EOT_EINVAL, "n*m too large");
   return EOT_OK;
 }
@@ -1175,8 +1269,9 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
     eot_status e = S->build_loop([&](cudaStream_t cs_) { return S->body_sknr(cs_); }, 0,
                                  &S->gr_sknr, &S->ex_sknr);
     if (e != EOT_OK) return e;
-    e = S->build_loop([&](cudaStream_t cs_) { return S->body_eig(cs_, 0, 0); }, 1, &S->gr_eig,
-                      &S->ex_eig);
+  }
+  if (ell > 0) {
+    eot_status e = S->ensure_eig_graph(o->eig_degree);
     if (e != EOT_OK) return e;
   }
   // ---- levels ----
@@ -1288,7 +1383,7 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
       CUDA_TRY(cudaGetLastError());
       launch_eig_small(S->p, ell, 0, S->GXX, S->Tm, S->cvec, S->Bm, S->theta, S->resid, S->efail, s);
       apply_kernel<<<ceil_div(n, 64), 256, (size_t)(S->p * S->p + 64 * S->p) * 4, s>>>(
-          S->Xb, S->cvec, S->Bm, n, S->p, S->Zb);
+          S->Xb, S->cvec, S->Bm, n, S->p, S->Zb, nullptr);
       eig_setup_kernel<<<1, 1, 0, s>>>(S->dSt, o->eig_tol, o->eig_max_iter,
                                        o->eig_max_iter + 4);
       eot_status e = S->run_loop(S->ex_eig, 1, o->eig_max_iter + 5);
@@ -1359,7 +1454,7 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
     else launches += (long long)hLev[t].body_runs * (2 * S->unroll_sk + 1);
     if (lev_eig[t]) {
       r.eig_iters += hLev[L + t].eig_iter;
-      launches += 1 + 3 + 1 + 1 + 1 + (long long)hLev[L + t].body_runs * 12 + 1;
+      launches += 1 + 3 + 1 + 1 + 1 + (long long)hLev[L + t].body_runs * S->eig_body_launches() + 1;
     }
   }
   launches += 5 + 2LL * verify_rounds;
@@ -2355,7 +2450,19 @@ eot_status eot_spectral_modes(int32_t n, int32_t m, const float* C, const double
                               int32_t ell, int32_t oversample, double tol, int32_t max_iter,
                               int32_t use_V_as_start, double* V, double* rho2,
                               int32_t* iters_out, double* resid_out, void* stream) {
+  return eot_spectral_modes_filtered(n, m, C, f, g, a, b, eps, ell, oversample, 0, tol, max_iter,
+                                     use_V_as_start, V, rho2, iters_out, resid_out, stream);
+}
+
+eot_status eot_spectral_modes_filtered(int32_t n, int32_t m, const float* C, const double* f,
+                                       const double* g, const double* a, const double* b,
+                                       double eps, int32_t ell, int32_t oversample,
+                                       int32_t degree, double tol, int32_t max_iter,
+                                       int32_t use_V_as_start, double* V, double* rho2,
+                                       int32_t* iters_out, double* resid_out, void* stream) {
   if (!C || !f || !g || !a || !b || !V) return fail(EOT_EINVAL, "null pointer");
+  if (degree < 0 || degree > kMaxChebDegree)
+    return fail(EOT_EINVAL, "the filter degree must be in [0, 8]");
   if (ell < 1 || oversample < 0 || ell + 1 > kMaxP || ell >= n)
     return fail(EOT_EINVAL, "need 1 <= ell < n and ell < 48");
   if (!finite_pos(eps) || !(tol > 0.0) || max_iter < 1) return fail(EOT_EINVAL, "bad eps/tol/max_iter");
@@ -2369,11 +2476,8 @@ eot_status eot_spectral_modes(int32_t n, int32_t m, const float* C, const double
   st = standalone_grid(S, C, f, n, g, m, eps, s, nullptr);
   if (st != EOT_OK) return st;
   S->match_graphs_to_cost();
-  if (!S->ex_eig) {
-    st = S->build_loop([&](cudaStream_t cs_) { return S->body_eig(cs_, 0, 0); }, 1, &S->gr_eig,
-                       &S->ex_eig);
-    if (st != EOT_OK) return st;
-  }
+  st = S->ensure_eig_graph(degree);
+  if (st != EOT_OK) return st;
   Prob& P = S->hP;
   CUDA_TRY(cudaMemcpyAsync(P.f[0], f, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(P.g[0], g, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -2395,7 +2499,7 @@ eot_status eot_spectral_modes(int32_t n, int32_t m, const float* C, const double
   CUDA_TRY(cudaGetLastError());
   launch_eig_small(p, ell, 0, S->GXX, S->Tm, S->cvec, S->Bm, S->theta, S->resid, S->efail, s);
   apply_kernel<<<ceil_div(n, 64), 256, (size_t)(p * p + 64 * p) * 4, s>>>(S->Xb, S->cvec, S->Bm, n,
-                                                                         p, S->Zb);
+                                                                         p, S->Zb, nullptr);
   eig_setup_kernel<<<1, 1, 0, s>>>(S->dSt, tol, max_iter, max_iter + 4);
   st = S->run_loop(S->ex_eig, 1, max_iter + 5);
   if (st != EOT_OK) return st;

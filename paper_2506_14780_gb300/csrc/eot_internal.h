@@ -16,6 +16,10 @@ constexpr int kThreads = 256;
 constexpr int kMaxK = 64;
 // Widest block of the subspace iteration (modes + oversampling).
 constexpr int kMaxP = 48;
+// Chebyshev filter of the subspace iteration: highest degree, and the doubles
+// of its state (c, e, sigma_1, sigma_k at 4 + k).
+constexpr int kMaxChebDegree = 8;
+constexpr int kChebSigDoubles = 16;
 
 // What the grid-wide final step of a pass does with its reductions.
 enum PassMode : int {
@@ -181,6 +185,7 @@ struct AccArgs {
   double* dw;            // (m) gradient weights d_j (SK-NR)
   double* wtw_part;      // [nblk][k*k + k] block partials (SK-NR)
   int cluster;           // staged kernel: merge a block's segments in a cluster (nseg <= 8)
+  const int* skip;       // products: nonzero *skip makes the launch return at once (NULL: run)
 };
 
 #ifdef __CUDACC__

@@ -22,13 +22,15 @@ __global__ void loop_ctl_kernel(cudaGraphConditionalHandle h, State* st, int whi
 }
 
 // Convergence bookkeeping of the mode computation after a Rayleigh-Ritz step.
+// A residual that is not a finite number (the block broke down) stops the
+// loop as not converged.
 __global__ void eig_ctl_kernel(State* st, const double* resid, const int* fail) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   st->eig_iter += 1;
   st->eig_resid = *resid;
   if (*fail) { st->eig_fail += 1; }
   if (*resid <= st->eig_tol) st->eig_done = 1;
-  else if (st->eig_iter >= st->eig_max_iter) st->eig_done = 2;
+  else if (st->eig_iter >= st->eig_max_iter || !isfinite(*resid)) st->eig_done = 2;
 }
 
 // Level set-up: write the level's eps-dependent constants into the problem and

@@ -39,7 +39,8 @@ constexpr double kNrRangeLn = 60.0 * 0.6931471805599453;   // |ln column sum| bo
 // (the k index, padded with zeros) of 32 floats (the chunk's rows of Z), part 0
 // the TF32-rounded value, part 1 the TF32-rounded remainder.
 __global__ void build_tiles_kernel(const float* __restrict__ Z, int n, int kk, int NN,
-                                   float* __restrict__ tiles) {
+                                   float* __restrict__ tiles, const int* __restrict__ skip) {
+  if (skip && *skip) return;
   const int nch = (n + kMmaKC - 1) / kMmaKC;
   const long total = (long)nch * NN * kMmaKC;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
@@ -494,6 +495,7 @@ __global__ void __launch_bounds__(256) colmma_kernel(AccArgs args, const float* 
   State* st = P.st;
   const bool s4 = args.mode == ACC_S4;
   if (s4 && st->done) return;
+  if (args.skip && *args.skip) return;
   const int fb = s4 ? st->cur_f : args.fbuf;
   const int gb = s4 ? st->cur_g : args.gbuf;
   const int dst_g = (st->cur_g + 1) % 3;
@@ -815,6 +817,7 @@ __global__ void __launch_bounds__(kTmThreads, 2)
   State* st = P.st;
   const bool s4 = !ROW && args.mode == ACC_S4;
   if (s4 && st->done) return;
+  if (args.skip && *args.skip) return;   // uniform over the grid (and any cluster)
   const int fb = s4 ? st->cur_f : args.fbuf;
   const int gb = s4 ? st->cur_g : args.gbuf;
   const int dst_g = (st->cur_g + 1) % 3;
@@ -1201,11 +1204,12 @@ cudaError_t launch_rowmma(const AccArgs& a, const float* tiles, int nrowblk, cud
   }
 }
 
-cudaError_t launch_build_tiles(const float* Z, int n, int kk, float* tiles, cudaStream_t s) {
+cudaError_t launch_build_tiles(const float* Z, int n, int kk, float* tiles, cudaStream_t s,
+                               const int* skip) {
   const int NN = mma_width(kk);
   const long total = (long)((n + kMmaKC - 1) / kMmaKC) * NN * kMmaKC;
   const int blocks = (int)((total + 255) / 256);
-  build_tiles_kernel<<<blocks < 4096 ? blocks : 4096, 256, 0, s>>>(Z, n, kk, NN, tiles);
+  build_tiles_kernel<<<blocks < 4096 ? blocks : 4096, 256, 0, s>>>(Z, n, kk, NN, tiles, skip);
   return cudaGetLastError();
 }
 

@@ -35,7 +35,9 @@ constexpr int kEGRows = 64;      // rows staged in shared memory at a time
 __global__ void __launch_bounds__(256) eig_gram_kernel(const float* __restrict__ X,
                                                        const float* __restrict__ Z,
                                                        const double* __restrict__ w, int len,
-                                                       int p, float* __restrict__ part) {
+                                                       int p, float* __restrict__ part,
+                                                       const int* __restrict__ skip) {
+  if (skip && *skip) return;
   extern __shared__ float sm[];
   float* sX = sm;                         // [kEGRows][p]
   float* sZ = sX + kEGRows * p;           // [kEGRows][p]
@@ -140,7 +142,9 @@ __global__ void __launch_bounds__(64) eig_gram_reduce_kernel(const float* __rest
                                                              int nch, int p, int withT,
                                                              double* __restrict__ G,
                                                              double* __restrict__ T,
-                                                             double* __restrict__ c) {
+                                                             double* __restrict__ c,
+                                                             const int* __restrict__ skip) {
+  if (skip && *skip) return;
   const int rec = 2 * p * p + p;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= rec) return;
@@ -165,12 +169,13 @@ __global__ void __launch_bounds__(64) eig_gram_reduce_kernel(const float* __rest
 }
 
 void launch_eig_gram(const float* X, const float* Z, const double* w, int len, int p,
-                     float* part, double* G, double* T, double* c, cudaStream_t s) {
+                     float* part, double* G, double* T, double* c, cudaStream_t s,
+                     const int* skip) {
   const int nch = std::max(1, std::min(kEGMaxChunks, (len + kEGRows - 1) / kEGRows));
   const size_t sm = ((size_t)2 * kEGRows * p + kEGRows) * sizeof(float);
-  eig_gram_kernel<<<nch, 256, sm, s>>>(X, Z, w, len, p, part);
+  eig_gram_kernel<<<nch, 256, sm, s>>>(X, Z, w, len, p, part, skip);
   const int rec = 2 * p * p + p;
-  eig_gram_reduce_kernel<<<(rec + 63) / 64, 64, 0, s>>>(part, nch, p, Z ? 1 : 0, G, T, c);
+  eig_gram_reduce_kernel<<<(rec + 63) / 64, 64, 0, s>>>(part, nch, p, Z ? 1 : 0, G, T, c, skip);
 }
 
 // ---------------------------------------------------------------------------
@@ -178,8 +183,11 @@ void launch_eig_gram(const float* X, const float* Z, const double* w, int len, i
 // lower triangle read), pivots 0..p-1, NB pivots at a time (right-looking,
 // outer products, no square roots).  Rows p..rows-1 are right-hand sides that
 // ride along as extra rows: their first p entries end as L1^{-1} b.  On
-// return H[r][j] = L1_rj D_j (r > j), H[j][j] = D_j, inv[j] = 1 / D_j, and
-// *fail = 1 if a pivot was not positive and finite (its inv is then 0).
+// return H[r][j] = L1_rj D_j (r > j), H[j][j] = D_j, inv[j] = 1 / D_j.  A pivot
+// that is not finite or not above `tiny` gets inv 0 (its column then takes no
+// part in the later updates) and sets *fail, except that with null_ok a pivot
+// of exactly 0 (a zero row and column: a direction that is not there) does
+// not count as a failure.
 // Every thread factors the NB x NB diagonal block in registers from shared
 // memory (no barrier for it); the panel below it and the trailing update take
 // one barrier each, NB pivots per pair of barriers instead of one barrier per
@@ -188,7 +196,8 @@ void launch_eig_gram(const float* X, const float* Z, const double* w, int len, i
 // elimination.  Called by every thread of the CTA.
 // ---------------------------------------------------------------------------
 template <int NB>
-__device__ void ldlt_blocked(float* H, int S, int p, int rows, float* inv, int* fail) {
+__device__ void ldlt_blocked(float* H, int S, int p, int rows, float* inv, int* fail, float tiny,
+                             bool null_ok) {
   const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
   const int NY = nt >> 4, ty = tid >> 4, tx = tid & 15;   // 16-wide tiling of the update
   for (int k0 = 0; k0 < p; k0 += NB) {
@@ -213,7 +222,7 @@ __device__ void ldlt_blocked(float* H, int S, int p, int rows, float* inv, int* 
 #pragma unroll
         for (int u = 0; u < j; ++u) t = __fmaf_rn(-(w[j][u] * di[u]), w[j][u], t);
         d[j] = t;
-        const bool ok = t > 0.f && isfinite(t);
+        const bool ok = t > tiny && isfinite(t);
         di[j] = ok ? 1.f / t : 0.f;
       }
     }
@@ -259,7 +268,7 @@ __device__ void ldlt_blocked(float* H, int S, int p, int rows, float* inv, int* 
           for (int i = 0; i < j; ++i) H[(k0 + j) * S + k0 + i] = w[j][i];
           H[(k0 + j) * S + k0 + j] = d[j];
           inv[k0 + j] = di[j];
-          if (!(d[j] > 0.f && isfinite(d[j]))) *fail = 1;
+          if (di[j] == 0.f && !(null_ok && d[j] == 0.f)) *fail = 1;
         }
       }
     }
@@ -305,7 +314,7 @@ __global__ void __launch_bounds__(256) newton_kernel(const Prob* __restrict__ PP
   __syncthreads();
   // elimination (8 pivots per pair of barriers): H[r][k] = L_rk D_k (r > k),
   // H[k][k] = D_k, and row l holds the forward-substituted right-hand side
-  ldlt_blocked<8>(H, kS, l, l + 1, s_inv, &s_fail);
+  ldlt_blocked<8>(H, kS, l, l + 1, s_inv, &s_fail, 0.f, true);
   if (tid >= 32) return;
   for (int k = lane; k < l; k += 32) g[k] = H[l * kS + k];
   __syncwarp();
@@ -392,7 +401,11 @@ __global__ void fprime_kernel(const Prob* __restrict__ PP) {
 //           the circle ordering, descending Ritz values),
 //           residual_k^2 = (Q^T GXX Q)_kk - theta_k^2, then
 //           L L^T = Q^T (GXX - c c^T) Q and B = Q L^{-T}.
-//   outputs B (p x p float32), theta (p), max residual over the first l.
+//   mode 2 (orthonormalise a badly scaled block): as mode 0 with the columns
+//           scaled first, Q = diag((GXX - c c^T)_kk^(-1/2)), B = Q L^{-T}.
+//   outputs B (p x p float32), theta (p), max residual over the first l
+//   (mode 1), and (mode 1, when Qout is given) the Ritz rotation Q.  A
+//   nonzero *skip makes the launch return at once.
 // Launched as one CTA of kMaxP/2 x kMaxP/2 threads (launch_eig_small).
 // ---------------------------------------------------------------------------
 constexpr int kEH = kMaxP / 2;   // at most kEH x kEH threads: one per pair of pairs
@@ -472,7 +485,10 @@ __global__ void __launch_bounds__(kEH * kEH) eig_small_kernel(int p, int l, int 
                                                               float* __restrict__ Bout,
                                                               double* __restrict__ theta_out,
                                                               double* __restrict__ resid_out,
-                                                              int* __restrict__ fail_out) {
+                                                              int* __restrict__ fail_out,
+                                                              float* __restrict__ Qout,
+                                                              const int* __restrict__ skip) {
+  if (skip && *skip) return;
   __shared__ float A0[kMaxP * kES];
   __shared__ float Q[kMaxP * kES];
   __shared__ __align__(16) float G[kMaxP * kES];
@@ -616,7 +632,14 @@ __global__ void __launch_bounds__(kEH * kEH) eig_small_kernel(int p, int l, int 
         cur ^= 1;
       }
     }
-    for (int k = tid; k < p; k += nt) th[k] = A[k * kES + k];
+    // descending order of the Ritz values by a strict total order (a value
+    // that is not a number sorts last, ties by index), so that the ranks are
+    // always a permutation of 0..p-1 and every order[] entry is written
+    for (int k = tid; k < p; k += nt) {
+      const float v = A[k * kES + k];
+      th[k] = v == v ? v : -INFINITY;
+      if (v != v) s_fail = 1;
+    }
     __syncthreads();
     for (int k = tid; k < p; k += nt) {
       int rank = 0;
@@ -629,18 +652,30 @@ __global__ void __launch_bounds__(kEH * kEH) eig_small_kernel(int p, int l, int 
     if (tid < p) theta_out[tid] = (double)th[order[tid]];
     __syncthreads();
     for (int r = ty; r < p; r += nx)
-      for (int q = tx; q < p; q += nx) Q[r * kES + q] = G[r * kES + q];
+      for (int q = tx; q < p; q += nx) {
+        Q[r * kES + q] = G[r * kES + q];
+        if (Qout) Qout[r * p + q] = G[r * kES + q];   // the Ritz rotation, for the filter
+      }
   } else {
     for (int r = ty; r < p; r += nx)
       for (int q = tx; q < p; q += nx) Q[r * kES + q] = (r == q) ? 1.f : 0.f;
   }
   __syncthreads();
   A = A0;
-  // G = GXX - c c^T (float), then (mode 1) G <- Q^T G Q
+  // G = GXX - c c^T (float), then (modes 1, 2) G <- Q^T G Q
   for (int r = ty; r < p; r += nx)
     for (int q = tx; q < p; q += nx) G[r * kES + q] = (float)(GXX[r * p + q] - c[r] * c[q]);
   __syncthreads();
-  if (mode == 1) {
+  if (mode == 2) {
+    // column scaling Q = diag(G_kk^(-1/2)): the block's columns may differ in
+    // scale by orders of magnitude (a filtered block), which the Cholesky
+    // factor of the scaled Gram matrix does not inherit
+    for (int r = ty; r < p; r += nx)
+      for (int q = tx; q < p; q += nx)
+        Q[r * kES + q] = (r == q) ? rsqrtf(fmaxf(G[r * kES + r], 1e-30f)) : 0.f;
+    __syncthreads();
+  }
+  if (mode >= 1) {
     // W = G Q: thread (ty, tx) forms rows ty, ty + nx and columns tx, tx + nx
     // (p <= 2 nx), each loaded value used twice
     block2_product(G, Q, W, p, ty, tx, nx, false);
@@ -655,7 +690,7 @@ __global__ void __launch_bounds__(kEH * kEH) eig_small_kernel(int p, int l, int 
     __syncthreads();
     // residual_k^2 = (Q^T GXX Q)_kk - theta_k^2 = G'_kk + (Q^T c)_k^2 - theta_k^2
     float rmax = 0.f;
-    for (int k = tid; k < l && k < p; k += nt) {
+    for (int k = tid; mode == 1 && k < l && k < p; k += nt) {
       const float t = (float)theta_out[k];
       const float r2 = A[k * kES + k] + qc[k] * qc[k] - t * t;
       rmax = fmaxf(rmax, r2 > 0.f ? sqrtf(r2) : 0.f);
@@ -664,7 +699,7 @@ __global__ void __launch_bounds__(kEH * kEH) eig_small_kernel(int p, int l, int 
     for (int o = 16; o > 0; o >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
     if ((tid & 31) == 0) red[tid >> 5] = rmax;
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && mode == 1) {
       float mx = 0.f;
       for (int w = 0; w < (nt + 31) / 32; ++w) mx = fmaxf(mx, red[w]);
       *resid_out = (double)mx;
@@ -674,11 +709,23 @@ __global__ void __launch_bounds__(kEH * kEH) eig_small_kernel(int p, int l, int 
     __syncthreads();
   }
   // G = L1 D L1^T (8 pivots per pair of barriers; th: scratch for 1 / D,
-  // the Ritz values are written out); L = L1 D^(1/2)
-  ldlt_blocked<8>(G, kES, p, p, th, &s_fail);
+  // the Ritz values are written out); L = L1 D^(1/2).  A pivot below 1e-9 of
+  // the largest diagonal entry (the block has lost rank: at large eps only a
+  // few rho_k^2 are not negligible) marks its column dead: the column becomes
+  // exactly zero (sq = 0) instead of amplified rounding noise, which would
+  // overflow in the next products.
+  if (tid == 0) {
+    float mx = 0.f;
+    for (int k = 0; k < p; ++k) mx = fmaxf(mx, G[k * kES + k]);
+    red[0] = fmaxf(1e-9f * mx, 1e-30f);
+  }
+  __syncthreads();
+  const float tiny = red[0];
+  __syncthreads();
+  ldlt_blocked<8>(G, kES, p, p, th, &s_fail, tiny, false);
   for (int k = tid; k < p; k += nt) {
     const float dk = G[k * kES + k];
-    sq[k] = dk > 0.f ? rsqrtf(dk) : 1.f;   // 1 / L_kk
+    sq[k] = th[k] > 0.f ? rsqrtf(dk) : 0.f;   // 1 / L_kk; 0: dead column
   }
   __syncthreads();
   // L below the diagonal: L_cq = G_cq / sqrt(D_q) (one product per element)
@@ -734,9 +781,10 @@ __global__ void __launch_bounds__(kEH * kEH) eig_small_kernel(int p, int l, int 
 
 void launch_eig_small(int p, int l, int mode, const double* GXX, const double* T,
                       const double* c, float* B, double* theta, double* resid, int* fail,
-                      cudaStream_t s) {
+                      cudaStream_t s, float* Qout, const int* skip) {
   const int half = std::max(4, ((p + 1) & ~1) / 2);   // one thread per pair of pairs
-  eig_small_kernel<<<1, dim3(half, half), 0, s>>>(p, l, mode, GXX, T, c, B, theta, resid, fail);
+  eig_small_kernel<<<1, dim3(half, half), 0, s>>>(p, l, mode, GXX, T, c, B, theta, resid, fail,
+                                                  Qout, skip);
 }
 
 // Z_i <- (X_i - c) B   (len x p, float32), c float64 (deflation of the constant).
@@ -744,7 +792,9 @@ void launch_eig_small(int p, int l, int mode, const double* GXX, const double* T
 __global__ void __launch_bounds__(256) apply_kernel(const float* __restrict__ X,
                                                     const double* __restrict__ c,
                                                     const float* __restrict__ B, int len, int p,
-                                                    float* __restrict__ Z) {
+                                                    float* __restrict__ Z,
+                                                    const int* __restrict__ skip) {
+  if (skip && *skip) return;
   extern __shared__ float sB[];
   float* sX = sB + p * p;   // [64][p]
   for (int e = threadIdx.x; e < p * p; e += blockDim.x) sB[e] = B[e];
@@ -763,6 +813,202 @@ __global__ void __launch_bounds__(256) apply_kernel(const float* __restrict__ X,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Chebyshev-filtered subspace iteration (Sec. 3: the rho^2 cluster near 1 slows
+// the plain power method; Sec. 4 asks for an efficient power method).  Between
+// two Rayleigh-Ritz steps the Ritz vectors Zr = Z Q are multiplied by the
+// Chebyshev polynomial T_d((M - c)/e) with [c - e, c + e] = [0, cut] covering
+// the spectrum below the block's smallest Ritz value theta_{p-1} (cut is at
+// least 1e-6 theta_0): the part of the spectrum below it stays bounded while
+// the wanted eigenvalues grow like cosh(d arccosh x).  The three-term
+// recurrence is the scaled one of Zhou and Saad (2007), which divides step k
+// by T_k at theta_0 so that the leading components stay of order one in
+// float32 (the same span as the unscaled recurrence):
+//   sigma_1 = e / (theta_0 - c),  Y_1 = (sigma_1 / e) (M - c) Y_0,
+//   sigma_k = 1 / (2 / sigma_1 - sigma_{k-1}),
+//   Y_k = (2 sigma_k / e) (M - c) Y_{k-1} - sigma_{k-1} sigma_k Y_{k-2}.
+// Every product M Y is deflated of the constant mode (Y - 1 a^T Y).  sig holds
+// c, e, sigma_1 and sigma_k at sig[4 + k].  A nonzero *skip (the mode loop
+// has converged) makes each step's launches return at once.
+// ---------------------------------------------------------------------------
+static_assert(kChebSigDoubles >= 5 + kMaxChebDegree, "filter state");
+
+// The Ritz pairs of a Rayleigh-Ritz step, z_k = (Z Q)_k and M z_k = ((X - 1 c^T)
+// Q)_k (X = M Z), and the a-norms of their residuals r_k = M z_k - theta_k z_k,
+// k < l, formed from the residual vectors themselves (the Gram-matrix identity
+// |r_k|^2 = |M z_k|^2 - theta_k^2 cancels to a float32 floor near 1e-3): per
+// CTA (64-row tiles, grid-stride) thread (group g, column q) adds
+// a_i r_iq^2 over its rows in a fixed order, and the CTA's partials go to
+// part[b][q] (deterministic).  With Y0, Y1 given it also starts the Chebyshev
+// filter: Y_0 = Z Q, Y_1 = (sigma_1 / e) (M Z Q - c Z Q), and writes the
+// filter's scalars into sig.
+__global__ void __launch_bounds__(256) ritz_kernel(const float* __restrict__ Z,
+                                                   const float* __restrict__ X,
+                                                   const double* __restrict__ cx,
+                                                   const float* __restrict__ Q,
+                                                   const double* __restrict__ theta,
+                                                   const double* __restrict__ a, int len, int p,
+                                                   int l, float* __restrict__ part,
+                                                   float* __restrict__ Y0, float* __restrict__ Y1,
+                                                   double* __restrict__ sig) {
+  extern __shared__ float sQ[];
+  float* sZ = sQ + p * p;   // [64][p]
+  float* sX = sZ + 64 * p;  // [64][p]
+  __shared__ float red[4][64];
+  const int q = threadIdx.x & 63, g = threadIdx.x >> 6;   // column, row group
+  double cs = 0.0, e = 1.0, s1 = 1.0;
+  if (Y0) {
+    const double t0 = theta[0];
+    const double cut = fmax(theta[p - 1], 1e-6 * t0);
+    cs = 0.5 * cut;
+    e = 0.5 * cut;
+    if (!(t0 > 0.0) || !(e > 0.0)) {   // no spectrum to separate: a plain power step
+      cs = 0.0;
+      e = 1.0;
+    }
+    s1 = (t0 > cs) ? e / (t0 - cs) : 1.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      sig[0] = cs;
+      sig[1] = e;
+      sig[2] = s1;
+      sig[5] = s1;
+    }
+  }
+  const float f1 = (float)(s1 / e), fc = (float)cs;
+  const float th = q < l ? (float)theta[q] : 0.f;
+  for (int i = threadIdx.x; i < p * p; i += blockDim.x) sQ[i] = Q[i];
+  float acc = 0.f;
+  const int ntiles = (len + 63) / 64;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int r0 = t * 64, nr = min(64, len - r0);
+    __syncthreads();   // the previous tile's rows are read
+    for (int i = threadIdx.x; i < 64 * p; i += blockDim.x) {
+      const int r = i / p, k = i - r * p;
+      sZ[i] = r < nr ? Z[(size_t)r0 * p + i] : 0.f;
+      sX[i] = r < nr ? X[(size_t)r0 * p + i] - (float)cx[k] : 0.f;
+    }
+    __syncthreads();
+    if (q < p) {
+      for (int r = g; r < nr; r += 4) {
+        float z = 0.f, x = 0.f;
+        for (int k = 0; k < p; ++k) {
+          z = __fmaf_rn(sZ[r * p + k], sQ[k * p + q], z);
+          x = __fmaf_rn(sX[r * p + k], sQ[k * p + q], x);
+        }
+        if (q < l) {
+          const float res = __fmaf_rn(-th, z, x);
+          acc = __fmaf_rn((float)a[r0 + r] * res, res, acc);
+        }
+        if (Y0) {
+          Y0[(size_t)(r0 + r) * p + q] = z;
+          Y1[(size_t)(r0 + r) * p + q] = f1 * __fmaf_rn(-fc, z, x);
+        }
+      }
+    }
+  }
+  red[g][q] = acc;
+  __syncthreads();
+  if (threadIdx.x < l) part[(size_t)blockIdx.x * l + threadIdx.x] =
+      (red[0][threadIdx.x] + red[1][threadIdx.x]) + (red[2][threadIdx.x] + red[3][threadIdx.x]);
+}
+
+// max_k |r_k|_a over the first l Ritz pairs from the nch partials (one CTA,
+// fixed order) into *resid.
+__global__ void __launch_bounds__(64) ritz_final_kernel(const float* __restrict__ part, int nch,
+                                                        int l, double* __restrict__ resid) {
+  __shared__ double r2[64];
+  const int q = threadIdx.x;
+  double t = 0.0;
+  if (q < l)
+    for (int b = 0; b < nch; ++b) t += (double)part[(size_t)b * l + q];
+  r2[q] = t;
+  __syncthreads();
+  if (q == 0) {
+    double mx = 0.0;
+    for (int k = 0; k < l; ++k) mx = (r2[k] == r2[k] && mx == mx) ? fmax(mx, r2[k]) : NAN;
+    *resid = sqrt(mx);   // NaN if any residual was (the loop then stops as failed)
+  }
+}
+
+// Partial sums a^T X over row ranges: part[b][k] for CTA b (8 warps over rows,
+// lanes over columns, fixed order).
+__global__ void __launch_bounds__(256) wsum_part_kernel(const float* __restrict__ X,
+                                                        const double* __restrict__ a, int len,
+                                                        int p, float* __restrict__ part,
+                                                        const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  __shared__ float red[8][kMaxP];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r_beg = (int)((long long)len * blockIdx.x / gridDim.x);
+  const int r_end = (int)((long long)len * (blockIdx.x + 1) / gridDim.x);
+  float s0 = 0.f, s1 = 0.f;
+  for (int i = r_beg + w; i < r_end; i += 8) {
+    const float ai = (float)a[i];
+    if (lane < p) s0 = __fmaf_rn(ai, X[(size_t)i * p + lane], s0);
+    if (lane + 32 < p) s1 = __fmaf_rn(ai, X[(size_t)i * p + lane + 32], s1);
+  }
+  if (lane < p) red[w][lane] = s0;
+  if (lane + 32 < p) red[w][lane + 32] = s1;
+  __syncthreads();
+  for (int k = threadIdx.x; k < p; k += blockDim.x) {
+    float t = 0.f;
+    for (int v = 0; v < 8; ++v) t += red[v][k];
+    part[(size_t)blockIdx.x * p + k] = t;
+  }
+}
+
+// Step k of the recurrence: Yp <- (2 sigma_k / e) ((X - 1 c^T) - c Yc) -
+// sigma_{k-1} sigma_k Yp, X = M Yc, c = a^T X from the nch partials.
+__global__ void __launch_bounds__(256) cheb_step_kernel(const float* __restrict__ X,
+                                                        const float* __restrict__ part, int nch,
+                                                        const float* __restrict__ Yc,
+                                                        float* __restrict__ Yp, int len, int p,
+                                                        int k, double* __restrict__ sig,
+                                                        const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  __shared__ float cx[kMaxP];
+  for (int q = threadIdx.x; q < p; q += blockDim.x) {
+    double t = 0.0;
+    for (int b = 0; b < nch; ++b) t += (double)part[(size_t)b * p + q];
+    cx[q] = (float)t;
+  }
+  const double cs = sig[0], e = sig[1], s1 = sig[2], sp = sig[4 + k - 1];
+  const double sk = 1.0 / (2.0 / s1 - sp);
+  if (blockIdx.x == 0 && threadIdx.x == 0) sig[4 + k] = sk;
+  __syncthreads();
+  const float fa = (float)(2.0 * sk / e), fb = (float)(sp * sk), fc = (float)cs;
+  const long long total = (long long)len * p;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(i % p);
+    const float mx = X[i] - cx[q];
+    Yp[i] = __fmaf_rn(fa, __fmaf_rn(-fc, Yc[i], mx), -fb * Yp[i]);
+  }
+}
+
+// The Ritz residuals (and, with Y0 given, the filter's start) into *resid;
+// part: at least 256 x l floats of scratch.
+void launch_ritz(const float* Z, const float* X, const double* cx, const float* Q,
+                 const double* theta, const double* a, int len, int p, int l, float* part,
+                 float* Y0, float* Y1, double* sig, double* resid, int nsm, cudaStream_t s) {
+  const int ntiles = (len + 63) / 64;
+  const int grid = std::max(1, std::min(ntiles, std::min(256, 2 * nsm)));
+  const size_t sm = ((size_t)p * p + 2 * 64 * p) * sizeof(float);
+  ritz_kernel<<<grid, 256, sm, s>>>(Z, X, cx, Q, theta, a, len, p, l, part, Y0, Y1, sig);
+  ritz_final_kernel<<<1, 64, 0, s>>>(part, grid, l, resid);
+}
+
+// One filter step after the product X = M Yc: the deflation sums and the
+// recurrence (part: at least 128 x p floats of scratch).
+void launch_cheb_step(const float* X, const double* a, const float* Yc, float* Yp, int len, int p,
+                      int k, double* sig, float* part, int nsm, const int* skip, cudaStream_t s) {
+  const int nch = std::max(1, std::min(128, (len + 31) / 32));
+  wsum_part_kernel<<<nch, 256, 0, s>>>(X, a, len, p, part, skip);
+  const long long total = (long long)len * p;
+  const int grid = (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 4LL * nsm));
+  cheb_step_kernel<<<grid, 256, 0, s>>>(X, part, nch, Yc, Yp, len, p, k, sig, skip);
+}
+
 // SplitMix64 start block (Steele, Lea & Flood 2014): u = top 53 bits / 2^53,
 // entry (i, k) uses counter seed + (i*p + k + 1) * gamma; columns < keep are
 // copied from src (n x keep, float32) instead.
@@ -771,8 +1017,11 @@ __global__ void init_block_kernel(float* __restrict__ Z, int len, int p, unsigne
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < len * p; e += gridDim.x * blockDim.x) {
     const int i = e / p, k = e - i * p;
     if (k < keep && src) {
-      Z[e] = src[(size_t)i * keep + k];
-      continue;
+      const float v = src[(size_t)i * keep + k];
+      if (v != 0.f) {   // a dead (zero) column of the previous modes is drawn anew
+        Z[e] = v;
+        continue;
+      }
     }
     unsigned long long z = seed + (unsigned long long)(e + 1) * 0x9E3779B97F4A7C15ull;
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;

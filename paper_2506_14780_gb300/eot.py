@@ -42,7 +42,8 @@ class eot_options(C.Structure):
                 ("sequential_modes", C.c_int32), ("oversample", C.c_int32),
                 ("eig_tol", C.c_double), ("eig_max_iter", C.c_int32), ("prec", C.c_int32),
                 ("hessian", C.c_int32), ("poll_every", C.c_int32), ("stream", C.c_void_p),
-                ("wait_limit_s", C.c_double), ("stall_window", C.c_int32)]
+                ("wait_limit_s", C.c_double), ("stall_window", C.c_int32),
+                ("eig_degree", C.c_int32)]
 
 
 class eot_result(C.Structure):
@@ -101,6 +102,11 @@ _SIGNATURES = {
                                      C.c_double, C.c_int32, C.c_int32, C.c_double, C.c_int32,
                                      C.c_int32, _PTR, _PTR, C.POINTER(C.c_int32),
                                      C.POINTER(C.c_double), _PTR]),
+    "eot_spectral_modes_filtered": (C.c_int, [C.c_int32, C.c_int32, _PTR, _PTR, _PTR, _PTR,
+                                              _PTR, C.c_double, C.c_int32, C.c_int32,
+                                              C.c_int32, C.c_double, C.c_int32, C.c_int32, _PTR,
+                                              _PTR, C.POINTER(C.c_int32),
+                                              C.POINTER(C.c_double), _PTR]),
     "eot_marginal_error": (C.c_int, [C.c_int32, C.c_int32, _PTR, _PTR, _PTR, _PTR, _PTR,
                                      C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                      _PTR]),
@@ -281,6 +287,19 @@ def eot_spectral_modes(n, m, Cdev, f, g, a, b, eps, ell, oversample, tol, max_it
                                    float(tol), max_iter, 1 if use_V_as_start else 0,
                                    V.data_ptr(), None if rho2 is None else rho2.data_ptr(),
                                    C.byref(it), C.byref(rs), stream)
+    return st, it.value, rs.value
+
+
+def eot_spectral_modes_filtered(n, m, Cdev, f, g, a, b, eps, ell, oversample, degree, tol,
+                                max_iter, use_V_as_start, V, rho2=None, stream=None):
+    it = C.c_int32(0)
+    rs = C.c_double(0.0)
+    st = load().eot_spectral_modes_filtered(n, m, Cdev.data_ptr(), f.data_ptr(), g.data_ptr(),
+                                            a.data_ptr(), b.data_ptr(), float(eps), ell,
+                                            oversample, degree, float(tol), max_iter,
+                                            1 if use_V_as_start else 0, V.data_ptr(),
+                                            None if rho2 is None else rho2.data_ptr(),
+                                            C.byref(it), C.byref(rs), stream)
     return st, it.value, rs.value
 
 
