@@ -98,7 +98,9 @@ typedef struct {
     double level_tol;       /* tolerance of intermediate levels (<= 0: use tol)        */
     int32_t sequential_modes; /* 1: recompute V at every level; 0: once at eps_start  */
     int32_t oversample;     /* extra block columns of the subspace iteration           */
-    double eig_tol;         /* Ritz residual ||M z - theta z||_a stopping threshold     */
+    double eig_tol;         /* Ritz residual ||M z - theta z||_a stopping threshold (below
+                               2e-3 formed from the residual vectors; above, from the
+                               Gram entries, whose float32 estimate floors near 6e-4) */
     int32_t eig_max_iter;   /* subspace iteration cap                                  */
     eot_prec prec;
     eot_hessian hessian;

@@ -89,7 +89,8 @@ __global__ void apply_kernel(const float*, const double*, const float*, int, int
                              const int*);
 void launch_ritz(const float* Z, const float* X, const double* cx, const float* Q,
                  const double* theta, const double* a, int len, int p, int l, float* part,
-                 float* Y0, float* Y1, double* sig, double* resid, int nsm, cudaStream_t s);
+                 unsigned* cnt, float* Y0, float* Y1, double* sig, double* resid, int nsm,
+                 cudaStream_t s);
 void launch_cheb_step(const float* X, const double* a, const float* Yc, float* Yp, int len, int p,
                       int k, double* sig, float* part, int nsm, const int* skip, cudaStream_t s);
 __global__ void init_block_kernel(float*, int, int, unsigned long long, const float*, int);
@@ -204,6 +205,10 @@ struct Arena {
     return p;
   }
 };
+
+// Stopping tolerance of the mode computation below which its residual is formed
+// from the residual vectors (the Gram-entry estimate floors near 6e-4).
+constexpr double kExplicitResidTol = 2e-3;
 
 static int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
@@ -385,7 +390,9 @@ struct Solver {
   // Ritz rotation and the filter's scalars
   float *F0 = nullptr, *F1 = nullptr, *Qm = nullptr;
   double* csig = nullptr;
+  unsigned* ritz_cnt = nullptr;   // arrival counter of the Ritz-residual kernel (rests at 0)
   int eig_graph_degree = -1;   // filter degree the mode loop's graph was captured with
+  bool eig_graph_explicit = false;   // ... and whether it forms the residual vectors
   // host mirrors
   State* hSt = nullptr;
   double* hScores = nullptr;
@@ -589,6 +596,7 @@ struct Solver {
       F1 = A.take<float>((size_t)n * p);
       Qm = A.take<float>((size_t)p * p);
       csig = A.take<double>(kChebSigDoubles);
+      ritz_cnt = A.take<unsigned>(1);
     }
   }
 
@@ -775,7 +783,10 @@ struct Solver {
     return e;
   }
 
-  cudaError_t body_eig(cudaStream_t s, int fb, int gb) {
+  // explicit: the stopping residual from the residual vectors (ritz_kernel);
+  // otherwise the Rayleigh-Ritz kernel's estimate from the Gram entries, whose
+  // absolute error near 6e-4 (float32) is harmless above kExplicitResidTol.
+  cudaError_t body_eig(cudaStream_t s, int fb, int gb, bool explicit_resid) {
     cudaError_t e = launch_build_tiles(Zb, n, p, tilesZ, s);
     if (e == cudaSuccess) e = launch_colmma(kcol_args(fb, gb, Zb, Yb), hP, tilesZ, mm_ncolblk, s);
     if (e == cudaSuccess) e = kapply_row(fb, gb, Yb, Xb, s);
@@ -784,10 +795,12 @@ struct Solver {
     launch_eig_gram(Xb, Zb, hP.a, n, p, eppart, GXX, Tm, cvec, s);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    launch_eig_small(p, ell, 1, GXX, Tm, cvec, Bm, theta, resid, efail, s, Qm);
+    launch_eig_small(p, ell, 1, GXX, Tm, cvec, Bm, theta, resid, efail, s,
+                     explicit_resid ? Qm : nullptr);
     // the residuals of the Ritz pairs, formed from the residual vectors
-    launch_ritz(Zb, Xb, cvec, Qm, theta, hP.a, n, p, ell, eppart, nullptr, nullptr, csig, resid,
-                ctx->nsm, s);
+    if (explicit_resid)
+      launch_ritz(Zb, Xb, cvec, Qm, theta, hP.a, n, p, ell, eppart, ritz_cnt, nullptr, nullptr,
+                  csig, resid, ctx->nsm, s);
     apply_kernel<<<ceil_div(n, 64), 256, (size_t)(p * p + 64 * p) * 4, s>>>(Xb, cvec, Bm, n, p,
                                                                            Zb, nullptr);
     eig_ctl_kernel<<<1, 1, 0, s>>>(dSt, resid, efail);
@@ -811,8 +824,8 @@ struct Solver {
     launch_eig_small(p, ell, 1, GXX, Tm, cvec, Bm, theta, resid, efail, s, Qm);
     // the Ritz residuals, and Y_0 = Z Q, Y_1 from the product already formed
     // (before the power step below overwrites Z)
-    launch_ritz(Zb, Xb, cvec, Qm, theta, hP.a, n, p, ell, eppart, F0, F1, csig, resid, ctx->nsm,
-                s);
+    launch_ritz(Zb, Xb, cvec, Qm, theta, hP.a, n, p, ell, eppart, ritz_cnt, F0, F1, csig, resid,
+                ctx->nsm, s);
     eig_ctl_kernel<<<1, 1, 0, s>>>(dSt, resid, efail);
     apply_kernel<<<ceil_div(n, 64), 256, (size_t)(p * p + 64 * p) * 4, s>>>(Xb, cvec, Bm, n, p,
                                                                            Zb, nullptr);
@@ -838,24 +851,30 @@ struct Solver {
 
   // Kernel launches of one body of the mode loop (the loop control included).
   int eig_body_launches() const {
-    const int plain = 14;   // tiles, two products (3), Gram (2), RR, residual (2), apply, ctl, loop
+    // tiles, two products (3), Gram (2), RR, [residual], apply, ctl, loop
+    const int plain = 12 + (eig_graph_explicit ? 1 : 0);
     const int dg = eig_graph_degree >= 2 ? eig_graph_degree : 0;
     return dg ? plain + (dg - 1) * 6 + 4 : plain;
   }
 
-  // The mode loop's graph for a filter degree (captured again when it changes;
-  // degrees 0 and 1 are the plain subspace iteration).
-  eot_status ensure_eig_graph(int degree) {
+  // The mode loop's graph for a filter degree and stopping tolerance (captured
+  // again when they change; degrees 0 and 1 are the plain subspace iteration,
+  // which forms the residual vectors only below kExplicitResidTol).
+  eot_status ensure_eig_graph(int degree, double tol) {
     const int dg = degree >= 2 ? degree : 0;
-    if (ex_eig && eig_graph_degree == dg) return EOT_OK;
+    const bool ex = dg > 0 || tol < kExplicitResidTol;
+    if (ex_eig && eig_graph_degree == dg && eig_graph_explicit == ex) return EOT_OK;
     if (ex_eig) cudaGraphExecDestroy(ex_eig);
     if (gr_eig) cudaGraphDestroy(gr_eig);
     ex_eig = nullptr;
     gr_eig = nullptr;
     eot_status e = build_loop(
-        [&](cudaStream_t cs_) { return dg ? body_cheb(cs_, 0, 0, dg) : body_eig(cs_, 0, 0); }, 1,
-        &gr_eig, &ex_eig);
-    if (e == EOT_OK) eig_graph_degree = dg;
+        [&](cudaStream_t cs_) { return dg ? body_cheb(cs_, 0, 0, dg) : body_eig(cs_, 0, 0, ex); },
+        1, &gr_eig, &ex_eig);
+    if (e == EOT_OK) {
+      eig_graph_degree = dg;
+      eig_graph_explicit = ex;
+    }
     return e;
   }
 
@@ -1271,7 +1290,7 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
     if (e != EOT_OK) return e;
   }
   if (ell > 0) {
-    eot_status e = S->ensure_eig_graph(o->eig_degree);
+    eot_status e = S->ensure_eig_graph(o->eig_degree, o->eig_tol);
     if (e != EOT_OK) return e;
   }
   // ---- levels ----
@@ -2476,7 +2495,7 @@ eot_status eot_spectral_modes_filtered(int32_t n, int32_t m, const float* C, con
   st = standalone_grid(S, C, f, n, g, m, eps, s, nullptr);
   if (st != EOT_OK) return st;
   S->match_graphs_to_cost();
-  st = S->ensure_eig_graph(degree);
+  st = S->ensure_eig_graph(degree, tol);
   if (st != EOT_OK) return st;
   Prob& P = S->hP;
   CUDA_TRY(cudaMemcpyAsync(P.f[0], f, n * sizeof(double), cudaMemcpyDeviceToDevice, s));

@@ -837,11 +837,13 @@ static_assert(kChebSigDoubles >= 5 + kMaxChebDegree, "filter state");
 // Q)_k (X = M Z), and the a-norms of their residuals r_k = M z_k - theta_k z_k,
 // k < l, formed from the residual vectors themselves (the Gram-matrix identity
 // |r_k|^2 = |M z_k|^2 - theta_k^2 cancels to a float32 floor near 1e-3): per
-// CTA (64-row tiles, grid-stride) thread (group g, column q) adds
-// a_i r_iq^2 over its rows in a fixed order, and the CTA's partials go to
-// part[b][q] (deterministic).  With Y0, Y1 given it also starts the Chebyshev
-// filter: Y_0 = Z Q, Y_1 = (sigma_1 / e) (M Z Q - c Z Q), and writes the
-// filter's scalars into sig.
+// CTA (16-row tiles, grid-stride) thread (group g, column q) adds
+// a_i r_iq^2 over its rows in a fixed order into part[b][q]; the last CTA to
+// arrive adds the CTAs' partials in a fixed order and writes max_k |r_k|_a to
+// *resid (NaN if any is not a number), then re-arms the counter.  With Y0, Y1
+// given it also starts the Chebyshev filter: Y_0 = Z Q, Y_1 = (sigma_1 / e)
+// (M Z Q - c Z Q), and writes the filter's scalars into sig.
+constexpr int kRitzRows = 16;
 __global__ void __launch_bounds__(256) ritz_kernel(const float* __restrict__ Z,
                                                    const float* __restrict__ X,
                                                    const double* __restrict__ cx,
@@ -849,12 +851,16 @@ __global__ void __launch_bounds__(256) ritz_kernel(const float* __restrict__ Z,
                                                    const double* __restrict__ theta,
                                                    const double* __restrict__ a, int len, int p,
                                                    int l, float* __restrict__ part,
+                                                   unsigned* __restrict__ cnt,
+                                                   double* __restrict__ resid,
                                                    float* __restrict__ Y0, float* __restrict__ Y1,
                                                    double* __restrict__ sig) {
   extern __shared__ float sQ[];
-  float* sZ = sQ + p * p;   // [64][p]
-  float* sX = sZ + 64 * p;  // [64][p]
+  float* sZ = sQ + p * p;            // [16][p]
+  float* sX = sZ + kRitzRows * p;    // [16][p]
   __shared__ float red[4][64];
+  __shared__ double r2[64];
+  __shared__ int s_last;
   const int q = threadIdx.x & 63, g = threadIdx.x >> 6;   // column, row group
   double cs = 0.0, e = 1.0, s1 = 1.0;
   if (Y0) {
@@ -878,11 +884,11 @@ __global__ void __launch_bounds__(256) ritz_kernel(const float* __restrict__ Z,
   const float th = q < l ? (float)theta[q] : 0.f;
   for (int i = threadIdx.x; i < p * p; i += blockDim.x) sQ[i] = Q[i];
   float acc = 0.f;
-  const int ntiles = (len + 63) / 64;
+  const int ntiles = (len + kRitzRows - 1) / kRitzRows;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int r0 = t * 64, nr = min(64, len - r0);
+    const int r0 = t * kRitzRows, nr = min(kRitzRows, len - r0);
     __syncthreads();   // the previous tile's rows are read
-    for (int i = threadIdx.x; i < 64 * p; i += blockDim.x) {
+    for (int i = threadIdx.x; i < kRitzRows * p; i += blockDim.x) {
       const int r = i / p, k = i - r * p;
       sZ[i] = r < nr ? Z[(size_t)r0 * p + i] : 0.f;
       sX[i] = r < nr ? X[(size_t)r0 * p + i] - (float)cx[k] : 0.f;
@@ -890,11 +896,24 @@ __global__ void __launch_bounds__(256) ritz_kernel(const float* __restrict__ Z,
     __syncthreads();
     if (q < p) {
       for (int r = g; r < nr; r += 4) {
-        float z = 0.f, x = 0.f;
-        for (int k = 0; k < p; ++k) {
-          z = __fmaf_rn(sZ[r * p + k], sQ[k * p + q], z);
-          x = __fmaf_rn(sX[r * p + k], sQ[k * p + q], x);
+        // four independent partial sums per product (short dependency chains)
+        float za[4] = {0.f, 0.f, 0.f, 0.f}, xa[4] = {0.f, 0.f, 0.f, 0.f};
+        int k = 0;
+        for (; k + 4 <= p; k += 4) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float qv = sQ[(k + u) * p + q];
+            za[u] = __fmaf_rn(sZ[r * p + k + u], qv, za[u]);
+            xa[u] = __fmaf_rn(sX[r * p + k + u], qv, xa[u]);
+          }
         }
+        for (; k < p; ++k) {
+          const float qv = sQ[k * p + q];
+          za[0] = __fmaf_rn(sZ[r * p + k], qv, za[0]);
+          xa[0] = __fmaf_rn(sX[r * p + k], qv, xa[0]);
+        }
+        const float z = (za[0] + za[1]) + (za[2] + za[3]);
+        const float x = (xa[0] + xa[1]) + (xa[2] + xa[3]);
         if (q < l) {
           const float res = __fmaf_rn(-th, z, x);
           acc = __fmaf_rn((float)a[r0 + r] * res, res, acc);
@@ -910,23 +929,36 @@ __global__ void __launch_bounds__(256) ritz_kernel(const float* __restrict__ Z,
   __syncthreads();
   if (threadIdx.x < l) part[(size_t)blockIdx.x * l + threadIdx.x] =
       (red[0][threadIdx.x] + red[1][threadIdx.x]) + (red[2][threadIdx.x] + red[3][threadIdx.x]);
-}
-
-// max_k |r_k|_a over the first l Ritz pairs from the nch partials (one CTA,
-// fixed order) into *resid.
-__global__ void __launch_bounds__(64) ritz_final_kernel(const float* __restrict__ part, int nch,
-                                                        int l, double* __restrict__ resid) {
-  __shared__ double r2[64];
-  const int q = threadIdx.x;
-  double t = 0.0;
-  if (q < l)
-    for (int b = 0; b < nch; ++b) t += (double)part[(size_t)b * l + q];
-  r2[q] = t;
+  __threadfence();
   __syncthreads();
-  if (q == 0) {
+  if (threadIdx.x == 0) s_last = atomicAdd(cnt, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // the last CTA: column q, chunk g of the partials, eight loads in flight
+  const int nch = gridDim.x;
+  double t = 0.0;
+  if (q < l) {
+    for (int b0 = g * 8; b0 < nch; b0 += 32) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        v[u] = b0 + u < nch ? __ldcg(part + (size_t)(b0 + u) * l + q) : 0.f;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) t += (double)v[u];
+    }
+  }
+  if (g == 0) r2[q] = 0.0;
+  __syncthreads();
+  for (int gg = 0; gg < 4; ++gg) {   // fixed order over the chunks
+    if (g == gg && q < l) r2[q] += t;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
     double mx = 0.0;
     for (int k = 0; k < l; ++k) mx = (r2[k] == r2[k] && mx == mx) ? fmax(mx, r2[k]) : NAN;
     *resid = sqrt(mx);   // NaN if any residual was (the loop then stops as failed)
+    *cnt = 0u;
   }
 }
 
@@ -969,7 +1001,13 @@ __global__ void __launch_bounds__(256) cheb_step_kernel(const float* __restrict_
   __shared__ float cx[kMaxP];
   for (int q = threadIdx.x; q < p; q += blockDim.x) {
     double t = 0.0;
-    for (int b = 0; b < nch; ++b) t += (double)part[(size_t)b * p + q];
+    for (int b0 = 0; b0 < nch; b0 += 8) {   // eight loads in flight, then the adds
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = b0 + u < nch ? part[(size_t)(b0 + u) * p + q] : 0.f;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) t += (double)v[u];
+    }
     cx[q] = (float)t;
   }
   const double cs = sig[0], e = sig[1], s1 = sig[2], sp = sig[4 + k - 1];
@@ -987,15 +1025,16 @@ __global__ void __launch_bounds__(256) cheb_step_kernel(const float* __restrict_
 }
 
 // The Ritz residuals (and, with Y0 given, the filter's start) into *resid;
-// part: at least 256 x l floats of scratch.
+// part: at least 256 x l floats of scratch, cnt: an arrival counter at 0.
 void launch_ritz(const float* Z, const float* X, const double* cx, const float* Q,
                  const double* theta, const double* a, int len, int p, int l, float* part,
-                 float* Y0, float* Y1, double* sig, double* resid, int nsm, cudaStream_t s) {
-  const int ntiles = (len + 63) / 64;
+                 unsigned* cnt, float* Y0, float* Y1, double* sig, double* resid, int nsm,
+                 cudaStream_t s) {
+  const int ntiles = (len + kRitzRows - 1) / kRitzRows;
   const int grid = std::max(1, std::min(ntiles, std::min(256, 2 * nsm)));
-  const size_t sm = ((size_t)p * p + 2 * 64 * p) * sizeof(float);
-  ritz_kernel<<<grid, 256, sm, s>>>(Z, X, cx, Q, theta, a, len, p, l, part, Y0, Y1, sig);
-  ritz_final_kernel<<<1, 64, 0, s>>>(part, grid, l, resid);
+  const size_t sm = ((size_t)p * p + 2 * kRitzRows * p) * sizeof(float);
+  ritz_kernel<<<grid, 256, sm, s>>>(Z, X, cx, Q, theta, a, len, p, l, part, cnt, resid, Y0, Y1,
+                                    sig);
 }
 
 // One filter step after the product X = M Yc: the deflation sums and the
