@@ -35,6 +35,7 @@ struct RowAccSmem {
 __global__ void __launch_bounds__(256) wtw_reduce_kernel(const AccArgs args,
                                                          double* __restrict__ WtW,
                                                          double* __restrict__ gw) {
+  pdl_enter();
   const State* st = args.P->st;
   if (st->done) return;
   __shared__ double sh[8][32];
@@ -69,6 +70,7 @@ __global__ void __launch_bounds__(256) wtw_reduce_kernel(const AccArgs args,
 // ---------------------------------------------------------------------------
 template <int K>
 __global__ void __launch_bounds__(kThreads) rowacc_kernel(AccArgs args) {
+  pdl_enter();
   if (args.skip && *args.skip) return;
   const Prob& P = *args.P;
   const float* __restrict__ cA = P.cs[args.gbuf].A;
@@ -274,7 +276,7 @@ __global__ void __launch_bounds__(kThreads) rowacc_kernel(AccArgs args) {
 template <int K>
 static cudaError_t launch_rowacc_k(const AccArgs& a, int nrowblk, cudaStream_t s) {
   dim3 grid(nrowblk, a.nseg);
-  rowacc_kernel<K><<<grid, kThreads, RowAccSmem<K>::bytes, s>>>(a);
+  launch_pdl(rowacc_kernel<K>, dim3(grid), dim3(kThreads), RowAccSmem<K>::bytes, s, a);
   return cudaGetLastError();
 }
 
@@ -309,7 +311,7 @@ cudaError_t launch_rowacc(const AccArgs& a, int nrowblk, cudaStream_t s) {
 
 cudaError_t launch_wtw_reduce(const AccArgs& a, double* WtW, double* gw, cudaStream_t s) {
   const int cnt = a.k * a.k + a.k;
-  wtw_reduce_kernel<<<(cnt + 31) / 32, 256, 0, s>>>(a, WtW, gw);
+  launch_pdl(wtw_reduce_kernel, dim3((cnt + 31) / 32), dim3(256), 0, s, a, WtW, gw);
   return cudaGetLastError();
 }
 

@@ -777,7 +777,7 @@ struct Solver {
       if (e != cudaSuccess) break;
       e = launch_newton(dP, a, WtW, gw, s);
       if (e != cudaSuccess) break;
-      fprime_kernel<<<std::min(ceil_div(n, 256), 4 * ctx->nsm), 256, 0, s>>>(dP);
+      launch_pdl(fprime_kernel, dim3(std::min(ceil_div(n, 256), 4 * ctx->nsm)), dim3(256), 0, s, dP);
       e = pass_col(MODE_TRIAL, s);
     }
     return e;
@@ -801,9 +801,9 @@ struct Solver {
     if (explicit_resid)
       launch_ritz(Zb, Xb, cvec, Qm, theta, hP.a, n, p, ell, eppart, ritz_cnt, nullptr, nullptr,
                   csig, resid, ctx->nsm, s);
-    apply_kernel<<<ceil_div(n, 64), 256, (size_t)(p * p + 64 * p) * 4, s>>>(Xb, cvec, Bm, n, p,
+    launch_pdl(apply_kernel, dim3(ceil_div(n, 64)), dim3(256), (size_t)(p * p + 64 * p) * 4, s, Xb, cvec, Bm, n, p,
                                                                            Zb, nullptr);
-    eig_ctl_kernel<<<1, 1, 0, s>>>(dSt, resid, efail);
+    launch_pdl(eig_ctl_kernel, dim3(1), dim3(1), 0, s, dSt, resid, efail);
     return cudaGetLastError();
   }
 
@@ -826,8 +826,8 @@ struct Solver {
     // (before the power step below overwrites Z)
     launch_ritz(Zb, Xb, cvec, Qm, theta, hP.a, n, p, ell, eppart, ritz_cnt, F0, F1, csig, resid,
                 ctx->nsm, s);
-    eig_ctl_kernel<<<1, 1, 0, s>>>(dSt, resid, efail);
-    apply_kernel<<<ceil_div(n, 64), 256, (size_t)(p * p + 64 * p) * 4, s>>>(Xb, cvec, Bm, n, p,
+    launch_pdl(eig_ctl_kernel, dim3(1), dim3(1), 0, s, dSt, resid, efail);
+    launch_pdl(apply_kernel, dim3(ceil_div(n, 64)), dim3(256), (size_t)(p * p + 64 * p) * 4, s, Xb, cvec, Bm, n, p,
                                                                            Zb, nullptr);
     float* Yp = F0;
     float* Yc = F1;
@@ -844,7 +844,7 @@ struct Solver {
     // the filtered block's Cholesky-QR (columns scaled first) into Z
     launch_eig_gram(Yc, nullptr, hP.a, n, p, eppart, GXX, nullptr, cvec, s, done);
     launch_eig_small(p, ell, 2, GXX, Tm, cvec, Bm, theta, resid, efail, s, nullptr, done);
-    apply_kernel<<<ceil_div(n, 64), 256, (size_t)(p * p + 64 * p) * 4, s>>>(Yc, cvec, Bm, n, p,
+    launch_pdl(apply_kernel, dim3(ceil_div(n, 64)), dim3(256), (size_t)(p * p + 64 * p) * 4, s, Yc, cvec, Bm, n, p,
                                                                            Zb, done);
     return cudaGetLastError();
   }
@@ -898,7 +898,7 @@ struct Solver {
       CUDA_TRY(cudaStreamBeginCaptureToGraph(s, bodyg, nullptr, nullptr, 0,
                                              cudaStreamCaptureModeThreadLocal));
       cudaError_t e = body(s);
-      loop_ctl_kernel<<<1, 1, 0, s>>>(h, dSt, which, 1);
+      launch_pdl(loop_ctl_kernel, dim3(1), dim3(1), 0, s, h, dSt, which, 1);
       cudaGraph_t tmp;
       cudaError_t e2 = cudaStreamEndCapture(s, &tmp);
       if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -910,7 +910,7 @@ struct Solver {
       CUDA_TRY(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0,
                                              cudaStreamCaptureModeThreadLocal));
       cudaError_t e = body(s);
-      loop_ctl_kernel<<<1, 1, 0, s>>>(0, dSt, which, 0);
+      launch_pdl(loop_ctl_kernel, dim3(1), dim3(1), 0, s, 0, dSt, which, 0);
       cudaGraph_t tmp;
       cudaError_t e2 = cudaStreamEndCapture(s, &tmp);
       if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -1401,7 +1401,7 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
       launch_eig_gram(S->Xb, nullptr, P.a, n, S->p, S->eppart, S->GXX, nullptr, S->cvec, s);
       CUDA_TRY(cudaGetLastError());
       launch_eig_small(S->p, ell, 0, S->GXX, S->Tm, S->cvec, S->Bm, S->theta, S->resid, S->efail, s);
-      apply_kernel<<<ceil_div(n, 64), 256, (size_t)(S->p * S->p + 64 * S->p) * 4, s>>>(
+      launch_pdl(apply_kernel, dim3(ceil_div(n, 64)), dim3(256), (size_t)(S->p * S->p + 64 * S->p) * 4, s, 
           S->Xb, S->cvec, S->Bm, n, S->p, S->Zb, nullptr);
       eig_setup_kernel<<<1, 1, 0, s>>>(S->dSt, o->eig_tol, o->eig_max_iter,
                                        o->eig_max_iter + 4);
@@ -2517,7 +2517,7 @@ eot_status eot_spectral_modes_filtered(int32_t n, int32_t m, const float* C, con
   launch_eig_gram(S->Xb, nullptr, P.a, n, p, S->eppart, S->GXX, nullptr, S->cvec, s);
   CUDA_TRY(cudaGetLastError());
   launch_eig_small(p, ell, 0, S->GXX, S->Tm, S->cvec, S->Bm, S->theta, S->resid, S->efail, s);
-  apply_kernel<<<ceil_div(n, 64), 256, (size_t)(p * p + 64 * p) * 4, s>>>(S->Xb, S->cvec, S->Bm, n,
+  launch_pdl(apply_kernel, dim3(ceil_div(n, 64)), dim3(256), (size_t)(p * p + 64 * p) * 4, s, S->Xb, S->cvec, S->Bm, n,
                                                                          p, S->Zb, nullptr);
   eig_setup_kernel<<<1, 1, 0, s>>>(S->dSt, tol, max_iter, max_iter + 4);
   st = S->run_loop(S->ex_eig, 1, max_iter + 5);
@@ -2597,7 +2597,7 @@ eot_status eot_sknr_step(int32_t n, int32_t m, int32_t ell, const float* C, cons
                            cudaMemcpyDeviceToDevice, s));
   CUDA_TRY(cudaEventRecord(ev[2], s));
   CUDA_TRY(launch_newton(S->dP, acc, S->WtW, S->gw, s));
-  fprime_kernel<<<std::min(ceil_div(n, 256), 4 * S->ctx->nsm), 256, 0, s>>>(S->dP);
+  launch_pdl(fprime_kernel, dim3(std::min(ceil_div(n, 256), 4 * S->ctx->nsm)), dim3(256), 0, s, S->dP);
   CUDA_TRY(cudaEventRecord(ev[3], s));
   CUDA_TRY(S->pass_col(MODE_TRIAL, s));
   CUDA_TRY(cudaEventRecord(ev[4], s));

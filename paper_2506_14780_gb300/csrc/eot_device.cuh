@@ -26,6 +26,22 @@
 
 namespace eotk {
 
+// Programmatic dependent launch.  pdl_wait (griddepcontrol.wait) returns once
+// the preceding kernel of the stream has completed and its memory operations
+// are visible (at once when the kernel was not launched as a dependent);
+// pdl_trigger lets the next kernel launch (its CTAs then wait in pdl_wait).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+// Entry of a kernel launched with launch_pdl: nothing the preceding kernels
+// write is touched before it.
+__device__ __forceinline__ void pdl_enter() {
+  pdl_wait();
+  pdl_trigger();
+}
+
+
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
 // Re-centring threshold of the running log-sum-exp (log2 units).

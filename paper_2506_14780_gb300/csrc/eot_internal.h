@@ -3,8 +3,29 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <utility>
 
 namespace eotk {
+
+// Launch with programmatic stream serialization: the kernel may be launched
+// while the preceding kernel of the stream is still running (its launch and
+// CTA start-up overlap that kernel's tail); the kernel calls pdl_enter (or
+// pdl_wait) before touching anything the preceding kernels write.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Column pass tile: 128 output columns per CTA (32 lanes x 4), 8 warps over rows.
 constexpr int kColTile = 128;

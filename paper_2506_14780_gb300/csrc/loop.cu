@@ -10,6 +10,7 @@ namespace eotk {
 
 // which = 0: Sinkhorn / SK-NR loop (State::done), 1: mode computation loop.
 __global__ void loop_ctl_kernel(cudaGraphConditionalHandle h, State* st, int which, int use_cond) {
+  pdl_enter();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   st->body_runs += 1;
   bool cont = which == 0 ? (st->done == 0) : (st->eig_done == 0);
@@ -25,6 +26,7 @@ __global__ void loop_ctl_kernel(cudaGraphConditionalHandle h, State* st, int whi
 // A residual that is not a finite number (the block broke down) stops the
 // loop as not converged.
 __global__ void eig_ctl_kernel(State* st, const double* resid, const int* fail) {
+  pdl_enter();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   st->eig_iter += 1;
   st->eig_resid = *resid;

@@ -40,6 +40,7 @@ constexpr double kNrRangeLn = 60.0 * 0.6931471805599453;   // |ln column sum| bo
 // the TF32-rounded value, part 1 the TF32-rounded remainder.
 __global__ void build_tiles_kernel(const float* __restrict__ Z, int n, int kk, int NN,
                                    float* __restrict__ tiles, const int* __restrict__ skip) {
+  pdl_enter();
   if (skip && *skip) return;
   const int nch = (n + kMmaKC - 1) / kMmaKC;
   const long total = (long)nch * NN * kMmaKC;
@@ -491,6 +492,7 @@ struct MmaSmem {
 
 template <int NN>
 __global__ void __launch_bounds__(256) colmma_kernel(AccArgs args, const float* __restrict__ tiles) {
+  pdl_enter();
   const Prob& P = *args.P;
   State* st = P.st;
   const bool s4 = args.mode == ACC_S4;
@@ -812,6 +814,7 @@ __global__ void __launch_bounds__(kTmThreads, 2)
     mma_tma_kernel(AccArgs args, const float* __restrict__ tiles) {
   static_assert(ClusterEpi<NN>::bytes_prod + 1024 <= TmaSmem<NN>::bytes, "epilogue smem");
   static_assert(NN > 48 || ClusterEpi<NN>::bytes_s4 + 1024 <= TmaSmem<NN>::bytes, "epilogue smem");
+  pdl_enter();
   const Prob* PP = args.P;
   const Prob& P = *PP;
   State* st = P.st;
@@ -1150,22 +1153,23 @@ static bool mma_cluster_merge(const AccArgs& a, int nseg) {
 // then hold shared memory and TMEM while the preceding pass finishes.)
 template <int NN, bool ROW>
 static cudaError_t launch_tma(const AccArgs& a, const float* tiles, dim3 grid, cudaStream_t s) {
-  if (!mma_cluster_merge(a, (int)grid.y)) {
-    mma_tma_kernel<NN, ROW, false><<<grid, kTmThreads, TmaSmem<NN>::bytes, s>>>(a, tiles);
-    return cudaGetLastError();
-  }
+  if (!mma_cluster_merge(a, (int)grid.y))
+    return launch_pdl(mma_tma_kernel<NN, ROW, false>, grid, dim3(kTmThreads), TmaSmem<NN>::bytes,
+                      s, a, tiles);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = dim3(kTmThreads);
   cfg.dynamicSmemBytes = TmaSmem<NN>::bytes;
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = 1;
   attr[0].val.clusterDim.y = grid.y;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
   return cudaLaunchKernelEx(&cfg, mma_tma_kernel<NN, ROW, true>, a, tiles);
 }
 
@@ -1174,8 +1178,7 @@ static cudaError_t launch_colmma_k(const AccArgs& a, bool tma, const float* tile
                                    cudaStream_t s) {
   dim3 grid(ncolblk, a.nseg);
   if (tma) return launch_tma<NN, false>(a, tiles, grid, s);
-  colmma_kernel<NN><<<grid, 256, MmaSmem<NN>::bytes, s>>>(a, tiles);
-  return cudaGetLastError();
+  return launch_pdl(colmma_kernel<NN>, grid, dim3(256), MmaSmem<NN>::bytes, s, a, tiles);
 }
 
 // The staged kernel needs the cost's tensor map (rows 16-byte aligned) and
@@ -1209,8 +1212,8 @@ cudaError_t launch_build_tiles(const float* Z, int n, int kk, float* tiles, cuda
   const int NN = mma_width(kk);
   const long total = (long)((n + kMmaKC - 1) / kMmaKC) * NN * kMmaKC;
   const int blocks = (int)((total + 255) / 256);
-  build_tiles_kernel<<<blocks < 4096 ? blocks : 4096, 256, 0, s>>>(Z, n, kk, NN, tiles, skip);
-  return cudaGetLastError();
+  return launch_pdl(build_tiles_kernel, dim3(blocks < 4096 ? blocks : 4096), dim3(256), 0, s, Z, n,
+                    kk, NN, tiles, skip);
 }
 
 template <int NN>

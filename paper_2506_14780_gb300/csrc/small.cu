@@ -37,6 +37,7 @@ __global__ void __launch_bounds__(256) eig_gram_kernel(const float* __restrict__
                                                        const double* __restrict__ w, int len,
                                                        int p, float* __restrict__ part,
                                                        const int* __restrict__ skip) {
+  pdl_enter();
   if (skip && *skip) return;
   extern __shared__ float sm[];
   float* sX = sm;                         // [kEGRows][p]
@@ -144,6 +145,7 @@ __global__ void __launch_bounds__(64) eig_gram_reduce_kernel(const float* __rest
                                                              double* __restrict__ T,
                                                              double* __restrict__ c,
                                                              const int* __restrict__ skip) {
+  pdl_enter();
   if (skip && *skip) return;
   const int rec = 2 * p * p + p;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -173,9 +175,9 @@ void launch_eig_gram(const float* X, const float* Z, const double* w, int len, i
                      const int* skip) {
   const int nch = std::max(1, std::min(kEGMaxChunks, (len + kEGRows - 1) / kEGRows));
   const size_t sm = ((size_t)2 * kEGRows * p + kEGRows) * sizeof(float);
-  eig_gram_kernel<<<nch, 256, sm, s>>>(X, Z, w, len, p, part, skip);
+  launch_pdl(eig_gram_kernel, dim3(nch), dim3(256), sm, s, X, Z, w, len, p, part, skip);
   const int rec = 2 * p * p + p;
-  eig_gram_reduce_kernel<<<(rec + 63) / 64, 64, 0, s>>>(part, nch, p, Z ? 1 : 0, G, T, c, skip);
+  launch_pdl(eig_gram_reduce_kernel, dim3((rec + 63) / 64), dim3(64), 0, s, part, nch, p, Z ? 1 : 0, G, T, c, skip);
 }
 
 // ---------------------------------------------------------------------------
@@ -291,6 +293,7 @@ __global__ void __launch_bounds__(256) newton_kernel(const Prob* __restrict__ PP
                                                      const double* __restrict__ WtW,
                                                      const double* __restrict__ gw,
                                                      const double* __restrict__ Dr) {
+  pdl_enter();
   const Prob& P = *PP;
   State* st = P.st;
   if (st->done) return;
@@ -355,12 +358,13 @@ cudaError_t launch_newton(const Prob* dP, const AccArgs& a, double* WtW, double*
                           cudaStream_t s) {
   cudaError_t e = launch_wtw_reduce(a, WtW, gw, s);
   if (e != cudaSuccess) return e;
-  newton_kernel<<<1, 256, 0, s>>>(dP, WtW, gw, nullptr);
+  launch_pdl(newton_kernel, dim3(1), dim3(256), 0, s, dP, WtW, gw, nullptr);
   return cudaGetLastError();
 }
 
 // f' = f_k + V Delta (float64 accumulation of float32 V), into the other f buffer.
 __global__ void fprime_kernel(const Prob* __restrict__ PP) {
+  pdl_enter();
   const Prob& P = *PP;
   const State* st = P.st;
   if (st->done || !st->nr_ok) return;
@@ -488,6 +492,7 @@ __global__ void __launch_bounds__(kEH * kEH) eig_small_kernel(int p, int l, int 
                                                               int* __restrict__ fail_out,
                                                               float* __restrict__ Qout,
                                                               const int* __restrict__ skip) {
+  pdl_enter();
   if (skip && *skip) return;
   __shared__ float A0[kMaxP * kES];
   __shared__ float Q[kMaxP * kES];
@@ -783,7 +788,7 @@ void launch_eig_small(int p, int l, int mode, const double* GXX, const double* T
                       const double* c, float* B, double* theta, double* resid, int* fail,
                       cudaStream_t s, float* Qout, const int* skip) {
   const int half = std::max(4, ((p + 1) & ~1) / 2);   // one thread per pair of pairs
-  eig_small_kernel<<<1, dim3(half, half), 0, s>>>(p, l, mode, GXX, T, c, B, theta, resid, fail,
+  launch_pdl(eig_small_kernel, dim3(1), dim3(dim3(half, half)), 0, s, p, l, mode, GXX, T, c, B, theta, resid, fail,
                                                   Qout, skip);
 }
 
@@ -794,6 +799,7 @@ __global__ void __launch_bounds__(256) apply_kernel(const float* __restrict__ X,
                                                     const float* __restrict__ B, int len, int p,
                                                     float* __restrict__ Z,
                                                     const int* __restrict__ skip) {
+  pdl_enter();
   if (skip && *skip) return;
   extern __shared__ float sB[];
   float* sX = sB + p * p;   // [64][p]
@@ -855,6 +861,7 @@ __global__ void __launch_bounds__(256) ritz_kernel(const float* __restrict__ Z,
                                                    double* __restrict__ resid,
                                                    float* __restrict__ Y0, float* __restrict__ Y1,
                                                    double* __restrict__ sig) {
+  pdl_enter();
   extern __shared__ float sQ[];
   float* sZ = sQ + p * p;            // [16][p]
   float* sX = sZ + kRitzRows * p;    // [16][p]
@@ -968,6 +975,7 @@ __global__ void __launch_bounds__(256) wsum_part_kernel(const float* __restrict_
                                                         const double* __restrict__ a, int len,
                                                         int p, float* __restrict__ part,
                                                         const int* __restrict__ skip) {
+  pdl_enter();
   if (skip && *skip) return;
   __shared__ float red[8][kMaxP];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -997,6 +1005,7 @@ __global__ void __launch_bounds__(256) cheb_step_kernel(const float* __restrict_
                                                         float* __restrict__ Yp, int len, int p,
                                                         int k, double* __restrict__ sig,
                                                         const int* __restrict__ skip) {
+  pdl_enter();
   if (skip && *skip) return;
   __shared__ float cx[kMaxP];
   for (int q = threadIdx.x; q < p; q += blockDim.x) {
@@ -1033,7 +1042,7 @@ void launch_ritz(const float* Z, const float* X, const double* cx, const float* 
   const int ntiles = (len + kRitzRows - 1) / kRitzRows;
   const int grid = std::max(1, std::min(ntiles, std::min(256, 2 * nsm)));
   const size_t sm = ((size_t)p * p + 2 * kRitzRows * p) * sizeof(float);
-  ritz_kernel<<<grid, 256, sm, s>>>(Z, X, cx, Q, theta, a, len, p, l, part, cnt, resid, Y0, Y1,
+  launch_pdl(ritz_kernel, dim3(grid), dim3(256), sm, s, Z, X, cx, Q, theta, a, len, p, l, part, cnt, resid, Y0, Y1,
                                     sig);
 }
 
@@ -1042,10 +1051,10 @@ void launch_ritz(const float* Z, const float* X, const double* cx, const float* 
 void launch_cheb_step(const float* X, const double* a, const float* Yc, float* Yp, int len, int p,
                       int k, double* sig, float* part, int nsm, const int* skip, cudaStream_t s) {
   const int nch = std::max(1, std::min(128, (len + 31) / 32));
-  wsum_part_kernel<<<nch, 256, 0, s>>>(X, a, len, p, part, skip);
+  launch_pdl(wsum_part_kernel, dim3(nch), dim3(256), 0, s, X, a, len, p, part, skip);
   const long long total = (long long)len * p;
   const int grid = (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 4LL * nsm));
-  cheb_step_kernel<<<grid, 256, 0, s>>>(X, part, nch, Yc, Yp, len, p, k, sig, skip);
+  launch_pdl(cheb_step_kernel, dim3(grid), dim3(256), 0, s, X, part, nch, Yc, Yp, len, p, k, sig, skip);
 }
 
 // SplitMix64 start block (Steele, Lea & Flood 2014): u = top 53 bits / 2^53,

@@ -74,13 +74,6 @@ __device__ __forceinline__ unsigned arrive_count(unsigned* p) {
   return old;
 }
 
-// Programmatic dependent launch: wait for the preceding kernel's results /
-// allow the next kernel to start its prologue.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
 // CTA whose chunk holds tile t (chunks [floor(kT/G), floor((k+1)T/G)), G <= T).
 __device__ __forceinline__ int st_owner(long long t, long long T, int G) {
   return (int)(((t + 1) * (long long)G - 1) / T);
