@@ -386,6 +386,27 @@ eot_status eot_ctransform_noalloc(eot_side side, int32_t n, int32_t m, const flo
                                   const double *pot, const double *w, const double *shift,
                                   double eps, double *out, double *log_ratio, void *stream);
 
+/* The coupling of a pair of potentials (Eq. pi(f,g)) and its scalars:
+ *   P_ij = a_i b_j exp((f_i + g_j - C_ij)/eps)        (n x m, float32, row major)
+ *   cost_out   = <C, P>,  mass_out = sum_ij P_ij,
+ *   primal_out = <C, P> + eps KL(P | a x b)            (Eq. primal_EOT), with
+ *                KL(P | a x b) = sum P log(P/(a b)); primal_out minus the dual
+ *                value Q_eps(f, g) is the duality gap <P1-a,f> + <P^T1-b,g> +
+ *                eps (sum P - 1).
+ * At a solution (f, g) of the dual, P is also the derivative of the optimal
+ * value with respect to the cost (envelope theorem: dQ_eps/dC_ij = P_ij), and
+ * the potentials are its derivatives with respect to a and b (up to a
+ * constant).  The exponent is formed in float64 from the float64 potentials and
+ * the float32 cost, the scalars summed in float64 in a fixed order.  C, f, g, a,
+ * b are device pointers (a, b as given: the solves return potentials for the
+ * weights normalised to sum 1); P (device, n*m floats) is optional, and so are
+ * the host outputs.  Runs on `stream` (NULL: the library's stream of the
+ * calling thread) and returns when the scalars are on the host.  Scratch of
+ * 24 n + 24 bytes comes from the stream-ordered allocator. */
+eot_status eot_plan(int32_t n, int32_t m, const float *C, const double *f, const double *g,
+                    const double *a, const double *b, double eps, float *P, double *cost_out,
+                    double *mass_out, double *primal_out, void *stream);
+
 /* The two exponentials of the float32 passes, elementwise, so that callers can
  * check their accuracy (not a step of the method; Sec. 2 only needs exp):
  *   variant 0: out_i = 2^(p_i + q_i) as the evaluation passes that verify a

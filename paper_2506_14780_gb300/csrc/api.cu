@@ -70,6 +70,9 @@ void stream_plan(int n, int m, bool col, int ctas, int* grid, int* slots);
 cudaError_t launch_sk_coop(const Prob* dP, const Prob& hP, int max_body, cudaStream_t s);
 cudaError_t launch_exp2_check(int count, const float* p, const float* q, int variant, float* out,
                               cudaStream_t s);
+cudaError_t launch_plan(int n, int m, const float* C, const double* f, const double* g,
+                        const double* a, const double* b, double eps, float* P, double* part,
+                        double* out, int nsm, cudaStream_t s);
 void init_gram_attributes();
 int gram_smem_bytes();
 void gram_plan(int nO, int nR, int ctas, int* grid, int* slots);
@@ -2449,6 +2452,33 @@ eot_status eot_marginal_error(int32_t n, int32_t m, const float* C, const double
   if (st != EOT_OK) return st;
   if (row_l1) *row_l1 = S->hScores[0];
   if (col_l1) *col_l1 = S->hScores[1];
+  return EOT_OK;
+}
+
+eot_status eot_plan(int32_t n, int32_t m, const float* C, const double* f, const double* g,
+                    const double* a, const double* b, double eps, float* P, double* cost_out,
+                    double* mass_out, double* primal_out, void* stream) {
+  if (!C || !f || !g || !a || !b) return fail(EOT_EINVAL, "C, f, g, a and b are required");
+  if (n < 1 || m < 1) return fail(EOT_EINVAL, "need n >= 1 and m >= 1");
+  if (!finite_pos(eps)) return fail(EOT_EINVAL, "eps must be finite and > 0");
+  DeviceCtx* ctx = nullptr;
+  eot_status cs = get_ctx(&ctx);
+  if (cs != EOT_OK) return cs;
+  cudaStream_t s = stream ? reinterpret_cast<cudaStream_t>(stream) : ctx->stream;
+  double* tmp = nullptr;
+  CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&tmp), ((size_t)n * 3 + 3) * sizeof(double), s));
+  cudaError_t e = launch_plan(n, m, C, f, g, a, b, eps, P, tmp, tmp + (size_t)n * 3, ctx->nsm, s);
+  double h[3] = {0.0, 0.0, 0.0};
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h, tmp + (size_t)n * 3, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  const cudaError_t ef = cudaFreeAsync(tmp, s);
+  const cudaError_t es = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = ef;
+  if (e == cudaSuccess) e = es;
+  if (e != cudaSuccess) return fail(EOT_ECUDA, cudaGetErrorString(e));
+  if (cost_out) *cost_out = h[0];
+  if (mass_out) *mass_out = h[1];
+  if (primal_out) *primal_out = h[0] + eps * h[2];
   return EOT_OK;
 }
 

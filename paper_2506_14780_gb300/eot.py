@@ -107,6 +107,9 @@ _SIGNATURES = {
                                               C.c_int32, C.c_double, C.c_int32, C.c_int32, _PTR,
                                               _PTR, C.POINTER(C.c_int32),
                                               C.POINTER(C.c_double), _PTR]),
+    "eot_plan": (C.c_int, [C.c_int32, C.c_int32, _PTR, _PTR, _PTR, _PTR, _PTR, C.c_double, _PTR,
+                           C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                           _PTR]),
     "eot_marginal_error": (C.c_int, [C.c_int32, C.c_int32, _PTR, _PTR, _PTR, _PTR, _PTR,
                                      C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                      _PTR]),
@@ -344,6 +347,16 @@ def eot_sknr_step(n, m, ell, Cdev, a, b, eps, g, V, f_k=None, h=None, W=None, gr
     d = {k: getattr(info, k) for k, _ in info._fields_}
     d["stage_seconds"] = list(info.stage_seconds)
     return st, d
+
+
+def eot_plan(n, m, Cdev, f, g, a, b, eps, P=None, stream=None):
+    """The coupling of (f, g) into P (optional n x m float32 device tensor) and
+    its transport cost, mass and primal value.  Returns (status, cost, mass, primal)."""
+    cost, mass, primal = C.c_double(0.0), C.c_double(0.0), C.c_double(0.0)
+    st = load().eot_plan(n, m, Cdev.data_ptr(), f.data_ptr(), g.data_ptr(), a.data_ptr(),
+                         b.data_ptr(), float(eps), None if P is None else P.data_ptr(),
+                         C.byref(cost), C.byref(mass), C.byref(primal), stream)
+    return st, cost.value, mass.value, primal.value
 
 
 def eot_marginal_error(n, m, Cdev, f, g, a, b, eps, stream=None):

@@ -694,3 +694,33 @@ def test_gram_form_of_the_cost_matches_entrywise_loop():
         for j in range(0, 50, 9):
             d = prob.X[i].astype(np.float64) - prob.Y[j].astype(np.float64)
             assert Cg[i, j] == pytest.approx(float(d @ d), rel=0, abs=1e-14)
+
+
+def test_plan_is_the_derivative_of_the_optimal_value_in_the_cost():
+    """Envelope theorem (Eq. def_Q at the optimum): the optimal value of the
+    entropic dual as a function of the cost has d/dC_ij = pi_ij, the coupling
+    of the optimal potentials.  Central differences of the converged value
+    against the plan, entry by entry, on a small random problem."""
+    rng = np.random.default_rng(21)
+    n, m, eps = 6, 5, 0.3
+    C = rng.random((n, m))
+    a = rng.random(n) + 0.2
+    a /= a.sum()
+    b = rng.random(m) + 0.2
+    b /= b.sum()
+
+    def value(Cc):
+        r = O.sinkhorn(Cc, a, b, eps, tol=1e-15, max_iter=100000)
+        return O.q_dual(r.f, r.g, Cc, a, b, eps), r
+
+    _, r = value(C)
+    P = O.plan(r.f, r.g, C, a, b, eps)
+    h = 1e-5
+    for i, j in [(0, 0), (2, 3), (5, 4), (3, 1)]:
+        Cp, Cm = C.copy(), C.copy()
+        Cp[i, j] += h
+        Cm[i, j] -= h
+        d = (value(Cp)[0] - value(Cm)[0]) / (2 * h)
+        assert abs(d - P[i, j]) < 1e-8, (i, j, d, P[i, j])
+    # the primal value at the optimum equals the dual one (zero gap)
+    assert abs(O.primal_value(P, C, a, b, eps) - O.q_dual(r.f, r.g, C, a, b, eps)) < 1e-12
