@@ -83,10 +83,36 @@ typedef struct {
     const void *C;         /* (n x m) cost: double for FP64, float otherwise; or NULL */
     const void *X, *Y;     /* point clouds (float32 in every mode; the FP64 mode forms
                               the cost from them in float64); or NULL                 */
-    eot_mem mem;           /* memory space of a, b, C, X, Y, f_init and the outputs   */
+    eot_mem mem;           /* memory space of a, b, C, X, Y, f_init, g_init, V_init,
+                              V_out and the outputs                                  */
     int32_t normalize_cost;/* 1: divide C by max_ij C_ij (after forming it from X, Y) */
     double eps;            /* target regularisation eps > 0                           */
     const double *f_init;  /* optional warm start f (n) (NULL: zeros; Alg. 4.1 line 1) */
+    /* Warm-start state (the resume side of a checkpoint (f, g, V)):
+     *  g_init (m): used when f_init is NULL; the solve starts from
+     *      f = g_init^{C,eps_0} (one row half-step, Eq. foc_f, at the first
+     *      level's eps).  NULL: not used.
+     *  V_init (n x ell, row-major): modes for SK-NR (needs ell > 0).  The first
+     *      level runs SK-NR on their span instead of plain Sinkhorn (the static
+     *      modes of Sec. 5); the library scales each column to unit root mean
+     *      square and makes them a-orthonormal and orthogonal to the constants
+     *      (Cholesky-QR in L2(a), in column order: the span of the first k
+     *      columns is kept for every k); a column whose part outside the
+     *      constants and the earlier columns has an a-norm below about 3e-3 of
+     *      the largest is dropped (zeroed).
+     *      With sequential_modes they also start the next level's mode
+     *      computation.  NULL: not used.
+     *  V_out (n x ell, row-major, output; needs ell > 0): the ell leading modes
+     *      (Sec. 3, descending rho_k^2) of the returned pair at eps,
+     *      a-orthonormal and orthogonal to a, as computed for a continuation
+     *      level (eig_tol, eig_max_iter, eig_degree); one more mode
+     *      computation after the last level, counted in seconds, seconds_eig
+     *      and eig_iters.  NULL: not computed.
+     * Entries must be finite (EOT_EINVAL otherwise).  Ignored by the server,
+     * which warm-starts from its own resident state (eot_server_submit). */
+    const double *g_init;
+    const double *V_init;
+    double *V_out;
 } eot_problem;
 
 typedef struct {
@@ -173,9 +199,11 @@ eot_status eot_solve(const eot_problem *prob, const eot_options *opt,
  * (host) holds each problem's status; the call returns the worst status.  Each
  * problem's result does not depend on which others share the batch, nor on how
  * many CTAs the scheduler gives it (bit for bit).  A problem with n > m and no
- * f_init runs transposed internally (Sinkhorn is symmetric in the two sides):
- * f_out, g_out, row_l1 and col_l1 are returned in the caller's roles, and its
- * q_semi is the semi-dual in g. */
+ * f_init runs transposed internally (Sinkhorn is symmetric in the two sides),
+ * and so does a plain-Sinkhorn problem given g_init and no f_init (its first
+ * half-step is then the row transform of g_init): f_out, g_out, row_l1 and
+ * col_l1 are returned in the caller's roles, and its q_semi is the semi-dual
+ * in g. */
 eot_status eot_solve_batch(int32_t count, const eot_problem *probs, const eot_options *opt,
                            double *const *f_out, double *const *g_out, eot_result *results);
 
@@ -186,7 +214,9 @@ typedef struct eot_server eot_server;
  * continuously: a request is admitted as soon as a slot is free and its device
  * footprint fits in hbm_budget_bytes; admitted requests share the device.
  * Potentials of requests submitted with a cloud_id stay resident and
- * warm-start later requests on the same cloud.  Ownership: *srv until destroy. */
+ * warm-start later requests on the same cloud (with ell > 0, so do the modes
+ * of the last level, which become the next request's V_init).  Ownership:
+ * *srv until destroy. */
 eot_status eot_server_create(const eot_options *opt, size_t hbm_budget_bytes,
                              int32_t max_slots, eot_server **srv);
 /* Deep-copies the problem (host memory only) and returns a ticket.  The
@@ -198,7 +228,10 @@ eot_status eot_server_create(const eot_options *opt, size_t hbm_budget_bytes,
  * least predicted work (n m times the iterations of its eps schedule) goes
  * first; a request that has waited more than 1 s goes before all others, and
  * while it does not fit no other request is admitted (no starvation); one
- * that can never fit the budget fails with EOT_ENOMEM. */
+ * that can never fit the budget fails with EOT_ENOMEM.  The problem's f_init,
+ * g_init, V_init and V_out are ignored: a request with a cloud_id warm-starts
+ * from the state the cloud's last completed request left resident, and with
+ * cloud_id 0 starts cold. */
 eot_status eot_server_submit(eot_server *srv, const eot_problem *prob, uint64_t cloud_id,
                              uint64_t *ticket);
 /* eot_server_submit with the request's own options (eps schedule, ell,
@@ -344,14 +377,15 @@ eot_status eot_sknr_step(int32_t n, int32_t m, int32_t ell, const float *C, cons
 
 /* The schedule eot_solve_batch would use, computed on the host only (no
  * device work, no GPU needed): for count problems of sizes n[k] x m[k] at
- * eps[k] (has_f_init[k] != 0 if the problem carries a warm start; NULL: none
- * does), the options' eps schedule and max_iter, a grid of grid_ctas resident
+ * eps[k] (has_f_init[k]: 0 no warm start, 2 a g_init and no f_init, any
+ * other value an f_init; NULL: none has one), the options' eps schedule and max_iter, a grid of grid_ctas resident
  * CTAs and a cost model (step_ns: one load-and-reduce step of a CTA; fix_ns:
  * the fixed cost of an iteration; bar_ns: one gang barrier; the library
  * calibrates these on the device before its first batch), gang_out[k]
  * receives the number of CTAs of problem k (a power of two, at most 32 and an
  * eighth of the grid) and transposed_out[k] 1 if it runs as the transposed
- * problem (n > m without a warm start).  Host arrays of count entries.
+ * problem (n > m without a warm start, or a g_init without f_init).  Host
+ * arrays of count entries.
  * Returns EOT_EINVAL on a member with n, m < 1 or eps <= 0, or a model with
  * step_ns <= 0. */
 eot_status eot_batch_plan(int32_t count, const int32_t *n, const int32_t *m, const double *eps,

@@ -96,7 +96,7 @@ void launch_ritz(const float* Z, const float* X, const double* cx, const float* 
                  cudaStream_t s);
 void launch_cheb_step(const float* X, const double* a, const float* Yc, float* Yp, int len, int p,
                       int k, double* sig, float* part, int nsm, const int* skip, cudaStream_t s);
-__global__ void init_block_kernel(float*, int, int, unsigned long long, const float*, int);
+__global__ void init_block_kernel(float*, int, int, unsigned long long, const float*, int, int);
 __global__ void take_cols_kernel(const float*, int, int, int, float*);
 __global__ void grad_weights_kernel(const Prob*, double*);
 __global__ void loop_ctl_kernel(cudaGraphConditionalHandle, State*, int, int);
@@ -1086,8 +1086,17 @@ static eot_status validate(const eot_problem* pr, const eot_options* o) {
   if (o->stall_window < 0) return fail(EOT_EINVAL, "stall_window must be >= 0");
   if (o->eig_degree < 0 || o->eig_degree > kMaxChebDegree)
     return fail(EOT_EINVAL, "eig_degree must be in [0, 8]");
+  if ((pr->V_init || pr->V_out) && o->ell == 0)
+    return fail(EOT_EINVAL, "V_init and V_out need ell > 0");
   if ((long long)pr->n * pr->m > (1ll << 34)) return fail(EOT_EINVAL, "n*m too large");
   return EOT_OK;
+}
+
+// y = x widened to float64 (the modes returned in V_out).
+__global__ void widen_kernel(const float* __restrict__ x, long long len, double* __restrict__ y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = (double)x[i];
 }
 
 // Device timestamp (globaltimer, ns): brackets a solve's work on the device,
@@ -1101,9 +1110,15 @@ __global__ void stamp_kernel(unsigned long long* t) {
 // ---------------------------------------------------------------------------
 // One solve.
 // ---------------------------------------------------------------------------
+// Internal warm-start state (the server's resident cache, device memory):
+// f_init_dev replaces pr->f_init; V_start_dev (n x ell float32, modes this
+// library computed: a-orthonormal, orthogonal to a) are the first level's
+// modes; f_keep_dev receives the returned f; V_keep_dev receives the modes
+// the last level used, and *V_kept whether there were any.
 static eot_status solve_one(const eot_problem* pr, const eot_options* o, double* f_out,
                             double* g_out, eot_result* res, const double* f_init_dev = nullptr,
-                            double* f_keep_dev = nullptr) {
+                            double* f_keep_dev = nullptr, const float* V_start_dev = nullptr,
+                            float* V_keep_dev = nullptr, int* V_kept = nullptr) {
   eot_status vs = validate(pr, o);
   if (vs != EOT_OK) return vs;
   DeviceCtx* ctx = nullptr;
@@ -1236,6 +1251,38 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
       fmax = std::max(fmax, std::fabs(v));
     }
   }
+  // g_init without f_init: the first level starts with f = g_init^{C,eps_0},
+  // a soft minimum over j of g_j - C_ij, so |f| <= max |g_init| + max C
+  const bool ginit = !finit && pr->g_init;
+  if (ginit) {
+    std::vector<double> hg(m);
+    CUDA_TRY(cudaMemcpy(hg.data(), pr->g_init, m * sizeof(double),
+                        dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+    double gmax = 0.0;
+    for (double v : hg) {
+      if (!std::isfinite(v)) return fail(EOT_EINVAL, "g_init has non-finite entries");
+      gmax = std::max(gmax, std::fabs(v));
+    }
+    fmax = gmax + cmax;
+  }
+  // V_init: float32 copy for the modes array (checked finite on the host)
+  std::vector<float> hvi;
+  if (pr->V_init) {
+    const size_t len = (size_t)n * o->ell;
+    std::vector<double> hv(len);
+    CUDA_TRY(cudaMemcpy(hv.data(), pr->V_init, len * sizeof(double),
+                        dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+    for (double v : hv)
+      if (!std::isfinite(v)) return fail(EOT_EINVAL, "V_init has non-finite entries");
+    // each column scaled to unit root-mean-square (the orthonormalisation's
+    // dead-column threshold is relative to the largest column)
+    const int l = o->ell;
+    std::vector<double> rms(l, 0.0);
+    for (size_t k = 0; k < len; ++k) rms[k % l] += hv[k] * hv[k];
+    for (int c = 0; c < l; ++c) rms[c] = rms[c] > 0.0 ? 1.0 / std::sqrt(rms[c] / n) : 0.0;
+    hvi.resize(len);
+    for (size_t k = 0; k < len; ++k) hvi[k] = (float)(hv[k] * rms[k % l]);
+  }
   const double R = 4.0 * (cmax + fmax + 40.0 * eps0) + 1e-30;
   int q = 22 - (int)std::ceil(std::log2(R));
   if (gram) {
@@ -1278,7 +1325,11 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   } else {
     CUDA_TRY(cudaMemsetAsync(P.f[0], 0, n * sizeof(double), s));
   }
-  CUDA_TRY(cudaMemsetAsync(P.g[0], 0, m * sizeof(double), s));
+  if (ginit) {
+    CUDA_TRY(cudaMemcpyAsync(P.g[0], pr->g_init, m * sizeof(double), kin, s));
+  } else {
+    CUDA_TRY(cudaMemsetAsync(P.g[0], 0, m * sizeof(double), s));
+  }
   // ---- graphs (captured once per solver and kernel choice) ----
   S->match_graphs_to_cost();
   if (!S->ex_sk) {
@@ -1313,6 +1364,59 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> eig_events;
   const int body_cap_sk = std::max(4, o->max_iter / S->unroll_sk + 4);
   const int body_cap_nr = std::max(4, o->max_iter / S->unroll_sknr + 4);
+  // Modes of the pair in buffers 0 (converged at the current level's eps;
+  // normalize_buffers_kernel re-split it) into S->V: a start block from the
+  // previous modes (random columns besides), orthonormalised, then the
+  // subspace iteration's graph.  Slot t of the mode states in hLev.
+  auto compute_modes = [&](int t) -> eot_status {
+    cudaEvent_t a0, a1;
+    CUDA_TRY(cudaEventCreate(&a0));
+    CUDA_TRY(cudaEventCreate(&a1));
+    CUDA_TRY(cudaEventRecord(a0, s));
+    const int keep = have_modes ? ell : 0;
+    init_block_kernel<<<std::min(ceil_div((long long)n * S->p, 256), 8 * ctx->nsm), 256, 0, s>>>(
+        S->Xb, n, S->p, 0x5EEDull + 977ull * (unsigned long long)t, have_modes ? S->V : nullptr,
+        keep, 1);
+    // orthonormalise the start block: Z = (X0 - 1 c^T) L^{-T}
+    launch_eig_gram(S->Xb, nullptr, P.a, n, S->p, S->eppart, S->GXX, nullptr, S->cvec, s);
+    CUDA_TRY(cudaGetLastError());
+    launch_eig_small(S->p, ell, 0, S->GXX, S->Tm, S->cvec, S->Bm, S->theta, S->resid, S->efail, s);
+    launch_pdl(apply_kernel, dim3(ceil_div(n, 64)), dim3(256), (size_t)(S->p * S->p + 64 * S->p) * 4, s,
+        S->Xb, S->cvec, S->Bm, n, S->p, S->Zb, nullptr);
+    eig_setup_kernel<<<1, 1, 0, s>>>(S->dSt, o->eig_tol, o->eig_max_iter, o->eig_max_iter + 4);
+    eot_status e = S->run_loop(S->ex_eig, 1, o->eig_max_iter + 5);
+    if (e != EOT_OK) return e;
+    take_cols_kernel<<<std::min(ceil_div((long long)n * ell, 256), 8 * ctx->nsm), 256, 0, s>>>(
+        S->Zb, n, S->p, ell, S->V);
+    CUDA_TRY(cudaEventRecord(a1, s));
+    eig_events.push_back({a0, a1});
+    CUDA_TRY(cudaMemcpyAsync(hLev + L + t, S->dSt, sizeof(State), cudaMemcpyDeviceToHost, s));
+    have_modes = true;
+    return EOT_OK;
+  };
+  if (V_start_dev) {
+    CUDA_TRY(cudaMemcpyAsync(S->V, V_start_dev, (size_t)n * ell * sizeof(float),
+                             cudaMemcpyDeviceToDevice, s));
+    have_modes = true;
+  } else if (!hvi.empty()) {
+    // V_init (columns scaled to unit root-mean-square on the host): made
+    // a-orthonormal and orthogonal to the constants in column order, Z =
+    // (V - 1 c^T) L^{-T} with L L^T = V^T D_a V - c c^T, c = V^T a; a column
+    // whose remaining squared a-norm is below 1e-5 of the largest pivot
+    // becomes zero (eig_small mode 3)
+    CUDA_TRY(cudaMemcpyAsync(S->V, hvi.data(), hvi.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    init_block_kernel<<<std::min(ceil_div((long long)n * S->p, 256), 8 * ctx->nsm), 256, 0, s>>>(
+        S->Xb, n, S->p, 0x5EEDull + 977ull * (unsigned long long)L, S->V, ell, 0);
+    launch_eig_gram(S->Xb, nullptr, P.a, n, S->p, S->eppart, S->GXX, nullptr, S->cvec, s);
+    CUDA_TRY(cudaGetLastError());
+    launch_eig_small(S->p, ell, 3, S->GXX, S->Tm, S->cvec, S->Bm, S->theta, S->resid, S->efail, s);
+    launch_pdl(apply_kernel, dim3(ceil_div(n, 64)), dim3(256), (size_t)(S->p * S->p + 64 * S->p) * 4, s,
+        S->Xb, S->cvec, S->Bm, n, S->p, S->Zb, nullptr);
+    take_cols_kernel<<<std::min(ceil_div((long long)n * ell, 256), 8 * ctx->nsm), 256, 0, s>>>(
+        S->Zb, n, S->p, ell, S->V);
+    CUDA_TRY(cudaGetLastError());
+    have_modes = true;
+  }
   for (int t = 0; t < L; ++t) {
     const double eps = levels[t];
     const bool last = t == L - 1;
@@ -1333,6 +1437,9 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
     // split arrays of the carried potentials (they depend on eps through eps*log w)
     // cur_f / cur_g are 0 at the start of every level (see the copy kernels below)
     CUDA_TRY(S->prep_level(s));
+    // g_init: f = g_init^{C,eps_0} (in place in buffer 0; the row pass's shift
+    // is the zero f there)
+    if (t == 0 && ginit) CUDA_TRY(S->pass_row(MODE_SK_ROW, s));
     CUDA_TRY(S->pass_col(MODE_G_INIT, s));
     if (use_nr) {
       // V^T D_a V and V^T a for this level's modes
@@ -1390,36 +1497,31 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
     reset_buffers_kernel<<<1, 1, 0, s>>>(S->dSt);
     const bool need_modes = ell > 0 && !last && (o->sequential_modes || !have_modes);
     if (need_modes) {
-      cudaEvent_t a0, a1;
-      CUDA_TRY(cudaEventCreate(&a0));
-      CUDA_TRY(cudaEventCreate(&a1));
-      CUDA_TRY(cudaEventRecord(a0, s));
-      // the modes use the converged (f, g) of this level: rs[0]/cs[0] splits
-      // were refreshed by normalize_buffers_kernel (which re-splits buffer 0)
-      const int keep = have_modes ? ell : 0;
-      init_block_kernel<<<std::min(ceil_div((long long)n * S->p, 256), 8 * ctx->nsm), 256, 0, s>>>(
-          S->Xb, n, S->p, 0x5EEDull + 977ull * (unsigned long long)t, have_modes ? S->V : nullptr,
-          keep);
-      // orthonormalise the start block: Z = (X0 - 1 c^T) L^{-T}
-      launch_eig_gram(S->Xb, nullptr, P.a, n, S->p, S->eppart, S->GXX, nullptr, S->cvec, s);
-      CUDA_TRY(cudaGetLastError());
-      launch_eig_small(S->p, ell, 0, S->GXX, S->Tm, S->cvec, S->Bm, S->theta, S->resid, S->efail, s);
-      launch_pdl(apply_kernel, dim3(ceil_div(n, 64)), dim3(256), (size_t)(S->p * S->p + 64 * S->p) * 4, s, 
-          S->Xb, S->cvec, S->Bm, n, S->p, S->Zb, nullptr);
-      eig_setup_kernel<<<1, 1, 0, s>>>(S->dSt, o->eig_tol, o->eig_max_iter,
-                                       o->eig_max_iter + 4);
-      eot_status e = S->run_loop(S->ex_eig, 1, o->eig_max_iter + 5);
+      eot_status e = compute_modes(t);
       if (e != EOT_OK) return e;
-      take_cols_kernel<<<std::min(ceil_div((long long)n * ell, 256), 8 * ctx->nsm), 256, 0, s>>>(
-          S->Zb, n, S->p, ell, S->V);
-      CUDA_TRY(cudaEventRecord(a1, s));
-      eig_events.push_back({a0, a1});
-      CUDA_TRY(cudaMemcpyAsync(hLev + L + t, S->dSt, sizeof(State), cudaMemcpyDeviceToHost, s));
       lev_eig[t] = 1;
-      have_modes = true;
     }
   }
   CUDA_TRY(cudaEventRecord(lev_ev[L], s));
+  if (V_kept) *V_kept = (V_keep_dev && have_modes) ? 1 : 0;
+  if (V_keep_dev && have_modes)
+    CUDA_TRY(cudaMemcpyAsync(V_keep_dev, S->V, (size_t)n * ell * sizeof(float),
+                             cudaMemcpyDeviceToDevice, s));
+  const size_t eig_before_vout = eig_events.size();
+  std::vector<float> hvo;
+  if (pr->V_out) {
+    // the modes of the returned pair at eps (buffers 0, split at eps)
+    eot_status e = compute_modes(L);
+    if (e != EOT_OK) return e;
+    if (dev) {
+      widen_kernel<<<std::min(ceil_div((long long)n * ell, 256), 8 * ctx->nsm), 256, 0, s>>>(
+          S->V, (long long)n * ell, pr->V_out);
+      CUDA_TRY(cudaGetLastError());
+    } else {
+      hvo.resize((size_t)n * ell);
+      CUDA_TRY(cudaMemcpyAsync(hvo.data(), S->V, hvo.size() * sizeof(float), cudaMemcpyDeviceToHost, s));
+    }
+  }
   // ---- finish: evaluation passes at (f, g) = buffers 0, scores, gauge ----
   CUDA_TRY(S->prep_level(s));
   CUDA_TRY(S->pass_row(MODE_EVAL, s));
@@ -1440,6 +1542,7 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   }
   CUDA_TRY(cudaEventSynchronize(ev1));
   CUDA_TRY(cudaGetLastError());
+  for (size_t k = 0; k < hvo.size(); ++k) pr->V_out[k] = (double)hvo[k];
   // ---- statistics ----
   eot_result r{};
   const State& fin = hLev[L - 1];
@@ -1452,7 +1555,7 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
     float em = 0.f;
     cudaEventElapsedTime(&em, eig_events[k].first, eig_events[k].second);
     eig_s += em * 1e-3;
-    if (k + 1 == eig_events.size()) last_eig = em * 1e-3;
+    if (k + 1 == eig_before_vout) last_eig = em * 1e-3;   // the modes the last level used
     cudaEventDestroy(eig_events[k].first);
     cudaEventDestroy(eig_events[k].second);
   }
@@ -1479,6 +1582,13 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
       launches += 1 + 3 + 1 + 1 + 1 + (long long)hLev[L + t].body_runs * S->eig_body_launches() + 1;
     }
   }
+  if (pr->V_out) {
+    r.eig_iters += hLev[2 * L].eig_iter;
+    launches += 1 + 3 + 1 + 1 + 1 + (long long)hLev[2 * L].body_runs * S->eig_body_launches() + 1 +
+                (dev ? 1 : 0);
+  }
+  if (!hvi.empty()) launches += 6;   // V_init: start block, Gram (2), Cholesky, apply, copy
+  if (ginit) launches += 1;          // the row half-step of g_init
   launches += 5 + 2LL * verify_rounds;
   launches += (long long)resumed_bodies * (lev_nr[L - 1] ? nr_body * S->unroll_sknr + 1 : 2 * S->unroll_sk + 1);
   launches += resumed_coop;
@@ -1571,8 +1681,15 @@ static double task_ns(const BatchModel& M, double iters, int n, int m, int G) {
 // Whether a batch member runs as the transposed problem: plain Sinkhorn is
 // symmetric in the two sides, and with more rows than columns the column
 // half-step (one CTA streams every row of its columns) gets the short side to
-// stream.  A warm start f_init fixes the roles.
-static bool batch_transposed(int n, int m, bool has_f_init) { return n > m && !has_f_init; }
+// stream.  A warm start fixes the roles: init = 1, an f_init (not transposed);
+// init = 2, a g_init without f_init (transposed: the transposed problem's f is
+// g, and its first half-step the row transform of g_init); 0, none.
+static bool batch_transposed(int n, int m, int init) {
+  return init == 2 ? true : (init != 0 ? false : n > m);
+}
+// The warm start of a batch member in the roles it runs in, and its kind.
+static const double* batch_init(const eot_problem& q) { return q.f_init ? q.f_init : q.g_init; }
+static int batch_init_kind(const eot_problem& q) { return q.f_init ? 1 : (q.g_init ? 2 : 0); }
 
 // Predicted iterations of a batch member: the sum over its eps levels of
 // min(0.66 / eps, max_iter), at least 1.
@@ -1744,7 +1861,7 @@ static eot_status run_batch(int count, const eot_problem* probs, const eot_optio
     // plain Sinkhorn is symmetric in the two sides: with more rows than
     // columns the problem runs transposed, so that the column half-step (one
     // CTA streams all rows of its columns) has the short side to stream
-    p.trans = batch_transposed(q.n, q.m, q.f_init != nullptr);
+    p.trans = batch_transposed(q.n, q.m, batch_init_kind(q));
     p.n = p.trans ? q.m : q.n;
     p.m = p.trans ? q.n : q.m;
     p.d = q.d;
@@ -1759,7 +1876,7 @@ static eot_status run_batch(int count, const eot_problem* probs, const eot_optio
       } else {
         p.h_c = htake(sizeof(float) * (size_t)q.n * q.m);
       }
-      if (q.f_init) p.h_f = htake(sizeof(double) * q.n);
+      if (batch_init(q)) p.h_f = htake(sizeof(double) * p.n);
     }
   }
   // ---- gang sizes (plan_gangs), iterations estimated from the eps schedule ----
@@ -1869,7 +1986,7 @@ static eot_status run_batch(int count, const eot_problem* probs, const eot_optio
     } else {
       std::memcpy(hst + p.h_c, q.C, sizeof(float) * (size_t)q.n * q.m);
     }
-    if (q.f_init) std::memcpy(hst + p.h_f, q.f_init, sizeof(double) * q.n);
+    if (batch_init(q)) std::memcpy(hst + p.h_f, batch_init(q), sizeof(double) * p.n);
   }
   if (hbytes) CUDA_TRY(cudaMemcpyAsync(dmem, hst, hbytes, cudaMemcpyHostToDevice, s));
   // ---- set-up descriptors and kernels ----
@@ -1915,8 +2032,8 @@ static eot_status run_batch(int count, const eot_problem* probs, const eot_optio
     I.cmax = d_cmax + k;
     I.bad = d_bad + 2 * k;
     maxrows = std::max(maxrows, p.n);
-    if (q.f_init)
-      CUDA_TRY(cudaMemcpyAsync(L.f, host ? (const void*)(dmem + p.h_f) : (const void*)q.f_init,
+    if (batch_init(q))
+      CUDA_TRY(cudaMemcpyAsync(L.f, host ? (const void*)(dmem + p.h_f) : (const void*)batch_init(q),
                                sizeof(double) * p.n, cudaMemcpyDeviceToDevice, s));
   }
   CUDA_TRY(cudaMemcpyAsync(d_in, hin.data(), sizeof(BatchIn) * count, cudaMemcpyHostToDevice, s));
@@ -1954,13 +2071,14 @@ static eot_status run_batch(int count, const eot_problem* probs, const eot_optio
     std::memcpy(&cmax, &bits, 8);
     if (q.normalize_cost && cmax > 0.0) cmax = 1.0;
     double fmax = 0.0;
-    if (q.f_init) {
+    if (batch_init(q)) {
       std::vector<double> hf(p.n);
-      if (q.mem == EOT_MEM_HOST) std::memcpy(hf.data(), q.f_init, sizeof(double) * p.n);
-      else CUDA_TRY(cudaMemcpy(hf.data(), q.f_init, sizeof(double) * p.n, cudaMemcpyDeviceToHost));
+      if (q.mem == EOT_MEM_HOST) std::memcpy(hf.data(), batch_init(q), sizeof(double) * p.n);
+      else CUDA_TRY(cudaMemcpy(hf.data(), batch_init(q), sizeof(double) * p.n, cudaMemcpyDeviceToHost));
       for (double v : hf) {
         if (!std::isfinite(v)) {
-          st[k] = fail(EOT_EINVAL, "f_init has non-finite entries");
+          st[k] = fail(EOT_EINVAL, q.f_init ? "f_init has non-finite entries"
+                                            : "g_init has non-finite entries");
           errs[k] = t_err;
           pl[k].ok = false;
           break;
@@ -2411,7 +2529,7 @@ eot_status eot_batch_plan(int32_t count, const int32_t* n, const int32_t* m, con
   std::unique_ptr<bool[]> ok(new bool[count]);
   for (int k = 0; k < count; ++k) {
     if (n[k] < 1 || m[k] < 1 || !finite_pos(eps[k])) return fail(EOT_EINVAL, "member with n, m < 1 or eps <= 0");
-    const bool tr = batch_transposed(n[k], m[k], has_f_init && has_f_init[k]);
+    const bool tr = batch_transposed(n[k], m[k], has_f_init ? (has_f_init[k] == 2 ? 2 : (has_f_init[k] ? 1 : 0)) : 0);
     transposed_out[k] = tr ? 1 : 0;
     nn[k] = tr ? m[k] : n[k];
     mm[k] = tr ? n[k] : m[k];
@@ -2543,7 +2661,7 @@ eot_status eot_spectral_modes_filtered(int32_t n, int32_t m, const float* C, con
     CUDA_TRY(cudaMemcpyAsync(S->V, hvf.data(), hvf.size() * sizeof(float), cudaMemcpyHostToDevice, s));
   }
   init_block_kernel<<<std::min(ceil_div((long long)n * p, 256), 8 * S->ctx->nsm), 256, 0, s>>>(
-      S->Xb, n, p, 0x5EEDull, use_V_as_start ? S->V : nullptr, use_V_as_start ? ell : 0);
+      S->Xb, n, p, 0x5EEDull, use_V_as_start ? S->V : nullptr, use_V_as_start ? ell : 0, 1);
   launch_eig_gram(S->Xb, nullptr, P.a, n, p, S->eppart, S->GXX, nullptr, S->cvec, s);
   CUDA_TRY(cudaGetLastError());
   launch_eig_small(p, ell, 0, S->GXX, S->Tm, S->cvec, S->Bm, S->theta, S->resid, S->efail, s);
@@ -2739,11 +2857,11 @@ struct eot_server {
     eot_status status = EOT_PENDING;
     bool done = false;
   };
-  // Device-resident potentials of a cloud, shared by the cache and by the
-  // solves that warm-start from them: the buffer is freed when the last
-  // holder lets go (a cache update does not free it under a running solve).
+  // Device-resident potentials (and modes) of a cloud, shared by the cache
+  // and by the solves that warm-start from them: a buffer is freed when the
+  // last holder lets go (a cache update does not free it under a running solve).
   struct DevBuf {
-    double* p = nullptr;
+    void* p = nullptr;
     ~DevBuf() {
       // stream-ordered: every solve that read it has completed (a holder lets
       // go only after its solve synchronised), and no device-wide sync
@@ -2751,9 +2869,10 @@ struct eot_server {
     }
   };
   struct Cached {
-    int n = 0, m = 0;
+    int n = 0, m = 0, ell = 0;
     double eps = 0;
     std::shared_ptr<DevBuf> f;
+    std::shared_ptr<DevBuf> V;   // n x ell float32: the modes of the last level (ell > 0)
   };
   eot_options opt{};
   size_t budget = 0;
@@ -2820,31 +2939,40 @@ struct eot_server {
       eot_options o = r->opt;
       o.stream = nullptr;
       const double* finit = nullptr;
+      const float* vstart = nullptr;
       if (warm.f) {
-        finit = warm.f->p;
+        finit = static_cast<const double*>(warm.f->p);
+        if (warm.V && o.ell > 0 && warm.ell == o.ell) vstart = static_cast<const float*>(warm.V->p);
         if (warm.eps > r->prob.eps) {
           o.eps_start = warm.eps * (o.eps_factor > 0 && o.eps_factor < 1 ? o.eps_factor : 0.5);
         } else {
           o.eps_start = 0.0;
         }
       }
-      std::shared_ptr<DevBuf> keep;
+      std::shared_ptr<DevBuf> keep, keepV;
       eotk::DeviceCtx* wctx = nullptr;
-      if (r->cloud_id && eotk::get_ctx(&wctx) == EOT_OK) {
-        keep = std::make_shared<DevBuf>();
-        if (cudaMallocAsync(reinterpret_cast<void**>(&keep->p), r->prob.n * sizeof(double),
-                            wctx->stream) != cudaSuccess) {
+      auto dev_buf = [&](size_t bytes) {
+        auto b = std::make_shared<DevBuf>();
+        if (cudaMallocAsync(&b->p, bytes, wctx->stream) != cudaSuccess) {
           cudaGetLastError();
-          keep->p = nullptr;
-          keep.reset();
+          b->p = nullptr;
+          b.reset();
         }
+        return b;
+      };
+      if (r->cloud_id && eotk::get_ctx(&wctx) == EOT_OK) {
+        keep = dev_buf(r->prob.n * sizeof(double));
+        if (keep && o.ell > 0) keepV = dev_buf((size_t)r->prob.n * o.ell * sizeof(float));
       }
       r->f.assign(r->prob.n, 0.0);
       r->g.assign(r->prob.m, 0.0);
+      int vkept = 0;
       eot_status st = eotk::solve_one(&r->prob, &o, r->f.data(), r->g.data(), &r->res, finit,
-                                      keep ? keep->p : nullptr);
+                                      keep ? static_cast<double*>(keep->p) : nullptr, vstart,
+                                      keepV ? static_cast<float*>(keepV->p) : nullptr, &vkept);
       eotk::drop_thread_cache();
-      warm.f.reset();   // this solve no longer reads the cached potentials
+      warm.f.reset();   // this solve no longer reads the cached potentials or modes
+      warm.V.reset();
       {
         std::lock_guard<std::mutex> lk(mu);
         in_use -= r->footprint;
@@ -2862,6 +2990,8 @@ struct eot_server {
           c.n = r->prob.n;
           c.m = r->prob.m;
           c.eps = r->prob.eps;
+          c.V = vkept ? keepV : nullptr;
+          c.ell = vkept ? o.ell : 0;
         }
       }
       cv.notify_all();
@@ -2985,7 +3115,11 @@ eot_status eot_server_submit_opts(eot_server* srv, const eot_problem* prob, uint
   if (ro.prec == EOT_PREC_FP32 && prob->X && prob->Y && prob->d >= 1 && prob->d <= 64 &&
       ro.ell == 0 && 4.0 * (double)prob->n * (double)prob->m > eotk::kServeStoredCostMax)
     ro.prec = EOT_PREC_SPLIT_TC;
-  eot_status vs = eotk::validate(prob, &ro);
+  // the server warm-starts from its own resident state only
+  eot_problem pv = *prob;
+  pv.f_init = pv.g_init = pv.V_init = nullptr;
+  pv.V_out = nullptr;
+  eot_status vs = eotk::validate(&pv, &ro);
   if (vs != EOT_OK) return vs;
   auto r = std::make_shared<eot_server::Request>();
   const int n = prob->n, m = prob->m, d = prob->d;
@@ -3002,7 +3136,8 @@ eot_status eot_server_submit_opts(eot_server* srv, const eot_problem* prob, uint
   r->prob.C = prob->C ? r->C.data() : nullptr;
   r->prob.X = prob->X ? r->X.data() : nullptr;
   r->prob.Y = prob->X ? r->Y.data() : nullptr;
-  r->prob.f_init = nullptr;
+  r->prob.f_init = r->prob.g_init = r->prob.V_init = nullptr;
+  r->prob.V_out = nullptr;
   r->cloud_id = cloud_id;
   r->opt = ro;
   eotk::DeviceCtx* ctx = nullptr;

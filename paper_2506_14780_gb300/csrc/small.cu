@@ -407,6 +407,10 @@ __global__ void fprime_kernel(const Prob* __restrict__ PP) {
 //           L L^T = Q^T (GXX - c c^T) Q and B = Q L^{-T}.
 //   mode 2 (orthonormalise a badly scaled block): as mode 0 with the columns
 //           scaled first, Q = diag((GXX - c c^T)_kk^(-1/2)), B = Q L^{-T}.
+//   mode 3 (orthonormalise given modes): as mode 0 with the dead-pivot
+//           threshold at 1e-5 of the largest pivot instead of 1e-9 (an exactly
+//           dependent column keeps a pivot near 1e-6 from the float32 Gram
+//           entries; it is dropped instead of becoming amplified noise).
 //   outputs B (p x p float32), theta (p), max residual over the first l
 //   (mode 1), and (mode 1, when Qout is given) the Ritz rotation Q.  A
 //   nonzero *skip makes the launch return at once.
@@ -680,7 +684,7 @@ __global__ void __launch_bounds__(kEH * kEH) eig_small_kernel(int p, int l, int 
         Q[r * kES + q] = (r == q) ? rsqrtf(fmaxf(G[r * kES + r], 1e-30f)) : 0.f;
     __syncthreads();
   }
-  if (mode >= 1) {
+  if (mode == 1 || mode == 2) {
     // W = G Q: thread (ty, tx) forms rows ty, ty + nx and columns tx, tx + nx
     // (p <= 2 nx), each loaded value used twice
     block2_product(G, Q, W, p, ty, tx, nx, false);
@@ -722,7 +726,7 @@ __global__ void __launch_bounds__(kEH * kEH) eig_small_kernel(int p, int l, int 
   if (tid == 0) {
     float mx = 0.f;
     for (int k = 0; k < p; ++k) mx = fmaxf(mx, G[k * kES + k]);
-    red[0] = fmaxf(1e-9f * mx, 1e-30f);
+    red[0] = fmaxf((mode == 3 ? 1e-5f : 1e-9f) * mx, 1e-30f);
   }
   __syncthreads();
   const float tiny = red[0];
@@ -1059,14 +1063,15 @@ void launch_cheb_step(const float* X, const double* a, const float* Yc, float* Y
 
 // SplitMix64 start block (Steele, Lea & Flood 2014): u = top 53 bits / 2^53,
 // entry (i, k) uses counter seed + (i*p + k + 1) * gamma; columns < keep are
-// copied from src (n x keep, float32) instead.
+// copied from src (n x keep, float32) instead, except (redraw_zero != 0) its
+// zero entries, so that a dead (zero) column of earlier modes is drawn anew.
 __global__ void init_block_kernel(float* __restrict__ Z, int len, int p, unsigned long long seed,
-                                  const float* __restrict__ src, int keep) {
+                                  const float* __restrict__ src, int keep, int redraw_zero) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < len * p; e += gridDim.x * blockDim.x) {
     const int i = e / p, k = e - i * p;
     if (k < keep && src) {
       const float v = src[(size_t)i * keep + k];
-      if (v != 0.f) {   // a dead (zero) column of the previous modes is drawn anew
+      if (v != 0.f || !redraw_zero) {
         Z[e] = v;
         continue;
       }

@@ -33,7 +33,8 @@ class eot_problem(C.Structure):
     _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("d", C.c_int32),
                 ("a", C.c_void_p), ("b", C.c_void_p), ("C", C.c_void_p),
                 ("X", C.c_void_p), ("Y", C.c_void_p), ("mem", C.c_int32),
-                ("normalize_cost", C.c_int32), ("eps", C.c_double), ("f_init", C.c_void_p)]
+                ("normalize_cost", C.c_int32), ("eps", C.c_double), ("f_init", C.c_void_p),
+                ("g_init", C.c_void_p), ("V_init", C.c_void_p), ("V_out", C.c_void_p)]
 
 
 class eot_options(C.Structure):
@@ -181,11 +182,15 @@ def default_options(**kw) -> eot_options:
 
 
 def make_problem(a, b, C=None, X=None, Y=None, eps=1e-2, normalize_cost=False, f_init=None,
-                 keep: Optional[list] = None, cost_dtype=np.float32) -> eot_problem:
+                 keep: Optional[list] = None, cost_dtype=np.float32, g_init=None, V_init=None,
+                 V_out=None) -> eot_problem:
     """Marshal a problem.  ``cost_dtype`` is float64 for ``EOT_PREC_FP64`` solves
-    (the cost matrix is read as double there) and float32 otherwise."""
+    (the cost matrix is read as double there) and float32 otherwise.  ``V_out``
+    (n x ell float64, written by the solve) must be a writable contiguous array
+    or tensor: it is passed as is."""
     keep = [] if keep is None else keep
-    dev = any(_is_torch(x) for x in (a, b, C, X, Y) if x is not None)
+    dev = any(_is_torch(x) for x in (a, b, C, X, Y, f_init, g_init, V_init, V_out)
+              if x is not None)
     p = eot_problem()
     p.n = int(a.shape[0])
     p.m = int(b.shape[0])
@@ -199,6 +204,13 @@ def make_problem(a, b, C=None, X=None, Y=None, eps=1e-2, normalize_cost=False, f
     p.normalize_cost = 1 if normalize_cost else 0
     p.eps = float(eps)
     p.f_init = _ptr(f_init, keep, np.float64)
+    p.g_init = _ptr(g_init, keep, np.float64)
+    p.V_init = _ptr(V_init, keep, np.float64)
+    if V_out is not None and not _is_torch(V_out) and not (
+            isinstance(V_out, np.ndarray) and V_out.dtype == np.float64
+            and V_out.flags.c_contiguous and V_out.flags.writeable):
+        raise ValueError("V_out must be a writable C-contiguous float64 array")
+    p.V_out = _ptr(V_out, keep, np.float64)
     return p
 
 
@@ -221,12 +233,18 @@ def eot_solve(problem: eot_problem, options: eot_options, f_out, g_out):
 
 
 def solve(prob, **opts):
-    """Solve a ``workloads.Problem`` (host arrays).  Returns (f, g, result dict)."""
+    """Solve a ``workloads.Problem`` (host arrays).  Returns (f, g, result dict).
+    Warm starts ``f_init``, ``g_init``, ``V_init`` pass through; with
+    ``return_modes=True`` (and ell > 0) the result dict holds the modes of the
+    returned pair under "V" (eot_problem.V_out)."""
     keep = []
     f64 = opts.get("prec", EOT_PREC_FP32) == EOT_PREC_FP64
+    want_V = opts.pop("return_modes", False)
+    V = np.zeros((prob.a.shape[0], opts.get("ell", 0))) if want_V else None
     p = make_problem(prob.a, prob.b, C=prob.C, X=prob.X, Y=prob.Y, eps=prob.eps,
                      normalize_cost=prob.normalize_cost, f_init=opts.pop("f_init", None),
-                     keep=keep, cost_dtype=np.float64 if f64 else np.float32)
+                     keep=keep, cost_dtype=np.float64 if f64 else np.float32,
+                     g_init=opts.pop("g_init", None), V_init=opts.pop("V_init", None), V_out=V)
     o = default_options(**opts)
     f = np.zeros(p.n)
     g = np.zeros(p.m)
@@ -235,6 +253,8 @@ def solve(prob, **opts):
     r["return_status"] = st
     if st < 0:
         r["error"] = last_error()
+    if want_V:
+        r["V"] = V
     return f, g, r
 
 

@@ -36,6 +36,10 @@ def test_warm_start_keeps_the_roles(eot):
     n, m, eps = [500, 500, 90], [90, 90, 500], [1e-2] * 3
     st, gang, tr = eot.eot_batch_plan(n, m, eps, _opts(eot), 304, **MODEL, has_f_init=[0, 1, 0])
     assert st == eot.EOT_OK and list(tr) == [1, 0, 0]
+    # a g_init without f_init (kind 2) runs transposed whatever the shape: the
+    # transposed problem's f is the caller's g
+    st, gang, tr = eot.eot_batch_plan(n, m, eps, _opts(eot), 304, **MODEL, has_f_init=[2, 2, 2])
+    assert st == eot.EOT_OK and list(tr) == [1, 1, 1]
 
 
 def test_cost_per_cta_floor(eot):
