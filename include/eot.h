@@ -190,6 +190,30 @@ void eot_default_options(eot_options *opt);
 eot_status eot_solve(const eot_problem *prob, const eot_options *opt,
                      double *f_out, double *g_out, eot_result *res);
 
+/* One record of a solve's iteration trace: iteration `iter` (1-based within
+ * its level; a final level continued after its verification restarts at 1)
+ * of the level at `eps`: the stop test's L1 value at f_k (the column term
+ * ||pi(f_k, g_k)^T 1 - b||_1; the row term is zero after the row half-step,
+ * Alg. 4.1 line 5) and Q_semi(f_k) (Eq. def_Q_semi); for SK-NR the Newton
+ * trial's dq = Q_semi(f') - Q_semi(f_k) and accepted = 1 (dq > 0), 0
+ * (rejected, or -H_V not positive definite: dq NaN); accepted = -1 and dq NaN
+ * for a plain Sinkhorn iteration or one whose test stopped the level. */
+typedef struct {
+    double eps, l1, q_semi, dq;
+    int32_t iter, accepted;
+} eot_trace_rec;
+
+/* eot_solve with the per-iteration trace: the device appends one record per
+ * iteration to a ring of trace_cap records (device memory of the call), copied
+ * back at the end: trace (host, trace_cap records) receives the last
+ * min(count, trace_cap) records, oldest first; *trace_count (may be NULL) the
+ * number of iterations recorded over all levels (count).  The solve's
+ * arithmetic and results are those of eot_solve.  EOT_EINVAL if trace is NULL
+ * or trace_cap < 1. */
+eot_status eot_solve_traced(const eot_problem *prob, const eot_options *opt, double *f_out,
+                            double *g_out, eot_result *res, eot_trace_rec *trace,
+                            int32_t trace_cap, int64_t *trace_count);
+
 /* Solve count independent problems of uneven sizes.  Plain Sinkhorn on float32
  * costs (opt->ell == 0, FP32) runs every problem in one persistent launch;
  * SK-NR (ell > 0) and the other precisions run each problem as a whole solve

@@ -61,7 +61,8 @@ def build(verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
     tmp = LIB + ".tmp"
-    cmd = [_nvcc(), "-shared"] + ARCH + ["-o", tmp] + objs
+    # -ldl: the NVTX v3 header finds a profiler's injection library with dlopen
+    cmd = [_nvcc(), "-shared"] + ARCH + ["-o", tmp] + objs + ["-ldl"]
     if verbose:
         print(" ".join(cmd), flush=True)
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -18,6 +18,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <atomic>
@@ -37,6 +38,16 @@
 #include "batch.h"
 
 namespace eotk {
+
+// NVTX range over a phase of the host driver (solve, level, modes, finish;
+// batch and server requests), for profilers that attach; without one a push
+// or pop is a check of a function pointer.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ---- kernels defined in the other translation units ----------------------
 cudaError_t launch_col_pass(const Prob* dP, const Prob& hP, int mode, cudaStream_t s);
@@ -1114,11 +1125,16 @@ __global__ void stamp_kernel(unsigned long long* t) {
 // f_init_dev replaces pr->f_init; V_start_dev (n x ell float32, modes this
 // library computed: a-orthonormal, orthogonal to a) are the first level's
 // modes; f_keep_dev receives the returned f; V_keep_dev receives the modes
-// the last level used, and *V_kept whether there were any.
+// the last level used, and *V_kept whether there were any.  trace_dev (device,
+// trace_cap records) receives the iteration trace, *trace_n the number of
+// records written (the last trace_cap are held, as a ring).
 static eot_status solve_one(const eot_problem* pr, const eot_options* o, double* f_out,
                             double* g_out, eot_result* res, const double* f_init_dev = nullptr,
                             double* f_keep_dev = nullptr, const float* V_start_dev = nullptr,
-                            float* V_keep_dev = nullptr, int* V_kept = nullptr) {
+                            float* V_keep_dev = nullptr, int* V_kept = nullptr,
+                            TraceRec* trace_dev = nullptr, int trace_cap = 0,
+                            long long* trace_n = nullptr) {
+  NvtxRange nv_solve("eot_solve");
   eot_status vs = validate(pr, o);
   if (vs != EOT_OK) return vs;
   DeviceCtx* ctx = nullptr;
@@ -1301,6 +1317,16 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   P.pot_bound = gram ? 1e300 : std::ldexp(1.0, 22 - q) / 2.0 - cmax;
   P.wait_ns = wait_ns(o);
   P.stall_window = o->stall_window;
+  // the solver's host copy forgets the trace buffer however the solve ends
+  struct TraceReset {
+    Prob* p;
+    ~TraceReset() {
+      p->trace = nullptr;
+      p->trace_cap = 0;
+    }
+  } trace_reset{&P};
+  P.trace = trace_dev;
+  P.trace_cap = trace_dev ? trace_cap : 0;
   P.eps = eps0;
   P.k2 = (float)(1.0 / (eps0 * std::log(2.0)));
   P.k2lo = (float)(1.0 / (eps0 * std::log(2.0)) - (double)P.k2);
@@ -1369,6 +1395,7 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   // previous modes (random columns besides), orthonormalised, then the
   // subspace iteration's graph.  Slot t of the mode states in hLev.
   auto compute_modes = [&](int t) -> eot_status {
+    NvtxRange nv_modes("modes");
     cudaEvent_t a0, a1;
     CUDA_TRY(cudaEventCreate(&a0));
     CUDA_TRY(cudaEventCreate(&a1));
@@ -1431,6 +1458,10 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
     const double tol = last ? (S->f64 ? o->tol : 0.75 * o->tol)
                             : (o->level_tol > 0.0 ? o->level_tol : o->tol);
     const bool use_nr = ell > 0 && have_modes;
+    char nv_name[64];
+    std::snprintf(nv_name, sizeof(nv_name), "level %d eps %.3g %s", t, eps,
+                  use_nr ? "SK-NR" : "Sinkhorn");
+    NvtxRange nv_level(nv_name);
     CUDA_TRY(cudaEventRecord(lev_ev[t], s));
     level_setup_kernel<<<1, 1, 0, s>>>(S->dP, eps, (float)(1.0 / (eps * std::log(2.0))), tol,
                                        o->max_iter, use_nr ? body_cap_nr : body_cap_sk);
@@ -1523,6 +1554,7 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
     }
   }
   // ---- finish: evaluation passes at (f, g) = buffers 0, scores, gauge ----
+  NvtxRange nv_finish("finish");
   CUDA_TRY(S->prep_level(s));
   CUDA_TRY(S->pass_row(MODE_EVAL, s));
   CUDA_TRY(S->pass_col(MODE_EVAL, s));
@@ -1613,6 +1645,7 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   else if (fin.done == 6) status = r.l1_marginal < o->tol ? EOT_OK : EOT_NOT_CONVERGED;
   else status = EOT_NOT_CONVERGED;
   r.stalled = fin.done == 6 ? 1 : 0;
+  if (trace_n) *trace_n = fin.trace_n;
   bool wait_gave_up = fin.done == 5;
   for (int t = 0; t < L - 1 && status == EOT_OK; ++t) {
     if (hLev[t].done == 3) status = EOT_ENUMERIC;
@@ -2271,6 +2304,47 @@ eot_status eot_solve(const eot_problem* prob, const eot_options* opt, double* f_
   else eot_default_options(&o);
   eot_status s = solve_one(prob, &o, f_out, g_out, res);
   if (res && s < 0) res->status = s;
+  return s;
+}
+
+static_assert(sizeof(eot_trace_rec) == sizeof(eotk::TraceRec), "eot_trace_rec layout");
+
+eot_status eot_solve_traced(const eot_problem* prob, const eot_options* opt, double* f_out,
+                            double* g_out, eot_result* res, eot_trace_rec* trace,
+                            int32_t trace_cap, int64_t* trace_count) {
+  if (!f_out || !g_out) return fail(EOT_EINVAL, "f_out and g_out are required");
+  if (!trace || trace_cap < 1) return fail(EOT_EINVAL, "trace needs trace_cap >= 1 host records");
+  eot_options o;
+  if (opt) o = *opt;
+  else eot_default_options(&o);
+  eotk::DeviceCtx* ctx = nullptr;
+  eot_status cs = eotk::get_ctx(&ctx);
+  if (cs != EOT_OK) return cs;
+  eotk::TraceRec* dtr = nullptr;
+  CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&dtr), sizeof(eotk::TraceRec) * trace_cap,
+                           ctx->stream));
+  long long cnt = 0;
+  eot_status s = solve_one(prob, &o, f_out, g_out, res, nullptr, nullptr, nullptr, nullptr,
+                           nullptr, dtr, trace_cap, &cnt);
+  if (res && s < 0) res->status = s;
+  std::vector<eotk::TraceRec> h(trace_cap);
+  cudaError_t e = cudaSuccess;
+  if (s >= 0) {
+    e = cudaMemcpyAsync(h.data(), dtr, sizeof(eotk::TraceRec) * trace_cap, cudaMemcpyDeviceToHost,
+                        ctx->stream);
+  }
+  const cudaError_t ef = cudaFreeAsync(dtr, ctx->stream);
+  const cudaError_t es = cudaStreamSynchronize(ctx->stream);
+  if (s < 0) return s;
+  if (e == cudaSuccess) e = ef;
+  if (e == cudaSuccess) e = es;
+  if (e != cudaSuccess) return fail(EOT_ECUDA, cudaGetErrorString(e));
+  // oldest record first
+  const long long held = std::min<long long>(cnt, trace_cap);
+  const long long k0 = cnt > trace_cap ? cnt % trace_cap : 0;
+  for (long long i = 0; i < held; ++i)
+    std::memcpy(&trace[i], &h[(size_t)((k0 + i) % trace_cap)], sizeof(eot_trace_rec));
+  if (trace_count) *trace_count = cnt;
   return s;
 }
 
@@ -2936,6 +3010,7 @@ struct eot_server {
             warm = it->second;
         }
       }
+      eotk::NvtxRange nv_req("server request");
       eot_options o = r->opt;
       o.stream = nullptr;
       const double* finit = nullptr;
@@ -3006,6 +3081,7 @@ eot_status eot_solve_batch(int32_t count, const eot_problem* probs, const eot_op
   if (count < 0 || (count > 0 && (!probs || !f_out || !g_out)))
     return fail(EOT_EINVAL, "bad batch arguments");
   if (count == 0) return EOT_OK;
+  eotk::NvtxRange nv_batch("eot_solve_batch");
   eot_options o;
   if (opt) o = *opt;
   else eot_default_options(&o);

@@ -58,6 +58,15 @@ enum PassMode : int {
 // Op(pi)^T Z, the fused SK-NR column pass S4, the row product Op(pi) Z.
 enum AccMode : int { ACC_KCOL = 0, ACC_S4 = 1, ACC_KROW = 2 };
 
+// One record of the per-solve iteration trace (the layout of eot_trace_rec):
+// the level's eps, the L1 test at f_k and Q_semi(f_k) of iteration `iter`,
+// and the Newton trial's dq with its outcome (1 accepted, 0 rejected or not
+// solvable, -1 no trial: plain Sinkhorn, or the level stopped at the test).
+struct TraceRec {
+  double eps, l1, q_semi, dq;
+  int iter, accepted;
+};
+
 // Device-resident solver state (one per problem).
 struct State {
   int iter;        // Algorithm 4.1 iterations done at the current level
@@ -88,6 +97,7 @@ struct State {
   int nr_degenerate;   // set when the SK-NR products saw exponentials out of range
   double stall_l1;     // L1 error at the last stall checkpoint of this level
   int stall_at;        // iteration of the next stall checkpoint
+  long long trace_n;   // iteration records written to Prob::trace (all levels)
 };
 
 // Split arrays of one potential buffer (see eot_device.cuh).
@@ -188,6 +198,9 @@ struct Prob {
   // plain-mode outputs
   double* out_plain;       // standalone transform output
   double* logratio_plain;
+  // iteration trace (eot_solve_traced): ring of trace_cap records, or NULL
+  TraceRec* trace;
+  int trace_cap;
 };
 
 // Arguments of the accumulating passes (accum.cu).
@@ -210,6 +223,27 @@ struct AccArgs {
 };
 
 #ifdef __CUDACC__
+// Iteration trace, written by the one thread that takes iteration `iter`'s
+// stop decision: a new record (the oldest is overwritten once trace_cap are
+// held); the Newton step of that iteration completes it (trace_trial).
+__device__ inline void trace_test(const Prob& P, State* st, int iter, double l1, double qsemi) {
+  if (!P.trace) return;
+  TraceRec& r = P.trace[st->trace_n % P.trace_cap];
+  r.eps = P.eps;
+  r.l1 = l1;
+  r.q_semi = qsemi;
+  r.dq = __longlong_as_double(0x7ff8000000000000ll);   // NaN: no trial (yet)
+  r.iter = iter;
+  r.accepted = -1;
+  st->trace_n += 1;
+}
+__device__ inline void trace_trial(const Prob& P, State* st, double dq, int accepted) {
+  if (!P.trace || st->trace_n == 0) return;
+  TraceRec& r = P.trace[(st->trace_n - 1) % P.trace_cap];
+  r.dq = dq;
+  r.accepted = accepted;
+}
+
 // Stop test of Algorithm 4.1 after iteration `iter` of a level with L1 marginal
 // error l1 (one thread): 1 converged (l1 < tol), 2 iteration cap, 6 stalled,
 // 0 go on.  Every `window` iterations l1 is compared with its value at the

@@ -249,6 +249,7 @@ __device__ __noinline__ void colmma_finish(const AccArgs& args, const Prob& P, u
     st->sum_wL = tot[1];
     st->qsemi = st->sum_af + tot[2];   // Q_semi(f_k) = <f_k, a> + <h, b>
     st->iter += 1;
+    trace_test(P, st, st->iter, tot[0], st->qsemi);
     st->nr_ok = 0;
     if (st->numeric > 0) st->done = 3;
     else st->done = stop_code(st, tot[0], st->iter, st->tol, st->max_iter, P.stall_window);
@@ -470,6 +471,7 @@ __device__ __noinline__ void cluster_finish(const AccArgs& args, const Prob& P,
         st->sum_wL = tot[1];
         st->qsemi = st->sum_af + tot[2];   // Q_semi(f_k) = <f_k, a> + <h, b>
         st->iter += 1;
+        trace_test(P, st, st->iter, tot[0], st->qsemi);
         st->nr_ok = 0;
         if (st->numeric > 0) st->done = 3;
         else st->done = stop_code(st, tot[0], st->iter, st->tol, st->max_iter, P.stall_window);

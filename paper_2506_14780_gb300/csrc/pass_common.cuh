@@ -99,6 +99,7 @@ __device__ inline void final_step(const Prob& P, int mode, const double t[3], in
       // Q_semi(f') - Q_semi(f_k) = <V Delta, a> + <h' - h, b>,  h' - h = -eps L
       const double dq = st->dot_vd_a - P.eps * t[1];
       st->dq = dq;
+      trace_trial(P, st, dq, dq > 0.0 ? 1 : 0);
       if (dq > 0.0) {
         st->nr_acc += 1;
         st->cur_f = 1 - st->cur_f;
@@ -113,6 +114,7 @@ __device__ inline void final_step(const Prob& P, int mode, const double t[3], in
       st->l1_col = t[0];
       st->qsemi = st->sum_af + t[2];   // Q_semi(f_k) = <f_k, a> + <f_k^{C,eps}, b>
       st->iter += 1;
+      trace_test(P, st, st->iter, t[0], st->qsemi);
       st->done = stop_code(st, t[0], st->iter, st->tol, st->max_iter, P.stall_window);
       if (!st->done) st->cur_g = dst;
       break;

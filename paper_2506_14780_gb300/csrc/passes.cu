@@ -693,6 +693,7 @@ __global__ void __launch_bounds__(128) col64_kernel(const Prob* __restrict__ PP,
       st->sum_wL = tot[1];
       st->qsemi = st->sum_af + tot[2];
       st->iter += 1;
+      trace_test(P, st, st->iter, tot[0], st->qsemi);
       st->nr_ok = 0;
       if (st->numeric > 0) st->done = 3;
       else st->done = stop_code(st, tot[0], st->iter, st->tol, st->max_iter, P.stall_window);

@@ -346,6 +346,7 @@ __global__ void __launch_bounds__(256) newton_kernel(const Prob* __restrict__ PP
     if (fail || !finite) {
       st->nr_ok = 0;
       st->nr_rej += 1;
+      trace_trial(P, st, __longlong_as_double(0x7ff8000000000000ll), 0);
       st->cur_g = (st->cur_g + 1) % 3;   // keep the Sinkhorn step: g_{k+1} = h
     } else {
       st->nr_ok = 1;

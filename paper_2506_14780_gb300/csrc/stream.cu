@@ -754,6 +754,7 @@ __global__ void __launch_bounds__(kStThreads, 2)
           st->sum_wL = tot[1];
           st->sum_wout = tot[2];
           st->iter = iter;
+          trace_test(P, st, iter, tot[0], st->qsemi);
           if (done) st->done = done;
           else st->cur_g = io.dst_g;
         }

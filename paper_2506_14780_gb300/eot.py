@@ -120,6 +120,9 @@ _SIGNATURES = {
     "eot_sknr_step": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, _PTR, _PTR, _PTR, C.c_double,
                                 _PTR, _PTR, _PTR, _PTR, _PTR, _PTR, _PTR, _PTR, _PTR, _PTR,
                                 _PTR, C.POINTER(eot_sknr_info), _PTR]),
+    "eot_solve_traced": (C.c_int, [C.POINTER(eot_problem), C.POINTER(eot_options), _PTR, _PTR,
+                                   C.POINTER(eot_result), _PTR, C.c_int32,
+                                   C.POINTER(C.c_int64)]),
     "eot_last_error": (C.c_char_p, []),
     "eot_version": (C.c_char_p, []),
 }
@@ -232,14 +235,35 @@ def eot_solve(problem: eot_problem, options: eot_options, f_out, g_out):
     return st, res
 
 
+TRACE_DTYPE = np.dtype([("eps", np.float64), ("l1", np.float64), ("q_semi", np.float64),
+                        ("dq", np.float64), ("iter", np.int32), ("accepted", np.int32)])
+
+
+def eot_solve_traced(problem: eot_problem, options: eot_options, f_out, g_out, trace_cap: int):
+    """Call eot_solve_traced.  Returns (status, eot_result, records, count):
+    records is a NumPy structured array (TRACE_DTYPE) of the last
+    min(count, trace_cap) iterations, oldest first."""
+    res = eot_result()
+    keep = []
+    rec = np.zeros(max(1, int(trace_cap)), dtype=TRACE_DTYPE)
+    cnt = C.c_int64(0)
+    st = load().eot_solve_traced(C.byref(problem), C.byref(options), _ptr(f_out, keep),
+                                 _ptr(g_out, keep), C.byref(res), rec.ctypes.data,
+                                 int(trace_cap), C.byref(cnt))
+    return st, res, rec[: min(cnt.value, int(trace_cap))].copy(), cnt.value
+
+
 def solve(prob, **opts):
     """Solve a ``workloads.Problem`` (host arrays).  Returns (f, g, result dict).
     Warm starts ``f_init``, ``g_init``, ``V_init`` pass through; with
     ``return_modes=True`` (and ell > 0) the result dict holds the modes of the
-    returned pair under "V" (eot_problem.V_out)."""
+    returned pair under "V" (eot_problem.V_out); with ``trace=K`` the solve
+    runs through eot_solve_traced and the dict holds the last K iteration
+    records under "trace" and their total under "trace_count"."""
     keep = []
     f64 = opts.get("prec", EOT_PREC_FP32) == EOT_PREC_FP64
     want_V = opts.pop("return_modes", False)
+    trace_cap = int(opts.pop("trace", 0))
     V = np.zeros((prob.a.shape[0], opts.get("ell", 0))) if want_V else None
     p = make_problem(prob.a, prob.b, C=prob.C, X=prob.X, Y=prob.Y, eps=prob.eps,
                      normalize_cost=prob.normalize_cost, f_init=opts.pop("f_init", None),
@@ -248,11 +272,17 @@ def solve(prob, **opts):
     o = default_options(**opts)
     f = np.zeros(p.n)
     g = np.zeros(p.m)
-    st, res = eot_solve(p, o, f, g)
+    if trace_cap > 0:
+        st, res, rec, cnt = eot_solve_traced(p, o, f, g, trace_cap)
+    else:
+        st, res = eot_solve(p, o, f, g)
     r = res.as_dict()
     r["return_status"] = st
     if st < 0:
         r["error"] = last_error()
+    if trace_cap > 0:
+        r["trace"] = rec
+        r["trace_count"] = cnt
     if want_V:
         r["V"] = V
     return f, g, r
