@@ -399,6 +399,23 @@ eot_status eot_sknr_step(int32_t n, int32_t m, int32_t ell, const float *C, cons
                          double *WtDW, double *delta, double *f_trial, double *h_trial,
                          eot_sknr_info *info, void *stream);
 
+/* The tuning of eot_solve_batch on the current device, run on first use (the
+ * first batch call runs it too): the gang cost model (step_ns, fix_ns, bar_ns;
+ * see eot_batch_plan) and the pass tiles picked by timing: tiles[c] for the
+ * problems whose column count m (rows being the shorter side, as the kernel
+ * runs them) is at most 64, 128, 256, 512, 1024, 2048 (c = 0..5) or larger
+ * (c = 6); bit 0 of a tile: 64-column blocks of the column half-step (two
+ * columns a lane) instead of 128; bit 1: eight rows a warp per chunk of the
+ * row half-step instead of four.  tile_ms[4 c + t] receives the calibration
+ * time of tile t on class c (a min(m, 256) x m problem, a copy on every
+ * resident CTA); a tile other than 0 is picked only when at least 2% faster
+ * than tile 0.  No tile
+ * changes a result (the order of every sum depends on the problem's shape
+ * alone); EOT_BATCH_TILE=t in the environment forces tile t.  Each output may
+ * be NULL (tiles: 7 entries, tile_ms: 28). */
+eot_status eot_batch_tuning(double *step_ns, double *fix_ns, double *bar_ns, int32_t *tiles,
+                            float *tile_ms);
+
 /* The schedule eot_solve_batch would use, computed on the host only (no
  * device work, no GPU needed): for count problems of sizes n[k] x m[k] at
  * eps[k] (has_f_init[k]: 0 no warm start, 2 a g_init and no f_init, any

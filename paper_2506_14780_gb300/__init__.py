@@ -11,7 +11,7 @@ from .eot import (  # noqa: F401
     EOT_PREC_FP32, EOT_PREC_SPLIT_TC, EOT_HESS_DIAG_ALPHA, EOT_HESS_EXACT, EOT_SIDE_COL,
     EOT_SIDE_ROW, Server, default_options, eot_cost, eot_ctransform, eot_kapply,
     eot_ctransform_noalloc, eot_exp2, eot_marginal_error, eot_plan, eot_solve, eot_solve_batch,
-    eot_solve_traced, TRACE_DTYPE,
+    eot_solve_traced, TRACE_DTYPE, eot_batch_tuning,
     eot_spectral_modes, eot_spectral_modes_filtered, eot_batch_plan, eot_sknr_step, eot_server_simulate,
     last_error, load,
     make_problem, solve,

@@ -1778,7 +1778,100 @@ static char* pinned_staging(size_t bytes) {
 
 static eot_status run_batch(int count, const eot_problem* probs, const eot_options& o,
                             double* const* f_out, double* const* g_out, eot_status* st,
-                            eot_result* rs, std::string* errs, int forced_G, float* kernel_ms);
+                            eot_result* rs, std::string* errs, int forced_G, float* kernel_ms,
+                            int forced_tile = -1);
+
+// One synthetic problem through run_batch: n x m points uniform in the unit
+// square (SplitMix64 draws of rnd), uniform weights, eps 0.05, a fixed number
+// of iterations (tol 1e-300, no stall check) on a gang of G CTAs with pass
+// tile `tile`, as `copies` identical members of one batch; *ms receives the
+// batch kernel's device time.
+template <class Rnd>
+static eot_status calib_run(int n, int m, int iters, int G, int tile, float* ms, Rnd& rnd,
+                            int copies = 1) {
+  std::vector<float> X(2 * n), Y(2 * m);
+  for (auto& v : X) v = rnd();
+  for (auto& v : Y) v = rnd();
+  std::vector<double> wa(n, 1.0 / n), wb(m, 1.0 / m), f(n), g(m);
+  eot_problem q{};
+  q.n = n;
+  q.m = m;
+  q.d = 2;
+  q.a = wa.data();
+  q.b = wb.data();
+  q.X = X.data();
+  q.Y = Y.data();
+  q.mem = EOT_MEM_HOST;
+  q.normalize_cost = 1;
+  q.eps = 0.05;
+  eot_options o;
+  eot_default_options(&o);
+  o.tol = 1e-300;
+  o.max_iter = iters;
+  o.stall_window = 0;
+  std::vector<eot_problem> qs(copies, q);
+  std::vector<double*> fo(copies, f.data()), go(copies, g.data());
+  std::vector<eot_status> st(copies);
+  std::vector<eot_result> r(copies);
+  std::vector<std::string> e(copies);
+  return run_batch(copies, qs.data(), o, fo.data(), go.data(), st.data(), r.data(), e.data(), G,
+                   ms, tile);
+}
+
+// Tile autotuner of the batch passes: per size class of a problem's column
+// count m (as the kernel runs it, after transposition: rows the shorter
+// side), the tile of kBTiles variants that ran a synthetic min(m, 256) x m
+// problem fastest with a copy on every resident CTA (the load a batch puts
+// on the memory system; 4M element-steps a copy, at least 16 iterations; the
+// first run is repeated as a warm-up).  Another tile replaces the default
+// (tile 0) only when it is at least 2% faster: a single CTA's time, or a
+// difference within the noise, did not carry over to the mixed batch.
+// Results do not depend on the tile, only the time does.
+constexpr int kBTileClasses = 7;   // m <= 64, 128, 256, 512, 1024, 2048, larger
+struct BatchTiles {
+  int tile[kBTileClasses] = {0, 0, 0, 0, 0, 0, 0};
+  float ms[kBTileClasses][kBTiles] = {};
+  bool done = false;
+};
+static BatchTiles g_btiles[64];
+static int batch_tile_class(int m) {
+  int c = 0;
+  while (c < kBTileClasses - 1 && m > (64 << c)) ++c;
+  return c;
+}
+static eot_status tune_batch_tiles(int dev) {
+  std::lock_guard<std::mutex> lk(g_bmodel_mu);
+  BatchTiles& B = g_btiles[dev & 63];
+  if (B.done) return EOT_OK;
+  uint64_t z = 0x2545F4914F6CDD1Dull;
+  auto rnd = [&]() {   // SplitMix64 draws in [0, 1)
+    z += 0x9E3779B97F4A7C15ull;
+    uint64_t x = z;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    x ^= x >> 31;
+    return (float)((x >> 40) * (1.0 / 16777216.0));
+  };
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int copies = std::max(1, batch_ctas_per_sm() * nsm);
+  for (int c = 0; c < kBTileClasses; ++c) {
+    const int m = 64 << c, n = std::min(m, 256);
+    const int iters = std::max(16, (int)((4LL << 20) / ((long long)n * m)));
+    int best = 0;
+    for (int t = 0; t < kBTiles; ++t) {
+      float ms = 0.f;
+      eot_status st = calib_run(n, m, iters, 1, t, &ms, rnd, copies);
+      if (st == EOT_OK && c == 0 && t == 0) st = calib_run(n, m, iters, 1, t, &ms, rnd, copies);
+      if (st != EOT_OK) return st;
+      B.ms[c][t] = ms;
+      if (ms < B.ms[c][best]) best = t;
+    }
+    B.tile[c] = B.ms[c][best] < 0.98f * B.ms[c][0] ? best : 0;
+  }
+  B.done = true;
+  return EOT_OK;
+}
 
 // Calibrate the gang-size model on this device with synthetic problems: a
 // 1024 x 1024 one run by one CTA (the element rate) and a 64 x 64 one run by
@@ -1798,30 +1891,7 @@ static eot_status calibrate_batch(int dev) {
     return (float)((x >> 40) * (1.0 / 16777216.0));
   };
   auto run = [&](int n, int iters, int G, float* ms) {
-    std::vector<float> X(2 * n), Y(2 * n);
-    for (auto& v : X) v = rnd();
-    for (auto& v : Y) v = rnd();
-    std::vector<double> w(n, 1.0 / n), f(n), g(n);
-    eot_problem q{};
-    q.n = q.m = n;
-    q.d = 2;
-    q.a = w.data();
-    q.b = w.data();
-    q.X = X.data();
-    q.Y = Y.data();
-    q.mem = EOT_MEM_HOST;
-    q.normalize_cost = 1;
-    q.eps = 0.05;
-    eot_options o;
-    eot_default_options(&o);
-    o.tol = 1e-300;
-    o.max_iter = iters;
-    double* fo[1] = {f.data()};
-    double* go[1] = {g.data()};
-    eot_status st;
-    eot_result r;
-    std::string e;
-    return run_batch(1, &q, o, fo, go, &st, &r, &e, G, ms);
+    return calib_run(n, n, iters, G, 0, ms, rnd);
   };
   const int it_big = 8, it_small = 64;
   float tb = 0.f, t1 = 0.f, t8 = 0.f;
@@ -1843,7 +1913,8 @@ static eot_status calibrate_batch(int dev) {
 
 static eot_status run_batch(int count, const eot_problem* probs, const eot_options& o,
                             double* const* f_out, double* const* g_out, eot_status* st,
-                            eot_result* rs, std::string* errs, int forced_G, float* kernel_ms) {
+                            eot_result* rs, std::string* errs, int forced_G, float* kernel_ms,
+                            int forced_tile) {
   DeviceCtx* ctx = nullptr;
   eot_status cs = get_ctx(&ctx);
   if (cs != EOT_OK) return cs;
@@ -1861,6 +1932,17 @@ static eot_status run_batch(int count, const eot_problem* probs, const eot_optio
     eot_status ce = calibrate_batch(ctx->dev);
     if (ce != EOT_OK) return ce;
   }
+  if (forced_tile < 0) {
+    // EOT_BATCH_TILE=t: every problem runs with tile t (results are the same
+    // for every tile)
+    const char* te = getenv("EOT_BATCH_TILE");
+    if (te && atoi(te) >= 0 && atoi(te) < kBTiles) forced_tile = atoi(te);
+  }
+  if (forced_tile < 0) {
+    eot_status te = tune_batch_tiles(ctx->dev);
+    if (te != EOT_OK) return te;
+  }
+  const BatchTiles& BT = g_btiles[ctx->dev & 63];
   const BatchModel& M = g_bmodel[ctx->dev & 63];
   struct PL {
     bool ok = false;
@@ -2132,6 +2214,7 @@ static eot_status run_batch(int count, const eot_problem* probs, const eot_optio
     T.G = p.G;
     T.max_iter = o.max_iter;
     T.lpr = batch_lpr(p.n > 0 ? p.m : 1);
+    T.tile = forced_tile >= 0 ? forced_tile : BT.tile[batch_tile_class(p.m)];
     T.C = L.C;
     T.af = L.af;
     T.bf = L.bf;
@@ -2581,6 +2664,27 @@ eot_status eot_cost(int32_t n, int32_t m, int32_t d, const float* X, const float
   CUDA_TRY(cudaFreeAsync(tmp, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   CUDA_TRY(cudaGetLastError());
+  return EOT_OK;
+}
+
+eot_status eot_batch_tuning(double* step_ns, double* fix_ns, double* bar_ns, int32_t* tiles,
+                            float* tile_ms) {
+  DeviceCtx* ctx = nullptr;
+  eot_status cs = get_ctx(&ctx);
+  if (cs != EOT_OK) return cs;
+  eot_status st = calibrate_batch(ctx->dev);
+  if (st == EOT_OK) st = tune_batch_tiles(ctx->dev);
+  if (st != EOT_OK) return st;
+  const BatchModel& M = g_bmodel[ctx->dev & 63];
+  const BatchTiles& B = g_btiles[ctx->dev & 63];
+  if (step_ns) *step_ns = M.step_ns;
+  if (fix_ns) *fix_ns = M.fix_ns;
+  if (bar_ns) *bar_ns = M.bar_ns;
+  for (int c = 0; c < kBTileClasses; ++c) {
+    if (tiles) tiles[c] = B.tile[c];
+    for (int t = 0; t < kBTiles; ++t)
+      if (tile_ms) tile_ms[c * kBTiles + t] = B.ms[c][t];
+  }
   return EOT_OK;
 }
 

@@ -273,14 +273,16 @@ __device__ __forceinline__ void brow_stream(const BatchTask& T, const Split& cs,
 // Row half-step over rows [r0, r1): f_i <- f_i - eps L_i (Eq. foc_f, delta
 // form), g from buffer gi; eval: L only.  A row is reduced by a group of LPR
 // lanes (a function of m alone, so every row sums in the same order whatever
-// the gang); the rows go in chunks whose states pass through shared memory to
-// warp 0, which finishes a whole chunk with full warps (the finish is float64
-// work, slow on this GPU) while the other warps stream the next chunk.
-__device__ void brow_pass(const BatchTask& T, int r0, int r1, int gi, double eps, float k2,
-                          float k2lo, bool eval, BShared& sh) {
+// the gang or the tile); the rows go in chunks of at least RPW rows a warp
+// (the task's tile), whose states pass through shared memory to warp 0, which
+// finishes a whole chunk with full warps (the finish is float64 work, slow on
+// this GPU) while the other warps stream the next chunk.
+template <int RPW>
+__device__ __forceinline__ void brow_pass(const BatchTask& T, int r0, int r1, int gi, double eps,
+                                       float k2, float k2lo, bool eval, BShared& sh) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int LPR = T.lpr, rpw = 32 / LPR, sub = lane & (LPR - 1), grp = lane / LPR;
-  const int rpwc = max(rpw, 4), CR = (kBThreads / 32) * rpwc;
+  const int rpwc = max(rpw, RPW), CR = (kBThreads / 32) * rpwc;
   const Split cs = T.gsp[gi];
   int k = 0;
   for (int q0 = r0; q0 < r1; q0 += CR, ++k) {
@@ -315,35 +317,64 @@ __device__ void brow_pass(const BatchTask& T, int r0, int r1, int gi, double eps
   }
 }
 
-// Partial log-sum-exp of the four columns j..j+3 over the 8-row blocks
+// Partial log-sum-exp of the CPL columns j..j+CPL-1 (CPL = 4 or 2: the
+// column tile of the task, 32 CPL columns a block) over the 8-row blocks
 // b = rg, rg + 8, ... (rg: the warp's row group): exponents
 // t (k2 + k2lo) + AL_i k2 with the exact t = (A_i - K_j) - C_ij, windowed
 // references per column and compensated pair sums (one compensated add per
-// block of eight rows).
-template <bool ACC>
+// block of eight rows).  Every column's arithmetic is its own (a reference
+// move folds the carried error of the moved column only), so a column's sum
+// does not depend on CPL: the tile is a pure schedule choice.
+template <bool ACC, int CPL>
 __device__ __forceinline__ void bcol_stream(const BatchTask& T, const Split& os, int j, int c1,
-                                            int rg, float k2, float k2lo, float4& Rout,
-                                            float4& Sout) {
+                                            int rg, float k2, float k2lo, float (&Rout)[CPL],
+                                            float (&Sout)[CPL]) {
+  static_assert(CPL == 2 || CPL == 4, "2 or 4 columns a lane");
+  constexpr int NP = CPL / 2;   // float2 pairs of columns
   const int n = T.n;
   const size_t pitch = (size_t)T.pitch;
-  const float4 K = *reinterpret_cast<const float4*>(os.K + j);
-  const float2 nK01 = f2(-K.x, -K.y), nK23 = f2(-K.z, -K.w), k2v = f2(k2, k2),
-               k2l = f2(k2lo, k2lo), m1 = f2(-1.f, -1.f);
-  const bool fullc = j + 4 <= c1;
+  float2 nK[NP];
+  if constexpr (CPL == 4) {
+    const float4 K = *reinterpret_cast<const float4*>(os.K + j);
+    nK[0] = f2(-K.x, -K.y);
+    nK[1] = f2(-K.z, -K.w);
+  } else {
+    const float2 K = *reinterpret_cast<const float2*>(os.K + j);
+    nK[0] = f2(-K.x, -K.y);
+  }
+  const float2 k2v = f2(k2, k2), k2l = f2(k2lo, k2lo), m1 = f2(-1.f, -1.f);
+  const bool fullc = j + CPL <= c1;
   const float* Cj = T.C + j;
-  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  float ref[4] = {0.f, 0.f, 0.f, 0.f};
-  float rr[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
+  float ref[CPL], rr[CPL];
+#pragma unroll
+  for (int q = 0; q < CPL; ++q) {
+    ref[q] = 0.f;
+    rr[q] = -INFINITY;
+  }
   bool ref0 = true;
-  float2 Sa[2] = {f2(0.f, 0.f), f2(0.f, 0.f)}, Ca[2] = {f2(0.f, 0.f), f2(0.f, 0.f)};
+  float2 Sa[NP], Ca[NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    Sa[p] = f2(0.f, 0.f);
+    Ca[p] = f2(0.f, 0.f);
+  }
   for (int b = rg; 8 * b < n; b += kBThreads / 32) {
     const int i0 = 8 * b;
     const bool fullr = i0 + 8 <= n;
-    float4 c[8];
+    float2 c[8][NP];
 #pragma unroll
-    for (int u = 0; u < 8; ++u)
-      c[u] = (fullr || i0 + u < n) ? __ldcg(reinterpret_cast<const float4*>(Cj + (size_t)(i0 + u) * pitch))
-                                   : z4;
+    for (int u = 0; u < 8; ++u) {
+      const bool in = fullr || i0 + u < n;
+      const float* src = Cj + (size_t)(i0 + u) * pitch;
+      if constexpr (CPL == 4) {
+        const float4 v = in ? __ldcg(reinterpret_cast<const float4*>(src))
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
+        c[u][0] = f2(v.x, v.y);
+        c[u][1] = f2(v.z, v.w);
+      } else {
+        c[u][0] = in ? __ldcg(reinterpret_cast<const float2*>(src)) : f2(0.f, 0.f);
+      }
+    }
     // the warp's next block into L2 while this one is reduced (measured on
     // the mixed 512-problem batch, with the row pass's prefetch: 0.45 -> 0.42 s)
     {
@@ -359,98 +390,113 @@ __device__ __forceinline__ void bcol_stream(const BatchTask& T, const Split& os,
     const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
     const float lv[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
     // exponents as in the row pass: rounded once, or t kept for ACC
-    float2 ya[8], yb[8];
+    float2 y[8][NP];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const float2 arr = f2(av[u], av[u]), alr = f2(lv[u], lv[u]);
-      const float2 ta = __ffma2_rn(f2(c[u].x, c[u].y), m1, __fadd2_rn(arr, nK01));
-      const float2 tb = __ffma2_rn(f2(c[u].z, c[u].w), m1, __fadd2_rn(arr, nK23));
-      if constexpr (ACC) {
-        ya[u] = ta;
-        yb[u] = tb;
-      } else {
-        ya[u] = __ffma2_rn(ta, k2v, __ffma2_rn(ta, k2l, alr));
-        yb[u] = __ffma2_rn(tb, k2v, __ffma2_rn(tb, k2l, alr));
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        const float2 t = __ffma2_rn(c[u][p], m1, __fadd2_rn(arr, nK[p]));
+        if constexpr (ACC) y[u][p] = t;
+        else y[u][p] = __ffma2_rn(t, k2v, __ffma2_rn(t, k2l, alr));
       }
     }
     if (!(fullr && fullc)) {
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const bool rv = i0 + u < n;
-        ya[u].x = (rv && j + 0 < c1) ? ya[u].x : -INFINITY;
-        ya[u].y = (rv && j + 1 < c1) ? ya[u].y : -INFINITY;
-        yb[u].x = (rv && j + 2 < c1) ? yb[u].x : -INFINITY;
-        yb[u].y = (rv && j + 3 < c1) ? yb[u].y : -INFINITY;
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+          y[u][p].x = (rv && j + 2 * p < c1) ? y[u][p].x : -INFINITY;
+          y[u][p].y = (rv && j + 2 * p + 1 < c1) ? y[u][p].y : -INFINITY;
+        }
       }
     }
     // running maxima from the raw exponents (max(y) - ref = max(y - ref))
-    float my[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    float my[CPL];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      float2 pa = ya[u], pb = yb[u];
-      if constexpr (ACC) {
-        pa = __fmul2_rn(pa, k2v);
-        pb = __fmul2_rn(pb, k2v);
+    for (int q = 0; q < CPL; ++q) my[q] = -INFINITY;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        float2 pv = y[u][p];
+        if constexpr (ACC) pv = __fmul2_rn(pv, k2v);
+        my[2 * p] = fmaxf(my[2 * p], pv.x);
+        my[2 * p + 1] = fmaxf(my[2 * p + 1], pv.y);
       }
-      my[0] = fmaxf(my[0], pa.x);
-      my[1] = fmaxf(my[1], pa.y);
-      my[2] = fmaxf(my[2], pb.x);
-      my[3] = fmaxf(my[3], pb.y);
-    }
+    bool mv[CPL];
     bool move = false;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < CPL; ++q) {
       rr[q] = fmaxf(rr[q], ref0 ? my[q] : my[q] - ref[q]);
-      move |= rr[q] > -INFINITY && needs_move(rr[q], ref[q]);
+      mv[q] = rr[q] > -INFINITY && needs_move(rr[q], ref[q]);
+      move |= mv[q];
     }
     if (move) {
-      kahan_fold2(Sa[0], Ca[0]);
-      kahan_fold2(Sa[1], Ca[1]);
-      move_ref(rr[0], ref[0], Sa[0].x);
-      move_ref(rr[1], ref[1], Sa[0].y);
-      move_ref(rr[2], ref[2], Sa[1].x);
-      move_ref(rr[3], ref[3], Sa[1].y);
-      ref0 = ref[0] == 0.f && ref[1] == 0.f && ref[2] == 0.f && ref[3] == 0.f;
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        if (mv[2 * p]) {
+          Sa[p].x = __fmaf_rn(Ca[p].x, -1.f, Sa[p].x);
+          Ca[p].x = 0.f;
+          move_ref(rr[2 * p], ref[2 * p], Sa[p].x);
+        }
+        if (mv[2 * p + 1]) {
+          Sa[p].y = __fmaf_rn(Ca[p].y, -1.f, Sa[p].y);
+          Ca[p].y = 0.f;
+          move_ref(rr[2 * p + 1], ref[2 * p + 1], Sa[p].y);
+        }
+      }
+      ref0 = true;
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) ref0 = ref0 && ref[q] == 0.f;
     }
-    const float2 na = f2(-ref[0], -ref[1]), nb = f2(-ref[2], -ref[3]);
+    float2 nr[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) nr[p] = f2(-ref[2 * p], -ref[2 * p + 1]);
     if constexpr (ACC) {
       // evaluation: terms 2^(p + q), one row after another
-      float2 ea = f2(0.f, 0.f), eb = f2(0.f, 0.f);
+      float2 e[NP];
+#pragma unroll
+      for (int p = 0; p < NP; ++p) e[p] = f2(0.f, 0.f);
 #pragma unroll 2
       for (int u = 0; u < 8; ++u) {
         const float2 alr = f2(lv[u], lv[u]);
-        const float2 pa = __fmul2_rn(ya[u], k2v), pb = __fmul2_rn(yb[u], k2v);
-        const float2 qa = __fadd2_rn(__ffma2_rn(ya[u], k2v, f2(-pa.x, -pa.y)),
-                                     __ffma2_rn(ya[u], k2l, alr));
-        const float2 qb = __fadd2_rn(__ffma2_rn(yb[u], k2v, f2(-pb.x, -pb.y)),
-                                     __ffma2_rn(yb[u], k2l, alr));
-        ea = __fadd2_rn(ea, f2(ex2_pq(__fsub_rn(pa.x, ref[0]), qa.x), ex2_pq(__fsub_rn(pa.y, ref[1]), qa.y)));
-        eb = __fadd2_rn(eb, f2(ex2_pq(__fsub_rn(pb.x, ref[2]), qb.x), ex2_pq(__fsub_rn(pb.y, ref[3]), qb.y)));
-      }
-      kahan_add2(Sa[0], Ca[0], ea);
-      kahan_add2(Sa[1], Ca[1], eb);
-    } else {
-      float2 ea[8], eb[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        ea[u] = ex2_2(ref0 ? ya[u] : __fadd2_rn(ya[u], na));
-        eb[u] = ex2_2(ref0 ? yb[u] : __fadd2_rn(yb[u], nb));
+        for (int p = 0; p < NP; ++p) {
+          const float2 pp = __fmul2_rn(y[u][p], k2v);
+          const float2 qq = __fadd2_rn(__ffma2_rn(y[u][p], k2v, f2(-pp.x, -pp.y)),
+                                       __ffma2_rn(y[u][p], k2l, alr));
+          e[p] = __fadd2_rn(e[p], f2(ex2_pq(__fsub_rn(pp.x, ref[2 * p]), qq.x),
+                                     ex2_pq(__fsub_rn(pp.y, ref[2 * p + 1]), qq.y)));
+        }
       }
+#pragma unroll
+      for (int p = 0; p < NP; ++p) kahan_add2(Sa[p], Ca[p], e[p]);
+    } else {
+      float2 e[8][NP];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int p = 0; p < NP; ++p) e[u][p] = ex2_2(ref0 ? y[u][p] : __fadd2_rn(y[u][p], nr[p]));
 #pragma unroll
       for (int w = 1; w < 8; w *= 2)
 #pragma unroll
-        for (int u = 0; u + w < 8; u += 2 * w) {
-          ea[u] = __fadd2_rn(ea[u], ea[u + w]);
-          eb[u] = __fadd2_rn(eb[u], eb[u + w]);
-        }
-      kahan_add2(Sa[0], Ca[0], ea[0]);
-      kahan_add2(Sa[1], Ca[1], eb[0]);
+        for (int u = 0; u + w < 8; u += 2 * w)
+#pragma unroll
+          for (int p = 0; p < NP; ++p) e[u][p] = __fadd2_rn(e[u][p], e[u + w][p]);
+#pragma unroll
+      for (int p = 0; p < NP; ++p) kahan_add2(Sa[p], Ca[p], e[0][p]);
     }
   }
-  kahan_fold2(Sa[0], Ca[0]);
-  kahan_fold2(Sa[1], Ca[1]);
-  Rout = make_float4(ref[0], ref[1], ref[2], ref[3]);
-  Sout = make_float4(Sa[0].x, Sa[0].y, Sa[1].x, Sa[1].y);
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    kahan_fold2(Sa[p], Ca[p]);
+    Rout[2 * p] = ref[2 * p];
+    Rout[2 * p + 1] = ref[2 * p + 1];
+    Sout[2 * p] = Sa[p].x;
+    Sout[2 * p + 1] = Sa[p].y;
+  }
 }
 
 __device__ __forceinline__ void lse_merge4(float4& R, float4& S, float4 r, float4 s) {
@@ -462,36 +508,41 @@ __device__ __forceinline__ void lse_merge4(float4& R, float4& S, float4 r, float
 
 // Column half-step over columns [c0, c1) (c0 a multiple of 4): g'_j = g_j -
 // eps L_j (Eq. foc_g, delta form) from buffer gi into buffer 1 - gi.  Blocks
-// of 128 columns, four a lane; each warp is one of eight row groups (8-row
+// of 32 CPL columns, CPL a lane; each warp is one of eight row groups (8-row
 // blocks, interleaved), whose states warp 0 merges in group order and
 // finishes while the others stream the next block.  The order of every sum
-// depends on n alone, not on the gang.
-__device__ void bcol_pass(const BatchTask& T, int c0, int c1, int gi, double eps, float k2,
-                          float k2lo, bool eval, BShared& sh) {
+// depends on n alone, not on the gang or on CPL.
+template <int CPL>
+__device__ __forceinline__ void bcol_pass(const BatchTask& T, int c0, int c1, int gi, double eps,
+                                       float k2, float k2lo, bool eval, BShared& sh) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const Split os = T.gsp[gi];
   const Split ns = T.gsp[1 - gi];
   const double* gcur = T.g[gi];
   double* gnew = T.g[1 - gi];
   int k = 0;
-  for (int cb = c0; cb < c1; cb += 128, ++k) {
+  for (int cb = c0; cb < c1; cb += 32 * CPL, ++k) {
     const int buf = k & 1;
-    const int j = cb + 4 * lane;
-    float4 R = make_float4(0.f, 0.f, 0.f, 0.f), S = R;
+    const int j = cb + CPL * lane;
+    float R[CPL], S[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) R[q] = S[q] = 0.f;
     if (j < c1) {
-      if (eval) bcol_stream<true>(T, os, j, c1, wid, k2, k2lo, R, S);
-      else bcol_stream<false>(T, os, j, c1, wid, k2, k2lo, R, S);
+      if (eval) bcol_stream<true, CPL>(T, os, j, c1, wid, k2, k2lo, R, S);
+      else bcol_stream<false, CPL>(T, os, j, c1, wid, k2, k2lo, R, S);
     }
-    sh.cref[buf][wid][lane] = R;
-    sh.csum[buf][wid][lane] = S;
+    sh.cref[buf][wid][lane] = make_float4(R[0], R[1], CPL == 4 ? R[CPL - 2] : 0.f,
+                                          CPL == 4 ? R[CPL - 1] : 0.f);
+    sh.csum[buf][wid][lane] = make_float4(S[0], S[1], CPL == 4 ? S[CPL - 2] : 0.f,
+                                          CPL == 4 ? S[CPL - 1] : 0.f);
     __syncthreads();
     if (wid == 0 && j < c1) {
-      R = sh.cref[buf][0][lane];
-      S = sh.csum[buf][0][lane];
-      for (int g2 = 1; g2 < kBThreads / 32; ++g2) lse_merge4(R, S, sh.cref[buf][g2][lane], sh.csum[buf][g2][lane]);
-      const float rv[4] = {R.x, R.y, R.z, R.w}, sv[4] = {S.x, S.y, S.z, S.w};
+      float4 R4 = sh.cref[buf][0][lane], S4 = sh.csum[buf][0][lane];
+      for (int g2 = 1; g2 < kBThreads / 32; ++g2)
+        lse_merge4(R4, S4, sh.cref[buf][g2][lane], sh.csum[buf][g2][lane]);
+      const float rv[4] = {R4.x, R4.y, R4.z, R4.w}, sv[4] = {S4.x, S4.y, S4.z, S4.w};
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < CPL; ++q) {
         const int jj = j + q;
         if (jj < c1)
           bfinish(T, rv[q], sv[q], os.KL[jj], gcur[jj], eps * T.logb[jj], eps, k2, gnew, ns,
@@ -501,9 +552,25 @@ __device__ void bcol_pass(const BatchTask& T, int c0, int c1, int gi, double eps
   }
 }
 
+// The task's tile (BatchTask::tile, a template argument of brun_task): bit 0,
+// two columns a lane in the column half-step (64-column blocks) instead of
+// four; bit 1, at least eight rows a warp per chunk of the row half-step
+// instead of four.
+template <int TILE>
+__device__ __forceinline__ void bcol_pass_t(const BatchTask& T, int c0, int c1, int gi, double eps,
+                                            float k2, float k2lo, bool eval, BShared& sh) {
+  bcol_pass<(TILE & 1) ? 2 : 4>(T, c0, c1, gi, eps, k2, k2lo, eval, sh);
+}
+template <int TILE>
+__device__ __forceinline__ void brow_pass_t(const BatchTask& T, int r0, int r1, int gi, double eps,
+                                            float k2, float k2lo, bool eval, BShared& sh) {
+  brow_pass<(TILE & 2) ? 8 : 4>(T, r0, r1, gi, eps, k2, k2lo, eval, sh);
+}
+
 // One task (problem) run by rank `rank` of its gang.  Gang-wide sums (the L1
 // test, the scores) are formed by every rank from the per-index arrays in one
 // fixed order, so they, and with them every decision, do not depend on G.
+template <int TILE>
 __device__ void brun_task(const BatchTask& T, int rank, BShared& sh) {
   const int G = T.G, n = T.n, m = T.m;
   const int r0 = (int)((long long)n * rank / G), r1 = (int)((long long)n * (rank + 1) / G);
@@ -540,7 +607,7 @@ __device__ void brun_task(const BatchTask& T, int rank, BShared& sh) {
       bsplit(T, T.g[gi][j], eps * T.logb[j], k2, T.gsp[gi], j);
     if (!sync()) break;
     // g_1 = f_0^{C,eps} (Algorithm 4.1 line 3 at the first iteration)
-    bcol_pass(T, c0, c1, gi, eps, k2, k2lo, false, sh);
+    bcol_pass_t<TILE>(T, c0, c1, gi, eps, k2, k2lo, false, sh);
     if (!sync()) break;
     if (numeric()) {
       status = 3;
@@ -554,9 +621,9 @@ __device__ void brun_task(const BatchTask& T, int rank, BShared& sh) {
     double stall_l1 = 1e300;
     int stall_at = T.stall_window;
     for (;;) {
-      brow_pass(T, r0, r1, gi, eps, k2, k2lo, false, sh);   // f_k = g_k^{C,eps}
+      brow_pass_t<TILE>(T, r0, r1, gi, eps, k2, k2lo, false, sh);   // f_k = g_k^{C,eps}
       if (!sync()) break;
-      bcol_pass(T, c0, c1, gi, eps, k2, k2lo, false, sh);   // f_k^{C,eps}: the L1 test
+      bcol_pass_t<TILE>(T, c0, c1, gi, eps, k2, k2lo, false, sh);   // f_k^{C,eps}: the L1 test
       if (!sync()) break;
       const double l1 = l1_side(T.Lcol, T.bf, m);
       ++iter;
@@ -571,8 +638,8 @@ __device__ void brun_task(const BatchTask& T, int rank, BShared& sh) {
         // verify the pair (f_k, g_k): both terms of the L1 error with the
         // unbiased exponential (the two passes read f_k, g_k and write
         // different arrays: one barrier after both)
-        brow_pass(T, r0, r1, gi, eps, k2, k2lo, true, sh);
-        bcol_pass(T, c0, c1, gi, eps, k2, k2lo, true, sh);
+        brow_pass_t<TILE>(T, r0, r1, gi, eps, k2, k2lo, true, sh);
+        bcol_pass_t<TILE>(T, c0, c1, gi, eps, k2, k2lo, true, sh);
         if (!sync()) break;
         row_l1 = l1_side(T.Lrow, T.af, n);
         col_l1 = l1_side(T.Lcol, T.bf, m);
@@ -612,8 +679,8 @@ __device__ void brun_task(const BatchTask& T, int rank, BShared& sh) {
     const float k2 = (float)k2d, k2lo = (float)(k2d - (double)k2);
     bool ok = true;
     if (!have_row) {
-      brow_pass(T, r0, r1, gi, eps, k2, k2lo, true, sh);
-      bcol_pass(T, c0, c1, gi, eps, k2, k2lo, true, sh);
+      brow_pass_t<TILE>(T, r0, r1, gi, eps, k2, k2lo, true, sh);
+      bcol_pass_t<TILE>(T, c0, c1, gi, eps, k2, k2lo, true, sh);
       ok = sync();
       if (ok) row_l1 = l1_side(T.Lrow, T.af, n);
     }
@@ -679,7 +746,13 @@ __global__ void __launch_bounds__(kBThreads, 2) batch_sk_kernel(const BatchTask*
     const int s = sh.slot;
     if (s >= nslots) return;
     const int2 e = slots[s];
-    brun_task(tasks[e.x], e.y, sh);
+    const BatchTask& T = tasks[e.x];
+    switch (T.tile) {
+      case 1: brun_task<1>(T, e.y, sh); break;
+      case 2: brun_task<2>(T, e.y, sh); break;
+      case 3: brun_task<3>(T, e.y, sh); break;
+      default: brun_task<0>(T, e.y, sh); break;
+    }
   }
 }
 

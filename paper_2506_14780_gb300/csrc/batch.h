@@ -21,8 +21,15 @@ struct BatchOut {
   unsigned long long t_begin, t_end, t_last_level;
 };
 
+// Tiles of the batch passes (BatchTask::tile, picked per size class of m by
+// the host's tuner): bit 0, two columns a lane in the column half-step
+// (64-column blocks) instead of four (128); bit 1, at least eight rows a warp
+// per chunk of the row half-step instead of four.  No tile changes a result.
+constexpr int kBTiles = 4;
+
 struct BatchTask {
   int n, m, pitch, nlev, G, max_iter;
+  int tile;                       // pass tiles (kBTiles variants)
   int lpr;                        // lanes per row of the row pass (batch_lpr(m))
   const float* C;                 // n x pitch
   const double *a, *b, *loga, *logb;

@@ -123,6 +123,8 @@ _SIGNATURES = {
     "eot_solve_traced": (C.c_int, [C.POINTER(eot_problem), C.POINTER(eot_options), _PTR, _PTR,
                                    C.POINTER(eot_result), _PTR, C.c_int32,
                                    C.POINTER(C.c_int64)]),
+    "eot_batch_tuning": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                   C.POINTER(C.c_double), _PTR, _PTR]),
     "eot_last_error": (C.c_char_p, []),
     "eot_version": (C.c_char_p, []),
 }
@@ -373,6 +375,18 @@ def eot_batch_plan(n, m, eps, options: eot_options, grid_ctas: int, step_ns: flo
                                int(grid_ctas), float(step_ns), float(fix_ns), float(bar_ns),
                                gang.ctypes.data, tr.ctypes.data)
     return st, gang, tr
+
+
+def eot_batch_tuning():
+    """The batch kernel's tuning on this device: (status, {"step_ns", "fix_ns",
+    "bar_ns", "tiles" (7 size classes of m), "tile_ms" (7 x 4)})."""
+    st_ns, fx, br = C.c_double(0), C.c_double(0), C.c_double(0)
+    tiles = np.zeros(7, dtype=np.int32)
+    tms = np.zeros((7, 4), dtype=np.float32)
+    st = load().eot_batch_tuning(C.byref(st_ns), C.byref(fx), C.byref(br), tiles.ctypes.data,
+                                 tms.ctypes.data)
+    return st, {"step_ns": st_ns.value, "fix_ns": fx.value, "bar_ns": br.value,
+                "tiles": tiles, "tile_ms": tms}
 
 
 def eot_exp2(p, q, variant: int, out, stream=None) -> int:

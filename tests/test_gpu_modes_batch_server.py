@@ -144,6 +144,53 @@ def test_batch_result_independent_of_gang_size(pkg, monkeypatch):
         assert O.evaluate(f0[k], g0[k], C, p.a, p.b, p.eps)["l1"] <= 1e-6
 
 
+def test_batch_result_independent_of_the_tile(pkg, monkeypatch):
+    """The tuner's pass tiles (64- or 128-column blocks of the column
+    half-step, four or eight rows a warp per chunk of the row half-step) change
+    only the schedule: every tile gives the same result bit for bit, at ragged
+    shapes (columns not a multiple of 4, rows not a multiple of 8, narrow and
+    wide rows), and the tuned choice is one of them."""
+    shapes = [(77, 61), (300, 1030), (1203, 207), (96, 700), (513, 129), (40, 2049)]
+    probs = [W.uniform_square(n, m, d=2, seed=40 + k, eps=[2e-2, 5e-3, 1e-2, 3e-3, 8e-3, 1e-2][k])
+             for k, (n, m) in enumerate(shapes)]
+    keep = []
+    ps = [pkg.make_problem(p.a, p.b, X=p.X, Y=p.Y, eps=p.eps, normalize_cost=True, keep=keep)
+          for p in probs]
+    o = pkg.default_options(tol=1e-6, max_iter=200000, eps_start=1e-1)
+    outs = []
+    for tile in ("0", "1", "2", "3", None):
+        if tile is None:
+            monkeypatch.delenv("EOT_BATCH_TILE", raising=False)
+        else:
+            monkeypatch.setenv("EOT_BATCH_TILE", tile)
+        fs = [np.zeros(p.n) for p in probs]
+        gs = [np.zeros(p.m) for p in probs]
+        st, res = pkg.eot_solve_batch(ps, o, fs, gs)
+        assert st == pkg.EOT_OK, (tile, pkg.last_error(), [r.status for r in res])
+        outs.append((fs, gs, [r.total_iters for r in res]))
+    f0, g0, it0 = outs[0]
+    for fs, gs, its in outs[1:]:
+        assert its == it0
+        for k in range(len(probs)):
+            assert np.array_equal(fs[k], f0[k]) and np.array_equal(gs[k], g0[k]), k
+    for k, p in enumerate(probs):
+        C = O.sq_euclidean_cost(p.X, p.Y, normalize=True).astype(np.float32).astype(np.float64)
+        assert O.evaluate(f0[k], g0[k], C, p.a, p.b, p.eps)["l1"] <= 1e-6
+    st, tun = pkg.eot_batch_tuning()
+    assert st == pkg.EOT_OK
+    assert tun["step_ns"] > 0 and tun["fix_ns"] > 0 and tun["bar_ns"] > 0
+    assert np.all((tun["tiles"] >= 0) & (tun["tiles"] < 4))
+    assert np.all(tun["tile_ms"] > 0)
+    for c in range(7):   # the fastest of its class, or the default within 2% of it
+        t = tun["tiles"][c]
+        ms = tun["tile_ms"][c]
+        if t == 0:
+            assert ms.min() >= np.float32(0.98) * ms[0]
+        else:
+            assert ms[t] == ms.min() and ms[t] < np.float32(0.98) * ms[0]
+    print("tiles", tun["tiles"].tolist(), "ms", np.round(tun["tile_ms"], 3).tolist())
+
+
 def test_batch_tall_problems_given_cost(pkg):
     """Problems with more rows than columns run transposed inside the batch
     (given cost read transposed, points and weights swapped): the returned
