@@ -541,8 +541,19 @@ def extras(pkg, torch, stream):
                        "cost_gb_streamed_per_s": round(cost_bytes / tb / 1e9, 1),
                        "note": "host arrays in and out; one persistent cooperative launch "
                                "(graph-captured) runs every problem, gang sizes from a "
-                               "calibrated cost model; median of 3 calls after a first call "
-                               "that also calibrates the model (first_call_seconds)"}
+                               "calibrated cost model, pass tiles from the autotuner; median "
+                               "of 3 calls after a first call that also calibrates the model "
+                               "and tunes the tiles (first_call_seconds)"}
+    stt, tun = pkg.eot_batch_tuning()
+    if stt == pkg.EOT_OK:
+        out["c4_batch"]["tuning"] = {
+            "tiles_by_m_class": tun["tiles"].tolist(),
+            "m_classes": "<=64, <=128, <=256, <=512, <=1024, <=2048, larger",
+            "tile_ms": np.round(tun["tile_ms"], 3).tolist(),
+            "step_ns": round(tun["step_ns"], 2), "fix_ns": round(tun["fix_ns"], 1),
+            "bar_ns": round(tun["bar_ns"], 1),
+            "note": "tile bit 0: 64-column blocks of the column half-step; bit 1: eight rows "
+                    "a warp per row chunk; calibrated with a copy on every resident CTA"}
     # the same batch with SK-NR(30): every problem a whole solve on one of the
     # worker threads (own stream), the longest predicted first
     stage("c4: batch, SK-NR(30)")
