@@ -589,11 +589,60 @@ def extras(pkg, torch, stream):
                             note="20 s Poisson stream at 0.5 x the solves/s measured at 2000/s"),
         "note": "n, m log-uniform in [128, 16384], d in {2, 3, 64}, eps in {1e-1, 1e-2, 1e-3}, "
                 "half the requests re-use an earlier cloud (warm start from its resident "
-                "potentials); every request SK-NR(30) on a stored float32 cost, continuation "
+                "potentials and modes); every request SK-NR(30) on a stored float32 cost, continuation "
                 "from 1e-1 (intermediate levels to 1e-4), a level stops on a stall (under 1% "
                 "gain per 1000 iterations); 8 slots, 48 GB budget; admitted solves overlap on "
                 "the device (own streams); converged = EOT_OK (the returned pair meets 1e-6)"}
+    stage("paper Sec. 5 workloads")
+    out["paper_sec5"] = paper_sec5(pkg)
     return out, c3_pair
+
+
+def paper_sec5(pkg):
+    """The paper's Sec. 5 experiments through the library (iteration counts and
+    device times; the paper prints figures only, so these are not compared with
+    numbers of its own): the 2-D Gaussian experiment of Fig. 5.1 (200 vs 400
+    points, raw cost, continuation from eps = 1 halving) under the sequential
+    and static-mode protocols and the l sweep at eps = 0.25 from eps' = 1, and
+    the single-cell shapes of Fig. 5.2 in R^30 (synthetic N(0, I)/8 clouds stand
+    in for the data set), eps from 1 halving to 1/64, l = 30."""
+    out = {}
+    p = workloads.gaussians_2d(200, seed=0)
+
+    def run(prob, eps, **kw):
+        prob.eps = eps
+        f, g, r = pkg.solve(prob, tol=TOL, max_iter=200000, **kw)
+        return r
+
+    levels = (1.0, 0.5, 0.25)
+    prot = {}
+    for name, kw in (("sinkhorn", dict(ell=0)), ("sequential_sknr10", dict(ell=10, sequential_modes=1)),
+                     ("static_sknr10", dict(ell=10, sequential_modes=0))):
+        rs = [run(p, e, eps_start=1.0, eps_factor=0.5, **kw) for e in levels]
+        prot[name] = {"iters_at_eps_1_0.5_0.25": [r["iters"] for r in rs],
+                      "status": [r["status_name"] for r in rs],
+                      "ms_to_0.25": round(rs[-1]["seconds"] * 1e3, 2)}
+    sweep = {}
+    for ell in (0, 2, 5, 10, 20):
+        r = run(p, 0.25, eps_start=1.0, eps_factor=0.25, ell=ell)
+        sweep[str(ell)] = {"iters_at_0.25": r["iters"], "ms": round(r["seconds"] * 1e3, 2),
+                           "status": r["status_name"]}
+    out["two_gaussians_200x400"] = {"protocols": prot, "modes_sweep_from_eps1": sweep}
+    cells = {}
+    for n, m in ((6507, 3815), (3815, 2982)):
+        q = workloads.gaussian_cloud(n, m, d=30, seed=n, eps=1.0 / 64)
+        q.normalize_cost = True
+        rr = {}
+        for ell in (0, 30):
+            f, g, r = pkg.solve(q, tol=TOL, max_iter=200000, eps_start=1.0, eps_factor=0.5, ell=ell)
+            rr["sinkhorn" if ell == 0 else "sknr30"] = {
+                "total_iters": r["total_iters"], "ms": round(r["seconds"] * 1e3, 2),
+                "status": r["status_name"]}
+        cells[f"{n}x{m}"] = rr
+    out["single_cell_shapes_R30"] = cells
+    out["note"] = ("L1 target 1e-6 at every level; iteration counts per level (iters) or over "
+                   "the continuation (total_iters); device time of the whole solve")
+    return out
 
 
 # The float64 oracle's own iteration counts on the benchmark workload (SK-NR(30)

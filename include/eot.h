@@ -503,6 +503,14 @@ const char *eot_last_error(void);
 /* Library version string. */
 const char *eot_version(void);
 
+/* 1 in a library built with -DEOT_DEBUG, else 0.  In that build the kernels
+ * check the indexes and launch shapes they rely on (shared-memory tables,
+ * partial-state slots, mode widths, gang ranks); a failed check records its
+ * site (100 x unit + k) in a device word and skips the access it guards, and
+ * the call that launched the work fails with EOT_ECUDA naming the site
+ * (eot_last_error).  The release build has no checks and the same results. */
+int32_t eot_debug_build(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,6 +19,9 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 OBJ_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libeot.so")
+# the bounds-checked build (-DEOT_DEBUG): its own objects and library
+OBJ_DIR_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(OUT_DIR, "libeot_debug.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE,
@@ -36,15 +39,15 @@ def sources() -> list:
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
-def _compile(src: str, verbose: bool) -> str:
-    obj = os.path.join(OBJ_DIR, os.path.basename(src)[:-3] + ".o")
+def _compile(src: str, verbose: bool, debug: bool = False) -> str:
+    obj = os.path.join(OBJ_DIR_DEBUG if debug else OBJ_DIR, os.path.basename(src)[:-3] + ".o")
     if os.path.exists(obj):
         newest = max(os.path.getmtime(p) for p in
                      [src] + [os.path.join(CSRC, h) for h in os.listdir(CSRC)
                               if h.endswith((".h", ".cuh"))] + [os.path.join(INCLUDE, "eot.h")])
         if os.path.getmtime(obj) >= newest:
             return obj
-    cmd = [_nvcc()] + CFLAGS + ARCH + ["-c", src, "-o", obj]
+    cmd = [_nvcc()] + CFLAGS + (["-DEOT_DEBUG"] if debug else []) + ARCH + ["-c", src, "-o", obj]
     if verbose:
         print(" ".join(cmd), flush=True)
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -53,14 +56,16 @@ def _compile(src: str, verbose: bool) -> str:
     return obj
 
 
-def build(verbose: bool = False) -> str:
-    """Compile and link; returns the path of libeot.so."""
+def build(verbose: bool = False, debug: bool = False) -> str:
+    """Compile and link; returns the path of libeot.so (debug: libeot_debug.so,
+    the kernels' bounds checks compiled in, see eot_debug_build)."""
+    lib = LIB_DEBUG if debug else LIB
     os.makedirs(OUT_DIR, exist_ok=True)
-    os.makedirs(OBJ_DIR, exist_ok=True)
+    os.makedirs(OBJ_DIR_DEBUG if debug else OBJ_DIR, exist_ok=True)
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
-    tmp = LIB + ".tmp"
+        objs = list(ex.map(lambda s: _compile(s, verbose, debug), srcs))
+    tmp = lib + ".tmp"
     # -ldl: the NVTX v3 header finds a profiler's injection library with dlopen
     cmd = [_nvcc(), "-shared"] + ARCH + ["-o", tmp] + objs + ["-ldl"]
     if verbose:
@@ -68,9 +73,9 @@ def build(verbose: bool = False) -> str:
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv))
+    print(build(verbose="-v" in sys.argv, debug="--debug" in sys.argv))

@@ -72,6 +72,7 @@ template <int K>
 __global__ void __launch_bounds__(kThreads) rowacc_kernel(AccArgs args) {
   pdl_enter();
   if (args.skip && *args.skip) return;
+  if (!EOT_CHECK(args.k >= 1 && args.k <= K, 501)) return;
   const Prob& P = *args.P;
   const float* __restrict__ cA = P.cs[args.gbuf].A;
   const float* __restrict__ cAL = P.cs[args.gbuf].AL;
@@ -314,5 +315,7 @@ cudaError_t launch_wtw_reduce(const AccArgs& a, double* WtW, double* gw, cudaStr
   launch_pdl(wtw_reduce_kernel, dim3((cnt + 31) / 32), dim3(256), 0, s, a, WtW, gw);
   return cudaGetLastError();
 }
+
+EOT_DEBUG_UNIT(accum)
 
 }  // namespace eotk

@@ -49,6 +49,25 @@ struct NvtxRange {
   NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
+// ---- debug words of the kernel units (-DEOT_DEBUG; 0 otherwise) ----------
+unsigned debug_site_small(bool reset);
+unsigned debug_site_stream(bool reset);
+unsigned debug_site_passes(bool reset);
+unsigned debug_site_mma(bool reset);
+unsigned debug_site_accum(bool reset);
+unsigned debug_site_batch(bool reset);
+// The first failed device bounds check of any unit since the last call (0:
+// none, always 0 without EOT_DEBUG); the words are reset.
+static unsigned debug_sites() {
+  unsigned v = 0;
+  for (auto fn : {debug_site_small, debug_site_stream, debug_site_passes, debug_site_mma,
+                  debug_site_accum, debug_site_batch}) {
+    const unsigned s = fn(true);
+    if (!v) v = s;
+  }
+  return v;
+}
+
 // ---- kernels defined in the other translation units ----------------------
 cudaError_t launch_col_pass(const Prob* dP, const Prob& hP, int mode, cudaStream_t s);
 cudaError_t launch_row_pass(const Prob* dP, const Prob& hP, int mode, cudaStream_t s);
@@ -1574,6 +1593,8 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   }
   CUDA_TRY(cudaEventSynchronize(ev1));
   CUDA_TRY(cudaGetLastError());
+  if (const unsigned ds = debug_sites())
+    return fail(EOT_ECUDA, "device bounds check failed at site " + std::to_string(ds));
   for (size_t k = 0; k < hvo.size(); ++k) pr->V_out[k] = (double)hvo[k];
   // ---- statistics ----
   eot_result r{};
@@ -2305,6 +2326,8 @@ static eot_status run_batch(int count, const eot_problem* probs, const eot_optio
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (kernel_ms) *kernel_ms = ms;
+  if (const unsigned ds = debug_sites())
+    return fail(EOT_ECUDA, "device bounds check failed at site " + std::to_string(ds));
   for (int k = 0; k < count; ++k) {
     if (!pl[k].ok) {
       rs[k] = eot_result{};
@@ -2435,6 +2458,14 @@ const char* eot_last_error(void) { return t_err.c_str(); }
 
 const char* eot_version(void) { return "eot-gb300 0.1 (sm_103a)"; }
 
+int32_t eot_debug_build(void) {
+#ifdef EOT_DEBUG
+  return 1;
+#else
+  return 0;
+#endif
+}
+
 }  // extern "C"
 
 // ===========================================================================
@@ -2520,6 +2551,8 @@ static eot_status standalone_finish(cudaStream_t s, void* user_stream) {
   }
   CUDA_TRY(cudaStreamSynchronize(s));
   CUDA_TRY(cudaGetLastError());
+  if (const unsigned ds = debug_sites())
+    return fail(EOT_ECUDA, "device bounds check failed at site " + std::to_string(ds));
   return EOT_OK;
 }
 

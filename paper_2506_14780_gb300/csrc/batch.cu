@@ -300,7 +300,7 @@ __device__ __forceinline__ void brow_pass(const BatchTask& T, int r0, int r1, in
         const float s2 = __shfl_xor_sync(0xffffffffu, ss, o);
         lse2_merge(rf, ss, r2, s2);
       }
-      if (sub == 0) {
+      if (sub == 0 && EOT_CHECK(lr < 256, 602)) {
         sh.rref[buf][lr] = rf;
         sh.rsum[buf][lr] = ss;
       }
@@ -747,6 +747,7 @@ __global__ void __launch_bounds__(kBThreads, 2) batch_sk_kernel(const BatchTask*
     if (s >= nslots) return;
     const int2 e = slots[s];
     const BatchTask& T = tasks[e.x];
+    if (!EOT_CHECK(e.y >= 0 && e.y < T.G && T.G <= kBMaxGang, 601)) continue;
     switch (T.tile) {
       case 1: brun_task<1>(T, e.y, sh); break;
       case 2: brun_task<2>(T, e.y, sh); break;
@@ -886,5 +887,7 @@ cudaError_t launch_batch_sk(const BatchTask* d_tasks, const int2* d_slots, int n
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, batch_sk_kernel, d_tasks, d_slots, nslots, d_next);
 }
+
+EOT_DEBUG_UNIT(batch)
 
 }  // namespace eotk

@@ -222,7 +222,48 @@ struct AccArgs {
   const int* skip;       // products: nonzero *skip makes the launch return at once (NULL: run)
 };
 
+// Debug build (-DEOT_DEBUG): a bounds check that fails records its site
+// number (100 x unit + k) in its translation unit's debug word, the first
+// failure winning, and the access it guards is skipped; the host reads every
+// unit's word after a call (debug_site_<unit>, declared in api.cu) and fails
+// the call with the site.  Without EOT_DEBUG a check is the constant true and
+// the accessors return 0.
+#ifdef EOT_DEBUG
 #ifdef __CUDACC__
+static __device__ unsigned g_eot_dbg_site;
+__device__ __forceinline__ bool eot_check(bool ok, unsigned site) {
+  if (!ok) atomicCAS(&g_eot_dbg_site, 0u, site);
+  return ok;
+}
+#define EOT_CHECK(cond, site) ::eotk::eot_check((cond), (site))
+#define EOT_DEBUG_UNIT(name)                                                   \
+  unsigned debug_site_##name(bool reset) {                                     \
+    unsigned v = 0;                                                            \
+    if (cudaMemcpyFromSymbol(&v, g_eot_dbg_site, sizeof(v)) != cudaSuccess) {  \
+      cudaGetLastError();                                                      \
+      return 0u;                                                               \
+    }                                                                          \
+    if (reset && v) {                                                          \
+      const unsigned z = 0;                                                    \
+      cudaMemcpyToSymbol(g_eot_dbg_site, &z, sizeof(z));                       \
+    }                                                                          \
+    return v;                                                                  \
+  }
+#endif
+#else
+#define EOT_CHECK(cond, site) true
+#define EOT_DEBUG_UNIT(name) \
+  unsigned debug_site_##name(bool) { return 0u; }
+#endif
+
+#ifdef __CUDACC__
+// Bytes of dynamic shared memory the running kernel was launched with.
+__device__ __forceinline__ unsigned dyn_smem_bytes() {
+  unsigned v;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(v));
+  return v;
+}
+
 // Iteration trace, written by the one thread that takes iteration `iter`'s
 // stop decision: a new record (the oldest is overwritten once trace_cap are
 // held); the Newton step of that iteration completes it (trace_trial).

@@ -42,6 +42,7 @@ __global__ void build_tiles_kernel(const float* __restrict__ Z, int n, int kk, i
                                    float* __restrict__ tiles, const int* __restrict__ skip) {
   pdl_enter();
   if (skip && *skip) return;
+  if (!EOT_CHECK(kk >= 1 && kk <= NN, 201)) return;
   const int nch = (n + kMmaKC - 1) / kMmaKC;
   const long total = (long)nch * NN * kMmaKC;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
@@ -500,6 +501,7 @@ __global__ void __launch_bounds__(256) colmma_kernel(AccArgs args, const float* 
   const bool s4 = args.mode == ACC_S4;
   if (s4 && st->done) return;
   if (args.skip && *args.skip) return;
+  if (!EOT_CHECK(args.k >= 1 && args.k <= NN, 202)) return;
   const int fb = s4 ? st->cur_f : args.fbuf;
   const int gb = s4 ? st->cur_g : args.gbuf;
   const int dst_g = (st->cur_g + 1) % 3;
@@ -822,6 +824,7 @@ __global__ void __launch_bounds__(kTmThreads, 2)
   State* st = P.st;
   const bool s4 = !ROW && args.mode == ACC_S4;
   if (s4 && st->done) return;
+  if (!EOT_CHECK(args.k >= 1 && args.k <= NN, 203)) return;
   if (args.skip && *args.skip) return;   // uniform over the grid (and any cluster)
   const int fb = s4 ? st->cur_f : args.fbuf;
   const int gb = s4 ? st->cur_g : args.gbuf;
@@ -1253,5 +1256,7 @@ void init_mma_attributes() {
   set_tma_attr<48>();
   set_tma_attr<64>();
 }
+
+EOT_DEBUG_UNIT(mma)
 
 }  // namespace eotk

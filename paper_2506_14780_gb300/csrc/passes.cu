@@ -169,7 +169,8 @@ __global__ void __launch_bounds__(kThreads) col_pass_kernel(const Prob* __restri
       const float2 q = s_part[w][threadIdx.x];
       merge_d(R, Sd, q.x, q.y);
     }
-    if (j < m) P.part_col[(size_t)stripe * m + j] = make_float2(R, (float)Sd);
+    if (j < m && EOT_CHECK(stripe < P.nstripe, 401))
+      P.part_col[(size_t)stripe * m + j] = make_float2(R, (float)Sd);
   }
   __threadfence();
   __syncthreads();
@@ -875,5 +876,7 @@ cudaError_t launch_exp2_check(int count, const float* p, const float* q, int var
   exp2_check_kernel<<<grid, 256, 0, s>>>(count, p, q, variant, out);
   return cudaGetLastError();
 }
+
+EOT_DEBUG_UNIT(passes)
 
 }  // namespace eotk

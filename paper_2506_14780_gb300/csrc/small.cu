@@ -298,6 +298,7 @@ __global__ void __launch_bounds__(256) newton_kernel(const Prob* __restrict__ PP
   State* st = P.st;
   if (st->done) return;
   const int l = P.ell;
+  if (!EOT_CHECK(l >= 1 && l <= kMaxK, 103)) return;
   const int tid = threadIdx.x, lane = tid & 31;
   const int ty = tid >> 4, tx = tid & 15;          // 16 x 16 tiling of the assembly
   constexpr int kS = kMaxK + 1;                    // odd row stride
@@ -499,6 +500,7 @@ __global__ void __launch_bounds__(kEH * kEH) eig_small_kernel(int p, int l, int 
                                                               const int* __restrict__ skip) {
   pdl_enter();
   if (skip && *skip) return;
+  if (!EOT_CHECK(p >= 1 && p <= kMaxP && l <= p && 2 * (int)blockDim.x >= p, 104)) return;
   __shared__ float A0[kMaxP * kES];
   __shared__ float Q[kMaxP * kES];
   __shared__ __align__(16) float G[kMaxP * kES];
@@ -658,8 +660,10 @@ __global__ void __launch_bounds__(kEH * kEH) eig_small_kernel(int p, int l, int 
     }
     __syncthreads();
     for (int r = ty; r < p; r += nx)      // G = Q with the columns in descending order
-      for (int q = tx; q < p; q += nx) G[r * kES + q] = Q[r * kES + order[q]];
-    if (tid < p) theta_out[tid] = (double)th[order[tid]];
+      for (int q = tx; q < p; q += nx)
+        G[r * kES + q] = EOT_CHECK(order[q] >= 0 && order[q] < p, 101) ? Q[r * kES + order[q]] : 0.f;
+    if (tid < p && EOT_CHECK(order[tid] >= 0 && order[tid] < p, 102))
+      theta_out[tid] = (double)th[order[tid]];
     __syncthreads();
     for (int r = ty; r < p; r += nx)
       for (int q = tx; q < p; q += nx) {
@@ -806,6 +810,8 @@ __global__ void __launch_bounds__(256) apply_kernel(const float* __restrict__ X,
                                                     const int* __restrict__ skip) {
   pdl_enter();
   if (skip && *skip) return;
+  if (!EOT_CHECK(p >= 1 && p <= kMaxP && (unsigned)(p * p + 64 * p) * 4u <= dyn_smem_bytes(), 105))
+    return;
   extern __shared__ float sB[];
   float* sX = sB + p * p;   // [64][p]
   for (int e = threadIdx.x; e < p * p; e += blockDim.x) sB[e] = B[e];
@@ -867,6 +873,9 @@ __global__ void __launch_bounds__(256) ritz_kernel(const float* __restrict__ Z,
                                                    float* __restrict__ Y0, float* __restrict__ Y1,
                                                    double* __restrict__ sig) {
   pdl_enter();
+  if (!EOT_CHECK(p >= 1 && p <= kMaxP && l <= p &&
+                     (unsigned)(p * p + 2 * kRitzRows * p) * 4u <= dyn_smem_bytes(), 106))
+    return;
   extern __shared__ float sQ[];
   float* sZ = sQ + p * p;            // [16][p]
   float* sX = sZ + kRitzRows * p;    // [16][p]
@@ -1102,5 +1111,7 @@ __global__ void grad_weights_kernel(const Prob* __restrict__ PP, double* __restr
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < P.m; j += gridDim.x * blockDim.x)
     d[j] = -(double)expm1f(P.Lcol[j]);
 }
+
+EOT_DEBUG_UNIT(small)
 
 }  // namespace eotk

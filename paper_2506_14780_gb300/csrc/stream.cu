@@ -339,8 +339,8 @@ __device__ void st_consume(const Prob& P, const StGeom& g, const PassIo& io, StS
         R = sh.mr[0][tid];
         Sd = sh.ms[0][tid];
       }
-      if (idx < lim) part[((size_t)b * slots + ((int)blockIdx.x - kf)) * width + tid] =
-          f2(R, (float)Sd);
+      if (idx < lim && EOT_CHECK((int)blockIdx.x - kf >= 0 && (int)blockIdx.x - kf < slots, 301))
+        part[((size_t)b * slots + ((int)blockIdx.x - kf)) * width + tid] = f2(R, (float)Sd);
     }
     cons_sync();
     if (tid == 0 && arrive_count(&cnt[b]) == (unsigned)(nc - 1)) sh.pend[sh.npend++] = b;
@@ -876,5 +876,7 @@ cudaError_t launch_sk_coop(const Prob* dP, const Prob& hP, int max_body, cudaStr
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, sk_coop_kernel, dP, max_body);
 }
+
+EOT_DEBUG_UNIT(stream)
 
 }  // namespace eotk

@@ -14,7 +14,9 @@ from typing import Optional
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "libeot.so")
+# EOT_LIBRARY selects another build of the library (the bounds-checked
+# _lib/libeot_debug.so of build.build(debug=True)); the default is the release
+LIB_PATH = os.environ.get("EOT_LIBRARY") or os.path.join(_HERE, "_lib", "libeot.so")
 
 # ---- enums (eot.h) ----
 EOT_OK, EOT_NOT_CONVERGED, EOT_PENDING = 0, 1, 2
@@ -125,6 +127,7 @@ _SIGNATURES = {
                                    C.POINTER(C.c_int64)]),
     "eot_batch_tuning": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double),
                                    C.POINTER(C.c_double), _PTR, _PTR]),
+    "eot_debug_build": (C.c_int32, []),
     "eot_last_error": (C.c_char_p, []),
     "eot_version": (C.c_char_p, []),
 }

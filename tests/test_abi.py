@@ -66,3 +66,17 @@ def test_unimplemented_hessian_is_rejected(lib):
     st, _ = eot.eot_solve(p, o, np.zeros(5), np.zeros(4))
     assert st == eot.EOT_EINVAL
     assert "D_a" in eot.last_error()
+
+
+def test_debug_build_compiles_with_its_checks(lib):
+    """The bounds-checked build (-DEOT_DEBUG) compiles, exports the same
+    symbols and reports itself; the release build reports 0 (no device)."""
+    import ctypes
+    from paper_2506_14780_gb300 import build
+    assert lib.eot_debug_build() == 0
+    path = build.build(debug=True)
+    dbg = ctypes.CDLL(path)
+    for name in _declared():
+        assert hasattr(dbg, name), name
+    dbg.eot_debug_build.restype = ctypes.c_int32
+    assert dbg.eot_debug_build() == 1

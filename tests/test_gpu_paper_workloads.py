@@ -90,3 +90,40 @@ def test_single_cell_shapes(pkg, n, m):
     print(f"{n}x{m}: Sinkhorn {out[0]['total_iters']} iterations ({out[0]['seconds']*1e3:.1f} ms),"
           f" SK-NR(30) {out[30]['total_iters']} ({out[30]['seconds']*1e3:.1f} ms)")
     assert out[30]["total_iters"] < out[0]["total_iters"]
+
+
+def test_spectrum_concentrates_on_the_device(pkg):
+    """Sec. 3, spectral stability, through the library: the square against
+    the annulus (160 x 160, raw cost) solved at eps = 0.256 ... 0.016, then the
+    ten leading modes of Op(pi) o Op(pi)^T by the device's subspace iteration
+    (eot_spectral_modes).  Its rho_k^2 equal numpy.linalg.eigh of the dense
+    operator at the same pair; each grows as eps halves (towards 1), while the
+    leading three-mode subspace moves little (the oracle's pin of the same
+    claims: test_spectrum_concentrates_as_eps_decreases)."""
+    p = W.square_annulus(160, 160, seed=0)
+    C32 = O.sq_euclidean_cost(p.X, p.Y).astype(np.float32)
+    C = C32.astype(np.float64)
+    dev = lambda x: torch.as_tensor(np.ascontiguousarray(x)).cuda()
+    rho, modes = [], []
+    for eps in (0.256, 0.128, 0.064, 0.032, 0.016):
+        p.eps = eps
+        f, g, res = pkg.solve(p, tol=1e-6, max_iter=200000)
+        assert res["return_status"] == pkg.EOT_OK, res
+        V = torch.zeros((160, 10), dtype=torch.float64, device="cuda")
+        r2 = torch.zeros(10, dtype=torch.float64, device="cuda")
+        st, it, resid = pkg.eot_spectral_modes(160, 160, dev(C32), dev(f), dev(g), dev(p.a),
+                                               dev(p.b), eps, 10, 10, 1e-5, 500, False, V, r2)
+        assert st == pkg.EOT_OK and resid <= 1e-5, (eps, st, it, resid)
+        _, rd = O.spectral_modes_dense(f, g, C, p.a, p.b, eps, 10)
+        r2 = r2.cpu().numpy()
+        assert np.abs(r2 - rd).max() < 1e-5, (eps, r2, rd)
+        rho.append(r2)
+        modes.append(V.cpu().numpy())
+    rho = np.array(rho)
+    print("rho_k^2 (rows: eps 0.256 ... 0.016):", np.round(rho[:, :4], 4).tolist())
+    assert np.all(np.diff(rho, axis=0) > 0)
+    assert rho[-1, 0] > 0.9 and rho[0, 0] < 0.5
+    sa = np.sqrt(p.a)[:, None]
+    Qu, _ = np.linalg.qr(sa * modes[0][:, :3])
+    Qv, _ = np.linalg.qr(sa * modes[2][:, :3])
+    assert np.linalg.svd(Qu.T @ Qv, compute_uv=False).min() > 0.95
