@@ -429,12 +429,13 @@ def coop_half_step(pkg, torch, stream):
 
 
 # DRAM traffic of one S4 launch (mma_tma_kernel<32, 0>) at 16384^2 with l = 30:
-# dram__bytes_read.sum + dram__bytes_write.sum from an ncu capture (summarised
-# under profiles/), valid while the kernel's sources hash to the recorded
-# SHA-256; None until a capture of the current sources is recorded.
-S4_TRAFFIC_BYTES = None
+# dram__bytes_read.sum + dram__bytes_write.sum of the 8192^2 launch of an ncu
+# capture (`bench.py --case s4_8k`; 285,006,848 B, 1.062 x its 4 n m bytes,
+# profiles/mma_tma_kernel_s4_8192.md) scaled by the 4x elements of the 16384^2
+# launch; valid while the kernel's sources hash to the recorded SHA-256.
+S4_TRAFFIC_BYTES = 4 * 285006848
 S4_TRAFFIC_SOURCES = ("mma.cu", "tc.cuh", "eot_device.cuh", "eot_internal.h")
-S4_TRAFFIC_SHA256 = None
+S4_TRAFFIC_SHA256 = "b000e60774c4db88aadfb436f74dc5dc3d76e8a90db2c322e0de8f0c8ef69cf7"
 
 
 def s4_traffic():
@@ -460,10 +461,10 @@ def _sources_sha(files):
 # summarised in profiles/sk_coop_kernel_16384_traffic.md).  It describes the kernel
 # built from the sources it was taken on, identified by their SHA-256: after any change
 # to them the bench reports no traffic until the capture is taken again.
-COOP_TRAFFIC_BYTES = 1082074816
+COOP_TRAFFIC_BYTES = 1082535040
 COOP_TRAFFIC_SOURCES = ("stream.cu", "stream_common.cuh", "eot_device.cuh", "eot_internal.h",
                         "pass_common.cuh", "reduce.cuh", "tc.cuh")
-COOP_TRAFFIC_SHA256 = "32e1fef245c6f90a201e747fb2bcca04238352e6b1755253323fc921c36100f8"
+COOP_TRAFFIC_SHA256 = "7b87389493b74b86d65b33e1e932f5301bd16ae52ada8b00f5a7a9ed1b076090"
 
 
 def coop_traffic():
@@ -606,6 +607,7 @@ def paper_sec5(pkg):
     and static-mode protocols and the l sweep at eps = 0.25 from eps' = 1, and
     the single-cell shapes of Fig. 5.2 in R^30 (synthetic N(0, I)/8 clouds stand
     in for the data set), eps from 1 halving to 1/64, l = 30."""
+    import workloads
     out = {}
     p = workloads.gaussians_2d(200, seed=0)
 
