@@ -475,6 +475,21 @@ def _sources_sha(files):
     return h.hexdigest()
 
 
+# Pipe use of one on-the-fly-cost pass (gram_pass_kernel, 20000 x 30000 x 64)
+# from an ncu capture of `bench.py --case gram` (profiles/gram_pass_kernel_20000x30000_d64.md):
+# the tensor pipe's active cycles and the MUFU (xu) and FMA pipes' instruction
+# rates, as % of their sustained peaks; valid while the kernel's sources hash to
+# the recorded SHA-256.
+GRAM_PIPES = {"tensor_pipe_active_pct": 44.37, "mufu_xu_pipe_pct": 16.01, "fma_pipe_pct": 24.35,
+              "duration_us_cold": 449.9}
+GRAM_PIPES_SOURCES = ('gram.cu', 'eot_device.cuh', 'eot_internal.h', 'pass_common.cuh', 'reduce.cuh', 'stream_common.cuh', 'tc.cuh')
+GRAM_PIPES_SHA256 = "d5ad9d2fdbbbab3d81383a50df85249e4e3951e44616fa08aebd517399790ab8"
+
+
+def gram_pipes():
+    return GRAM_PIPES if _sources_sha(GRAM_PIPES_SOURCES) == GRAM_PIPES_SHA256 else None
+
+
 # DRAM traffic of one sk_coop_kernel half-step at 16384^2 (dram__bytes_read.sum +
 # dram__bytes_write.sum of one launch of four half-steps, divided by four; ncu capture
 # summarised in profiles/sk_coop_kernel_16384_traffic.md).  It describes the kernel
@@ -527,7 +542,8 @@ def extras(pkg, torch, stream):
         "tensor_peak_note": "TF32 peak = measured bf16 x (1.1 / 2.25) nominal ratio",
         "stored_cost_equivalent_gbs": round(4.0 * n3 * m3 / (pp * 1e-3) / 1e9, 1),
         "solve_ms": round(e0.elapsed_time(e1), 1), "status": r3["status_name"],
-        "total_iters": r3["total_iters"], "l1_marginal_own_cost": r3["l1_marginal"]}
+        "total_iters": r3["total_iters"], "l1_marginal_own_cost": r3["l1_marginal"],
+        "ncu_pipes": gram_pipes()}
     c3_pair = (c3.X, c3.Y, c3.a, c3.b, 1e-3, f3.cpu().numpy(), g3.cpu().numpy())
     del X3, Y3, f3, g3
     # c4: batch of problems of uneven size and eps (one call)
