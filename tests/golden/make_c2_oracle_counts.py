@@ -9,7 +9,8 @@ continuation 1e-1 -> 1e-3 by halving (Sec. 5), L1 marginal tolerance 1e-4 at
 the intermediate levels (warm starts) and 1e-6 at the last (Algorithm 4.1's
 stopping test), as the benchmark runs it; SK-NR(30) with the D_a Hessian,
 modes refreshed at every level by block subspace iteration (block 40, Ritz
-residual 1e-2, at most 100 steps, started from the previous level's modes);
+residual EIG_TOL = 5e-2 as the benchmark runs it, at most 100 steps, started
+from the previous level's modes);
 plain Sinkhorn on the same schedule.
 
 Calls only ``oracle`` and ``workloads``.  Run from the repository root:
@@ -29,6 +30,7 @@ import oracle as O  # noqa: E402
 import workloads as W  # noqa: E402
 
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "c2_oracle_counts.json")
+EIG_TOL = 5e-2
 
 
 def main():
@@ -36,7 +38,7 @@ def main():
     C = O.sq_euclidean_cost(prob.X, prob.Y, normalize=True).astype(np.float32).astype(np.float64)
     levels = O.eps_schedule(1e-1, 1e-3, 0.5)
     out = {"workload": "gaussian_mixture_4096x4096_d3 seed 0, float32 cost normalised to max 1",
-           "levels": levels, "tol": 1e-6, "level_tol": 1e-4}
+           "levels": levels, "tol": 1e-6, "level_tol": 1e-4, "eig_tol": EIG_TOL}
     for name, ell in (("sknr30", 30), ("sinkhorn", 0)):
         f = np.zeros(4096)
         V = None
@@ -52,7 +54,7 @@ def main():
                    "eig_iters": 0}
             if ell and t < len(levels) - 1:
                 V, _, it, _ = O.spectral_modes_subspace(res.f, res.g, C, prob.a, prob.b, e, ell,
-                                                        oversample=10, tol=1e-2, max_iter=100,
+                                                        oversample=10, tol=EIG_TOL, max_iter=100,
                                                         seed=t, V0=V)
                 row["eig_iters"] = it
             rows.append(row)
