@@ -950,7 +950,8 @@ def profile_case(name):
         prob = workloads.gaussian_mixture(N, M, seed=0, eps=EPS)
         for _ in range(2):
             _, _, res = pkg.solve(prob, tol=TOL, ell=ELL, eps_start=1e-1, max_iter=200000,
-                                  level_tol=LEVEL_TOL)
+                                  level_tol=LEVEL_TOL, oversample=10, eig_tol=EIG_TOL,
+                                  eig_max_iter=100)
     elif name == "batch":
         probs = workloads.batch_problems(512, seed=0)
         keepb = []
