@@ -232,7 +232,7 @@ def run_ours(args):
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": WORKLOAD, "n": N, "m": M, "d": 3, "eps": EPS, "tol": TOL,
                       "ell": ELL, "eps_schedule": "1e-1 x 0.5^k -> 1e-3 (8 levels)",
-                      "level_tol": LEVEL_TOL,
+                      "level_tol": LEVEL_TOL, "eig_tol": EIG_TOL, "oversample": 10,
                       "potentials": "f64 (exponents formed exactly, f32 exp/sums)",
                       "l2": "flushed between steps (512 MB write)",
                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"}}
@@ -901,7 +901,8 @@ def run_reference(args):
            "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "n": N, "m": M, "d": 3, "eps": EPS, "tol": TOL,
-                      "ell": ELL, "level_tol": LEVEL_TOL}, "impl": "reference",
+                      "ell": ELL, "level_tol": LEVEL_TOL, "eig_tol": EIG_TOL,
+                      "oversample": 10}, "impl": "reference",
            "cpu_baseline": cb,
            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
