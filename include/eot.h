@@ -153,6 +153,14 @@ typedef struct {
                                this degree that damps the spectrum below the block's
                                smallest Ritz value (eig_degree applications per step;
                                eig_max_iter counts Rayleigh-Ritz steps).  Default 0.  */
+    int32_t newton_solver;  /* solve of the projected Newton system (eps H_V) Delta =
+                               -eps grad_V of Algorithm 4.1 line 10: 0 (default), L D L^T
+                               factorisation; 1, conjugate gradients (Sec. 4 design
+                               remarks: the iterative solve, the form that parallelises
+                               over many problems): float32, stops at a relative residual
+                               of 1e-6 or after 10 l steps; a search direction of
+                               non-positive curvature rejects the step, as a failed
+                               factorisation does.  Other values: EOT_EINVAL.           */
 } eot_options;
 
 typedef struct {
@@ -392,12 +400,14 @@ typedef struct {
  * Outputs (device pointers, each optional): f_k (n), h (m), W (m x ell,
  * float32), grad (ell), GV (ell x ell), WtDW (ell x ell), delta (ell),
  * f_trial (n) and h_trial (m) (left untouched when newton_ok is 0); info
- * (host, optional).  Synchronises `stream` before it returns. */
+ * (host, optional).  newton_solver: the Newton system's solve, as
+ * eot_options.newton_solver (0: L D L^T, 1: conjugate gradients).
+ * Synchronises `stream` before it returns. */
 eot_status eot_sknr_step(int32_t n, int32_t m, int32_t ell, const float *C, const double *a,
                          const double *b, double eps, const double *g, const double *V,
                          double *f_k, double *h, float *W, double *grad, double *GV,
                          double *WtDW, double *delta, double *f_trial, double *h_trial,
-                         eot_sknr_info *info, void *stream);
+                         eot_sknr_info *info, int32_t newton_solver, void *stream);
 
 /* The tuning of eot_solve_batch on the current device, run on first use (the
  * first batch call runs it too): the gang cost model (step_ns, fix_ns, bar_ns;

@@ -85,7 +85,7 @@ int rowacc_rows(int k);
 void init_acc_attributes();
 cudaError_t launch_wtw_reduce(const AccArgs& a, double* WtW, double* gw, cudaStream_t s);
 cudaError_t launch_newton(const Prob* dP, const AccArgs& a, double* WtW, double* gw,
-                          cudaStream_t s);
+                          cudaStream_t s, int cg);
 cudaError_t launch_colmma(const AccArgs& a, const Prob& hP, const float* tiles, int ncolblk,
                           cudaStream_t s);
 cudaError_t launch_build_tiles(const float* Z, int n, int kk, float* tiles, cudaStream_t s,
@@ -758,6 +758,17 @@ struct Solver {
   // The captured graphs bake in the choice between the staged (tensor-map)
   // kernels and the others: drop them when that choice changes.
   int graph_tma = -1;
+  // Newton system solver baked into the captured SK-NR loop body (a kernel
+  // argument): 0 L D L^T, 1 conjugate gradients
+  int newton_cg = 0;
+  void use_newton_solver(int cg) {
+    if (cg == newton_cg) return;
+    if (ex_sknr) cudaGraphExecDestroy(ex_sknr);
+    if (gr_sknr) cudaGraphDestroy(gr_sknr);
+    ex_sknr = nullptr;
+    gr_sknr = nullptr;
+    newton_cg = cg;
+  }
   void match_graphs_to_cost() {
     const int want = hP.has_tmC ? 1 : 0;
     if (graph_tma == want) return;
@@ -808,7 +819,7 @@ struct Solver {
       if (e == cudaSuccess)
         e = f64 ? launch_col64(dP, hP, MODE_S4, a, s) : launch_colmma(a, hP, tilesV, mm_ncolblk, s);
       if (e != cudaSuccess) break;
-      e = launch_newton(dP, a, WtW, gw, s);
+      e = launch_newton(dP, a, WtW, gw, s, newton_cg);
       if (e != cudaSuccess) break;
       launch_pdl(fprime_kernel, dim3(std::min(ceil_div(n, 256), 4 * ctx->nsm)), dim3(256), 0, s, dP);
       e = pass_col(MODE_TRIAL, s);
@@ -1118,6 +1129,8 @@ static eot_status validate(const eot_problem* pr, const eot_options* o) {
     return fail(EOT_EINVAL, "eig_degree must be in [0, 8]");
   if ((pr->V_init || pr->V_out) && o->ell == 0)
     return fail(EOT_EINVAL, "V_init and V_out need ell > 0");
+  if (o->newton_solver != 0 && o->newton_solver != 1)
+    return fail(EOT_EINVAL, "newton_solver must be 0 (L D L^T) or 1 (conjugate gradients)");
   if ((long long)pr->n * pr->m > (1ll << 34)) return fail(EOT_EINVAL, "n*m too large");
   return EOT_OK;
 }
@@ -1377,6 +1390,7 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
   }
   // ---- graphs (captured once per solver and kernel choice) ----
   S->match_graphs_to_cost();
+  S->use_newton_solver(o->newton_solver == 1 ? 1 : 0);
   if (!S->ex_sk) {
     eot_status e = S->build_loop([&](cudaStream_t cs_) { return S->body_sk(cs_); }, 0, &S->gr_sk,
                                  &S->ex_sk);
@@ -2903,8 +2917,10 @@ eot_status eot_sknr_step(int32_t n, int32_t m, int32_t ell, const float* C, cons
                          const double* b, double eps, const double* g, const double* V,
                          double* f_k, double* h, float* W, double* grad, double* GV,
                          double* WtDW, double* delta, double* f_trial, double* h_trial,
-                         eot_sknr_info* info, void* stream) {
+                         eot_sknr_info* info, int32_t newton_solver, void* stream) {
   if (!C || !a || !b || !g || !V) return fail(EOT_EINVAL, "C, a, b, g and V are required");
+  if (newton_solver != 0 && newton_solver != 1)
+    return fail(EOT_EINVAL, "newton_solver must be 0 (L D L^T) or 1 (conjugate gradients)");
   if (n < 3 || m < 1) return fail(EOT_EINVAL, "need n >= 3 and m >= 1");
   if (ell < 1 || ell + 1 > kMaxP || ell >= n) return fail(EOT_EINVAL, "need 1 <= ell <= 47, ell < n");
   if (!finite_pos(eps)) return fail(EOT_EINVAL, "eps must be finite and > 0");
@@ -2955,7 +2971,7 @@ eot_status eot_sknr_step(int32_t n, int32_t m, int32_t ell, const float* C, cons
   CUDA_TRY(cudaMemcpyAsync(S->stats + 6, &S->dSt->nr_degenerate, sizeof(int),
                            cudaMemcpyDeviceToDevice, s));
   CUDA_TRY(cudaEventRecord(ev[2], s));
-  CUDA_TRY(launch_newton(S->dP, acc, S->WtW, S->gw, s));
+  CUDA_TRY(launch_newton(S->dP, acc, S->WtW, S->gw, s, newton_solver));
   launch_pdl(fprime_kernel, dim3(std::min(ceil_div(n, 256), 4 * S->ctx->nsm)), dim3(256), 0, s, S->dP);
   CUDA_TRY(cudaEventRecord(ev[3], s));
   CUDA_TRY(S->pass_col(MODE_TRIAL, s));

@@ -278,6 +278,55 @@ __device__ void ldlt_blocked(float* H, int S, int p, int rows, float* inv, int* 
   }
 }
 
+// Conjugate gradients (Hestenes-Stiefel) for A x = rhs, A the symmetric l x l
+// matrix held by its lower triangle in H (row stride kS), rhs in row l of H:
+// float32, by the 64 threads of warps 0 and 1 (thread t holds entry t), the
+// dot products summed per warp and then over the two warps in order (named
+// barrier 1).  Stops at a relative residual of 1e-6 or after 10 l steps;
+// returns false when a search direction has non-positive curvature
+// p^T A p <= 0 (A is not positive definite along it).  x (shared, l) gets
+// the iterate.  Uniform control flow over the 64 threads.
+__device__ __forceinline__ void bar64() { asm volatile("bar.sync 1, 64;" ::: "memory"); }
+__device__ float cg_dot64(float v, float* red2) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red2[threadIdx.x >> 5] = v;
+  bar64();
+  const float t = red2[0] + red2[1];
+  bar64();
+  return t;
+}
+__device__ bool cg_solve64(const float* H, int kS, int l, float* x, float* sp, float* red2) {
+  const int t = threadIdx.x;
+  float rv = t < l ? H[l * kS + t] : 0.f, pv = rv, xv = 0.f;
+  if (t < 64) sp[t] = pv;
+  float rr = cg_dot64(rv * rv, red2);
+  const float stop = 1e-12f * fmaxf(rr, 1e-30f);
+  bool ok = true;
+  for (int it = 0; it < 10 * l && rr > stop; ++it) {
+    float ap = 0.f;
+    if (t < l)
+      for (int c = 0; c < l; ++c)
+        ap = __fmaf_rn(c <= t ? H[t * kS + c] : H[c * kS + t], sp[c], ap);
+    const float curv = cg_dot64(pv * ap, red2);   // its barriers end the reads of sp
+    if (!(curv > 0.f)) {
+      ok = false;
+      break;
+    }
+    const float alpha = rr / curv;
+    xv = __fmaf_rn(alpha, pv, xv);
+    rv = __fmaf_rn(-alpha, ap, rv);
+    const float rrn = cg_dot64(rv * rv, red2);
+    pv = __fmaf_rn(rrn / rr, pv, rv);
+    rr = rrn;
+    if (t < 64) sp[t] = pv;
+    bar64();
+  }
+  if (t < l) x[t] = xv;
+  bar64();
+  return ok;
+}
+
 // ---------------------------------------------------------------------------
 // Newton step on V (one CTA of 256 threads).  GV = V^T D_a V (or V^T D_r V),
 // WtW = sum_j W_j W_j^T / b_j, gw = sum_j d_j W_j (d_j = -expm1(L_j)),
@@ -288,11 +337,13 @@ __device__ void ldlt_blocked(float* H, int S, int p, int rows, float* inv, int* 
 // substitution of grad_V = -gw riding along as an extra row;
 // Delta = (-H_V)^{-1} grad_V = eps (GV - WtW)^{-1} grad_V.  A pivot that is not
 // positive (the restricted Hessian is not negative definite) rejects the step.
+// With cg != 0 the system is solved by conjugate gradients (cg_solve64)
+// instead of the factorisation; non-positive curvature rejects the step.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) newton_kernel(const Prob* __restrict__ PP,
                                                      const double* __restrict__ WtW,
                                                      const double* __restrict__ gw,
-                                                     const double* __restrict__ Dr) {
+                                                     const double* __restrict__ Dr, int cg) {
   pdl_enter();
   const Prob& P = *PP;
   State* st = P.st;
@@ -316,19 +367,28 @@ __global__ void __launch_bounds__(256) newton_kernel(const Prob* __restrict__ PP
     }
   for (int k = tid; k < l; k += 256) H[l * kS + k] = (float)(-gw[k]);
   __syncthreads();
-  // elimination (8 pivots per pair of barriers): H[r][k] = L_rk D_k (r > k),
-  // H[k][k] = D_k, and row l holds the forward-substituted right-hand side
-  ldlt_blocked<8>(H, kS, l, l + 1, s_inv, &s_fail, 0.f, true);
-  if (tid >= 32) return;
-  for (int k = lane; k < l; k += 32) g[k] = H[l * kS + k];
-  __syncwarp();
-  // D z = y, then L^T x = z (column oriented, lanes over rows)
-  for (int k = lane; k < l; k += 32) g[k] = s_fail ? 0.f : g[k] * s_inv[k];
-  __syncwarp();
-  for (int k = l - 1; k >= 0; --k) {
-    const float xk = g[k];
-    for (int i = lane; i < k; i += 32) g[i] = __fmaf_rn(-H[k * kS + i] * s_inv[i], xk, g[i]);
+  if (cg) {
+    __shared__ float s_p[64], s_red2[2];
+    if (tid >= 64) return;
+    const bool ok = cg_solve64(H, kS, l, g, s_p, s_red2);
+    if (tid >= 32) return;
+    if (lane == 0 && !ok) s_fail = 1;
     __syncwarp();
+  } else {
+    // elimination (8 pivots per pair of barriers): H[r][k] = L_rk D_k (r > k),
+    // H[k][k] = D_k, and row l holds the forward-substituted right-hand side
+    ldlt_blocked<8>(H, kS, l, l + 1, s_inv, &s_fail, 0.f, true);
+    if (tid >= 32) return;
+    for (int k = lane; k < l; k += 32) g[k] = H[l * kS + k];
+    __syncwarp();
+    // D z = y, then L^T x = z (column oriented, lanes over rows)
+    for (int k = lane; k < l; k += 32) g[k] = s_fail ? 0.f : g[k] * s_inv[k];
+    __syncwarp();
+    for (int k = l - 1; k >= 0; --k) {
+      const float xk = g[k];
+      for (int i = lane; i < k; i += 32) g[i] = __fmaf_rn(-H[k * kS + i] * s_inv[i], xk, g[i]);
+      __syncwarp();
+    }
   }
   double dva = 0.0;
   bool finite = true;
@@ -357,10 +417,10 @@ __global__ void __launch_bounds__(256) newton_kernel(const Prob* __restrict__ PP
 }
 
 cudaError_t launch_newton(const Prob* dP, const AccArgs& a, double* WtW, double* gw,
-                          cudaStream_t s) {
+                          cudaStream_t s, int cg) {
   cudaError_t e = launch_wtw_reduce(a, WtW, gw, s);
   if (e != cudaSuccess) return e;
-  launch_pdl(newton_kernel, dim3(1), dim3(256), 0, s, dP, WtW, gw, nullptr);
+  launch_pdl(newton_kernel, dim3(1), dim3(256), 0, s, dP, WtW, gw, nullptr, cg);
   return cudaGetLastError();
 }
 

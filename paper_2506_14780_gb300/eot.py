@@ -46,7 +46,7 @@ class eot_options(C.Structure):
                 ("eig_tol", C.c_double), ("eig_max_iter", C.c_int32), ("prec", C.c_int32),
                 ("hessian", C.c_int32), ("poll_every", C.c_int32), ("stream", C.c_void_p),
                 ("wait_limit_s", C.c_double), ("stall_window", C.c_int32),
-                ("eig_degree", C.c_int32)]
+                ("eig_degree", C.c_int32), ("newton_solver", C.c_int32)]
 
 
 class eot_result(C.Structure):
@@ -121,7 +121,7 @@ _SIGNATURES = {
     "eot_exp2": (C.c_int, [C.c_int32, _PTR, _PTR, C.c_int32, _PTR, _PTR]),
     "eot_sknr_step": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, _PTR, _PTR, _PTR, C.c_double,
                                 _PTR, _PTR, _PTR, _PTR, _PTR, _PTR, _PTR, _PTR, _PTR, _PTR,
-                                _PTR, C.POINTER(eot_sknr_info), _PTR]),
+                                _PTR, C.POINTER(eot_sknr_info), C.c_int32, _PTR]),
     "eot_solve_traced": (C.c_int, [C.POINTER(eot_problem), C.POINTER(eot_options), _PTR, _PTR,
                                    C.POINTER(eot_result), _PTR, C.c_int32,
                                    C.POINTER(C.c_int64)]),
@@ -399,7 +399,8 @@ def eot_exp2(p, q, variant: int, out, stream=None) -> int:
 
 
 def eot_sknr_step(n, m, ell, Cdev, a, b, eps, g, V, f_k=None, h=None, W=None, grad=None,
-                  GV=None, WtDW=None, delta=None, f_trial=None, h_trial=None, stream=None):
+                  GV=None, WtDW=None, delta=None, f_trial=None, h_trial=None, stream=None,
+                  newton_solver=0):
     """One SK-NR iteration from g with modes V (device tensors; outputs are
     optional device tensors).  Returns (status, info dict)."""
     info = eot_sknr_info()
@@ -410,7 +411,7 @@ def eot_sknr_step(n, m, ell, Cdev, a, b, eps, g, V, f_k=None, h=None, W=None, gr
     st = load().eot_sknr_step(n, m, ell, Cdev.data_ptr(), a.data_ptr(), b.data_ptr(),
                               float(eps), g.data_ptr(), V.data_ptr(), ptr(f_k), ptr(h), ptr(W),
                               ptr(grad), ptr(GV), ptr(WtDW), ptr(delta), ptr(f_trial),
-                              ptr(h_trial), C.byref(info), stream)
+                              ptr(h_trial), C.byref(info), int(newton_solver), stream)
     d = {k: getattr(info, k) for k, _ in info._fields_}
     d["stage_seconds"] = list(info.stage_seconds)
     return st, d

@@ -60,7 +60,7 @@ def _dev(x, dtype=None):
     return (t if dtype is None else t.to(dtype)).cuda()
 
 
-def _step(pkg, C32, a, b, eps, g, V32):
+def _step(pkg, C32, a, b, eps, g, V32, newton_solver=0):
     n, m = C32.shape
     ell = V32.shape[1]
     z = lambda k: torch.zeros(k, dtype=torch.float64, device="cuda")  # noqa: E731
@@ -69,18 +69,24 @@ def _step(pkg, C32, a, b, eps, g, V32):
            "WtDW": torch.zeros((ell, ell), dtype=torch.float64, device="cuda"),
            "delta": z(ell), "f_trial": z(n), "h_trial": z(m)}
     st, info = pkg.eot_sknr_step(n, m, ell, _dev(C32), _dev(a), _dev(b), eps, _dev(g), _dev(V32),
-                                 **out)
+                                 newton_solver=newton_solver, **out)
     assert st == pkg.EOT_OK, pkg.last_error()
     return {k: v.cpu().numpy().astype(np.float64) for k, v in out.items()}, info
 
 
-def _compare(pkg, C32, a, b, eps, g, V32):
+def _compare(pkg, C32, a, b, eps, g, V32, newton_solver=0):
     """Run one device step and the oracle's from the same (g, V); assert every
-    bound; return the oracle's step (for chaining) and a short report."""
+    bound; return the oracle's step (for chaining) and a short report.
+    newton_solver 1: both solve the Newton system by conjugate gradients (the
+    device in float32 to a relative residual of 1e-6, which bounds its error by
+    kappa 1e-6 like the factorisation's rounding; 1e-5 allows for the
+    residual's float32 floor)."""
     C = C32.astype(np.float64)
-    d, info = _step(pkg, C32, a, b, eps, g, V32)
+    d, info = _step(pkg, C32, a, b, eps, g, V32, newton_solver)
     f_k = O.c_transform_g(g, C, b, eps)
-    o = O.newton_step(f_k, C, a, b, eps, V32, hessian="diag_alpha")
+    o = O.newton_step(f_k, C, a, b, eps, V32, hessian="diag_alpha",
+                      newton="cg" if newton_solver else "direct")
+    solve_tol = 1e-5 if newton_solver else 1e-6
     rep = {}
     # line 4 and the column transform at f_k
     e_f = np.abs(d["f_k"] - f_k).max()
@@ -116,7 +122,7 @@ def _compare(pkg, C32, a, b, eps, g, V32):
     if not o["ok"]:
         return o, rep
     if kappa * rA < 0.5:
-        tol_d = kappa * (rA + rg) / (1.0 - kappa * rA) + kappa * 1e-6
+        tol_d = kappa * (rA + rg) / (1.0 - kappa * rA) + kappa * solve_tol
         e_d = np.linalg.norm(d["delta"] - o["delta"]) / np.linalg.norm(o["delta"])
         assert e_d <= tol_d, (e_d, tol_d, kappa)
         rep.update(kappa=kappa, e_delta=e_d)
@@ -158,6 +164,48 @@ def test_sknr_step_matches_oracle_512(pkg):
         accepted += bool(o["accepted"])
         g = o["h_trial"] if o["ok"] and o["accepted"] else o["h"]
     assert accepted >= 1
+
+
+def test_sknr_step_conjugate_gradients_512(pkg):
+    """The Newton system solved by conjugate gradients on the device
+    (newton_solver = 1) against the oracle's newton_cg (Sec. 4 design
+    remarks), on the same three iterations as the factorised test."""
+    prob = W.gaussian_mixture(512, 512, seed=0, eps=1e-3)
+    C32 = O.sq_euclidean_cost(prob.X, prob.Y, normalize=True).astype(np.float32)
+    C = C32.astype(np.float64)
+    a, b = prob.a, prob.b
+    prev = O.continuation(C, a, b, 2e-3, tol=1e-6, eps_start=1e-1, ell=0, level_tol=1e-4)
+    V, _ = O.spectral_modes_dense(prev.f, prev.g, C, a, b, 2e-3, 30)
+    V32 = _modes32(V)
+    eps = 1e-3
+    g = O.sinkhorn(C, a, b, eps, tol=3e-3, max_iter=10000, f0=prev.f).g
+    accepted = 0
+    for k in range(3):
+        o, rep = _compare(pkg, C32, a, b, eps, g, V32, newton_solver=1)
+        print(f"512^2 CG step {k}: {rep}")
+        accepted += bool(o["accepted"])
+        g = o["h_trial"] if o["ok"] and o["accepted"] else o["h"]
+    assert accepted >= 1
+
+
+def test_solve_with_conjugate_gradients(pkg):
+    """SK-NR(20) solves with the Newton system by conjugate gradients reach the
+    tolerance (the oracle's float64 evaluation) in about as many iterations as
+    with the factorisation; an unknown solver is rejected."""
+    prob = W.gaussian_mixture(512, 640, seed=21, eps=5e-3)
+    C = O.sq_euclidean_cost(prob.X, prob.Y, normalize=True).astype(np.float32).astype(np.float64)
+    out = {}
+    for ns in (0, 1):
+        f, g, res = pkg.solve(prob, tol=1e-6, max_iter=100000, ell=20, eps_start=1e-1,
+                              newton_solver=ns)
+        assert res["return_status"] == pkg.EOT_OK, res
+        assert O.evaluate(f, g, C, prob.a, prob.b, prob.eps)["l1"] <= 1e-6
+        out[ns] = res
+    print({ns: (r["total_iters"], r["nr_accepted"], r["nr_rejected"]) for ns, r in out.items()})
+    assert out[1]["nr_accepted"] >= 1
+    assert out[1]["total_iters"] <= 1.5 * out[0]["total_iters"] + 5, out
+    _, _, bad = pkg.solve(prob, tol=1e-6, ell=20, newton_solver=2)
+    assert bad["return_status"] == pkg.EOT_EINVAL
 
 
 def test_sknr_step_matches_oracle_4096(pkg):
