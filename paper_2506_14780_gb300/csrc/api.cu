@@ -1454,17 +1454,20 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
     have_modes = true;
     return EOT_OK;
   };
-  if (V_start_dev) {
-    CUDA_TRY(cudaMemcpyAsync(S->V, V_start_dev, (size_t)n * ell * sizeof(float),
-                             cudaMemcpyDeviceToDevice, s));
-    have_modes = true;
-  } else if (!hvi.empty()) {
-    // V_init (columns scaled to unit root-mean-square on the host): made
-    // a-orthonormal and orthogonal to the constants in column order, Z =
+  if (V_start_dev || !hvi.empty()) {
+    // the first level's modes: V_init (columns scaled to unit root-mean-square
+    // on the host) or the server's resident modes of the cloud (computed for
+    // the weights of an earlier request), made a-orthonormal and orthogonal to
+    // the constants for this problem's weights in column order, Z =
     // (V - 1 c^T) L^{-T} with L L^T = V^T D_a V - c c^T, c = V^T a; a column
     // whose remaining squared a-norm is below 1e-5 of the largest pivot
     // becomes zero (eig_small mode 3)
-    CUDA_TRY(cudaMemcpyAsync(S->V, hvi.data(), hvi.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    if (V_start_dev)
+      CUDA_TRY(cudaMemcpyAsync(S->V, V_start_dev, (size_t)n * ell * sizeof(float),
+                               cudaMemcpyDeviceToDevice, s));
+    else
+      CUDA_TRY(cudaMemcpyAsync(S->V, hvi.data(), hvi.size() * sizeof(float),
+                               cudaMemcpyHostToDevice, s));
     init_block_kernel<<<std::min(ceil_div((long long)n * S->p, 256), 8 * ctx->nsm), 256, 0, s>>>(
         S->Xb, n, S->p, 0x5EEDull + 977ull * (unsigned long long)L, S->V, ell, 0);
     launch_eig_gram(S->Xb, nullptr, P.a, n, S->p, S->eppart, S->GXX, nullptr, S->cvec, s);
@@ -1654,7 +1657,7 @@ static eot_status solve_one(const eot_problem* pr, const eot_options* o, double*
     launches += 1 + 3 + 1 + 1 + 1 + (long long)hLev[2 * L].body_runs * S->eig_body_launches() + 1 +
                 (dev ? 1 : 0);
   }
-  if (!hvi.empty()) launches += 6;   // V_init: start block, Gram (2), Cholesky, apply, copy
+  if (V_start_dev || !hvi.empty()) launches += 6;   // given modes: start block, Gram (2), Cholesky, apply, copy
   if (ginit) launches += 1;          // the row half-step of g_init
   launches += 5 + 2LL * verify_rounds;
   launches += (long long)resumed_bodies * (lev_nr[L - 1] ? nr_body * S->unroll_sknr + 1 : 2 * S->unroll_sk + 1);
