@@ -80,3 +80,34 @@ def test_debug_build_compiles_with_its_checks(lib):
         assert hasattr(dbg, name), name
     dbg.eot_debug_build.restype = ctypes.c_int32
     assert dbg.eot_debug_build() == 1
+
+
+def test_trace_record_layout_matches_the_header():
+    """eot_trace_rec (include/eot.h): four doubles then two int32, 40 bytes;
+    the binding's NumPy record must read it field by field."""
+    from paper_2506_14780_gb300 import eot
+    dt = eot.TRACE_DTYPE
+    assert dt.itemsize == 40
+    assert [dt.fields[k][1] for k in ("eps", "l1", "q_semi", "dq", "iter", "accepted")] == \
+        [0, 8, 16, 24, 32, 36]
+
+
+def test_warm_start_fields_and_output_checks(lib):
+    """eot_problem carries g_init, V_init and V_out after f_init; V_out must be
+    a writable C-contiguous float64 array (it is written in place)."""
+    import numpy as np
+    from paper_2506_14780_gb300 import eot
+    names = [n for n, _ in eot.eot_problem._fields_]
+    assert names[-4:] == ["f_init", "g_init", "V_init", "V_out"]
+    a = np.ones(4) / 4
+    C = np.zeros((4, 4), np.float32)
+    with pytest.raises(ValueError):
+        eot.make_problem(a, a, C=C, V_out=np.zeros((4, 2), np.float32))
+    with pytest.raises(ValueError):
+        eot.make_problem(a, a, C=C, V_out=np.zeros((2, 4)).T)
+    p = eot.make_problem(a, a, C=C, V_out=np.zeros((4, 2)), g_init=np.zeros(4))
+    assert p.V_out and p.g_init and not p.V_init
+    # an option of the Newton solve outside {0, 1} is rejected on the host
+    o = eot.default_options(ell=2, newton_solver=3)
+    st, _ = eot.eot_solve(eot.make_problem(a, a, C=C, eps=0.1), o, np.zeros(4), np.zeros(4))
+    assert st == eot.EOT_EINVAL and "newton_solver" in eot.last_error()
