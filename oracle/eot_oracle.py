@@ -631,13 +631,14 @@ def continuation(C, a, b, eps, tol: float = 1e-6, eps_start: float = 1e-1,
                  max_iter: int = 100000, level_tol: Optional[float] = None,
                  hessian: str = "exact", modes: str = "dense", oversample: int = 10,
                  eig_tol: float = 1e-6, eig_max_iter: int = 200, seed: int = 0,
-                 return_levels: bool = False):
+                 return_levels: bool = False, newton: str = "direct"):
     """eps-continuation with spectral warm start (Sec. 4 and Sec. 5, Fig. 5.1/5.2).
 
     Levels come from ``eps_schedule``.  Potentials are carried from level to
     level.  With l > 0 the modes V_l(eps') are computed at the converged
     potentials of a level and used at the next one: refreshed at every level
     (``sequential``) or computed once at the first level (static warm start).
+    ``newton`` selects the Newton system's solve in ``sknr`` ("direct" or "cg").
     """
     levels = eps_schedule(eps_start, eps, eps_factor)
     n = np.shape(C)[0]
@@ -649,7 +650,7 @@ def continuation(C, a, b, eps, tol: float = 1e-6, eps_start: float = 1e-1,
         last = t == len(levels) - 1
         tl = tol if (last or level_tol is None) else level_tol
         out = sknr(C, a, b, e, V if ell > 0 else None, tol=tl, max_iter=max_iter, f0=f,
-                   hessian=hessian)
+                   hessian=hessian, newton=newton)
         history.append({"eps": e, "iters": out.iters, "converged": out.converged,
                         "nr_accepted": out.nr_accepted, "nr_rejected": out.nr_rejected})
         f = out.f

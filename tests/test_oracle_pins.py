@@ -520,6 +520,24 @@ def test_sknr_with_cg_repeats_the_direct_newton():
     assert np.abs(r1.f - r2.f).max() <= 1e-9 * eps
 
 
+def test_static_mode_continuation_with_cg():
+    """The protocol of SK-NR over many problems: modes computed once, at the
+    first level (Sec. 5's static warm start), and the Newton system solved by
+    conjugate gradients (Sec. 4 design remarks) -- the continuation repeats
+    the direct solve's levels step for step (iterations, accepted and rejected
+    steps) and ends at the same potentials to rounding."""
+    p = W.gaussian_mixture(120, 110, seed=8)
+    C = O.sq_euclidean_cost(p.X, p.Y, normalize=True)
+    kw = dict(tol=2e-6, eps_start=4e-2, ell=10, sequential=False, hessian="diag_alpha",
+              level_tol=1e-4, return_levels=True)
+    r1, h1 = O.continuation(C, p.a, p.b, 5e-3, **kw)
+    r2, h2 = O.continuation(C, p.a, p.b, 5e-3, newton="cg", **kw)
+    steps = lambda h: [(x["iters"], x["nr_accepted"], x["nr_rejected"]) for x in h]  # noqa: E731
+    assert steps(h1) == steps(h2), (steps(h1), steps(h2))
+    assert sum(x["nr_accepted"] for x in h1) >= 1
+    assert r1.converged and np.abs(r1.f - r2.f).max() <= 1e-9 * 5e-3
+
+
 def test_chebyshev_filtered_subspace_iteration():
     """The Chebyshev-filtered spectral step against numpy.linalg.eigh (same
     Ritz values and subspace as the dense eigendecomposition), and its reason
